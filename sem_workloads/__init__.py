@@ -1,0 +1,213 @@
+"""Seeded synthetic workloads for the σ-transformed SEM wave model.
+
+This module only builds inputs: mesh parameters, still-water depth h(x) at
+the mesh columns, and initial free-surface states (η, φ̃).  It holds none of
+the method's arithmetic (no basis, no operator, no solver), so both the CPU
+oracle and the CUDA library can be fed from it without sharing code.
+
+Node layout used by every array here: the mesh has ``Ncol`` columns
+(``Nx*P`` when periodic, ``Nx*P+1`` between walls); column ``ix`` sits at
+the GLL node ``a = ix - P*ex`` of x-element ``ex``.  Column positions are
+returned by :func:`column_x`, which needs the GLL nodes and therefore takes
+them as an argument (callers pass their own).
+
+Workloads (paper §4.2 linear theory, §4.3 steep waves, §5.3 bar):
+
+* ``c1_linear_standing`` – L=2π, h=1, 4×1 elements, P=4, H/L=0.001,
+  η=(H/2)cos x, φ̃=0, dt=T/64, one period.
+* ``c2_steep_periodic`` – L=2π, h=1, 64×4 elements, P=6, H/L=0.08,
+  η=(H/2)cos x+(kH²/8)cos 2x, φ̃ from linear theory at z=η, dt=T/200,
+  over-integration P_f=⌈3P/2⌉, filter (α,s,i_c)=(36,12,P-1).
+* ``c3_instances`` – 512 periodic tanks from splitmix64(seed 0).
+* ``roofline_tank`` – one long periodic tank (Nx=65536, Nz=4, P=6) for
+  HBM-bound operator measurements.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field, asdict
+
+import numpy as np
+
+G_EARTH = 9.81
+
+
+def linear_omega(k: float, h: float, g: float = G_EARTH) -> float:
+    """Angular frequency from the linear dispersion relation ω² = g k tanh(kh) (§4.2)."""
+    return math.sqrt(g * k * math.tanh(k * h))
+
+
+@dataclass
+class Workload:
+    name: str
+    P: int
+    Nx: int
+    Nz: int
+    length: float
+    periodic: bool
+    depth: float
+    g: float = G_EARTH
+    Pf: int = 0                 # over-integration order; 0 means P (none)
+    filter_alpha: float = 0.0
+    filter_s: float = 0.0
+    filter_ic: int = -1         # -1: no filter
+    dt: float = 0.0
+    nsteps: int = 0
+    wave_height: float = 0.0
+    wavenumber: float = 1.0
+    init: str = "progressive"   # "standing": η=(H/2)cos kx, φ̃=0
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def ncol(self) -> int:
+        return self.Nx * self.P if self.periodic else self.Nx * self.P + 1
+
+    @property
+    def nrow(self) -> int:
+        return self.Nz * self.P + 1
+
+    @property
+    def n_nodes(self) -> int:
+        return self.ncol * self.nrow
+
+    @property
+    def n_unknowns(self) -> int:
+        return self.ncol * (self.nrow - 1)
+
+    def element_edges(self) -> np.ndarray:
+        return np.linspace(0.0, self.length, self.Nx + 1)
+
+    def as_dict(self) -> dict:
+        d = asdict(self)
+        d["ncol"], d["nrow"] = self.ncol, self.nrow
+        return d
+
+
+def column_x(wl: Workload, gll_nodes: np.ndarray, edges: np.ndarray | None = None) -> np.ndarray:
+    """x-coordinate of each mesh column, given the caller's GLL nodes on [-1, 1]."""
+    if edges is None:
+        edges = wl.element_edges()
+    P = wl.P
+    ix = np.arange(wl.ncol)
+    ex = np.minimum(ix // P, wl.Nx - 1)
+    a = ix - ex * P
+    x0, x1 = edges[ex], edges[ex + 1]
+    return x0 + 0.5 * (np.asarray(gll_nodes)[a] + 1.0) * (x1 - x0)
+
+
+def c1_linear_standing() -> Workload:
+    k, h = 1.0, 1.0
+    T = 2 * math.pi / linear_omega(k, h)
+    return Workload(name="C1 linear standing wave 4x1 P=4", P=4, Nx=4, Nz=1,
+                    length=2 * math.pi, periodic=True, depth=h, dt=T / 64, nsteps=64,
+                    wave_height=0.001 * 2 * math.pi, wavenumber=k, init="standing")
+
+
+def c2_steep_periodic() -> Workload:
+    k, h, P = 1.0, 1.0, 6
+    T = 2 * math.pi / linear_omega(k, h)
+    return Workload(name="C2 steep periodic wave 64x4 P=6", P=P, Nx=64, Nz=4,
+                    length=2 * math.pi, periodic=True, depth=h,
+                    Pf=(3 * P + 1) // 2, filter_alpha=36.0, filter_s=12.0, filter_ic=P - 1,
+                    dt=T / 200, nsteps=20000, wave_height=0.08 * 2 * math.pi, wavenumber=k)
+
+
+def roofline_tank(Nx: int = 65536, Nz: int = 4, P: int = 6) -> Workload:
+    k, h = 1.0, 1.0
+    T = 2 * math.pi / linear_omega(k, h)
+    return Workload(name=f"long periodic tank {Nx}x{Nz} P={P}", P=P, Nx=Nx, Nz=Nz,
+                    length=2 * math.pi * Nx / 64, periodic=True, depth=h,
+                    Pf=(3 * P + 1) // 2, filter_alpha=36.0, filter_s=12.0, filter_ic=P - 1,
+                    dt=T / 200, nsteps=1, wave_height=0.04 * 2 * math.pi, wavenumber=k)
+
+
+def small_case(P: int = 5, Nx: int = 6, Nz: int = 2, periodic: bool = True,
+               H_over_L: float = 0.05, Pf: int | None = None, filt: bool = True) -> Workload:
+    """A small steep-wave tank that spans several elements and layers (parity cases)."""
+    k, h = 1.0, 1.0
+    T = 2 * math.pi / linear_omega(k, h)
+    return Workload(name=f"small {Nx}x{Nz} P={P} {'periodic' if periodic else 'walls'}",
+                    P=P, Nx=Nx, Nz=Nz, length=2 * math.pi, periodic=periodic, depth=h,
+                    Pf=(3 * P + 1) // 2 if Pf is None else Pf,
+                    filter_alpha=36.0 if filt else 0.0, filter_s=12.0 if filt else 0.0,
+                    filter_ic=(P - 1) if filt else -1,
+                    dt=T / 100, nsteps=2, wave_height=H_over_L * 2 * math.pi, wavenumber=k)
+
+
+def depth_columns(wl: Workload, xcol: np.ndarray, bar: bool = False) -> np.ndarray:
+    """Still-water depth at each column: constant, or a smooth submerged bar.
+
+    The bar (used for variable-bathymetry cases) rises from ``depth`` to
+    ``depth/4`` over the middle third of the tank with a raised-cosine
+    profile, so h and h_x are smooth.
+    """
+    h = np.full_like(xcol, wl.depth, dtype=np.float64)
+    if bar:
+        L = wl.length
+        x0, x1 = L / 3, 2 * L / 3
+        s = np.clip((xcol - x0) / (x1 - x0), 0.0, 1.0)
+        h = wl.depth - 0.75 * wl.depth * 0.5 * (1 - np.cos(2 * math.pi * s)) * (s > 0) * (s < 1)
+    return h
+
+
+def initial_state(wl: Workload, xcol: np.ndarray, h: np.ndarray | None = None):
+    """Initial (η, φ̃) at the columns.
+
+    ``init == "standing"``: η=(H/2)cos kx, φ̃=0.
+    Otherwise: η=(H/2)cos kx + (kH²/8)cos 2kx and φ̃ from linear theory of a
+    progressive wave evaluated at z=η:
+    φ̃ = (gH/2ω)·cosh(k(η+h))/cosh(kh)·sin kx.
+    """
+    k, H = wl.wavenumber, wl.wave_height
+    if h is None:
+        h = np.full_like(xcol, wl.depth, dtype=np.float64)
+    if wl.init == "standing":
+        eta = 0.5 * H * np.cos(k * xcol)
+        return eta, np.zeros_like(eta)
+    eta = 0.5 * H * np.cos(k * xcol) + (k * H * H / 8.0) * np.cos(2 * k * xcol)
+    om = linear_omega(k, wl.depth, wl.g)
+    phis = (wl.g * H / (2 * om)) * np.cosh(k * (eta + h)) / np.cosh(k * wl.depth) * np.sin(k * xcol)
+    return eta, phis
+
+
+# --- splitmix64: counter-based generator for instance lists (Steele, Lea & Flood 2014) ---
+_MASK = (1 << 64) - 1
+
+
+def splitmix64(seed: int):
+    state = seed & _MASK
+    while True:
+        state = (state + 0x9E3779B97F4A7C15) & _MASK
+        z = state
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _MASK
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _MASK
+        yield z ^ (z >> 31)
+
+
+def _uniform(gen) -> float:
+    return (next(gen) >> 11) * (1.0 / (1 << 53))
+
+
+def c3_instances(count: int = 512, seed: int = 0) -> list[Workload]:
+    """Uneven periodic tanks: Nx∈[16,128], Nz∈{1,2,4}, P∈{4..8}, kh∈[0.5,3], H/L∈[0.01,0.09]."""
+    gen = splitmix64(seed)
+    out = []
+    for i in range(count):
+        Nx = 16 + int(_uniform(gen) * 113)
+        Nz = (1, 2, 4)[int(_uniform(gen) * 3)]
+        P = 4 + int(_uniform(gen) * 5)
+        kh = 0.5 + 2.5 * _uniform(gen)
+        HL = 0.01 + 0.08 * _uniform(gen)
+        k = 1.0
+        h = kh / k
+        T = 2 * math.pi / linear_omega(k, h)
+        out.append(Workload(name=f"C3 tank {i}", P=P, Nx=Nx, Nz=Nz, length=2 * math.pi / k,
+                            periodic=True, depth=h, Pf=(3 * P + 1) // 2,
+                            filter_alpha=36.0, filter_s=12.0, filter_ic=P - 1,
+                            dt=T / 200, nsteps=1, wave_height=HL * 2 * math.pi / k, wavenumber=k))
+    return out
+
+
+def random_field(n: int, seed: int) -> np.ndarray:
+    """Seeded standard-normal vector (parity inputs for operator applies)."""
+    return np.random.default_rng(seed).standard_normal(n)
