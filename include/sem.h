@@ -1,0 +1,189 @@
+/*
+ * sem.h — C ABI of the GB300 library for the stabilised nodal spectral
+ * element method for fully nonlinear potential-flow water waves
+ * (Engsig-Karup, Eskilsson & Bigoni, arXiv 1512.02548).
+ *
+ * The library solves, on one GPU, the free-surface problem of §2: find the
+ * surface elevation η(x,t) and surface potential φ̃(x,t) evolving by the
+ * Zakharov equations (eq. FSeqs), where the vertical surface velocity w̃ comes
+ * from the Laplace problem (eq. laplaceproblem) solved in the σ-transformed
+ * domain (eqs. sigtrans–symTransformedLaplace2) on a 2D x–σ mesh of
+ * tensor-product Gauss–Lobatto–Legendre (GLL) quadrilaterals (§3.1).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Layout.  The mesh has Nx elements along x and Nz layers along σ ∈ [0,1],
+ * order P in both directions.  Columns ix = 0..Ncol-1 with Ncol = Nx·P
+ * (periodic) or Nx·P+1 (walls); rows iz = 0..Nrow-1, Nrow = Nz·P+1, from the
+ * bottom (iz = 0) to the free surface (iz = Nrow-1).  A volume field is a
+ * contiguous FP64 array of n = Ncol·Nrow values, node (ix,iz) at index
+ * ix·Nrow + iz.  A surface field is a contiguous FP64 array of Ncol values.
+ *
+ * Pointers.  "_d" arguments are device pointers on the mesh's device, "_h"
+ * arguments host pointers.  The caller owns every array it passes; the mesh
+ * owns its own workspace (allocated once in sem_mesh_create).  Arrays passed
+ * to one call must not overlap unless stated.
+ *
+ * Streams.  `stream` is a cudaStream_t (NULL = legacy default stream).  Work
+ * is enqueued on it.  Calls marked "synchronises" wait for the stream at the
+ * end to read the mesh's device status word; all others return as soon as
+ * the work is enqueued.
+ *
+ * Tuning.  The environment variable SEM_GRID_LIMIT, read by sem_mesh_create, caps
+ * the number of CTAs of the persistent Krylov kernel (default: all co-resident).
+ *
+ * Errors.  Every call returns SEM_OK (0) or one of the codes below;
+ * sem_last_error() gives a message for the calling thread's last failure.
+ * A status raised on the device (no convergence, non-finite values, a
+ * timed-out grid barrier) is reported by the next synchronising call.
+ */
+#ifndef SEM_GB300_H
+#define SEM_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SEM_MAX_P 12
+
+enum sem_status {
+  SEM_OK = 0,
+  SEM_ERR_INVALID_ARG = 1,   /* bad size, pointer or parameter            */
+  SEM_ERR_OOM = 2,           /* device or host allocation failed          */
+  SEM_ERR_CUDA = 3,          /* a CUDA runtime call failed                */
+  SEM_ERR_NOT_CONVERGED = 4, /* Laplace solve hit max_iter above tol      */
+  SEM_ERR_NONFINITE = 5,     /* NaN/Inf in a residual                     */
+  SEM_ERR_TIMEOUT = 6        /* a device grid barrier gave up waiting     */
+};
+
+enum sem_precision {
+  SEM_PREC_FP64 = 0,  /* every step in FP64                                      */
+  SEM_PREC_MIXED = 1  /* FP32 inner Krylov iterations, FP64 residual refinement  */
+};
+
+/* Discretisation and solver parameters (§3.1, §3.3, §3.4). */
+typedef struct sem_params {
+  int P;               /* GLL order in x and σ, 2 ≤ P ≤ SEM_MAX_P                    */
+  int Nx;              /* elements along x (periodic: Nx ≥ 3; walls: Nx ≥ 1)         */
+  int Nz;              /* layers along σ, 1 ≤ Nz ≤ 16                                 */
+  int periodic;        /* 1: periodic in x; 0: impermeable walls at both ends        */
+  int Pf;              /* over-integration order of §3.3 (0 → P, i.e. none), ≤ 3P    */
+  int filter_ic;       /* filter cut-off index i_c of §3.4; < 0 disables the filter  */
+  double filter_alpha; /* filter strength α                                          */
+  double filter_s;     /* filter order s (s = 0: constant factor e^-α above i_c)     */
+  double g;            /* gravitational acceleration                                 */
+  double tol;          /* Laplace solve: stop when ‖r‖₂ ≤ tol·‖b‖₂ (0 → 1e-13)       */
+  int max_iter;        /* Laplace solve: Krylov iteration cap (0 → 5000)             */
+  int precision;       /* enum sem_precision                                          */
+} sem_params;
+
+typedef struct sem_info {
+  int64_t n_nodes;     /* Ncol·Nrow                           */
+  int64_t n_unknowns;  /* Ncol·(Nrow-1): Laplace unknowns      */
+  int ncol, nrow;
+  int n_elements;      /* Nx·Nz                               */
+  int P, Pf, Nx, Nz, periodic, precision;
+  int grid_ctas;       /* CTAs of the persistent Krylov kernel */
+} sem_info;
+
+typedef struct sem_solve_stats {
+  int iterations;        /* Krylov iterations of the last solve (inner, all refinements) */
+  int refinements;       /* FP64 residual refinements (mixed precision), else 0          */
+  double rel_residual;   /* final ‖r‖₂/‖b‖₂ in FP64                                       */
+} sem_solve_stats;
+
+typedef struct sem_counters {
+  int64_t solves;            /* Laplace solves since creation / last reset    */
+  int64_t iterations;        /* total Krylov iterations over those solves     */
+  int64_t refinements;       /* total FP64 refinements (mixed precision)      */
+  double max_rel_residual;   /* worst final relative residual                  */
+} sem_counters;
+
+typedef struct sem_mesh sem_mesh;
+
+/* Create a mesh on the current CUDA device (§3.1): element edges x_edges_h[Nx+1]
+ * (strictly increasing, host), still-water depth h_h[Ncol] at the columns (host,
+ * > 0).  Builds the GLL tables, the surface-mass factorisation and all workspace
+ * (owned by the mesh).  On failure *out is NULL. */
+int sem_mesh_create(const sem_params* p, const double* x_edges_h, const double* h_h,
+                    sem_mesh** out);
+void sem_mesh_destroy(sem_mesh* m);
+int sem_mesh_info(const sem_mesh* m, sem_info* info);
+
+/* Element-to-global map used by every gather/scatter (§3.1.2, assembly over
+ * elements): l2g_d[((ex·Nz + l)·(P+1) + a)·(P+1) + b] = global id of local node
+ * (a,b) of element (ex,l), written by a device kernel.  l2g_d: device, int32,
+ * Nx·Nz·(P+1)² entries. */
+int sem_mesh_l2g(sem_mesh* m, int32_t* l2g_d, void* stream);
+
+/* σ-geometry for the current surface (§2, eqs. sigtrans, jacobian,
+ * symTransformedLaplace2): d = η + h, element-local ∂x d, and the Jacobi
+ * diagonal of the Laplace operator.  eta_d: device, Ncol.  Must precede
+ * sem_laplace_apply / sem_laplace_solve for that η. */
+int sem_update_geometry(sem_mesh* m, const double* eta_d, void* stream);
+
+/* y = 𝓛 x with 𝓛_ij = −Σ_k ∫ (K∇N_j)·∇N_i over the mesh (§3.1.2), matrix-free,
+ * all n rows (no Dirichlet modification), for the last sem_update_geometry.
+ * x_d, y_d: device, n values, must not overlap. */
+int sem_laplace_apply(sem_mesh* m, const double* x_d, double* y_d, void* stream);
+
+/* Laplace problem of eq. (laplaceproblem) for the last sem_update_geometry:
+ * 𝓛Φ = 0 at interior nodes, Φ = φ̃ at the surface (eq. FSeqs BC), solved by
+ * preconditioned conjugate gradients on the Dirichlet-eliminated SPD system
+ * (§3.1.2 names PCG for large systems).  phis_d: device, Ncol.  Phi_d: device,
+ * n; on entry its interior values are the initial guess, on exit the solution
+ * (surface rows set to φ̃).  If st is non-NULL the call synchronises and fills
+ * it; otherwise device status is reported by the next synchronising call. */
+int sem_laplace_solve(sem_mesh* m, const double* phis_d, double* Phi_d,
+                      sem_solve_stats* st, void* stream);
+
+/* Gradient recovery (§3.1.3): w̃ = w at the surface from 𝓜w = 𝓢_zΦ
+ * (eq. velocpot2), and the C⁰ derivatives from M'u = S_x f (eq.
+ * representationU) for f = η and f = φ̃.  Uses the geometry of the last
+ * sem_update_geometry (for 1/d).  Inputs Phi_d (n), eta_d, phis_d (Ncol);
+ * outputs w_surf_d, etax_d, phisx_d (Ncol each); all device. */
+int sem_recover_gradient(sem_mesh* m, const double* Phi_d, const double* eta_d,
+                         const double* phis_d, double* w_surf_d, double* etax_d,
+                         double* phisx_d, void* stream);
+
+/* Right-hand side of the semi-discrete free-surface equations (§3.1.1 with
+ * the PDE form of eq. FSeqs, over-integrated at order Pf per §3.3):
+ * M' ∂tη = ∫(−ηxφ̃x + w̃(1+ηx²))N_i,  M' ∂tφ̃ = ∫(−gη − ½(φ̃x² − w̃²(1+ηx²)))N_i.
+ * Runs geometry, the Laplace solve (warm-started from the mesh's previous
+ * potential), recovery and the projection.  t is unused (no forcing zones).
+ * eta_d, phis_d in; deta_d, dphis_d out; device, Ncol each. */
+int sem_zakharov_rhs(sem_mesh* m, const double* eta_d, const double* phis_d, double t,
+                     double* deta_d, double* dphis_d, void* stream);
+
+/* Per-element modal filter F = V̂SV̂⁻¹ of §3.4 applied in place to a surface
+ * field (no-op if filter_ic < 0).  q_d: device, Ncol. */
+int sem_apply_filter(sem_mesh* m, double* q_d, void* stream);
+
+/* nsteps classical RK4 steps of size dt on (η, φ̃) in place, each followed by
+ * the filter (§3.1.1, §3.4); *t advances by nsteps·dt.  eta_d, phis_d: device,
+ * Ncol.  Synchronises once at the end. */
+int sem_rk4_step(sem_mesh* m, double* eta_d, double* phis_d, double* t, double dt,
+                 int nsteps, void* stream);
+
+/* As sem_rk4_step for callers holding the state in host memory: copies eta_h,
+ * phis_h (host, Ncol each; pinned memory recommended) to the device, steps,
+ * and copies the result back.  Synchronises. */
+int sem_rk4_step_host(sem_mesh* m, double* eta_h, double* phis_h, double* t, double dt,
+                      int nsteps, void* stream);
+
+/* Solver counters accumulated on the device; reading synchronises the stream. */
+int sem_get_counters(sem_mesh* m, sem_counters* c, void* stream);
+int sem_reset_counters(sem_mesh* m, void* stream);
+
+/* Number of kernels this library has launched in the calling process. */
+int64_t sem_launch_count(void);
+
+/* Message for the calling thread's last error ("" if none). */
+const char* sem_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SEM_GB300_H */

@@ -1,0 +1,226 @@
+"""GB300 library for the stabilised nodal SEM water-wave model (arXiv 1512.02548).
+
+Thin ctypes binding of the C ABI in ``include/sem.h``: argument marshalling only.
+Every step of the method runs in the CUDA kernels of ``libsem_gb300.so``; there is
+no CPU fallback, and using the binding without the built library raises.
+
+Device arrays are ``torch.Tensor`` objects on the mesh's CUDA device (FP64,
+contiguous); the current torch stream is passed to every call.  PyTorch is used
+only for device memory and streams.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsem_gb300.so")
+
+SEM_OK = 0
+SEM_ERRORS = {1: "SEM_ERR_INVALID_ARG", 2: "SEM_ERR_OOM", 3: "SEM_ERR_CUDA",
+              4: "SEM_ERR_NOT_CONVERGED", 5: "SEM_ERR_NONFINITE", 6: "SEM_ERR_TIMEOUT"}
+SEM_PREC_FP64, SEM_PREC_MIXED = 0, 1
+
+EXPORTED = ("sem_mesh_create", "sem_mesh_destroy", "sem_mesh_info", "sem_mesh_l2g",
+            "sem_update_geometry", "sem_laplace_apply", "sem_laplace_solve",
+            "sem_recover_gradient", "sem_zakharov_rhs", "sem_apply_filter", "sem_rk4_step",
+            "sem_rk4_step_host", "sem_get_counters", "sem_reset_counters", "sem_launch_count",
+            "sem_last_error")
+
+
+class sem_params(ctypes.Structure):
+    _fields_ = [("P", ctypes.c_int), ("Nx", ctypes.c_int), ("Nz", ctypes.c_int),
+                ("periodic", ctypes.c_int), ("Pf", ctypes.c_int), ("filter_ic", ctypes.c_int),
+                ("filter_alpha", ctypes.c_double), ("filter_s", ctypes.c_double),
+                ("g", ctypes.c_double), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
+                ("precision", ctypes.c_int)]
+
+
+class sem_info(ctypes.Structure):
+    _fields_ = [("n_nodes", ctypes.c_int64), ("n_unknowns", ctypes.c_int64),
+                ("ncol", ctypes.c_int), ("nrow", ctypes.c_int), ("n_elements", ctypes.c_int),
+                ("P", ctypes.c_int), ("Pf", ctypes.c_int), ("Nx", ctypes.c_int), ("Nz", ctypes.c_int),
+                ("periodic", ctypes.c_int), ("precision", ctypes.c_int), ("grid_ctas", ctypes.c_int)]
+
+
+class sem_solve_stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("refinements", ctypes.c_int),
+                ("rel_residual", ctypes.c_double)]
+
+
+class sem_counters(ctypes.Structure):
+    _fields_ = [("solves", ctypes.c_int64), ("iterations", ctypes.c_int64),
+                ("refinements", ctypes.c_int64), ("max_rel_residual", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libsem_gb300.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it first (python -m paper_1512_02548_gb300.build)")
+    lib = ctypes.CDLL(path)
+    vp, dp, ip = ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int
+    lib.sem_mesh_create.argtypes = [ctypes.POINTER(sem_params), dp, dp, ctypes.POINTER(vp)]
+    lib.sem_mesh_destroy.argtypes = [vp]
+    lib.sem_mesh_destroy.restype = None
+    lib.sem_mesh_info.argtypes = [vp, ctypes.POINTER(sem_info)]
+    lib.sem_mesh_l2g.argtypes = [vp, dp, vp]
+    lib.sem_update_geometry.argtypes = [vp, dp, vp]
+    lib.sem_laplace_apply.argtypes = [vp, dp, dp, vp]
+    lib.sem_laplace_solve.argtypes = [vp, dp, dp, ctypes.POINTER(sem_solve_stats), vp]
+    lib.sem_recover_gradient.argtypes = [vp, dp, dp, dp, dp, dp, dp, vp]
+    lib.sem_zakharov_rhs.argtypes = [vp, dp, dp, ctypes.c_double, dp, dp, vp]
+    lib.sem_apply_filter.argtypes = [vp, dp, vp]
+    lib.sem_rk4_step.argtypes = [vp, dp, dp, ctypes.POINTER(ctypes.c_double), ctypes.c_double, ip, vp]
+    lib.sem_rk4_step_host.argtypes = [vp, dp, dp, ctypes.POINTER(ctypes.c_double), ctypes.c_double, ip, vp]
+    lib.sem_get_counters.argtypes = [vp, ctypes.POINTER(sem_counters), vp]
+    lib.sem_reset_counters.argtypes = [vp, vp]
+    lib.sem_launch_count.restype = ctypes.c_int64
+    lib.sem_launch_count.argtypes = []
+    lib.sem_last_error.restype = ctypes.c_char_p
+    lib.sem_last_error.argtypes = []
+    for name in EXPORTED:
+        if name not in ("sem_mesh_destroy", "sem_launch_count", "sem_last_error"):
+            getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+class SemError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{SEM_ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _check(code: int):
+    if code != SEM_OK:
+        raise SemError(code, load_library().sem_last_error().decode())
+
+
+def _stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not (t.is_cuda and t.is_contiguous()):
+        raise ValueError("expected a contiguous CUDA tensor")
+    import torch
+    if t.dtype not in (torch.float64, torch.int32):
+        raise ValueError("expected float64 (or int32 for l2g)")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def launch_count() -> int:
+    return int(load_library().sem_launch_count())
+
+
+class Mesh:
+    """One σ-mesh on the current CUDA device; wraps ``sem_mesh``.
+
+    Method names follow the C ABI (``sem_<name>``); arrays are torch CUDA tensors.
+    """
+
+    def __init__(self, P: int, Nx: int, Nz: int, x_edges, h, periodic: bool = True, Pf: int = 0,
+                 filter_alpha: float = 0.0, filter_s: float = 0.0, filter_ic: int = -1,
+                 g: float = 9.81, tol: float = 1e-13, max_iter: int = 5000, precision: str = "fp64"):
+        lib = load_library()
+        prm = sem_params(P=P, Nx=Nx, Nz=Nz, periodic=int(bool(periodic)), Pf=Pf, filter_ic=filter_ic,
+                         filter_alpha=filter_alpha, filter_s=filter_s, g=g, tol=tol, max_iter=max_iter,
+                         precision=SEM_PREC_MIXED if precision == "mixed" else SEM_PREC_FP64)
+        xe = np.ascontiguousarray(x_edges, dtype=np.float64)
+        hh = np.ascontiguousarray(h, dtype=np.float64)
+        handle = ctypes.c_void_p()
+        _check(lib.sem_mesh_create(ctypes.byref(prm), xe.ctypes.data_as(ctypes.c_void_p),
+                                   hh.ctypes.data_as(ctypes.c_void_p), ctypes.byref(handle)))
+        self._h = handle
+        self.info = sem_info()
+        _check(lib.sem_mesh_info(self._h, ctypes.byref(self.info)))
+        self.ncol, self.nrow = self.info.ncol, self.info.nrow
+        self.n = int(self.info.n_nodes)
+        self.n_unknowns = int(self.info.n_unknowns)
+
+    @classmethod
+    def from_workload(cls, wl, h=None, precision: str = "fp64", tol: float = 1e-13, max_iter: int = 5000):
+        edges = wl.element_edges()
+        if h is None:
+            h = np.full(wl.ncol, wl.depth)
+        return cls(wl.P, wl.Nx, wl.Nz, edges, h, periodic=wl.periodic, Pf=wl.Pf,
+                   filter_alpha=wl.filter_alpha, filter_s=wl.filter_s, filter_ic=wl.filter_ic,
+                   g=wl.g, tol=tol, max_iter=max_iter, precision=precision)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load_library().sem_mesh_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- C ABI calls -----------------------------------------------------------------
+    def l2g(self, out):
+        _check(load_library().sem_mesh_l2g(self._h, _ptr(out), _stream()))
+        return out
+
+    def update_geometry(self, eta):
+        _check(load_library().sem_update_geometry(self._h, _ptr(eta), _stream()))
+
+    def laplace_apply(self, x, y):
+        _check(load_library().sem_laplace_apply(self._h, _ptr(x), _ptr(y), _stream()))
+        return y
+
+    def laplace_solve(self, phis, Phi, stats: bool = True):
+        st = sem_solve_stats()
+        _check(load_library().sem_laplace_solve(self._h, _ptr(phis), _ptr(Phi),
+                                                ctypes.byref(st) if stats else None, _stream()))
+        return st if stats else None
+
+    def recover_gradient(self, Phi, eta, phis, w, etax, phisx):
+        _check(load_library().sem_recover_gradient(self._h, _ptr(Phi), _ptr(eta), _ptr(phis),
+                                                   _ptr(w), _ptr(etax), _ptr(phisx), _stream()))
+
+    def zakharov_rhs(self, eta, phis, deta, dphis, t: float = 0.0):
+        _check(load_library().sem_zakharov_rhs(self._h, _ptr(eta), _ptr(phis), ctypes.c_double(t),
+                                               _ptr(deta), _ptr(dphis), _stream()))
+
+    def apply_filter(self, q):
+        _check(load_library().sem_apply_filter(self._h, _ptr(q), _stream()))
+
+    def rk4_step(self, eta, phis, dt: float, nsteps: int = 1, t: float = 0.0) -> float:
+        tt = ctypes.c_double(t)
+        _check(load_library().sem_rk4_step(self._h, _ptr(eta), _ptr(phis), ctypes.byref(tt),
+                                           ctypes.c_double(dt), int(nsteps), _stream()))
+        return tt.value
+
+    def rk4_step_host(self, eta, phis, dt: float, nsteps: int = 1, t: float = 0.0) -> float:
+        """eta, phis: host float64 arrays (numpy or pinned CPU tensors), updated in place."""
+        def hp(a):
+            if isinstance(a, np.ndarray):
+                if a.dtype != np.float64 or not a.flags.c_contiguous:
+                    raise ValueError("expected a contiguous float64 array")
+                return a.ctypes.data_as(ctypes.c_void_p)
+            return ctypes.c_void_p(a.data_ptr())
+        tt = ctypes.c_double(t)
+        _check(load_library().sem_rk4_step_host(self._h, hp(eta), hp(phis), ctypes.byref(tt),
+                                                ctypes.c_double(dt), int(nsteps), _stream()))
+        return tt.value
+
+    def counters(self) -> sem_counters:
+        c = sem_counters()
+        _check(load_library().sem_get_counters(self._h, ctypes.byref(c), _stream()))
+        return c
+
+    def reset_counters(self):
+        _check(load_library().sem_reset_counters(self._h, _stream()))

@@ -1,0 +1,535 @@
+// C ABI of the library (declared in include/sem.h): mesh set-up, host-side tables and
+// the orchestration of the kernels for one Laplace solve, the recovery, the Zakharov
+// right-hand side and RK4 (§2–§3 of arXiv 1512.02548).
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/sem.h"
+#include "sem_internal.cuh"
+#include "tables.h"
+
+using namespace semgb;
+
+namespace semgb {
+static std::atomic<long long> g_launches{0};
+void count_launch(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+}  // namespace semgb
+
+namespace {
+
+thread_local std::string t_err;
+
+int fail(int code, const std::string& msg) {
+  t_err = msg;
+  return code;
+}
+
+#define CUDA_TRY(call)                                                                      \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess)                                                                  \
+      return fail(SEM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));        \
+  } while (0)
+
+std::mutex g_tables_mu;
+bool g_tables_done[64] = {false};
+
+int ensure_device_tables(int dev) {
+  std::lock_guard<std::mutex> lk(g_tables_mu);
+  if (dev < 0 || dev >= 64) return fail(SEM_ERR_INVALID_ARG, "device index out of range");
+  if (g_tables_done[dev]) return SEM_OK;
+  std::vector<double> D(kDTotal, 0.0), w(kWTotal, 0.0);
+  for (int P = 1; P <= kMaxP; ++P) {
+    Line L = make_line(P);
+    std::memcpy(&D[d_off(P)], L.D.data(), sizeof(double) * (P + 1) * (P + 1));
+    std::memcpy(&w[w_off(P)], L.w.data(), sizeof(double) * (P + 1));
+  }
+  CUDA_TRY(upload_line_tables(D.data(), w.data()));
+  g_tables_done[dev] = true;
+  return SEM_OK;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+// Bump allocator over one device allocation (256-byte aligned slices).
+struct Carve {
+  size_t off = 0;
+  template <class T> size_t take(size_t count) {
+    size_t o = (off + 255) & ~size_t(255);
+    off = o + count * sizeof(T);
+    return o;
+  }
+};
+
+}  // namespace
+
+struct sem_mesh {
+  sem_params p{};
+  int device = 0;
+  int ncol = 0, nrow = 0, Pf = 0, nif = 0;
+  long long n = 0;
+  int grid = 0;
+  size_t smem = 0;
+  unsigned char* pool = nullptr;
+  DevGeom g{};
+  SurfTables st{};
+  PcgArgs pa{};
+  SolveRecord* rec = nullptr;
+  // workspace
+  double *Phi = nullptr, *qtmp = nullptr, *edgetmp = nullptr;
+  double *wt = nullptr, *etax = nullptr, *phisx = nullptr, *R = nullptr, *scr = nullptr;
+  double *ke = nullptr, *kp = nullptr, *ae = nullptr, *ap = nullptr, *se = nullptr, *sp = nullptr;
+  double *eta_dev = nullptr, *phis_dev = nullptr;
+};
+
+namespace {
+
+int read_status(sem_mesh* m, cudaStream_t s) {
+  int st = 0;
+  CUDA_TRY(cudaMemcpyAsync(&st, m->g.status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if (st == 0) return SEM_OK;
+  CUDA_TRY(cudaMemsetAsync(m->g.status, 0, sizeof(int), s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if (st & ST_TIMEOUT) return fail(SEM_ERR_TIMEOUT, "a grid barrier of the Krylov kernel timed out");
+  if (st & ST_BAD_DEPTH) return fail(SEM_ERR_NONFINITE, "water depth d = eta + h is not positive and finite");
+  if (st & ST_NONFINITE) return fail(SEM_ERR_NONFINITE, "non-finite residual in the Laplace solve");
+  if (st & ST_NOT_CONVERGED) return fail(SEM_ERR_NOT_CONVERGED, "Laplace solve reached max_iter above tol");
+  return fail(SEM_ERR_CUDA, "unknown device status");
+}
+
+int do_solve(sem_mesh* m, const double* phis, double* Phi, cudaStream_t s) {
+  PcgArgs a = m->pa;
+  a.x = Phi;
+  a.phis = phis;
+  CUDA_TRY(launch_pcg(m->g, a, m->grid, m->smem, s));
+  return SEM_OK;
+}
+
+int do_rhs(sem_mesh* m, const double* eta, const double* phis, double* de, double* dp, cudaStream_t s) {
+  const int Q = m->p.P + 1;
+  CUDA_TRY(launch_geometry(m->g, eta, s));
+  int rc = do_solve(m, phis, m->Phi, s);
+  if (rc) return rc;
+  CUDA_TRY(launch_wsurf(m->st, m->Phi, eta, m->wt, s));
+  CUDA_TRY(launch_sx(m->st, eta, phis, m->R, s));
+  CUDA_TRY(launch_mass1d(m->st, m->R, 2, m->etax, m->phisx, m->scr, s));
+  CUDA_TRY(launch_zakharov(m->st, eta, m->etax, m->phisx, m->wt, m->R, s));
+  CUDA_TRY(launch_mass1d(m->st, m->R, 2, de, dp, m->scr, s));
+  (void)Q;
+  return SEM_OK;
+}
+
+int do_rk4(sem_mesh* m, double* eta, double* phis, double dt, int nsteps, cudaStream_t s) {
+  const int n = m->ncol;
+  for (int step = 0; step < nsteps; ++step) {
+    for (int stage = 1; stage <= 4; ++stage) {
+      const double* ei = stage == 1 ? eta : m->se;
+      const double* pi = stage == 1 ? phis : m->sp;
+      int rc = do_rhs(m, ei, pi, m->ke, m->kp, s);
+      if (rc) return rc;
+      CUDA_TRY(launch_rk4_stage(stage, n, dt, eta, phis, m->ke, m->kp, m->ae, m->ap, m->se, m->sp, s));
+    }
+    CUDA_TRY(launch_filter(m->st, eta, phis, s));
+  }
+  return SEM_OK;
+}
+
+std::vector<double> matmul(const std::vector<double>& A, const std::vector<double>& B, int n, int k, int mcols) {
+  std::vector<double> C((size_t)n * mcols, 0.0);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < mcols; ++j) {
+      long double s = 0.0L;
+      for (int q = 0; q < k; ++q) s += (long double)A[(size_t)i * k + q] * B[(size_t)q * mcols + j];
+      C[(size_t)i * mcols + j] = (double)s;
+    }
+  return C;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sem_last_error(void) { return t_err.c_str(); }
+
+int64_t sem_launch_count(void) { return g_launches.load(); }
+
+int sem_mesh_create(const sem_params* pin, const double* x_edges_h, const double* h_h, sem_mesh** out) {
+  if (!out) return fail(SEM_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!pin || !x_edges_h || !h_h) return fail(SEM_ERR_INVALID_ARG, "NULL argument");
+  sem_params p = *pin;
+  if (p.P < 2 || p.P > SEM_MAX_P) return fail(SEM_ERR_INVALID_ARG, "P must be in [2, 12]");
+  if (p.Nz < 1 || p.Nz > kMaxNz) return fail(SEM_ERR_INVALID_ARG, "Nz must be in [1, 16]");
+  if (p.periodic ? p.Nx < 3 : p.Nx < 1) return fail(SEM_ERR_INVALID_ARG, "Nx too small (periodic needs >= 3)");
+  if (p.Pf == 0) p.Pf = p.P;
+  if (p.Pf < p.P || p.Pf > 3 * p.P) return fail(SEM_ERR_INVALID_ARG, "Pf must be in [P, 3P]");
+  if (p.precision != SEM_PREC_FP64 && p.precision != SEM_PREC_MIXED)
+    return fail(SEM_ERR_INVALID_ARG, "unknown precision");
+  if (p.tol <= 0.0) p.tol = 1e-13;
+  if (p.max_iter <= 0) p.max_iter = 5000;
+  const int P = p.P, Q = P + 1, Nx = p.Nx, Nz = p.Nz;
+  const int ncol = p.periodic ? Nx * P : Nx * P + 1;
+  const int nrow = Nz * P + 1;
+  const long long n = (long long)ncol * nrow;
+  for (int i = 0; i < Nx; ++i)
+    if (!(x_edges_h[i + 1] > x_edges_h[i])) return fail(SEM_ERR_INVALID_ARG, "x_edges must increase");
+  for (int i = 0; i < ncol; ++i)
+    if (!(h_h[i] > 0.0) || !std::isfinite(h_h[i])) return fail(SEM_ERR_INVALID_ARG, "h must be positive");
+
+  int dev = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  int rc = ensure_device_tables(dev);
+  if (rc) return rc;
+
+  // ---- host tables --------------------------------------------------------------
+  Line L, Lf;
+  try {
+    L = make_line(P);
+    Lf = make_line(p.Pf);
+  } catch (const std::exception& e) {
+    return fail(SEM_ERR_INVALID_ARG, e.what());
+  }
+  const int Qf = p.Pf + 1, Pm = P - 1;
+  std::vector<double> dxe(Nx), dsl(Nz), sig(nrow), hx_loc((size_t)Nx * Q), se(Nx);
+  for (int e = 0; e < Nx; ++e) { dxe[e] = x_edges_h[e + 1] - x_edges_h[e]; se[e] = 0.5 * dxe[e]; }
+  for (int l = 0; l < Nz; ++l) dsl[l] = 1.0 / Nz;
+  for (int iz = 0; iz < nrow; ++iz) {
+    int l = iz / P; if (l >= Nz) l = Nz - 1;
+    const int b = iz - l * P;
+    sig[iz] = (double)l / Nz + 0.5 * (L.r[b] + 1.0) * dsl[l];
+  }
+  sig[nrow - 1] = 1.0;
+  for (int e = 0; e < Nx; ++e)
+    for (int a = 0; a < Q; ++a) {
+      long double s = 0.0L;
+      for (int c = 0; c < Q; ++c) {
+        int col = e * P + c; if (col >= ncol) col -= ncol;
+        s += (long double)L.D[a * Q + c] * h_h[col];
+      }
+      hx_loc[(size_t)e * Q + a] = (double)(s * 2.0L / dxe[e]);
+    }
+  std::vector<double> MD = matmul(L.M, L.D, Q, Q, Q);
+  std::vector<double> I = interpolation(L, Lf);                     // Qf×Q
+  std::vector<double> It(Q * Qf);
+  for (int q = 0; q < Qf; ++q) for (int c = 0; c < Q; ++c) It[c * Qf + q] = I[q * Q + c];
+  std::vector<double> B = matmul(It, Lf.M, Q, Qf, Qf);               // Q×Qf = Iᵀ M_f
+  std::vector<double> F = filter_matrix(L, p.filter_alpha, p.filter_s, p.filter_ic);
+  // w̃ weights: v = M_σ⁻¹ e_top, c_l = (Δσ_l/2) M v|_l
+  std::vector<double> cw((size_t)Nz * Q);
+  {
+    std::vector<long double> Ms((size_t)nrow * nrow, 0.0L);
+    for (int l = 0; l < Nz; ++l)
+      for (int a = 0; a < Q; ++a)
+        for (int b = 0; b < Q; ++b) Ms[(size_t)(l * P + a) * nrow + l * P + b] += 0.5L * dsl[l] * L.M[a * Q + b];
+    if (!invert(Ms, nrow)) return fail(SEM_ERR_INVALID_ARG, "sigma mass is singular");
+    for (int l = 0; l < Nz; ++l)
+      for (int b = 0; b < Q; ++b) {
+        long double s = 0.0L;
+        for (int c = 0; c < Q; ++c) s += 0.5L * dsl[l] * L.M[b * Q + c] * Ms[(size_t)(l * P + c) * nrow + (nrow - 1)];
+        cw[(size_t)l * Q + b] = (double)s;
+      }
+  }
+  // static condensation of M' (element scale Δx/2 · M)
+  std::vector<double> Aii((size_t)Pm * Pm), Z((size_t)2 * Pm);
+  long double S00, S01, S11;
+  {
+    std::vector<long double> Mii((size_t)Pm * Pm);
+    for (int i = 0; i < Pm; ++i) for (int k = 0; k < Pm; ++k) Mii[i * Pm + k] = L.M[(i + 1) * Q + (k + 1)];
+    if (!invert(Mii, Pm)) return fail(SEM_ERR_INVALID_ARG, "interior mass is singular");
+    for (int i = 0; i < Pm * Pm; ++i) Aii[i] = (double)Mii[i];
+    const int bn[2] = {0, P};
+    long double Zl[2][kMaxP];
+    for (int s2 = 0; s2 < 2; ++s2)
+      for (int i = 0; i < Pm; ++i) {
+        long double acc = 0.0L;
+        for (int k = 0; k < Pm; ++k) acc += (long double)L.M[bn[s2] * Q + (k + 1)] * Mii[k * Pm + i];
+        Zl[s2][i] = acc;
+        Z[s2 * Pm + i] = (double)acc;
+      }
+    auto sch = [&](int s1, int s2) {
+      long double acc = L.M[bn[s1] * Q + bn[s2]];
+      for (int i = 0; i < Pm; ++i) acc -= Zl[s1][i] * (long double)L.M[(i + 1) * Q + bn[s2]];
+      return acc;
+    };
+    S00 = sch(0, 0); S01 = sch(0, 1); S11 = sch(1, 1);
+  }
+  const int N = p.periodic ? Nx : Nx + 1;
+  std::vector<double> th_e(N, 0.0), th_m(N, 0.0), th_cp(N, 0.0), th_z(N, 0.0);
+  double th_vlast = 0.0, th_fac = 0.0;
+  {
+    std::vector<long double> d(N, 0.0L), e(N, 0.0L);
+    for (int j = 0; j < Nx; ++j) {
+      const int jr = (j + 1) % N;
+      d[j] += se[j] * S00;
+      d[jr] += se[j] * S11;
+      e[j] = se[j] * S01;            // coupling j ↔ j+1 (periodic: e[N−1] is the corner)
+    }
+    long double gamma = 0.0L, corner = 0.0L;
+    if (p.periodic) {
+      corner = e[N - 1];
+      gamma = -d[0];
+      d[0] -= gamma;
+      d[N - 1] -= corner * corner / gamma;
+    }
+    std::vector<long double> m(N), cp(N, 0.0L);
+    for (int j = 0; j < N; ++j) {
+      const long double piv = j == 0 ? d[0] : d[j] - e[j - 1] * cp[j - 1];
+      m[j] = 1.0L / piv;
+      if (j < N - 1) cp[j] = e[j] * m[j];
+    }
+    for (int j = 0; j < N; ++j) { th_e[j] = (double)e[j]; th_m[j] = (double)m[j]; th_cp[j] = (double)cp[j]; }
+    if (p.periodic) {
+      std::vector<long double> u(N, 0.0L), y(N);
+      u[0] = gamma;
+      u[N - 1] = corner;
+      for (int j = 0; j < N; ++j) y[j] = (j == 0 ? u[0] : u[j] - e[j - 1] * y[j - 1]) * m[j];
+      for (int j = N - 2; j >= 0; --j) y[j] -= cp[j] * y[j + 1];
+      const long double vl = corner / gamma;
+      for (int j = 0; j < N; ++j) th_z[j] = (double)y[j];
+      th_vlast = (double)vl;
+      th_fac = (double)(1.0L / (1.0L + y[0] + vl * y[N - 1]));
+    }
+  }
+
+  // ---- device allocation -------------------------------------------------------
+  sem_mesh* m = new sem_mesh;
+  m->p = p; m->device = dev; m->ncol = ncol; m->nrow = nrow; m->n = n; m->Pf = p.Pf; m->nif = N;
+  cudaError_t ge = pcg_grid_size(P, Nz, nrow, Nx, p.precision == SEM_PREC_MIXED, &m->grid, &m->smem);
+  if (ge != cudaSuccess) { delete m; return fail(SEM_ERR_CUDA, std::string("Krylov kernel occupancy: ") + cudaGetErrorString(ge)); }
+  if (const char* lim = std::getenv("SEM_GRID_LIMIT")) {   // tuning/testing knob: cap the Krylov grid
+    const int v = std::atoi(lim);
+    if (v >= 1 && v < m->grid) m->grid = v;
+  }
+
+  Carve cv;
+  const size_t nE = (size_t)Nx * nrow;
+  const size_t o_h = cv.take<double>(ncol), o_hx = cv.take<double>((size_t)Nx * Q), o_dxe = cv.take<double>(Nx),
+               o_dsl = cv.take<double>(Nz), o_sig = cv.take<double>(nrow), o_geo64 = cv.take<double>((size_t)Nx * Q * 4),
+               o_geo32 = cv.take<float>((size_t)Nx * Q * 4), o_id64 = cv.take<double>(n), o_id32 = cv.take<float>(n),
+               o_status = cv.take<int>(4), o_rec = cv.take<SolveRecord>(1), o_bar = cv.take<unsigned>(4),
+               o_part = cv.take<double>((size_t)16 * m->grid);
+  const size_t o_r64 = cv.take<double>(n), o_z64 = cv.take<double>(n), o_p64a = cv.take<double>(n),
+               o_p64b = cv.take<double>(n), o_q64 = cv.take<double>(n), o_q64b = cv.take<double>(n),
+               o_e64 = cv.take<double>(nE), o_e64b = cv.take<double>(nE);
+  const size_t o_d32 = cv.take<float>(n), o_r32 = cv.take<float>(n), o_z32 = cv.take<float>(n),
+               o_p32a = cv.take<float>(n), o_p32b = cv.take<float>(n), o_q32 = cv.take<float>(n),
+               o_e32 = cv.take<float>(nE);
+  const size_t o_Phi = cv.take<double>(n), o_qtmp = cv.take<double>(n), o_etmp = cv.take<double>(nE);
+  const size_t o_wt = cv.take<double>(ncol), o_etax = cv.take<double>(ncol), o_phisx = cv.take<double>(ncol),
+               o_R = cv.take<double>((size_t)2 * Nx * Q), o_scr = cv.take<double>((size_t)4 * Nx + 2 * (N + 1)),
+               o_ke = cv.take<double>(ncol), o_kp = cv.take<double>(ncol), o_ae = cv.take<double>(ncol),
+               o_ap = cv.take<double>(ncol), o_se = cv.take<double>(ncol), o_sp = cv.take<double>(ncol),
+               o_etad = cv.take<double>(ncol), o_phisd = cv.take<double>(ncol);
+  // surface tables
+  const size_t o_tD = cv.take<double>(Q * Q), o_tMD = cv.take<double>(Q * Q), o_tB = cv.take<double>((size_t)Q * Qf),
+               o_tI = cv.take<double>((size_t)Qf * Q), o_tF = cv.take<double>(Q * Q), o_tcw = cv.take<double>((size_t)Nz * Q),
+               o_tAii = cv.take<double>((size_t)Pm * Pm + 1), o_tZ = cv.take<double>((size_t)2 * Pm + 1),
+               o_tse = cv.take<double>(Nx), o_te = cv.take<double>(N), o_tm = cv.take<double>(N),
+               o_tcp = cv.take<double>(N), o_tz = cv.take<double>(N);
+  const size_t total = cv.off + 256;
+  cudaError_t ae = cudaMalloc(&m->pool, total);
+  if (ae != cudaSuccess) { delete m; return fail(SEM_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(ae)); }
+  auto D_ = [&](size_t o) { return reinterpret_cast<double*>(m->pool + o); };
+  auto F_ = [&](size_t o) { return reinterpret_cast<float*>(m->pool + o); };
+  int code = SEM_OK;
+  auto up = [&](size_t o, const std::vector<double>& v) {
+    if (code == SEM_OK && !v.empty()) {
+      cudaError_t e = cudaMemcpy(m->pool + o, v.data(), v.size() * sizeof(double), cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) code = fail(SEM_ERR_CUDA, std::string("upload: ") + cudaGetErrorString(e));
+    }
+  };
+  {
+    cudaError_t e = cudaMemset(m->pool, 0, total);
+    if (e != cudaSuccess) code = fail(SEM_ERR_CUDA, std::string("memset: ") + cudaGetErrorString(e));
+  }
+  up(o_h, std::vector<double>(h_h, h_h + ncol));
+  up(o_hx, hx_loc); up(o_dxe, dxe); up(o_dsl, dsl); up(o_sig, sig);
+  up(o_tD, L.D); up(o_tMD, MD); up(o_tB, B); up(o_tI, I); up(o_tF, F); up(o_tcw, cw);
+  up(o_tAii, Aii); up(o_tZ, Z); up(o_tse, se); up(o_te, th_e); up(o_tm, th_m); up(o_tcp, th_cp); up(o_tz, th_z);
+  if (code != SEM_OK) { cudaFree(m->pool); delete m; return code; }
+
+  DevGeom& g = m->g;
+  g.P = P; g.Nx = Nx; g.Nz = Nz; g.ncol = ncol; g.nrow = nrow; g.periodic = p.periodic ? 1 : 0;
+  g.h = D_(o_h); g.hx_loc = D_(o_hx); g.dxe = D_(o_dxe); g.dsl = D_(o_dsl); g.sig = D_(o_sig);
+  g.geo64 = D_(o_geo64); g.geo32 = F_(o_geo32); g.invdiag64 = D_(o_id64); g.invdiag32 = F_(o_id32);
+  g.status = reinterpret_cast<int*>(m->pool + o_status);
+  m->rec = reinterpret_cast<SolveRecord*>(m->pool + o_rec);
+
+  PcgArgs& a = m->pa;
+  a.r64 = D_(o_r64); a.z64 = D_(o_z64); a.p64a = D_(o_p64a); a.p64b = D_(o_p64b);
+  a.q64 = D_(o_q64); a.q64b = D_(o_q64b); a.edge64 = D_(o_e64); a.edge64b = D_(o_e64b);
+  a.d32 = F_(o_d32); a.r32 = F_(o_r32); a.z32 = F_(o_z32); a.p32a = F_(o_p32a); a.p32b = F_(o_p32b);
+  a.q32 = F_(o_q32); a.edge32 = F_(o_e32);
+  a.part = D_(o_part); a.part_stride = m->grid;
+  a.bar = reinterpret_cast<unsigned int*>(m->pool + o_bar);
+  a.rec = m->rec;
+  a.tol = p.tol; a.inner_rtol = 1e-4; a.max_iter = p.max_iter; a.mixed = p.precision == SEM_PREC_MIXED;
+
+  m->Phi = D_(o_Phi); m->qtmp = D_(o_qtmp); m->edgetmp = D_(o_etmp);
+  m->wt = D_(o_wt); m->etax = D_(o_etax); m->phisx = D_(o_phisx); m->R = D_(o_R); m->scr = D_(o_scr);
+  m->ke = D_(o_ke); m->kp = D_(o_kp); m->ae = D_(o_ae); m->ap = D_(o_ap); m->se = D_(o_se); m->sp = D_(o_sp);
+  m->eta_dev = D_(o_etad); m->phis_dev = D_(o_phisd);
+
+  SurfTables& t = m->st;
+  t.P = P; t.Pf = p.Pf; t.Nx = Nx; t.Nz = Nz; t.ncol = ncol; t.nrow = nrow; t.periodic = g.periodic; t.g = p.g;
+  t.D = D_(o_tD); t.MD = D_(o_tMD); t.B = D_(o_tB); t.I = D_(o_tI); t.F = D_(o_tF); t.cw = D_(o_tcw);
+  t.Aii = D_(o_tAii); t.Z = D_(o_tZ); t.se = D_(o_tse); t.dsl = g.dsl; t.h = g.h;
+  t.th_e = D_(o_te); t.th_m = D_(o_tm); t.th_cp = D_(o_tcp); t.th_z = D_(o_tz);
+  t.th_vlast = th_vlast; t.th_fac = th_fac; t.nif = N; t.filter_on = (p.filter_ic >= 0 && p.filter_ic < P) ? 1 : 0;
+  *out = m;
+  return SEM_OK;
+}
+
+void sem_mesh_destroy(sem_mesh* m) {
+  if (!m) return;
+  DeviceGuard dg(m->device);
+  cudaFree(m->pool);
+  delete m;
+}
+
+int sem_mesh_info(const sem_mesh* m, sem_info* info) {
+  if (!m || !info) return fail(SEM_ERR_INVALID_ARG, "NULL argument");
+  info->n_nodes = m->n;
+  info->n_unknowns = (int64_t)m->ncol * (m->nrow - 1);
+  info->ncol = m->ncol; info->nrow = m->nrow;
+  info->n_elements = m->p.Nx * m->p.Nz;
+  info->P = m->p.P; info->Pf = m->Pf; info->Nx = m->p.Nx; info->Nz = m->p.Nz;
+  info->periodic = m->p.periodic; info->precision = m->p.precision;
+  info->grid_ctas = m->grid;
+  return SEM_OK;
+}
+
+int sem_mesh_l2g(sem_mesh* m, int32_t* l2g_d, void* stream) {
+  if (!m || !l2g_d) return fail(SEM_ERR_INVALID_ARG, "NULL argument");
+  DeviceGuard dg(m->device);
+  CUDA_TRY(launch_l2g(m->g, l2g_d, (cudaStream_t)stream));
+  return SEM_OK;
+}
+
+int sem_update_geometry(sem_mesh* m, const double* eta_d, void* stream) {
+  if (!m || !eta_d) return fail(SEM_ERR_INVALID_ARG, "NULL argument");
+  DeviceGuard dg(m->device);
+  CUDA_TRY(launch_geometry(m->g, eta_d, (cudaStream_t)stream));
+  return SEM_OK;
+}
+
+int sem_laplace_apply(sem_mesh* m, const double* x_d, double* y_d, void* stream) {
+  if (!m || !x_d || !y_d || x_d == y_d) return fail(SEM_ERR_INVALID_ARG, "bad pointer");
+  DeviceGuard dg(m->device);
+  CUDA_TRY(launch_apply(m->g, x_d, y_d, m->qtmp, m->edgetmp, (cudaStream_t)stream));
+  return SEM_OK;
+}
+
+int sem_laplace_solve(sem_mesh* m, const double* phis_d, double* Phi_d, sem_solve_stats* st, void* stream) {
+  if (!m || !phis_d || !Phi_d) return fail(SEM_ERR_INVALID_ARG, "NULL argument");
+  DeviceGuard dg(m->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = do_solve(m, phis_d, Phi_d, s);
+  if (rc) return rc;
+  if (st) {
+    SolveRecord r{};
+    CUDA_TRY(cudaMemcpyAsync(&r, m->rec, sizeof(r), cudaMemcpyDeviceToHost, s));
+    rc = read_status(m, s);
+    st->iterations = r.iterations;
+    st->refinements = r.refinements;
+    st->rel_residual = r.rel_residual;
+    return rc;
+  }
+  return SEM_OK;
+}
+
+int sem_recover_gradient(sem_mesh* m, const double* Phi_d, const double* eta_d, const double* phis_d,
+                         double* w_surf_d, double* etax_d, double* phisx_d, void* stream) {
+  if (!m || !Phi_d || !eta_d || !phis_d || !w_surf_d || !etax_d || !phisx_d)
+    return fail(SEM_ERR_INVALID_ARG, "NULL argument");
+  DeviceGuard dg(m->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  CUDA_TRY(launch_wsurf(m->st, Phi_d, eta_d, w_surf_d, s));
+  CUDA_TRY(launch_sx(m->st, eta_d, phis_d, m->R, s));
+  CUDA_TRY(launch_mass1d(m->st, m->R, 2, etax_d, phisx_d, m->scr, s));
+  return SEM_OK;
+}
+
+int sem_zakharov_rhs(sem_mesh* m, const double* eta_d, const double* phis_d, double t, double* deta_d,
+                     double* dphis_d, void* stream) {
+  (void)t;
+  if (!m || !eta_d || !phis_d || !deta_d || !dphis_d) return fail(SEM_ERR_INVALID_ARG, "NULL argument");
+  DeviceGuard dg(m->device);
+  return do_rhs(m, eta_d, phis_d, deta_d, dphis_d, (cudaStream_t)stream);
+}
+
+int sem_apply_filter(sem_mesh* m, double* q_d, void* stream) {
+  if (!m || !q_d) return fail(SEM_ERR_INVALID_ARG, "NULL argument");
+  DeviceGuard dg(m->device);
+  CUDA_TRY(launch_filter(m->st, q_d, nullptr, (cudaStream_t)stream));
+  return SEM_OK;
+}
+
+int sem_rk4_step(sem_mesh* m, double* eta_d, double* phis_d, double* t, double dt, int nsteps, void* stream) {
+  if (!m || !eta_d || !phis_d || nsteps < 0 || !(dt > 0.0)) return fail(SEM_ERR_INVALID_ARG, "bad argument");
+  DeviceGuard dg(m->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = do_rk4(m, eta_d, phis_d, dt, nsteps, s);
+  if (rc) return rc;
+  rc = read_status(m, s);
+  if (t) *t += nsteps * dt;
+  return rc;
+}
+
+int sem_rk4_step_host(sem_mesh* m, double* eta_h, double* phis_h, double* t, double dt, int nsteps,
+                      void* stream) {
+  if (!m || !eta_h || !phis_h || nsteps < 0 || !(dt > 0.0)) return fail(SEM_ERR_INVALID_ARG, "bad argument");
+  DeviceGuard dg(m->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = sizeof(double) * m->ncol;
+  CUDA_TRY(cudaMemcpyAsync(m->eta_dev, eta_h, bytes, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(m->phis_dev, phis_h, bytes, cudaMemcpyHostToDevice, s));
+  int rc = do_rk4(m, m->eta_dev, m->phis_dev, dt, nsteps, s);
+  if (rc) return rc;
+  CUDA_TRY(cudaMemcpyAsync(eta_h, m->eta_dev, bytes, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaMemcpyAsync(phis_h, m->phis_dev, bytes, cudaMemcpyDeviceToHost, s));
+  rc = read_status(m, s);
+  if (t) *t += nsteps * dt;
+  return rc;
+}
+
+int sem_get_counters(sem_mesh* m, sem_counters* c, void* stream) {
+  if (!m || !c) return fail(SEM_ERR_INVALID_ARG, "NULL argument");
+  DeviceGuard dg(m->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  SolveRecord r{};
+  CUDA_TRY(cudaMemcpyAsync(&r, m->rec, sizeof(r), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  c->solves = r.solves;
+  c->iterations = r.total_iterations;
+  c->refinements = r.total_refinements;
+  c->max_rel_residual = r.max_rel_residual;
+  return SEM_OK;
+}
+
+int sem_reset_counters(sem_mesh* m, void* stream) {
+  if (!m) return fail(SEM_ERR_INVALID_ARG, "NULL argument");
+  DeviceGuard dg(m->device);
+  CUDA_TRY(cudaMemsetAsync(m->rec, 0, sizeof(SolveRecord), (cudaStream_t)stream));
+  return SEM_OK;
+}
+
+}  // extern "C"
