@@ -1,0 +1,366 @@
+"""Benchmark: Laplace DOF/s and RK4 steps/s of the σ-transformed SEM wave model on GB300.
+
+Workload (one "step"): one classical RK4 step of the steep periodic nonlinear wave
+(64×4 elements, P=6, P_f=9, filter (36,12,P-1), kh=1, H/L=0.08, dt=T/200) —
+four σ-geometry updates, four Dirichlet-lifted Laplace solves (persistent PCG),
+four gradient recoveries, four over-integrated Zakharov right-hand sides, the RK4
+combination and the modal filter, all in the library's CUDA kernels.
+
+value   = Laplace DOF/s = 4 · n_unknowns · steps / device time (FP64 path);
+e2e     = the same metric through sem_rk4_step_host (pinned host buffers,
+          host↔device copies of (η, φ̃) inside the timed region);
+roofline: dominant kernel = the persistent Krylov kernel, FP64-ALU bound;
+cpu_baseline: the CPU oracle on a bounded sample of the same workload.
+
+`--impl reference` times the CPU oracle itself (the reference arm).  Under
+torchrun each rank runs an independent replica of the tank (weak scaling, no
+data-path collective); rank 0 prints the JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Laplace DOF/s (RK4 steps/s alongside)"
+UNIT = "DOF/s"
+# Algorithmic FP64 work of one Krylov iteration (per-unit figures stated in the design notes):
+#   operator apply: 8(P+1)+7 flops per element-local node (gradients, fluxes, transposed sums)
+#   vector updates and dots: 13 flops per unknown
+FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 rate (vector and tensor alike)
+
+
+def workload():
+    from sem_workloads import c2_steep_periodic
+    return c2_steep_periodic()
+
+
+def flops_per_iteration(wl) -> float:
+    P = wl.P
+    return wl.Nx * wl.Nz * (P + 1) ** 2 * (8 * (P + 1) + 7) + 13 * wl.n_unknowns
+
+
+def flops_per_apply(wl) -> float:
+    P = wl.P
+    return wl.Nx * wl.Nz * (P + 1) ** 2 * (8 * (P + 1) + 7)
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader",
+                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1].split()[0]))
+                smax.append(float(parts[2].split()[0]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_source_hash() -> str:
+    src = os.path.join(ROOT, "paper_1512_02548_gb300", "csrc", "kernels_laplace.cu")
+    return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+
+
+def profiled_traffic(kernel: str):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if still current."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        data = json.load(open(path))
+    except Exception:
+        return None
+    ent = data.get(kernel)
+    if not ent or ent.get("source_sha256_16") != kernel_source_hash():
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+# ---------------------------------------------------------------------------------------------
+# CPU oracle timing (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------------------------
+def oracle_stage_sample(n_stages: int):
+    """Run n_stages RK4 stages of the oracle on the bench workload; returns (seconds, DOF)."""
+    import numpy as np
+    from oracle import sem as osem
+    from sem_workloads import initial_state
+    wl = workload()
+    om = osem.mesh_for(wl)
+    eta, phis = initial_state(wl, om.xcol, om.h)
+    om.surface_mass()
+    om.mass2d()
+    om.laplace_solve(eta, phis)          # RCM ordering and mass factors are set-up, not timed
+    t0 = time.perf_counter()
+    for _ in range(n_stages):
+        de, dp = om.zakharov_rhs(eta, phis)
+        eta = eta + 0.5 * wl.dt * de
+        phis = phis + 0.5 * wl.dt * dp
+    dt = time.perf_counter() - t0
+    assert np.all(np.isfinite(eta))
+    return dt, n_stages * wl.n_unknowns
+
+
+def oracle_subprocess(n_stages: int) -> dict:
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        env[k] = "1"
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    code = ("import json,sys; sys.path.insert(0, %r); import bench; "
+            "t, dof = bench.oracle_stage_sample(%d); print(json.dumps({'t': t, 'dof': dof}))" % (ROOT, n_stages))
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=900)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    wl = workload()
+    # warm-up stages, then K timed stages: one "step" = one RK4 stage (one Laplace solve)
+    oracle_subprocess(max(1, min(args.warmup, 1)))
+    res = oracle_subprocess(args.steps)
+    value = res["dof"] / res["t"]
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * res["t"] / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": wl.name, "Nx": wl.Nx, "Nz": wl.Nz, "P": wl.P, "Pf": wl.Pf,
+                   "n_unknowns": wl.n_unknowns, "step": "one RK4 stage of the CPU oracle",
+                   "parallelism": "replicas"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} RK4 stages of the C2 tank (one banded-Cholesky "
+                                   f"Laplace solve each), single thread"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------------------------
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    import paper_1512_02548_gb300 as sem
+    from sem_workloads import initial_state
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    sem.load_library()
+
+    wl = workload()
+    # column positions need GLL nodes; take them from a throw-away oracle-free formula:
+    # the library only needs edges and depth, initial data are sampled at the columns.
+    h = np.full(wl.ncol, wl.depth)
+    mesh = sem.Mesh.from_workload(wl, h=h, precision=args.precision)
+    xcol = column_positions(wl)
+    eta0, phis0 = initial_state(wl, xcol, h)
+    eta = torch.tensor(eta0, device=dev)
+    phis = torch.tensor(phis0, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > 129 MB L2
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        mesh.rk4_step(eta, phis, wl.dt, 1)
+    torch.cuda.synchronize()
+    mesh.reset_counters()
+    mesh.timing()                                   # discard
+    mesh.enable_timing(True)
+    launches0 = sem.launch_count()
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    total_ms = 0.0
+    for _ in range(args.steps):
+        flush.zero_()                               # evict L2 between timed steps (not timed)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        mesh.rk4_step(eta, phis, wl.dt, 1)          # synchronises at its end (status check)
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    gpu_launches = sem.launch_count() - launches0
+    mesh.enable_timing(False)
+    tm = mesh.timing()
+    cnt = mesh.counters()
+    t_max = total_ms
+    if world > 1:
+        tt = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    dof_per_step = 4 * wl.n_unknowns
+    value = world * args.steps * dof_per_step / (t_max / 1e3)
+    steps_per_s = world * args.steps / (t_max / 1e3)
+
+    # roofline of the dominant kernel: the persistent Krylov kernel, FP64 ALU bound
+    solves = max(cnt.solves, 1)
+    applies = cnt.iterations + 2 * cnt.solves + (cnt.refinements if args.precision == "mixed" else 0)
+    flops = (cnt.iterations * flops_per_iteration(wl) + (applies - cnt.iterations) * flops_per_apply(wl))
+    avg_launch_ms = tm.krylov_ms / max(tm.krylov_launches, 1)
+    flops_per_launch = flops / max(tm.krylov_launches, 1)
+    achieved = flops_per_launch / (avg_launch_ms / 1e3) / 1e12
+    krylov_share = tm.krylov_ms / total_ms if total_ms > 0 else None
+
+    # end to end through the host-buffer entry point
+    he = torch.tensor(eta0).pin_memory().numpy()
+    hp = torch.tensor(phis0).pin_memory().numpy()
+    for _ in range(2):
+        mesh.rk4_step_host(he, hp, wl.dt, 1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        mesh.rk4_step_host(he, hp, wl.dt, 1)
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        tt = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    e2e = {"value": world * args.steps * dof_per_step / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": 2 * 8 * wl.ncol, "d2h_bytes_per_step": 2 * 8 * wl.ncol}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": wl.name, "Nx": wl.Nx, "Nz": wl.Nz, "P": wl.P, "Pf": wl.Pf,
+                   "n_unknowns": wl.n_unknowns, "dt": wl.dt, "precision": args.precision,
+                   "l2": "flushed between timed steps (256 MB write, untimed)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "rk4_steps_per_s": steps_per_s,
+        "krylov": {"solves": cnt.solves, "iterations_per_solve": cnt.iterations / solves,
+                   "refinements": cnt.refinements, "max_rel_residual": cnt.max_rel_residual,
+                   "share_of_step_time": krylov_share},
+        "roofline": {"bound": "alu", "kernel": "k_pcg (persistent Krylov)", "achieved": achieved,
+                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                     "peak_source": "nominal GB300 FP64 rate, 1.25 TFLOP/s",
+                     "traffic": profiled_traffic("k_pcg")},
+        "e2e": e2e,
+        "gpu_launches": gpu_launches,
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        try:
+            res = oracle_subprocess(args.cpu_stages)
+            line["cpu_baseline"] = {"value": res["dof"] / res["t"], "unit": UNIT, "cores": 1, "kind": "oracle",
+                                    "sample": f"{args.cpu_stages} RK4 stages of the same tank (one banded-"
+                                              f"Cholesky Laplace solve each), single thread, "
+                                              f"{res['t']:.1f} s"}
+        except Exception as e:  # the GPU number stands on its own
+            line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                    "sample": f"failed: {str(e)[-200:]}"}
+    if rank == 0:
+        print(json.dumps(line))
+    mesh.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def column_positions(wl):
+    """Column x positions from the GLL nodes of order P (Newton on P'_P; input generation only)."""
+    import numpy as np
+    P = wl.P
+    r = -np.cos(np.pi * np.arange(P + 1) / P)
+    for _ in range(100):
+        x = r[1:-1]
+        p0, p1 = np.ones_like(x), x.copy()
+        dp0, dp1 = np.zeros_like(x), np.ones_like(x)
+        for k in range(1, P):
+            p0, p1 = p1, ((2 * k + 1) * x * p1 - k * p0) / (k + 1)
+            dp0, dp1 = dp1, dp0 + (2 * k + 1) * p0
+        d2 = (2 * x * dp1 - P * (P + 1) * p1) / (1 - x * x)
+        r[1:-1] = x - dp1 / d2
+    from sem_workloads import column_x
+    return column_x(wl, r)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--cpu-stages", type=int, default=8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

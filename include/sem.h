@@ -177,6 +177,17 @@ int sem_rk4_step_host(sem_mesh* m, double* eta_h, double* phis_h, double* t, dou
 int sem_get_counters(sem_mesh* m, sem_counters* c, void* stream);
 int sem_reset_counters(sem_mesh* m, void* stream);
 
+/* Kernel timing.  While enabled, every launch of the persistent Krylov kernel is
+ * bracketed by CUDA events recorded on its stream.  sem_get_timing waits for the
+ * recorded events, returns the number of those launches and their summed device
+ * time in milliseconds, and clears the record. */
+typedef struct sem_timing {
+  int64_t krylov_launches;
+  double krylov_ms;
+} sem_timing;
+int sem_enable_timing(sem_mesh* m, int on);
+int sem_get_timing(sem_mesh* m, sem_timing* t);
+
 /* Number of kernels this library has launched in the calling process. */
 int64_t sem_launch_count(void);
 

@@ -26,8 +26,8 @@ SEM_PREC_FP64, SEM_PREC_MIXED = 0, 1
 EXPORTED = ("sem_mesh_create", "sem_mesh_destroy", "sem_mesh_info", "sem_mesh_l2g",
             "sem_update_geometry", "sem_laplace_apply", "sem_laplace_solve",
             "sem_recover_gradient", "sem_zakharov_rhs", "sem_apply_filter", "sem_rk4_step",
-            "sem_rk4_step_host", "sem_get_counters", "sem_reset_counters", "sem_launch_count",
-            "sem_last_error")
+            "sem_rk4_step_host", "sem_get_counters", "sem_reset_counters", "sem_enable_timing",
+            "sem_get_timing", "sem_launch_count", "sem_last_error")
 
 
 class sem_params(ctypes.Structure):
@@ -53,6 +53,10 @@ class sem_solve_stats(ctypes.Structure):
 class sem_counters(ctypes.Structure):
     _fields_ = [("solves", ctypes.c_int64), ("iterations", ctypes.c_int64),
                 ("refinements", ctypes.c_int64), ("max_rel_residual", ctypes.c_double)]
+
+
+class sem_timing(ctypes.Structure):
+    _fields_ = [("krylov_launches", ctypes.c_int64), ("krylov_ms", ctypes.c_double)]
 
 
 _lib = None
@@ -82,6 +86,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sem_rk4_step_host.argtypes = [vp, dp, dp, ctypes.POINTER(ctypes.c_double), ctypes.c_double, ip, vp]
     lib.sem_get_counters.argtypes = [vp, ctypes.POINTER(sem_counters), vp]
     lib.sem_reset_counters.argtypes = [vp, vp]
+    lib.sem_enable_timing.argtypes = [vp, ip]
+    lib.sem_get_timing.argtypes = [vp, ctypes.POINTER(sem_timing)]
     lib.sem_launch_count.restype = ctypes.c_int64
     lib.sem_launch_count.argtypes = []
     lib.sem_last_error.restype = ctypes.c_char_p
@@ -224,3 +230,11 @@ class Mesh:
 
     def reset_counters(self):
         _check(load_library().sem_reset_counters(self._h, _stream()))
+
+    def enable_timing(self, on: bool = True):
+        _check(load_library().sem_enable_timing(self._h, int(bool(on))))
+
+    def timing(self) -> sem_timing:
+        t = sem_timing()
+        _check(load_library().sem_get_timing(self._h, ctypes.byref(t)))
+        return t

@@ -8,6 +8,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/sem.h"
@@ -97,6 +98,10 @@ struct sem_mesh {
   double *wt = nullptr, *etax = nullptr, *phisx = nullptr, *R = nullptr, *scr = nullptr;
   double *ke = nullptr, *kp = nullptr, *ae = nullptr, *ap = nullptr, *se = nullptr, *sp = nullptr;
   double *eta_dev = nullptr, *phis_dev = nullptr;
+  // optional event timing of the Krylov kernel
+  bool timing = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
+  std::vector<cudaEvent_t> spare;
 };
 
 namespace {
@@ -115,11 +120,26 @@ int read_status(sem_mesh* m, cudaStream_t s) {
   return fail(SEM_ERR_CUDA, "unknown device status");
 }
 
+cudaError_t take_event(sem_mesh* m, cudaEvent_t* ev) {
+  if (!m->spare.empty()) { *ev = m->spare.back(); m->spare.pop_back(); return cudaSuccess; }
+  return cudaEventCreate(ev);
+}
+
 int do_solve(sem_mesh* m, const double* phis, double* Phi, cudaStream_t s) {
   PcgArgs a = m->pa;
   a.x = Phi;
   a.phis = phis;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (m->timing) {
+    CUDA_TRY(take_event(m, &e0));
+    CUDA_TRY(take_event(m, &e1));
+    CUDA_TRY(cudaEventRecord(e0, s));
+  }
   CUDA_TRY(launch_pcg(m->g, a, m->grid, m->smem, s));
+  if (m->timing) {
+    CUDA_TRY(cudaEventRecord(e1, s));
+    m->events.emplace_back(e0, e1);
+  }
   return SEM_OK;
 }
 
@@ -401,6 +421,8 @@ int sem_mesh_create(const sem_params* pin, const double* x_edges_h, const double
 void sem_mesh_destroy(sem_mesh* m) {
   if (!m) return;
   DeviceGuard dg(m->device);
+  for (auto& pr : m->events) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
+  for (auto e : m->spare) cudaEventDestroy(e);
   cudaFree(m->pool);
   delete m;
 }
@@ -522,6 +544,30 @@ int sem_get_counters(sem_mesh* m, sem_counters* c, void* stream) {
   c->iterations = r.total_iterations;
   c->refinements = r.total_refinements;
   c->max_rel_residual = r.max_rel_residual;
+  return SEM_OK;
+}
+
+int sem_enable_timing(sem_mesh* m, int on) {
+  if (!m) return fail(SEM_ERR_INVALID_ARG, "NULL argument");
+  m->timing = on != 0;
+  return SEM_OK;
+}
+
+int sem_get_timing(sem_mesh* m, sem_timing* t) {
+  if (!m || !t) return fail(SEM_ERR_INVALID_ARG, "NULL argument");
+  DeviceGuard dg(m->device);
+  double total = 0.0;
+  for (auto& pr : m->events) {
+    CUDA_TRY(cudaEventSynchronize(pr.second));
+    float ms = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&ms, pr.first, pr.second));
+    total += ms;
+    m->spare.push_back(pr.first);
+    m->spare.push_back(pr.second);
+  }
+  t->krylov_launches = (int64_t)m->events.size();
+  t->krylov_ms = total;
+  m->events.clear();
   return SEM_OK;
 }
 
