@@ -63,6 +63,11 @@ enum sem_precision {
   SEM_PREC_MIXED = 1  /* FP32 inner Krylov iterations, FP64 residual refinement  */
 };
 
+enum sem_preconditioner {
+  SEM_PRECOND_SEPARABLE = 0, /* exact inverse of the σ-separable part (slope terms dropped) */
+  SEM_PRECOND_JACOBI = 1     /* diagonal                                                   */
+};
+
 /* Discretisation and solver parameters (§3.1, §3.3, §3.4). */
 typedef struct sem_params {
   int P;               /* GLL order in x and σ, 2 ≤ P ≤ SEM_MAX_P                    */
@@ -77,6 +82,7 @@ typedef struct sem_params {
   double tol;          /* Laplace solve: stop when ‖r‖₂ ≤ tol·‖b‖₂ (0 → 1e-13)       */
   int max_iter;        /* Laplace solve: Krylov iteration cap (0 → 5000)             */
   int precision;       /* enum sem_precision                                          */
+  int precond;         /* enum sem_preconditioner                                     */
 } sem_params;
 
 typedef struct sem_info {

@@ -22,6 +22,7 @@ SEM_OK = 0
 SEM_ERRORS = {1: "SEM_ERR_INVALID_ARG", 2: "SEM_ERR_OOM", 3: "SEM_ERR_CUDA",
               4: "SEM_ERR_NOT_CONVERGED", 5: "SEM_ERR_NONFINITE", 6: "SEM_ERR_TIMEOUT"}
 SEM_PREC_FP64, SEM_PREC_MIXED = 0, 1
+SEM_PRECOND_SEPARABLE, SEM_PRECOND_JACOBI = 0, 1
 
 EXPORTED = ("sem_mesh_create", "sem_mesh_destroy", "sem_mesh_info", "sem_mesh_l2g",
             "sem_update_geometry", "sem_laplace_apply", "sem_laplace_solve",
@@ -35,7 +36,7 @@ class sem_params(ctypes.Structure):
                 ("periodic", ctypes.c_int), ("Pf", ctypes.c_int), ("filter_ic", ctypes.c_int),
                 ("filter_alpha", ctypes.c_double), ("filter_s", ctypes.c_double),
                 ("g", ctypes.c_double), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
-                ("precision", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("precond", ctypes.c_int)]
 
 
 class sem_info(ctypes.Structure):
@@ -138,11 +139,15 @@ class Mesh:
 
     def __init__(self, P: int, Nx: int, Nz: int, x_edges, h, periodic: bool = True, Pf: int = 0,
                  filter_alpha: float = 0.0, filter_s: float = 0.0, filter_ic: int = -1,
-                 g: float = 9.81, tol: float = 1e-13, max_iter: int = 5000, precision: str = "fp64"):
+                 g: float = 9.81, tol: float = 1e-13, max_iter: int = 5000, precision: str = "fp64",
+                 precond: str = "separable"):
         lib = load_library()
+        if precision not in ("fp64", "mixed") or precond not in ("separable", "jacobi"):
+            raise ValueError("precision must be fp64|mixed and precond separable|jacobi")
         prm = sem_params(P=P, Nx=Nx, Nz=Nz, periodic=int(bool(periodic)), Pf=Pf, filter_ic=filter_ic,
                          filter_alpha=filter_alpha, filter_s=filter_s, g=g, tol=tol, max_iter=max_iter,
-                         precision=SEM_PREC_MIXED if precision == "mixed" else SEM_PREC_FP64)
+                         precision=SEM_PREC_MIXED if precision == "mixed" else SEM_PREC_FP64,
+                         precond=SEM_PRECOND_JACOBI if precond == "jacobi" else SEM_PRECOND_SEPARABLE)
         xe = np.ascontiguousarray(x_edges, dtype=np.float64)
         hh = np.ascontiguousarray(h, dtype=np.float64)
         handle = ctypes.c_void_p()
@@ -156,13 +161,14 @@ class Mesh:
         self.n_unknowns = int(self.info.n_unknowns)
 
     @classmethod
-    def from_workload(cls, wl, h=None, precision: str = "fp64", tol: float = 1e-13, max_iter: int = 5000):
+    def from_workload(cls, wl, h=None, precision: str = "fp64", tol: float = 1e-13, max_iter: int = 5000,
+                      precond: str = "separable"):
         edges = wl.element_edges()
         if h is None:
             h = np.full(wl.ncol, wl.depth)
         return cls(wl.P, wl.Nx, wl.Nz, edges, h, periodic=wl.periodic, Pf=wl.Pf,
                    filter_alpha=wl.filter_alpha, filter_s=wl.filter_s, filter_ic=wl.filter_ic,
-                   g=wl.g, tol=tol, max_iter=max_iter, precision=precision)
+                   g=wl.g, tol=tol, max_iter=max_iter, precision=precision, precond=precond)
 
     def close(self):
         if getattr(self, "_h", None):

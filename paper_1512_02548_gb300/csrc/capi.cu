@@ -92,6 +92,7 @@ struct sem_mesh {
   DevGeom g{};
   SurfTables st{};
   PcgArgs pa{};
+  PrecSetup ps{};
   SolveRecord* rec = nullptr;
   // workspace
   double *Phi = nullptr, *qtmp = nullptr, *edgetmp = nullptr;
@@ -143,9 +144,16 @@ int do_solve(sem_mesh* m, const double* phis, double* Phi, cudaStream_t s) {
   return SEM_OK;
 }
 
+int do_geometry(sem_mesh* m, const double* eta, cudaStream_t s) {
+  CUDA_TRY(launch_geometry(m->g, eta, s));
+  if (m->p.precond == SEM_PRECOND_SEPARABLE) CUDA_TRY(launch_prec_setup(m->g, m->ps, s));
+  return SEM_OK;
+}
+
 int do_rhs(sem_mesh* m, const double* eta, const double* phis, double* de, double* dp, cudaStream_t s) {
   const int Q = m->p.P + 1;
-  CUDA_TRY(launch_geometry(m->g, eta, s));
+  int rc0 = do_geometry(m, eta, s);
+  if (rc0) return rc0;
   int rc = do_solve(m, phis, m->Phi, s);
   if (rc) return rc;
   CUDA_TRY(launch_wsurf(m->st, m->Phi, eta, m->wt, s));
@@ -203,6 +211,8 @@ int sem_mesh_create(const sem_params* pin, const double* x_edges_h, const double
   if (p.Pf < p.P || p.Pf > 3 * p.P) return fail(SEM_ERR_INVALID_ARG, "Pf must be in [P, 3P]");
   if (p.precision != SEM_PREC_FP64 && p.precision != SEM_PREC_MIXED)
     return fail(SEM_ERR_INVALID_ARG, "unknown precision");
+  if (p.precond != SEM_PRECOND_SEPARABLE && p.precond != SEM_PRECOND_JACOBI)
+    return fail(SEM_ERR_INVALID_ARG, "unknown preconditioner");
   if (p.tol <= 0.0) p.tol = 1e-13;
   if (p.max_iter <= 0) p.max_iter = 5000;
   const int P = p.P, Q = P + 1, Nx = p.Nx, Nz = p.Nz;
@@ -329,10 +339,35 @@ int sem_mesh_create(const sem_params* pin, const double* x_edges_h, const double
     }
   }
 
+  // σ-separable preconditioner: Kσ S = Mσ S Λ on the interior rows (Dirichlet at the surface),
+  // Kσ = Σ_l (2/Δσ_l) Dᵀ W D, Mσ = Σ_l (Δσ_l/2) W (GLL-lumped, as in the stiffness quadrature).
+  const int nr = nrow - 1;
+  std::vector<double> Sg((size_t)nr * nr), lam(nr);
+  {
+    std::vector<long double> Ks((size_t)nrow * nrow, 0.0L), Ms(nrow, 0.0L);
+    for (int l = 0; l < Nz; ++l)
+      for (int a = 0; a < Q; ++a) {
+        Ms[l * P + a] += 0.5L * dsl[l] * L.w[a];
+        for (int b = 0; b < Q; ++b) {
+          long double s2 = 0.0L;
+          for (int c = 0; c < Q; ++c) s2 += (long double)L.D[c * Q + a] * L.w[c] * L.D[c * Q + b];
+          Ks[(size_t)(l * P + a) * nrow + l * P + b] += (2.0L / dsl[l]) * s2;
+        }
+      }
+    std::vector<long double> B((size_t)nr * nr), ev, V;
+    for (int i = 0; i < nr; ++i)
+      for (int j = 0; j < nr; ++j) B[(size_t)i * nr + j] = Ks[(size_t)i * nrow + j] / std::sqrt(Ms[i] * Ms[j]);
+    sym_eig(B, nr, ev, V);
+    for (int k = 0; k < nr; ++k) lam[k] = (double)ev[k];
+    for (int j = 0; j < nr; ++j)
+      for (int k = 0; k < nr; ++k) Sg[(size_t)j * nr + k] = (double)(V[(size_t)j * nr + k] / std::sqrt(Ms[j]));
+  }
+  const size_t tri_bytes = (size_t)3 * N * sizeof(double) <= 96 * 1024 ? (size_t)3 * N * sizeof(double) : 0;
+
   // ---- device allocation -------------------------------------------------------
   sem_mesh* m = new sem_mesh;
   m->p = p; m->device = dev; m->ncol = ncol; m->nrow = nrow; m->n = n; m->Pf = p.Pf; m->nif = N;
-  cudaError_t ge = pcg_grid_size(P, Nz, nrow, Nx, p.precision == SEM_PREC_MIXED, &m->grid, &m->smem);
+  cudaError_t ge = pcg_grid_size(P, Nz, nrow, Nx, p.precision == SEM_PREC_MIXED, tri_bytes, &m->grid, &m->smem);
   if (ge != cudaSuccess) { delete m; return fail(SEM_ERR_CUDA, std::string("Krylov kernel occupancy: ") + cudaGetErrorString(ge)); }
   if (const char* lim = std::getenv("SEM_GRID_LIMIT")) {   // tuning/testing knob: cap the Krylov grid
     const int v = std::atoi(lim);
@@ -353,6 +388,19 @@ int sem_mesh_create(const sem_params* pin, const double* x_edges_h, const double
                o_p32a = cv.take<float>(n), o_p32b = cv.take<float>(n), o_q32 = cv.take<float>(n),
                o_e32 = cv.take<float>(nE);
   const size_t o_Phi = cv.take<double>(n), o_qtmp = cv.take<double>(n), o_etmp = cv.take<double>(nE);
+  const size_t o_r64b = cv.take<double>(n), o_r32b = cv.take<float>(n);
+  const size_t nEl = (size_t)nr * Nx, nIf = (size_t)nr * N;
+  const size_t o_S64 = cv.take<double>((size_t)nr * nr), o_S32 = cv.take<float>((size_t)nr * nr),
+               o_lam = cv.take<double>(nr), o_schur = cv.take<double>(nEl * 3),
+               o_A64 = cv.take<double>(nEl * Pm * Pm + 1), o_A32 = cv.take<float>(nEl * Pm * Pm + 1),
+               o_Z64 = cv.take<double>(nEl * 2 * Pm + 1), o_Z32 = cv.take<float>(nEl * 2 * Pm + 1),
+               o_te64 = cv.take<double>(nIf), o_tm64 = cv.take<double>(nIf), o_tcp64 = cv.take<double>(nIf),
+               o_tz64 = cv.take<double>(nIf), o_te32 = cv.take<float>(nIf), o_tm32 = cv.take<float>(nIf),
+               o_tcp32 = cv.take<float>(nIf), o_tz32 = cv.take<float>(nIf), o_tvl64 = cv.take<double>(nr),
+               o_tfac64 = cv.take<double>(nr), o_tvl32 = cv.take<float>(nr), o_tfac32 = cv.take<float>(nr),
+               o_gL64 = cv.take<double>(nEl), o_gR64 = cv.take<double>(nEl), o_gL32 = cv.take<float>(nEl),
+               o_gR32 = cv.take<float>(nEl), o_zb64 = cv.take<double>(nIf), o_zb32 = cv.take<float>(nIf),
+               o_rh64 = cv.take<double>((size_t)ncol * nr), o_rh32 = cv.take<float>((size_t)ncol * nr);
   const size_t o_wt = cv.take<double>(ncol), o_etax = cv.take<double>(ncol), o_phisx = cv.take<double>(ncol),
                o_R = cv.take<double>((size_t)2 * Nx * Q), o_scr = cv.take<double>((size_t)4 * Nx + 2 * (N + 1)),
                o_ke = cv.take<double>(ncol), o_kp = cv.take<double>(ncol), o_ae = cv.take<double>(ncol),
@@ -384,6 +432,12 @@ int sem_mesh_create(const sem_params* pin, const double* x_edges_h, const double
   up(o_hx, hx_loc); up(o_dxe, dxe); up(o_dsl, dsl); up(o_sig, sig);
   up(o_tD, L.D); up(o_tMD, MD); up(o_tB, B); up(o_tI, I); up(o_tF, F); up(o_tcw, cw);
   up(o_tAii, Aii); up(o_tZ, Z); up(o_tse, se); up(o_te, th_e); up(o_tm, th_m); up(o_tcp, th_cp); up(o_tz, th_z);
+  up(o_S64, Sg); up(o_lam, lam);
+  if (code == SEM_OK) {
+    std::vector<float> S32(Sg.begin(), Sg.end());
+    cudaError_t e = cudaMemcpy(m->pool + o_S32, S32.data(), S32.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) code = fail(SEM_ERR_CUDA, std::string("upload: ") + cudaGetErrorString(e));
+  }
   if (code != SEM_OK) { cudaFree(m->pool); delete m; return code; }
 
   DevGeom& g = m->g;
@@ -402,6 +456,23 @@ int sem_mesh_create(const sem_params* pin, const double* x_edges_h, const double
   a.bar = reinterpret_cast<unsigned int*>(m->pool + o_bar);
   a.rec = m->rec;
   a.tol = p.tol; a.inner_rtol = 1e-4; a.max_iter = p.max_iter; a.mixed = p.precision == SEM_PREC_MIXED;
+  a.r64b = D_(o_r64b); a.r32b = F_(o_r32b);
+  a.precond = p.precond == SEM_PRECOND_JACOBI ? PREC_JACOBI : PREC_SEPARABLE;
+  a.tri_smem = (int)tri_bytes;
+  a.tri_smem_offset = (int)tri_smem_offset(P, nrow, Nz);
+  PrecSetup& ps = m->ps;
+  ps.nr = nr; ps.nif = N; ps.lam = D_(o_lam); ps.schur = D_(o_schur);
+  ps.Aii64 = D_(o_A64); ps.Z64 = D_(o_Z64); ps.te64 = D_(o_te64); ps.tm64 = D_(o_tm64); ps.tcp64 = D_(o_tcp64);
+  ps.tz64 = D_(o_tz64); ps.tvl64 = D_(o_tvl64); ps.tfac64 = D_(o_tfac64);
+  ps.Aii32 = F_(o_A32); ps.Z32 = F_(o_Z32); ps.te32 = F_(o_te32); ps.tm32 = F_(o_tm32); ps.tcp32 = F_(o_tcp32);
+  ps.tz32 = F_(o_tz32); ps.tvl32 = F_(o_tvl32); ps.tfac32 = F_(o_tfac32);
+  ps.scratch = nullptr;
+  ps.v64 = PrecView<double>{nr, N, D_(o_S64), ps.Aii64, ps.Z64, ps.te64, ps.tm64, ps.tcp64, ps.tz64, ps.tvl64,
+                            ps.tfac64, D_(o_gL64), D_(o_gR64), D_(o_zb64), D_(o_rh64)};
+  ps.v32 = PrecView<float>{nr, N, F_(o_S32), ps.Aii32, ps.Z32, ps.te32, ps.tm32, ps.tcp32, ps.tz32, ps.tvl32,
+                           ps.tfac32, F_(o_gL32), F_(o_gR32), F_(o_zb32), F_(o_rh32)};
+  a.pv64 = ps.v64;
+  a.pv32 = ps.v32;
 
   m->Phi = D_(o_Phi); m->qtmp = D_(o_qtmp); m->edgetmp = D_(o_etmp);
   m->wt = D_(o_wt); m->etax = D_(o_etax); m->phisx = D_(o_phisx); m->R = D_(o_R); m->scr = D_(o_scr);
@@ -449,8 +520,7 @@ int sem_mesh_l2g(sem_mesh* m, int32_t* l2g_d, void* stream) {
 int sem_update_geometry(sem_mesh* m, const double* eta_d, void* stream) {
   if (!m || !eta_d) return fail(SEM_ERR_INVALID_ARG, "NULL argument");
   DeviceGuard dg(m->device);
-  CUDA_TRY(launch_geometry(m->g, eta_d, (cudaStream_t)stream));
-  return SEM_OK;
+  return do_geometry(m, eta_d, (cudaStream_t)stream);
 }
 
 int sem_laplace_apply(sem_mesh* m, const double* x_d, double* y_d, void* stream) {

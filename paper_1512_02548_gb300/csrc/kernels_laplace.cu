@@ -194,9 +194,9 @@ template <> __device__ __forceinline__ const float* geo_ptr<float>(const DevGeom
 
 // Apply A = −𝓛 on element column ex.  `loadx(ex,a,iz)` gives the input value of local
 // column a, row iz; `store(ex,a,iz,y)` receives the element column's contribution.
-// Returns this thread's share of Σ x·(A_e x) over the element column.
+// Returns this thread's share of Σ x·(A_e x) over the element column (accumulated in T).
 template <int P, class T, class LoadX, class Store>
-__device__ __forceinline__ double apply_element_column(const DevGeom& g, Smem<P, T>& s, int ex,
+__device__ __forceinline__ T apply_element_column(const DevGeom& g, Smem<P, T>& s, int ex,
                                                        LoadX loadx, Store store) {
   constexpr int Q = P + 1;
   const int nrow = g.nrow, Nz = g.Nz;
@@ -235,7 +235,7 @@ __device__ __forceinline__ double apply_element_column(const DevGeom& g, Smem<P,
     s.F2[t] = fmx(G12, ur, G22 * ut);
   }
   __syncthreads();
-  double part = 0.0;
+  T part = 0;
   for (int t = threadIdx.x; t < Q * nrow; t += blockDim.x) {
     const int a = t / nrow, iz = t - a * nrow;
     const int l = iz / P, b = iz - l * P;
@@ -260,7 +260,7 @@ __device__ __forceinline__ double apply_element_column(const DevGeom& g, Smem<P,
       }
     }
     store(ex, a, iz, y);
-    part += (double)s.X[t] * (double)y;
+    part = fmx(s.X[t], y, part);
   }
   __syncthreads();
   return part;
@@ -366,22 +366,23 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* bar, int* status, int
   return *s_flag != 0;
 }
 
-// Deterministic block sum of K values (all threads get the result).
-template <int K>
-__device__ __forceinline__ void block_sum(double (&v)[K], double* red) {
+// Deterministic block sum of K values of type A (all threads get the result).
+template <int K, class A>
+__device__ __forceinline__ void block_sum(A (&v)[K], double* red) {
 #pragma unroll
   for (int k = 0; k < K; ++k)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+  A* rr = reinterpret_cast<A*>(red);
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   __syncthreads();
   if (lane == 0)
 #pragma unroll
-    for (int k = 0; k < K; ++k) red[k * 32 + wid] = v[k];
+    for (int k = 0; k < K; ++k) rr[k * 32 + wid] = v[k];
   __syncthreads();
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    double s = lane < nw ? red[k * 32 + lane] : 0.0;
+    A s = lane < nw ? rr[k * 32 + lane] : A(0);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     v[k] = s;
@@ -397,9 +398,9 @@ __device__ __forceinline__ void grid_sum(const double* part, int stride, int slo
   if (threadIdx.x < 32) {
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      const volatile double* p = part + ((size_t)slot * 4 + k) * stride;
+      const double* p = part + ((size_t)slot * 4 + k) * stride;
       double s = 0.0;
-      for (int c = lane; c < (int)gridDim.x; c += 32) s += p[c];
+      for (int c = lane; c < (int)gridDim.x; c += 32) s += __ldcg(p + c);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
       if (lane == 0) red[128 + k] = s;
@@ -411,11 +412,11 @@ __device__ __forceinline__ void grid_sum(const double* part, int stride, int slo
   __syncthreads();
 }
 
-template <int K>
-__device__ __forceinline__ void put_partials(double* part, int stride, int slot, const double (&v)[K]) {
+template <int K, class A>
+__device__ __forceinline__ void put_partials(double* part, int stride, int slot, const A (&v)[K]) {
   if (threadIdx.x == 0)
 #pragma unroll
-    for (int k = 0; k < K; ++k) part[((size_t)slot * 4 + k) * stride + blockIdx.x] = v[k];
+    for (int k = 0; k < K; ++k) part[((size_t)slot * 4 + k) * stride + blockIdx.x] = (double)v[k];
 }
 
 // ------------------------------------------------------------------------------------
@@ -433,73 +434,298 @@ __device__ __forceinline__ Range my_range(const DevGeom& g) {
   return r;
 }
 
-// Inner PCG on A x = r0 (vectors of type T), starting from x (given) and residual r.
-// Expects r, z, rz, rr already computed for the start (slot `sl` holds rr, rz).
-// Stops when rr ≤ target or after max_it iterations.  Returns iterations, or −1 on
-// a barrier timeout.
-template <int P, class T>
-__device__ int inner_pcg(const DevGeom& g, Smem<P, T>& s, const Range& R, T* x, T* r, T* z, T* pa,
-                         T* pb, T* q, T* edge, const T* invdiag, double* part, int stride,
-                         unsigned int* bar, double* red, int* s_flag, double rr, double rz,
+__device__ __forceinline__ bool owns_local_col(const DevGeom& g, int ex, int a) {
+  return a < g.P || (!g.periodic && ex == g.Nx - 1);
+}
+
+// ---- σ-separable preconditioner ----------------------------------------------------
+// M⁻¹ = (I⊗S) [Kx(d) ⊗ I + Mx(1/d) ⊗ Λ]⁻¹ (I⊗Sᵀ), the exact inverse of the Kronecker-sum
+// operator obtained from A by dropping the K12 (slope) coupling and the K12² part of K22.
+// Kx(d) = Σ_e (2/Δx) Dᵀ diag(w d) D and Mx(1/d) = Σ_e (Δx/2) diag(w/d) are 1D operators in x
+// (periodic or walls); Kσ S = Mσ S Λ is the generalized eigenproblem of the 1D σ stiffness
+// (Dirichlet at the surface) against the GLL-lumped σ mass.  Each σ-mode is a 1D SEM problem
+// in x, solved by static condensation of the element interiors and a tridiagonal (cyclic)
+// interface system.
+
+// Phase "update": r_new = r_old − α q on owned nodes (and the halo column, in shared memory),
+// x += α p; then r̂ = Sᵀ r per column and the per-mode condensed right-hand sides gL, gR.
+// With update == false, r_new is r_old.  Accumulates Σ r² (own) into acc[0]; for the
+// Jacobi preconditioner also z = D⁻¹ r and Σ r z into acc[1].
+template <int P, class T, class A>
+__device__ void phase_update(const DevGeom& g, Smem<P, T>& s, const Range& R, bool update, T alpha,
+                             T* x, const T* p, const T* q, const T* edge, const T* r_old, T* r_new,
+                             const T* invdiag, T* z, int precond, const PrecView<T>& pv, A (&acc)[2]) {
+  constexpr int Q = P + 1, Pm = P - 1;
+  const int nrow = g.nrow;
+  if (precond == PREC_JACOBI) {
+    const int ncols = R.c1 - R.c0;
+    for (int t = threadIdx.x; t < ncols * nrow; t += blockDim.x) {
+      const int col = R.c0 + t / nrow, iz = t - (t / nrow) * nrow;
+      if (iz == nrow - 1) continue;
+      const size_t i = (size_t)col * nrow + iz;
+      T rv = r_old[i];
+      if (update) {
+        T qv = q[i];
+        if (has_left_edge(g, col)) qv += ldcg(edge + (size_t)left_element(g, col) * nrow + iz);
+        x[i] = fmx(alpha, p[i], x[i]);
+        rv = fmx(-alpha, qv, rv);
+        r_new[i] = rv;
+      }
+      const T zv = rv * invdiag[i];
+      z[i] = zv;
+      acc[0] += (A)rv * (A)rv;
+      acc[1] += (A)rv * (A)zv;
+    }
+    return;
+  }
+  const int nr = pv.nr;
+  T* X = s.X;     // [Q][nr] residual of the element column
+  T* RH = s.F1;   // [Q][nr] σ-transformed residual
+  for (int ex = R.e0; ex < R.e1; ++ex) {
+    for (int t = threadIdx.x; t < Q * nr; t += blockDim.x) {
+      const int a = t / nr, j = t - a * nr;
+      const int col = col_of(g, ex, a);
+      const size_t i = (size_t)col * nrow + j;
+      const bool own = owns_local_col(g, ex, a);
+      T rv = ldcg(r_old + i);
+      if (update) {
+        T qv = ldcg(q + i);
+        if (has_left_edge(g, col)) qv += ldcg(edge + (size_t)left_element(g, col) * nrow + j);
+        rv = fmx(-alpha, qv, rv);
+        if (own) {
+          r_new[i] = rv;
+          x[i] = fmx(alpha, p[i], x[i]);
+        }
+      }
+      if (own) acc[0] += (A)rv * (A)rv;
+      X[t] = rv;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < Q * nr; t += blockDim.x) {
+      const int a = t / nr, k = t - a * nr;
+      const T* Xa = X + a * nr;
+      T v = 0;
+      for (int j = 0; j < nr; ++j) v = fmx(pv.S[j * nr + k], Xa[j], v);
+      RH[t] = v;
+      if (owns_local_col(g, ex, a)) pv.rhat[(size_t)col_of(g, ex, a) * nr + k] = v;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < nr; k += blockDim.x) {
+      const T* Zk = pv.Z + ((size_t)k * g.Nx + ex) * 2 * Pm;
+      T l = RH[k], r = RH[P * nr + k];
+#pragma unroll
+      for (int m = 0; m < Pm; ++m) {
+        const T f = RH[(1 + m) * nr + k];
+        l = fmx(-Zk[m], f, l);
+        r = fmx(-Zk[Pm + m], f, r);
+      }
+      pv.gL[(size_t)k * g.Nx + ex] = l;
+      pv.gR[(size_t)k * g.Nx + ex] = r;
+    }
+    __syncthreads();
+  }
+}
+
+// Interface solve per σ-mode (modes spread over CTAs): assemble g_j = gL_j + gR_{j−1}, Thomas
+// sweep with the pivots of the set-up, Sherman–Morrison closure when periodic.  `sm` is shared
+// scratch of 3·nif values (right-hand side, forward coefficients, backward coefficients), or
+// nullptr to run the sweeps on global memory.
+template <class T>
+__device__ void phase_interface(const DevGeom& g, const PrecView<T>& pv, T* sm, T* s_c) {
+  const int N = pv.nif, Nx = g.Nx;
+  for (int k = blockIdx.x; k < pv.nr; k += gridDim.x) {
+    const T* gl = pv.gL + (size_t)k * Nx;
+    const T* gr = pv.gR + (size_t)k * Nx;
+    const T* te = pv.te + (size_t)k * N;
+    const T* tm = pv.tm + (size_t)k * N;
+    const T* tcp = pv.tcp + (size_t)k * N;
+    T* zb = pv.zb + (size_t)k * N;
+    T* G = sm ? sm : zb;
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+      T v;
+      if (g.periodic) v = ldcg(gl + j) + ldcg(gr + (j == 0 ? Nx - 1 : j - 1));
+      else v = (j < Nx ? ldcg(gl + j) : T(0)) + (j > 0 ? ldcg(gr + j - 1) : T(0));
+      G[j] = v * tm[j];                                   // g_j m_j
+      if (sm) {
+        sm[N + j] = j > 0 ? te[j - 1] * tm[j] : T(0);     // e_{j−1} m_j
+        sm[2 * N + j] = tcp[j];                           // c'_j
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      // forward: y_j = g_j m_j − (e_{j−1} m_j) y_{j−1};  backward: y_j −= c'_j y_{j+1}
+      T prev = G[0];
+      for (int j = 1; j < N; ++j) {
+        const T a = sm ? sm[N + j] : te[j - 1] * tm[j];
+        prev = fmx(-a, prev, G[j]);
+        G[j] = prev;
+      }
+      T next = G[N - 1];
+      for (int j = N - 2; j >= 0; --j) {
+        next = fmx(-(sm ? sm[2 * N + j] : tcp[j]), next, G[j]);
+        G[j] = next;
+      }
+      *s_c = g.periodic ? (G[0] + pv.tvl[k] * G[N - 1]) * pv.tfac[k] : T(0);
+    }
+    __syncthreads();
+    const T c = *s_c;
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+      const T y = G[j];
+      zb[j] = g.periodic ? fmx(-c, pv.tz[(size_t)k * N + j], y) : y;
+    }
+    __syncthreads();
+  }
+}
+
+// Back-substitution of the element interiors and z = S ẑ on owned columns; Σ r z into acc.
+template <int P, class T, class A>
+__device__ void phase_backsub(const DevGeom& g, Smem<P, T>& s, const Range& R, const PrecView<T>& pv,
+                              const T* r, T* z, A& acc) {
+  constexpr int Q = P + 1, Pm = P - 1;
+  const int nrow = g.nrow, nr = pv.nr, N = pv.nif;
+  T* ZH = s.F1;   // [Q][nr]
+  for (int ex = R.e0; ex < R.e1; ++ex) {
+    const int jl = ex, jr = (ex + 1 == N) ? 0 : ex + 1;
+    for (int t = threadIdx.x; t < Q * nr; t += blockDim.x) {
+      const int a = t / nr, k = t - a * nr;
+      const T zl = ldcg(pv.zb + (size_t)k * N + jl);
+      const T zr = ldcg(pv.zb + (size_t)k * N + jr);
+      T v;
+      if (a == 0) v = zl;
+      else if (a == P) v = zr;
+      else {
+        const int i = a - 1;
+        const T* Ai = pv.Aii + (((size_t)k * g.Nx + ex) * Pm + i) * Pm;
+        const T* Zk = pv.Z + ((size_t)k * g.Nx + ex) * 2 * Pm;
+        v = 0;
+#pragma unroll
+        for (int m = 0; m < Pm; ++m) v = fmx(Ai[m], pv.rhat[(size_t)(ex * P + 1 + m) * nr + k], v);
+        v = fmx(-Zk[i], zl, v);
+        v = fmx(-Zk[Pm + i], zr, v);
+      }
+      ZH[t] = v;
+    }
+    __syncthreads();
+    const int na = owns_local_col(g, ex, P) ? Q : P;
+    for (int t = threadIdx.x; t < na * nr; t += blockDim.x) {
+      const int a = t / nr, j = t - a * nr;
+      const T* Za = ZH + a * nr;
+      const T* Sj = pv.S + j * nr;
+      T v = 0;
+      for (int k = 0; k < nr; ++k) v = fmx(Sj[k], Za[k], v);
+      const size_t i = (size_t)col_of(g, ex, a) * nrow + j;
+      z[i] = v;
+      acc += (A)r[i] * (A)v;
+    }
+    __syncthreads();
+  }
+}
+
+// z = M⁻¹ r (and the update of r when `update`), three grid phases for the separable
+// preconditioner, one for Jacobi.  On return red-sums: rr (own r²) and rz.  False on timeout.
+template <int P, class T, class A>
+__device__ bool precondition(const DevGeom& g, Smem<P, T>& s, const Range& R, const PcgArgs& PA,
+                             const PrecView<T>& pv, bool update, T alpha, T* x, const T* p, const T* q,
+                             const T* edge, const T* r_old, T* r_new, const T* invdiag, T* z,
+                             T* tri_sm, double* red, int* s_flag, double& rr, double& rz) {
+  A acc[2] = {A(0), A(0)};
+  phase_update<P, T, A>(g, s, R, update, alpha, x, p, q, edge, r_old, r_new, invdiag, z, PA.precond, pv,
+                        acc);
+  const T* rcur = update ? r_new : r_old;
+  if (PA.precond != PREC_JACOBI) {
+    A a1[1] = {acc[0]};
+    block_sum<1, A>(a1, red);
+    acc[0] = a1[0];
+    if (!grid_barrier(PA.bar, g.status, s_flag)) return false;
+    phase_interface<T>(g, pv, tri_sm, reinterpret_cast<T*>(red + 150));
+    if (!grid_barrier(PA.bar, g.status, s_flag)) return false;
+    A rzl = A(0);
+    phase_backsub<P, T, A>(g, s, R, pv, rcur, z, rzl);
+    A a2[1] = {rzl};
+    block_sum<1, A>(a2, red);
+    double out[2] = {(double)acc[0], (double)a2[0]};
+    put_partials<2, double>(PA.part, PA.part_stride, 3, out);
+  } else {
+    block_sum<2, A>(acc, red);
+    double out[2] = {(double)acc[0], (double)acc[1]};
+    put_partials<2, double>(PA.part, PA.part_stride, 3, out);
+  }
+  if (!grid_barrier(PA.bar, g.status, s_flag)) return false;
+  double sums[2];
+  grid_sum<2>(PA.part, PA.part_stride, 3, sums, red);
+  rr = sums[0];
+  rz = sums[1];
+  return true;
+}
+
+// Inner PCG on A x = r (vectors of type T, accumulations in A), from the given x and the
+// residual in r[0] with z, rr, rz already computed.  Stops when rr ≤ target or after max_it
+// iterations.  Returns iterations, or −1 on a barrier timeout.
+template <int P, class T, class A>
+__device__ int inner_pcg(const DevGeom& g, Smem<P, T>& s, const Range& R, const PcgArgs& PA,
+                         const PrecView<T>& pv, T* x, T* r0, T* r1, T* z, T* pa, T* pb, T* q, T* edge,
+                         const T* invdiag, T* tri_sm, double* red, int* s_flag, double rr, double rz,
                          double target, int max_it, double* rr_out) {
   const int nrow = g.nrow;
   int k = 0;
   double rz_prev = 1.0;
   T* p_old = pa;
   T* p_new = pb;
+  T* r_cur = r0;
+  T* r_nxt = r1;
+  __shared__ T s_scal[2];
+  __shared__ int s_stop;
   while (true) {
-    if (!(rr == rr) || isinf(rr)) { if (threadIdx.x == 0) atomicOr(g.status, ST_NONFINITE); break; }
-    if (rr <= target || k >= max_it) break;
-    const T beta = (T)(k == 0 ? 0.0 : rz / rz_prev);
+    // scalar control on one thread (FP64 work on every thread would cost the FP64 pipe)
+    if (threadIdx.x == 0) {
+      int stop = 0;
+      if (!(rr == rr) || isinf(rr)) { atomicOr(g.status, ST_NONFINITE); stop = 1; }
+      else if (rr <= target || k >= max_it) stop = 1;
+      s_stop = stop;
+      s_scal[1] = (T)(k == 0 ? 0.0 : rz / rz_prev);
+    }
+    __syncthreads();
+    if (s_stop) break;
+    const T beta = s_scal[1];
     const bool first = (k == 0);
     // Phase A: p_new = z + β p_old (own columns written, halo column rebuilt), q = A p_new
-    double pap[1] = {0.0};
+    A pap[1] = {A(0)};
     for (int ex = R.e0; ex < R.e1; ++ex) {
-      pap[0] += apply_element_column<P, T>(
+      pap[0] += (A)apply_element_column<P, T>(
           g, s, ex,
           [&](int e, int a, int iz) -> T {
             if (iz == nrow - 1) return (T)0;
             const size_t i = (size_t)col_of(g, e, a) * nrow + iz;
             const T zi = ldcg(z + i);
             const T pn = first ? zi : fmx(beta, ldcg(p_old + i), zi);
-            if (a < P || (!g.periodic && e == g.Nx - 1)) p_new[i] = pn;
+            if (owns_local_col(g, e, a)) p_new[i] = pn;
             return pn;
           },
           [&](int e, int a, int iz, T y) {
-            if (a < P || (!g.periodic && e == g.Nx - 1)) q[(size_t)col_of(g, e, a) * nrow + iz] = y;
+            if (owns_local_col(g, e, a)) q[(size_t)col_of(g, e, a) * nrow + iz] = y;
             else edge[(size_t)e * nrow + iz] = y;
           });
     }
-    block_sum<1>(pap, red);
-    put_partials<1>(part, stride, 2, pap);
-    if (!grid_barrier(bar, g.status, s_flag)) return -1;
-    grid_sum<1>(part, stride, 2, pap, red);
-    const T alpha = (T)(rz / pap[0]);
-    // Phase B: x += α p, r −= α q, z = M⁻¹ r on owned nodes
-    double acc[2] = {0.0, 0.0};
-    const int ncols = R.c1 - R.c0;
-    for (int t = threadIdx.x; t < ncols * nrow; t += blockDim.x) {
-      const int col = R.c0 + t / nrow, iz = t - (t / nrow) * nrow;
-      if (iz == nrow - 1) continue;
-      const size_t i = (size_t)col * nrow + iz;
-      T qv = q[i];
-      if (has_left_edge(g, col)) qv += ldcg(edge + (size_t)left_element(g, col) * nrow + iz);
-      x[i] = fmx(alpha, p_new[i], x[i]);
-      const T rv = fmx(-alpha, qv, r[i]);
-      r[i] = rv;
-      const T zv = rv * invdiag[i];
-      z[i] = zv;
-      acc[0] += (double)rv * (double)rv;
-      acc[1] += (double)rv * (double)zv;
+    block_sum<1, A>(pap, red);
+    put_partials<1, A>(PA.part, PA.part_stride, 2, pap);
+    if (!grid_barrier(PA.bar, g.status, s_flag)) return -1;
+    double papd[1];
+    grid_sum<1>(PA.part, PA.part_stride, 2, papd, red);
+    if (threadIdx.x == 0) s_scal[0] = (T)(rz / papd[0]);
+    __syncthreads();
+    const T alpha = s_scal[0];
+    // Phase B(+C+D): x += α p, r −= α q, z = M⁻¹ r
+    double rr_n, rz_n;
+    if (!precondition<P, T, A>(g, s, R, PA, pv, true, alpha, x, p_new, q, edge, r_cur, r_nxt, invdiag, z,
+                               tri_sm, red, s_flag, rr_n, rz_n))
+      return -1;
+    if (threadIdx.x == 0) {
+      rr = rr_n;
+      rz_prev = rz;
+      rz = rz_n;
     }
-    block_sum<2>(acc, red);
-    put_partials<2>(part, stride, 3, acc);
-    if (!grid_barrier(bar, g.status, s_flag)) return -1;
-    grid_sum<2>(part, stride, 3, acc, red);
-    rr = acc[0];
-    rz_prev = rz;
-    rz = acc[1];
     T* tmp = p_old; p_old = p_new; p_new = tmp;
+    tmp = r_cur; r_cur = r_nxt; r_nxt = tmp;
     ++k;
   }
   *rr_out = rr;
@@ -507,12 +733,10 @@ __device__ int inner_pcg(const DevGeom& g, Smem<P, T>& s, const Range& R, T* x, 
 }
 
 // FP64 residual r = b − A_II x = −(A [x; φ̃])_I on owned nodes, with ‖b‖² when asked
-// (b = −(A [0; φ̃])_I).  Two passes: element columns, then edge fix.  Returns false on
-// a barrier timeout.  On return rr/bb (and rz for z = M⁻¹r when want_z) are summed.
+// (b = −(A [0; φ̃])_I).  Returns false on a barrier timeout; rr (and bb) summed on return.
 template <int P>
 __device__ bool fp64_residual(const DevGeom& g, Smem<P, double>& s, const Range& R, const PcgArgs& A,
-                              bool want_b, bool want_z, double* red, int* s_flag, double& rr,
-                              double& bb, double& rz) {
+                              bool want_b, double* red, int* s_flag, double& rr, double& bb) {
   const int nrow = g.nrow;
   const double* x = A.x;
   const double* phis = A.phis;
@@ -524,7 +748,7 @@ __device__ bool fp64_residual(const DevGeom& g, Smem<P, double>& s, const Range&
           return iz == nrow - 1 ? phis[col] : ldcg(x + (size_t)col * nrow + iz);
         },
         [&](int e, int a, int iz, double y) {
-          if (a < P || (!g.periodic && e == g.Nx - 1)) A.q64[(size_t)col_of(g, e, a) * nrow + iz] = y;
+          if (owns_local_col(g, e, a)) A.q64[(size_t)col_of(g, e, a) * nrow + iz] = y;
           else A.edge64[(size_t)e * nrow + iz] = y;
         });
     if (want_b)
@@ -532,12 +756,12 @@ __device__ bool fp64_residual(const DevGeom& g, Smem<P, double>& s, const Range&
           g, s, ex,
           [&](int e, int a, int iz) -> double { return iz == nrow - 1 ? phis[col_of(g, e, a)] : 0.0; },
           [&](int e, int a, int iz, double y) {
-            if (a < P || (!g.periodic && e == g.Nx - 1)) A.q64b[(size_t)col_of(g, e, a) * nrow + iz] = y;
+            if (owns_local_col(g, e, a)) A.q64b[(size_t)col_of(g, e, a) * nrow + iz] = y;
             else A.edge64b[(size_t)e * nrow + iz] = y;
           });
   }
   if (!grid_barrier(A.bar, g.status, s_flag)) return false;
-  double acc[3] = {0.0, 0.0, 0.0};
+  double acc[2] = {0.0, 0.0};
   const int ncols = R.c1 - R.c0;
   for (int t = threadIdx.x; t < ncols * nrow; t += blockDim.x) {
     const int col = R.c0 + t / nrow, iz = t - (t / nrow) * nrow;
@@ -555,19 +779,13 @@ __device__ bool fp64_residual(const DevGeom& g, Smem<P, double>& s, const Range&
       if (le) bv += ldcg(A.edge64b + ie);
       acc[1] += bv * bv;
     }
-    if (want_z) {
-      const double zv = rv * g.invdiag64[i];
-      A.z64[i] = zv;
-      acc[2] += rv * zv;
-    }
   }
-  block_sum<3>(acc, red);
-  put_partials<3>(A.part, A.part_stride, 0, acc);
+  block_sum<2, double>(acc, red);
+  put_partials<2, double>(A.part, A.part_stride, 0, acc);
   if (!grid_barrier(A.bar, g.status, s_flag)) return false;
-  grid_sum<3>(A.part, A.part_stride, 0, acc, red);
+  grid_sum<2>(A.part, A.part_stride, 0, acc, red);
   rr = acc[0];
   if (want_b) bb = acc[1];
-  rz = acc[2];
   return true;
 }
 
@@ -581,9 +799,9 @@ __global__ void __launch_bounds__(kThreads) k_pcg(DevGeom g, PcgArgs A) {
   Smem<P, double> s64;
   s64.carve(smem_raw, nrow, g.Nz);
   s64.load_tables(g);
+  unsigned char* tri_raw = smem_raw + A.tri_smem_offset;
   double rr = 0.0, bb = 0.0, rz = 0.0;
-  // r = b − A x0 and ‖b‖ (FP64)
-  if (!fp64_residual<P>(g, s64, R, A, true, !MIXED, red, &s_flag, rr, bb, rz)) return;
+  if (!fp64_residual<P>(g, s64, R, A, true, red, &s_flag, rr, bb)) return;
   const double target = A.tol * A.tol * bb;
   int iters = 0, refinements = 0;
   if (bb == 0.0) {
@@ -595,44 +813,43 @@ __global__ void __launch_bounds__(kThreads) k_pcg(DevGeom g, PcgArgs A) {
     }
     rr = 0.0;
   } else if (!MIXED) {
+    double* tri = A.tri_smem ? reinterpret_cast<double*>(tri_raw) : nullptr;
+    double rr0;
+    if (!precondition<P, double, double>(g, s64, R, A, A.pv64, false, 0.0, A.x, nullptr, nullptr, nullptr,
+                                         A.r64, A.r64, g.invdiag64, A.z64, tri, red, &s_flag, rr0, rz))
+      return;
     double rr_out = rr;
-    iters = inner_pcg<P, double>(g, s64, R, A.x, A.r64, A.z64, A.p64a, A.p64b, A.q64, A.edge64,
-                                 g.invdiag64, A.part, A.part_stride, A.bar, red, &s_flag, rr, rz,
-                                 target, A.max_iter, &rr_out);
+    iters = inner_pcg<P, double, double>(g, s64, R, A, A.pv64, A.x, A.r64, A.r64b, A.z64, A.p64a, A.p64b,
+                                         A.q64, A.edge64, g.invdiag64, tri, red, &s_flag, rr, rz, target,
+                                         A.max_iter, &rr_out);
     if (iters < 0) return;
     rr = rr_out;
   } else {
     Smem<P, float> s32;
     s32.carve(smem_raw, nrow, g.Nz);
+    float* tri = A.tri_smem ? reinterpret_cast<float*>(tri_raw) : nullptr;
     while (rr > target && iters < A.max_iter) {
       if (!(rr == rr) || isinf(rr)) { if (threadIdx.x == 0) atomicOr(g.status, ST_NONFINITE); break; }
-      // inner: A δ = r in FP32 from δ = 0
       __syncthreads();
       s32.load_tables(g);
-      __syncthreads();
-      double acc[2] = {0.0, 0.0};
+      // inner: A δ = r in FP32 from δ = 0
       const int ncols = R.c1 - R.c0;
       for (int t = threadIdx.x; t < ncols * nrow; t += blockDim.x) {
         const int col = R.c0 + t / nrow, iz = t - (t / nrow) * nrow;
         const size_t i = (size_t)col * nrow + iz;
-        if (iz == nrow - 1) { A.d32[i] = 0.f; A.r32[i] = 0.f; A.z32[i] = 0.f; continue; }
-        const float rv = (float)A.r64[i];
-        const float zv = rv * g.invdiag32[i];
         A.d32[i] = 0.f;
-        A.r32[i] = rv;
-        A.z32[i] = zv;
-        acc[0] += (double)rv * rv;
-        acc[1] += (double)rv * zv;
+        A.r32[i] = iz == nrow - 1 ? 0.f : (float)A.r64[i];
       }
-      block_sum<2>(acc, red);
-      put_partials<2>(A.part, A.part_stride, 1, acc);
       if (!grid_barrier(A.bar, g.status, &s_flag)) return;
-      grid_sum<2>(A.part, A.part_stride, 1, acc, red);
-      double rr_in = acc[0];
-      const double tgt_in = fmax(A.inner_rtol * A.inner_rtol * acc[0], 0.25 * target);
-      const int it = inner_pcg<P, float>(g, s32, R, A.d32, A.r32, A.z32, A.p32a, A.p32b, A.q32,
-                                         A.edge32, g.invdiag32, A.part, A.part_stride, A.bar, red,
-                                         &s_flag, acc[0], acc[1], tgt_in, A.max_iter - iters, &rr_in);
+      double rr_in, rz_in;
+      if (!precondition<P, float, float>(g, s32, R, A, A.pv32, false, 0.f, A.d32, nullptr, nullptr, nullptr,
+                                         A.r32, A.r32, g.invdiag32, A.z32, tri, red, &s_flag, rr_in, rz_in))
+        return;
+      const double tgt_in = fmax(A.inner_rtol * A.inner_rtol * rr_in, 0.25 * target);
+      double rr_out = rr_in;
+      const int it = inner_pcg<P, float, float>(g, s32, R, A, A.pv32, A.d32, A.r32, A.r32b, A.z32, A.p32a,
+                                                A.p32b, A.q32, A.edge32, g.invdiag32, tri, red, &s_flag,
+                                                rr_in, rz_in, tgt_in, A.max_iter - iters, &rr_out);
       if (it < 0) return;
       iters += it;
       ++refinements;
@@ -646,8 +863,8 @@ __global__ void __launch_bounds__(kThreads) k_pcg(DevGeom g, PcgArgs A) {
       __syncthreads();
       s64.load_tables(g);
       if (!grid_barrier(A.bar, g.status, &s_flag)) return;
-      double dummy_b = 0.0, dummy_z = 0.0;
-      if (!fp64_residual<P>(g, s64, R, A, false, false, red, &s_flag, rr, dummy_b, dummy_z)) return;
+      double dummy_b = 0.0;
+      if (!fp64_residual<P>(g, s64, R, A, false, red, &s_flag, rr, dummy_b)) return;
       if (it == 0) break;   // no progress possible
     }
   }
@@ -662,6 +879,141 @@ __global__ void __launch_bounds__(kThreads) k_pcg(DevGeom g, PcgArgs A) {
     rec->total_refinements += refinements;
     if (rel > rec->max_rel_residual) rec->max_rel_residual = rel;
     if (rr > target) atomicOr(g.status, ST_NOT_CONVERGED);
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// Set-up of the separable preconditioner for the current geometry.
+// ------------------------------------------------------------------------------------
+// One thread per (mode k, element e): element matrix E = (2/Δx) Dᵀ diag(w d) D +
+// λ_k (Δx/2) diag(w/d), inverse of its interior block, Z = E_bi E_ii⁻¹ and the 2×2 Schur block.
+template <int P>
+__global__ void k_prec_elem(DevGeom g, PrecSetup ps) {
+  constexpr int Q = P + 1, Pm = P - 1;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ps.nr * g.Nx) return;
+  const int k = t / g.Nx, ex = t - k * g.Nx;
+  const double* D = c_D64 + d_off(P);
+  const double* w = c_w64 + w_off(P);
+  const double* geo = g.geo64 + (size_t)ex * Q * 4;
+  const double dxe = g.dxe[ex], lam = ps.lam[k];
+  double E[Q][Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i)
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+      double s = 0.0;
+#pragma unroll
+      for (int a = 0; a < Q; ++a) s = fma(D[a * Q + i] * w[a] * geo[a * 4 + 0], D[a * Q + j], s);
+      E[i][j] = (2.0 / dxe) * s;
+    }
+#pragma unroll
+  for (int i = 0; i < Q; ++i) E[i][i] += lam * 0.5 * dxe * w[i] * geo[i * 4 + 1];
+  // invert the interior block (SPD) by Gauss–Jordan without pivoting
+  double Ai[Pm][Pm], Bm[Pm][Pm];
+#pragma unroll
+  for (int i = 0; i < Pm; ++i)
+#pragma unroll
+    for (int j = 0; j < Pm; ++j) { Bm[i][j] = E[1 + i][1 + j]; Ai[i][j] = (i == j) ? 1.0 : 0.0; }
+#pragma unroll
+  for (int c = 0; c < Pm; ++c) {
+    const double inv = 1.0 / Bm[c][c];
+#pragma unroll
+    for (int j = 0; j < Pm; ++j) { Bm[c][j] *= inv; Ai[c][j] *= inv; }
+#pragma unroll
+    for (int r = 0; r < Pm; ++r) {
+      if (r == c) continue;
+      const double f = Bm[r][c];
+#pragma unroll
+      for (int j = 0; j < Pm; ++j) { Bm[r][j] -= f * Bm[c][j]; Ai[r][j] -= f * Ai[c][j]; }
+    }
+  }
+  double Z0[Pm], Z1[Pm];
+#pragma unroll
+  for (int i = 0; i < Pm; ++i) {
+    double a0 = 0.0, a1 = 0.0;
+#pragma unroll
+    for (int m = 0; m < Pm; ++m) { a0 = fma(E[0][1 + m], Ai[m][i], a0); a1 = fma(E[P][1 + m], Ai[m][i], a1); }
+    Z0[i] = a0; Z1[i] = a1;
+  }
+  double S00 = E[0][0], S01 = E[0][P], S11 = E[P][P];
+#pragma unroll
+  for (int i = 0; i < Pm; ++i) {
+    S00 -= Z0[i] * E[1 + i][0];
+    S01 -= Z0[i] * E[1 + i][P];
+    S11 -= Z1[i] * E[1 + i][P];
+  }
+  const size_t base = (size_t)t;
+  double* A64 = ps.Aii64 + base * Pm * Pm;
+  float* A32 = ps.Aii32 + base * Pm * Pm;
+#pragma unroll
+  for (int i = 0; i < Pm; ++i)
+#pragma unroll
+    for (int j = 0; j < Pm; ++j) { A64[i * Pm + j] = Ai[i][j]; A32[i * Pm + j] = (float)Ai[i][j]; }
+  double* Z64 = ps.Z64 + base * 2 * Pm;
+  float* Z32 = ps.Z32 + base * 2 * Pm;
+#pragma unroll
+  for (int i = 0; i < Pm; ++i) {
+    Z64[i] = Z0[i]; Z64[Pm + i] = Z1[i];
+    Z32[i] = (float)Z0[i]; Z32[Pm + i] = (float)Z1[i];
+  }
+  ps.schur[base * 3 + 0] = S00;
+  ps.schur[base * 3 + 1] = S01;
+  ps.schur[base * 3 + 2] = S11;
+}
+
+// One thread per mode: interface tridiagonal, Thomas pivots and the Sherman–Morrison closure
+// for periodic meshes (γ = −d_0, u = (γ,0,…,0,e_{N−1}), v = (1,0,…,0,e_{N−1}/γ)).
+__global__ void k_prec_tri(DevGeom g, PrecSetup ps) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= ps.nr) return;
+  const int N = ps.nif, Nx = g.Nx;
+  const double* sc = ps.schur + (size_t)k * Nx * 3;
+  double* te = ps.te64 + (size_t)k * N;
+  double* tm = ps.tm64 + (size_t)k * N;
+  double* tcp = ps.tcp64 + (size_t)k * N;
+  double* tz = ps.tz64 + (size_t)k * N;
+  // d_j = S00(j) + S11(j−1), e_j = S01(j)
+  auto dj = [&](int j) {
+    double v = 0.0;
+    if (g.periodic) v = sc[j * 3 + 0] + sc[(j == 0 ? Nx - 1 : j - 1) * 3 + 2];
+    else v = (j < Nx ? sc[j * 3 + 0] : 0.0) + (j > 0 ? sc[(j - 1) * 3 + 2] : 0.0);
+    return v;
+  };
+  const double corner = g.periodic ? sc[(Nx - 1) * 3 + 1] : 0.0;
+  const double gamma = g.periodic ? -dj(0) : 0.0;
+  double cp_prev = 0.0, e_prev = 0.0;
+  for (int j = 0; j < N; ++j) {
+    double d = dj(j);
+    if (g.periodic && j == 0) d -= gamma;
+    if (g.periodic && j == N - 1) d -= corner * corner / gamma;
+    const double e = (j < N - 1) ? sc[j * 3 + 1] : 0.0;
+    const double m = 1.0 / (j == 0 ? d : d - e_prev * cp_prev);
+    const double cp = e * m;
+    te[j] = e; tm[j] = m; tcp[j] = cp;
+    cp_prev = cp; e_prev = e;
+  }
+  if (g.periodic) {
+    // y = T'⁻¹ u
+    double prev = gamma * tm[0];
+    tz[0] = prev;
+    for (int j = 1; j < N; ++j) {
+      const double uj = (j == N - 1) ? corner : 0.0;
+      prev = (uj - te[j - 1] * prev) * tm[j];
+      tz[j] = prev;
+    }
+    for (int j = N - 2; j >= 0; --j) tz[j] -= tcp[j] * tz[j + 1];
+    const double vl = corner / gamma;
+    ps.tvl64[k] = vl;
+    ps.tfac64[k] = 1.0 / (1.0 + tz[0] + vl * tz[N - 1]);
+    ps.tvl32[k] = (float)vl;
+    ps.tfac32[k] = (float)ps.tfac64[k];
+  }
+  for (int j = 0; j < N; ++j) {
+    ps.te32[(size_t)k * N + j] = (float)te[j];
+    ps.tm32[(size_t)k * N + j] = (float)tm[j];
+    ps.tcp32[(size_t)k * N + j] = (float)tcp[j];
+    ps.tz32[(size_t)k * N + j] = (float)tz[j];
   }
 }
 
@@ -736,8 +1088,13 @@ static cudaError_t pcg_occupancy(size_t smem, int* per_sm) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_pcg<P, MIXED>, kThreads, smem);
 }
 
-cudaError_t pcg_grid_size(int P, int Nz, int nrow, int Nx, int mixed, int* grid, size_t* smem) {
-  *smem = apply_smem_bytes(P, nrow, Nz, sizeof(double));
+size_t tri_smem_offset(int P, int nrow, int Nz) {
+  return (apply_smem_bytes(P, nrow, Nz, sizeof(double)) + 15) & ~size_t(15);
+}
+
+cudaError_t pcg_grid_size(int P, int Nz, int nrow, int Nx, int mixed, size_t tri_smem, int* grid,
+                          size_t* smem) {
+  *smem = tri_smem_offset(P, nrow, Nz) + tri_smem;
   int dev = 0, sms = 0, per_sm = 0;
   cudaError_t e;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
@@ -749,6 +1106,17 @@ cudaError_t pcg_grid_size(int P, int Nz, int nrow, int Nx, int mixed, int* grid,
   long long cap = (long long)per_sm * sms;
   *grid = (int)(Nx < cap ? Nx : cap);
   return cudaSuccess;
+}
+
+cudaError_t launch_prec_setup(const DevGeom& g, const PrecSetup& ps, cudaStream_t s) {
+  const int n1 = ps.nr * g.Nx;
+  SEM_DISPATCH_P(g.P, (k_prec_elem<PP><<<(n1 + 63) / 64, 64, 0, s>>>(g, ps)));
+  count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_prec_tri<<<(ps.nr + 31) / 32, 32, 0, s>>>(g, ps);
+  count_launch();
+  return cudaGetLastError();
 }
 
 cudaError_t launch_pcg(const DevGeom& g, const PcgArgs& a, int grid, size_t smem, cudaStream_t s) {

@@ -45,6 +45,42 @@ struct SolveRecord {
   double max_rel_residual;
 };
 
+enum : int { PREC_SEPARABLE = 0, PREC_JACOBI = 1 };
+
+// σ-separable preconditioner (exact inverse of Kx(d)⊗Mσ + Mx(1/d)⊗Kσ, see kernels_laplace.cu).
+// All per-mode arrays are mode-major.
+template <class T>
+struct PrecView {
+  int nr;                  // σ modes = interior rows (Nrow − 1)
+  int nif;                 // interface unknowns per mode (Nx periodic, Nx+1 walls)
+  const T* S;              // [nr*nr]   S[j*nr + k]: σ-eigenvectors, Sᵀ Mσ S = I
+  const T* Aii;            // [nr][Nx][(P−1)²] inverse interior block of the mode-k element matrix
+  const T* Z;              // [nr][Nx][2][P−1]  E_bi E_ii⁻¹ (left, right boundary rows)
+  const T* te;             // [nr][nif] interface tridiagonal off-diagonals
+  const T* tm;             // [nr][nif] Thomas pivots 1/(d_j − e_{j−1} c'_{j−1})
+  const T* tcp;            // [nr][nif] Thomas c'_j
+  const T* tz;             // [nr][nif] periodic: T'⁻¹u of the Sherman–Morrison closure
+  const T* tvl;            // [nr] periodic: v_{N−1}
+  const T* tfac;           // [nr] periodic: 1/(1 + vᵀT'⁻¹u)
+  T* gL;                   // [nr][Nx] condensed right-hand side, left interface of element
+  T* gR;                   // [nr][Nx] condensed right-hand side, right interface of element
+  T* zb;                   // [nr][nif] interface solution
+  T* rhat;                 // [ncol][nr] σ-transformed residual
+};
+
+// Set-up data written per stage by the preconditioner set-up kernels (FP64 masters + FP32 copies).
+struct PrecSetup {
+  int nr, nif;
+  const double* lam;       // [nr] σ eigenvalues
+  double* schur;           // [nr][Nx][3]  S00, S01, S11 of the condensed element matrix
+  PrecView<double> v64;
+  PrecView<float> v32;
+  // writable aliases of the factor arrays
+  double *Aii64, *Z64, *te64, *tm64, *tcp64, *tz64, *tvl64, *tfac64;
+  float *Aii32, *Z32, *te32, *tm32, *tcp32, *tz32, *tvl32, *tfac32;
+  double* scratch;         // [nr][4*nif] for large interface systems
+};
+
 struct PcgArgs {
   double* x;              // Φ [n]
   const double* phis;     // φ̃ [ncol]
@@ -56,6 +92,13 @@ struct PcgArgs {
   int part_stride;        // max grid
   unsigned int* bar;      // grid barrier {arrive, generation}
   SolveRecord* rec;
+  double* r64b;           // second residual buffer (double-buffered update)
+  float* r32b;
+  PrecView<double> pv64;
+  PrecView<float> pv32;
+  int precond;            // PREC_SEPARABLE or PREC_JACOBI
+  int tri_smem;           // bytes of dynamic shared memory reserved for the interface solves (0: global)
+  int tri_smem_offset;    // their offset in the dynamic shared memory
   double tol;
   double inner_rtol;
   int max_iter;
@@ -93,7 +136,10 @@ cudaError_t launch_geometry(const DevGeom& g, const double* eta, cudaStream_t s)
 cudaError_t launch_apply(const DevGeom& g, const double* x, double* y, double* qtmp, double* edge,
                          cudaStream_t s);
 cudaError_t launch_l2g(const DevGeom& g, int32_t* l2g, cudaStream_t s);
-cudaError_t pcg_grid_size(int P, int Nz, int nrow, int Nx, int mixed, int* grid, size_t* smem);
+cudaError_t pcg_grid_size(int P, int Nz, int nrow, int Nx, int mixed, size_t tri_smem, int* grid,
+                          size_t* smem);
+cudaError_t launch_prec_setup(const DevGeom& g, const PrecSetup& ps, cudaStream_t s);
+size_t tri_smem_offset(int P, int nrow, int Nz);
 cudaError_t launch_pcg(const DevGeom& g, const PcgArgs& a, int grid, size_t smem, cudaStream_t s);
 
 // ---- launchers (kernels_surface.cu) ----

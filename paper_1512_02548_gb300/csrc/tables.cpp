@@ -125,6 +125,53 @@ bool invert(std::vector<ld>& a, int n) {
   return true;
 }
 
+void sym_eig(std::vector<ld> a, int n, std::vector<ld>& evals, std::vector<ld>& evecs) {
+  std::vector<ld> v((size_t)n * n, 0.0L);
+  for (int i = 0; i < n; ++i) v[(size_t)i * n + i] = 1.0L;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    ld off = 0.0L, diag = 0.0L;
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j)
+        (i == j ? diag : off) += a[(size_t)i * n + j] * a[(size_t)i * n + j];
+    if (off <= 1e-36L * diag) break;
+    for (int p = 0; p < n - 1; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        const ld apq = a[(size_t)p * n + q];
+        if (std::fabs(apq) < 1e-300L) continue;
+        const ld app = a[(size_t)p * n + p], aqq = a[(size_t)q * n + q];
+        const ld theta = (aqq - app) / (2.0L * apq);
+        const ld t = (theta >= 0 ? 1.0L : -1.0L) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0L));
+        const ld c = 1.0L / std::sqrt(t * t + 1.0L), sn = t * c;
+        for (int k = 0; k < n; ++k) {   // A ← A J (columns p, q)
+          const ld akp = a[(size_t)k * n + p], akq = a[(size_t)k * n + q];
+          a[(size_t)k * n + p] = c * akp - sn * akq;
+          a[(size_t)k * n + q] = sn * akp + c * akq;
+        }
+        for (int k = 0; k < n; ++k) {   // A ← Jᵀ A (rows p, q)
+          const ld apk = a[(size_t)p * n + k], aqk = a[(size_t)q * n + k];
+          a[(size_t)p * n + k] = c * apk - sn * aqk;
+          a[(size_t)q * n + k] = sn * apk + c * aqk;
+        }
+        for (int k = 0; k < n; ++k) {   // V ← V J
+          const ld vkp = v[(size_t)k * n + p], vkq = v[(size_t)k * n + q];
+          v[(size_t)k * n + p] = c * vkp - sn * vkq;
+          v[(size_t)k * n + q] = sn * vkp + c * vkq;
+        }
+      }
+  }
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  for (int i = 0; i < n; ++i)
+    for (int j = i + 1; j < n; ++j)
+      if (a[(size_t)order[j] * n + order[j]] < a[(size_t)order[i] * n + order[i]]) std::swap(order[i], order[j]);
+  evals.resize(n);
+  evecs.assign((size_t)n * n, 0.0L);
+  for (int k = 0; k < n; ++k) {
+    evals[k] = a[(size_t)order[k] * n + order[k]];
+    for (int i = 0; i < n; ++i) evecs[(size_t)i * n + k] = v[(size_t)i * n + order[k]];
+  }
+}
+
 Line make_line(int P) {
   if (P < 1 || P > 24) throw std::invalid_argument("GLL order out of range");
   Line L;

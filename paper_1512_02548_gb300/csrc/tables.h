@@ -28,4 +28,9 @@ std::vector<double> filter_matrix(const Line& L, double alpha, double s, int ic)
 // Dense inverse (Gauss–Jordan with partial pivoting); returns false if singular.
 bool invert(std::vector<long double>& a, int n);
 
+// Eigen-decomposition of a symmetric n×n matrix (cyclic Jacobi rotations): on return
+// evals[k] ascending and evecs[i*n+k] the orthonormal eigenvector k.
+void sym_eig(std::vector<long double> a, int n, std::vector<long double>& evals,
+             std::vector<long double>& evecs);
+
 }  // namespace semgb

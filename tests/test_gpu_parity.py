@@ -43,14 +43,14 @@ def T(x):
 
 
 def make_pair(P=5, Nx=7, Nz=2, periodic=True, bar=False, Pf=None, filt=True, precision="fp64",
-              grid_limit=None, tol=1e-13):
+              grid_limit=None, tol=1e-13, precond="separable"):
     wl = small_case(P=P, Nx=Nx, Nz=Nz, periodic=periodic, Pf=Pf, filt=filt)
     om = osem.mesh_for(wl, bar=bar)
     old = os.environ.get("SEM_GRID_LIMIT")
     if grid_limit:
         os.environ["SEM_GRID_LIMIT"] = str(grid_limit)
     try:
-        gm = sem.Mesh.from_workload(wl, h=om.h, precision=precision, tol=tol)
+        gm = sem.Mesh.from_workload(wl, h=om.h, precision=precision, tol=tol, precond=precond)
     finally:
         if grid_limit:
             if old is None:
@@ -117,6 +117,33 @@ def test_laplace_solve_matches_banded_direct(case):
     # warm start from the solution: converges at once to the same answer
     st2 = gm.laplace_solve(T(phis), Phi)
     assert st2.iterations <= 2 and rel(Phi, ref) < TOL_FP64
+
+
+@pytest.mark.parametrize("case", CASES[:6], ids=lambda c: "-".join(f"{k}{v}" for k, v in c.items()))
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_jacobi_preconditioner_solve(case, precision):
+    wl, om, gm = make_pair(precond="jacobi", precision=precision, tol=1e-12 if precision == "mixed" else 1e-13,
+                           **case)
+    eta, phis = surface(om, seed=9)
+    gm.update_geometry(T(eta))
+    Phi = torch.zeros(om.n, dtype=torch.float64, device=DEV)
+    gm.laplace_solve(T(phis), Phi)
+    assert rel(Phi, om.laplace_solve(eta, phis)) < (TOL_MIXED if precision == "mixed" else TOL_FP64)
+
+
+def test_separable_preconditioner_needs_few_iterations():
+    # C2-sized tank: the σ-separable preconditioner converges in tens of iterations where
+    # Jacobi needs hundreds
+    wl = c2_steep_periodic()
+    om = osem.mesh_for(wl)
+    e, p = initial_state(wl, om.xcol, om.h)
+    its = {}
+    for pc in ("separable", "jacobi"):
+        gm = sem.Mesh.from_workload(wl, h=om.h, precond=pc)
+        gm.update_geometry(T(e))
+        Phi = torch.zeros(om.n, dtype=torch.float64, device=DEV)
+        its[pc] = gm.laplace_solve(T(p), Phi).iterations
+    assert its["separable"] <= 30 and its["jacobi"] > 10 * its["separable"]
 
 
 def test_laplace_solve_zero_surface_potential():
