@@ -512,7 +512,9 @@ __device__ void phase_update(const DevGeom& g, Smem<P, T>& s, const Range& R, bo
     __syncthreads();
     for (int k = threadIdx.x; k < nr; k += blockDim.x) {
       const T* Zk = pv.Z + ((size_t)k * g.Nx + ex) * 2 * Pm;
-      T l = RH[k], r = RH[P * nr + k];
+      // the assembled residual at an interface node enters once: with the element that owns
+      // that column (its left end), plus the walls' last column with the last element
+      T l = RH[k], r = owns_local_col(g, ex, P) ? RH[P * nr + k] : T(0);
 #pragma unroll
       for (int m = 0; m < Pm; ++m) {
         const T f = RH[(1 + m) * nr + k];
