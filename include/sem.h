@@ -135,6 +135,23 @@ int sem_update_geometry(sem_mesh* m, const double* eta_d, void* stream);
  * x_d, y_d: device, n values, must not overlap. */
 int sem_laplace_apply(sem_mesh* m, const double* x_d, double* y_d, void* stream);
 
+/* Allocation-free form of sem_laplace_apply (the paper has no counterpart; this is a
+ * service of the library).  For callers that may not allocate device memory at the time
+ * of the call: code recording a CUDA graph by stream capture (allocation is not allowed
+ * inside a capture), real-time loops that forbid allocator calls, and hosts whose own
+ * memory manager owns the device and rejects raw cudaMalloc.  It computes y = 𝓛x
+ * exactly as sem_laplace_apply does, for the last sem_update_geometry, but touches no
+ * workspace of the mesh and calls no allocator: y receives partial sums first, and the
+ * one temporary the apply needs (the shared x-interface column of every element column,
+ * Nx·Nrow values) lives in a static device array of 2^20 doubles (8 MiB) that every
+ * device which loads the library holds until the process exits.  Nx·Nrow above 2^20 is
+ * rejected with SEM_ERR_INVALID_ARG.  The first call on a device looks up the array's
+ * device address; make that first call before any stream capture.  All calls on a
+ * device share the array, so calls that can overlap on the GPU (other streams, other
+ * meshes) race and must be serialised by the caller.  x_d, y_d: device, n values, must
+ * not overlap. */
+int sem_laplace_apply_noalloc(const sem_mesh* m, const double* x_d, double* y_d, void* stream);
+
 /* Laplace problem of eq. (laplaceproblem) for the last sem_update_geometry:
  * 𝓛Φ = 0 at interior nodes, Φ = φ̃ at the surface (eq. FSeqs BC), solved by
  * preconditioned conjugate gradients on the Dirichlet-eliminated SPD system

@@ -25,7 +25,7 @@ SEM_PREC_FP64, SEM_PREC_MIXED = 0, 1
 SEM_PRECOND_SEPARABLE, SEM_PRECOND_JACOBI = 0, 1
 
 EXPORTED = ("sem_mesh_create", "sem_mesh_destroy", "sem_mesh_info", "sem_mesh_l2g",
-            "sem_update_geometry", "sem_laplace_apply", "sem_laplace_solve",
+            "sem_update_geometry", "sem_laplace_apply", "sem_laplace_apply_noalloc", "sem_laplace_solve",
             "sem_recover_gradient", "sem_zakharov_rhs", "sem_apply_filter", "sem_rk4_step",
             "sem_rk4_step_host", "sem_get_counters", "sem_reset_counters", "sem_enable_timing",
             "sem_get_timing", "sem_launch_count", "sem_last_error")
@@ -79,6 +79,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sem_mesh_l2g.argtypes = [vp, dp, vp]
     lib.sem_update_geometry.argtypes = [vp, dp, vp]
     lib.sem_laplace_apply.argtypes = [vp, dp, dp, vp]
+    lib.sem_laplace_apply_noalloc.argtypes = [vp, dp, dp, vp]
     lib.sem_laplace_solve.argtypes = [vp, dp, dp, ctypes.POINTER(sem_solve_stats), vp]
     lib.sem_recover_gradient.argtypes = [vp, dp, dp, dp, dp, dp, dp, vp]
     lib.sem_zakharov_rhs.argtypes = [vp, dp, dp, ctypes.c_double, dp, dp, vp]
@@ -191,6 +192,11 @@ class Mesh:
 
     def laplace_apply(self, x, y):
         _check(load_library().sem_laplace_apply(self._h, _ptr(x), _ptr(y), _stream()))
+        return y
+
+    def laplace_apply_noalloc(self, x, y):
+        """y = 𝓛x without any allocation by the library (static device scratch, see sem.h)."""
+        _check(load_library().sem_laplace_apply_noalloc(self._h, _ptr(x), _ptr(y), _stream()))
         return y
 
     def laplace_solve(self, phis, Phi, stats: bool = True):

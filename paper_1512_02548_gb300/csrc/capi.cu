@@ -530,6 +530,17 @@ int sem_laplace_apply(sem_mesh* m, const double* x_d, double* y_d, void* stream)
   return SEM_OK;
 }
 
+int sem_laplace_apply_noalloc(const sem_mesh* m, const double* x_d, double* y_d, void* stream) {
+  if (!m || !x_d || !y_d || x_d == y_d) return fail(SEM_ERR_INVALID_ARG, "bad pointer");
+  if ((size_t)m->p.Nx * (size_t)m->nrow > kNoAllocEdgeMax)
+    return fail(SEM_ERR_INVALID_ARG, "sem_laplace_apply_noalloc: Nx*Nrow = " +
+                                         std::to_string((size_t)m->p.Nx * m->nrow) + " exceeds the static scratch of " +
+                                         std::to_string(kNoAllocEdgeMax) + " values");
+  DeviceGuard dg(m->device);
+  CUDA_TRY(launch_apply_noalloc(m->g, x_d, y_d, (cudaStream_t)stream));
+  return SEM_OK;
+}
+
 int sem_laplace_solve(sem_mesh* m, const double* phis_d, double* Phi_d, sem_solve_stats* st, void* stream) {
   if (!m || !phis_d || !Phi_d) return fail(SEM_ERR_INVALID_ARG, "NULL argument");
   DeviceGuard dg(m->device);

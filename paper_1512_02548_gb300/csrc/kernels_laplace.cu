@@ -25,6 +25,8 @@
 // iterations run in FP32 and the kernel refines the FP64 residual.
 #include <cooperative_groups.h>
 
+#include <mutex>
+
 #include "sem_internal.cuh"
 
 namespace semgb {
@@ -1069,6 +1071,67 @@ cudaError_t launch_apply(const DevGeom& g, const double* x, double* y, double* q
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const long long n = (long long)g.ncol * g.nrow;
   k_apply_fix<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g, qtmp, edge, y);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------
+// Allocation-free variant of the stand-alone apply.  The only scratch the apply needs
+// beyond its input and output is the per-element-column copy of the shared x-interface
+// column; here it lives in one file-scope device array instead of the mesh workspace, and
+// the output array doubles as the owned-column buffer.  The array is shared by every call
+// on a device: calls that overlap on the GPU race on it.  Every entry that a call reads
+// is written earlier in the same call, so nothing has to be cleared between calls.
+// ------------------------------------------------------------------------------------
+static __device__ __align__(256) double g_noalloc_edge[kNoAllocEdgeMax];
+
+static std::mutex g_noalloc_mu;
+static double* g_noalloc_ptr[64] = {nullptr};
+
+// Device address of g_noalloc_edge for the current device, looked up once per device.
+static cudaError_t noalloc_edge_address(double** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    double* p = nullptr;
+    e = cudaGetSymbolAddress(reinterpret_cast<void**>(&p), g_noalloc_edge);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return cudaSuccess;
+}
+
+// y ← −(y + edge of the left neighbour) in place: y holds the owned columns' A x.
+__global__ void k_apply_fix_inplace(DevGeom g, const double* __restrict__ edge, double* y) {
+  const long long n = (long long)g.ncol * g.nrow;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const int col = (int)(t / g.nrow), iz = (int)(t - (long long)col * g.nrow);
+  double v = y[t];
+  if (has_left_edge(g, col)) v += edge[(size_t)left_element(g, col) * g.nrow + iz];
+  y[t] = -v;
+}
+
+cudaError_t launch_apply_noalloc(const DevGeom& g, const double* x, double* y, cudaStream_t s) {
+  if ((size_t)g.Nx * (size_t)g.nrow > kNoAllocEdgeMax) return cudaErrorInvalidValue;
+  double* edge = nullptr;
+  cudaError_t e = noalloc_edge_address(&edge);
+  if (e != cudaSuccess) return e;
+  const size_t smem = apply_smem_bytes(g.P, g.nrow, g.Nz, sizeof(double));
+  const int grid = g.Nx < 4096 ? g.Nx : 4096;
+  SEM_DISPATCH_P(g.P, {
+    e = cudaFuncSetAttribute(k_apply<PP>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e == cudaSuccess) k_apply<PP><<<grid, kThreads, smem, s>>>(g, x, y, edge);
+  });
+  if (e != cudaSuccess) return e;
+  count_launch();
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const long long n = (long long)g.ncol * g.nrow;
+  k_apply_fix_inplace<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g, edge, y);
   count_launch();
   return cudaGetLastError();
 }

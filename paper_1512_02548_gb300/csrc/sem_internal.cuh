@@ -136,6 +136,9 @@ cudaError_t launch_geometry(const DevGeom& g, const double* eta, cudaStream_t s)
 cudaError_t launch_apply(const DevGeom& g, const double* x, double* y, double* qtmp, double* edge,
                          cudaStream_t s);
 cudaError_t launch_l2g(const DevGeom& g, int32_t* l2g, cudaStream_t s);
+// Allocation-free apply (scratch in a static device array of kNoAllocEdgeMax doubles).
+constexpr size_t kNoAllocEdgeMax = size_t(1) << 20;
+cudaError_t launch_apply_noalloc(const DevGeom& g, const double* x, double* y, cudaStream_t s);
 cudaError_t pcg_grid_size(int P, int Nz, int nrow, int Nx, int mixed, size_t tri_smem, int* grid,
                           size_t* smem);
 cudaError_t launch_prec_setup(const DevGeom& g, const PrecSetup& ps, cudaStream_t s);
