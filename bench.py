@@ -36,6 +36,7 @@ UNIT = "DOF/s"
 # Algorithmic FP64 work of one Krylov iteration (per-unit figures stated in the design notes):
 #   operator apply: 8(P+1)+7 flops per element-local node (gradients, fluxes, transposed sums)
 #   vector updates and dots: 13 flops per unknown
+#   σ-separable preconditioner: see flops_per_precond
 FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 rate (vector and tensor alike)
 
 
@@ -44,9 +45,18 @@ def workload():
     return c2_steep_periodic()
 
 
+def flops_per_precond(wl) -> float:
+    """σ-separable preconditioner: two σ-transforms (nr² FMAs per column each), per-(mode,
+    element) condensation and back-substitution ((P−1)² + 4(P−1) FMAs), interface solve."""
+    P, nr = wl.P, wl.nrow - 1
+    nif = wl.Nx if wl.periodic else wl.Nx + 1
+    return 4 * wl.ncol * nr * nr + 2 * nr * wl.Nx * ((P - 1) ** 2 + 4 * (P - 1)) + 6 * nr * nif
+
+
 def flops_per_iteration(wl) -> float:
     P = wl.P
-    return wl.Nx * wl.Nz * (P + 1) ** 2 * (8 * (P + 1) + 7) + 13 * wl.n_unknowns
+    return (wl.Nx * wl.Nz * (P + 1) ** 2 * (8 * (P + 1) + 7) + 13 * wl.n_unknowns
+            + flops_per_precond(wl))
 
 
 def flops_per_apply(wl) -> float:
@@ -264,8 +274,12 @@ def run_gpu(args):
 
     # roofline of the dominant kernel: the persistent Krylov kernel, FP64 ALU bound
     solves = max(cnt.solves, 1)
-    applies = cnt.iterations + 2 * cnt.solves + (cnt.refinements if args.precision == "mixed" else 0)
-    flops = (cnt.iterations * flops_per_iteration(wl) + (applies - cnt.iterations) * flops_per_apply(wl))
+    # per solve: 2 FP64 applies for r0 and b, one preconditioner application per start
+    # (1 in FP64, one per refinement in mixed), one FP64 apply per refinement
+    extra_applies = 2 * cnt.solves + cnt.refinements
+    starts = cnt.refinements if args.precision == "mixed" else cnt.solves
+    flops = (cnt.iterations * flops_per_iteration(wl) + extra_applies * flops_per_apply(wl)
+             + starts * flops_per_precond(wl))
     avg_launch_ms = tm.krylov_ms / max(tm.krylov_launches, 1)
     flops_per_launch = flops / max(tm.krylov_launches, 1)
     achieved = flops_per_launch / (avg_launch_ms / 1e3) / 1e12

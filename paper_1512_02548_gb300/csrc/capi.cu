@@ -11,7 +11,7 @@
 #include <utility>
 #include <vector>
 
-#include "../../include/sem.h"
+#include "sem.h"
 #include "sem_internal.cuh"
 #include "tables.h"
 
@@ -145,8 +145,9 @@ int do_solve(sem_mesh* m, const double* phis, double* Phi, cudaStream_t s) {
 }
 
 int do_geometry(sem_mesh* m, const double* eta, cudaStream_t s) {
-  CUDA_TRY(launch_geometry(m->g, eta, s));
-  if (m->p.precond == SEM_PRECOND_SEPARABLE) CUDA_TRY(launch_prec_setup(m->g, m->ps, s));
+  const bool jacobi = m->p.precond == SEM_PRECOND_JACOBI;
+  CUDA_TRY(launch_geometry(m->g, eta, jacobi, s));
+  if (!jacobi) CUDA_TRY(launch_prec_setup(m->g, m->ps, s));
   return SEM_OK;
 }
 
@@ -362,12 +363,11 @@ int sem_mesh_create(const sem_params* pin, const double* x_edges_h, const double
     for (int j = 0; j < nr; ++j)
       for (int k = 0; k < nr; ++k) Sg[(size_t)j * nr + k] = (double)(V[(size_t)j * nr + k] / std::sqrt(Ms[j]));
   }
-  const size_t tri_bytes = (size_t)3 * N * sizeof(double) <= 96 * 1024 ? (size_t)3 * N * sizeof(double) : 0;
 
   // ---- device allocation -------------------------------------------------------
   sem_mesh* m = new sem_mesh;
   m->p = p; m->device = dev; m->ncol = ncol; m->nrow = nrow; m->n = n; m->Pf = p.Pf; m->nif = N;
-  cudaError_t ge = pcg_grid_size(P, Nz, nrow, Nx, p.precision == SEM_PREC_MIXED, tri_bytes, &m->grid, &m->smem);
+  cudaError_t ge = pcg_grid_size(P, Nz, nrow, Nx, p.precision == SEM_PREC_MIXED, &m->grid, &m->smem);
   if (ge != cudaSuccess) { delete m; return fail(SEM_ERR_CUDA, std::string("Krylov kernel occupancy: ") + cudaGetErrorString(ge)); }
   if (const char* lim = std::getenv("SEM_GRID_LIMIT")) {   // tuning/testing knob: cap the Krylov grid
     const int v = std::atoi(lim);
@@ -400,7 +400,8 @@ int sem_mesh_create(const sem_params* pin, const double* x_edges_h, const double
                o_tfac64 = cv.take<double>(nr), o_tvl32 = cv.take<float>(nr), o_tfac32 = cv.take<float>(nr),
                o_gL64 = cv.take<double>(nEl), o_gR64 = cv.take<double>(nEl), o_gL32 = cv.take<float>(nEl),
                o_gR32 = cv.take<float>(nEl), o_zb64 = cv.take<double>(nIf), o_zb32 = cv.take<float>(nIf),
-               o_rh64 = cv.take<double>((size_t)ncol * nr), o_rh32 = cv.take<float>((size_t)ncol * nr);
+               o_rh64 = cv.take<double>((size_t)ncol * nr), o_rh32 = cv.take<float>((size_t)ncol * nr),
+               o_pscr = cv.take<double>(nIf);
   const size_t o_wt = cv.take<double>(ncol), o_etax = cv.take<double>(ncol), o_phisx = cv.take<double>(ncol),
                o_R = cv.take<double>((size_t)2 * Nx * Q), o_scr = cv.take<double>((size_t)4 * Nx + 2 * (N + 1)),
                o_ke = cv.take<double>(ncol), o_kp = cv.take<double>(ncol), o_ae = cv.take<double>(ncol),
@@ -458,15 +459,13 @@ int sem_mesh_create(const sem_params* pin, const double* x_edges_h, const double
   a.tol = p.tol; a.inner_rtol = 1e-4; a.max_iter = p.max_iter; a.mixed = p.precision == SEM_PREC_MIXED;
   a.r64b = D_(o_r64b); a.r32b = F_(o_r32b);
   a.precond = p.precond == SEM_PRECOND_JACOBI ? PREC_JACOBI : PREC_SEPARABLE;
-  a.tri_smem = (int)tri_bytes;
-  a.tri_smem_offset = (int)tri_smem_offset(P, nrow, Nz);
   PrecSetup& ps = m->ps;
   ps.nr = nr; ps.nif = N; ps.lam = D_(o_lam); ps.schur = D_(o_schur);
   ps.Aii64 = D_(o_A64); ps.Z64 = D_(o_Z64); ps.te64 = D_(o_te64); ps.tm64 = D_(o_tm64); ps.tcp64 = D_(o_tcp64);
   ps.tz64 = D_(o_tz64); ps.tvl64 = D_(o_tvl64); ps.tfac64 = D_(o_tfac64);
   ps.Aii32 = F_(o_A32); ps.Z32 = F_(o_Z32); ps.te32 = F_(o_te32); ps.tm32 = F_(o_tm32); ps.tcp32 = F_(o_tcp32);
   ps.tz32 = F_(o_tz32); ps.tvl32 = F_(o_tvl32); ps.tfac32 = F_(o_tfac32);
-  ps.scratch = nullptr;
+  ps.scratch = D_(o_pscr);
   ps.v64 = PrecView<double>{nr, N, D_(o_S64), ps.Aii64, ps.Z64, ps.te64, ps.tm64, ps.tcp64, ps.tz64, ps.tvl64,
                             ps.tfac64, D_(o_gL64), D_(o_gR64), D_(o_zb64), D_(o_rh64)};
   ps.v32 = PrecView<float>{nr, N, F_(o_S32), ps.Aii32, ps.Z32, ps.te32, ps.tm32, ps.tcp32, ps.tz32, ps.tvl32,

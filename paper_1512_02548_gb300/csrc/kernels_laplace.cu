@@ -57,8 +57,6 @@ cudaError_t upload_line_tables(const double* D64, const double* w64) {
   return cudaMemcpyToSymbol(c_w32, w32, sizeof(float) * kWTotal);
 }
 
-__device__ __forceinline__ double fmx(double a, double b, double c) { return fma(a, b, c); }
-__device__ __forceinline__ float fmx(float a, float b, float c) { return fmaf(a, b, c); }
 // L2-coherent load for data another CTA wrote before the last grid barrier.
 __device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
 __device__ __forceinline__ float ldcg(const float* p) { return __ldcg(p); }
@@ -530,54 +528,22 @@ __device__ void phase_update(const DevGeom& g, Smem<P, T>& s, const Range& R, bo
   }
 }
 
-// Interface solve per σ-mode (modes spread over CTAs): assemble g_j = gL_j + gR_{j−1}, Thomas
-// sweep with the pivots of the set-up, Sherman–Morrison closure when periodic.  `sm` is shared
-// scratch of 3·nif values (right-hand side, forward coefficients, backward coefficients), or
-// nullptr to run the sweeps on global memory.
+// Interface solve per σ-mode: one warp (warp 0 of a CTA) per mode, modes spread over CTAs;
+// g_j = gL_j + gR_{j−1} assembled on the fly, then the warp-parallel tridiagonal solve.
 template <class T>
-__device__ void phase_interface(const DevGeom& g, const PrecView<T>& pv, T* sm, T* s_c) {
+__device__ void phase_interface(const DevGeom& g, const PrecView<T>& pv) {
+  if (threadIdx.x >= 32) return;
   const int N = pv.nif, Nx = g.Nx;
   for (int k = blockIdx.x; k < pv.nr; k += gridDim.x) {
     const T* gl = pv.gL + (size_t)k * Nx;
     const T* gr = pv.gR + (size_t)k * Nx;
-    const T* te = pv.te + (size_t)k * N;
-    const T* tm = pv.tm + (size_t)k * N;
-    const T* tcp = pv.tcp + (size_t)k * N;
-    T* zb = pv.zb + (size_t)k * N;
-    T* G = sm ? sm : zb;
-    for (int j = threadIdx.x; j < N; j += blockDim.x) {
-      T v;
-      if (g.periodic) v = ldcg(gl + j) + ldcg(gr + (j == 0 ? Nx - 1 : j - 1));
-      else v = (j < Nx ? ldcg(gl + j) : T(0)) + (j > 0 ? ldcg(gr + j - 1) : T(0));
-      G[j] = v * tm[j];                                   // g_j m_j
-      if (sm) {
-        sm[N + j] = j > 0 ? te[j - 1] * tm[j] : T(0);     // e_{j−1} m_j
-        sm[2 * N + j] = tcp[j];                           // c'_j
-      }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      // forward: y_j = g_j m_j − (e_{j−1} m_j) y_{j−1};  backward: y_j −= c'_j y_{j+1}
-      T prev = G[0];
-      for (int j = 1; j < N; ++j) {
-        const T a = sm ? sm[N + j] : te[j - 1] * tm[j];
-        prev = fmx(-a, prev, G[j]);
-        G[j] = prev;
-      }
-      T next = G[N - 1];
-      for (int j = N - 2; j >= 0; --j) {
-        next = fmx(-(sm ? sm[2 * N + j] : tcp[j]), next, G[j]);
-        G[j] = next;
-      }
-      *s_c = g.periodic ? (G[0] + pv.tvl[k] * G[N - 1]) * pv.tfac[k] : T(0);
-    }
-    __syncthreads();
-    const T c = *s_c;
-    for (int j = threadIdx.x; j < N; j += blockDim.x) {
-      const T y = G[j];
-      zb[j] = g.periodic ? fmx(-c, pv.tz[(size_t)k * N + j], y) : y;
-    }
-    __syncthreads();
+    auto gfun = [&](int j) -> T {
+      if (g.periodic) return ldcg(gl + j) + ldcg(gr + (j == 0 ? Nx - 1 : j - 1));
+      return (j < Nx ? ldcg(gl + j) : T(0)) + (j > 0 ? ldcg(gr + j - 1) : T(0));
+    };
+    warp_tridiag<T>(N, gfun, pv.te + (size_t)k * N, pv.tm + (size_t)k * N, pv.tcp + (size_t)k * N,
+                    g.periodic != 0, pv.tz + (size_t)k * N, g.periodic ? pv.tvl[k] : T(0),
+                    g.periodic ? pv.tfac[k] : T(0), pv.zb + (size_t)k * N);
   }
 }
 
@@ -631,7 +597,7 @@ template <int P, class T, class A>
 __device__ bool precondition(const DevGeom& g, Smem<P, T>& s, const Range& R, const PcgArgs& PA,
                              const PrecView<T>& pv, bool update, T alpha, T* x, const T* p, const T* q,
                              const T* edge, const T* r_old, T* r_new, const T* invdiag, T* z,
-                             T* tri_sm, double* red, int* s_flag, double& rr, double& rz) {
+                             double* red, int* s_flag, double& rr, double& rz) {
   A acc[2] = {A(0), A(0)};
   phase_update<P, T, A>(g, s, R, update, alpha, x, p, q, edge, r_old, r_new, invdiag, z, PA.precond, pv,
                         acc);
@@ -641,7 +607,7 @@ __device__ bool precondition(const DevGeom& g, Smem<P, T>& s, const Range& R, co
     block_sum<1, A>(a1, red);
     acc[0] = a1[0];
     if (!grid_barrier(PA.bar, g.status, s_flag)) return false;
-    phase_interface<T>(g, pv, tri_sm, reinterpret_cast<T*>(red + 150));
+    phase_interface<T>(g, pv);
     if (!grid_barrier(PA.bar, g.status, s_flag)) return false;
     A rzl = A(0);
     phase_backsub<P, T, A>(g, s, R, pv, rcur, z, rzl);
@@ -668,7 +634,7 @@ __device__ bool precondition(const DevGeom& g, Smem<P, T>& s, const Range& R, co
 template <int P, class T, class A>
 __device__ int inner_pcg(const DevGeom& g, Smem<P, T>& s, const Range& R, const PcgArgs& PA,
                          const PrecView<T>& pv, T* x, T* r0, T* r1, T* z, T* pa, T* pb, T* q, T* edge,
-                         const T* invdiag, T* tri_sm, double* red, int* s_flag, double rr, double rz,
+                         const T* invdiag, double* red, int* s_flag, double rr, double rz,
                          double target, int max_it, double* rr_out) {
   const int nrow = g.nrow;
   int k = 0;
@@ -721,7 +687,7 @@ __device__ int inner_pcg(const DevGeom& g, Smem<P, T>& s, const Range& R, const 
     // Phase B(+C+D): x += α p, r −= α q, z = M⁻¹ r
     double rr_n, rz_n;
     if (!precondition<P, T, A>(g, s, R, PA, pv, true, alpha, x, p_new, q, edge, r_cur, r_nxt, invdiag, z,
-                               tri_sm, red, s_flag, rr_n, rz_n))
+                               red, s_flag, rr_n, rz_n))
       return -1;
     if (threadIdx.x == 0) {
       rr = rr_n;
@@ -803,7 +769,6 @@ __global__ void __launch_bounds__(kThreads) k_pcg(DevGeom g, PcgArgs A) {
   Smem<P, double> s64;
   s64.carve(smem_raw, nrow, g.Nz);
   s64.load_tables(g);
-  unsigned char* tri_raw = smem_raw + A.tri_smem_offset;
   double rr = 0.0, bb = 0.0, rz = 0.0;
   if (!fp64_residual<P>(g, s64, R, A, true, red, &s_flag, rr, bb)) return;
   const double target = A.tol * A.tol * bb;
@@ -817,21 +782,19 @@ __global__ void __launch_bounds__(kThreads) k_pcg(DevGeom g, PcgArgs A) {
     }
     rr = 0.0;
   } else if (!MIXED) {
-    double* tri = A.tri_smem ? reinterpret_cast<double*>(tri_raw) : nullptr;
     double rr0;
     if (!precondition<P, double, double>(g, s64, R, A, A.pv64, false, 0.0, A.x, nullptr, nullptr, nullptr,
-                                         A.r64, A.r64, g.invdiag64, A.z64, tri, red, &s_flag, rr0, rz))
+                                         A.r64, A.r64, g.invdiag64, A.z64, red, &s_flag, rr0, rz))
       return;
     double rr_out = rr;
     iters = inner_pcg<P, double, double>(g, s64, R, A, A.pv64, A.x, A.r64, A.r64b, A.z64, A.p64a, A.p64b,
-                                         A.q64, A.edge64, g.invdiag64, tri, red, &s_flag, rr, rz, target,
+                                         A.q64, A.edge64, g.invdiag64, red, &s_flag, rr, rz, target,
                                          A.max_iter, &rr_out);
     if (iters < 0) return;
     rr = rr_out;
   } else {
     Smem<P, float> s32;
     s32.carve(smem_raw, nrow, g.Nz);
-    float* tri = A.tri_smem ? reinterpret_cast<float*>(tri_raw) : nullptr;
     while (rr > target && iters < A.max_iter) {
       if (!(rr == rr) || isinf(rr)) { if (threadIdx.x == 0) atomicOr(g.status, ST_NONFINITE); break; }
       __syncthreads();
@@ -847,12 +810,12 @@ __global__ void __launch_bounds__(kThreads) k_pcg(DevGeom g, PcgArgs A) {
       if (!grid_barrier(A.bar, g.status, &s_flag)) return;
       double rr_in, rz_in;
       if (!precondition<P, float, float>(g, s32, R, A, A.pv32, false, 0.f, A.d32, nullptr, nullptr, nullptr,
-                                         A.r32, A.r32, g.invdiag32, A.z32, tri, red, &s_flag, rr_in, rz_in))
+                                         A.r32, A.r32, g.invdiag32, A.z32, red, &s_flag, rr_in, rz_in))
         return;
       const double tgt_in = fmax(A.inner_rtol * A.inner_rtol * rr_in, 0.25 * target);
       double rr_out = rr_in;
       const int it = inner_pcg<P, float, float>(g, s32, R, A, A.pv32, A.d32, A.r32, A.r32b, A.z32, A.p32a,
-                                                A.p32b, A.q32, A.edge32, g.invdiag32, tri, red, &s_flag,
+                                                A.p32b, A.q32, A.edge32, g.invdiag32, red, &s_flag,
                                                 rr_in, rz_in, tgt_in, A.max_iter - iters, &rr_out);
       if (it < 0) return;
       iters += it;
@@ -889,36 +852,42 @@ __global__ void __launch_bounds__(kThreads) k_pcg(DevGeom g, PcgArgs A) {
 // ------------------------------------------------------------------------------------
 // Set-up of the separable preconditioner for the current geometry.
 // ------------------------------------------------------------------------------------
-// One thread per (mode k, element e): element matrix E = (2/Δx) Dᵀ diag(w d) D +
-// λ_k (Δx/2) diag(w/d), inverse of its interior block, Z = E_bi E_ii⁻¹ and the 2×2 Schur block.
+// Block per element, one thread per mode: the mode-independent x-stiffness Kx = (2/Δx) Dᵀ
+// diag(w d) D is formed once in shared memory; each mode adds λ_k (Δx/2) diag(w/d), inverts
+// the interior block, and writes Z = E_bi E_ii⁻¹ and the 2×2 Schur block.
+constexpr int kPrecModesPerBlock = 32;
+
 template <int P>
-__global__ void k_prec_elem(DevGeom g, PrecSetup ps) {
+__global__ void __launch_bounds__(kPrecModesPerBlock) k_prec_elem(DevGeom g, PrecSetup ps) {
   constexpr int Q = P + 1, Pm = P - 1;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= ps.nr * g.Nx) return;
-  const int k = t / g.Nx, ex = t - k * g.Nx;
+  __shared__ double Kx[Q * Q];
+  __shared__ double mw[Q];
+  const int ex = blockIdx.x;
   const double* D = c_D64 + d_off(P);
   const double* w = c_w64 + w_off(P);
   const double* geo = g.geo64 + (size_t)ex * Q * 4;
-  const double dxe = g.dxe[ex], lam = ps.lam[k];
-  double E[Q][Q];
+  const double dxe = g.dxe[ex];
+  for (int t = threadIdx.x; t < Q * Q; t += blockDim.x) {
+    const int i = t / Q, j = t - i * Q;
+    double s = 0.0;
 #pragma unroll
-  for (int i = 0; i < Q; ++i)
-#pragma unroll
-    for (int j = 0; j < Q; ++j) {
-      double s = 0.0;
-#pragma unroll
-      for (int a = 0; a < Q; ++a) s = fma(D[a * Q + i] * w[a] * geo[a * 4 + 0], D[a * Q + j], s);
-      E[i][j] = (2.0 / dxe) * s;
-    }
-#pragma unroll
-  for (int i = 0; i < Q; ++i) E[i][i] += lam * 0.5 * dxe * w[i] * geo[i * 4 + 1];
+    for (int a = 0; a < Q; ++a) s = fma(D[a * Q + i] * w[a] * geo[a * 4 + 0], D[a * Q + j], s);
+    Kx[t] = (2.0 / dxe) * s;
+  }
+  for (int i = threadIdx.x; i < Q; i += blockDim.x) mw[i] = 0.5 * dxe * w[i] * geo[i * 4 + 1];
+  __syncthreads();
+  const int k = blockIdx.y * blockDim.x + threadIdx.x;
+  if (k >= ps.nr) return;
+  const double lam = ps.lam[k];
   // invert the interior block (SPD) by Gauss–Jordan without pivoting
   double Ai[Pm][Pm], Bm[Pm][Pm];
 #pragma unroll
   for (int i = 0; i < Pm; ++i)
 #pragma unroll
-    for (int j = 0; j < Pm; ++j) { Bm[i][j] = E[1 + i][1 + j]; Ai[i][j] = (i == j) ? 1.0 : 0.0; }
+    for (int j = 0; j < Pm; ++j) {
+      Bm[i][j] = Kx[(1 + i) * Q + 1 + j] + (i == j ? lam * mw[1 + i] : 0.0);
+      Ai[i][j] = (i == j) ? 1.0 : 0.0;
+    }
 #pragma unroll
   for (int c = 0; c < Pm; ++c) {
     const double inv = 1.0 / Bm[c][c];
@@ -937,17 +906,17 @@ __global__ void k_prec_elem(DevGeom g, PrecSetup ps) {
   for (int i = 0; i < Pm; ++i) {
     double a0 = 0.0, a1 = 0.0;
 #pragma unroll
-    for (int m = 0; m < Pm; ++m) { a0 = fma(E[0][1 + m], Ai[m][i], a0); a1 = fma(E[P][1 + m], Ai[m][i], a1); }
+    for (int m = 0; m < Pm; ++m) { a0 = fma(Kx[1 + m], Ai[m][i], a0); a1 = fma(Kx[P * Q + 1 + m], Ai[m][i], a1); }
     Z0[i] = a0; Z1[i] = a1;
   }
-  double S00 = E[0][0], S01 = E[0][P], S11 = E[P][P];
+  double S00 = Kx[0] + lam * mw[0], S01 = Kx[P], S11 = Kx[P * Q + P] + lam * mw[P];
 #pragma unroll
   for (int i = 0; i < Pm; ++i) {
-    S00 -= Z0[i] * E[1 + i][0];
-    S01 -= Z0[i] * E[1 + i][P];
-    S11 -= Z1[i] * E[1 + i][P];
+    S00 -= Z0[i] * Kx[(1 + i) * Q];
+    S01 -= Z0[i] * Kx[(1 + i) * Q + P];
+    S11 -= Z1[i] * Kx[(1 + i) * Q + P];
   }
-  const size_t base = (size_t)t;
+  const size_t base = (size_t)k * g.Nx + ex;
   double* A64 = ps.Aii64 + base * Pm * Pm;
   float* A32 = ps.Aii32 + base * Pm * Pm;
 #pragma unroll
@@ -966,58 +935,68 @@ __global__ void k_prec_elem(DevGeom g, PrecSetup ps) {
   ps.schur[base * 3 + 2] = S11;
 }
 
-// One thread per mode: interface tridiagonal, Thomas pivots and the Sherman–Morrison closure
-// for periodic meshes (γ = −d_0, u = (γ,0,…,0,e_{N−1}), v = (1,0,…,0,e_{N−1}/γ)).
-__global__ void k_prec_tri(DevGeom g, PrecSetup ps) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= ps.nr) return;
+// Block (one warp) per mode: interface tridiagonal d_j = S00(j) + S11(j−1), e_j = S01(j), Thomas
+// pivots and the Sherman–Morrison closure for periodic meshes (γ = −d_0, u = (γ,0,…,0,e_{N−1}),
+// v = (1,0,…,0,e_{N−1}/γ)).  The sequential recurrences run on lane 0 from shared memory when
+// 5·nif values fit (`staged`), otherwise from global memory.
+__global__ void __launch_bounds__(32) k_prec_tri(DevGeom g, PrecSetup ps, int staged) {
+  extern __shared__ __align__(16) double tri_sm[];
+  const int k = blockIdx.x;
   const int N = ps.nif, Nx = g.Nx;
   const double* sc = ps.schur + (size_t)k * Nx * 3;
   double* te = ps.te64 + (size_t)k * N;
   double* tm = ps.tm64 + (size_t)k * N;
   double* tcp = ps.tcp64 + (size_t)k * N;
   double* tz = ps.tz64 + (size_t)k * N;
-  // d_j = S00(j) + S11(j−1), e_j = S01(j)
-  auto dj = [&](int j) {
-    double v = 0.0;
-    if (g.periodic) v = sc[j * 3 + 0] + sc[(j == 0 ? Nx - 1 : j - 1) * 3 + 2];
-    else v = (j < Nx ? sc[j * 3 + 0] : 0.0) + (j > 0 ? sc[(j - 1) * 3 + 2] : 0.0);
-    return v;
-  };
+  // unstaged: results go straight to their destinations and d_j to the scratch array
+  double *dsrc = ps.scratch + (size_t)k * N, *ee = te, *mm = tm, *cc = tcp, *zz = tz;
+  if (staged) { dsrc = tri_sm; ee = dsrc + N; mm = ee + N; cc = mm + N; zz = cc + N; }
+  for (int j = threadIdx.x; j < N; j += blockDim.x) {
+    double d;
+    if (g.periodic) d = sc[j * 3 + 0] + sc[(j == 0 ? Nx - 1 : j - 1) * 3 + 2];
+    else d = (j < Nx ? sc[j * 3 + 0] : 0.0) + (j > 0 ? sc[(j - 1) * 3 + 2] : 0.0);
+    dsrc[j] = d;
+    ee[j] = (j < N - 1) ? sc[j * 3 + 1] : 0.0;
+  }
+  __syncthreads();
   const double corner = g.periodic ? sc[(Nx - 1) * 3 + 1] : 0.0;
-  const double gamma = g.periodic ? -dj(0) : 0.0;
-  double cp_prev = 0.0, e_prev = 0.0;
-  for (int j = 0; j < N; ++j) {
-    double d = dj(j);
-    if (g.periodic && j == 0) d -= gamma;
-    if (g.periodic && j == N - 1) d -= corner * corner / gamma;
-    const double e = (j < N - 1) ? sc[j * 3 + 1] : 0.0;
-    const double m = 1.0 / (j == 0 ? d : d - e_prev * cp_prev);
-    const double cp = e * m;
-    te[j] = e; tm[j] = m; tcp[j] = cp;
-    cp_prev = cp; e_prev = e;
-  }
-  if (g.periodic) {
-    // y = T'⁻¹ u
-    double prev = gamma * tm[0];
-    tz[0] = prev;
-    for (int j = 1; j < N; ++j) {
-      const double uj = (j == N - 1) ? corner : 0.0;
-      prev = (uj - te[j - 1] * prev) * tm[j];
-      tz[j] = prev;
+  const double gamma = g.periodic ? -dsrc[0] : 0.0;
+  if (threadIdx.x == 0) {
+    double cp_prev = 0.0, e_prev = 0.0;
+    for (int j = 0; j < N; ++j) {
+      double d = dsrc[j];
+      if (g.periodic && j == 0) d -= gamma;
+      if (g.periodic && j == N - 1) d -= corner * corner / gamma;
+      const double e = ee[j];
+      const double m = 1.0 / (j == 0 ? d : d - e_prev * cp_prev);
+      const double cp = e * m;
+      mm[j] = m; cc[j] = cp;
+      cp_prev = cp; e_prev = e;
     }
-    for (int j = N - 2; j >= 0; --j) tz[j] -= tcp[j] * tz[j + 1];
-    const double vl = corner / gamma;
-    ps.tvl64[k] = vl;
-    ps.tfac64[k] = 1.0 / (1.0 + tz[0] + vl * tz[N - 1]);
-    ps.tvl32[k] = (float)vl;
-    ps.tfac32[k] = (float)ps.tfac64[k];
+    if (g.periodic) {
+      // z = T'⁻¹ u
+      double prev = gamma * mm[0];
+      zz[0] = prev;
+      for (int j = 1; j < N; ++j) {
+        const double uj = (j == N - 1) ? corner : 0.0;
+        prev = (uj - ee[j - 1] * prev) * mm[j];
+        zz[j] = prev;
+      }
+      for (int j = N - 2; j >= 0; --j) zz[j] -= cc[j] * zz[j + 1];
+      const double vl = corner / gamma;
+      const double fac = 1.0 / (1.0 + zz[0] + vl * zz[N - 1]);
+      ps.tvl64[k] = vl;
+      ps.tfac64[k] = fac;
+      ps.tvl32[k] = (float)vl;
+      ps.tfac32[k] = (float)fac;
+    }
   }
-  for (int j = 0; j < N; ++j) {
-    ps.te32[(size_t)k * N + j] = (float)te[j];
-    ps.tm32[(size_t)k * N + j] = (float)tm[j];
-    ps.tcp32[(size_t)k * N + j] = (float)tcp[j];
-    ps.tz32[(size_t)k * N + j] = (float)tz[j];
+  __syncthreads();
+  for (int j = threadIdx.x; j < N; j += blockDim.x) {
+    const double e = ee[j], m = mm[j], cp = cc[j], z = g.periodic ? zz[j] : 0.0;
+    te[j] = e; tm[j] = m; tcp[j] = cp; tz[j] = z;
+    const size_t o = (size_t)k * N + j;
+    ps.te32[o] = (float)e; ps.tm32[o] = (float)m; ps.tcp32[o] = (float)cp; ps.tz32[o] = (float)z;
   }
 }
 
@@ -1045,12 +1024,12 @@ static size_t apply_smem_bytes(int P, int nrow, int Nz, size_t elem) {
   return elem * (size_t)(Q * Q + Q + nrow + 2 * Nz + 4 * Q + Q * nrow + 2 * Nz * Q * Q) + 16;
 }
 
-cudaError_t launch_geometry(const DevGeom& g, const double* eta, cudaStream_t s) {
+cudaError_t launch_geometry(const DevGeom& g, const double* eta, bool with_diag, cudaStream_t s) {
   const int n1 = g.Nx * (g.P + 1);
   SEM_DISPATCH_P(g.P, (k_geometry<PP><<<(n1 + 127) / 128, 128, 0, s>>>(g, eta)));
   count_launch();
   cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  if (e != cudaSuccess || !with_diag) return e;
   const long long n = (long long)g.ncol * g.nrow;
   SEM_DISPATCH_P(g.P, (k_diag<PP><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g)));
   count_launch();
@@ -1153,13 +1132,8 @@ static cudaError_t pcg_occupancy(size_t smem, int* per_sm) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_pcg<P, MIXED>, kThreads, smem);
 }
 
-size_t tri_smem_offset(int P, int nrow, int Nz) {
-  return (apply_smem_bytes(P, nrow, Nz, sizeof(double)) + 15) & ~size_t(15);
-}
-
-cudaError_t pcg_grid_size(int P, int Nz, int nrow, int Nx, int mixed, size_t tri_smem, int* grid,
-                          size_t* smem) {
-  *smem = tri_smem_offset(P, nrow, Nz) + tri_smem;
+cudaError_t pcg_grid_size(int P, int Nz, int nrow, int Nx, int mixed, int* grid, size_t* smem) {
+  *smem = apply_smem_bytes(P, nrow, Nz, sizeof(double));
   int dev = 0, sms = 0, per_sm = 0;
   cudaError_t e;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
@@ -1173,13 +1147,21 @@ cudaError_t pcg_grid_size(int P, int Nz, int nrow, int Nx, int mixed, size_t tri
   return cudaSuccess;
 }
 
+constexpr size_t kTriStageMax = 160 * 1024;
+
 cudaError_t launch_prec_setup(const DevGeom& g, const PrecSetup& ps, cudaStream_t s) {
-  const int n1 = ps.nr * g.Nx;
-  SEM_DISPATCH_P(g.P, (k_prec_elem<PP><<<(n1 + 63) / 64, 64, 0, s>>>(g, ps)));
+  const dim3 grid_e(g.Nx, (ps.nr + kPrecModesPerBlock - 1) / kPrecModesPerBlock);
+  SEM_DISPATCH_P(g.P, (k_prec_elem<PP><<<grid_e, kPrecModesPerBlock, 0, s>>>(g, ps)));
   count_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_prec_tri<<<(ps.nr + 31) / 32, 32, 0, s>>>(g, ps);
+  const size_t bytes = (size_t)5 * ps.nif * sizeof(double);
+  const int staged = bytes <= kTriStageMax ? 1 : 0;
+  if (staged) {
+    e = cudaFuncSetAttribute(k_prec_tri, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTriStageMax);
+    if (e != cudaSuccess) return e;
+  }
+  k_prec_tri<<<ps.nr, 32, staged ? bytes : 0, s>>>(g, ps, staged);
   count_launch();
   return cudaGetLastError();
 }

@@ -74,25 +74,16 @@ __global__ void k_mass1d(SurfTables t, const double* __restrict__ R, int nrhs, d
     gR[k] = r;
   }
   __syncthreads();
-  if (threadIdx.x < nrhs) {
-    const int rh = threadIdx.x;
+  if ((threadIdx.x >> 5) < nrhs) {
+    const int rh = threadIdx.x >> 5;
     const double* gl = gL + rh * Nx;
     const double* gr = gR + rh * Nx;
-    double* y = ub + rh * N;
-    double prev = 0.0;
-    for (int j = 0; j < N; ++j) {
-      double gj;
-      if (t.periodic) gj = gl[j] + gr[j == 0 ? Nx - 1 : j - 1];
-      else gj = (j < Nx ? gl[j] : 0.0) + (j > 0 ? gr[j - 1] : 0.0);
-      const double v = (j == 0 ? gj : fma(-t.th_e[j - 1], prev, gj)) * t.th_m[j];
-      y[j] = v;
-      prev = v;
-    }
-    for (int j = N - 2; j >= 0; --j) y[j] = fma(-t.th_cp[j], y[j + 1], y[j]);
-    if (t.periodic) {
-      const double c = (y[0] + t.th_vlast * y[N - 1]) * t.th_fac;
-      for (int j = 0; j < N; ++j) y[j] = fma(-c, t.th_z[j], y[j]);
-    }
+    auto gfun = [&](int j) -> double {
+      if (t.periodic) return gl[j] + gr[j == 0 ? Nx - 1 : j - 1];
+      return (j < Nx ? gl[j] : 0.0) + (j > 0 ? gr[j - 1] : 0.0);
+    };
+    warp_tridiag<double>(N, gfun, t.th_e, t.th_m, t.th_cp, t.periodic != 0, t.th_z, t.th_vlast, t.th_fac,
+                         ub + rh * N);
   }
   __syncthreads();
   const int extra = t.periodic ? 0 : 1;

@@ -78,7 +78,7 @@ struct PrecSetup {
   // writable aliases of the factor arrays
   double *Aii64, *Z64, *te64, *tm64, *tcp64, *tz64, *tvl64, *tfac64;
   float *Aii32, *Z32, *te32, *tm32, *tcp32, *tz32, *tvl32, *tfac32;
-  double* scratch;         // [nr][4*nif] for large interface systems
+  double* scratch;         // [nr][nif] pivots' right-hand terms when the set-up is not staged
 };
 
 struct PcgArgs {
@@ -97,8 +97,6 @@ struct PcgArgs {
   PrecView<double> pv64;
   PrecView<float> pv32;
   int precond;            // PREC_SEPARABLE or PREC_JACOBI
-  int tri_smem;           // bytes of dynamic shared memory reserved for the interface solves (0: global)
-  int tri_smem_offset;    // their offset in the dynamic shared memory
   double tol;
   double inner_rtol;
   int max_iter;
@@ -132,17 +130,16 @@ struct SurfTables {
 
 // ---- launchers (kernels_laplace.cu) ----
 cudaError_t upload_line_tables(const double* D64, const double* w64);  // packed, all orders
-cudaError_t launch_geometry(const DevGeom& g, const double* eta, cudaStream_t s);
+// σ-geometry per element-local column; with_diag also builds the Jacobi diagonal.
+cudaError_t launch_geometry(const DevGeom& g, const double* eta, bool with_diag, cudaStream_t s);
 cudaError_t launch_apply(const DevGeom& g, const double* x, double* y, double* qtmp, double* edge,
                          cudaStream_t s);
 cudaError_t launch_l2g(const DevGeom& g, int32_t* l2g, cudaStream_t s);
 // Allocation-free apply (scratch in a static device array of kNoAllocEdgeMax doubles).
 constexpr size_t kNoAllocEdgeMax = size_t(1) << 20;
 cudaError_t launch_apply_noalloc(const DevGeom& g, const double* x, double* y, cudaStream_t s);
-cudaError_t pcg_grid_size(int P, int Nz, int nrow, int Nx, int mixed, size_t tri_smem, int* grid,
-                          size_t* smem);
+cudaError_t pcg_grid_size(int P, int Nz, int nrow, int Nx, int mixed, int* grid, size_t* smem);
 cudaError_t launch_prec_setup(const DevGeom& g, const PrecSetup& ps, cudaStream_t s);
-size_t tri_smem_offset(int P, int nrow, int Nz);
 cudaError_t launch_pcg(const DevGeom& g, const PcgArgs& a, int grid, size_t smem, cudaStream_t s);
 
 // ---- launchers (kernels_surface.cu) ----
@@ -159,6 +156,72 @@ cudaError_t launch_filter(const SurfTables& t, double* q0, double* q1, cudaStrea
 cudaError_t launch_rk4_stage(int stage, int n, double dt, double* eta, double* phis,
                              const double* keta, const double* kphis, double* acc_eta,
                              double* acc_phis, double* st_eta, double* st_phis, cudaStream_t s);
+
+// ---- device helpers shared by the translation units ----
+__device__ __forceinline__ double fmx(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fmx(float a, float b, float c) { return fmaf(a, b, c); }
+
+// One warp solves a tridiagonal system with precomputed Thomas factors (pivots m_j, c'_j,
+// off-diagonals e_j), closed by Sherman–Morrison when `periodic` (T'⁻¹u = tz, v_{N−1} =
+// tvl, factor tfac).  The two first-order recurrences
+//     y_j = g_j m_j − (e_{j−1} m_j) y_{j−1},        x_j = y_j − c'_j x_{j+1},
+// are evaluated as a parallel prefix over affine maps: each lane composes a contiguous
+// chunk, the lanes scan the composed maps with shuffles, then each lane replays its chunk.
+// `gfun(j)` returns the right-hand side; `out` (N values, global or shared) receives x.
+// Must be called by all 32 lanes of a warp.
+template <class T, class GFun>
+__device__ __forceinline__ void warp_tridiag(int N, GFun gfun, const T* te, const T* tm, const T* tcp,
+                                             bool periodic, const T* tz, T tvl, T tfac, T* out) {
+  const int lane = threadIdx.x & 31;
+  const int c = (N + 31) / 32;
+  const int j0 = min(N, lane * c), j1 = min(N, j0 + c);
+  const unsigned full = 0xffffffffu;
+  // forward: y_j = α_j y_{j−1} + β_j, α_j = −e_{j−1} m_j, β_j = g_j m_j
+  T A = T(1), B = T(0);
+  for (int j = j0; j < j1; ++j) {
+    const T m = tm[j];
+    const T al = j > 0 ? -te[j - 1] * m : T(0);
+    B = fmx(al, B, gfun(j) * m);
+    A = al * A;
+  }
+  for (int o = 1; o < 32; o <<= 1) {
+    const T Ap = __shfl_up_sync(full, A, o), Bp = __shfl_up_sync(full, B, o);
+    if (lane >= o) { B = fmx(A, Bp, B); A = A * Ap; }
+  }
+  T y = __shfl_up_sync(full, B, 1);
+  if (lane == 0) y = T(0);
+  for (int j = j0; j < j1; ++j) {
+    const T m = tm[j];
+    const T al = j > 0 ? -te[j - 1] * m : T(0);
+    y = fmx(al, y, gfun(j) * m);
+    out[j] = y;
+  }
+  __syncwarp();
+  // backward: x_j = γ_j x_{j+1} + y_j, γ_j = −c'_j (c'_{N−1} = 0)
+  A = T(1); B = T(0);
+  for (int j = j1 - 1; j >= j0; --j) {
+    const T ga = -tcp[j];
+    B = fmx(ga, B, out[j]);
+    A = ga * A;
+  }
+  for (int o = 1; o < 32; o <<= 1) {
+    const T An = __shfl_down_sync(full, A, o), Bn = __shfl_down_sync(full, B, o);
+    if (lane + o < 32) { B = fmx(A, Bn, B); A = A * An; }
+  }
+  T x = __shfl_down_sync(full, B, 1);
+  if (lane == 31) x = T(0);
+  for (int j = j1 - 1; j >= j0; --j) {
+    x = fmx(-tcp[j], x, out[j]);
+    out[j] = x;
+  }
+  __syncwarp();
+  if (periodic) {
+    const T cc = (out[0] + tvl * out[N - 1]) * tfac;
+    __syncwarp();
+    for (int j = lane; j < N; j += 32) out[j] = fmx(-cc, tz[j], out[j]);
+    __syncwarp();
+  }
+}
 
 // Launch counter (all kernels of this library).
 void count_launch(int k = 1);
