@@ -389,6 +389,8 @@ int sem_mesh_create(const sem_params* pin, const double* x_edges_h, const double
                o_e32 = cv.take<float>(nE);
   const size_t o_Phi = cv.take<double>(n), o_qtmp = cv.take<double>(n), o_etmp = cv.take<double>(nE);
   const size_t o_r64b = cv.take<double>(n), o_r32b = cv.take<float>(n);
+  const size_t o_s64b = cv.take<double>(n), o_s32b = cv.take<float>(n);
+  const size_t o_uh64 = cv.take<double>((size_t)m->grid * nrow), o_uh32 = cv.take<float>((size_t)m->grid * nrow);
   const size_t nEl = (size_t)nr * Nx, nIf = (size_t)nr * N;
   const size_t o_S64 = cv.take<double>((size_t)nr * nr), o_S32 = cv.take<float>((size_t)nr * nr),
                o_lam = cv.take<double>(nr), o_schur = cv.take<double>(nEl * 3),
@@ -458,6 +460,8 @@ int sem_mesh_create(const sem_params* pin, const double* x_edges_h, const double
   a.rec = m->rec;
   a.tol = p.tol; a.inner_rtol = 1e-4; a.max_iter = p.max_iter; a.mixed = p.precision == SEM_PREC_MIXED;
   a.r64b = D_(o_r64b); a.r32b = F_(o_r32b);
+  a.s64b = D_(o_s64b); a.s32b = F_(o_s32b);
+  a.uh64 = D_(o_uh64); a.uh32 = F_(o_uh32);
   a.precond = p.precond == SEM_PRECOND_JACOBI ? PREC_JACOBI : PREC_SEPARABLE;
   PrecSetup& ps = m->ps;
   ps.nr = nr; ps.nif = N; ps.lam = D_(o_lam); ps.schur = D_(o_schur);

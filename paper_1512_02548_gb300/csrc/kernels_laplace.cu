@@ -447,38 +447,41 @@ __device__ __forceinline__ bool owns_local_col(const DevGeom& g, int ex, int a) 
 // in x, solved by static condensation of the element interiors and a tridiagonal (cyclic)
 // interface system.
 
-// Phase "update": r_new = r_old − α q on owned nodes (and the halo column, in shared memory),
-// x += α p; then r̂ = Sᵀ r per column and the per-mode condensed right-hand sides gL, gR.
-// With update == false, r_new is r_old.  Accumulates Σ r² (own) into acc[0]; for the
-// Jacobi preconditioner also z = D⁻¹ r and Σ r z into acc[1].
-template <int P, class T, class A>
-__device__ void phase_update(const DevGeom& g, Smem<P, T>& s, const Range& R, bool update, T alpha,
-                             T* x, const T* p, const T* q, const T* edge, const T* r_old, T* r_new,
-                             const T* invdiag, T* z, int precond, const PrecView<T>& pv, A (&acc)[2]) {
+// Vectors of one Krylov level (type T).  Owned-column values live in the global arrays; `uh`
+// holds M⁻¹r on this CTA's halo column (the first column of the next CTA), which each CTA
+// rebuilds itself so that no barrier separates the preconditioner from the next apply.
+template <class T>
+struct CgVecs {
+  T* x;              // solution (FP64 level) or correction (FP32 level)
+  T* r[2];           // residual, double-buffered
+  T* s[2];           // s = A p, double-buffered
+  T* p;              // search direction (owned columns only)
+  T* u;              // u = M⁻¹ r (owned columns)
+  T* uh;             // u on the CTA's halo column, [grid][nrow]
+  T* w;              // w = A u (owned columns)
+  T* edge;           // A u contribution to the next element column's first column
+  const T* invdiag;  // Jacobi preconditioner
+};
+
+__device__ __forceinline__ bool is_halo_col(const DevGeom& g, const Range& R, int ex, int a) {
+  return a == g.P && ex == R.e1 - 1 && !owns_local_col(g, ex, g.P);
+}
+
+// Update of the Chronopoulos–Gear recurrences on owned nodes (and, for r, on the halo column),
+// then the first part of u = M⁻¹ r:
+//   s ← w + β s,  r ← r − α s,  p ← u + β p,  x ← x + α p      (first iteration: s ← w, p ← u).
+// With update == false only the preconditioner part runs on r[cur].  Jacobi completes u here;
+// the separable preconditioner transforms the residual to the σ-eigenbasis and condenses.
+template <int P, class T>
+__device__ void cg_update(const DevGeom& g, Smem<P, T>& s, const Range& R, const PrecView<T>& pv,
+                          int precond, const CgVecs<T>& V, int cur, bool update, bool first, T alpha,
+                          T beta) {
   constexpr int Q = P + 1, Pm = P - 1;
-  const int nrow = g.nrow;
-  if (precond == PREC_JACOBI) {
-    const int ncols = R.c1 - R.c0;
-    for (int t = threadIdx.x; t < ncols * nrow; t += blockDim.x) {
-      const int col = R.c0 + t / nrow, iz = t - (t / nrow) * nrow;
-      if (iz == nrow - 1) continue;
-      const size_t i = (size_t)col * nrow + iz;
-      T rv = r_old[i];
-      if (update) {
-        T qv = q[i];
-        if (has_left_edge(g, col)) qv += ldcg(edge + (size_t)left_element(g, col) * nrow + iz);
-        x[i] = fmx(alpha, p[i], x[i]);
-        rv = fmx(-alpha, qv, rv);
-        r_new[i] = rv;
-      }
-      const T zv = rv * invdiag[i];
-      z[i] = zv;
-      acc[0] += (A)rv * (A)rv;
-      acc[1] += (A)rv * (A)zv;
-    }
-    return;
-  }
-  const int nr = pv.nr;
+  const int nrow = g.nrow, nr = nrow - 1;
+  const T* r_old = V.r[cur];
+  T* r_new = V.r[cur ^ 1];
+  const T* s_old = V.s[cur];
+  T* s_new = V.s[cur ^ 1];
   T* X = s.X;     // [Q][nr] residual of the element column
   T* RH = s.F1;   // [Q][nr] σ-transformed residual
   for (int ex = R.e0; ex < R.e1; ++ex) {
@@ -487,19 +490,32 @@ __device__ void phase_update(const DevGeom& g, Smem<P, T>& s, const Range& R, bo
       const int col = col_of(g, ex, a);
       const size_t i = (size_t)col * nrow + j;
       const bool own = owns_local_col(g, ex, a);
-      T rv = ldcg(r_old + i);
+      T rv;
       if (update) {
-        T qv = ldcg(q + i);
-        if (has_left_edge(g, col)) qv += ldcg(edge + (size_t)left_element(g, col) * nrow + j);
-        rv = fmx(-alpha, qv, rv);
+        T wv = ldcg(V.w + i);
+        if (has_left_edge(g, col)) wv += ldcg(V.edge + (size_t)left_element(g, col) * nrow + j);
+        const T sv = first ? wv : fmx(beta, ldcg(s_old + i), wv);
+        rv = fmx(-alpha, sv, ldcg(r_old + i));
         if (own) {
+          s_new[i] = sv;
           r_new[i] = rv;
-          x[i] = fmx(alpha, p[i], x[i]);
+          const T uo = V.u[i];
+          const T pn = first ? uo : fmx(beta, V.p[i], uo);
+          V.p[i] = pn;
+          V.x[i] = fmx(alpha, pn, V.x[i]);
         }
+      } else {
+        rv = ldcg(r_old + i);
       }
-      if (own) acc[0] += (A)rv * (A)rv;
-      X[t] = rv;
+      if (precond == PREC_JACOBI) {
+        const T uv = rv * V.invdiag[i];
+        if (own) V.u[i] = uv;
+        else if (is_halo_col(g, R, ex, a)) V.uh[(size_t)blockIdx.x * nrow + j] = uv;
+      } else {
+        X[t] = rv;
+      }
     }
+    if (precond == PREC_JACOBI) continue;
     __syncthreads();
     for (int t = threadIdx.x; t < Q * nr; t += blockDim.x) {
       const int a = t / nr, k = t - a * nr;
@@ -547,10 +563,11 @@ __device__ void phase_interface(const DevGeom& g, const PrecView<T>& pv) {
   }
 }
 
-// Back-substitution of the element interiors and z = S ẑ on owned columns; Σ r z into acc.
-template <int P, class T, class A>
+// Back-substitution of the element interiors, then u = S ẑ on owned columns and on the halo
+// column (whose modal values are interface unknowns, known to every CTA after the solve).
+template <int P, class T>
 __device__ void phase_backsub(const DevGeom& g, Smem<P, T>& s, const Range& R, const PrecView<T>& pv,
-                              const T* r, T* z, A& acc) {
+                              const CgVecs<T>& V) {
   constexpr int Q = P + 1, Pm = P - 1;
   const int nrow = g.nrow, nr = pv.nr, N = pv.nif;
   T* ZH = s.F1;   // [Q][nr]
@@ -576,126 +593,105 @@ __device__ void phase_backsub(const DevGeom& g, Smem<P, T>& s, const Range& R, c
       ZH[t] = v;
     }
     __syncthreads();
-    const int na = owns_local_col(g, ex, P) ? Q : P;
-    for (int t = threadIdx.x; t < na * nr; t += blockDim.x) {
+    for (int t = threadIdx.x; t < Q * nr; t += blockDim.x) {
       const int a = t / nr, j = t - a * nr;
+      const bool own = owns_local_col(g, ex, a);
+      const bool halo = is_halo_col(g, R, ex, a);
+      if (!own && !halo) continue;
       const T* Za = ZH + a * nr;
       const T* Sj = pv.S + j * nr;
       T v = 0;
       for (int k = 0; k < nr; ++k) v = fmx(Sj[k], Za[k], v);
-      const size_t i = (size_t)col_of(g, ex, a) * nrow + j;
-      z[i] = v;
-      acc += (A)r[i] * (A)v;
+      if (own) V.u[(size_t)col_of(g, ex, a) * nrow + j] = v;
+      else V.uh[(size_t)blockIdx.x * nrow + j] = v;
     }
     __syncthreads();
   }
 }
 
-// z = M⁻¹ r (and the update of r when `update`), three grid phases for the separable
-// preconditioner, one for Jacobi.  On return red-sums: rr (own r²) and rz.  False on timeout.
-template <int P, class T, class A>
-__device__ bool precondition(const DevGeom& g, Smem<P, T>& s, const Range& R, const PcgArgs& PA,
-                             const PrecView<T>& pv, bool update, T alpha, T* x, const T* p, const T* q,
-                             const T* edge, const T* r_old, T* r_new, const T* invdiag, T* z,
-                             double* red, int* s_flag, double& rr, double& rz) {
-  A acc[2] = {A(0), A(0)};
-  phase_update<P, T, A>(g, s, R, update, alpha, x, p, q, edge, r_old, r_new, invdiag, z, PA.precond, pv,
-                        acc);
-  const T* rcur = update ? r_new : r_old;
-  if (PA.precond != PREC_JACOBI) {
-    A a1[1] = {acc[0]};
-    block_sum<1, A>(a1, red);
-    acc[0] = a1[0];
-    if (!grid_barrier(PA.bar, g.status, s_flag)) return false;
-    phase_interface<T>(g, pv);
-    if (!grid_barrier(PA.bar, g.status, s_flag)) return false;
-    A rzl = A(0);
-    phase_backsub<P, T, A>(g, s, R, pv, rcur, z, rzl);
-    A a2[1] = {rzl};
-    block_sum<1, A>(a2, red);
-    double out[2] = {(double)acc[0], (double)a2[0]};
-    put_partials<2, double>(PA.part, PA.part_stride, 3, out);
-  } else {
-    block_sum<2, A>(acc, red);
-    double out[2] = {(double)acc[0], (double)acc[1]};
-    put_partials<2, double>(PA.part, PA.part_stride, 3, out);
-  }
+// Remaining grid phases of u = M⁻¹ r after cg_update (separable: interface solve and
+// back-substitution; Jacobi: nothing but a barrier that protects w and edge).
+template <int P, class T>
+__device__ bool finish_precondition(const DevGeom& g, Smem<P, T>& s, const Range& R, const PcgArgs& PA,
+                                    const PrecView<T>& pv, const CgVecs<T>& V, int* s_flag) {
+  if (PA.precond == PREC_JACOBI) return grid_barrier(PA.bar, g.status, s_flag);
   if (!grid_barrier(PA.bar, g.status, s_flag)) return false;
-  double sums[2];
-  grid_sum<2>(PA.part, PA.part_stride, 3, sums, red);
-  rr = sums[0];
-  rz = sums[1];
+  phase_interface<T>(g, pv);
+  if (!grid_barrier(PA.bar, g.status, s_flag)) return false;
+  phase_backsub<P, T>(g, s, R, pv, V);
   return true;
 }
 
-// Inner PCG on A x = r (vectors of type T, accumulations in A), from the given x and the
-// residual in r[0] with z, rr, rz already computed.  Stops when rr ≤ target or after max_it
-// iterations.  Returns iterations, or −1 on a barrier timeout.
+// Preconditioned conjugate gradients in the Chronopoulos–Gear form: one grid reduction per
+// iteration, (γ, δ, ‖r‖²) = ((r,u), (u,Au), (r,r)) taken together with the apply w = A u.
+//   β = γ/γ_prev, α = γ/(δ − βγ/α_prev)  (first: β = 0, α = γ/δ).
+// Starts from V.x with its residual in V.r[0].  Stops when ‖r‖² ≤ target or after max_it
+// iterations.  Returns the iterations, or −1 on a barrier timeout; ‖r‖² of the final residual
+// (on thread 0) in *rr_out.
 template <int P, class T, class A>
-__device__ int inner_pcg(const DevGeom& g, Smem<P, T>& s, const Range& R, const PcgArgs& PA,
-                         const PrecView<T>& pv, T* x, T* r0, T* r1, T* z, T* pa, T* pb, T* q, T* edge,
-                         const T* invdiag, double* red, int* s_flag, double rr, double rz,
-                         double target, int max_it, double* rr_out) {
+__device__ int cg_solve(const DevGeom& g, Smem<P, T>& s, const Range& R, const PcgArgs& PA,
+                        const PrecView<T>& pv, const CgVecs<T>& V, double target, int max_it, double* red,
+                        int* s_flag, double* rr_out) {
   const int nrow = g.nrow;
-  int k = 0;
-  double rz_prev = 1.0;
-  T* p_old = pa;
-  T* p_new = pb;
-  T* r_cur = r0;
-  T* r_nxt = r1;
   __shared__ T s_scal[2];
   __shared__ int s_stop;
+  int cur = 0;
+  cg_update<P, T>(g, s, R, pv, PA.precond, V, cur, false, true, T(0), T(0));
+  if (!finish_precondition<P, T>(g, s, R, PA, pv, V, s_flag)) return -1;
+  int k = 0;
+  double gamma_prev = 1.0, alpha_prev = 1.0, rr = 0.0;
   while (true) {
-    // scalar control on one thread (FP64 work on every thread would cost the FP64 pipe)
+    // w = A u and the three inner products (u on owned columns and the halo column)
+    const T* rc = V.r[cur];
+    A acc[3] = {A(0), A(0), A(0)};   // γ = (r,u), δ = (u,Au), (r,r)
+    for (int ex = R.e0; ex < R.e1; ++ex) {
+      acc[1] += (A)apply_element_column<P, T>(
+          g, s, ex,
+          [&](int e, int a, int iz) -> T {
+            if (iz == nrow - 1) return T(0);
+            if (is_halo_col(g, R, e, a)) return V.uh[(size_t)blockIdx.x * nrow + iz];
+            const size_t i = (size_t)col_of(g, e, a) * nrow + iz;
+            const T uv = V.u[i];
+            if (owns_local_col(g, e, a)) {
+              const T rv = rc[i];
+              acc[0] += (A)rv * (A)uv;
+              acc[2] += (A)rv * (A)rv;
+            }
+            return uv;
+          },
+          [&](int e, int a, int iz, T y) {
+            if (owns_local_col(g, e, a)) V.w[(size_t)col_of(g, e, a) * nrow + iz] = y;
+            else V.edge[(size_t)e * nrow + iz] = y;
+          });
+    }
+    block_sum<3, A>(acc, red);
+    put_partials<3, A>(PA.part, PA.part_stride, 2, acc);
+    if (!grid_barrier(PA.bar, g.status, s_flag)) return -1;
+    double sums[3];
+    grid_sum<3>(PA.part, PA.part_stride, 2, sums, red);
     if (threadIdx.x == 0) {
+      rr = sums[2];
       int stop = 0;
-      if (!(rr == rr) || isinf(rr)) { atomicOr(g.status, ST_NONFINITE); stop = 1; }
+      if (!(rr == rr) || isinf(rr) || !(sums[1] == sums[1])) { atomicOr(g.status, ST_NONFINITE); stop = 1; }
       else if (rr <= target || k >= max_it) stop = 1;
+      if (!stop) {
+        const double gam = sums[0], del = sums[1];
+        double alpha, beta;
+        if (k == 0) { beta = 0.0; alpha = gam / del; }
+        else { beta = gam / gamma_prev; alpha = gam / (del - beta * gam / alpha_prev); }
+        gamma_prev = gam;
+        alpha_prev = alpha;
+        s_scal[0] = (T)alpha;
+        s_scal[1] = (T)beta;
+      }
       s_stop = stop;
-      s_scal[1] = (T)(k == 0 ? 0.0 : rz / rz_prev);
     }
     __syncthreads();
     if (s_stop) break;
-    const T beta = s_scal[1];
-    const bool first = (k == 0);
-    // Phase A: p_new = z + β p_old (own columns written, halo column rebuilt), q = A p_new
-    A pap[1] = {A(0)};
-    for (int ex = R.e0; ex < R.e1; ++ex) {
-      pap[0] += (A)apply_element_column<P, T>(
-          g, s, ex,
-          [&](int e, int a, int iz) -> T {
-            if (iz == nrow - 1) return (T)0;
-            const size_t i = (size_t)col_of(g, e, a) * nrow + iz;
-            const T zi = ldcg(z + i);
-            const T pn = first ? zi : fmx(beta, ldcg(p_old + i), zi);
-            if (owns_local_col(g, e, a)) p_new[i] = pn;
-            return pn;
-          },
-          [&](int e, int a, int iz, T y) {
-            if (owns_local_col(g, e, a)) q[(size_t)col_of(g, e, a) * nrow + iz] = y;
-            else edge[(size_t)e * nrow + iz] = y;
-          });
-    }
-    block_sum<1, A>(pap, red);
-    put_partials<1, A>(PA.part, PA.part_stride, 2, pap);
-    if (!grid_barrier(PA.bar, g.status, s_flag)) return -1;
-    double papd[1];
-    grid_sum<1>(PA.part, PA.part_stride, 2, papd, red);
-    if (threadIdx.x == 0) s_scal[0] = (T)(rz / papd[0]);
-    __syncthreads();
-    const T alpha = s_scal[0];
-    // Phase B(+C+D): x += α p, r −= α q, z = M⁻¹ r
-    double rr_n, rz_n;
-    if (!precondition<P, T, A>(g, s, R, PA, pv, true, alpha, x, p_new, q, edge, r_cur, r_nxt, invdiag, z,
-                               red, s_flag, rr_n, rz_n))
-      return -1;
-    if (threadIdx.x == 0) {
-      rr = rr_n;
-      rz_prev = rz;
-      rz = rz_n;
-    }
-    T* tmp = p_old; p_old = p_new; p_new = tmp;
-    tmp = r_cur; r_cur = r_nxt; r_nxt = tmp;
+    const T alpha = s_scal[0], beta = s_scal[1];
+    cg_update<P, T>(g, s, R, pv, PA.precond, V, cur, true, k == 0, alpha, beta);
+    cur ^= 1;
+    if (!finish_precondition<P, T>(g, s, R, PA, pv, V, s_flag)) return -1;
     ++k;
   }
   *rr_out = rr;
@@ -769,7 +765,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg(DevGeom g, PcgArgs A) {
   Smem<P, double> s64;
   s64.carve(smem_raw, nrow, g.Nz);
   s64.load_tables(g);
-  double rr = 0.0, bb = 0.0, rz = 0.0;
+  double rr = 0.0, bb = 0.0;
   if (!fp64_residual<P>(g, s64, R, A, true, red, &s_flag, rr, bb)) return;
   const double target = A.tol * A.tol * bb;
   int iters = 0, refinements = 0;
@@ -782,24 +778,28 @@ __global__ void __launch_bounds__(kThreads) k_pcg(DevGeom g, PcgArgs A) {
     }
     rr = 0.0;
   } else if (!MIXED) {
-    double rr0;
-    if (!precondition<P, double, double>(g, s64, R, A, A.pv64, false, 0.0, A.x, nullptr, nullptr, nullptr,
-                                         A.r64, A.r64, g.invdiag64, A.z64, red, &s_flag, rr0, rz))
-      return;
+    const CgVecs<double> V{A.x, {A.r64, A.r64b}, {A.p64b, A.s64b}, A.p64a, A.z64, A.uh64, A.q64, A.edge64,
+                           g.invdiag64};
     double rr_out = rr;
-    iters = inner_pcg<P, double, double>(g, s64, R, A, A.pv64, A.x, A.r64, A.r64b, A.z64, A.p64a, A.p64b,
-                                         A.q64, A.edge64, g.invdiag64, red, &s_flag, rr, rz, target,
-                                         A.max_iter, &rr_out);
+    iters = cg_solve<P, double, double>(g, s64, R, A, A.pv64, V, target, A.max_iter, red, &s_flag, &rr_out);
     if (iters < 0) return;
     rr = rr_out;
   } else {
     Smem<P, float> s32;
     s32.carve(smem_raw, nrow, g.Nz);
-    while (rr > target && iters < A.max_iter) {
-      if (!(rr == rr) || isinf(rr)) { if (threadIdx.x == 0) atomicOr(g.status, ST_NONFINITE); break; }
+    const CgVecs<float> V{A.d32, {A.r32, A.r32b}, {A.p32b, A.s32b}, A.p32a, A.z32, A.uh32, A.q32, A.edge32,
+                          g.invdiag32};
+    __shared__ int s_go;
+    while (true) {
+      if (threadIdx.x == 0) {
+        int go = rr > target && iters < A.max_iter;
+        if (!(rr == rr) || isinf(rr)) { atomicOr(g.status, ST_NONFINITE); go = 0; }
+        s_go = go;
+      }
       __syncthreads();
+      if (!s_go) break;
       s32.load_tables(g);
-      // inner: A δ = r in FP32 from δ = 0
+      // inner: A δ = r in FP32 from δ = 0, to a relative residual inner_rtol (or the outer target)
       const int ncols = R.c1 - R.c0;
       for (int t = threadIdx.x; t < ncols * nrow; t += blockDim.x) {
         const int col = R.c0 + t / nrow, iz = t - (t / nrow) * nrow;
@@ -808,15 +808,10 @@ __global__ void __launch_bounds__(kThreads) k_pcg(DevGeom g, PcgArgs A) {
         A.r32[i] = iz == nrow - 1 ? 0.f : (float)A.r64[i];
       }
       if (!grid_barrier(A.bar, g.status, &s_flag)) return;
-      double rr_in, rz_in;
-      if (!precondition<P, float, float>(g, s32, R, A, A.pv32, false, 0.f, A.d32, nullptr, nullptr, nullptr,
-                                         A.r32, A.r32, g.invdiag32, A.z32, red, &s_flag, rr_in, rz_in))
-        return;
-      const double tgt_in = fmax(A.inner_rtol * A.inner_rtol * rr_in, 0.25 * target);
-      double rr_out = rr_in;
-      const int it = inner_pcg<P, float, float>(g, s32, R, A, A.pv32, A.d32, A.r32, A.r32b, A.z32, A.p32a,
-                                                A.p32b, A.q32, A.edge32, g.invdiag32, red, &s_flag,
-                                                rr_in, rz_in, tgt_in, A.max_iter - iters, &rr_out);
+      const double tgt_in = fmax(A.inner_rtol * A.inner_rtol * rr, 0.25 * target);
+      double rr_in = rr;
+      const int it = cg_solve<P, float, float>(g, s32, R, A, A.pv32, V, tgt_in, A.max_iter - iters, red, &s_flag,
+                                               &rr_in);
       if (it < 0) return;
       iters += it;
       ++refinements;

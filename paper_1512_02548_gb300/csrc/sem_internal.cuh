@@ -94,6 +94,10 @@ struct PcgArgs {
   SolveRecord* rec;
   double* r64b;           // second residual buffer (double-buffered update)
   float* r32b;
+  double* s64b;           // second buffer of s = A p
+  float* s32b;
+  double* uh64;           // preconditioned residual on each CTA's halo column, [grid][nrow]
+  float* uh32;
   PrecView<double> pv64;
   PrecView<float> pv32;
   int precond;            // PREC_SEPARABLE or PREC_JACOBI
