@@ -64,6 +64,23 @@ def flops_per_apply(wl) -> float:
     return wl.Nx * wl.Nz * (P + 1) ** 2 * (8 * (P + 1) + 7)
 
 
+def max_over_ranks(value: float, device=None) -> float:
+    """Max of a per-rank scalar over all ranks (identity without torch.distributed)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, steps: int, units_per_step: float, t_max_ms: float) -> float:
+    """Whole-job units/s: every rank runs `steps` steps of its own replica; the job takes the
+    slowest rank's time (weak scaling, no data-path collective)."""
+    return world * steps * units_per_step / (t_max_ms / 1e3)
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -204,6 +221,58 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------------------------
+# Supplementary: the operator apply on a long tank (working set above L2)
+# ---------------------------------------------------------------------------------------------
+def apply_roofline(dev, reps: int = 20):
+    """Time sem_laplace_apply (FP64) on a 65536×4, P=6 periodic tank, 9.8 M nodes.
+
+    Algorithmic work per apply: (8(P+1)+7) flops per element-local node; algorithmic bytes:
+    read x + write y (16 B per node) + geometry (4 doubles per element-local column).
+    Returns achieved FP64 TFLOP/s and HBM GB/s against the FP64 and measured-copy peaks.
+    """
+    import numpy as np
+    import torch
+    import paper_1512_02548_gb300 as sem
+    from sem_workloads import roofline_tank
+    wl = roofline_tank()
+    mesh = sem.Mesh.from_workload(wl)
+    xcol = column_positions(wl)
+    eta = torch.tensor(0.05 * np.cos(2 * np.pi * xcol / wl.length * 64), device=dev)
+    mesh.update_geometry(eta)
+    x = torch.randn(mesh.n, dtype=torch.float64, device=dev)
+    y = torch.empty_like(x)
+    for _ in range(3):
+        mesh.laplace_apply(x, y)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        mesh.laplace_apply(x, y)
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    P = wl.P
+    flops = wl.Nx * wl.Nz * (P + 1) ** 2 * (8 * (P + 1) + 7)
+    nbytes = 16 * mesh.n + 32 * wl.Nx * (P + 1)
+    peaks = measured_peaks()
+    out = {"workload": wl.name, "n_nodes": mesh.n, "ms_per_apply": ms,
+           "fp64_tflops": flops / ms / 1e9, "fp64_peak": FP64_PEAK_TFLOPS,
+           "fp64_frac": flops / ms / 1e9 / FP64_PEAK_TFLOPS,
+           "hbm_gbs": nbytes / ms / 1e6, "hbm_peak": peaks.get("hbm_gbs"),
+           "note": "two kernels per apply (element columns, then the shared edge columns)"}
+    mesh.close()
+    return out
+
+
+def measured_peaks() -> dict:
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+
+
+# ---------------------------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------------------------
 def run_gpu(args):
@@ -263,14 +332,10 @@ def run_gpu(args):
     mesh.enable_timing(False)
     tm = mesh.timing()
     cnt = mesh.counters()
-    t_max = total_ms
-    if world > 1:
-        tt = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
+    t_max = max_over_ranks(total_ms, dev)
     dof_per_step = 4 * wl.n_unknowns
-    value = world * args.steps * dof_per_step / (t_max / 1e3)
-    steps_per_s = world * args.steps / (t_max / 1e3)
+    value = job_throughput(world, args.steps, dof_per_step, t_max)
+    steps_per_s = job_throughput(world, args.steps, 1, t_max)
 
     # roofline of the dominant kernel: the persistent Krylov kernel, FP64 ALU bound
     solves = max(cnt.solves, 1)
@@ -294,12 +359,8 @@ def run_gpu(args):
     t0 = time.perf_counter()
     for _ in range(args.steps):
         mesh.rk4_step_host(he, hp, wl.dt, 1)
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        tt = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
-    e2e = {"value": world * args.steps * dof_per_step / e2e_s, "unit": UNIT,
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dev)
+    e2e = {"value": job_throughput(world, args.steps, dof_per_step, 1e3 * e2e_s), "unit": UNIT,
            "h2d_bytes_per_step": 2 * 8 * wl.ncol, "d2h_bytes_per_step": 2 * 8 * wl.ncol}
 
     line = {
@@ -323,6 +384,8 @@ def run_gpu(args):
         "gpu_launches": gpu_launches,
         "clocks": clk,
     }
+    if not args.no_apply_roofline:
+        line["apply_long_tank"] = apply_roofline(dev)
     if rank == 0 and not args.no_cpu_baseline:
         try:
             res = oracle_subprocess(args.cpu_stages)
@@ -368,6 +431,7 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--cpu-stages", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-apply-roofline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
