@@ -83,6 +83,9 @@ typedef struct sem_params {
   int max_iter;        /* Laplace solve: Krylov iteration cap (0 → 5000)             */
   int precision;       /* enum sem_precision                                          */
   int precond;         /* enum sem_preconditioner                                     */
+  double relax_left;   /* §2.2 generation zone length at the left end (0: none)           */
+  double relax_right;  /* §2.2 absorption zone length at the right end (0: none)          */
+  double relax_tau;    /* relaxation time τ (0: the RK4 step dt, as the paper chooses)     */
 } sem_params;
 
 typedef struct sem_info {
@@ -173,12 +176,23 @@ int sem_recover_gradient(sem_mesh* m, const double* Phi_d, const double* eta_d,
 
 /* Right-hand side of the semi-discrete free-surface equations (§3.1.1 with
  * the PDE form of eq. FSeqs, over-integrated at order Pf per §3.3):
- * M' ∂tη = ∫(−ηxφ̃x + w̃(1+ηx²))N_i,  M' ∂tφ̃ = ∫(−gη − ½(φ̃x² − w̃²(1+ηx²)))N_i.
- * Runs geometry, the Laplace solve (warm-started from the mesh's previous
- * potential), recovery and the projection.  t is unused (no forcing zones).
+ * M' ∂tη = ∫(−ηxφ̃x + w̃(1+ηx²))N_i,  M' ∂tφ̃ = ∫(−gη − ½(φ̃x² − w̃²(1+ηx²)))N_i,
+ * plus the relaxation source of §2.2 at time t when zones are configured (then
+ * relax_tau must be > 0).  Runs geometry, the Laplace solve (warm-started from the
+ * mesh's previous potential), recovery and the projection.
  * eta_d, phis_d in; deta_d, dphis_d out; device, Ncol each. */
 int sem_zakharov_rhs(sem_mesh* m, const double* eta_d, const double* phis_d, double t,
                      double* deta_d, double* dphis_d, void* stream);
+
+/* Wave input of the generation zone (§2.2): the left zone relaxes (η, φ̃) towards the
+ * linear superposition η_a = Σ a_i cos(ω_i t − k_i x + θ_i), φ̃_a = −Σ (g a_i/ω_i)
+ * sin(ω_i t − k_i x + θ_i); the right zone relaxes towards rest.  The relaxation source
+ * (1 − γ(x))(q_a − q)/τ is added at the surface nodes, with γ a smooth step ξ²(3−2ξ) across
+ * each zone.  Arrays are host, ncomp ≤ 4096 entries each; ncomp = 0 clears the signal.
+ * The copy is synchronous and not ordered with `stream` work: call it while no step of
+ * this mesh is in flight. */
+int sem_set_wave_input(sem_mesh* m, int ncomp, const double* amp_h, const double* omega_h,
+                       const double* k_h, const double* phase_h);
 
 /* Per-element modal filter F = V̂SV̂⁻¹ of §3.4 applied in place to a surface
  * field (no-op if filter_ic < 0).  q_d: device, Ncol. */

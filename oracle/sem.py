@@ -54,6 +54,32 @@ class Params:
     filter_alpha: float = 0.0
     filter_s: float = 0.0
     filter_ic: int = -1     # -1: no filter
+    relax_left: float = 0.0     # length of the generation zone at the left end (0: none)
+    relax_right: float = 0.0    # length of the absorption zone at the right end (0: none)
+    relax_tau: float = 0.0      # relaxation time τ; 0: the RK4 step size (§2.2 takes τ = Δt)
+    wave: tuple | None = None   # (a_i, ω_i, k_i, θ_i) arrays of the generated signal
+
+
+def relaxation_gamma(x, x0: float, x1: float, left: float, right: float):
+    """γ(x) of §2.2: 1 outside the zones, a smooth step ξ²(3−2ξ) from 0 at the outer end of a
+    zone to 1 at its inner end (reading: the paper leaves the shape open)."""
+    x = np.asarray(x, dtype=np.float64)
+    g = np.ones_like(x)
+    if left > 0:
+        xi = np.clip((x - x0) / left, 0.0, 1.0)
+        g = np.where(x < x0 + left, xi * xi * (3 - 2 * xi), g)
+    if right > 0:
+        xi = np.clip((x1 - x) / right, 0.0, 1.0)
+        g = np.where(x > x1 - right, np.minimum(g, xi * xi * (3 - 2 * xi)), g)
+    return g
+
+
+def linear_wave_signal(x, t: float, wave, g: float):
+    """Linear superposition at the free surface (§4.2 linear theory per component):
+    η_a = Σ a cos(ωt − kx + θ),  φ̃_a = −Σ (g a/ω) sin(ωt − kx + θ)."""
+    a, om, k, th = (np.asarray(v, dtype=np.float64) for v in wave)
+    ph = np.outer(np.asarray(x, dtype=np.float64), -k) + (om * t + th)[None, :]
+    return np.cos(ph) @ a, -(np.sin(ph) @ (g * a / om))
 
 
 def sigma_K(d, hx, dxd, sig):
@@ -250,8 +276,23 @@ class Mesh:
         return w[self.surface]
 
     # ---- free-surface right-hand side (§3.1.1, §3.3) ----------------------------------
-    def zakharov_rhs(self, eta: np.ndarray, phis: np.ndarray, return_parts: bool = False):
-        """(∂tη, ∂tφ̃) from the Galerkin form of eq. (FSproblem) with over-integration."""
+    def relaxation(self, eta: np.ndarray, phis: np.ndarray, t: float, tau: float):
+        """Embedded penalty source of §2.2 at the nodes: (1 − γ)(q_a − q)/τ for q = η, φ̃.
+        The left zone relaxes towards the generated signal, the right zone towards rest."""
+        prm = self.params
+        x0, x1 = self.x_edges[0], self.x_edges[-1]
+        gam = relaxation_gamma(self.xcol, x0, x1, prm.relax_left, prm.relax_right)
+        ea = np.zeros(self.ncol)
+        pa = np.zeros(self.ncol)
+        if prm.wave is not None and prm.relax_left > 0:
+            left = self.xcol < x0 + prm.relax_left
+            ea[left], pa[left] = linear_wave_signal(self.xcol[left], t, prm.wave, prm.g)
+        return (1 - gam) * (ea - eta) / tau, (1 - gam) * (pa - phis) / tau
+
+    def zakharov_rhs(self, eta: np.ndarray, phis: np.ndarray, return_parts: bool = False,
+                     t: float = 0.0, tau: float | None = None):
+        """(∂tη, ∂tφ̃) from the Galerkin form of eq. (FSproblem) with over-integration, plus
+        the relaxation source of §2.2 when zones are configured (τ = tau or Params.relax_tau)."""
         prm = self.params
         P = self.P
         Pf = prm.Pf if prm.Pf > 0 else P
@@ -272,6 +313,12 @@ class Mesh:
             np.add.at(rhs_e, c, scale * (Ip.T @ (Mf @ Fe)))
             np.add.at(rhs_p, c, scale * (Ip.T @ (Mf @ Fp)))
         sol = self.surface_mass_solve(np.stack([rhs_e, rhs_p], axis=1))
+        if prm.relax_left > 0 or prm.relax_right > 0:
+            tau_ = prm.relax_tau if tau is None else tau
+            if not tau_ > 0:
+                raise ValueError("relaxation zones need τ > 0")
+            se, sp_ = self.relaxation(eta, phis, t, tau_)
+            sol = sol + np.stack([se, sp_], axis=1)
         if return_parts:
             return sol[:, 0], sol[:, 1], dict(Phi=Phi, w=wt, etax=etax, phisx=phisx,
                                               rhs_eta=rhs_e, rhs_phi=rhs_p)
@@ -291,12 +338,14 @@ class Mesh:
             np.add.at(cnt, c, 1.0)
         return acc / cnt
 
-    def rk4_step(self, eta: np.ndarray, phis: np.ndarray, dt: float):
-        """Classical four-stage RK4 on (η, φ̃), then the filter."""
-        k1e, k1p = self.zakharov_rhs(eta, phis)
-        k2e, k2p = self.zakharov_rhs(eta + 0.5 * dt * k1e, phis + 0.5 * dt * k1p)
-        k3e, k3p = self.zakharov_rhs(eta + 0.5 * dt * k2e, phis + 0.5 * dt * k2p)
-        k4e, k4p = self.zakharov_rhs(eta + dt * k3e, phis + dt * k3p)
+    def rk4_step(self, eta: np.ndarray, phis: np.ndarray, dt: float, t: float = 0.0):
+        """Classical four-stage RK4 on (η, φ̃) from time t, then the filter.  The relaxation
+        time is Params.relax_tau, or dt when that is 0 (§2.2)."""
+        tau = self.params.relax_tau if self.params.relax_tau > 0 else dt
+        k1e, k1p = self.zakharov_rhs(eta, phis, t=t, tau=tau)
+        k2e, k2p = self.zakharov_rhs(eta + 0.5 * dt * k1e, phis + 0.5 * dt * k1p, t=t + 0.5 * dt, tau=tau)
+        k3e, k3p = self.zakharov_rhs(eta + 0.5 * dt * k2e, phis + 0.5 * dt * k2p, t=t + 0.5 * dt, tau=tau)
+        k4e, k4p = self.zakharov_rhs(eta + dt * k3e, phis + dt * k3p, t=t + dt, tau=tau)
         eta_n = eta + dt / 6.0 * (k1e + 2 * k2e + 2 * k3e + k4e)
         phis_n = phis + dt / 6.0 * (k1p + 2 * k2p + 2 * k3p + k4p)
         return self.apply_filter(eta_n), self.apply_filter(phis_n)
@@ -313,6 +362,7 @@ class Mesh:
 
 
 def mesh_for(wl, h_col=None, bar: bool = False) -> Mesh:
+    """Oracle mesh for a workload; bathymetry from ``wl.bathymetry`` unless given."""
     """Build an oracle mesh for a ``sem_workloads.Workload`` (inputs only; no arithmetic shared)."""
     P = wl.P
     r, _ = poly.gll_nodes_weights(P)
@@ -323,7 +373,8 @@ def mesh_for(wl, h_col=None, bar: bool = False) -> Mesh:
     xcol = edges[ex] + 0.5 * (r[a] + 1) * (edges[ex + 1] - edges[ex])
     if h_col is None:
         from sem_workloads import depth_columns
-        h_col = depth_columns(wl, xcol, bar=bar)
+        h_col = depth_columns(wl, xcol, bar=bar or wl.bathymetry == "bar")
     prm = Params(g=wl.g, Pf=wl.Pf, filter_alpha=wl.filter_alpha, filter_s=wl.filter_s,
-                 filter_ic=wl.filter_ic)
+                 filter_ic=wl.filter_ic, relax_left=wl.relax_left, relax_right=wl.relax_right,
+                 relax_tau=wl.relax_tau, wave=wl.wave)
     return Mesh(P, wl.Nx, wl.Nz, edges, wl.periodic, h_col, prm)

@@ -26,7 +26,7 @@ SEM_PRECOND_SEPARABLE, SEM_PRECOND_JACOBI = 0, 1
 
 EXPORTED = ("sem_mesh_create", "sem_mesh_destroy", "sem_mesh_info", "sem_mesh_l2g",
             "sem_update_geometry", "sem_laplace_apply", "sem_laplace_apply_noalloc", "sem_laplace_solve",
-            "sem_recover_gradient", "sem_zakharov_rhs", "sem_apply_filter", "sem_rk4_step",
+            "sem_recover_gradient", "sem_zakharov_rhs", "sem_set_wave_input", "sem_apply_filter", "sem_rk4_step",
             "sem_rk4_step_host", "sem_get_counters", "sem_reset_counters", "sem_enable_timing",
             "sem_get_timing", "sem_launch_count", "sem_last_error")
 
@@ -36,7 +36,9 @@ class sem_params(ctypes.Structure):
                 ("periodic", ctypes.c_int), ("Pf", ctypes.c_int), ("filter_ic", ctypes.c_int),
                 ("filter_alpha", ctypes.c_double), ("filter_s", ctypes.c_double),
                 ("g", ctypes.c_double), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
-                ("precision", ctypes.c_int), ("precond", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("precond", ctypes.c_int),
+                ("relax_left", ctypes.c_double), ("relax_right", ctypes.c_double),
+                ("relax_tau", ctypes.c_double)]
 
 
 class sem_info(ctypes.Structure):
@@ -84,6 +86,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sem_recover_gradient.argtypes = [vp, dp, dp, dp, dp, dp, dp, vp]
     lib.sem_zakharov_rhs.argtypes = [vp, dp, dp, ctypes.c_double, dp, dp, vp]
     lib.sem_apply_filter.argtypes = [vp, dp, vp]
+    lib.sem_set_wave_input.argtypes = [vp, ip, dp, dp, dp, dp]
     lib.sem_rk4_step.argtypes = [vp, dp, dp, ctypes.POINTER(ctypes.c_double), ctypes.c_double, ip, vp]
     lib.sem_rk4_step_host.argtypes = [vp, dp, dp, ctypes.POINTER(ctypes.c_double), ctypes.c_double, ip, vp]
     lib.sem_get_counters.argtypes = [vp, ctypes.POINTER(sem_counters), vp]
@@ -141,14 +144,16 @@ class Mesh:
     def __init__(self, P: int, Nx: int, Nz: int, x_edges, h, periodic: bool = True, Pf: int = 0,
                  filter_alpha: float = 0.0, filter_s: float = 0.0, filter_ic: int = -1,
                  g: float = 9.81, tol: float = 1e-13, max_iter: int = 5000, precision: str = "fp64",
-                 precond: str = "separable"):
+                 precond: str = "separable", relax_left: float = 0.0, relax_right: float = 0.0,
+                 relax_tau: float = 0.0, wave=None):
         lib = load_library()
         if precision not in ("fp64", "mixed") or precond not in ("separable", "jacobi"):
             raise ValueError("precision must be fp64|mixed and precond separable|jacobi")
         prm = sem_params(P=P, Nx=Nx, Nz=Nz, periodic=int(bool(periodic)), Pf=Pf, filter_ic=filter_ic,
                          filter_alpha=filter_alpha, filter_s=filter_s, g=g, tol=tol, max_iter=max_iter,
                          precision=SEM_PREC_MIXED if precision == "mixed" else SEM_PREC_FP64,
-                         precond=SEM_PRECOND_JACOBI if precond == "jacobi" else SEM_PRECOND_SEPARABLE)
+                         precond=SEM_PRECOND_JACOBI if precond == "jacobi" else SEM_PRECOND_SEPARABLE,
+                         relax_left=relax_left, relax_right=relax_right, relax_tau=relax_tau)
         xe = np.ascontiguousarray(x_edges, dtype=np.float64)
         hh = np.ascontiguousarray(h, dtype=np.float64)
         handle = ctypes.c_void_p()
@@ -160,6 +165,8 @@ class Mesh:
         self.ncol, self.nrow = self.info.ncol, self.info.nrow
         self.n = int(self.info.n_nodes)
         self.n_unknowns = int(self.info.n_unknowns)
+        if wave is not None:
+            self.set_wave_input(*wave)
 
     @classmethod
     def from_workload(cls, wl, h=None, precision: str = "fp64", tol: float = 1e-13, max_iter: int = 5000,
@@ -169,7 +176,9 @@ class Mesh:
             h = np.full(wl.ncol, wl.depth)
         return cls(wl.P, wl.Nx, wl.Nz, edges, h, periodic=wl.periodic, Pf=wl.Pf,
                    filter_alpha=wl.filter_alpha, filter_s=wl.filter_s, filter_ic=wl.filter_ic,
-                   g=wl.g, tol=tol, max_iter=max_iter, precision=precision, precond=precond)
+                   g=wl.g, tol=tol, max_iter=max_iter, precision=precision, precond=precond,
+                   relax_left=wl.relax_left, relax_right=wl.relax_right, relax_tau=wl.relax_tau,
+                   wave=wl.wave)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -212,6 +221,11 @@ class Mesh:
     def zakharov_rhs(self, eta, phis, deta, dphis, t: float = 0.0):
         _check(load_library().sem_zakharov_rhs(self._h, _ptr(eta), _ptr(phis), ctypes.c_double(t),
                                                _ptr(deta), _ptr(dphis), _stream()))
+
+    def set_wave_input(self, amp, omega, k, phase):
+        arrs = [np.ascontiguousarray(v, dtype=np.float64) for v in (amp, omega, k, phase)]
+        n = len(arrs[0])
+        _check(load_library().sem_set_wave_input(self._h, n, *(a.ctypes.data_as(ctypes.c_void_p) for a in arrs)))
 
     def apply_filter(self, q):
         _check(load_library().sem_apply_filter(self._h, _ptr(q), _stream()))

@@ -1,6 +1,7 @@
 // C ABI of the library (declared in include/sem.h): mesh set-up, host-side tables and
 // the orchestration of the kernels for one Laplace solve, the recovery, the Zakharov
 // right-hand side and RK4 (§2–§3 of arXiv 1512.02548).
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdio>
@@ -24,6 +25,7 @@ void count_launch(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 namespace {
 
+constexpr int kMaxWaveComp = 4096;
 thread_local std::string t_err;
 
 int fail(int code, const std::string& msg) {
@@ -151,7 +153,10 @@ int do_geometry(sem_mesh* m, const double* eta, cudaStream_t s) {
   return SEM_OK;
 }
 
-int do_rhs(sem_mesh* m, const double* eta, const double* phis, double* de, double* dp, cudaStream_t s) {
+bool has_zones(const sem_mesh* m) { return m->p.relax_left > 0.0 || m->p.relax_right > 0.0; }
+
+int do_rhs(sem_mesh* m, const double* eta, const double* phis, double time, double tau, double* de,
+           double* dp, cudaStream_t s) {
   const int Q = m->p.P + 1;
   int rc0 = do_geometry(m, eta, s);
   if (rc0) return rc0;
@@ -162,17 +167,21 @@ int do_rhs(sem_mesh* m, const double* eta, const double* phis, double* de, doubl
   CUDA_TRY(launch_mass1d(m->st, m->R, 2, m->etax, m->phisx, m->scr, s));
   CUDA_TRY(launch_zakharov(m->st, eta, m->etax, m->phisx, m->wt, m->R, s));
   CUDA_TRY(launch_mass1d(m->st, m->R, 2, de, dp, m->scr, s));
+  if (has_zones(m)) CUDA_TRY(launch_relax(m->st, eta, phis, time, 1.0 / tau, de, dp, s));
   (void)Q;
   return SEM_OK;
 }
 
-int do_rk4(sem_mesh* m, double* eta, double* phis, double dt, int nsteps, cudaStream_t s) {
+int do_rk4(sem_mesh* m, double* eta, double* phis, double t0, double dt, int nsteps, cudaStream_t s) {
   const int n = m->ncol;
+  const double tau = m->p.relax_tau > 0.0 ? m->p.relax_tau : dt;
   for (int step = 0; step < nsteps; ++step) {
+    const double ts = t0 + step * dt;
     for (int stage = 1; stage <= 4; ++stage) {
       const double* ei = stage == 1 ? eta : m->se;
       const double* pi = stage == 1 ? phis : m->sp;
-      int rc = do_rhs(m, ei, pi, m->ke, m->kp, s);
+      const double tstage = ts + (stage == 1 ? 0.0 : (stage == 4 ? dt : 0.5 * dt));
+      int rc = do_rhs(m, ei, pi, tstage, tau, m->ke, m->kp, s);
       if (rc) return rc;
       CUDA_TRY(launch_rk4_stage(stage, n, dt, eta, phis, m->ke, m->kp, m->ae, m->ap, m->se, m->sp, s));
     }
@@ -205,6 +214,7 @@ int sem_mesh_create(const sem_params* pin, const double* x_edges_h, const double
   *out = nullptr;
   if (!pin || !x_edges_h || !h_h) return fail(SEM_ERR_INVALID_ARG, "NULL argument");
   sem_params p = *pin;
+  const int Nx_in = p.Nx > 0 ? p.Nx : 0;
   if (p.P < 2 || p.P > SEM_MAX_P) return fail(SEM_ERR_INVALID_ARG, "P must be in [2, 12]");
   if (p.Nz < 1 || p.Nz > kMaxNz) return fail(SEM_ERR_INVALID_ARG, "Nz must be in [1, 16]");
   if (p.periodic ? p.Nx < 3 : p.Nx < 1) return fail(SEM_ERR_INVALID_ARG, "Nx too small (periodic needs >= 3)");
@@ -214,6 +224,9 @@ int sem_mesh_create(const sem_params* pin, const double* x_edges_h, const double
     return fail(SEM_ERR_INVALID_ARG, "unknown precision");
   if (p.precond != SEM_PRECOND_SEPARABLE && p.precond != SEM_PRECOND_JACOBI)
     return fail(SEM_ERR_INVALID_ARG, "unknown preconditioner");
+  if (p.relax_left < 0.0 || p.relax_right < 0.0 || p.relax_tau < 0.0 ||
+      p.relax_left + p.relax_right > x_edges_h[Nx_in] - x_edges_h[0])
+    return fail(SEM_ERR_INVALID_ARG, "relaxation zones must be non-negative and fit in the tank");
   if (p.tol <= 0.0) p.tol = 1e-13;
   if (p.max_iter <= 0) p.max_iter = 5000;
   const int P = p.P, Q = P + 1, Nx = p.Nx, Nz = p.Nz;
@@ -404,6 +417,7 @@ int sem_mesh_create(const sem_params* pin, const double* x_edges_h, const double
                o_gR32 = cv.take<float>(nEl), o_zb64 = cv.take<double>(nIf), o_zb32 = cv.take<float>(nIf),
                o_rh64 = cv.take<double>((size_t)ncol * nr), o_rh32 = cv.take<float>((size_t)ncol * nr),
                o_pscr = cv.take<double>(nIf);
+  const size_t o_xcol = cv.take<double>(ncol), o_wave = cv.take<double>(4 * kMaxWaveComp);
   const size_t o_wt = cv.take<double>(ncol), o_etax = cv.take<double>(ncol), o_phisx = cv.take<double>(ncol),
                o_R = cv.take<double>((size_t)2 * Nx * Q), o_scr = cv.take<double>((size_t)4 * Nx + 2 * (N + 1)),
                o_ke = cv.take<double>(ncol), o_kp = cv.take<double>(ncol), o_ae = cv.take<double>(ncol),
@@ -436,6 +450,14 @@ int sem_mesh_create(const sem_params* pin, const double* x_edges_h, const double
   up(o_tD, L.D); up(o_tMD, MD); up(o_tB, B); up(o_tI, I); up(o_tF, F); up(o_tcw, cw);
   up(o_tAii, Aii); up(o_tZ, Z); up(o_tse, se); up(o_te, th_e); up(o_tm, th_m); up(o_tcp, th_cp); up(o_tz, th_z);
   up(o_S64, Sg); up(o_lam, lam);
+  {
+    std::vector<double> xc(ncol);
+    for (int c = 0; c < ncol; ++c) {
+      const int e = std::min(c / P, Nx - 1), a = c - e * P;
+      xc[c] = x_edges_h[e] + 0.5 * (L.r[a] + 1.0) * dxe[e];
+    }
+    up(o_xcol, xc);
+  }
   if (code == SEM_OK) {
     std::vector<float> S32(Sg.begin(), Sg.end());
     cudaError_t e = cudaMemcpy(m->pool + o_S32, S32.data(), S32.size() * sizeof(float), cudaMemcpyHostToDevice);
@@ -488,6 +510,8 @@ int sem_mesh_create(const sem_params* pin, const double* x_edges_h, const double
   t.Aii = D_(o_tAii); t.Z = D_(o_tZ); t.se = D_(o_tse); t.dsl = g.dsl; t.h = g.h;
   t.th_e = D_(o_te); t.th_m = D_(o_tm); t.th_cp = D_(o_tcp); t.th_z = D_(o_tz);
   t.th_vlast = th_vlast; t.th_fac = th_fac; t.nif = N; t.filter_on = (p.filter_ic >= 0 && p.filter_ic < P) ? 1 : 0;
+  t.xcol = D_(o_xcol); t.x0 = x_edges_h[0]; t.x1 = x_edges_h[Nx];
+  t.relax_left = p.relax_left; t.relax_right = p.relax_right; t.ncomp = 0; t.wave = D_(o_wave);
   *out = m;
   return SEM_OK;
 }
@@ -576,10 +600,26 @@ int sem_recover_gradient(sem_mesh* m, const double* Phi_d, const double* eta_d, 
 
 int sem_zakharov_rhs(sem_mesh* m, const double* eta_d, const double* phis_d, double t, double* deta_d,
                      double* dphis_d, void* stream) {
-  (void)t;
   if (!m || !eta_d || !phis_d || !deta_d || !dphis_d) return fail(SEM_ERR_INVALID_ARG, "NULL argument");
+  if (has_zones(m) && !(m->p.relax_tau > 0.0))
+    return fail(SEM_ERR_INVALID_ARG, "relaxation zones need relax_tau > 0 outside sem_rk4_step");
   DeviceGuard dg(m->device);
-  return do_rhs(m, eta_d, phis_d, deta_d, dphis_d, (cudaStream_t)stream);
+  return do_rhs(m, eta_d, phis_d, t, m->p.relax_tau, deta_d, dphis_d, (cudaStream_t)stream);
+}
+
+int sem_set_wave_input(sem_mesh* m, int ncomp, const double* amp_h, const double* omega_h,
+                       const double* k_h, const double* phase_h) {
+  if (!m || ncomp < 0 || ncomp > kMaxWaveComp) return fail(SEM_ERR_INVALID_ARG, "ncomp must be in [0, 4096]");
+  if (ncomp > 0 && (!amp_h || !omega_h || !k_h || !phase_h)) return fail(SEM_ERR_INVALID_ARG, "NULL argument");
+  for (int i = 0; i < ncomp; ++i)
+    if (!(omega_h[i] > 0.0)) return fail(SEM_ERR_INVALID_ARG, "wave frequencies must be positive");
+  DeviceGuard dg(m->device);
+  double* w = const_cast<double*>(m->st.wave);
+  const double* src[4] = {amp_h, omega_h, k_h, phase_h};
+  for (int q = 0; q < 4 && ncomp > 0; ++q)
+    CUDA_TRY(cudaMemcpy(w + (size_t)q * ncomp, src[q], sizeof(double) * ncomp, cudaMemcpyHostToDevice));
+  m->st.ncomp = ncomp;
+  return SEM_OK;
 }
 
 int sem_apply_filter(sem_mesh* m, double* q_d, void* stream) {
@@ -593,7 +633,7 @@ int sem_rk4_step(sem_mesh* m, double* eta_d, double* phis_d, double* t, double d
   if (!m || !eta_d || !phis_d || nsteps < 0 || !(dt > 0.0)) return fail(SEM_ERR_INVALID_ARG, "bad argument");
   DeviceGuard dg(m->device);
   cudaStream_t s = (cudaStream_t)stream;
-  int rc = do_rk4(m, eta_d, phis_d, dt, nsteps, s);
+  int rc = do_rk4(m, eta_d, phis_d, t ? *t : 0.0, dt, nsteps, s);
   if (rc) return rc;
   rc = read_status(m, s);
   if (t) *t += nsteps * dt;
@@ -608,7 +648,7 @@ int sem_rk4_step_host(sem_mesh* m, double* eta_h, double* phis_h, double* t, dou
   const size_t bytes = sizeof(double) * m->ncol;
   CUDA_TRY(cudaMemcpyAsync(m->eta_dev, eta_h, bytes, cudaMemcpyHostToDevice, s));
   CUDA_TRY(cudaMemcpyAsync(m->phis_dev, phis_h, bytes, cudaMemcpyHostToDevice, s));
-  int rc = do_rk4(m, m->eta_dev, m->phis_dev, dt, nsteps, s);
+  int rc = do_rk4(m, m->eta_dev, m->phis_dev, t ? *t : 0.0, dt, nsteps, s);
   if (rc) return rc;
   CUDA_TRY(cudaMemcpyAsync(eta_h, m->eta_dev, bytes, cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaMemcpyAsync(phis_h, m->phis_dev, bytes, cudaMemcpyDeviceToHost, s));

@@ -188,6 +188,43 @@ __global__ void k_filter(SurfTables t, double* __restrict__ q0, double* __restri
   }
 }
 
+// Embedded penalty forcing of §2.2 at the surface nodes: q̇ += (1 − γ(x))(q_a(x,t) − q)/τ with
+// γ = ξ²(3 − 2ξ) across each zone (1 outside); q_a is the linear superposition of the wave
+// input in the left zone, rest in the right zone.
+__global__ void k_relax(SurfTables t, const double* __restrict__ eta, const double* __restrict__ phis,
+                        double time, double inv_tau, double* __restrict__ de, double* __restrict__ dp) {
+  const int col = blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= t.ncol) return;
+  const double x = t.xcol[col];
+  double gam = 1.0;
+  const bool left = t.relax_left > 0.0 && x < t.x0 + t.relax_left;
+  if (left) {
+    const double xi = fmin(fmax((x - t.x0) / t.relax_left, 0.0), 1.0);
+    gam = xi * xi * (3.0 - 2.0 * xi);
+  }
+  if (t.relax_right > 0.0 && x > t.x1 - t.relax_right) {
+    const double xi = fmin(fmax((t.x1 - x) / t.relax_right, 0.0), 1.0);
+    gam = fmin(gam, xi * xi * (3.0 - 2.0 * xi));
+  }
+  if (gam >= 1.0) return;
+  double ea = 0.0, pa = 0.0;
+  if (left) {
+    const double* a = t.wave;
+    const double* om = a + t.ncomp;
+    const double* k = om + t.ncomp;
+    const double* th = k + t.ncomp;
+    for (int i = 0; i < t.ncomp; ++i) {
+      double sn, cs;
+      sincos(om[i] * time - k[i] * x + th[i], &sn, &cs);
+      ea = fma(a[i], cs, ea);
+      pa = fma(-t.g * a[i] / om[i], sn, pa);
+    }
+  }
+  const double c = (1.0 - gam) * inv_tau;
+  de[col] = fma(c, ea - eta[col], de[col]);
+  dp[col] = fma(c, pa - phis[col], dp[col]);
+}
+
 // Classical RK4 stage bookkeeping on (η, φ̃) with k = right-hand side of this stage:
 //   stage 1: acc = k,   st = q + dt/2 k
 //   stage 2: acc += 2k, st = q + dt/2 k
@@ -245,6 +282,14 @@ cudaError_t launch_zakharov(const SurfTables& t, const double* eta, const double
 cudaError_t launch_filter(const SurfTables& t, double* q0, double* q1, cudaStream_t s) {
   if (!t.filter_on) return cudaSuccess;
   k_filter<<<(t.Nx + kZakWarps - 1) / kZakWarps, 32 * kZakWarps, 0, s>>>(t, q0, q1);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_relax(const SurfTables& t, const double* eta, const double* phis, double time,
+                         double inv_tau, double* de, double* dp, cudaStream_t s) {
+  if (!(t.relax_left > 0.0) && !(t.relax_right > 0.0)) return cudaSuccess;
+  k_relax<<<(t.ncol + 127) / 128, 128, 0, s>>>(t, eta, phis, time, inv_tau, de, dp);
   count_launch();
   return cudaGetLastError();
 }

@@ -130,6 +130,12 @@ struct SurfTables {
   double th_fac;          // periodic: 1/(1 + vᵀ T'⁻¹u)
   int nif;                // interface unknowns N
   int filter_on;
+  // relaxation zones (§2.2)
+  const double* xcol;     // [ncol] column positions
+  double x0, x1;          // tank ends
+  double relax_left, relax_right;
+  int ncomp;              // components of the generated signal
+  const double* wave;     // [4][ncomp]: a, ω, k, θ
 };
 
 // ---- launchers (kernels_laplace.cu) ----
@@ -156,6 +162,9 @@ cudaError_t launch_mass1d(const SurfTables& t, const double* R, int nrhs, double
 cudaError_t launch_zakharov(const SurfTables& t, const double* eta, const double* etax,
                             const double* phisx, const double* w, double* R, cudaStream_t s);
 cudaError_t launch_filter(const SurfTables& t, double* q0, double* q1, cudaStream_t s);
+// Adds the relaxation source (1 − γ)(q_a − q)/τ to (de, dp) in the zones.
+cudaError_t launch_relax(const SurfTables& t, const double* eta, const double* phis, double time,
+                         double inv_tau, double* de, double* dp, cudaStream_t s);
 // RK4 stage update on (η, φ̃): see kernels_surface.cu for the stage semantics.
 cudaError_t launch_rk4_stage(int stage, int n, double dt, double* eta, double* phis,
                              const double* keta, const double* kphis, double* acc_eta,

@@ -55,7 +55,12 @@ class Workload:
     nsteps: int = 0
     wave_height: float = 0.0
     wavenumber: float = 1.0
-    init: str = "progressive"   # "standing": η=(H/2)cos kx, φ̃=0
+    init: str = "progressive"   # "standing": η=(H/2)cos kx, φ̃=0; "rest": η=φ̃=0
+    bathymetry: str = "flat"    # "flat", "bar" (raised cosine) or "shoal" (trapezoidal bar)
+    relax_left: float = 0.0     # generation zone length at the left end
+    relax_right: float = 0.0    # absorption zone length at the right end
+    relax_tau: float = 0.0      # 0: τ = dt
+    wave: tuple | None = None   # generated signal components (a, ω, k, θ)
     extra: dict = field(default_factory=dict)
 
     @property
@@ -134,6 +139,30 @@ def small_case(P: int = 5, Nx: int = 6, Nz: int = 2, periodic: bool = True,
                     dt=T / 100, nsteps=2, wave_height=H_over_L * 2 * math.pi, wavenumber=k)
 
 
+def _smooth_ramp(s: np.ndarray, delta: float) -> np.ndarray:
+    """clamp(s, 0, 1) with C¹ quadratic blends of half-width delta at both corners."""
+    out = np.clip(s, 0.0, 1.0)
+    lo = np.abs(s) < delta
+    out = np.where(lo, (s + delta) ** 2 / (4 * delta), out)
+    hi = np.abs(s - 1.0) < delta
+    out = np.where(hi, 1.0 - (1.0 + delta - s) ** 2 / (4 * delta), out)
+    return out
+
+
+def shoal_depth(x: np.ndarray, length: float, depth: float = 1.0, crest: float = 0.25,
+                up_slope: float = 1 / 20, down_slope: float = 1 / 10, blend: float = 0.5) -> np.ndarray:
+    """Trapezoidal bar in the middle third: rises from `depth` to `crest` at `up_slope`, stays
+    at the crest, falls back at `down_slope`; corners smoothed over `blend` metres (C¹)."""
+    x = np.asarray(x, dtype=np.float64)
+    rise = depth - crest
+    xa = length / 3.0
+    run_up, run_dn = rise / up_slope, rise / down_slope
+    xb = 2.0 * length / 3.0 - run_dn
+    up = _smooth_ramp((x - xa) / run_up, 0.5 * blend / run_up)
+    dn = _smooth_ramp((x - xb) / run_dn, 0.5 * blend / run_dn)
+    return depth - rise * (up - dn)
+
+
 def depth_columns(wl: Workload, xcol: np.ndarray, bar: bool = False) -> np.ndarray:
     """Still-water depth at each column: constant, or a smooth submerged bar.
 
@@ -142,6 +171,8 @@ def depth_columns(wl: Workload, xcol: np.ndarray, bar: bool = False) -> np.ndarr
     profile, so h and h_x are smooth.
     """
     h = np.full_like(xcol, wl.depth, dtype=np.float64)
+    if wl.bathymetry == "shoal":
+        return shoal_depth(xcol, wl.length, wl.depth)
     if bar:
         L = wl.length
         x0, x1 = L / 3, 2 * L / 3
@@ -164,6 +195,8 @@ def initial_state(wl: Workload, xcol: np.ndarray, h: np.ndarray | None = None):
     if wl.init == "standing":
         eta = 0.5 * H * np.cos(k * xcol)
         return eta, np.zeros_like(eta)
+    if wl.init == "rest":
+        return np.zeros_like(xcol, dtype=np.float64), np.zeros_like(xcol, dtype=np.float64)
     eta = 0.5 * H * np.cos(k * xcol) + (k * H * H / 8.0) * np.cos(2 * k * xcol)
     om = linear_omega(k, wl.depth, wl.g)
     phis = (wl.g * H / (2 * om)) * np.cosh(k * (eta + h)) / np.cosh(k * wl.depth) * np.sin(k * xcol)
@@ -206,6 +239,58 @@ def c3_instances(count: int = 512, seed: int = 0) -> list[Workload]:
                             filter_alpha=36.0, filter_s=12.0, filter_ic=P - 1,
                             dt=T / 200, nsteps=1, wave_height=HL * 2 * math.pi / k, wavenumber=k))
     return out
+
+
+def wavenumber(omega: float, h: float, g: float = G_EARTH) -> float:
+    """k with ω² = g k tanh(kh), by Newton's method."""
+    k = omega * omega / g / math.sqrt(math.tanh(omega * omega * h / g))
+    for _ in range(60):
+        th = math.tanh(k * h)
+        f = g * k * th - omega * omega
+        df = g * th + g * k * h * (1 - th * th)
+        dk = f / df
+        k -= dk
+        if abs(dk) < 1e-15 * k:
+            break
+    return k
+
+
+def jonswap_components(omega_p: float, Hs: float, n: int = 256, lo: float = 0.6, hi: float = 3.0,
+                       gamma: float = 3.3, sigma_a: float = 0.07, sigma_b: float = 0.09,
+                       depth: float = 1.0, seed: int = 0, g: float = G_EARTH):
+    """Components (a_i, ω_i, k_i, θ_i) of a JONSWAP sea (Hasselmann et al. 1973 shape) on a
+    uniform ω grid in [lo·ω_p, hi·ω_p]; amplitudes √(2SΔω) rescaled so that 4√m0 = Hs, phases
+    uniform in [0, 2π) from splitmix64(seed), wavenumbers from the linear dispersion relation."""
+    dw = (hi - lo) * omega_p / n
+    om = lo * omega_p + (np.arange(n) + 0.5) * dw
+    sig = np.where(om <= omega_p, sigma_a, sigma_b)
+    S = om ** -5 * np.exp(-1.25 * (omega_p / om) ** 4) * gamma ** np.exp(-((om - omega_p) ** 2) / (2 * sig ** 2 * omega_p ** 2))
+    a = np.sqrt(2 * S * dw)
+    m0 = 0.5 * np.sum(a * a)
+    a *= Hs / (4 * math.sqrt(m0))
+    gen = splitmix64(seed)
+    th = np.array([2 * math.pi * _uniform(gen) for _ in range(n)])
+    k = np.array([wavenumber(w, depth, g) for w in om])
+    return a, om, k, th
+
+
+def c4_shoal(Nx: int = 2048, Nz: int = 2, P: int = 6, n_comp: int = 256, nsteps: int = 5000) -> Workload:
+    """Irregular waves over a synthetic shoal: tank of 50 peak wavelengths (k_p h = 1.5),
+    walls, trapezoidal bar to h = 0.25 in the middle third, JONSWAP (γ = 3.3, Hs k_p/2 = 0.05)
+    generated in a 2L_p zone on the left and absorbed in a 2L_p zone on the right; dt from a
+    Courant number 0.5 on the element length."""
+    h, kp = 1.0, 1.5
+    om_p = linear_omega(kp, h)
+    Lp = 2 * math.pi / kp
+    L = 50 * Lp
+    Hs = 2 * 0.05 / kp
+    cp = om_p / kp
+    dx_e = L / Nx
+    wave = jonswap_components(om_p, Hs, n=n_comp, depth=h)
+    return Workload(name=f"C4 JONSWAP over shoal {Nx}x{Nz} P={P}", P=P, Nx=Nx, Nz=Nz, length=L,
+                    periodic=False, depth=h, Pf=(3 * P + 1) // 2, filter_alpha=36.0, filter_s=12.0,
+                    filter_ic=P - 1, dt=0.5 * dx_e / cp, nsteps=nsteps, wave_height=Hs, wavenumber=kp,
+                    init="rest", bathymetry="shoal", relax_left=2 * Lp, relax_right=2 * Lp, wave=wave)
 
 
 def random_field(n: int, seed: int) -> np.ndarray:

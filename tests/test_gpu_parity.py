@@ -301,3 +301,53 @@ def test_counters_and_launch_count():
     c = gm.counters()
     assert c.solves == 4 and c.iterations > 0 and c.max_rel_residual <= 1e-13
     assert sem.launch_count() - n0 >= 4 * 7
+
+
+def _zone_pair(precision="fp64"):
+    from sem_workloads import Workload
+    wave = (np.array([0.02, 0.01]), np.array([2.7, 3.4]), np.array([0.77, 1.19]), np.array([0.1, 2.0]))
+    wl = Workload(name="zones", P=5, Nx=10, Nz=2, length=4 * math.pi, periodic=False, depth=1.0, Pf=8,
+                  filter_alpha=36.0, filter_s=12.0, filter_ic=4, dt=0.04, init="rest", bathymetry="bar",
+                  relax_left=2.5, relax_right=3.0, relax_tau=0.0, wave=wave)
+    om = osem.mesh_for(wl)
+    gm = sem.Mesh.from_workload(wl, h=om.h, precision=precision, tol=1e-13 if precision == "fp64" else 1e-12)
+    return wl, om, gm
+
+
+def test_relaxation_zones_rk4_steps():
+    wl, om, gm = _zone_pair()
+    x = om.xcol
+    e0 = 0.01 * np.cos(0.8 * x) + 0.005
+    p0 = 0.05 * np.sin(0.8 * x)
+    eta, phis = T(e0), T(p0)
+    t = gm.rk4_step(eta, phis, wl.dt, 2, t=0.3)
+    e, p = e0, p0
+    for s in range(2):
+        e, p = om.rk4_step(e, p, wl.dt, t=0.3 + s * wl.dt)
+    assert t == pytest.approx(0.3 + 2 * wl.dt)
+    assert rel(eta, e) < TOL_FP64 and rel(phis, p) < TOL_FP64
+
+
+def test_zakharov_rhs_with_zones_needs_tau():
+    wl, om, gm = _zone_pair()
+    de = torch.empty(om.ncol, dtype=torch.float64, device=DEV)
+    with pytest.raises(sem.SemError):
+        gm.zakharov_rhs(T(np.zeros(om.ncol)), T(np.zeros(om.ncol)), de, torch.empty_like(de), t=0.5)
+
+
+@pytest.mark.slow
+def test_c4_shoal_full_size_two_steps():
+    from sem_workloads import c4_shoal
+    wl = c4_shoal()
+    om = osem.mesh_for(wl)
+    for precision, tol in (("fp64", TOL_FP64), ("mixed", TOL_MIXED)):
+        gm = sem.Mesh.from_workload(wl, h=om.h, precision=precision, tol=1e-13 if precision == "fp64" else 1e-12)
+        e0, p0 = np.zeros(om.ncol), np.zeros(om.ncol)
+        eta, phis = T(e0), T(p0)
+        gm.rk4_step(eta, phis, wl.dt, 2, t=1.0)
+        if precision == "fp64":
+            e, p = e0, p0
+            for s in range(2):
+                e, p = om.rk4_step(e, p, wl.dt, t=1.0 + s * wl.dt)
+        assert np.abs(e).max() > 1e-5               # the zone is generating waves
+        assert rel(eta, e) < tol and rel(phis, p) < tol

@@ -23,7 +23,7 @@ def test_rk4_equals_taylor_polynomial_on_linear_rhs():
     n = m.ncol
     rng = np.random.default_rng(7)
     A = rng.standard_normal((2 * n, 2 * n)) * 0.3
-    m.zakharov_rhs = lambda e, p: tuple(np.split(A @ np.r_[e, p], 2))
+    m.zakharov_rhs = lambda e, p, **kw: tuple(np.split(A @ np.r_[e, p], 2))
     q = rng.standard_normal(2 * n)
     dt = 0.11
     e1, p1 = m.rk4_step(q[:n], q[n:], dt)
