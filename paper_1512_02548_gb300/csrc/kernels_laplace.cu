@@ -848,8 +848,11 @@ __global__ void __launch_bounds__(kThreads) k_pcg(DevGeom g, PcgArgs A) {
 // Set-up of the separable preconditioner for the current geometry.
 // ------------------------------------------------------------------------------------
 // Block per element, one thread per mode: the mode-independent x-stiffness Kx = (2/Δx) Dᵀ
-// diag(w d) D is formed once in shared memory; each mode adds λ_k (Δx/2) diag(w/d), inverts
-// the interior block, and writes Z = E_bi E_ii⁻¹ and the 2×2 Schur block.
+// diag(w d) D is formed once in shared memory (FP64); each mode adds λ_k (Δx/2) diag(w/d) and
+// inverts the interior block in FP32 (a sequential FP64 Gauss–Jordan costs ~64 cycles per
+// instruction on this part).  The inverse is symmetrised, so the condensed solve is the exact
+// inverse of a symmetric operator within FP32 of E; Z = E_bi Ã_ii and the 2×2 Schur block are
+// then formed in FP64 from that same Ã_ii, which keeps the FP64 preconditioner symmetric.
 constexpr int kPrecModesPerBlock = 32;
 
 template <int P>
@@ -874,34 +877,49 @@ __global__ void __launch_bounds__(kPrecModesPerBlock) k_prec_elem(DevGeom g, Pre
   const int k = blockIdx.y * blockDim.x + threadIdx.x;
   if (k >= ps.nr) return;
   const double lam = ps.lam[k];
-  // invert the interior block (SPD) by Gauss–Jordan without pivoting
-  double Ai[Pm][Pm], Bm[Pm][Pm];
+  float Ai[Pm][Pm], Bm[Pm][Pm];
 #pragma unroll
   for (int i = 0; i < Pm; ++i)
 #pragma unroll
     for (int j = 0; j < Pm; ++j) {
-      Bm[i][j] = Kx[(1 + i) * Q + 1 + j] + (i == j ? lam * mw[1 + i] : 0.0);
-      Ai[i][j] = (i == j) ? 1.0 : 0.0;
+      Bm[i][j] = (float)(Kx[(1 + i) * Q + 1 + j] + (i == j ? lam * mw[1 + i] : 0.0));
+      Ai[i][j] = (i == j) ? 1.f : 0.f;
     }
 #pragma unroll
   for (int c = 0; c < Pm; ++c) {
-    const double inv = 1.0 / Bm[c][c];
+    const float inv = 1.f / Bm[c][c];
 #pragma unroll
     for (int j = 0; j < Pm; ++j) { Bm[c][j] *= inv; Ai[c][j] *= inv; }
 #pragma unroll
     for (int r = 0; r < Pm; ++r) {
       if (r == c) continue;
-      const double f = Bm[r][c];
+      const float f = Bm[r][c];
 #pragma unroll
-      for (int j = 0; j < Pm; ++j) { Bm[r][j] -= f * Bm[c][j]; Ai[r][j] -= f * Ai[c][j]; }
+      for (int j = 0; j < Pm; ++j) { Bm[r][j] = fmaf(-f, Bm[c][j], Bm[r][j]); Ai[r][j] = fmaf(-f, Ai[c][j], Ai[r][j]); }
     }
   }
+  const size_t base = (size_t)k * g.Nx + ex;
+  double* A64 = ps.Aii64 + base * Pm * Pm;
+  float* A32 = ps.Aii32 + base * Pm * Pm;
+#pragma unroll
+  for (int i = 0; i < Pm; ++i)
+#pragma unroll
+    for (int j = 0; j < Pm; ++j) {
+      const float v = 0.5f * (Ai[i][j] + Ai[j][i]);
+      A32[i * Pm + j] = v;
+      A64[i * Pm + j] = (double)v;
+    }
+  // Z and the Schur block in FP64 from the symmetrised inverse (read back: the same values)
   double Z0[Pm], Z1[Pm];
 #pragma unroll
   for (int i = 0; i < Pm; ++i) {
     double a0 = 0.0, a1 = 0.0;
 #pragma unroll
-    for (int m = 0; m < Pm; ++m) { a0 = fma(Kx[1 + m], Ai[m][i], a0); a1 = fma(Kx[P * Q + 1 + m], Ai[m][i], a1); }
+    for (int m = 0; m < Pm; ++m) {
+      const double am = (double)(0.5f * (Ai[m][i] + Ai[i][m]));
+      a0 = fma(Kx[1 + m], am, a0);
+      a1 = fma(Kx[P * Q + 1 + m], am, a1);
+    }
     Z0[i] = a0; Z1[i] = a1;
   }
   double S00 = Kx[0] + lam * mw[0], S01 = Kx[P], S11 = Kx[P * Q + P] + lam * mw[P];
@@ -911,13 +929,6 @@ __global__ void __launch_bounds__(kPrecModesPerBlock) k_prec_elem(DevGeom g, Pre
     S01 -= Z0[i] * Kx[(1 + i) * Q + P];
     S11 -= Z1[i] * Kx[(1 + i) * Q + P];
   }
-  const size_t base = (size_t)k * g.Nx + ex;
-  double* A64 = ps.Aii64 + base * Pm * Pm;
-  float* A32 = ps.Aii32 + base * Pm * Pm;
-#pragma unroll
-  for (int i = 0; i < Pm; ++i)
-#pragma unroll
-    for (int j = 0; j < Pm; ++j) { A64[i * Pm + j] = Ai[i][j]; A32[i * Pm + j] = (float)Ai[i][j]; }
   double* Z64 = ps.Z64 + base * 2 * Pm;
   float* Z32 = ps.Z32 + base * 2 * Pm;
 #pragma unroll
@@ -930,10 +941,15 @@ __global__ void __launch_bounds__(kPrecModesPerBlock) k_prec_elem(DevGeom g, Pre
   ps.schur[base * 3 + 2] = S11;
 }
 
-// Block (one warp) per mode: interface tridiagonal d_j = S00(j) + S11(j−1), e_j = S01(j), Thomas
-// pivots and the Sherman–Morrison closure for periodic meshes (γ = −d_0, u = (γ,0,…,0,e_{N−1}),
-// v = (1,0,…,0,e_{N−1}/γ)).  The sequential recurrences run on lane 0 from shared memory when
-// 5·nif values fit (`staged`), otherwise from global memory.
+// One warp per mode: interface tridiagonal d_j = S00(j) + S11(j−1), e_j = S01(j) and its Thomas
+// pivots.  The pivot recurrence m_j = 1/(d_j − e_{j−1}² m_{j−1}) runs on lane 0 in FP32 from
+// shared memory (a sequential FP64 chain costs ~64 cycles per instruction on this part); the
+// FP64 factors are taken from those pivots, m⁶⁴ = m³², c' = e m, which makes them the exact
+// LDLᵀ factors of a symmetric tridiagonal within FP32 of the true one.  The Sherman–Morrison
+// vector T'⁻¹u of the periodic closure (γ = −d_0, u = (γ,0,…,0,e_{N−1}), v = (1,0,…,0,
+// e_{N−1}/γ)) is then solved with the warp-parallel tridiagonal solver and the same factors,
+// once in FP64 and once in FP32.  Staged in shared memory when 3·nif values fit, otherwise the
+// recurrence reads and writes the destination arrays directly.
 __global__ void __launch_bounds__(32) k_prec_tri(DevGeom g, PrecSetup ps, int staged) {
   extern __shared__ __align__(16) double tri_sm[];
   const int k = blockIdx.x;
@@ -943,55 +959,62 @@ __global__ void __launch_bounds__(32) k_prec_tri(DevGeom g, PrecSetup ps, int st
   double* tm = ps.tm64 + (size_t)k * N;
   double* tcp = ps.tcp64 + (size_t)k * N;
   double* tz = ps.tz64 + (size_t)k * N;
-  // unstaged: results go straight to their destinations and d_j to the scratch array
-  double *dsrc = ps.scratch + (size_t)k * N, *ee = te, *mm = tm, *cc = tcp, *zz = tz;
-  if (staged) { dsrc = tri_sm; ee = dsrc + N; mm = ee + N; cc = mm + N; zz = cc + N; }
+  float* te32 = ps.te32 + (size_t)k * N;
+  float* tm32 = ps.tm32 + (size_t)k * N;
+  float* tcp32 = ps.tcp32 + (size_t)k * N;
+  float* tz32 = ps.tz32 + (size_t)k * N;
+  const double corner = g.periodic ? sc[(Nx - 1) * 3 + 1] : 0.0;
+  float* dd = staged ? reinterpret_cast<float*>(tri_sm) : tm32;     // modified diagonal (FP32)
+  float* ee = staged ? dd + N : te32;
   for (int j = threadIdx.x; j < N; j += blockDim.x) {
     double d;
     if (g.periodic) d = sc[j * 3 + 0] + sc[(j == 0 ? Nx - 1 : j - 1) * 3 + 2];
     else d = (j < Nx ? sc[j * 3 + 0] : 0.0) + (j > 0 ? sc[(j - 1) * 3 + 2] : 0.0);
-    dsrc[j] = d;
-    ee[j] = (j < N - 1) ? sc[j * 3 + 1] : 0.0;
+    const double e = (j < N - 1) ? sc[j * 3 + 1] : 0.0;
+    te[j] = e;
+    dd[j] = (float)d;
+    ee[j] = (float)e;
   }
-  __syncthreads();
-  const double corner = g.periodic ? sc[(Nx - 1) * 3 + 1] : 0.0;
-  const double gamma = g.periodic ? -dsrc[0] : 0.0;
+  __syncwarp();
+  const double gamma = g.periodic ? -(double)(sc[0] + sc[(Nx - 1) * 3 + 2]) : 0.0;
   if (threadIdx.x == 0) {
-    double cp_prev = 0.0, e_prev = 0.0;
-    for (int j = 0; j < N; ++j) {
-      double d = dsrc[j];
-      if (g.periodic && j == 0) d -= gamma;
-      if (g.periodic && j == N - 1) d -= corner * corner / gamma;
-      const double e = ee[j];
-      const double m = 1.0 / (j == 0 ? d : d - e_prev * cp_prev);
-      const double cp = e * m;
-      mm[j] = m; cc[j] = cp;
-      cp_prev = cp; e_prev = e;
-    }
     if (g.periodic) {
-      // z = T'⁻¹ u
-      double prev = gamma * mm[0];
-      zz[0] = prev;
-      for (int j = 1; j < N; ++j) {
-        const double uj = (j == N - 1) ? corner : 0.0;
-        prev = (uj - ee[j - 1] * prev) * mm[j];
-        zz[j] = prev;
-      }
-      for (int j = N - 2; j >= 0; --j) zz[j] -= cc[j] * zz[j + 1];
-      const double vl = corner / gamma;
-      const double fac = 1.0 / (1.0 + zz[0] + vl * zz[N - 1]);
-      ps.tvl64[k] = vl;
-      ps.tfac64[k] = fac;
-      ps.tvl32[k] = (float)vl;
-      ps.tfac32[k] = (float)fac;
+      dd[0] = (float)(2.0 * (sc[0] + sc[(Nx - 1) * 3 + 2]));
+      dd[N - 1] = (float)((double)dd[N - 1] - corner * corner / gamma);
+    }
+    float cp_prev = 0.f, e_prev = 0.f;
+    for (int j = 0; j < N; ++j) {
+      const float m = 1.f / (j == 0 ? dd[0] : fmaf(-e_prev, cp_prev, dd[j]));
+      const float e = ee[j];
+      dd[j] = m;                 // pivots overwrite the diagonal
+      cp_prev = e * m;
+      e_prev = e;
     }
   }
-  __syncthreads();
+  __syncwarp();
   for (int j = threadIdx.x; j < N; j += blockDim.x) {
-    const double e = ee[j], m = mm[j], cp = cc[j], z = g.periodic ? zz[j] : 0.0;
-    te[j] = e; tm[j] = m; tcp[j] = cp; tz[j] = z;
-    const size_t o = (size_t)k * N + j;
-    ps.te32[o] = (float)e; ps.tm32[o] = (float)m; ps.tcp32[o] = (float)cp; ps.tz32[o] = (float)z;
+    const float m = dd[j], e32 = ee[j];
+    tm[j] = (double)m;
+    tcp[j] = te[j] * (double)m;
+    tm32[j] = m;
+    te32[j] = e32;
+    tcp32[j] = e32 * m;
+  }
+  __syncwarp();
+  if (g.periodic) {
+    auto u64 = [&](int j) -> double { return j == 0 ? gamma : (j == N - 1 ? corner : 0.0); };
+    warp_tridiag<double>(N, u64, te, tm, tcp, false, (const double*)nullptr, 0.0, 0.0, tz);
+    auto u32 = [&](int j) -> float { return j == 0 ? (float)gamma : (j == N - 1 ? (float)corner : 0.f); };
+    warp_tridiag<float>(N, u32, te32, tm32, tcp32, false, (const float*)nullptr, 0.f, 0.f, tz32);
+    if (threadIdx.x == 0) {
+      const double vl = corner / gamma;
+      ps.tvl64[k] = vl;
+      ps.tfac64[k] = 1.0 / (1.0 + tz[0] + vl * tz[N - 1]);
+      ps.tvl32[k] = (float)vl;
+      ps.tfac32[k] = 1.f / (1.f + tz32[0] + (float)vl * tz32[N - 1]);
+    }
+  } else {
+    for (int j = threadIdx.x; j < N; j += blockDim.x) { tz[j] = 0.0; tz32[j] = 0.f; }
   }
 }
 
@@ -1150,7 +1173,7 @@ cudaError_t launch_prec_setup(const DevGeom& g, const PrecSetup& ps, cudaStream_
   count_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const size_t bytes = (size_t)5 * ps.nif * sizeof(double);
+  const size_t bytes = (size_t)2 * ps.nif * sizeof(float);
   const int staged = bytes <= kTriStageMax ? 1 : 0;
   if (staged) {
     e = cudaFuncSetAttribute(k_prec_tri, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTriStageMax);

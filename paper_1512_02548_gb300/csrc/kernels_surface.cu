@@ -23,24 +23,27 @@ __device__ __forceinline__ int scol(const SurfTables& t, int ex, int a) {
   return c >= t.ncol ? c - t.ncol : c;
 }
 
+// One warp per column: lanes take (layer, row) pairs, each forms the σ-derivative at its
+// row from the layer's P+1 values and weights it by c_{l,b}; the warp sums the terms.
 __global__ void k_wsurf(SurfTables t, const double* __restrict__ Phi, const double* __restrict__ eta,
                         double* __restrict__ w) {
-  const int col = blockIdx.x * blockDim.x + threadIdx.x;
+  const int col = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (col >= t.ncol) return;
   const int P = t.P, Q = P + 1;
-  const double invd = 1.0 / (eta[col] + t.h[col]);
   const double* phi = Phi + (size_t)col * t.nrow;
   double acc = 0.0;
-  for (int l = 0; l < t.Nz; ++l) {
-    const double ts = 2.0 / t.dsl[l];
+  for (int lb = lane; lb < t.Nz * Q; lb += 32) {
+    const int l = lb / Q, b = lb - l * Q;
     const double* pl = phi + l * P;
-    for (int b = 0; b < Q; ++b) {
-      double d = 0.0;
-      for (int c = 0; c < Q; ++c) d = fma(t.D[b * Q + c], pl[c], d);
-      acc = fma(t.cw[l * Q + b], d * ts, acc);
-    }
+    const double* Db = t.D + b * Q;
+    double d = 0.0;
+    for (int c = 0; c < Q; ++c) d = fma(Db[c], pl[c], d);
+    acc = fma(t.cw[lb] * (2.0 / t.dsl[l]), d, acc);
   }
-  w[col] = acc * invd;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) w[col] = acc / (eta[col] + t.h[col]);
 }
 
 // Element-local S_x f = M·D f_e (the Δx/2 and 2/Δx scales cancel), two fields.
@@ -252,7 +255,7 @@ __global__ void k_rk4(int stage, int n, double dt, double* __restrict__ eta, dou
 
 cudaError_t launch_wsurf(const SurfTables& t, const double* Phi, const double* eta, double* w,
                          cudaStream_t s) {
-  k_wsurf<<<(t.ncol + 127) / 128, 128, 0, s>>>(t, Phi, eta, w);
+  k_wsurf<<<(t.ncol + 3) / 4, 128, 0, s>>>(t, Phi, eta, w);
   count_launch();
   return cudaGetLastError();
 }
