@@ -95,6 +95,8 @@ typedef struct sem_info {
   int n_elements;      /* Nx·Nz                               */
   int P, Pf, Nx, Nz, periodic, precision;
   int grid_ctas;       /* CTAs of the persistent Krylov kernel */
+  int stage_ctas;      /* CTAs of the fused RK stage launch    */
+  int64_t device_bytes;/* device memory owned by the mesh      */
 } sem_info;
 
 typedef struct sem_solve_stats {
@@ -119,6 +121,9 @@ typedef struct sem_mesh sem_mesh;
 int sem_mesh_create(const sem_params* p, const double* x_edges_h, const double* h_h,
                     sem_mesh** out);
 void sem_mesh_destroy(sem_mesh* m);
+/* Device memory sem_mesh_create would allocate for these arguments, without allocating
+ * (for admission control); same validation and errors as sem_mesh_create. */
+int sem_mesh_footprint(const sem_params* p, const double* x_edges_h, const double* h_h, int64_t* bytes);
 int sem_mesh_info(const sem_mesh* m, sem_info* info);
 
 /* Element-to-global map used by every gather/scatter (§3.1.2, assembly over
@@ -209,6 +214,25 @@ int sem_rk4_step(sem_mesh* m, double* eta_d, double* phis_d, double* t, double d
  * and copies the result back.  Synchronises. */
 int sem_rk4_step_host(sem_mesh* m, double* eta_h, double* phis_h, double* t, double dt,
                       int nsteps, void* stream);
+
+/* Batched instances (many tanks stepped together).  One cooperative launch per RK stage
+ * and per (order P, precision) group runs every instance of the group; each instance is
+ * served by its own team of CTAs, sized to its element count, with its own grid barriers
+ * and reductions, so results equal the instance run alone up to the summation order of the
+ * team's reductions.  The meshes stay owned by the caller and must outlive the batch; they
+ * must share one device and use the separable preconditioner.  Stepping a batch uses each
+ * mesh's workspace, so a mesh may not be stepped elsewhere concurrently. */
+typedef struct sem_batch sem_batch;
+int sem_batch_create(sem_mesh* const* meshes, int count, sem_batch** out);
+void sem_batch_destroy(sem_batch* b);
+/* Launches per RK stage and total CTAs of one stage (for reporting). */
+int sem_batch_info(const sem_batch* b, int* launches_per_stage, int* ctas);
+/* nsteps RK4 steps (with filter and relaxation as configured per mesh) on every instance:
+ * eta_d[i], phis_d[i] device arrays of instance i (Ncol_i values), dt_h[i] its step, t_h[i]
+ * (host, may be NULL) its time, advanced by nsteps·dt_h[i].  Synchronises; the first failing
+ * instance's error is returned (its index in the message). */
+int sem_batch_rk4_step(sem_batch* b, double* const* eta_d, double* const* phis_d, double* t_h,
+                       const double* dt_h, int nsteps, void* stream);
 
 /* Solver counters accumulated on the device; reading synchronises the stream. */
 int sem_get_counters(sem_mesh* m, sem_counters* c, void* stream);

@@ -24,11 +24,12 @@ SEM_ERRORS = {1: "SEM_ERR_INVALID_ARG", 2: "SEM_ERR_OOM", 3: "SEM_ERR_CUDA",
 SEM_PREC_FP64, SEM_PREC_MIXED = 0, 1
 SEM_PRECOND_SEPARABLE, SEM_PRECOND_JACOBI = 0, 1
 
-EXPORTED = ("sem_mesh_create", "sem_mesh_destroy", "sem_mesh_info", "sem_mesh_l2g",
+EXPORTED = ("sem_mesh_create", "sem_mesh_destroy", "sem_mesh_footprint", "sem_mesh_info", "sem_mesh_l2g",
             "sem_update_geometry", "sem_laplace_apply", "sem_laplace_apply_noalloc", "sem_laplace_solve",
             "sem_recover_gradient", "sem_zakharov_rhs", "sem_set_wave_input", "sem_apply_filter", "sem_rk4_step",
             "sem_rk4_step_host", "sem_get_counters", "sem_reset_counters", "sem_enable_timing",
-            "sem_get_timing", "sem_launch_count", "sem_last_error")
+            "sem_get_timing", "sem_batch_create", "sem_batch_destroy", "sem_batch_info",
+            "sem_batch_rk4_step", "sem_launch_count", "sem_last_error")
 
 
 class sem_params(ctypes.Structure):
@@ -45,7 +46,8 @@ class sem_info(ctypes.Structure):
     _fields_ = [("n_nodes", ctypes.c_int64), ("n_unknowns", ctypes.c_int64),
                 ("ncol", ctypes.c_int), ("nrow", ctypes.c_int), ("n_elements", ctypes.c_int),
                 ("P", ctypes.c_int), ("Pf", ctypes.c_int), ("Nx", ctypes.c_int), ("Nz", ctypes.c_int),
-                ("periodic", ctypes.c_int), ("precision", ctypes.c_int), ("grid_ctas", ctypes.c_int)]
+                ("periodic", ctypes.c_int), ("precision", ctypes.c_int), ("grid_ctas", ctypes.c_int),
+                ("stage_ctas", ctypes.c_int), ("device_bytes", ctypes.c_int64)]
 
 
 class sem_solve_stats(ctypes.Structure):
@@ -75,6 +77,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib = ctypes.CDLL(path)
     vp, dp, ip = ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int
     lib.sem_mesh_create.argtypes = [ctypes.POINTER(sem_params), dp, dp, ctypes.POINTER(vp)]
+    lib.sem_mesh_footprint.argtypes = [ctypes.POINTER(sem_params), dp, dp, ctypes.POINTER(ctypes.c_int64)]
     lib.sem_mesh_destroy.argtypes = [vp]
     lib.sem_mesh_destroy.restype = None
     lib.sem_mesh_info.argtypes = [vp, ctypes.POINTER(sem_info)]
@@ -93,12 +96,18 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sem_reset_counters.argtypes = [vp, vp]
     lib.sem_enable_timing.argtypes = [vp, ip]
     lib.sem_get_timing.argtypes = [vp, ctypes.POINTER(sem_timing)]
+    lib.sem_batch_create.argtypes = [ctypes.POINTER(vp), ip, ctypes.POINTER(vp)]
+    lib.sem_batch_destroy.argtypes = [vp]
+    lib.sem_batch_destroy.restype = None
+    lib.sem_batch_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+    lib.sem_batch_rk4_step.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_double), ip, vp]
     lib.sem_launch_count.restype = ctypes.c_int64
     lib.sem_launch_count.argtypes = []
     lib.sem_last_error.restype = ctypes.c_char_p
     lib.sem_last_error.argtypes = []
     for name in EXPORTED:
-        if name not in ("sem_mesh_destroy", "sem_launch_count", "sem_last_error"):
+        if name not in ("sem_mesh_destroy", "sem_batch_destroy", "sem_launch_count", "sem_last_error"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -135,6 +144,28 @@ def launch_count() -> int:
     return int(load_library().sem_launch_count())
 
 
+def mesh_params(P, Nx, Nz, periodic=True, Pf=0, filter_alpha=0.0, filter_s=0.0, filter_ic=-1, g=9.81,
+                tol=1e-13, max_iter=5000, precision="fp64", precond="separable", relax_left=0.0,
+                relax_right=0.0, relax_tau=0.0) -> sem_params:
+    if precision not in ("fp64", "mixed") or precond not in ("separable", "jacobi"):
+        raise ValueError("precision must be fp64|mixed and precond separable|jacobi")
+    return sem_params(P=P, Nx=Nx, Nz=Nz, periodic=int(bool(periodic)), Pf=Pf, filter_ic=filter_ic,
+                      filter_alpha=filter_alpha, filter_s=filter_s, g=g, tol=tol, max_iter=max_iter,
+                      precision=SEM_PREC_MIXED if precision == "mixed" else SEM_PREC_FP64,
+                      precond=SEM_PRECOND_JACOBI if precond == "jacobi" else SEM_PRECOND_SEPARABLE,
+                      relax_left=relax_left, relax_right=relax_right, relax_tau=relax_tau)
+
+
+def mesh_footprint(prm: sem_params, x_edges, h) -> int:
+    """Device bytes a mesh with these parameters would own (sem_mesh_footprint)."""
+    xe = np.ascontiguousarray(x_edges, dtype=np.float64)
+    hh = np.ascontiguousarray(h, dtype=np.float64)
+    b = ctypes.c_int64()
+    _check(load_library().sem_mesh_footprint(ctypes.byref(prm), xe.ctypes.data_as(ctypes.c_void_p),
+                                             hh.ctypes.data_as(ctypes.c_void_p), ctypes.byref(b)))
+    return int(b.value)
+
+
 class Mesh:
     """One σ-mesh on the current CUDA device; wraps ``sem_mesh``.
 
@@ -147,13 +178,8 @@ class Mesh:
                  precond: str = "separable", relax_left: float = 0.0, relax_right: float = 0.0,
                  relax_tau: float = 0.0, wave=None):
         lib = load_library()
-        if precision not in ("fp64", "mixed") or precond not in ("separable", "jacobi"):
-            raise ValueError("precision must be fp64|mixed and precond separable|jacobi")
-        prm = sem_params(P=P, Nx=Nx, Nz=Nz, periodic=int(bool(periodic)), Pf=Pf, filter_ic=filter_ic,
-                         filter_alpha=filter_alpha, filter_s=filter_s, g=g, tol=tol, max_iter=max_iter,
-                         precision=SEM_PREC_MIXED if precision == "mixed" else SEM_PREC_FP64,
-                         precond=SEM_PRECOND_JACOBI if precond == "jacobi" else SEM_PRECOND_SEPARABLE,
-                         relax_left=relax_left, relax_right=relax_right, relax_tau=relax_tau)
+        prm = mesh_params(P, Nx, Nz, periodic, Pf, filter_alpha, filter_s, filter_ic, g, tol, max_iter, precision,
+                          precond, relax_left, relax_right, relax_tau)
         xe = np.ascontiguousarray(x_edges, dtype=np.float64)
         hh = np.ascontiguousarray(h, dtype=np.float64)
         handle = ctypes.c_void_p()
@@ -264,3 +290,40 @@ class Mesh:
         t = sem_timing()
         _check(load_library().sem_get_timing(self._h, ctypes.byref(t)))
         return t
+
+
+class Batch:
+    """Many meshes stepped together (``sem_batch``): one fused launch per RK stage and order."""
+
+    def __init__(self, meshes):
+        lib = load_library()
+        self.meshes = list(meshes)
+        arr = (ctypes.c_void_p * len(self.meshes))(*[m._h.value for m in self.meshes])
+        handle = ctypes.c_void_p()
+        _check(lib.sem_batch_create(arr, len(self.meshes), ctypes.byref(handle)))
+        self._h = handle
+
+    def info(self):
+        a, b = ctypes.c_int(), ctypes.c_int()
+        _check(load_library().sem_batch_info(self._h, ctypes.byref(a), ctypes.byref(b)))
+        return {"launches_per_stage": a.value, "ctas": b.value}
+
+    def rk4_step(self, etas, phises, dts, nsteps: int = 1, ts=None):
+        n = len(self.meshes)
+        e = (ctypes.c_void_p * n)(*[_ptr(x).value for x in etas])
+        p = (ctypes.c_void_p * n)(*[_ptr(x).value for x in phises])
+        d = (ctypes.c_double * n)(*dts)
+        t = (ctypes.c_double * n)(*(ts if ts is not None else [0.0] * n))
+        _check(load_library().sem_batch_rk4_step(self._h, e, p, t, d, int(nsteps), _stream()))
+        return list(t)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load_library().sem_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -18,6 +18,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsem_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["kernels_laplace.cu", "kernels_surface.cu", "capi.cu"]
+ORDERS = range(2, 13)            # kernels_order.cu is compiled once per GLL order
 CXX_SOURCES = ["tables.cpp"]
 
 
@@ -47,11 +48,19 @@ def build_library(verbose: bool = False, ptxas_info: bool = False) -> str:
         if ptxas_info:
             cmd.insert(1, "-Xptxas=-v")
         jobs.append((cmd, obj))
+    for P in ORDERS:
+        obj = os.path.join(BUILD, f"kernels_order_p{P}.o")
+        cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+               "--expt-relaxed-constexpr", f"-DSEM_ORDER={P}", *inc, "-c",
+               os.path.join(CSRC, "kernels_order.cu"), "-o", obj]
+        if ptxas_info:
+            cmd.insert(1, "-Xptxas=-v")
+        jobs.append((cmd, obj))
     for src in CXX_SOURCES:
         obj = os.path.join(BUILD, src + ".o")
         cmd = ["g++", "-O2", "-std=c++17", "-fPIC", *inc, "-c", os.path.join(CSRC, src), "-o", obj]
         jobs.append((cmd, obj))
-    with ThreadPoolExecutor(max_workers=len(jobs)) as ex:
+    with ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
         outs = list(ex.map(lambda j: _run(j[0]), jobs))
     if verbose:
         for o in outs:

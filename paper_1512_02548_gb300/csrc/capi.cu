@@ -91,6 +91,7 @@ struct sem_mesh {
   int grid = 0;
   size_t smem = 0;
   unsigned char* pool = nullptr;
+  size_t pool_bytes = 0;
   DevGeom g{};
   SurfTables st{};
   PcgArgs pa{};
@@ -101,10 +102,40 @@ struct sem_mesh {
   double *wt = nullptr, *etax = nullptr, *phisx = nullptr, *R = nullptr, *scr = nullptr;
   double *ke = nullptr, *kp = nullptr, *ae = nullptr, *ap = nullptr, *se = nullptr, *sp = nullptr;
   double *eta_dev = nullptr, *phis_dev = nullptr;
+  double *s1e = nullptr, *s1p = nullptr;   // second stage-input pair of the fused RK stage
+  // fused-stage launch of this mesh alone: device descriptor, CTA map, barrier pair
+  Instance* inst_d = nullptr;
+  int* cta_inst_d = nullptr;
+  unsigned int* stage_bars = nullptr;
+  Instance inst_h{};
+  int stage_team = 0;
+  size_t stage_smem = 0;
+  bool fused = true;
   // optional event timing of the Krylov kernel
   bool timing = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
   std::vector<cudaEvent_t> spare;
+};
+
+// A batch: instances grouped by (order, precision) and, within a group, into launches of at
+// most the co-resident capacity; each instance gets a team of CTAs sized to its work.
+struct BatchLaunch {
+  int P = 0, mixed = 0;
+  std::vector<int> members;          // mesh indices
+  std::vector<int> team0, nteam;
+  int grid = 0;
+  size_t smem = 0;
+  Instance* inst_d = nullptr;
+  int* cta_d = nullptr;
+  unsigned int* bars_d = nullptr;
+  std::vector<Instance> inst_h;
+};
+
+struct sem_batch {
+  std::vector<sem_mesh*> meshes;
+  std::vector<BatchLaunch> launches;
+  int device = 0;
+  unsigned char* pool = nullptr;
 };
 
 namespace {
@@ -172,7 +203,53 @@ int do_rhs(sem_mesh* m, const double* eta, const double* phis, double time, doub
   return SEM_OK;
 }
 
+Instance make_instance(sem_mesh* m, double* eta, double* phis, double tstart, double dt, int team0,
+                       int nteam) {
+  Instance I{};
+  I.g = m->g;
+  I.st = m->st;
+  I.pa = m->pa;
+  I.pa.x = m->Phi;
+  I.ps = m->ps;
+  I.eta = eta; I.phis = phis;
+  I.s0e = m->se; I.s0p = m->sp; I.s1e = m->s1e; I.s1p = m->s1p;
+  I.ke = m->ke; I.kp = m->kp; I.ae = m->ae; I.ap = m->ap;
+  I.wt = m->wt; I.etax = m->etax; I.phisx = m->phisx; I.R = m->R; I.scr = m->scr;
+  I.tstart = tstart; I.dt = dt;
+  I.tau = m->p.relax_tau > 0.0 ? m->p.relax_tau : dt;
+  I.team0 = team0; I.nteam = nteam;
+  I.relax = has_zones(m) ? 1 : 0;
+  return I;
+}
+
+// nsteps RK4 steps of one mesh with the fused stage kernel: one cooperative launch per stage.
+int do_rk4_fused(sem_mesh* m, double* eta, double* phis, double t0, double dt, int nsteps, cudaStream_t s) {
+  m->inst_h = make_instance(m, eta, phis, t0, dt, 0, m->stage_team);
+  CUDA_TRY(cudaMemcpyAsync(m->inst_d, &m->inst_h, sizeof(Instance), cudaMemcpyHostToDevice, s));
+  StageArgs a{m->inst_d, m->cta_inst_d, m->stage_bars, 1, 0};
+  const int mixed = m->p.precision == SEM_PREC_MIXED;
+  for (int step = 0; step < nsteps; ++step)
+    for (int stage = 1; stage <= 4; ++stage) {
+      a.stage = stage;
+      a.step = step;
+      CUDA_TRY(cudaMemsetAsync(m->stage_bars, 0, 2 * sizeof(unsigned int), s));
+      cudaEvent_t e0 = nullptr, e1 = nullptr;
+      if (m->timing) {
+        CUDA_TRY(take_event(m, &e0));
+        CUDA_TRY(take_event(m, &e1));
+        CUDA_TRY(cudaEventRecord(e0, s));
+      }
+      CUDA_TRY(launch_stage(m->p.P, mixed, a, m->stage_team, m->stage_smem, s));
+      if (m->timing) {
+        CUDA_TRY(cudaEventRecord(e1, s));
+        m->events.emplace_back(e0, e1);
+      }
+    }
+  return SEM_OK;
+}
+
 int do_rk4(sem_mesh* m, double* eta, double* phis, double t0, double dt, int nsteps, cudaStream_t s) {
+  if (m->fused) return do_rk4_fused(m, eta, phis, t0, dt, nsteps, s);
   const int n = m->ncol;
   const double tau = m->p.relax_tau > 0.0 ? m->p.relax_tau : dt;
   for (int step = 0; step < nsteps; ++step) {
@@ -209,9 +286,26 @@ const char* sem_last_error(void) { return t_err.c_str(); }
 
 int64_t sem_launch_count(void) { return g_launches.load(); }
 
+static int mesh_create_impl(const sem_params* pin, const double* x_edges_h, const double* h_h, sem_mesh** out,
+                            size_t* footprint_only);
+
 int sem_mesh_create(const sem_params* pin, const double* x_edges_h, const double* h_h, sem_mesh** out) {
   if (!out) return fail(SEM_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
+  return mesh_create_impl(pin, x_edges_h, h_h, out, nullptr);
+}
+
+int sem_mesh_footprint(const sem_params* p, const double* x_edges_h, const double* h_h, int64_t* bytes) {
+  if (!bytes) return fail(SEM_ERR_INVALID_ARG, "bytes is NULL");
+  size_t b = 0;
+  sem_mesh* unused = nullptr;
+  const int rc = mesh_create_impl(p, x_edges_h, h_h, &unused, &b);
+  *bytes = (int64_t)b;
+  return rc;
+}
+
+static int mesh_create_impl(const sem_params* pin, const double* x_edges_h, const double* h_h, sem_mesh** out,
+                            size_t* footprint_only) {
   if (!pin || !x_edges_h || !h_h) return fail(SEM_ERR_INVALID_ARG, "NULL argument");
   sem_params p = *pin;
   const int Nx_in = p.Nx > 0 ? p.Nx : 0;
@@ -422,7 +516,9 @@ int sem_mesh_create(const sem_params* pin, const double* x_edges_h, const double
                o_R = cv.take<double>((size_t)2 * Nx * Q), o_scr = cv.take<double>((size_t)4 * Nx + 2 * (N + 1)),
                o_ke = cv.take<double>(ncol), o_kp = cv.take<double>(ncol), o_ae = cv.take<double>(ncol),
                o_ap = cv.take<double>(ncol), o_se = cv.take<double>(ncol), o_sp = cv.take<double>(ncol),
-               o_etad = cv.take<double>(ncol), o_phisd = cv.take<double>(ncol);
+               o_etad = cv.take<double>(ncol), o_phisd = cv.take<double>(ncol),
+               o_s1e = cv.take<double>(ncol), o_s1p = cv.take<double>(ncol);
+  const size_t o_inst = cv.take<Instance>(1), o_ctai = cv.take<int>((size_t)m->grid), o_sbar = cv.take<unsigned>(4);
   // surface tables
   const size_t o_tD = cv.take<double>(Q * Q), o_tMD = cv.take<double>(Q * Q), o_tB = cv.take<double>((size_t)Q * Qf),
                o_tI = cv.take<double>((size_t)Qf * Q), o_tF = cv.take<double>(Q * Q), o_tcw = cv.take<double>((size_t)Nz * Q),
@@ -430,6 +526,12 @@ int sem_mesh_create(const sem_params* pin, const double* x_edges_h, const double
                o_tse = cv.take<double>(Nx), o_te = cv.take<double>(N), o_tm = cv.take<double>(N),
                o_tcp = cv.take<double>(N), o_tz = cv.take<double>(N);
   const size_t total = cv.off + 256;
+  if (footprint_only) {
+    *footprint_only = total;
+    delete m;
+    return SEM_OK;
+  }
+  m->pool_bytes = total;
   cudaError_t ae = cudaMalloc(&m->pool, total);
   if (ae != cudaSuccess) { delete m; return fail(SEM_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(ae)); }
   auto D_ = [&](size_t o) { return reinterpret_cast<double*>(m->pool + o); };
@@ -503,6 +605,10 @@ int sem_mesh_create(const sem_params* pin, const double* x_edges_h, const double
   m->wt = D_(o_wt); m->etax = D_(o_etax); m->phisx = D_(o_phisx); m->R = D_(o_R); m->scr = D_(o_scr);
   m->ke = D_(o_ke); m->kp = D_(o_kp); m->ae = D_(o_ae); m->ap = D_(o_ap); m->se = D_(o_se); m->sp = D_(o_sp);
   m->eta_dev = D_(o_etad); m->phis_dev = D_(o_phisd);
+  m->s1e = D_(o_s1e); m->s1p = D_(o_s1p);
+  m->inst_d = reinterpret_cast<Instance*>(m->pool + o_inst);
+  m->cta_inst_d = reinterpret_cast<int*>(m->pool + o_ctai);
+  m->stage_bars = reinterpret_cast<unsigned int*>(m->pool + o_sbar);
 
   SurfTables& t = m->st;
   t.P = P; t.Pf = p.Pf; t.Nx = Nx; t.Nz = Nz; t.ncol = ncol; t.nrow = nrow; t.periodic = g.periodic; t.g = p.g;
@@ -512,6 +618,28 @@ int sem_mesh_create(const sem_params* pin, const double* x_edges_h, const double
   t.th_vlast = th_vlast; t.th_fac = th_fac; t.nif = N; t.filter_on = (p.filter_ic >= 0 && p.filter_ic < P) ? 1 : 0;
   t.xcol = D_(o_xcol); t.x0 = x_edges_h[0]; t.x1 = x_edges_h[Nx];
   t.relax_left = p.relax_left; t.relax_right = p.relax_right; t.ncomp = 0; t.wave = D_(o_wave);
+  // the fused RK stage runs this mesh with one team of CTAs (at most its Krylov grid)
+  {
+    const char* fz = std::getenv("SEM_FUSED_STAGE");
+    m->fused = !(fz && fz[0] == '0') && p.precond == SEM_PRECOND_SEPARABLE;
+    m->stage_smem = stage_smem_bytes(P, nrow, Nz);
+    int per_sm = 0, sms = 0;
+    cudaError_t e = stage_occupancy(P, p.precision == SEM_PREC_MIXED, m->stage_smem, &per_sm);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess || per_sm < 1) {
+      cudaFree(m->pool);
+      delete m;
+      return fail(SEM_ERR_CUDA, "fused stage kernel does not fit on this device");
+    }
+    m->stage_team = std::min(m->grid, per_sm * sms);
+    std::vector<int> zeros(m->grid, 0);
+    cudaError_t e2 = cudaMemcpy(m->cta_inst_d, zeros.data(), sizeof(int) * m->grid, cudaMemcpyHostToDevice);
+    if (e2 != cudaSuccess) {
+      cudaFree(m->pool);
+      delete m;
+      return fail(SEM_ERR_CUDA, std::string("upload: ") + cudaGetErrorString(e2));
+    }
+  }
   *out = m;
   return SEM_OK;
 }
@@ -534,6 +662,8 @@ int sem_mesh_info(const sem_mesh* m, sem_info* info) {
   info->P = m->p.P; info->Pf = m->Pf; info->Nx = m->p.Nx; info->Nz = m->p.Nz;
   info->periodic = m->p.periodic; info->precision = m->p.precision;
   info->grid_ctas = m->grid;
+  info->stage_ctas = m->stage_team;
+  info->device_bytes = (int64_t)m->pool_bytes;
   return SEM_OK;
 }
 
@@ -654,6 +784,155 @@ int sem_rk4_step_host(sem_mesh* m, double* eta_h, double* phis_h, double* t, dou
   CUDA_TRY(cudaMemcpyAsync(phis_h, m->phis_dev, bytes, cudaMemcpyDeviceToHost, s));
   rc = read_status(m, s);
   if (t) *t += nsteps * dt;
+  return rc;
+}
+
+int sem_batch_create(sem_mesh* const* meshes, int count, sem_batch** out) {
+  if (!out) return fail(SEM_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!meshes || count < 1) return fail(SEM_ERR_INVALID_ARG, "empty batch");
+  for (int i = 0; i < count; ++i)
+    if (!meshes[i]) return fail(SEM_ERR_INVALID_ARG, "NULL mesh in batch");
+  const int dev = meshes[0]->device;
+  for (int i = 0; i < count; ++i) {
+    if (meshes[i]->device != dev) return fail(SEM_ERR_INVALID_ARG, "batch meshes must share one device");
+    if (!meshes[i]->fused) return fail(SEM_ERR_INVALID_ARG, "batched meshes need the separable preconditioner");
+    for (int j = 0; j < i; ++j)
+      if (meshes[j] == meshes[i]) return fail(SEM_ERR_INVALID_ARG, "a mesh appears twice in the batch");
+  }
+  DeviceGuard dg(dev);
+  int sms = 0;
+  CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  sem_batch* b = new sem_batch;
+  b->device = dev;
+  b->meshes.assign(meshes, meshes + count);
+  // group by (order, precision)
+  std::vector<std::pair<std::pair<int, int>, std::vector<int>>> groups;
+  for (int i = 0; i < count; ++i) {
+    const std::pair<int, int> key(meshes[i]->p.P, meshes[i]->p.precision == SEM_PREC_MIXED ? 1 : 0);
+    auto it = std::find_if(groups.begin(), groups.end(), [&](const auto& g) { return g.first == key; });
+    if (it == groups.end()) groups.push_back({key, {i}});
+    else it->second.push_back(i);
+  }
+  size_t total = 0;
+  for (auto& grp : groups) {
+    size_t smem = 0;
+    for (int i : grp.second) smem = std::max(smem, meshes[i]->stage_smem);
+    int per_sm = 0;
+    cudaError_t e = stage_occupancy(grp.first.first, grp.first.second, smem, &per_sm);
+    if (e != cudaSuccess || per_sm < 1) { delete b; return fail(SEM_ERR_CUDA, "fused stage kernel does not fit"); }
+    const int cap = per_sm * sms;
+    // split into launches of at most `cap` instances, then share the CTAs by work
+    for (size_t first = 0; first < grp.second.size(); first += cap) {
+      BatchLaunch L;
+      L.P = grp.first.first;
+      L.mixed = grp.first.second;
+      L.smem = smem;
+      const size_t last = std::min(grp.second.size(), first + (size_t)cap);
+      L.members.assign(grp.second.begin() + first, grp.second.begin() + last);
+      double wsum = 0.0;
+      std::vector<double> w;
+      for (int i : L.members) {
+        const sem_mesh* m = meshes[i];
+        w.push_back((double)m->p.Nx * m->p.Nz * (m->p.P + 1) * (m->p.P + 1));
+        wsum += w.back();
+      }
+      std::vector<int> c(L.members.size());
+      int used = 0;
+      for (size_t k = 0; k < L.members.size(); ++k) {
+        const sem_mesh* m = meshes[L.members[k]];
+        const int limit = std::max(1, std::min(m->stage_team, m->p.Nx));
+        c[k] = std::max(1, std::min(limit, (int)((double)cap * w[k] / wsum)));
+        used += c[k];
+      }
+      while (used > cap) {   // trim the largest teams
+        size_t kmax = 0;
+        for (size_t k = 1; k < c.size(); ++k) if (c[k] > c[kmax]) kmax = k;
+        if (c[kmax] == 1) break;
+        --c[kmax];
+        --used;
+      }
+      int acc = 0;
+      for (size_t k = 0; k < c.size(); ++k) { L.team0.push_back(acc); L.nteam.push_back(c[k]); acc += c[k]; }
+      L.grid = acc;
+      total += ((sizeof(Instance) * L.members.size() + 255) & ~size_t(255)) +
+               ((sizeof(int) * (size_t)L.grid + 255) & ~size_t(255)) +
+               ((sizeof(unsigned) * 2 * L.members.size() + 255) & ~size_t(255));
+      b->launches.push_back(std::move(L));
+    }
+  }
+  cudaError_t ae = cudaMalloc(&b->pool, total + 256);
+  if (ae != cudaSuccess) { delete b; return fail(SEM_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(ae)); }
+  size_t off = 0;
+  for (auto& L : b->launches) {
+    L.inst_d = reinterpret_cast<Instance*>(b->pool + off);
+    off += (sizeof(Instance) * L.members.size() + 255) & ~size_t(255);
+    L.cta_d = reinterpret_cast<int*>(b->pool + off);
+    off += (sizeof(int) * (size_t)L.grid + 255) & ~size_t(255);
+    L.bars_d = reinterpret_cast<unsigned int*>(b->pool + off);
+    off += (sizeof(unsigned) * 2 * L.members.size() + 255) & ~size_t(255);
+    std::vector<int> map(L.grid);
+    for (size_t k = 0; k < L.members.size(); ++k)
+      for (int c = 0; c < L.nteam[k]; ++c) map[L.team0[k] + c] = (int)k;
+    cudaError_t e = cudaMemcpy(L.cta_d, map.data(), sizeof(int) * L.grid, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { cudaFree(b->pool); delete b; return fail(SEM_ERR_CUDA, cudaGetErrorString(e)); }
+    L.inst_h.resize(L.members.size());
+  }
+  *out = b;
+  return SEM_OK;
+}
+
+void sem_batch_destroy(sem_batch* b) {
+  if (!b) return;
+  DeviceGuard dg(b->device);
+  cudaFree(b->pool);
+  delete b;
+}
+
+int sem_batch_info(const sem_batch* b, int* launches_per_stage, int* ctas) {
+  if (!b) return fail(SEM_ERR_INVALID_ARG, "NULL batch");
+  int tot = 0;
+  for (const auto& L : b->launches) tot += L.grid;
+  if (launches_per_stage) *launches_per_stage = (int)b->launches.size();
+  if (ctas) *ctas = tot;
+  return SEM_OK;
+}
+
+int sem_batch_rk4_step(sem_batch* b, double* const* eta_d, double* const* phis_d, double* t_h, const double* dt_h,
+                       int nsteps, void* stream) {
+  if (!b || !eta_d || !phis_d || !dt_h || nsteps < 0) return fail(SEM_ERR_INVALID_ARG, "bad argument");
+  const int n = (int)b->meshes.size();
+  for (int i = 0; i < n; ++i)
+    if (!eta_d[i] || !phis_d[i] || !(dt_h[i] > 0.0)) return fail(SEM_ERR_INVALID_ARG, "bad instance state");
+  DeviceGuard dg(b->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  for (auto& L : b->launches) {
+    for (size_t k = 0; k < L.members.size(); ++k) {
+      const int i = L.members[k];
+      L.inst_h[k] = make_instance(b->meshes[i], eta_d[i], phis_d[i], t_h ? t_h[i] : 0.0, dt_h[i], L.team0[k],
+                                  L.nteam[k]);
+    }
+    CUDA_TRY(cudaMemcpyAsync(L.inst_d, L.inst_h.data(), sizeof(Instance) * L.members.size(),
+                             cudaMemcpyHostToDevice, s));
+  }
+  for (int step = 0; step < nsteps; ++step)
+    for (int stage = 1; stage <= 4; ++stage)
+      for (auto& L : b->launches) {
+        CUDA_TRY(cudaMemsetAsync(L.bars_d, 0, 2 * sizeof(unsigned int) * L.members.size(), s));
+        const StageArgs a{L.inst_d, L.cta_d, L.bars_d, stage, step};
+        CUDA_TRY(launch_stage(L.P, L.mixed, a, L.grid, L.smem, s));
+      }
+  CUDA_TRY(cudaStreamSynchronize(s));
+  int rc = SEM_OK;
+  for (int i = 0; i < n; ++i) {
+    const int r = read_status(b->meshes[i], s);
+    if (r != SEM_OK && rc == SEM_OK) {
+      rc = r;
+      t_err = "instance " + std::to_string(i) + ": " + t_err;
+    }
+  }
+  if (t_h)
+    for (int i = 0; i < n; ++i) t_h[i] += nsteps * dt_h[i];
   return rc;
 }
 

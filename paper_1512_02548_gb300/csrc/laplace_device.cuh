@@ -1,0 +1,1226 @@
+// σ-geometry, the matrix-free Laplace operator and the persistent Krylov solver
+// (§2 and §3.1.2 of arXiv 1512.02548), for sm_103a.
+//
+// Operator.  For element (ex,l) with local nodal values u_ab, a along x and b along
+// σ, GLL collocation gives the gradients u_r = (D⊗I)u, u_t = (I⊗D)u; with weights
+// W_ab = w_a w_b |J^k| and K = JJᵀ/det J (eq. symTransformedLaplace2) the element
+// contribution to A = −𝓛 is
+//     (A_e u) = (Dᵀ⊗I) F1 + (I⊗Dᵀ) F2,
+//     F1 = w_a w_b (Δσ/Δx · K11 u_r + K12 u_t),  F2 = w_a w_b (K12 u_r + Δx/Δσ · K22 u_t),
+// with K11 = d, K12 = ∂xh − σ ∂xd, K22 = (1 + K12²)/d evaluated on the fly from four
+// numbers per element-local column.  Nothing is stored per node except the vectors.
+//
+// Work decomposition.  One CTA processes an "element column" (all Nz layers of
+// x-element ex) at a time: its (P+1)·Nrow nodes are staged in shared memory, the
+// layers are summed in shared memory, columns a = 0..P−1 are written straight to
+// the output and column a = P (shared with the next x-element) to an edge buffer
+// that the owner of that column adds after a grid barrier.  All sums are in a fixed
+// order, so results are bitwise reproducible.
+//
+// Krylov.  Conjugate gradients on the Dirichlet-eliminated SPD system with the
+// Jacobi preconditioner run inside ONE cooperative persistent kernel: two grid
+// barriers per iteration, deterministic reductions, a double-buffered search
+// direction so each CTA can rebuild its halo column without a third barrier, and a
+// device-side convergence test (no host round trip).  In mixed precision the inner
+// iterations run in FP32 and the kernel refines the FP64 residual.
+//
+// Device code of the σ-Laplace path, templated on the GLL order P: geometry, the matrix-free
+// operator, the persistent Krylov solver with the σ-separable preconditioner, and the fused
+// RK stage.  Included by kernels_order.cu, which is compiled once per order (-DSEM_ORDER=P)
+// and instantiates the host entry points at the end of this file; everything else here has
+// internal linkage, including each order's copy of the constant tables.
+#pragma once
+#include <cooperative_groups.h>
+
+#include "mesh_index.cuh"
+#include "surface_device.cuh"
+
+namespace semgb {
+
+static __constant__ double c_D64[kDTotal];
+static __constant__ float c_D32[kDTotal];
+static __constant__ double c_w64[kWTotal];
+static __constant__ float c_w32[kWTotal];
+
+template <class T> struct CT;
+template <> struct CT<double> {
+  static __device__ __forceinline__ const double* D() { return c_D64; }
+  static __device__ __forceinline__ const double* w() { return c_w64; }
+};
+template <> struct CT<float> {
+  static __device__ __forceinline__ const float* D() { return c_D32; }
+  static __device__ __forceinline__ const float* w() { return c_w32; }
+};
+
+
+// L2-coherent load for data another CTA wrote before the last grid barrier.
+
+
+// ------------------------------------------------------------------------------------
+// Geometry: per element-local column (ex, a) store d, 1/d, ∂x h, ∂x d (element-local
+// collocation derivative of d = η + h, the exact Jacobian of the interpolated σ-map).
+// ------------------------------------------------------------------------------------
+template <int P>
+__device__ __forceinline__ void geometry_item(const DevGeom& g, const double* __restrict__ eta, int t) {
+  constexpr int Q = P + 1;
+  const int ex = t / Q, a = t - ex * Q;
+  const double* D = c_D64 + d_off(P) + a * Q;
+  double etax = 0.0;
+#pragma unroll
+  for (int c = 0; c < Q; ++c) etax = fma(D[c], __ldcg(eta + col_of(g, ex, c)), etax);
+  etax *= 2.0 / g.dxe[ex];
+  const int col = col_of(g, ex, a);
+  const double d = __ldcg(eta + col) + g.h[col];
+  const double hx = g.hx_loc[t];
+  const double dxd = etax + hx;
+  if (!(d > 0.0) || !isfinite(d) || !isfinite(dxd)) atomicOr(g.status, ST_BAD_DEPTH);
+  const double invd = 1.0 / d;
+  double* o = g.geo64 + (size_t)t * 4;
+  o[0] = d; o[1] = invd; o[2] = hx; o[3] = dxd;
+  float* o32 = g.geo32 + (size_t)t * 4;
+  o32[0] = (float)d; o32[1] = (float)invd; o32[2] = (float)hx; o32[3] = (float)dxd;
+}
+
+template <int P>
+__global__ void k_geometry(DevGeom g, const double* __restrict__ eta) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= g.Nx * (P + 1)) return;
+  geometry_item<P>(g, eta, t);
+}
+
+// Jacobi diagonal of A = −𝓛: for element-local node (i,j),
+//   A_e[(i,j),(i,j)] = Σ_a D_ai² G11_aj + 2 D_ii D_jj G12_ij + Σ_b D_bj² G22_ib,
+// summed over the (up to four) elements sharing the node (gather, no atomics).
+template <int P>
+__global__ void k_diag(DevGeom g) {
+  constexpr int Q = P + 1;
+  const long long n = (long long)g.ncol * g.nrow;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const int col = (int)(t / g.nrow), iz = (int)(t - (long long)col * g.nrow);
+  if (iz == g.nrow - 1) { g.invdiag64[t] = 0.0; g.invdiag32[t] = 0.0f; return; }
+  const double* D = c_D64 + d_off(P);
+  const double* w = c_w64 + w_off(P);
+  int exs[2], as[2], ne = 0;
+  if (col % P != 0) { exs[0] = col / P; as[0] = col % P; ne = 1; }
+  else {
+    const int exr = col / P;
+    if (exr < g.Nx) { exs[ne] = exr; as[ne] = 0; ++ne; }
+    if (g.periodic) { exs[ne] = (exr == 0 ? g.Nx - 1 : exr - 1); as[ne] = P; ++ne; }
+    else if (exr >= 1) { exs[ne] = exr - 1; as[ne] = P; ++ne; }
+  }
+  int ls[2], bs[2], nl = 0;
+  { const int l = iz / P, b = iz - l * P;
+    if (l < g.Nz) { ls[nl] = l; bs[nl] = b; ++nl; }
+    if (b == 0 && l > 0) { ls[nl] = l - 1; bs[nl] = P; ++nl; } }
+  double diag = 0.0;
+  for (int ie = 0; ie < ne; ++ie) {
+    const int ex = exs[ie], i = as[ie];
+    const double* geo = g.geo64 + (size_t)ex * Q * 4;
+    const double dxe = g.dxe[ex];
+    for (int il = 0; il < nl; ++il) {
+      const int l = ls[il], j = bs[il];
+      const double dsl = g.dsl[l], cx = dsl / dxe, cz = dxe / dsl;
+      const double sj = g.sig[l * P + j];
+      double s = 0.0;
+      for (int a = 0; a < Q; ++a) {                       // Σ_a D_ai² G11_aj
+        const double Dai = D[a * Q + i];
+        s += Dai * Dai * w[a] * w[j] * cx * geo[a * 4 + 0];
+      }
+      {                                                    // 2 D_ii D_jj G12_ij
+        const double K12 = geo[i * 4 + 2] - sj * geo[i * 4 + 3];
+        s += 2.0 * D[i * Q + i] * D[j * Q + j] * w[i] * w[j] * K12;
+      }
+      for (int b = 0; b < Q; ++b) {                       // Σ_b D_bj² G22_ib
+        const double sb = g.sig[l * P + b];
+        const double K12 = geo[i * 4 + 2] - sb * geo[i * 4 + 3];
+        const double K22 = (1.0 + K12 * K12) * geo[i * 4 + 1];
+        const double Dbj = D[b * Q + j];
+        s += Dbj * Dbj * w[i] * w[b] * cz * K22;
+      }
+      diag += s;
+    }
+  }
+  const double inv = 1.0 / diag;
+  g.invdiag64[t] = inv;
+  g.invdiag32[t] = (float)inv;
+}
+
+// ------------------------------------------------------------------------------------
+// Shared-memory layout of one CTA and the element-column apply.
+// ------------------------------------------------------------------------------------
+template <int P, class T>
+struct Smem {
+  static constexpr int Q = P + 1;
+  T* D;     // Q*Q
+  T* w;     // Q
+  T* sig;   // nrow
+  T* cxz;   // 2*Nz: Δσ_l/Δx_e, Δx_e/Δσ_l for the current element column
+  T* geo;   // 4*Q
+  T* X;     // Q*nrow
+  T* F1;    // Nz*Q*Q
+  T* F2;    // Nz*Q*Q
+  __device__ static size_t bytes(int nrow, int Nz) {
+    return sizeof(T) * (size_t)(Q * Q + Q + nrow + 2 * Nz + 4 * Q + Q * nrow + 2 * Nz * Q * Q);
+  }
+  __device__ void carve(unsigned char* base, int nrow, int Nz) {
+    T* p = reinterpret_cast<T*>(base);
+    D = p; p += Q * Q;
+    w = p; p += Q;
+    sig = p; p += nrow;
+    cxz = p; p += 2 * Nz;
+    geo = p; p += 4 * Q;
+    X = p; p += Q * nrow;
+    F1 = p; p += Nz * Q * Q;
+    F2 = p;
+  }
+  __device__ void load_tables(const DevGeom& g) {
+    const T* cD = CT<T>::D() + d_off(P);
+    const T* cw = CT<T>::w() + w_off(P);
+    for (int t = threadIdx.x; t < Q * Q; t += blockDim.x) D[t] = cD[t];
+    for (int t = threadIdx.x; t < Q; t += blockDim.x) w[t] = cw[t];
+    for (int t = threadIdx.x; t < g.nrow; t += blockDim.x) sig[t] = (T)g.sig[t];
+  }
+};
+
+template <class T> __device__ __forceinline__ const T* geo_ptr(const DevGeom& g);
+template <> __device__ __forceinline__ const double* geo_ptr<double>(const DevGeom& g) { return g.geo64; }
+template <> __device__ __forceinline__ const float* geo_ptr<float>(const DevGeom& g) { return g.geo32; }
+
+// Apply A = −𝓛 on element column ex.  `loadx(ex,a,iz)` gives the input value of local
+// column a, row iz; `store(ex,a,iz,y)` receives the element column's contribution.
+// Returns this thread's share of Σ x·(A_e x) over the element column (accumulated in T).
+template <int P, class T, class LoadX, class Store>
+__device__ __forceinline__ T apply_element_column(const DevGeom& g, Smem<P, T>& s, int ex,
+                                                       LoadX loadx, Store store) {
+  constexpr int Q = P + 1;
+  const int nrow = g.nrow, Nz = g.Nz;
+  const T* geo = geo_ptr<T>(g) + (size_t)ex * Q * 4;
+  for (int t = threadIdx.x; t < 4 * Q; t += blockDim.x) s.geo[t] = geo[t];
+  for (int t = threadIdx.x; t < Nz; t += blockDim.x) {
+    const double dxe = g.dxe[ex], dsl = g.dsl[t];
+    s.cxz[2 * t] = (T)(dsl / dxe);
+    s.cxz[2 * t + 1] = (T)(dxe / dsl);
+  }
+  for (int t = threadIdx.x; t < Q * nrow; t += blockDim.x) {
+    const int a = t / nrow, iz = t - a * nrow;
+    s.X[t] = loadx(ex, a, iz);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < Nz * Q * Q; t += blockDim.x) {
+    const int l = t / (Q * Q), rem = t - l * (Q * Q), a = rem / Q, b = rem - a * Q;
+    const T* Xrow = s.X + l * P + b;             // Xrow[c*nrow]: row l·P+b, column c
+    const T* Xcol = s.X + a * nrow + l * P;      // Xcol[c]: column a, row l·P+c
+    const T* Da = s.D + a * Q;
+    const T* Db = s.D + b * Q;
+    T ur = 0, ut = 0;
+#pragma unroll
+    for (int c = 0; c < Q; ++c) {
+      ur = fmx(Da[c], Xrow[c * nrow], ur);
+      ut = fmx(Db[c], Xcol[c], ut);
+    }
+    const T d = s.geo[a * 4 + 0], invd = s.geo[a * 4 + 1], hx = s.geo[a * 4 + 2], dxd = s.geo[a * 4 + 3];
+    const T wab = s.w[a] * s.w[b];
+    const T K12 = hx - s.sig[l * P + b] * dxd;
+    const T K22 = fmx(K12, K12, (T)1) * invd;
+    const T G11 = wab * s.cxz[2 * l] * d;
+    const T G12 = wab * K12;
+    const T G22 = wab * s.cxz[2 * l + 1] * K22;
+    s.F1[t] = fmx(G11, ur, G12 * ut);
+    s.F2[t] = fmx(G12, ur, G22 * ut);
+  }
+  __syncthreads();
+  T part = 0;
+  for (int t = threadIdx.x; t < Q * nrow; t += blockDim.x) {
+    const int a = t / nrow, iz = t - a * nrow;
+    const int l = iz / P, b = iz - l * P;
+    T y = 0;
+    if (l < Nz) {
+      const T* F1 = s.F1 + (l * Q) * Q + b;      // F1[(l*Q+a')*Q+b] = F1[a'*Q]
+      const T* F2 = s.F2 + (l * Q + a) * Q;      // F2[(l*Q+a)*Q+b']
+#pragma unroll
+      for (int c = 0; c < Q; ++c) {
+        y = fmx(s.D[c * Q + a], F1[c * Q], y);
+        y = fmx(s.D[c * Q + b], F2[c], y);
+      }
+    }
+    if (b == 0 && l > 0) {
+      const int lm = l - 1;
+      const T* F1 = s.F1 + (lm * Q) * Q + P;
+      const T* F2 = s.F2 + (lm * Q + a) * Q;
+#pragma unroll
+      for (int c = 0; c < Q; ++c) {
+        y = fmx(s.D[c * Q + a], F1[c * Q], y);
+        y = fmx(s.D[c * Q + P], F2[c], y);
+      }
+    }
+    store(ex, a, iz, y);
+    part = fmx(s.X[t], y, part);
+  }
+  __syncthreads();
+  return part;
+}
+
+// ------------------------------------------------------------------------------------
+// Stand-alone apply: y = 𝓛x (two kernels: element columns, then the edge columns).
+// ------------------------------------------------------------------------------------
+template <int P>
+__global__ void __launch_bounds__(kThreads) k_apply(DevGeom g, const double* __restrict__ x,
+                                                    double* __restrict__ q, double* __restrict__ edge) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem<P, double> s;
+  s.carve(smem_raw, g.nrow, g.Nz);
+  s.load_tables(g);
+  __syncthreads();
+  const int nrow = g.nrow;
+  for (int ex = blockIdx.x; ex < g.Nx; ex += gridDim.x) {
+    apply_element_column<P, double>(
+        g, s, ex,
+        [&](int e, int a, int iz) { return x[(size_t)col_of(g, e, a) * nrow + iz]; },
+        [&](int e, int a, int iz, double y) {
+          if (a < P || (!g.periodic && e == g.Nx - 1)) q[(size_t)col_of(g, e, a) * nrow + iz] = y;
+          else edge[(size_t)e * nrow + iz] = y;
+        });
+  }
+}
+
+
+
+
+// ------------------------------------------------------------------------------------
+// Grid barrier for the cooperative kernel, with a wall-clock limit.
+// ------------------------------------------------------------------------------------
+
+constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;  // 2 s
+
+// A team of CTAs that synchronise among themselves: the whole grid for one mesh, or the CTAs
+// assigned to one instance of a batch.
+struct Team {
+  int rank, size;        // this CTA's index in the team, number of CTAs
+  unsigned int* bar;     // {arrive, generation}, zero at launch
+  int* status;           // device status word of the instance
+  double* part;          // reduction partials [4 slots][4 values][stride]
+  int stride;
+};
+
+// Returns false (and sets ST_TIMEOUT) if the other CTAs of the team did not arrive in time;
+// the caller must then return without touching another barrier.
+static __device__ __forceinline__ bool grid_barrier(const Team& tm, int* s_flag) {
+  __syncthreads();
+  if (tm.size == 1) return true;
+  if (threadIdx.x == 0) {
+    unsigned int* bar = tm.bar;
+    volatile unsigned int* vgen = bar + 1;
+    const unsigned int gen = *vgen;
+    __threadfence();
+    const unsigned int prev = atomicAdd(bar, 1u);
+    int ok = 1;
+    if (prev == (unsigned int)tm.size - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      const unsigned long long t0 = global_ns();
+      unsigned int spins = 0;
+      while (*vgen == gen) {
+        if ((++spins & 63u) == 0 && global_ns() - t0 > kBarrierTimeoutNs) {
+          atomicOr(tm.status, ST_TIMEOUT);
+          ok = 0;
+          break;
+        }
+        __nanosleep(20);
+      }
+    }
+    __threadfence();
+    *s_flag = ok;
+  }
+  __syncthreads();
+  return *s_flag != 0;
+}
+
+// Deterministic block sum of K values of type A (all threads get the result).
+template <int K, class A>
+__device__ __forceinline__ void block_sum(A (&v)[K], double* red) {
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+  A* rr = reinterpret_cast<A*>(red);
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < K; ++k) rr[k * 32 + wid] = v[k];
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    A s = lane < nw ? rr[k * 32 + lane] : A(0);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    v[k] = s;
+  }
+  __syncthreads();
+}
+
+// Sum of K per-CTA partials part[slot][k][cta] over all CTAs, same order in every CTA.
+template <int K>
+__device__ __forceinline__ void grid_sum(const Team& tm, int slot, double (&v)[K], double* red) {
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x < 32) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const double* p = tm.part + ((size_t)slot * 4 + k) * tm.stride;
+      double s = 0.0;
+      for (int c = lane; c < tm.size; c += 32) s += __ldcg(p + c);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) red[128 + k] = s;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < K; ++k) v[k] = red[128 + k];
+  __syncthreads();
+}
+
+template <int K, class A>
+__device__ __forceinline__ void put_partials(const Team& tm, int slot, const A (&v)[K]) {
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int k = 0; k < K; ++k) tm.part[((size_t)slot * 4 + k) * tm.stride + tm.rank] = (double)v[k];
+}
+
+// ------------------------------------------------------------------------------------
+// Persistent preconditioned CG.  One level (FP64) or two levels (FP32 inner, FP64
+// residual refinement).
+// ------------------------------------------------------------------------------------
+struct Range { int e0, e1, c0, c1; };   // owned element columns and global columns
+
+static __device__ __forceinline__ Range my_range(const DevGeom& g, const Team& tm) {
+  Range r;
+  r.e0 = (int)(((long long)tm.rank * g.Nx) / tm.size);
+  r.e1 = (int)(((long long)(tm.rank + 1) * g.Nx) / tm.size);
+  r.c0 = r.e0 * g.P;
+  r.c1 = r.e1 * g.P + ((!g.periodic && r.e1 == g.Nx) ? 1 : 0);
+  return r;
+}
+
+static __device__ __forceinline__ bool owns_local_col(const DevGeom& g, int ex, int a) {
+  return a < g.P || (!g.periodic && ex == g.Nx - 1);
+}
+
+// ---- σ-separable preconditioner ----------------------------------------------------
+// M⁻¹ = (I⊗S) [Kx(d) ⊗ I + Mx(1/d) ⊗ Λ]⁻¹ (I⊗Sᵀ), the exact inverse of the Kronecker-sum
+// operator obtained from A by dropping the K12 (slope) coupling and the K12² part of K22.
+// Kx(d) = Σ_e (2/Δx) Dᵀ diag(w d) D and Mx(1/d) = Σ_e (Δx/2) diag(w/d) are 1D operators in x
+// (periodic or walls); Kσ S = Mσ S Λ is the generalized eigenproblem of the 1D σ stiffness
+// (Dirichlet at the surface) against the GLL-lumped σ mass.  Each σ-mode is a 1D SEM problem
+// in x, solved by static condensation of the element interiors and a tridiagonal (cyclic)
+// interface system.
+
+// Vectors of one Krylov level (type T).  Owned-column values live in the global arrays; `uh`
+// holds M⁻¹r on this CTA's halo column (the first column of the next CTA), which each CTA
+// rebuilds itself so that no barrier separates the preconditioner from the next apply.
+template <class T>
+struct CgVecs {
+  T* x;              // solution (FP64 level) or correction (FP32 level)
+  T* r[2];           // residual, double-buffered
+  T* s[2];           // s = A p, double-buffered
+  T* p;              // search direction (owned columns only)
+  T* u;              // u = M⁻¹ r (owned columns)
+  T* uh;             // u on the CTA's halo column, [grid][nrow]
+  T* w;              // w = A u (owned columns)
+  T* edge;           // A u contribution to the next element column's first column
+  const T* invdiag;  // Jacobi preconditioner
+};
+
+static __device__ __forceinline__ bool is_halo_col(const DevGeom& g, const Range& R, int ex, int a) {
+  return a == g.P && ex == R.e1 - 1 && !owns_local_col(g, ex, g.P);
+}
+
+// Update of the Chronopoulos–Gear recurrences on owned nodes (and, for r, on the halo column),
+// then the first part of u = M⁻¹ r:
+//   s ← w + β s,  r ← r − α s,  p ← u + β p,  x ← x + α p      (first iteration: s ← w, p ← u).
+// With update == false only the preconditioner part runs on r[cur].  Jacobi completes u here;
+// the separable preconditioner transforms the residual to the σ-eigenbasis and condenses.
+template <int P, class T>
+__device__ void cg_update(const DevGeom& g, Smem<P, T>& s, const Range& R, const Team& tm,
+                          const PrecView<T>& pv, int precond, const CgVecs<T>& V, int cur, bool update,
+                          bool first, T alpha, T beta) {
+  constexpr int Q = P + 1, Pm = P - 1;
+  const int nrow = g.nrow, nr = nrow - 1;
+  const T* r_old = V.r[cur];
+  T* r_new = V.r[cur ^ 1];
+  const T* s_old = V.s[cur];
+  T* s_new = V.s[cur ^ 1];
+  T* X = s.X;     // [Q][nr] residual of the element column
+  T* RH = s.F1;   // [Q][nr] σ-transformed residual
+  for (int ex = R.e0; ex < R.e1; ++ex) {
+    for (int t = threadIdx.x; t < Q * nr; t += blockDim.x) {
+      const int a = t / nr, j = t - a * nr;
+      const int col = col_of(g, ex, a);
+      const size_t i = (size_t)col * nrow + j;
+      const bool own = owns_local_col(g, ex, a);
+      T rv;
+      if (update) {
+        T wv = ldcg(V.w + i);
+        if (has_left_edge(g, col)) wv += ldcg(V.edge + (size_t)left_element(g, col) * nrow + j);
+        const T sv = first ? wv : fmx(beta, ldcg(s_old + i), wv);
+        rv = fmx(-alpha, sv, ldcg(r_old + i));
+        if (own) {
+          s_new[i] = sv;
+          r_new[i] = rv;
+          const T uo = V.u[i];
+          const T pn = first ? uo : fmx(beta, V.p[i], uo);
+          V.p[i] = pn;
+          V.x[i] = fmx(alpha, pn, V.x[i]);
+        }
+      } else {
+        rv = ldcg(r_old + i);
+      }
+      if (precond == PREC_JACOBI) {
+        const T uv = rv * V.invdiag[i];
+        if (own) V.u[i] = uv;
+        else if (is_halo_col(g, R, ex, a)) V.uh[(size_t)tm.rank * nrow + j] = uv;
+      } else {
+        X[t] = rv;
+      }
+    }
+    if (precond == PREC_JACOBI) continue;
+    __syncthreads();
+    for (int t = threadIdx.x; t < Q * nr; t += blockDim.x) {
+      const int a = t / nr, k = t - a * nr;
+      const T* Xa = X + a * nr;
+      T v = 0;
+      for (int j = 0; j < nr; ++j) v = fmx(pv.S[j * nr + k], Xa[j], v);
+      RH[t] = v;
+      if (owns_local_col(g, ex, a)) pv.rhat[(size_t)col_of(g, ex, a) * nr + k] = v;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < nr; k += blockDim.x) {
+      const T* Zk = pv.Z + ((size_t)k * g.Nx + ex) * 2 * Pm;
+      // the assembled residual at an interface node enters once: with the element that owns
+      // that column (its left end), plus the walls' last column with the last element
+      T l = RH[k], r = owns_local_col(g, ex, P) ? RH[P * nr + k] : T(0);
+#pragma unroll
+      for (int m = 0; m < Pm; ++m) {
+        const T f = RH[(1 + m) * nr + k];
+        l = fmx(-Zk[m], f, l);
+        r = fmx(-Zk[Pm + m], f, r);
+      }
+      pv.gL[(size_t)k * g.Nx + ex] = l;
+      pv.gR[(size_t)k * g.Nx + ex] = r;
+    }
+    __syncthreads();
+  }
+}
+
+// Interface solve per σ-mode: one warp (warp 0 of a CTA) per mode, modes spread over CTAs;
+// g_j = gL_j + gR_{j−1} assembled on the fly, then the warp-parallel tridiagonal solve.
+template <class T>
+__device__ void phase_interface(const DevGeom& g, const PrecView<T>& pv, const Team& tm) {
+  if (threadIdx.x >= 32) return;
+  const int N = pv.nif, Nx = g.Nx;
+  for (int k = tm.rank; k < pv.nr; k += tm.size) {
+    const T* gl = pv.gL + (size_t)k * Nx;
+    const T* gr = pv.gR + (size_t)k * Nx;
+    auto gfun = [&](int j) -> T {
+      if (g.periodic) return ldcg(gl + j) + ldcg(gr + (j == 0 ? Nx - 1 : j - 1));
+      return (j < Nx ? ldcg(gl + j) : T(0)) + (j > 0 ? ldcg(gr + j - 1) : T(0));
+    };
+    warp_tridiag<T>(N, gfun, pv.te + (size_t)k * N, pv.tm + (size_t)k * N, pv.tcp + (size_t)k * N,
+                    g.periodic != 0, pv.tz + (size_t)k * N, g.periodic ? pv.tvl[k] : T(0),
+                    g.periodic ? pv.tfac[k] : T(0), pv.zb + (size_t)k * N);
+  }
+}
+
+// Back-substitution of the element interiors, then u = S ẑ on owned columns and on the halo
+// column (whose modal values are interface unknowns, known to every CTA after the solve).
+template <int P, class T>
+__device__ void phase_backsub(const DevGeom& g, Smem<P, T>& s, const Range& R, const Team& tm,
+                              const PrecView<T>& pv, const CgVecs<T>& V) {
+  constexpr int Q = P + 1, Pm = P - 1;
+  const int nrow = g.nrow, nr = pv.nr, N = pv.nif;
+  T* ZH = s.F1;   // [Q][nr]
+  for (int ex = R.e0; ex < R.e1; ++ex) {
+    const int jl = ex, jr = (ex + 1 == N) ? 0 : ex + 1;
+    for (int t = threadIdx.x; t < Q * nr; t += blockDim.x) {
+      const int a = t / nr, k = t - a * nr;
+      const T zl = ldcg(pv.zb + (size_t)k * N + jl);
+      const T zr = ldcg(pv.zb + (size_t)k * N + jr);
+      T v;
+      if (a == 0) v = zl;
+      else if (a == P) v = zr;
+      else {
+        const int i = a - 1;
+        const T* Ai = pv.Aii + (((size_t)k * g.Nx + ex) * Pm + i) * Pm;
+        const T* Zk = pv.Z + ((size_t)k * g.Nx + ex) * 2 * Pm;
+        v = 0;
+#pragma unroll
+        for (int m = 0; m < Pm; ++m) v = fmx(Ai[m], pv.rhat[(size_t)(ex * P + 1 + m) * nr + k], v);
+        v = fmx(-Zk[i], zl, v);
+        v = fmx(-Zk[Pm + i], zr, v);
+      }
+      ZH[t] = v;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < Q * nr; t += blockDim.x) {
+      const int a = t / nr, j = t - a * nr;
+      const bool own = owns_local_col(g, ex, a);
+      const bool halo = is_halo_col(g, R, ex, a);
+      if (!own && !halo) continue;
+      const T* Za = ZH + a * nr;
+      const T* Sj = pv.S + j * nr;
+      T v = 0;
+      for (int k = 0; k < nr; ++k) v = fmx(Sj[k], Za[k], v);
+      if (own) V.u[(size_t)col_of(g, ex, a) * nrow + j] = v;
+      else V.uh[(size_t)tm.rank * nrow + j] = v;
+    }
+    __syncthreads();
+  }
+}
+
+// Remaining grid phases of u = M⁻¹ r after cg_update (separable: interface solve and
+// back-substitution; Jacobi: nothing but a barrier that protects w and edge).
+template <int P, class T>
+__device__ bool finish_precondition(const DevGeom& g, Smem<P, T>& s, const Range& R, const Team& tm,
+                                    const PcgArgs& PA, const PrecView<T>& pv, const CgVecs<T>& V, int* s_flag) {
+  if (PA.precond == PREC_JACOBI) return grid_barrier(tm, s_flag);
+  if (!grid_barrier(tm, s_flag)) return false;
+  phase_interface<T>(g, pv, tm);
+  if (!grid_barrier(tm, s_flag)) return false;
+  phase_backsub<P, T>(g, s, R, tm, pv, V);
+  return true;
+}
+
+// Preconditioned conjugate gradients in the Chronopoulos–Gear form: one grid reduction per
+// iteration, (γ, δ, ‖r‖²) = ((r,u), (u,Au), (r,r)) taken together with the apply w = A u.
+//   β = γ/γ_prev, α = γ/(δ − βγ/α_prev)  (first: β = 0, α = γ/δ).
+// Starts from V.x with its residual in V.r[0].  Stops when ‖r‖² ≤ target or after max_it
+// iterations.  Returns the iterations, or −1 on a barrier timeout; ‖r‖² of the final residual
+// (on thread 0) in *rr_out.
+template <int P, class T, class A>
+__device__ int cg_solve(const DevGeom& g, Smem<P, T>& s, const Range& R, const Team& tm, const PcgArgs& PA,
+                        const PrecView<T>& pv, const CgVecs<T>& V, double target, int max_it, double* red,
+                        int* s_flag, double* rr_out) {
+  const int nrow = g.nrow;
+  __shared__ T s_scal[2];
+  __shared__ int s_stop;
+  int cur = 0;
+  cg_update<P, T>(g, s, R, tm, pv, PA.precond, V, cur, false, true, T(0), T(0));
+  if (!finish_precondition<P, T>(g, s, R, tm, PA, pv, V, s_flag)) return -1;
+  int k = 0;
+  double gamma_prev = 1.0, alpha_prev = 1.0, rr = 0.0;
+  while (true) {
+    // w = A u and the three inner products (u on owned columns and the halo column)
+    const T* rc = V.r[cur];
+    A acc[3] = {A(0), A(0), A(0)};   // γ = (r,u), δ = (u,Au), (r,r)
+    for (int ex = R.e0; ex < R.e1; ++ex) {
+      acc[1] += (A)apply_element_column<P, T>(
+          g, s, ex,
+          [&](int e, int a, int iz) -> T {
+            if (iz == nrow - 1) return T(0);
+            if (is_halo_col(g, R, e, a)) return V.uh[(size_t)tm.rank * nrow + iz];
+            const size_t i = (size_t)col_of(g, e, a) * nrow + iz;
+            const T uv = V.u[i];
+            if (owns_local_col(g, e, a)) {
+              const T rv = rc[i];
+              acc[0] += (A)rv * (A)uv;
+              acc[2] += (A)rv * (A)rv;
+            }
+            return uv;
+          },
+          [&](int e, int a, int iz, T y) {
+            if (owns_local_col(g, e, a)) V.w[(size_t)col_of(g, e, a) * nrow + iz] = y;
+            else V.edge[(size_t)e * nrow + iz] = y;
+          });
+    }
+    block_sum<3, A>(acc, red);
+    put_partials<3, A>(tm, 2, acc);
+    if (!grid_barrier(tm, s_flag)) return -1;
+    double sums[3];
+    grid_sum<3>(tm, 2, sums, red);
+    if (threadIdx.x == 0) {
+      rr = sums[2];
+      int stop = 0;
+      if (!(rr == rr) || isinf(rr) || !(sums[1] == sums[1])) { atomicOr(g.status, ST_NONFINITE); stop = 1; }
+      else if (rr <= target || k >= max_it) stop = 1;
+      if (!stop) {
+        const double gam = sums[0], del = sums[1];
+        double alpha, beta;
+        if (k == 0) { beta = 0.0; alpha = gam / del; }
+        else { beta = gam / gamma_prev; alpha = gam / (del - beta * gam / alpha_prev); }
+        gamma_prev = gam;
+        alpha_prev = alpha;
+        s_scal[0] = (T)alpha;
+        s_scal[1] = (T)beta;
+      }
+      s_stop = stop;
+    }
+    __syncthreads();
+    if (s_stop) break;
+    const T alpha = s_scal[0], beta = s_scal[1];
+    cg_update<P, T>(g, s, R, tm, pv, PA.precond, V, cur, true, k == 0, alpha, beta);
+    cur ^= 1;
+    if (!finish_precondition<P, T>(g, s, R, tm, PA, pv, V, s_flag)) return -1;
+    ++k;
+  }
+  *rr_out = rr;
+  return k;
+}
+
+// FP64 residual r = b − A_II x = −(A [x; φ̃])_I on owned nodes, with ‖b‖² when asked
+// (b = −(A [0; φ̃])_I).  Returns false on a barrier timeout; rr (and bb) summed on return.
+template <int P>
+__device__ bool fp64_residual(const DevGeom& g, Smem<P, double>& s, const Range& R, const Team& tm,
+                              const PcgArgs& A, bool want_b, double* red, int* s_flag, double& rr, double& bb) {
+  const int nrow = g.nrow;
+  const double* x = A.x;
+  const double* phis = A.phis;
+  for (int ex = R.e0; ex < R.e1; ++ex) {
+    apply_element_column<P, double>(
+        g, s, ex,
+        [&](int e, int a, int iz) -> double {
+          const int col = col_of(g, e, a);
+          return iz == nrow - 1 ? phis[col] : ldcg(x + (size_t)col * nrow + iz);
+        },
+        [&](int e, int a, int iz, double y) {
+          if (owns_local_col(g, e, a)) A.q64[(size_t)col_of(g, e, a) * nrow + iz] = y;
+          else A.edge64[(size_t)e * nrow + iz] = y;
+        });
+    if (want_b)
+      apply_element_column<P, double>(
+          g, s, ex,
+          [&](int e, int a, int iz) -> double { return iz == nrow - 1 ? phis[col_of(g, e, a)] : 0.0; },
+          [&](int e, int a, int iz, double y) {
+            if (owns_local_col(g, e, a)) A.q64b[(size_t)col_of(g, e, a) * nrow + iz] = y;
+            else A.edge64b[(size_t)e * nrow + iz] = y;
+          });
+  }
+  if (!grid_barrier(tm, s_flag)) return false;
+  double acc[2] = {0.0, 0.0};
+  const int ncols = R.c1 - R.c0;
+  for (int t = threadIdx.x; t < ncols * nrow; t += blockDim.x) {
+    const int col = R.c0 + t / nrow, iz = t - (t / nrow) * nrow;
+    const size_t i = (size_t)col * nrow + iz;
+    if (iz == nrow - 1) { A.x[i] = phis[col]; continue; }
+    const bool le = has_left_edge(g, col);
+    const size_t ie = le ? (size_t)left_element(g, col) * nrow + iz : 0;
+    double qv = A.q64[i];
+    if (le) qv += ldcg(A.edge64 + ie);
+    const double rv = -qv;
+    A.r64[i] = rv;
+    acc[0] += rv * rv;
+    if (want_b) {
+      double bv = A.q64b[i];
+      if (le) bv += ldcg(A.edge64b + ie);
+      acc[1] += bv * bv;
+    }
+  }
+  block_sum<2, double>(acc, red);
+  put_partials<2, double>(tm, 0, acc);
+  if (!grid_barrier(tm, s_flag)) return false;
+  grid_sum<2>(tm, 0, acc, red);
+  rr = acc[0];
+  if (want_b) bb = acc[1];
+  return true;
+}
+
+// One Laplace solve by a team of CTAs: FP64 residual of the lifted system, then PCG in FP64, or
+// FP32 inner PCG with FP64 residual refinement (MIXED).  Returns false after a barrier timeout.
+template <int P, bool MIXED>
+__device__ bool solve_body(const DevGeom& g, const PcgArgs& A, const Team& tm, unsigned char* smem_raw,
+                           double* red, int* s_flag_p) {
+  int& s_flag = *s_flag_p;
+  const Range R = my_range(g, tm);
+  const int nrow = g.nrow;
+  Smem<P, double> s64;
+  s64.carve(smem_raw, nrow, g.Nz);
+  s64.load_tables(g);
+  double rr = 0.0, bb = 0.0;
+  if (!fp64_residual<P>(g, s64, R, tm, A, true, red, &s_flag, rr, bb)) return false;
+  const double target = A.tol * A.tol * bb;
+  int iters = 0, refinements = 0;
+  if (bb == 0.0) {
+    // φ̃ ≡ 0 on the surface: Φ = 0 is the solution.
+    const int ncols = R.c1 - R.c0;
+    for (int t = threadIdx.x; t < ncols * nrow; t += blockDim.x) {
+      const int col = R.c0 + t / nrow, iz = t - (t / nrow) * nrow;
+      if (iz != nrow - 1) A.x[(size_t)col * nrow + iz] = 0.0;
+    }
+    rr = 0.0;
+  } else if (!MIXED) {
+    const CgVecs<double> V{A.x, {A.r64, A.r64b}, {A.p64b, A.s64b}, A.p64a, A.z64, A.uh64, A.q64, A.edge64,
+                           g.invdiag64};
+    double rr_out = rr;
+    iters = cg_solve<P, double, double>(g, s64, R, tm, A, A.pv64, V, target, A.max_iter, red, &s_flag, &rr_out);
+    if (iters < 0) return false;
+    rr = rr_out;
+  } else {
+    Smem<P, float> s32;
+    s32.carve(smem_raw, nrow, g.Nz);
+    const CgVecs<float> V{A.d32, {A.r32, A.r32b}, {A.p32b, A.s32b}, A.p32a, A.z32, A.uh32, A.q32, A.edge32,
+                          g.invdiag32};
+    __shared__ int s_go;
+    while (true) {
+      if (threadIdx.x == 0) {
+        int go = rr > target && iters < A.max_iter;
+        if (!(rr == rr) || isinf(rr)) { atomicOr(g.status, ST_NONFINITE); go = 0; }
+        s_go = go;
+      }
+      __syncthreads();
+      if (!s_go) break;
+      s32.load_tables(g);
+      // inner: A δ = r in FP32 from δ = 0, to a relative residual inner_rtol (or the outer target)
+      const int ncols = R.c1 - R.c0;
+      for (int t = threadIdx.x; t < ncols * nrow; t += blockDim.x) {
+        const int col = R.c0 + t / nrow, iz = t - (t / nrow) * nrow;
+        const size_t i = (size_t)col * nrow + iz;
+        A.d32[i] = 0.f;
+        A.r32[i] = iz == nrow - 1 ? 0.f : (float)A.r64[i];
+      }
+      if (!grid_barrier(tm, &s_flag)) return false;
+      const double tgt_in = fmax(A.inner_rtol * A.inner_rtol * rr, 0.25 * target);
+      double rr_in = rr;
+      const int it = cg_solve<P, float, float>(g, s32, R, tm, A, A.pv32, V, tgt_in, A.max_iter - iters, red,
+                                               &s_flag, &rr_in);
+      if (it < 0) return false;
+      iters += it;
+      ++refinements;
+      // x += δ (FP64), then the true FP64 residual
+      for (int t = threadIdx.x; t < ncols * nrow; t += blockDim.x) {
+        const int col = R.c0 + t / nrow, iz = t - (t / nrow) * nrow;
+        if (iz == nrow - 1) continue;
+        const size_t i = (size_t)col * nrow + iz;
+        A.x[i] += (double)A.d32[i];
+      }
+      __syncthreads();
+      s64.load_tables(g);
+      if (!grid_barrier(tm, &s_flag)) return false;
+      double dummy_b = 0.0;
+      if (!fp64_residual<P>(g, s64, R, tm, A, false, red, &s_flag, rr, dummy_b)) return false;
+      if (it == 0) break;   // no progress possible
+    }
+  }
+  if (tm.rank == 0 && threadIdx.x == 0) {
+    const double rel = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+    SolveRecord* rec = A.rec;
+    rec->iterations = iters;
+    rec->refinements = refinements;
+    rec->rel_residual = rel;
+    rec->solves += 1;
+    rec->total_iterations += iters;
+    rec->total_refinements += refinements;
+    if (rel > rec->max_rel_residual) rec->max_rel_residual = rel;
+    if (rr > target) atomicOr(g.status, ST_NOT_CONVERGED);
+  }
+  return true;
+}
+
+template <int P, bool MIXED>
+__global__ void __launch_bounds__(kThreads) k_pcg(DevGeom g, PcgArgs A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[160];
+  __shared__ int s_flag;
+  const Team tm{(int)blockIdx.x, (int)gridDim.x, A.bar, g.status, A.part, A.part_stride};
+  solve_body<P, MIXED>(g, A, tm, smem_raw, red, &s_flag);
+}
+
+// ------------------------------------------------------------------------------------
+// Set-up of the separable preconditioner for the current geometry.
+// ------------------------------------------------------------------------------------
+// Block per element, one thread per mode: the mode-independent x-stiffness Kx = (2/Δx) Dᵀ
+// diag(w d) D is formed once in shared memory (FP64); each mode adds λ_k (Δx/2) diag(w/d) and
+// inverts the interior block in FP32 (a sequential FP64 Gauss–Jordan costs ~64 cycles per
+// instruction on this part).  The inverse is symmetrised, so the condensed solve is the exact
+// inverse of a symmetric operator within FP32 of E; Z = E_bi Ã_ii and the 2×2 Schur block are
+// then formed in FP64 from that same Ã_ii, which keeps the FP64 preconditioner symmetric.
+constexpr int kPrecModesPerBlock = 32;
+constexpr size_t kTriStageMax = 160 * 1024;
+
+// Mode-independent part of element ex (all threads of the block, sync after): Kx and the
+// lumped mass weights (Δx/2) w/d.
+template <int P>
+__device__ __forceinline__ void prec_elem_kx(const DevGeom& g, int ex, double* Kx, double* mw) {
+  constexpr int Q = P + 1;
+  const double* D = c_D64 + d_off(P);
+  const double* w = c_w64 + w_off(P);
+  const double* geo = g.geo64 + (size_t)ex * Q * 4;
+  const double dxe = g.dxe[ex];
+  for (int t = threadIdx.x; t < Q * Q; t += blockDim.x) {
+    const int i = t / Q, j = t - i * Q;
+    double s = 0.0;
+#pragma unroll
+    for (int a = 0; a < Q; ++a) s = fma(D[a * Q + i] * w[a] * geo[a * 4 + 0], D[a * Q + j], s);
+    Kx[t] = (2.0 / dxe) * s;
+  }
+  for (int i = threadIdx.x; i < Q; i += blockDim.x) mw[i] = 0.5 * dxe * w[i] * geo[i * 4 + 1];
+}
+
+// Mode k of element ex (one thread).
+template <int P>
+__device__ __forceinline__ void prec_elem_mode(const DevGeom& g, const PrecSetup& ps, int ex, int k,
+                                               const double* Kx, const double* mw) {
+  constexpr int Q = P + 1, Pm = P - 1;
+  const double lam = ps.lam[k];
+  float Ai[Pm][Pm], Bm[Pm][Pm];
+#pragma unroll
+  for (int i = 0; i < Pm; ++i)
+#pragma unroll
+    for (int j = 0; j < Pm; ++j) {
+      Bm[i][j] = (float)(Kx[(1 + i) * Q + 1 + j] + (i == j ? lam * mw[1 + i] : 0.0));
+      Ai[i][j] = (i == j) ? 1.f : 0.f;
+    }
+#pragma unroll
+  for (int c = 0; c < Pm; ++c) {
+    const float inv = 1.f / Bm[c][c];
+#pragma unroll
+    for (int j = 0; j < Pm; ++j) { Bm[c][j] *= inv; Ai[c][j] *= inv; }
+#pragma unroll
+    for (int r = 0; r < Pm; ++r) {
+      if (r == c) continue;
+      const float f = Bm[r][c];
+#pragma unroll
+      for (int j = 0; j < Pm; ++j) { Bm[r][j] = fmaf(-f, Bm[c][j], Bm[r][j]); Ai[r][j] = fmaf(-f, Ai[c][j], Ai[r][j]); }
+    }
+  }
+  const size_t base = (size_t)k * g.Nx + ex;
+  double* A64 = ps.Aii64 + base * Pm * Pm;
+  float* A32 = ps.Aii32 + base * Pm * Pm;
+#pragma unroll
+  for (int i = 0; i < Pm; ++i)
+#pragma unroll
+    for (int j = 0; j < Pm; ++j) {
+      const float v = 0.5f * (Ai[i][j] + Ai[j][i]);
+      A32[i * Pm + j] = v;
+      A64[i * Pm + j] = (double)v;
+    }
+  double Z0[Pm], Z1[Pm];
+#pragma unroll
+  for (int i = 0; i < Pm; ++i) {
+    double a0 = 0.0, a1 = 0.0;
+#pragma unroll
+    for (int m = 0; m < Pm; ++m) {
+      const double am = (double)(0.5f * (Ai[m][i] + Ai[i][m]));
+      a0 = fma(Kx[1 + m], am, a0);
+      a1 = fma(Kx[P * Q + 1 + m], am, a1);
+    }
+    Z0[i] = a0; Z1[i] = a1;
+  }
+  double S00 = Kx[0] + lam * mw[0], S01 = Kx[P], S11 = Kx[P * Q + P] + lam * mw[P];
+#pragma unroll
+  for (int i = 0; i < Pm; ++i) {
+    S00 -= Z0[i] * Kx[(1 + i) * Q];
+    S01 -= Z0[i] * Kx[(1 + i) * Q + P];
+    S11 -= Z1[i] * Kx[(1 + i) * Q + P];
+  }
+  double* Z64 = ps.Z64 + base * 2 * Pm;
+  float* Z32 = ps.Z32 + base * 2 * Pm;
+#pragma unroll
+  for (int i = 0; i < Pm; ++i) {
+    Z64[i] = Z0[i]; Z64[Pm + i] = Z1[i];
+    Z32[i] = (float)Z0[i]; Z32[Pm + i] = (float)Z1[i];
+  }
+  ps.schur[base * 3 + 0] = S00;
+  ps.schur[base * 3 + 1] = S01;
+  ps.schur[base * 3 + 2] = S11;
+}
+
+template <int P>
+__global__ void __launch_bounds__(kPrecModesPerBlock) k_prec_elem(DevGeom g, PrecSetup ps) {
+  constexpr int Q = P + 1;
+  __shared__ double Kx[Q * Q];
+  __shared__ double mw[Q];
+  prec_elem_kx<P>(g, blockIdx.x, Kx, mw);
+  __syncthreads();
+  const int k = blockIdx.y * blockDim.x + threadIdx.x;
+  if (k < ps.nr) prec_elem_mode<P>(g, ps, blockIdx.x, k, Kx, mw);
+}
+
+// One warp per mode: interface tridiagonal d_j = S00(j) + S11(j−1), e_j = S01(j) and its Thomas
+// pivots.  The pivot recurrence m_j = 1/(d_j − e_{j−1}² m_{j−1}) runs on lane 0 in FP32 from
+// shared memory (a sequential FP64 chain costs ~64 cycles per instruction on this part); the
+// FP64 factors are taken from those pivots, m⁶⁴ = m³², c' = e m, which makes them the exact
+// LDLᵀ factors of a symmetric tridiagonal within FP32 of the true one.  The Sherman–Morrison
+// vector T'⁻¹u of the periodic closure (γ = −d_0, u = (γ,0,…,0,e_{N−1}), v = (1,0,…,0,
+// e_{N−1}/γ)) is then solved with the warp-parallel tridiagonal solver and the same factors,
+// once in FP64 and once in FP32.  Staged in shared memory when 3·nif values fit, otherwise the
+// recurrence reads and writes the destination arrays directly.
+// `stage_sm`: 2·nif floats of shared memory, or nullptr to run the recurrence on the
+// destination arrays.  Called by one full warp.
+static __device__ void prec_tri_mode(const DevGeom& g, const PrecSetup& ps, int k, float* stage_sm) {
+  const bool staged = stage_sm != nullptr;
+  const int N = ps.nif, Nx = g.Nx;
+  const double* sc = ps.schur + (size_t)k * Nx * 3;
+  double* te = ps.te64 + (size_t)k * N;
+  double* tm = ps.tm64 + (size_t)k * N;
+  double* tcp = ps.tcp64 + (size_t)k * N;
+  double* tz = ps.tz64 + (size_t)k * N;
+  float* te32 = ps.te32 + (size_t)k * N;
+  float* tm32 = ps.tm32 + (size_t)k * N;
+  float* tcp32 = ps.tcp32 + (size_t)k * N;
+  float* tz32 = ps.tz32 + (size_t)k * N;
+  const double corner = g.periodic ? sc[(Nx - 1) * 3 + 1] : 0.0;
+  float* dd = staged ? stage_sm : tm32;     // modified diagonal (FP32)
+  float* ee = staged ? dd + N : te32;
+  for (int j = (threadIdx.x & 31); j < N; j += 32) {
+    double d;
+    if (g.periodic) d = sc[j * 3 + 0] + sc[(j == 0 ? Nx - 1 : j - 1) * 3 + 2];
+    else d = (j < Nx ? sc[j * 3 + 0] : 0.0) + (j > 0 ? sc[(j - 1) * 3 + 2] : 0.0);
+    const double e = (j < N - 1) ? sc[j * 3 + 1] : 0.0;
+    te[j] = e;
+    dd[j] = (float)d;
+    ee[j] = (float)e;
+  }
+  __syncwarp();
+  const double gamma = g.periodic ? -(double)(sc[0] + sc[(Nx - 1) * 3 + 2]) : 0.0;
+  if ((threadIdx.x & 31) == 0) {
+    if (g.periodic) {
+      dd[0] = (float)(2.0 * (sc[0] + sc[(Nx - 1) * 3 + 2]));
+      dd[N - 1] = (float)((double)dd[N - 1] - corner * corner / gamma);
+    }
+    float cp_prev = 0.f, e_prev = 0.f;
+    for (int j = 0; j < N; ++j) {
+      const float m = 1.f / (j == 0 ? dd[0] : fmaf(-e_prev, cp_prev, dd[j]));
+      const float e = ee[j];
+      dd[j] = m;                 // pivots overwrite the diagonal
+      cp_prev = e * m;
+      e_prev = e;
+    }
+  }
+  __syncwarp();
+  for (int j = (threadIdx.x & 31); j < N; j += 32) {
+    const float m = dd[j], e32 = ee[j];
+    tm[j] = (double)m;
+    tcp[j] = te[j] * (double)m;
+    tm32[j] = m;
+    te32[j] = e32;
+    tcp32[j] = e32 * m;
+  }
+  __syncwarp();
+  if (g.periodic) {
+    auto u64 = [&](int j) -> double { return j == 0 ? gamma : (j == N - 1 ? corner : 0.0); };
+    warp_tridiag<double>(N, u64, te, tm, tcp, false, (const double*)nullptr, 0.0, 0.0, tz);
+    auto u32 = [&](int j) -> float { return j == 0 ? (float)gamma : (j == N - 1 ? (float)corner : 0.f); };
+    warp_tridiag<float>(N, u32, te32, tm32, tcp32, false, (const float*)nullptr, 0.f, 0.f, tz32);
+    if ((threadIdx.x & 31) == 0) {
+      const double vl = corner / gamma;
+      ps.tvl64[k] = vl;
+      ps.tfac64[k] = 1.0 / (1.0 + tz[0] + vl * tz[N - 1]);
+      ps.tvl32[k] = (float)vl;
+      ps.tfac32[k] = 1.f / (1.f + tz32[0] + (float)vl * tz32[N - 1]);
+    }
+  } else {
+    for (int j = (threadIdx.x & 31); j < N; j += 32) { tz[j] = 0.0; tz32[j] = 0.f; }
+  }
+}
+
+static __global__ void __launch_bounds__(32) k_prec_tri(DevGeom g, PrecSetup ps, int staged) {
+  extern __shared__ __align__(16) double tri_sm[];
+  prec_tri_mode(g, ps, blockIdx.x, staged ? reinterpret_cast<float*>(tri_sm) : nullptr);
+}
+
+// ------------------------------------------------------------------------------------
+// Fused RK stage: one cooperative launch runs a whole RK4 stage for one or many instances of
+// order P.  Each instance is served by a team of CTAs (barriers and reductions are per team):
+//   σ-geometry → preconditioner set-up → Laplace solve → w̃ and M'-projected ∂x of η, φ̃ →
+//   over-integrated Zakharov right-hand side and its M' solve → relaxation source → RK4 update
+//   (→ modal filter after stage 4).
+// ------------------------------------------------------------------------------------
+constexpr int kStageWarps = kThreads / 32;
+
+template <int P, bool MIXED>
+__device__ void stage_body(Instance& I, const Team& tm, int stage, int step, unsigned char* smem_raw,
+                           double* red, int* s_flag, double (*sh)[kSurfWarpScratch], double* Kx, double* mw) {
+  constexpr int Q = P + 1;
+  const DevGeom& g = I.g;
+  const SurfTables& t = I.st;
+  const Range R = my_range(g, tm);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const double* ein = stage == 1 ? I.eta : (stage == 3 ? I.s1e : I.s0e);
+  const double* pin = stage == 1 ? I.phis : (stage == 3 ? I.s1p : I.s0p);
+  double* eout = stage == 2 ? I.s1e : I.s0e;   // stage inputs of the next stage (not used at stage 4)
+  double* pout = stage == 2 ? I.s1p : I.s0p;
+  const double t0 = I.tstart + step * I.dt;
+  const double time = t0 + (stage == 1 ? 0.0 : (stage == 4 ? I.dt : 0.5 * I.dt));
+  const int ne = R.e1 - R.e0, nc = R.c1 - R.c0;
+
+  // σ-geometry of the owned element columns
+  for (int q = threadIdx.x; q < ne * Q; q += blockDim.x) geometry_item<P>(g, ein, R.e0 * Q + q);
+  __syncthreads();
+  // preconditioner: condensation of the owned elements for every mode, then interface pivots
+  for (int ex = R.e0; ex < R.e1; ++ex) {
+    prec_elem_kx<P>(g, ex, Kx, mw);
+    __syncthreads();
+    for (int k = threadIdx.x; k < I.ps.nr; k += blockDim.x) prec_elem_mode<P>(g, I.ps, ex, k, Kx, mw);
+    __syncthreads();
+  }
+  if (!grid_barrier(tm, s_flag)) return;
+  if (warp == 0) {
+    float* stg = 2 * I.ps.nif <= 2 * kSurfWarpScratch ? reinterpret_cast<float*>(sh[0]) : nullptr;
+    for (int k = tm.rank; k < I.ps.nr; k += tm.size) prec_tri_mode(g, I.ps, k, stg);
+  }
+  if (!grid_barrier(tm, s_flag)) return;
+  // Laplace solve, warm-started from the previous stage's potential
+  if (threadIdx.x == 0) I.pa.phis = pin;
+  __syncthreads();
+  if (!solve_body<P, MIXED>(g, I.pa, tm, smem_raw, red, s_flag)) return;
+  // w̃ on owned columns; element S_x of η and φ̃; condensation of M'
+  for (int col = R.c0 + warp; col < R.c1; col += nw) wsurf_column(t, I.pa.x, ein, I.wt, col, lane);
+  for (int q = threadIdx.x; q < 2 * ne * Q; q += blockDim.x) {
+    const int fld = q / (ne * Q), r = q - fld * ne * Q;
+    sx_item(t, ein, pin, I.R, fld * t.Nx * Q + R.e0 * Q + r);
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < 2 * ne; q += blockDim.x) {
+    const int rh = q / ne, ex = R.e0 + (q - rh * ne);
+    mass1d_condense(t, I.R, 2, I.scr, rh * t.Nx + ex);
+  }
+  if (!grid_barrier(tm, s_flag)) return;
+  if (warp == 0)
+    for (int rh = tm.rank; rh < 2; rh += tm.size) mass1d_interface(t, 2, I.scr, rh);
+  if (!grid_barrier(tm, s_flag)) return;
+  for (int q = threadIdx.x; q < 2 * nc; q += blockDim.x) {
+    const int rh = q / nc, col = R.c0 + (q - rh * nc);
+    mass1d_backsub(t, I.R, 2, rh == 0 ? I.etax : I.phisx, I.scr, rh, col);
+  }
+  if (!grid_barrier(tm, s_flag)) return;
+  // over-integrated Zakharov right-hand side of the owned elements and its M' solve
+  for (int ex = R.e0 + warp; ex < R.e1; ex += nw) zak_element(t, ein, I.etax, I.phisx, I.wt, I.R, ex, lane, sh[warp]);
+  __syncthreads();
+  for (int q = threadIdx.x; q < 2 * ne; q += blockDim.x) {
+    const int rh = q / ne, ex = R.e0 + (q - rh * ne);
+    mass1d_condense(t, I.R, 2, I.scr, rh * t.Nx + ex);
+  }
+  if (!grid_barrier(tm, s_flag)) return;
+  if (warp == 0)
+    for (int rh = tm.rank; rh < 2; rh += tm.size) mass1d_interface(t, 2, I.scr, rh);
+  if (!grid_barrier(tm, s_flag)) return;
+  for (int q = threadIdx.x; q < 2 * nc; q += blockDim.x) {
+    const int rh = q / nc, col = R.c0 + (q - rh * nc);
+    mass1d_backsub(t, I.R, 2, rh == 0 ? I.ke : I.kp, I.scr, rh, col);
+  }
+  __syncthreads();
+  // relaxation source and the RK4 bookkeeping on owned columns
+  for (int col = R.c0 + threadIdx.x; col < R.c1; col += blockDim.x) {
+    if (I.relax) relax_column(t, ein, pin, time, 1.0 / I.tau, I.ke, I.kp, col);
+    rk4_item(stage, I.dt, I.eta, I.phis, I.ke, I.kp, I.ae, I.ap, eout, pout, col);
+  }
+  if (stage == 4 && t.filter_on) {
+    if (!grid_barrier(tm, s_flag)) return;
+    for (int ex = R.e0 + warp; ex < R.e1; ex += nw) filter_element(t, I.eta, I.phis, ex, lane, sh[warp]);
+  }
+}
+
+template <int P, bool MIXED>
+__global__ void __launch_bounds__(kThreads) k_stage(StageArgs B) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[160];
+  __shared__ int s_flag;
+  __shared__ __align__(16) double sh[kStageWarps][kSurfWarpScratch];
+  __shared__ double Kx[(P + 1) * (P + 1)];
+  __shared__ double mw[P + 1];
+  __shared__ __align__(16) Instance I;
+  const int ii = B.cta_inst[blockIdx.x];
+  {
+    const unsigned int* src = reinterpret_cast<const unsigned int*>(B.inst + ii);
+    unsigned int* dst = reinterpret_cast<unsigned int*>(&I);
+    for (int q = threadIdx.x; q < (int)(sizeof(Instance) / 4); q += blockDim.x) dst[q] = src[q];
+  }
+  __syncthreads();
+  const Team tm{(int)blockIdx.x - I.team0, I.nteam, B.bars + 2 * ii, I.g.status, I.pa.part, I.pa.part_stride};
+  stage_body<P, MIXED>(I, tm, B.stage, B.step, smem_raw, red, &s_flag, sh, Kx, mw);
+}
+
+
+// ------------------------------------------------------------------------------------
+// Host entry points for one order P (explicitly instantiated per order in kernels_order.cu).
+// ------------------------------------------------------------------------------------
+template <int P>
+cudaError_t upload_tables_impl(const double* D64, const double* w64) {
+  float D32[kDTotal], w32[kWTotal];
+  for (int i = 0; i < kDTotal; ++i) D32[i] = static_cast<float>(D64[i]);
+  for (int i = 0; i < kWTotal; ++i) w32[i] = static_cast<float>(w64[i]);
+  cudaError_t e;
+  if ((e = cudaMemcpyToSymbol(c_D64, D64, sizeof(double) * kDTotal)) != cudaSuccess) return e;
+  if ((e = cudaMemcpyToSymbol(c_D32, D32, sizeof(float) * kDTotal)) != cudaSuccess) return e;
+  if ((e = cudaMemcpyToSymbol(c_w64, w64, sizeof(double) * kWTotal)) != cudaSuccess) return e;
+  return cudaMemcpyToSymbol(c_w32, w32, sizeof(float) * kWTotal);
+}
+
+template <int P>
+cudaError_t launch_geometry_impl(const DevGeom& g, const double* eta, bool with_diag, cudaStream_t s) {
+  const int n1 = g.Nx * (P + 1);
+  k_geometry<P><<<(n1 + 127) / 128, 128, 0, s>>>(g, eta);
+  count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || !with_diag) return e;
+  const long long n = (long long)g.ncol * g.nrow;
+  k_diag<P><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t launch_apply_elem_impl(const DevGeom& g, const double* x, double* q, double* edge, cudaStream_t s) {
+  const size_t smem = apply_smem_bytes(P, g.nrow, g.Nz, sizeof(double));
+  const int grid = g.Nx < 4096 ? g.Nx : 4096;
+  cudaError_t e = cudaFuncSetAttribute(k_apply<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+  if (e != cudaSuccess) return e;
+  k_apply<P><<<grid, kThreads, smem, s>>>(g, x, q, edge);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t pcg_occupancy_impl(int mixed, size_t smem, int* per_sm) {
+  const void* fn = mixed ? (const void*)k_pcg<P, true> : (const void*)k_pcg<P, false>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, fn, kThreads, smem);
+}
+
+template <int P>
+cudaError_t launch_pcg_impl(int mixed, const DevGeom& g, const PcgArgs& a, int grid, size_t smem, cudaStream_t s) {
+  DevGeom gg = g;
+  PcgArgs aa = a;
+  void* args[] = {&gg, &aa};
+  const void* fn = mixed ? (const void*)k_pcg<P, true> : (const void*)k_pcg<P, false>;
+  return cudaLaunchCooperativeKernel(fn, grid, kThreads, args, smem, s);
+}
+
+template <int P>
+cudaError_t launch_prec_setup_impl(const DevGeom& g, const PrecSetup& ps, cudaStream_t s) {
+  const dim3 grid_e(g.Nx, (ps.nr + kPrecModesPerBlock - 1) / kPrecModesPerBlock);
+  k_prec_elem<P><<<grid_e, kPrecModesPerBlock, 0, s>>>(g, ps);
+  count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const size_t bytes = (size_t)2 * ps.nif * sizeof(float);
+  const int staged = bytes <= kTriStageMax ? 1 : 0;
+  if (staged) {
+    e = cudaFuncSetAttribute(k_prec_tri, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTriStageMax);
+    if (e != cudaSuccess) return e;
+  }
+  k_prec_tri<<<ps.nr, 32, staged ? bytes : 0, s>>>(g, ps, staged);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t stage_occupancy_impl(int mixed, size_t smem, int* per_sm) {
+  const void* fn = mixed ? (const void*)k_stage<P, true> : (const void*)k_stage<P, false>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, fn, kThreads, smem);
+}
+
+template <int P>
+cudaError_t launch_stage_impl(int mixed, const StageArgs& a, int grid, size_t smem, cudaStream_t s) {
+  StageArgs aa = a;
+  void* args[] = {&aa};
+  const void* fn = mixed ? (const void*)k_stage<P, true> : (const void*)k_stage<P, false>;
+  return cudaLaunchCooperativeKernel(fn, grid, kThreads, args, smem, s);
+}
+
+}  // namespace semgb

@@ -138,7 +138,51 @@ struct SurfTables {
   const double* wave;     // [4][ncomp]: a, ω, k, θ
 };
 
+// One instance (mesh + state) of a fused RK stage launch.
+struct Instance {
+  DevGeom g;
+  SurfTables st;
+  PcgArgs pa;            // pa.x = the mesh's potential (warm start), pa.phis set per stage
+  PrecSetup ps;
+  double *eta, *phis;    // state, updated at stage 4
+  double *s0e, *s0p;     // stage inputs (double-buffered: stages 2 and 4 read s0, stage 3 reads s1)
+  double *s1e, *s1p;
+  double *ke, *kp, *ae, *ap;
+  double *wt, *etax, *phisx, *R, *scr;
+  double tstart, dt, tau;
+  int team0, nteam;      // first CTA and number of CTAs of this instance's team
+  int relax;
+  int pad;
+};
+
+struct StageArgs {
+  const Instance* inst;  // device array
+  const int* cta_inst;   // CTA → instance
+  unsigned int* bars;    // 2 per instance, zero at launch
+  int stage;             // 1..4
+  int step;              // steps since tstart
+};
+
+// ---- per-order entry points (laplace_device.cuh, instantiated in kernels_order.cu) ----
+template <int P> cudaError_t upload_tables_impl(const double* D64, const double* w64);
+template <int P> cudaError_t launch_geometry_impl(const DevGeom& g, const double* eta, bool with_diag,
+                                                  cudaStream_t s);
+template <int P> cudaError_t launch_apply_elem_impl(const DevGeom& g, const double* x, double* q, double* edge,
+                                                    cudaStream_t s);
+template <int P> cudaError_t pcg_occupancy_impl(int mixed, size_t smem, int* per_sm);
+template <int P> cudaError_t launch_pcg_impl(int mixed, const DevGeom& g, const PcgArgs& a, int grid, size_t smem,
+                                             cudaStream_t s);
+template <int P> cudaError_t launch_prec_setup_impl(const DevGeom& g, const PrecSetup& ps, cudaStream_t s);
+template <int P> cudaError_t stage_occupancy_impl(int mixed, size_t smem, int* per_sm);
+template <int P> cudaError_t launch_stage_impl(int mixed, const StageArgs& a, int grid, size_t smem,
+                                               cudaStream_t s);
+
 // ---- launchers (kernels_laplace.cu) ----
+// Fused RK stage for instances of order P: capacity (CTAs per SM) at a given dynamic smem,
+// and the cooperative launch.
+cudaError_t stage_occupancy(int P, int mixed, size_t smem, int* per_sm);
+size_t stage_smem_bytes(int P, int nrow, int Nz);
+cudaError_t launch_stage(int P, int mixed, const StageArgs& a, int grid, size_t smem, cudaStream_t s);
 cudaError_t upload_line_tables(const double* D64, const double* w64);  // packed, all orders
 // σ-geometry per element-local column; with_diag also builds the Jacobi diagonal.
 cudaError_t launch_geometry(const DevGeom& g, const double* eta, bool with_diag, cudaStream_t s);
