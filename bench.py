@@ -326,6 +326,38 @@ def c3_batch(dev, count: int = 512, steps: int = 3):
     return out
 
 
+def c5_serving(rate: float = 1000.0, count: int = 400):
+    """C5: Poisson stream of Laplace solves and 10-step RK4 runs (seed 0) served by the
+    continuous-batching loop (mixed precision and FP64, 150 GB admission budget), against the
+    same requests run one after another on the plain FP64 path.  Wall-clock from the first
+    arrival; latency = completion − arrival."""
+    import numpy as np
+    from paper_1512_02548_gb300.serve import GpuExecutor, Request, Server, sequential
+    from sem_workloads import c5_requests, initial_state
+    base = []
+    for i, (kind, t, wl, ns) in enumerate(c5_requests(rate, count, 0)):
+        e0, p0 = initial_state(wl, column_positions(wl), np.full(wl.ncol, wl.depth))
+        base.append(Request(i, kind, wl, e0, p0, ns, t))
+
+    def fresh():
+        return [Request(r.rid, r.kind, r.wl, r.eta0, r.phis0, r.nsteps, r.arrival) for r in base]
+
+    Server(GpuExecutor("mixed"), 150 << 30).run(fresh()[:8])          # warm-up
+    out = {"rate_per_s": rate, "requests": count, "laplace_share": sum(r.kind == "laplace" for r in base) / count,
+           "nodes_total": int(sum(r.wl.n_nodes for r in base))}
+    for prec in ("mixed", "fp64"):
+        s = Server(GpuExecutor(prec), 150 << 30, keep_results=False).run(fresh())
+        out[f"served_{prec}"] = {k: s[k] for k in ("p50_ms", "p99_ms", "laplace_dof_per_s", "rk4_steps_per_s",
+                                                   "requests_per_s", "wall_s", "ticks", "peak_active",
+                                                   "completed", "failed")}
+    s = sequential(fresh(), "fp64")
+    out["sequential_fp64"] = {k: s[k] for k in ("p50_ms", "p99_ms", "laplace_dof_per_s", "rk4_steps_per_s",
+                                               "requests_per_s", "wall_s", "completed", "failed")}
+    out["served_mixed_dof_speedup_vs_sequential_fp64"] = (out["served_mixed"]["laplace_dof_per_s"] /
+                                                          out["sequential_fp64"]["laplace_dof_per_s"])
+    return out
+
+
 def measured_peaks() -> dict:
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -451,6 +483,8 @@ def run_gpu(args):
         line["apply_long_tank"] = apply_roofline(dev)
     if not args.no_c3:
         line["c3_uneven_batch"] = c3_batch(dev)
+    if not args.no_c5:
+        line["c5_serving"] = c5_serving(args.c5_rate, args.c5_requests)
     if rank == 0 and not args.no_cpu_baseline:
         try:
             res = oracle_subprocess(args.cpu_stages)
@@ -498,6 +532,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-apply-roofline", action="store_true")
     ap.add_argument("--no-c3", action="store_true")
+    ap.add_argument("--no-c5", action="store_true")
+    ap.add_argument("--c5-rate", type=float, default=1000.0)
+    ap.add_argument("--c5-requests", type=int, default=400)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -233,6 +233,19 @@ int sem_batch_info(const sem_batch* b, int* launches_per_stage, int* ctas);
  * instance's error is returned (its index in the message). */
 int sem_batch_rk4_step(sem_batch* b, double* const* eta_d, double* const* phis_d, double* t_h,
                        const double* dt_h, int nsteps, void* stream);
+/* One Laplace solve per instance in one cooperative launch per (order, precision) group:
+ * the σ-geometry and preconditioner of mesh i are rebuilt for eta_d[i] (as sem_update_geometry
+ * does), then 𝓛Φ = 0 with Φ = φ̃ = phis_d[i] at the surface is solved as sem_laplace_solve
+ * does.  Phi_d[i]: device, n_i values; on entry its interior values are the initial guess, on
+ * exit the solution.  eta_d[i], phis_d[i]: device, Ncol_i.  Synchronises; the first failing
+ * instance's error is returned (its index in the message). */
+int sem_batch_laplace_solve(sem_batch* b, const double* const* eta_d, const double* const* phis_d,
+                            double* const* Phi_d, void* stream);
+/* Per-instance result of the last sem_batch_rk4_step or sem_batch_laplace_solve:
+ * codes_h[i] (host, one per instance) = SEM_OK or the instance's own error code, so a caller
+ * can fail one instance and keep the others (each instance's state is advanced or solved
+ * independently of the others' outcome).  All SEM_OK before the first call. */
+int sem_batch_status(const sem_batch* b, int* codes_h);
 
 /* Solver counters accumulated on the device; reading synchronises the stream. */
 int sem_get_counters(sem_mesh* m, sem_counters* c, void* stream);

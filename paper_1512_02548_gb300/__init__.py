@@ -19,6 +19,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libsem_gb300.so")
 
 SEM_OK = 0
+(SEM_ERR_INVALID_ARG, SEM_ERR_OOM, SEM_ERR_CUDA, SEM_ERR_NOT_CONVERGED, SEM_ERR_NONFINITE,
+ SEM_ERR_TIMEOUT) = range(1, 7)
 SEM_ERRORS = {1: "SEM_ERR_INVALID_ARG", 2: "SEM_ERR_OOM", 3: "SEM_ERR_CUDA",
               4: "SEM_ERR_NOT_CONVERGED", 5: "SEM_ERR_NONFINITE", 6: "SEM_ERR_TIMEOUT"}
 SEM_PREC_FP64, SEM_PREC_MIXED = 0, 1
@@ -29,7 +31,7 @@ EXPORTED = ("sem_mesh_create", "sem_mesh_destroy", "sem_mesh_footprint", "sem_me
             "sem_recover_gradient", "sem_zakharov_rhs", "sem_set_wave_input", "sem_apply_filter", "sem_rk4_step",
             "sem_rk4_step_host", "sem_get_counters", "sem_reset_counters", "sem_enable_timing",
             "sem_get_timing", "sem_batch_create", "sem_batch_destroy", "sem_batch_info",
-            "sem_batch_rk4_step", "sem_launch_count", "sem_last_error")
+            "sem_batch_rk4_step", "sem_batch_laplace_solve", "sem_batch_status", "sem_launch_count", "sem_last_error")
 
 
 class sem_params(ctypes.Structure):
@@ -102,6 +104,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sem_batch_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     lib.sem_batch_rk4_step.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_double), ip, vp]
+    lib.sem_batch_laplace_solve.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
+    lib.sem_batch_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     lib.sem_launch_count.restype = ctypes.c_int64
     lib.sem_launch_count.argtypes = []
     lib.sem_last_error.restype = ctypes.c_char_p
@@ -293,7 +297,7 @@ class Mesh:
 
 
 class Batch:
-    """Many meshes stepped together (``sem_batch``): one fused launch per RK stage and order."""
+    """Many meshes stepped or solved together (``sem_batch``): one fused launch per RK stage and order."""
 
     def __init__(self, meshes):
         lib = load_library()
@@ -316,6 +320,21 @@ class Batch:
         t = (ctypes.c_double * n)(*(ts if ts is not None else [0.0] * n))
         _check(load_library().sem_batch_rk4_step(self._h, e, p, t, d, int(nsteps), _stream()))
         return list(t)
+
+    def laplace_solve(self, etas, phises, Phis):
+        """One Laplace solve per instance (geometry rebuilt for etas[i]); Phis[i] in/out."""
+        n = len(self.meshes)
+        e = (ctypes.c_void_p * n)(*[_ptr(x).value for x in etas])
+        p = (ctypes.c_void_p * n)(*[_ptr(x).value for x in phises])
+        f = (ctypes.c_void_p * n)(*[_ptr(x).value for x in Phis])
+        _check(load_library().sem_batch_laplace_solve(self._h, e, p, f, _stream()))
+        return Phis
+
+    def status(self) -> list[int]:
+        """Per-instance SEM error codes of the last step or solve (0 = ok)."""
+        c = (ctypes.c_int * len(self.meshes))()
+        _check(load_library().sem_batch_status(self._h, c))
+        return list(c)
 
     def close(self):
         if getattr(self, "_h", None):

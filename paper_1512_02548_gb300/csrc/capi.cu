@@ -128,11 +128,14 @@ struct BatchLaunch {
   Instance* inst_d = nullptr;
   int* cta_d = nullptr;
   unsigned int* bars_d = nullptr;
+  int* status_d = nullptr;           // gathered status words of the members
   std::vector<Instance> inst_h;
+  std::vector<int> status_h;
 };
 
 struct sem_batch {
   std::vector<sem_mesh*> meshes;
+  std::vector<int> codes;            // per-instance error code of the last step or solve
   std::vector<BatchLaunch> launches;
   int device = 0;
   unsigned char* pool = nullptr;
@@ -140,18 +143,39 @@ struct sem_batch {
 
 namespace {
 
-int read_status(sem_mesh* m, cudaStream_t s) {
-  int st = 0;
-  CUDA_TRY(cudaMemcpyAsync(&st, m->g.status, sizeof(int), cudaMemcpyDeviceToHost, s));
-  CUDA_TRY(cudaStreamSynchronize(s));
+// Error code of a device status word (no message).
+int status_code(int st) {
   if (st == 0) return SEM_OK;
-  CUDA_TRY(cudaMemsetAsync(m->g.status, 0, sizeof(int), s));
-  CUDA_TRY(cudaStreamSynchronize(s));
+  if (st & ST_TIMEOUT) return SEM_ERR_TIMEOUT;
+  if (st & (ST_BAD_DEPTH | ST_NONFINITE)) return SEM_ERR_NONFINITE;
+  if (st & ST_NOT_CONVERGED) return SEM_ERR_NOT_CONVERGED;
+  return SEM_ERR_CUDA;
+}
+
+int status_error(int st) {
+  if (st == 0) return SEM_OK;
   if (st & ST_TIMEOUT) return fail(SEM_ERR_TIMEOUT, "a grid barrier of the Krylov kernel timed out");
   if (st & ST_BAD_DEPTH) return fail(SEM_ERR_NONFINITE, "water depth d = eta + h is not positive and finite");
   if (st & ST_NONFINITE) return fail(SEM_ERR_NONFINITE, "non-finite residual in the Laplace solve");
   if (st & ST_NOT_CONVERGED) return fail(SEM_ERR_NOT_CONVERGED, "Laplace solve reached max_iter above tol");
   return fail(SEM_ERR_CUDA, "unknown device status");
+}
+
+// After a failed step the mesh's warm-start potential may hold non-finite values; the next
+// solve on this mesh starts from zero instead.
+cudaError_t reset_warm_start(sem_mesh* m, cudaStream_t s) {
+  return cudaMemsetAsync(m->Phi, 0, sizeof(double) * (size_t)m->n, s);
+}
+
+int read_status(sem_mesh* m, cudaStream_t s) {
+  int st = 0;
+  CUDA_TRY(cudaMemcpyAsync(&st, m->g.status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if (st == 0) return SEM_OK;
+  CUDA_TRY(reset_warm_start(m, s));
+  CUDA_TRY(cudaMemsetAsync(m->g.status, 0, sizeof(int), s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return status_error(st);
 }
 
 cudaError_t take_event(sem_mesh* m, cudaEvent_t* ev) {
@@ -857,7 +881,8 @@ int sem_batch_create(sem_mesh* const* meshes, int count, sem_batch** out) {
       L.grid = acc;
       total += ((sizeof(Instance) * L.members.size() + 255) & ~size_t(255)) +
                ((sizeof(int) * (size_t)L.grid + 255) & ~size_t(255)) +
-               ((sizeof(unsigned) * 2 * L.members.size() + 255) & ~size_t(255));
+               ((sizeof(unsigned) * 2 * L.members.size() + 255) & ~size_t(255)) +
+               ((sizeof(int) * L.members.size() + 255) & ~size_t(255));
       b->launches.push_back(std::move(L));
     }
   }
@@ -871,12 +896,15 @@ int sem_batch_create(sem_mesh* const* meshes, int count, sem_batch** out) {
     off += (sizeof(int) * (size_t)L.grid + 255) & ~size_t(255);
     L.bars_d = reinterpret_cast<unsigned int*>(b->pool + off);
     off += (sizeof(unsigned) * 2 * L.members.size() + 255) & ~size_t(255);
+    L.status_d = reinterpret_cast<int*>(b->pool + off);
+    off += (sizeof(int) * L.members.size() + 255) & ~size_t(255);
     std::vector<int> map(L.grid);
     for (size_t k = 0; k < L.members.size(); ++k)
       for (int c = 0; c < L.nteam[k]; ++c) map[L.team0[k] + c] = (int)k;
     cudaError_t e = cudaMemcpy(L.cta_d, map.data(), sizeof(int) * L.grid, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { cudaFree(b->pool); delete b; return fail(SEM_ERR_CUDA, cudaGetErrorString(e)); }
     L.inst_h.resize(L.members.size());
+    L.status_h.resize(L.members.size());
   }
   *out = b;
   return SEM_OK;
@@ -897,6 +925,10 @@ int sem_batch_info(const sem_batch* b, int* launches_per_stage, int* ctas) {
   if (ctas) *ctas = tot;
   return SEM_OK;
 }
+
+namespace {
+int batch_status(sem_batch* b, cudaStream_t s);
+}  // namespace
 
 int sem_batch_rk4_step(sem_batch* b, double* const* eta_d, double* const* phis_d, double* t_h, const double* dt_h,
                        int nsteps, void* stream) {
@@ -922,18 +954,74 @@ int sem_batch_rk4_step(sem_batch* b, double* const* eta_d, double* const* phis_d
         const StageArgs a{L.inst_d, L.cta_d, L.bars_d, stage, step};
         CUDA_TRY(launch_stage(L.P, L.mixed, a, L.grid, L.smem, s));
       }
-  CUDA_TRY(cudaStreamSynchronize(s));
-  int rc = SEM_OK;
-  for (int i = 0; i < n; ++i) {
-    const int r = read_status(b->meshes[i], s);
-    if (r != SEM_OK && rc == SEM_OK) {
-      rc = r;
-      t_err = "instance " + std::to_string(i) + ": " + t_err;
-    }
-  }
+  int rc = batch_status(b, s);
   if (t_h)
     for (int i = 0; i < n; ++i) t_h[i] += nsteps * dt_h[i];
   return rc;
+}
+
+int sem_batch_laplace_solve(sem_batch* b, const double* const* eta_d, const double* const* phis_d,
+                            double* const* Phi_d, void* stream) {
+  if (!b || !eta_d || !phis_d || !Phi_d) return fail(SEM_ERR_INVALID_ARG, "bad argument");
+  const int n = (int)b->meshes.size();
+  for (int i = 0; i < n; ++i)
+    if (!eta_d[i] || !phis_d[i] || !Phi_d[i]) return fail(SEM_ERR_INVALID_ARG, "bad instance state");
+  DeviceGuard dg(b->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  for (auto& L : b->launches) {
+    for (size_t k = 0; k < L.members.size(); ++k) {
+      const int i = L.members[k];
+      L.inst_h[k] = make_instance(b->meshes[i], const_cast<double*>(eta_d[i]), const_cast<double*>(phis_d[i]),
+                                  0.0, 1.0, L.team0[k], L.nteam[k]);
+      L.inst_h[k].pa.x = Phi_d[i];
+    }
+    CUDA_TRY(cudaMemcpyAsync(L.inst_d, L.inst_h.data(), sizeof(Instance) * L.members.size(),
+                             cudaMemcpyHostToDevice, s));
+  }
+  for (auto& L : b->launches) {
+    CUDA_TRY(cudaMemsetAsync(L.bars_d, 0, 2 * sizeof(unsigned int) * L.members.size(), s));
+    const StageArgs a{L.inst_d, L.cta_d, L.bars_d, 0, 0};
+    CUDA_TRY(launch_stage(L.P, L.mixed, a, L.grid, L.smem, s));
+  }
+  return batch_status(b, s);
+}
+
+namespace {
+// One gather of every member's status word and one copy per launch group; returns the
+// first failing instance's error.
+int batch_status(sem_batch* b, cudaStream_t s) {
+  const int n = (int)b->meshes.size();
+  for (auto& L : b->launches) {
+    CUDA_TRY(launch_gather_status(L.inst_d, (int)L.members.size(), L.status_d, s));
+    CUDA_TRY(cudaMemcpyAsync(L.status_h.data(), L.status_d, sizeof(int) * L.members.size(),
+                             cudaMemcpyDeviceToHost, s));
+  }
+  CUDA_TRY(cudaStreamSynchronize(s));
+  int rc = SEM_OK, first = n;
+  b->codes.assign(n, SEM_OK);
+  for (const auto& L : b->launches)
+    for (size_t k = 0; k < L.members.size(); ++k) {
+      b->codes[L.members[k]] = status_code(L.status_h[k]);
+      if (L.status_h[k] && L.members[k] < first) {
+        first = L.members[k];
+        rc = L.status_h[k];
+      }
+    }
+  if (rc != SEM_OK) {
+    for (int i = 0; i < n; ++i)
+      if (b->codes[i] != SEM_OK) CUDA_TRY(reset_warm_start(b->meshes[i], s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    rc = status_error(rc);
+    t_err = "instance " + std::to_string(first) + ": " + t_err;
+  }
+  return rc;
+}
+}  // namespace
+
+int sem_batch_status(const sem_batch* b, int* codes_h) {
+  if (!b || !codes_h) return fail(SEM_ERR_INVALID_ARG, "NULL argument");
+  for (size_t i = 0; i < b->meshes.size(); ++i) codes_h[i] = i < b->codes.size() ? b->codes[i] : SEM_OK;
+  return SEM_OK;
 }
 
 int sem_get_counters(sem_mesh* m, sem_counters* c, void* stream) {

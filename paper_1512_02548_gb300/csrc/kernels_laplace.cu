@@ -166,6 +166,22 @@ cudaError_t launch_stage(int P, int mixed, const StageArgs& a, int grid, size_t 
   return e;
 }
 
+__global__ void k_gather_status(const Instance* __restrict__ inst, int n, int* __restrict__ out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  int* p = inst[k].g.status;
+  const int v = *p;
+  out[k] = v;
+  if (v) *p = 0;
+}
+
+cudaError_t launch_gather_status(const Instance* inst, int n, int* out, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_gather_status<<<(n + 127) / 128, 128, 0, s>>>(inst, n, out);
+  count_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_prec_setup(const DevGeom& g, const PrecSetup& ps, cudaStream_t s) {
   cudaError_t e = cudaSuccess;
   SEM_DISPATCH_P(g.P, (e = launch_prec_setup_impl<PP>(g, ps, s)));

@@ -673,7 +673,10 @@ __device__ int cg_solve(const DevGeom& g, Smem<P, T>& s, const Range& R, const T
 // (b = −(A [0; φ̃])_I).  Returns false on a barrier timeout; rr (and bb) summed on return.
 template <int P>
 __device__ bool fp64_residual(const DevGeom& g, Smem<P, double>& s, const Range& R, const Team& tm,
-                              const PcgArgs& A, bool want_b, double* red, int* s_flag, double& rr, double& bb) {
+                              const PcgArgs& A, bool want_b, double* red, int* s_flag, double& rr, double& bb,
+                              double* dx = nullptr) {
+  // dx (optional): on entry dx[0] is this thread's partial ‖δ‖² of the last correction; on
+  // exit dx[0] = ‖δ‖² and dx[1] = ‖x‖² over the whole team (interior nodes).
   const int nrow = g.nrow;
   const double* x = A.x;
   const double* phis = A.phis;
@@ -698,12 +701,13 @@ __device__ bool fp64_residual(const DevGeom& g, Smem<P, double>& s, const Range&
           });
   }
   if (!grid_barrier(tm, s_flag)) return false;
-  double acc[2] = {0.0, 0.0};
+  double acc[4] = {0.0, 0.0, dx ? dx[0] : 0.0, 0.0};
   const int ncols = R.c1 - R.c0;
   for (int t = threadIdx.x; t < ncols * nrow; t += blockDim.x) {
     const int col = R.c0 + t / nrow, iz = t - (t / nrow) * nrow;
     const size_t i = (size_t)col * nrow + iz;
     if (iz == nrow - 1) { A.x[i] = phis[col]; continue; }
+    if (dx) acc[3] += A.x[i] * A.x[i];
     const bool le = has_left_edge(g, col);
     const size_t ie = le ? (size_t)left_element(g, col) * nrow + iz : 0;
     double qv = A.q64[i];
@@ -717,12 +721,13 @@ __device__ bool fp64_residual(const DevGeom& g, Smem<P, double>& s, const Range&
       acc[1] += bv * bv;
     }
   }
-  block_sum<2, double>(acc, red);
-  put_partials<2, double>(tm, 0, acc);
+  block_sum<4, double>(acc, red);
+  put_partials<4, double>(tm, 0, acc);
   if (!grid_barrier(tm, s_flag)) return false;
-  grid_sum<2>(tm, 0, acc, red);
+  grid_sum<4>(tm, 0, acc, red);
   rr = acc[0];
   if (want_b) bb = acc[1];
+  if (dx) { dx[0] = acc[2]; dx[1] = acc[3]; }
   return true;
 }
 
@@ -741,6 +746,7 @@ __device__ bool solve_body(const DevGeom& g, const PcgArgs& A, const Team& tm, u
   if (!fp64_residual<P>(g, s64, R, tm, A, true, red, &s_flag, rr, bb)) return false;
   const double target = A.tol * A.tol * bb;
   int iters = 0, refinements = 0;
+  bool rr_floor_ok = false;   // stopped at the FP64 residual floor with converged corrections
   if (bb == 0.0) {
     // φ̃ ≡ 0 on the surface: Φ = 0 is the solution.
     const int ncols = R.c1 - R.c0;
@@ -761,10 +767,16 @@ __device__ bool solve_body(const DevGeom& g, const PcgArgs& A, const Team& tm, u
     s32.carve(smem_raw, nrow, g.Nz);
     const CgVecs<float> V{A.d32, {A.r32, A.r32b}, {A.p32b, A.s32b}, A.p32a, A.z32, A.uh32, A.q32, A.edge32,
                           g.invdiag32};
+    // Refinement stops at the target residual, or once the corrections stop shrinking
+    // (‖δ_i‖ > ½‖δ_{i−1}‖): the true residual has then reached the rounding floor of its
+    // FP64 evaluation, which can lie above tol·‖b‖ when ‖A‖‖x‖ ≫ ‖b‖.  A stalled solve
+    // counts as converged only if its last correction is below tol·‖x‖.
     __shared__ int s_go;
+    double dd_prev = INFINITY, dx[2] = {0.0, 0.0};
+    bool stalled = false;
     while (true) {
       if (threadIdx.x == 0) {
-        int go = rr > target && iters < A.max_iter;
+        int go = rr > target && iters < A.max_iter && !stalled;
         if (!(rr == rr) || isinf(rr)) { atomicOr(g.status, ST_NONFINITE); go = 0; }
         s_go = go;
       }
@@ -788,19 +800,25 @@ __device__ bool solve_body(const DevGeom& g, const PcgArgs& A, const Team& tm, u
       iters += it;
       ++refinements;
       // x += δ (FP64), then the true FP64 residual
+      dx[0] = 0.0;
       for (int t = threadIdx.x; t < ncols * nrow; t += blockDim.x) {
         const int col = R.c0 + t / nrow, iz = t - (t / nrow) * nrow;
         if (iz == nrow - 1) continue;
         const size_t i = (size_t)col * nrow + iz;
-        A.x[i] += (double)A.d32[i];
+        const double d = (double)A.d32[i];
+        A.x[i] += d;
+        dx[0] += d * d;
       }
       __syncthreads();
       s64.load_tables(g);
       if (!grid_barrier(tm, &s_flag)) return false;
       double dummy_b = 0.0;
-      if (!fp64_residual<P>(g, s64, R, tm, A, false, red, &s_flag, rr, dummy_b)) return false;
+      if (!fp64_residual<P>(g, s64, R, tm, A, false, red, &s_flag, rr, dummy_b, dx)) return false;
+      stalled = dx[0] > 0.25 * dd_prev;
+      dd_prev = dx[0];
       if (it == 0) break;   // no progress possible
     }
+    if (rr > target && stalled && dx[0] <= A.tol * A.tol * dx[1]) rr_floor_ok = true;
   }
   if (tm.rank == 0 && threadIdx.x == 0) {
     const double rel = bb > 0.0 ? sqrt(rr / bb) : 0.0;
@@ -812,7 +830,7 @@ __device__ bool solve_body(const DevGeom& g, const PcgArgs& A, const Team& tm, u
     rec->total_iterations += iters;
     rec->total_refinements += refinements;
     if (rel > rec->max_rel_residual) rec->max_rel_residual = rel;
-    if (rr > target) atomicOr(g.status, ST_NOT_CONVERGED);
+    if (rr > target && !rr_floor_ok) atomicOr(g.status, ST_NOT_CONVERGED);
   }
   return true;
 }
@@ -1037,8 +1055,9 @@ __device__ void stage_body(Instance& I, const Team& tm, int stage, int step, uns
   const SurfTables& t = I.st;
   const Range R = my_range(g, tm);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  const double* ein = stage == 1 ? I.eta : (stage == 3 ? I.s1e : I.s0e);
-  const double* pin = stage == 1 ? I.phis : (stage == 3 ? I.s1p : I.s0p);
+  // stage 0: Laplace solve only (geometry, preconditioner and solve from the state itself)
+  const double* ein = stage <= 1 ? I.eta : (stage == 3 ? I.s1e : I.s0e);
+  const double* pin = stage <= 1 ? I.phis : (stage == 3 ? I.s1p : I.s0p);
   double* eout = stage == 2 ? I.s1e : I.s0e;   // stage inputs of the next stage (not used at stage 4)
   double* pout = stage == 2 ? I.s1p : I.s0p;
   const double t0 = I.tstart + step * I.dt;
@@ -1065,6 +1084,7 @@ __device__ void stage_body(Instance& I, const Team& tm, int stage, int step, uns
   if (threadIdx.x == 0) I.pa.phis = pin;
   __syncthreads();
   if (!solve_body<P, MIXED>(g, I.pa, tm, smem_raw, red, s_flag)) return;
+  if (stage == 0) return;
   // w̃ on owned columns; element S_x of η and φ̃; condensation of M'
   for (int col = R.c0 + warp; col < R.c1; col += nw) wsurf_column(t, I.pa.x, ein, I.wt, col, lane);
   for (int q = threadIdx.x; q < 2 * ne * Q; q += blockDim.x) {

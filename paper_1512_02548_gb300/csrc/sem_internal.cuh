@@ -159,7 +159,7 @@ struct StageArgs {
   const Instance* inst;  // device array
   const int* cta_inst;   // CTA → instance
   unsigned int* bars;    // 2 per instance, zero at launch
-  int stage;             // 1..4
+  int stage;             // 1..4; 0 = Laplace solve only
   int step;              // steps since tstart
 };
 
@@ -183,6 +183,8 @@ template <int P> cudaError_t launch_stage_impl(int mixed, const StageArgs& a, in
 cudaError_t stage_occupancy(int P, int mixed, size_t smem, int* per_sm);
 size_t stage_smem_bytes(int P, int nrow, int Nz);
 cudaError_t launch_stage(int P, int mixed, const StageArgs& a, int grid, size_t smem, cudaStream_t s);
+// out[k] = status word of inst[k]; a nonzero word is cleared after it is read.
+cudaError_t launch_gather_status(const Instance* inst, int n, int* out, cudaStream_t s);
 cudaError_t upload_line_tables(const double* D64, const double* w64);  // packed, all orders
 // σ-geometry per element-local column; with_diag also builds the Jacobi diagonal.
 cudaError_t launch_geometry(const DevGeom& g, const double* eta, bool with_diag, cudaStream_t s);

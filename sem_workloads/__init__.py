@@ -19,6 +19,8 @@ Workloads (paper §4.2 linear theory, §4.3 steep waves, §5.3 bar):
   η=(H/2)cos x+(kH²/8)cos 2x, φ̃ from linear theory at z=η, dt=T/200,
   over-integration P_f=⌈3P/2⌉, filter (α,s,i_c)=(36,12,P-1).
 * ``c3_instances`` – 512 periodic tanks from splitmix64(seed 0).
+* ``c5_requests`` – Poisson request stream (Laplace solves and short RK4 runs) for the
+  serving loop.
 * ``roofline_tank`` – one long periodic tank (Nx=65536, Nz=4, P=6) for
   HBM-bound operator measurements.
 """
@@ -291,6 +293,35 @@ def c4_shoal(Nx: int = 2048, Nz: int = 2, P: int = 6, n_comp: int = 256, nsteps:
                     periodic=False, depth=h, Pf=(3 * P + 1) // 2, filter_alpha=36.0, filter_s=12.0,
                     filter_ic=P - 1, dt=0.5 * dx_e / cp, nsteps=nsteps, wave_height=Hs, wavenumber=kp,
                     init="rest", bathymetry="shoal", relax_left=2 * Lp, relax_right=2 * Lp, wave=wave)
+
+
+def c5_requests(rate: float, count: int = 2000, seed: int = 0, nmin: float = 1e3, nmax: float = 2e5,
+                nsteps: int = 10) -> list[tuple[str, float, Workload, int]]:
+    """Request stream for the serving loop: Poisson arrivals at ``rate`` per second, half
+    Laplace solves and half ``nsteps``-step RK4 runs, on periodic tanks whose node count is
+    log-uniform in [nmin, nmax]: P∈{4..10}, Nz∈{1,2,4}, Nx = max(2, round(n/(P(Nz·P+1)))),
+    kh∈[0.5,3] and H/L∈[0.01,0.09] as for the uneven batch.  Returns (kind, arrival s,
+    workload, steps) sorted by arrival."""
+    gen = splitmix64(seed)
+    t = 0.0
+    out = []
+    for i in range(count):
+        t += -math.log(1.0 - _uniform(gen)) / rate
+        kind = "laplace" if _uniform(gen) < 0.5 else "rk4"
+        n = math.exp(math.log(nmin) + _uniform(gen) * (math.log(nmax) - math.log(nmin)))
+        P = 4 + int(_uniform(gen) * 7)
+        Nz = (1, 2, 4)[int(_uniform(gen) * 3)]
+        Nx = max(2, int(round(n / (P * (Nz * P + 1)))))
+        kh = 0.5 + 2.5 * _uniform(gen)
+        HL = 0.01 + 0.08 * _uniform(gen)
+        k = 1.0
+        T = 2 * math.pi / linear_omega(k, kh / k)
+        wl = Workload(name=f"C5 request {i}", P=P, Nx=Nx, Nz=Nz, length=2 * math.pi / k, periodic=True,
+                      depth=kh / k, Pf=(3 * P + 1) // 2, filter_alpha=36.0, filter_s=12.0, filter_ic=P - 1,
+                      dt=T / 200, nsteps=nsteps if kind == "rk4" else 0, wave_height=HL * 2 * math.pi / k,
+                      wavenumber=k)
+        out.append((kind, t, wl, nsteps if kind == "rk4" else 0))
+    return out
 
 
 def random_field(n: int, seed: int) -> np.ndarray:

@@ -143,3 +143,66 @@ def test_c3_batch_runs_and_matches_alone_on_a_sample():
         m2.rk4_step(e, p, dts[k], 1)
         assert rel(etas[k], e) < 1e-8 and rel(phis[k], p) < 1e-8
     batch.close()
+
+
+def test_batch_laplace_solve_equals_alone_and_oracle():
+    cases = _uneven_instances()
+    oms = [osem.mesh_for(wl) for wl, _ in cases]
+    states = [state(wl, om, 10 + i) for i, ((wl, _), om) in enumerate(zip(cases, oms))]
+    meshes = [mesh_for(wl, om, prec) for (wl, prec), om in zip(cases, oms)]
+    batch = sem.Batch(meshes)
+    Phis = [torch.zeros(om.n, dtype=torch.float64, device=DEV) for om in oms]
+    batch.laplace_solve([T(e) for e, _ in states], [T(p) for _, p in states], Phis)
+    assert batch.status() == [0] * len(cases)
+    for k, ((wl, prec), om, (e0, p0)) in enumerate(zip(cases, oms, states)):
+        tol = 1e-10 if prec == "fp64" else 1e-8
+        m = mesh_for(wl, om, prec)
+        m.update_geometry(T(e0))
+        Phi = torch.zeros(om.n, dtype=torch.float64, device=DEV)
+        m.laplace_solve(T(p0), Phi)
+        m.close()
+        assert rel(Phis[k], Phi) < tol, (k, wl.name)
+        assert rel(Phis[k], om.laplace_solve(e0, p0)) < tol, (k, wl.name)
+    # the batched solve leaves each mesh's geometry at the given surface: a recovery call
+    # that follows sees the same σ-geometry as after sem_update_geometry
+    wl, _ = cases[2]
+    om, (e0, p0) = oms[2], states[2]
+    w, ex, px = (torch.zeros(om.ncol, dtype=torch.float64, device=DEV) for _ in range(3))
+    meshes[2].recover_gradient(Phis[2], T(e0), T(p0), w, ex, px)
+    assert rel(w, om.w_surface(e0, om.laplace_solve(e0, p0))) < 1e-10
+    batch.close()
+
+
+def test_batch_failure_stays_with_its_instance():
+    """A non-finite surface in one instance fails that instance only; the others are
+    stepped exactly as without it."""
+    cases = _uneven_instances()[:4]
+    oms = [osem.mesh_for(wl) for wl, _ in cases]
+    states = [state(wl, om, 20 + i) for i, ((wl, _), om) in enumerate(zip(cases, oms))]
+    bad = 1
+    meshes = [mesh_for(wl, om, prec) for (wl, prec), om in zip(cases, oms)]
+    batch = sem.Batch(meshes)
+    etas = [T(e) for e, _ in states]
+    phis = [T(p) for _, p in states]
+    etas[bad][3] = float("nan")
+    with pytest.raises(sem.SemError) as ei:
+        batch.rk4_step(etas, phis, [wl.dt for wl, _ in cases], 1)
+    assert ei.value.code == sem.SEM_ERR_NONFINITE and f"instance {bad}" in str(ei.value)
+    codes = batch.status()
+    assert codes[bad] == sem.SEM_ERR_NONFINITE
+    assert all(c == 0 for k, c in enumerate(codes) if k != bad)
+    for k, ((wl, prec), om, (e0, p0)) in enumerate(zip(cases, oms, states)):
+        if k == bad:
+            continue
+        e, p = om.rk4_step(e0, p0, wl.dt)
+        assert rel(etas[k], e) < 1e-10 and rel(phis[k], p) < 1e-10, k
+    # the failed instance's mesh is usable again afterwards
+    e0, p0 = states[bad]
+    ea, pa = T(e0), T(p0)
+    batch.rk4_step([T(s[0]) if k != bad else ea for k, s in enumerate(states)],
+                   [T(s[1]) if k != bad else pa for k, s in enumerate(states)],
+                   [wl.dt for wl, _ in cases], 1)
+    assert batch.status() == [0] * len(cases)
+    e, p = oms[bad].rk4_step(e0, p0, cases[bad][0].dt)
+    assert rel(ea, e) < 1e-10 and rel(pa, p) < 1e-10
+    batch.close()
