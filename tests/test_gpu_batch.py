@@ -128,8 +128,8 @@ def test_c3_batch_runs_and_matches_alone_on_a_sample():
     meshes, etas, phis, dts = [], [], [], []
     for i, wl in enumerate(wls):
         m = sem.Mesh.from_workload(wl, precision="mixed", tol=1e-12)
-        xcol = np.linspace(0, wl.length, wl.ncol, endpoint=False)
-        e0, p0 = initial_state(wl, xcol, np.full(wl.ncol, wl.depth))
+        om = osem.mesh_for(wl)
+        e0, p0 = initial_state(wl, om.xcol, om.h)
         meshes.append(m)
         etas.append(T(e0))
         phis.append(T(p0))
