@@ -224,11 +224,14 @@ def run_reference(args):
 # Supplementary: the operator apply on a long tank (working set above L2)
 # ---------------------------------------------------------------------------------------------
 def apply_roofline(dev, reps: int = 20):
-    """Time sem_laplace_apply (FP64) on a 65536×4, P=6 periodic tank, 9.8 M nodes.
+    """The operator apply y = 𝓛x on a 65536×4, P=6 periodic tank (9.8 M nodes), three kernels:
+    the FP64 element-column kernel (sem_laplace_apply), the FP64 tiled kernel (same call with
+    SEM_APPLY_KERNEL=tile) and the FP32 tiled kernel of the mixed path (sem_laplace_apply_f32).
 
     Algorithmic work per apply: (8(P+1)+7) flops per element-local node; algorithmic bytes:
-    read x + write y (16 B per node) + geometry (4 doubles per element-local column).
-    Returns achieved FP64 TFLOP/s and HBM GB/s against the FP64 and measured-copy peaks.
+    read x + write y, 16 B (FP64) or 8 B (FP32) per node.  Design bytes add the per-column
+    geometry (4 values per element-local column).  Each apply is timed alone with CUDA events,
+    with L2 flushed (256 MB written) before it; the median of `reps` is reported.
     """
     import numpy as np
     import torch
@@ -241,26 +244,56 @@ def apply_roofline(dev, reps: int = 20):
     mesh.update_geometry(eta)
     x = torch.randn(mesh.n, dtype=torch.float64, device=dev)
     y = torch.empty_like(x)
-    for _ in range(3):
-        mesh.laplace_apply(x, y)
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(reps):
-        mesh.laplace_apply(x, y)
-    e1.record()
-    e1.synchronize()
-    ms = e0.elapsed_time(e1) / reps
+    x32 = x.float()
+    y32 = torch.empty_like(x32)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts))
+
+    def tile64():
+        old = os.environ.get("SEM_APPLY_KERNEL")
+        os.environ["SEM_APPLY_KERNEL"] = "tile"
+        try:
+            mesh.laplace_apply(x, y)
+        finally:
+            if old is None:
+                del os.environ["SEM_APPLY_KERNEL"]
+            else:
+                os.environ["SEM_APPLY_KERNEL"] = old
+
     P = wl.P
     flops = wl.Nx * wl.Nz * (P + 1) ** 2 * (8 * (P + 1) + 7)
-    nbytes = 16 * mesh.n + 32 * wl.Nx * (P + 1)
+    geo_cols = wl.Nx * (P + 1)
     peaks = measured_peaks()
-    out = {"workload": wl.name, "n_nodes": mesh.n, "ms_per_apply": ms,
-           "fp64_tflops": flops / ms / 1e9, "fp64_peak": FP64_PEAK_TFLOPS,
-           "fp64_frac": flops / ms / 1e9 / FP64_PEAK_TFLOPS,
-           "hbm_gbs": nbytes / ms / 1e6, "hbm_peak": peaks.get("hbm_gbs"),
-           "note": "two kernels per apply (element columns, then the shared edge columns)"}
+    hbm = peaks.get("hbm_gbs")
+    out = {"workload": wl.name, "n_nodes": mesh.n, "flops_per_apply": flops, "l2_flushed": True}
+    for name, fn, elem in (("fp64_column", lambda: mesh.laplace_apply(x, y), 8), ("fp64_tile", tile64, 8),
+                           ("fp32_tile", lambda: mesh.laplace_apply_f32(x32, y32), 4)):
+        ms = timed(fn)
+        alg = 2 * elem * mesh.n
+        design = alg + 4 * elem * geo_cols
+        out[name] = {"ms_per_apply": ms, "tflops": flops / ms / 1e9,
+                     "algorithmic_bytes": alg, "hbm_gbs": alg / ms / 1e6, "hbm_frac": alg / ms / 1e6 / hbm,
+                     "design_bytes": design, "design_hbm_frac": design / ms / 1e6 / hbm}
+        if elem == 8:
+            out[name]["fp64_frac"] = flops / ms / 1e9 / FP64_PEAK_TFLOPS
+    out["hbm_peak"] = hbm
+    out["fp64_peak"] = FP64_PEAK_TFLOPS
+    out["fp32_vs_fp64_rel_l2"] = float(torch.linalg.norm(y32.double() - y) / torch.linalg.norm(y))
     mesh.close()
     return out
 

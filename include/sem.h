@@ -140,8 +140,17 @@ int sem_update_geometry(sem_mesh* m, const double* eta_d, void* stream);
 
 /* y = 𝓛 x with 𝓛_ij = −Σ_k ∫ (K∇N_j)·∇N_i over the mesh (§3.1.2), matrix-free,
  * all n rows (no Dirichlet modification), for the last sem_update_geometry.
- * x_d, y_d: device, n values, must not overlap. */
+ * x_d, y_d: device, n values, must not overlap.  Environment: SEM_APPLY_KERNEL=tile
+ * selects the tiled kernel of sem_laplace_apply_f32 in FP64 (same result up to rounding
+ * order); otherwise the element-column kernel with the mesh's edge workspace runs. */
 int sem_laplace_apply(sem_mesh* m, const double* x_d, double* y_d, void* stream);
+
+/* The same operator in FP32 (the arithmetic of the mixed-precision inner solve): y = 𝓛 x
+ * with the FP32 copy of the geometry of the last sem_update_geometry.  One kernel, tiles of
+ * consecutive x-elements with the element left of each tile recomputed, so every output
+ * column is complete in one CTA and written once; uses no workspace.  x_d, y_d: device,
+ * float, n values, must not overlap. */
+int sem_laplace_apply_f32(const sem_mesh* m, const float* x_d, float* y_d, void* stream);
 
 /* Allocation-free form of sem_laplace_apply (the paper has no counterpart; this is a
  * service of the library).  For callers that may not allocate device memory at the time

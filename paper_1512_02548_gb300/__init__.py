@@ -27,7 +27,7 @@ SEM_PREC_FP64, SEM_PREC_MIXED = 0, 1
 SEM_PRECOND_SEPARABLE, SEM_PRECOND_JACOBI = 0, 1
 
 EXPORTED = ("sem_mesh_create", "sem_mesh_destroy", "sem_mesh_footprint", "sem_mesh_info", "sem_mesh_l2g",
-            "sem_update_geometry", "sem_laplace_apply", "sem_laplace_apply_noalloc", "sem_laplace_solve",
+            "sem_update_geometry", "sem_laplace_apply", "sem_laplace_apply_f32", "sem_laplace_apply_noalloc", "sem_laplace_solve",
             "sem_recover_gradient", "sem_zakharov_rhs", "sem_set_wave_input", "sem_apply_filter", "sem_rk4_step",
             "sem_rk4_step_host", "sem_get_counters", "sem_reset_counters", "sem_enable_timing",
             "sem_get_timing", "sem_batch_create", "sem_batch_destroy", "sem_batch_info",
@@ -87,6 +87,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sem_update_geometry.argtypes = [vp, dp, vp]
     lib.sem_laplace_apply.argtypes = [vp, dp, dp, vp]
     lib.sem_laplace_apply_noalloc.argtypes = [vp, dp, dp, vp]
+    lib.sem_laplace_apply_f32.argtypes = [vp, vp, vp, vp]
     lib.sem_laplace_solve.argtypes = [vp, dp, dp, ctypes.POINTER(sem_solve_stats), vp]
     lib.sem_recover_gradient.argtypes = [vp, dp, dp, dp, dp, dp, dp, vp]
     lib.sem_zakharov_rhs.argtypes = [vp, dp, dp, ctypes.c_double, dp, dp, vp]
@@ -133,13 +134,16 @@ def _stream():
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
 
 
-def _ptr(t):
+def _ptr(t, dtype=None):
     if t is None:
         return None
     if not (t.is_cuda and t.is_contiguous()):
         raise ValueError("expected a contiguous CUDA tensor")
     import torch
-    if t.dtype not in (torch.float64, torch.int32):
+    if dtype is not None:
+        if t.dtype != dtype:
+            raise ValueError(f"expected {dtype}")
+    elif t.dtype not in (torch.float64, torch.int32):
         raise ValueError("expected float64 (or int32 for l2g)")
     return ctypes.c_void_p(t.data_ptr())
 
@@ -231,6 +235,13 @@ class Mesh:
 
     def laplace_apply(self, x, y):
         _check(load_library().sem_laplace_apply(self._h, _ptr(x), _ptr(y), _stream()))
+        return y
+
+    def laplace_apply_f32(self, x, y):
+        """y = 𝓛x in FP32 (float32 tensors), tiled kernel (sem_laplace_apply_f32)."""
+        import torch
+        _check(load_library().sem_laplace_apply_f32(self._h, _ptr(x, torch.float32), _ptr(y, torch.float32),
+                                                     _stream()))
         return y
 
     def laplace_apply_noalloc(self, x, y):

@@ -707,7 +707,16 @@ int sem_update_geometry(sem_mesh* m, const double* eta_d, void* stream) {
 int sem_laplace_apply(sem_mesh* m, const double* x_d, double* y_d, void* stream) {
   if (!m || !x_d || !y_d || x_d == y_d) return fail(SEM_ERR_INVALID_ARG, "bad pointer");
   DeviceGuard dg(m->device);
-  CUDA_TRY(launch_apply(m->g, x_d, y_d, m->qtmp, m->edgetmp, (cudaStream_t)stream));
+  const char* k = std::getenv("SEM_APPLY_KERNEL");   // "tile": the tiled kernel, else element columns
+  if (k && std::strcmp(k, "tile") == 0) CUDA_TRY(launch_apply_tile(0, m->g, x_d, y_d, (cudaStream_t)stream));
+  else CUDA_TRY(launch_apply(m->g, x_d, y_d, m->qtmp, m->edgetmp, (cudaStream_t)stream));
+  return SEM_OK;
+}
+
+int sem_laplace_apply_f32(const sem_mesh* m, const float* x_d, float* y_d, void* stream) {
+  if (!m || !x_d || !y_d || x_d == y_d) return fail(SEM_ERR_INVALID_ARG, "bad pointer");
+  DeviceGuard dg(m->device);
+  CUDA_TRY(launch_apply_tile(1, m->g, x_d, y_d, (cudaStream_t)stream));
   return SEM_OK;
 }
 

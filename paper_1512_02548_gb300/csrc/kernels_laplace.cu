@@ -130,6 +130,12 @@ cudaError_t launch_apply_noalloc(const DevGeom& g, const double* x, double* y, c
   return cudaGetLastError();
 }
 
+cudaError_t launch_apply_tile(int fp32, const DevGeom& g, const void* x, void* y, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  SEM_DISPATCH_P(g.P, (e = launch_apply_tile_impl<PP>(fp32, g, x, y, s)));
+  return e;
+}
+
 cudaError_t launch_l2g(const DevGeom& g, int32_t* l2g, cudaStream_t s) {
   const long long total = (long long)g.Nx * g.Nz * (g.P + 1) * (g.P + 1);
   k_l2g<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(g, l2g);

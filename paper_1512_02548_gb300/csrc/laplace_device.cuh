@@ -287,6 +287,12 @@ __global__ void __launch_bounds__(kThreads) k_apply(DevGeom g, const double* __r
 
 
 
+}  // namespace semgb
+
+#include "apply_tile.cuh"
+
+namespace semgb {
+
 // ------------------------------------------------------------------------------------
 // Grid barrier for the cooperative kernel, with a wall-clock limit.
 // ------------------------------------------------------------------------------------
@@ -1241,6 +1247,36 @@ cudaError_t launch_stage_impl(int mixed, const StageArgs& a, int grid, size_t sm
   void* args[] = {&aa};
   const void* fn = mixed ? (const void*)k_stage<P, true> : (const void*)k_stage<P, false>;
   return cudaLaunchCooperativeKernel(fn, grid, kThreads, args, smem, s);
+}
+
+
+// Tiled apply (apply_tile.cuh): widest tile of at most 16 elements whose shared memory keeps
+// four CTAs per SM; one CTA per tile up to the co-resident count, grid-stride beyond.
+constexpr size_t kTileSmemTarget = 56 * 1024;
+
+template <int P>
+cudaError_t launch_apply_tile_impl(int fp32, const DevGeom& g, const void* x, void* y, cudaStream_t s) {
+  const size_t elem = fp32 ? sizeof(float) : sizeof(double);
+  int E = 16;
+  while (E > 1 && apply_tile_smem<P>(E, g.nrow, g.Nz, elem) > kTileSmemTarget) E >>= 1;
+  const size_t smem = apply_tile_smem<P>(E, g.nrow, g.Nz, elem);
+  if (smem > (size_t)kMaxDynSmem) return cudaErrorInvalidValue;
+  const void* fn = fp32 ? (const void*)k_apply_tile<P, float> : (const void*)k_apply_tile<P, double>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, per_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem)) != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const long long ntiles = (g.Nx + E - 1) / E;
+  const int grid = (int)(ntiles < (long long)per_sm * sms ? ntiles : (long long)per_sm * sms);
+  if (fp32) k_apply_tile<P, float><<<grid, kThreads, smem, s>>>(g, static_cast<const float*>(x),
+                                                               static_cast<float*>(y), E);
+  else k_apply_tile<P, double><<<grid, kThreads, smem, s>>>(g, static_cast<const double*>(x),
+                                                            static_cast<double*>(y), E);
+  count_launch();
+  return cudaGetLastError();
 }
 
 }  // namespace semgb

@@ -173,6 +173,8 @@ template <int P> cudaError_t pcg_occupancy_impl(int mixed, size_t smem, int* per
 template <int P> cudaError_t launch_pcg_impl(int mixed, const DevGeom& g, const PcgArgs& a, int grid, size_t smem,
                                              cudaStream_t s);
 template <int P> cudaError_t launch_prec_setup_impl(const DevGeom& g, const PrecSetup& ps, cudaStream_t s);
+template <int P> cudaError_t launch_apply_tile_impl(int fp32, const DevGeom& g, const void* x, void* y,
+                                                    cudaStream_t s);
 template <int P> cudaError_t stage_occupancy_impl(int mixed, size_t smem, int* per_sm);
 template <int P> cudaError_t launch_stage_impl(int mixed, const StageArgs& a, int grid, size_t smem,
                                                cudaStream_t s);
@@ -191,6 +193,9 @@ cudaError_t launch_geometry(const DevGeom& g, const double* eta, bool with_diag,
 cudaError_t launch_apply(const DevGeom& g, const double* x, double* y, double* qtmp, double* edge,
                          cudaStream_t s);
 cudaError_t launch_l2g(const DevGeom& g, int32_t* l2g, cudaStream_t s);
+// Tiled apply y = 𝓛x at every node in FP32 (fp32 = 1, x, y float) or FP64 (x, y double), from the
+// geometry of the last launch_geometry; x and y must not overlap.  No workspace.
+cudaError_t launch_apply_tile(int fp32, const DevGeom& g, const void* x, void* y, cudaStream_t s);
 // Allocation-free apply (scratch in a static device array of kNoAllocEdgeMax doubles).
 constexpr size_t kNoAllocEdgeMax = size_t(1) << 20;
 cudaError_t launch_apply_noalloc(const DevGeom& g, const double* x, double* y, cudaStream_t s);
