@@ -223,7 +223,7 @@ def run_reference(args):
 # ---------------------------------------------------------------------------------------------
 # Supplementary: the operator apply on a long tank (working set above L2)
 # ---------------------------------------------------------------------------------------------
-def apply_roofline(dev, reps: int = 20):
+def apply_roofline(dev, reps: int = 20, Nx: int = 65536, kernels=("fp64_column", "fp64_tile", "fp32_tile")):
     """The operator apply y = 𝓛x on a 65536×4, P=6 periodic tank (9.8 M nodes), three kernels:
     the FP64 element-column kernel (sem_laplace_apply), the FP64 tiled kernel (same call with
     SEM_APPLY_KERNEL=tile) and the FP32 tiled kernel of the mixed path (sem_laplace_apply_f32).
@@ -237,10 +237,10 @@ def apply_roofline(dev, reps: int = 20):
     import torch
     import paper_1512_02548_gb300 as sem
     from sem_workloads import roofline_tank
-    wl = roofline_tank()
+    wl = roofline_tank(Nx=Nx)
     mesh = sem.Mesh.from_workload(wl)
     xcol = column_positions(wl)
-    eta = torch.tensor(0.05 * np.cos(2 * np.pi * xcol / wl.length * 64), device=dev)
+    eta = torch.tensor(0.05 * np.cos(2 * np.pi * xcol / wl.length * (Nx // 1024)), device=dev)
     mesh.update_geometry(eta)
     x = torch.randn(mesh.n, dtype=torch.float64, device=dev)
     y = torch.empty_like(x)
@@ -283,6 +283,8 @@ def apply_roofline(dev, reps: int = 20):
     out = {"workload": wl.name, "n_nodes": mesh.n, "flops_per_apply": flops, "l2_flushed": True}
     for name, fn, elem in (("fp64_column", lambda: mesh.laplace_apply(x, y), 8), ("fp64_tile", tile64, 8),
                            ("fp32_tile", lambda: mesh.laplace_apply_f32(x32, y32), 4)):
+        if name not in kernels:
+            continue
         ms = timed(fn)
         alg = 2 * elem * mesh.n
         design = alg + 4 * elem * geo_cols
@@ -293,7 +295,8 @@ def apply_roofline(dev, reps: int = 20):
             out[name]["fp64_frac"] = flops / ms / 1e9 / FP64_PEAK_TFLOPS
     out["hbm_peak"] = hbm
     out["fp64_peak"] = FP64_PEAK_TFLOPS
-    out["fp32_vs_fp64_rel_l2"] = float(torch.linalg.norm(y32.double() - y) / torch.linalg.norm(y))
+    if "fp32_tile" in kernels and len(kernels) > 1:
+        out["fp32_vs_fp64_rel_l2"] = float(torch.linalg.norm(y32.double() - y) / torch.linalg.norm(y))
     mesh.close()
     return out
 
@@ -568,7 +571,16 @@ def main():
     ap.add_argument("--no-c5", action="store_true")
     ap.add_argument("--c5-rate", type=float, default=1000.0)
     ap.add_argument("--c5-requests", type=int, default=400)
+    ap.add_argument("--apply-only", default=None,
+                    help="comma list of fp64_column,fp64_tile,fp32_tile: time only these applies (for profiling)")
+    ap.add_argument("--apply-nx", type=int, default=65536)
+    ap.add_argument("--apply-reps", type=int, default=20)
     args = ap.parse_args()
+    if args.apply_only:
+        import torch
+        print(json.dumps(apply_roofline(torch.device("cuda", 0), args.apply_reps, args.apply_nx,
+                                        tuple(args.apply_only.split(",")))))
+        return 0
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -498,7 +498,8 @@ static int mesh_create_impl(const sem_params* pin, const double* x_edges_h, cons
   // ---- device allocation -------------------------------------------------------
   sem_mesh* m = new sem_mesh;
   m->p = p; m->device = dev; m->ncol = ncol; m->nrow = nrow; m->n = n; m->Pf = p.Pf; m->nif = N;
-  cudaError_t ge = pcg_grid_size(P, Nz, nrow, Nx, p.precision == SEM_PREC_MIXED, &m->grid, &m->smem);
+  const int chunk = chunk_width(P, Nz);
+  cudaError_t ge = pcg_grid_size(P, Nz, nrow, Nx, chunk, p.precision == SEM_PREC_MIXED, &m->grid, &m->smem);
   if (ge != cudaSuccess) { delete m; return fail(SEM_ERR_CUDA, std::string("Krylov kernel occupancy: ") + cudaGetErrorString(ge)); }
   if (const char* lim = std::getenv("SEM_GRID_LIMIT")) {   // tuning/testing knob: cap the Krylov grid
     const int v = std::atoi(lim);
@@ -592,7 +593,7 @@ static int mesh_create_impl(const sem_params* pin, const double* x_edges_h, cons
   if (code != SEM_OK) { cudaFree(m->pool); delete m; return code; }
 
   DevGeom& g = m->g;
-  g.P = P; g.Nx = Nx; g.Nz = Nz; g.ncol = ncol; g.nrow = nrow; g.periodic = p.periodic ? 1 : 0;
+  g.P = P; g.Nx = Nx; g.Nz = Nz; g.ncol = ncol; g.nrow = nrow; g.periodic = p.periodic ? 1 : 0; g.chunk = chunk;
   g.h = D_(o_h); g.hx_loc = D_(o_hx); g.dxe = D_(o_dxe); g.dsl = D_(o_dsl); g.sig = D_(o_sig);
   g.geo64 = D_(o_geo64); g.geo32 = F_(o_geo32); g.invdiag64 = D_(o_id64); g.invdiag32 = F_(o_id32);
   g.status = reinterpret_cast<int*>(m->pool + o_status);
@@ -646,7 +647,7 @@ static int mesh_create_impl(const sem_params* pin, const double* x_edges_h, cons
   {
     const char* fz = std::getenv("SEM_FUSED_STAGE");
     m->fused = !(fz && fz[0] == '0') && p.precond == SEM_PRECOND_SEPARABLE;
-    m->stage_smem = stage_smem_bytes(P, nrow, Nz);
+    m->stage_smem = stage_smem_bytes(P, nrow, Nz, chunk);
     int per_sm = 0, sms = 0;
     cudaError_t e = stage_occupancy(P, p.precision == SEM_PREC_MIXED, m->stage_smem, &per_sm);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -874,7 +875,7 @@ int sem_batch_create(sem_mesh* const* meshes, int count, sem_batch** out) {
       int used = 0;
       for (size_t k = 0; k < L.members.size(); ++k) {
         const sem_mesh* m = meshes[L.members[k]];
-        const int limit = std::max(1, std::min(m->stage_team, m->p.Nx));
+        const int limit = std::max(1, std::min(m->stage_team, (m->p.Nx + m->g.chunk - 1) / m->g.chunk));
         c[k] = std::max(1, std::min(limit, (int)((double)cap * w[k] / wsum)));
         used += c[k];
       }

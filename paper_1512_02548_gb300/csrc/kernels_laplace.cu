@@ -143,8 +143,8 @@ cudaError_t launch_l2g(const DevGeom& g, int32_t* l2g, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t pcg_grid_size(int P, int Nz, int nrow, int Nx, int mixed, int* grid, size_t* smem) {
-  *smem = apply_smem_bytes(P, nrow, Nz, sizeof(double));
+cudaError_t pcg_grid_size(int P, int Nz, int nrow, int Nx, int chunk, int mixed, int* grid, size_t* smem) {
+  *smem = apply_smem_bytes(P, nrow, Nz, chunk, sizeof(double));
   int dev = 0, sms = 0, per_sm = 0;
   cudaError_t e;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
@@ -152,12 +152,14 @@ cudaError_t pcg_grid_size(int P, int Nz, int nrow, int Nx, int mixed, int* grid,
   SEM_DISPATCH_P(P, (e = pcg_occupancy_impl<PP>(mixed, *smem, &per_sm)));
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  long long cap = (long long)per_sm * sms;
-  *grid = (int)(Nx < cap ? Nx : cap);
+  const long long cap = (long long)per_sm * sms, want = (Nx + chunk - 1) / chunk;
+  *grid = (int)(want < cap ? want : cap);
   return cudaSuccess;
 }
 
-size_t stage_smem_bytes(int P, int nrow, int Nz) { return apply_smem_bytes(P, nrow, Nz, sizeof(double)); }
+size_t stage_smem_bytes(int P, int nrow, int Nz, int chunk) {
+  return apply_smem_bytes(P, nrow, Nz, chunk, sizeof(double));
+}
 
 cudaError_t stage_occupancy(int P, int mixed, size_t smem, int* per_sm) {
   cudaError_t e = cudaSuccess;

@@ -155,23 +155,20 @@ struct Smem {
   T* D;     // Q*Q
   T* w;     // Q
   T* sig;   // nrow
-  T* cxz;   // 2*Nz: Δσ_l/Δx_e, Δx_e/Δσ_l for the current element column
-  T* geo;   // 4*Q
-  T* X;     // Q*nrow
-  T* F1;    // Nz*Q*Q
-  T* F2;    // Nz*Q*Q
-  __device__ static size_t bytes(int nrow, int Nz) {
-    return sizeof(T) * (size_t)(Q * Q + Q + nrow + 2 * Nz + 4 * Q + Q * nrow + 2 * Nz * Q * Q);
-  }
-  __device__ void carve(unsigned char* base, int nrow, int Nz) {
+  T* cxz;   // E*2*Nz: Δσ_l/Δx_e, Δx_e/Δσ_l of the chunk's element columns
+  T* geo;   // E*4*Q
+  T* X;     // E*Q*nrow
+  T* F1;    // E*Nz*Q*Q
+  T* F2;    // E*Nz*Q*Q
+  __device__ void carve(unsigned char* base, int nrow, int Nz, int E) {
     T* p = reinterpret_cast<T*>(base);
     D = p; p += Q * Q;
     w = p; p += Q;
     sig = p; p += nrow;
-    cxz = p; p += 2 * Nz;
-    geo = p; p += 4 * Q;
-    X = p; p += Q * nrow;
-    F1 = p; p += Nz * Q * Q;
+    cxz = p; p += 2 * Nz * E;
+    geo = p; p += 4 * Q * E;
+    X = p; p += Q * nrow * E;
+    F1 = p; p += Nz * Q * Q * E;
     F2 = p;
   }
   __device__ void load_tables(const DevGeom& g) {
@@ -187,30 +184,37 @@ template <class T> __device__ __forceinline__ const T* geo_ptr(const DevGeom& g)
 template <> __device__ __forceinline__ const double* geo_ptr<double>(const DevGeom& g) { return g.geo64; }
 template <> __device__ __forceinline__ const float* geo_ptr<float>(const DevGeom& g) { return g.geo32; }
 
-// Apply A = −𝓛 on element column ex.  `loadx(ex,a,iz)` gives the input value of local
-// column a, row iz; `store(ex,a,iz,y)` receives the element column's contribution.
-// Returns this thread's share of Σ x·(A_e x) over the element column (accumulated in T).
+// Apply A = −𝓛 on the ne consecutive element columns ex0..ex0+ne−1 (a chunk, processed
+// together so that small element columns still occupy the CTA).  `loadx(ex,a,iz)` gives the
+// input value of local column a, row iz of element column ex; `store(ex,a,iz,y)` receives the
+// element column's contribution.  Returns this thread's share of Σ x·(A_e x) over the chunk
+// (accumulated in T).
 template <int P, class T, class LoadX, class Store>
-__device__ __forceinline__ T apply_element_column(const DevGeom& g, Smem<P, T>& s, int ex,
-                                                       LoadX loadx, Store store) {
+__device__ __forceinline__ T apply_element_chunk(const DevGeom& g, Smem<P, T>& s, int ex0, int ne,
+                                                 LoadX loadx, Store store) {
   constexpr int Q = P + 1;
   const int nrow = g.nrow, Nz = g.Nz;
-  const T* geo = geo_ptr<T>(g) + (size_t)ex * Q * 4;
-  for (int t = threadIdx.x; t < 4 * Q; t += blockDim.x) s.geo[t] = geo[t];
-  for (int t = threadIdx.x; t < Nz; t += blockDim.x) {
-    const double dxe = g.dxe[ex], dsl = g.dsl[t];
+  const int colsz = Q * nrow, elsz = Nz * Q * Q;
+  const T* geo = geo_ptr<T>(g) + (size_t)ex0 * Q * 4;
+  for (int t = threadIdx.x; t < ne * 4 * Q; t += blockDim.x) s.geo[t] = geo[t];
+  for (int t = threadIdx.x; t < ne * Nz; t += blockDim.x) {
+    const int e = t / Nz, l = t - e * Nz;
+    const double dxe = g.dxe[ex0 + e], dsl = g.dsl[l];
     s.cxz[2 * t] = (T)(dsl / dxe);
     s.cxz[2 * t + 1] = (T)(dxe / dsl);
   }
-  for (int t = threadIdx.x; t < Q * nrow; t += blockDim.x) {
-    const int a = t / nrow, iz = t - a * nrow;
-    s.X[t] = loadx(ex, a, iz);
+  for (int t = threadIdx.x; t < ne * colsz; t += blockDim.x) {
+    const int e = t / colsz, rem = t - e * colsz;
+    const int a = rem / nrow, iz = rem - a * nrow;
+    s.X[t] = loadx(ex0 + e, a, iz);
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < Nz * Q * Q; t += blockDim.x) {
-    const int l = t / (Q * Q), rem = t - l * (Q * Q), a = rem / Q, b = rem - a * Q;
-    const T* Xrow = s.X + l * P + b;             // Xrow[c*nrow]: row l·P+b, column c
-    const T* Xcol = s.X + a * nrow + l * P;      // Xcol[c]: column a, row l·P+c
+  for (int t = threadIdx.x; t < ne * elsz; t += blockDim.x) {
+    const int e = t / elsz, rem0 = t - e * elsz;
+    const int l = rem0 / (Q * Q), rem = rem0 - l * (Q * Q), a = rem / Q, b = rem - a * Q;
+    const T* Xe = s.X + e * colsz;
+    const T* Xrow = Xe + l * P + b;              // Xrow[c*nrow]: row l·P+b, column c
+    const T* Xcol = Xe + a * nrow + l * P;       // Xcol[c]: column a, row l·P+c
     const T* Da = s.D + a * Q;
     const T* Db = s.D + b * Q;
     T ur = 0, ut = 0;
@@ -219,25 +223,30 @@ __device__ __forceinline__ T apply_element_column(const DevGeom& g, Smem<P, T>& 
       ur = fmx(Da[c], Xrow[c * nrow], ur);
       ut = fmx(Db[c], Xcol[c], ut);
     }
-    const T d = s.geo[a * 4 + 0], invd = s.geo[a * 4 + 1], hx = s.geo[a * 4 + 2], dxd = s.geo[a * 4 + 3];
+    const T* ge = s.geo + e * 4 * Q + a * 4;
+    const T d = ge[0], invd = ge[1], hx = ge[2], dxd = ge[3];
+    const T* cz = s.cxz + 2 * (e * Nz + l);
     const T wab = s.w[a] * s.w[b];
     const T K12 = hx - s.sig[l * P + b] * dxd;
     const T K22 = fmx(K12, K12, (T)1) * invd;
-    const T G11 = wab * s.cxz[2 * l] * d;
+    const T G11 = wab * cz[0] * d;
     const T G12 = wab * K12;
-    const T G22 = wab * s.cxz[2 * l + 1] * K22;
+    const T G22 = wab * cz[1] * K22;
     s.F1[t] = fmx(G11, ur, G12 * ut);
     s.F2[t] = fmx(G12, ur, G22 * ut);
   }
   __syncthreads();
   T part = 0;
-  for (int t = threadIdx.x; t < Q * nrow; t += blockDim.x) {
-    const int a = t / nrow, iz = t - a * nrow;
+  for (int t = threadIdx.x; t < ne * colsz; t += blockDim.x) {
+    const int e = t / colsz, rem = t - e * colsz;
+    const int a = rem / nrow, iz = rem - a * nrow;
     const int l = iz / P, b = iz - l * P;
+    const T* F1e = s.F1 + e * elsz;
+    const T* F2e = s.F2 + e * elsz;
     T y = 0;
     if (l < Nz) {
-      const T* F1 = s.F1 + (l * Q) * Q + b;      // F1[(l*Q+a')*Q+b] = F1[a'*Q]
-      const T* F2 = s.F2 + (l * Q + a) * Q;      // F2[(l*Q+a)*Q+b']
+      const T* F1 = F1e + (l * Q) * Q + b;       // F1[(l*Q+a')*Q+b] = F1[a'*Q]
+      const T* F2 = F2e + (l * Q + a) * Q;       // F2[(l*Q+a)*Q+b']
 #pragma unroll
       for (int c = 0; c < Q; ++c) {
         y = fmx(s.D[c * Q + a], F1[c * Q], y);
@@ -246,15 +255,15 @@ __device__ __forceinline__ T apply_element_column(const DevGeom& g, Smem<P, T>& 
     }
     if (b == 0 && l > 0) {
       const int lm = l - 1;
-      const T* F1 = s.F1 + (lm * Q) * Q + P;
-      const T* F2 = s.F2 + (lm * Q + a) * Q;
+      const T* F1 = F1e + (lm * Q) * Q + P;
+      const T* F2 = F2e + (lm * Q + a) * Q;
 #pragma unroll
       for (int c = 0; c < Q; ++c) {
         y = fmx(s.D[c * Q + a], F1[c * Q], y);
         y = fmx(s.D[c * Q + P], F2[c], y);
       }
     }
-    store(ex, a, iz, y);
+    store(ex0 + e, a, iz, y);
     part = fmx(s.X[t], y, part);
   }
   __syncthreads();
@@ -269,13 +278,13 @@ __global__ void __launch_bounds__(kThreads) k_apply(DevGeom g, const double* __r
                                                     double* __restrict__ q, double* __restrict__ edge) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem<P, double> s;
-  s.carve(smem_raw, g.nrow, g.Nz);
+  s.carve(smem_raw, g.nrow, g.Nz, g.chunk);
   s.load_tables(g);
   __syncthreads();
-  const int nrow = g.nrow;
-  for (int ex = blockIdx.x; ex < g.Nx; ex += gridDim.x) {
-    apply_element_column<P, double>(
-        g, s, ex,
+  const int nrow = g.nrow, E = g.chunk;
+  for (int ex0 = blockIdx.x * E; ex0 < g.Nx; ex0 += gridDim.x * E) {
+    apply_element_chunk<P, double>(
+        g, s, ex0, min(E, g.Nx - ex0),
         [&](int e, int a, int iz) { return x[(size_t)col_of(g, e, a) * nrow + iz]; },
         [&](int e, int a, int iz, double y) {
           if (a < P || (!g.periodic && e == g.Nx - 1)) q[(size_t)col_of(g, e, a) * nrow + iz] = y;
@@ -459,11 +468,14 @@ __device__ void cg_update(const DevGeom& g, Smem<P, T>& s, const Range& R, const
   T* r_new = V.r[cur ^ 1];
   const T* s_old = V.s[cur];
   T* s_new = V.s[cur ^ 1];
-  T* X = s.X;     // [Q][nr] residual of the element column
-  T* RH = s.F1;   // [Q][nr] σ-transformed residual
-  for (int ex = R.e0; ex < R.e1; ++ex) {
-    for (int t = threadIdx.x; t < Q * nr; t += blockDim.x) {
-      const int a = t / nr, j = t - a * nr;
+  T* X = s.X;     // [E][Q][nr] residual of the chunk's element columns
+  T* RH = s.F1;   // [E][Q][nr] σ-transformed residual
+  const int E = g.chunk, qn = Q * nr;
+  for (int ex0 = R.e0; ex0 < R.e1; ex0 += E) {
+    const int ne = min(E, R.e1 - ex0);
+    for (int t = threadIdx.x; t < ne * qn; t += blockDim.x) {
+      const int e = t / qn, rem = t - e * qn;
+      const int a = rem / nr, j = rem - a * nr, ex = ex0 + e;
       const int col = col_of(g, ex, a);
       const size_t i = (size_t)col * nrow + j;
       const bool own = owns_local_col(g, ex, a);
@@ -494,23 +506,26 @@ __device__ void cg_update(const DevGeom& g, Smem<P, T>& s, const Range& R, const
     }
     if (precond == PREC_JACOBI) continue;
     __syncthreads();
-    for (int t = threadIdx.x; t < Q * nr; t += blockDim.x) {
-      const int a = t / nr, k = t - a * nr;
-      const T* Xa = X + a * nr;
+    for (int t = threadIdx.x; t < ne * qn; t += blockDim.x) {
+      const int e = t / qn, rem = t - e * qn;
+      const int a = rem / nr, k = rem - a * nr, ex = ex0 + e;
+      const T* Xa = X + e * qn + a * nr;
       T v = 0;
       for (int j = 0; j < nr; ++j) v = fmx(pv.S[j * nr + k], Xa[j], v);
       RH[t] = v;
       if (owns_local_col(g, ex, a)) pv.rhat[(size_t)col_of(g, ex, a) * nr + k] = v;
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < nr; k += blockDim.x) {
+    for (int t = threadIdx.x; t < ne * nr; t += blockDim.x) {
+      const int e = t / nr, k = t - e * nr, ex = ex0 + e;
+      const T* RHe = RH + e * qn;
       const T* Zk = pv.Z + ((size_t)k * g.Nx + ex) * 2 * Pm;
       // the assembled residual at an interface node enters once: with the element that owns
       // that column (its left end), plus the walls' last column with the last element
-      T l = RH[k], r = owns_local_col(g, ex, P) ? RH[P * nr + k] : T(0);
+      T l = RHe[k], r = owns_local_col(g, ex, P) ? RHe[P * nr + k] : T(0);
 #pragma unroll
       for (int m = 0; m < Pm; ++m) {
-        const T f = RH[(1 + m) * nr + k];
+        const T f = RHe[(1 + m) * nr + k];
         l = fmx(-Zk[m], f, l);
         r = fmx(-Zk[Pm + m], f, r);
       }
@@ -547,11 +562,14 @@ __device__ void phase_backsub(const DevGeom& g, Smem<P, T>& s, const Range& R, c
                               const PrecView<T>& pv, const CgVecs<T>& V) {
   constexpr int Q = P + 1, Pm = P - 1;
   const int nrow = g.nrow, nr = pv.nr, N = pv.nif;
-  T* ZH = s.F1;   // [Q][nr]
-  for (int ex = R.e0; ex < R.e1; ++ex) {
-    const int jl = ex, jr = (ex + 1 == N) ? 0 : ex + 1;
-    for (int t = threadIdx.x; t < Q * nr; t += blockDim.x) {
-      const int a = t / nr, k = t - a * nr;
+  T* ZH = s.F1;   // [E][Q][nr]
+  const int E = g.chunk, qn = Q * nr;
+  for (int ex0 = R.e0; ex0 < R.e1; ex0 += E) {
+    const int ne = min(E, R.e1 - ex0);
+    for (int t = threadIdx.x; t < ne * qn; t += blockDim.x) {
+      const int e = t / qn, rem = t - e * qn;
+      const int a = rem / nr, k = rem - a * nr, ex = ex0 + e;
+      const int jl = ex, jr = (ex + 1 == N) ? 0 : ex + 1;
       const T zl = ldcg(pv.zb + (size_t)k * N + jl);
       const T zr = ldcg(pv.zb + (size_t)k * N + jr);
       T v;
@@ -570,12 +588,13 @@ __device__ void phase_backsub(const DevGeom& g, Smem<P, T>& s, const Range& R, c
       ZH[t] = v;
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < Q * nr; t += blockDim.x) {
-      const int a = t / nr, j = t - a * nr;
+    for (int t = threadIdx.x; t < ne * qn; t += blockDim.x) {
+      const int e = t / qn, rem = t - e * qn;
+      const int a = rem / nr, j = rem - a * nr, ex = ex0 + e;
       const bool own = owns_local_col(g, ex, a);
       const bool halo = is_halo_col(g, R, ex, a);
       if (!own && !halo) continue;
-      const T* Za = ZH + a * nr;
+      const T* Za = ZH + e * qn + a * nr;
       const T* Sj = pv.S + j * nr;
       T v = 0;
       for (int k = 0; k < nr; ++k) v = fmx(Sj[k], Za[k], v);
@@ -621,9 +640,9 @@ __device__ int cg_solve(const DevGeom& g, Smem<P, T>& s, const Range& R, const T
     // w = A u and the three inner products (u on owned columns and the halo column)
     const T* rc = V.r[cur];
     A acc[3] = {A(0), A(0), A(0)};   // γ = (r,u), δ = (u,Au), (r,r)
-    for (int ex = R.e0; ex < R.e1; ++ex) {
-      acc[1] += (A)apply_element_column<P, T>(
-          g, s, ex,
+    for (int ex0 = R.e0; ex0 < R.e1; ex0 += g.chunk) {
+      acc[1] += (A)apply_element_chunk<P, T>(
+          g, s, ex0, min(g.chunk, R.e1 - ex0),
           [&](int e, int a, int iz) -> T {
             if (iz == nrow - 1) return T(0);
             if (is_halo_col(g, R, e, a)) return V.uh[(size_t)tm.rank * nrow + iz];
@@ -686,9 +705,10 @@ __device__ bool fp64_residual(const DevGeom& g, Smem<P, double>& s, const Range&
   const int nrow = g.nrow;
   const double* x = A.x;
   const double* phis = A.phis;
-  for (int ex = R.e0; ex < R.e1; ++ex) {
-    apply_element_column<P, double>(
-        g, s, ex,
+  for (int ex0 = R.e0; ex0 < R.e1; ex0 += g.chunk) {
+    const int ne = min(g.chunk, R.e1 - ex0);
+    apply_element_chunk<P, double>(
+        g, s, ex0, ne,
         [&](int e, int a, int iz) -> double {
           const int col = col_of(g, e, a);
           return iz == nrow - 1 ? phis[col] : ldcg(x + (size_t)col * nrow + iz);
@@ -698,8 +718,8 @@ __device__ bool fp64_residual(const DevGeom& g, Smem<P, double>& s, const Range&
           else A.edge64[(size_t)e * nrow + iz] = y;
         });
     if (want_b)
-      apply_element_column<P, double>(
-          g, s, ex,
+      apply_element_chunk<P, double>(
+          g, s, ex0, ne,
           [&](int e, int a, int iz) -> double { return iz == nrow - 1 ? phis[col_of(g, e, a)] : 0.0; },
           [&](int e, int a, int iz, double y) {
             if (owns_local_col(g, e, a)) A.q64b[(size_t)col_of(g, e, a) * nrow + iz] = y;
@@ -746,7 +766,7 @@ __device__ bool solve_body(const DevGeom& g, const PcgArgs& A, const Team& tm, u
   const Range R = my_range(g, tm);
   const int nrow = g.nrow;
   Smem<P, double> s64;
-  s64.carve(smem_raw, nrow, g.Nz);
+  s64.carve(smem_raw, nrow, g.Nz, g.chunk);
   s64.load_tables(g);
   double rr = 0.0, bb = 0.0;
   if (!fp64_residual<P>(g, s64, R, tm, A, true, red, &s_flag, rr, bb)) return false;
@@ -770,7 +790,7 @@ __device__ bool solve_body(const DevGeom& g, const PcgArgs& A, const Team& tm, u
     rr = rr_out;
   } else {
     Smem<P, float> s32;
-    s32.carve(smem_raw, nrow, g.Nz);
+    s32.carve(smem_raw, nrow, g.Nz, g.chunk);
     const CgVecs<float> V{A.d32, {A.r32, A.r32b}, {A.p32b, A.s32b}, A.p32a, A.z32, A.uh32, A.q32, A.edge32,
                           g.invdiag32};
     // Refinement stops at the target residual, or once the corrections stop shrinking
@@ -1189,8 +1209,9 @@ cudaError_t launch_geometry_impl(const DevGeom& g, const double* eta, bool with_
 
 template <int P>
 cudaError_t launch_apply_elem_impl(const DevGeom& g, const double* x, double* q, double* edge, cudaStream_t s) {
-  const size_t smem = apply_smem_bytes(P, g.nrow, g.Nz, sizeof(double));
-  const int grid = g.Nx < 4096 ? g.Nx : 4096;
+  const size_t smem = apply_smem_bytes(P, g.nrow, g.Nz, g.chunk, sizeof(double));
+  const int nch = (g.Nx + g.chunk - 1) / g.chunk;
+  const int grid = nch < 4096 ? nch : 4096;
   cudaError_t e = cudaFuncSetAttribute(k_apply<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
   if (e != cudaSuccess) return e;
   k_apply<P><<<grid, kThreads, smem, s>>>(g, x, q, edge);

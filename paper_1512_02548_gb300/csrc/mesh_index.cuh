@@ -35,9 +35,9 @@ static __device__ __forceinline__ unsigned long long global_ns() {
 constexpr int kMaxDynSmem = 180 * 1024;   // opt-in ceiling; each launch passes its own size
 
 // Dynamic shared memory of the element-column apply (tables, one element column, fluxes).
-static inline size_t apply_smem_bytes(int P, int nrow, int Nz, size_t elem) {
+static inline size_t apply_smem_bytes(int P, int nrow, int Nz, int E, size_t elem) {
   const int Q = P + 1;
-  return elem * (size_t)(Q * Q + Q + nrow + 2 * Nz + 4 * Q + Q * nrow + 2 * Nz * Q * Q) + 16;
+  return elem * (size_t)(Q * Q + Q + nrow + (size_t)E * (2 * Nz + 4 * Q + Q * nrow + 2 * Nz * Q * Q)) + 16;
 }
 
 }  // namespace semgb

@@ -22,6 +22,7 @@ enum : int { ST_NOT_CONVERGED = 1, ST_NONFINITE = 2, ST_TIMEOUT = 4, ST_BAD_DEPT
 // Read-only view of a mesh for the volume kernels.
 struct DevGeom {
   int P, Nx, Nz, ncol, nrow, periodic;
+  int chunk;             // element columns a CTA processes together in one pass (≥ 1)
   const double* h;       // [ncol] still-water depth at the columns
   const double* hx_loc;  // [Nx*(P+1)] element-local ∂x h
   const double* dxe;     // [Nx] element widths Δx_e
@@ -33,6 +34,14 @@ struct DevGeom {
   float* invdiag32;      // same in FP32
   int* status;           // device status word
 };
+
+// Element columns processed together per CTA pass: enough that a pass has ~256–512 work
+// items when the element columns are small (few layers, low order), at most 16.
+inline int chunk_width(int P, int Nz) {
+  const int per = Nz * (P + 1) * (P + 1);
+  const int E = 384 / per;
+  return E < 1 ? 1 : (E > 16 ? 16 : E);
+}
 
 // Per-solve record written by the Krylov kernel and accumulated counters.
 struct SolveRecord {
@@ -183,7 +192,7 @@ template <int P> cudaError_t launch_stage_impl(int mixed, const StageArgs& a, in
 // Fused RK stage for instances of order P: capacity (CTAs per SM) at a given dynamic smem,
 // and the cooperative launch.
 cudaError_t stage_occupancy(int P, int mixed, size_t smem, int* per_sm);
-size_t stage_smem_bytes(int P, int nrow, int Nz);
+size_t stage_smem_bytes(int P, int nrow, int Nz, int chunk);
 cudaError_t launch_stage(int P, int mixed, const StageArgs& a, int grid, size_t smem, cudaStream_t s);
 // out[k] = status word of inst[k]; a nonzero word is cleared after it is read.
 cudaError_t launch_gather_status(const Instance* inst, int n, int* out, cudaStream_t s);
@@ -199,7 +208,7 @@ cudaError_t launch_apply_tile(int fp32, const DevGeom& g, const void* x, void* y
 // Allocation-free apply (scratch in a static device array of kNoAllocEdgeMax doubles).
 constexpr size_t kNoAllocEdgeMax = size_t(1) << 20;
 cudaError_t launch_apply_noalloc(const DevGeom& g, const double* x, double* y, cudaStream_t s);
-cudaError_t pcg_grid_size(int P, int Nz, int nrow, int Nx, int mixed, int* grid, size_t* smem);
+cudaError_t pcg_grid_size(int P, int Nz, int nrow, int Nx, int chunk, int mixed, int* grid, size_t* smem);
 cudaError_t launch_prec_setup(const DevGeom& g, const PrecSetup& ps, cudaStream_t s);
 cudaError_t launch_pcg(const DevGeom& g, const PcgArgs& a, int grid, size_t smem, cudaStream_t s);
 

@@ -301,7 +301,11 @@ def c5_requests(rate: float, count: int = 2000, seed: int = 0, nmin: float = 1e3
     Laplace solves and half ``nsteps``-step RK4 runs, on periodic tanks whose node count is
     log-uniform in [nmin, nmax]: P∈{4..10}, Nz∈{1,2,4}, Nx = max(2, round(n/(P(Nz·P+1)))),
     kh∈[0.5,3] and H/L∈[0.01,0.09] as for the uneven batch.  Returns (kind, arrival s,
-    workload, steps) sorted by arrival."""
+    workload, steps) sorted by arrival.
+
+    The step is dt = min(T/200, dt_max): fine meshes resolve short gravity waves, whose
+    frequency ω_max = (g π/Δx_min)^½ on the smallest GLL spacing Δx_min ≈ (Δx_e/2)(1 − cos π/P)
+    must satisfy ω_max dt ≤ 2.8 (RK4 on the imaginary axis); dt_max takes half of that."""
     gen = splitmix64(seed)
     t = 0.0
     out = []
@@ -316,10 +320,12 @@ def c5_requests(rate: float, count: int = 2000, seed: int = 0, nmin: float = 1e3
         HL = 0.01 + 0.08 * _uniform(gen)
         k = 1.0
         T = 2 * math.pi / linear_omega(k, kh / k)
+        dx_min = 0.5 * (2 * math.pi / k / Nx) * (1 - math.cos(math.pi / P))
+        dt_max = 0.5 * 2.8 / math.sqrt(G_EARTH * math.pi / dx_min)
         wl = Workload(name=f"C5 request {i}", P=P, Nx=Nx, Nz=Nz, length=2 * math.pi / k, periodic=True,
                       depth=kh / k, Pf=(3 * P + 1) // 2, filter_alpha=36.0, filter_s=12.0, filter_ic=P - 1,
-                      dt=T / 200, nsteps=nsteps if kind == "rk4" else 0, wave_height=HL * 2 * math.pi / k,
-                      wavenumber=k)
+                      dt=min(T / 200, dt_max), nsteps=nsteps if kind == "rk4" else 0,
+                      wave_height=HL * 2 * math.pi / k, wavenumber=k)
         out.append((kind, t, wl, nsteps if kind == "rk4" else 0))
     return out
 

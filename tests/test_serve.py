@@ -94,6 +94,12 @@ def test_c5_request_stream_matches_its_recipe():
         assert 4 <= wl.P <= 10 and wl.Nz in (1, 2, 4) and wl.Nx >= 2 and wl.periodic
         assert ns == (10 if kind == "rk4" else 0)
         assert 0.5 <= wl.depth <= 3.0 and wl.Pf == (3 * wl.P + 1) // 2
+        # stable explicit step: at most T/200, and short waves on the finest GLL spacing
+        # resolved within half of RK4's imaginary-axis limit
+        T = 2 * math.pi / math.sqrt(9.81 * math.tanh(wl.depth))
+        dx_min = 0.5 * (wl.length / wl.Nx) * (1 - math.cos(math.pi / wl.P))
+        assert wl.dt <= T / 200 * (1 + 1e-12)
+        assert math.sqrt(9.81 * math.pi / dx_min) * wl.dt <= 1.4 * (1 + 1e-12)
     n = np.array([x[2].n_nodes for x in r])
     assert n.min() > 500 and n.max() < 2.5e5
     # node counts log-uniform: median near the geometric mean of the range
