@@ -7,7 +7,10 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <tuple>
+#include <memory>
 #include <string>
 #include <utility>
 #include <vector>
@@ -310,6 +313,117 @@ const char* sem_last_error(void) { return t_err.c_str(); }
 
 int64_t sem_launch_count(void) { return g_launches.load(); }
 
+// Host tables of one (P, Nz, Pf, filter) combination, shared by every mesh that has it.
+struct ColumnTables {
+  Line L;
+  std::vector<double> MD, I, B, F, cw, Aii, Z, Sg, lam, dsl, sig;
+  long double S00 = 0, S01 = 0, S11 = 0;
+};
+
+static std::mutex g_ct_mu;
+static std::map<std::tuple<int, int, int, double, double, int>, std::shared_ptr<const ColumnTables>> g_ct;
+
+static int column_tables(const sem_params& p, std::shared_ptr<const ColumnTables>* out) {
+  const auto key = std::make_tuple(p.P, p.Nz, p.Pf, p.filter_alpha, p.filter_s, p.filter_ic);
+  {
+    std::lock_guard<std::mutex> lk(g_ct_mu);
+    auto it = g_ct.find(key);
+    if (it != g_ct.end()) { *out = it->second; return SEM_OK; }
+  }
+  auto t = std::make_shared<ColumnTables>();
+  const int P = p.P, Q = P + 1, Nz = p.Nz, nrow = Nz * P + 1, Qf = p.Pf + 1, Pm = P - 1;
+  Line Lf;
+  try {
+    t->L = make_line(P);
+    Lf = make_line(p.Pf);
+  } catch (const std::exception& e) {
+    return fail(SEM_ERR_INVALID_ARG, e.what());
+  }
+  const Line& L = t->L;
+  t->dsl.assign(Nz, 1.0 / Nz);
+  const std::vector<double>& dsl = t->dsl;
+  t->sig.resize(nrow);
+  for (int iz = 0; iz < nrow; ++iz) {
+    int l = iz / P; if (l >= Nz) l = Nz - 1;
+    const int b = iz - l * P;
+    t->sig[iz] = (double)l / Nz + 0.5 * (L.r[b] + 1.0) * dsl[l];
+  }
+  t->sig[nrow - 1] = 1.0;
+  t->MD = matmul(L.M, L.D, Q, Q, Q);
+  t->I = interpolation(L, Lf);                                        // Qf×Q
+  std::vector<double> It(Q * Qf);
+  for (int q = 0; q < Qf; ++q) for (int c = 0; c < Q; ++c) It[c * Qf + q] = t->I[q * Q + c];
+  t->B = matmul(It, Lf.M, Q, Qf, Qf);                                 // Q×Qf = Iᵀ M_f
+  t->F = filter_matrix(L, p.filter_alpha, p.filter_s, p.filter_ic);
+  // w̃ weights: v = M_σ⁻¹ e_top, c_l = (Δσ_l/2) M v|_l
+  t->cw.assign((size_t)Nz * Q, 0.0);
+  {
+    std::vector<long double> Ms((size_t)nrow * nrow, 0.0L);
+    for (int l = 0; l < Nz; ++l)
+      for (int a = 0; a < Q; ++a)
+        for (int b = 0; b < Q; ++b) Ms[(size_t)(l * P + a) * nrow + l * P + b] += 0.5L * dsl[l] * L.M[a * Q + b];
+    if (!invert(Ms, nrow)) return fail(SEM_ERR_INVALID_ARG, "sigma mass is singular");
+    for (int l = 0; l < Nz; ++l)
+      for (int b = 0; b < Q; ++b) {
+        long double s = 0.0L;
+        for (int c = 0; c < Q; ++c) s += 0.5L * dsl[l] * L.M[b * Q + c] * Ms[(size_t)(l * P + c) * nrow + (nrow - 1)];
+        t->cw[(size_t)l * Q + b] = (double)s;
+      }
+  }
+  // static condensation of M' (element scale Δx/2 · M)
+  t->Aii.assign((size_t)Pm * Pm, 0.0);
+  t->Z.assign((size_t)2 * Pm, 0.0);
+  {
+    std::vector<long double> Mii((size_t)Pm * Pm);
+    for (int i = 0; i < Pm; ++i) for (int k = 0; k < Pm; ++k) Mii[i * Pm + k] = L.M[(i + 1) * Q + (k + 1)];
+    if (!invert(Mii, Pm)) return fail(SEM_ERR_INVALID_ARG, "interior mass is singular");
+    for (int i = 0; i < Pm * Pm; ++i) t->Aii[i] = (double)Mii[i];
+    const int bn[2] = {0, P};
+    long double Zl[2][kMaxP];
+    for (int s2 = 0; s2 < 2; ++s2)
+      for (int i = 0; i < Pm; ++i) {
+        long double acc = 0.0L;
+        for (int k = 0; k < Pm; ++k) acc += (long double)L.M[bn[s2] * Q + (k + 1)] * Mii[k * Pm + i];
+        Zl[s2][i] = acc;
+        t->Z[s2 * Pm + i] = (double)acc;
+      }
+    auto sch = [&](int s1, int s2) {
+      long double acc = L.M[bn[s1] * Q + bn[s2]];
+      for (int i = 0; i < Pm; ++i) acc -= Zl[s1][i] * (long double)L.M[(i + 1) * Q + bn[s2]];
+      return acc;
+    };
+    t->S00 = sch(0, 0); t->S01 = sch(0, 1); t->S11 = sch(1, 1);
+  }
+  // σ-separable preconditioner: Kσ S = Mσ S Λ on the interior rows (Dirichlet at the surface),
+  // Kσ = Σ_l (2/Δσ_l) Dᵀ W D, Mσ = Σ_l (Δσ_l/2) W (GLL-lumped, as in the stiffness quadrature).
+  const int nr = nrow - 1;
+  t->Sg.assign((size_t)nr * nr, 0.0);
+  t->lam.assign(nr, 0.0);
+  {
+    std::vector<long double> Ks((size_t)nrow * nrow, 0.0L), Ms(nrow, 0.0L);
+    for (int l = 0; l < Nz; ++l)
+      for (int a = 0; a < Q; ++a) {
+        Ms[l * P + a] += 0.5L * dsl[l] * L.w[a];
+        for (int b = 0; b < Q; ++b) {
+          long double s2 = 0.0L;
+          for (int c = 0; c < Q; ++c) s2 += (long double)L.D[c * Q + a] * L.w[c] * L.D[c * Q + b];
+          Ks[(size_t)(l * P + a) * nrow + l * P + b] += (2.0L / dsl[l]) * s2;
+        }
+      }
+    std::vector<long double> Bm((size_t)nr * nr), ev, V;
+    for (int i = 0; i < nr; ++i)
+      for (int j = 0; j < nr; ++j) Bm[(size_t)i * nr + j] = Ks[(size_t)i * nrow + j] / std::sqrt(Ms[i] * Ms[j]);
+    sym_eig(Bm, nr, ev, V);
+    for (int k = 0; k < nr; ++k) t->lam[k] = (double)ev[k];
+    for (int j = 0; j < nr; ++j)
+      for (int k = 0; k < nr; ++k) t->Sg[(size_t)j * nr + k] = (double)(V[(size_t)j * nr + k] / std::sqrt(Ms[j]));
+  }
+  std::lock_guard<std::mutex> lk(g_ct_mu);
+  auto ins = g_ct.emplace(key, std::shared_ptr<const ColumnTables>(t));
+  *out = ins.first->second;
+  return SEM_OK;
+}
+
 static int mesh_create_impl(const sem_params* pin, const double* x_edges_h, const double* h_h, sem_mesh** out,
                             size_t* footprint_only);
 
@@ -362,138 +476,76 @@ static int mesh_create_impl(const sem_params* pin, const double* x_edges_h, cons
   if (rc) return rc;
 
   // ---- host tables --------------------------------------------------------------
-  Line L, Lf;
-  try {
-    L = make_line(P);
-    Lf = make_line(p.Pf);
-  } catch (const std::exception& e) {
-    return fail(SEM_ERR_INVALID_ARG, e.what());
-  }
+  // Tables that depend only on (P, Nz, Pf, filter) come from a per-process cache (they are
+  // built in long double, which is software-emulated on some hosts); the x-dependent ones
+  // below are O(Nx) in double.
+  std::shared_ptr<const ColumnTables> ct;
+  rc = column_tables(p, &ct);
+  if (rc) return rc;
+  const Line& L = ct->L;
+  const std::vector<double>& MD = ct->MD;
+  const std::vector<double>& I = ct->I;
+  const std::vector<double>& B = ct->B;
+  const std::vector<double>& F = ct->F;
+  const std::vector<double>& cw = ct->cw;
+  const std::vector<double>& Aii = ct->Aii;
+  const std::vector<double>& Z = ct->Z;
+  const std::vector<double>& Sg = ct->Sg;
+  const std::vector<double>& lam = ct->lam;
+  const std::vector<double>& dsl = ct->dsl;
+  const std::vector<double>& sig = ct->sig;
   const int Qf = p.Pf + 1, Pm = P - 1;
-  std::vector<double> dxe(Nx), dsl(Nz), sig(nrow), hx_loc((size_t)Nx * Q), se(Nx);
+  std::vector<double> dxe(Nx), hx_loc((size_t)Nx * Q), se(Nx);
   for (int e = 0; e < Nx; ++e) { dxe[e] = x_edges_h[e + 1] - x_edges_h[e]; se[e] = 0.5 * dxe[e]; }
-  for (int l = 0; l < Nz; ++l) dsl[l] = 1.0 / Nz;
-  for (int iz = 0; iz < nrow; ++iz) {
-    int l = iz / P; if (l >= Nz) l = Nz - 1;
-    const int b = iz - l * P;
-    sig[iz] = (double)l / Nz + 0.5 * (L.r[b] + 1.0) * dsl[l];
-  }
-  sig[nrow - 1] = 1.0;
   for (int e = 0; e < Nx; ++e)
     for (int a = 0; a < Q; ++a) {
-      long double s = 0.0L;
+      double s = 0.0;
       for (int c = 0; c < Q; ++c) {
         int col = e * P + c; if (col >= ncol) col -= ncol;
-        s += (long double)L.D[a * Q + c] * h_h[col];
+        s = std::fma(L.D[a * Q + c], h_h[col], s);
       }
-      hx_loc[(size_t)e * Q + a] = (double)(s * 2.0L / dxe[e]);
+      hx_loc[(size_t)e * Q + a] = s * 2.0 / dxe[e];
     }
-  std::vector<double> MD = matmul(L.M, L.D, Q, Q, Q);
-  std::vector<double> I = interpolation(L, Lf);                     // Qf×Q
-  std::vector<double> It(Q * Qf);
-  for (int q = 0; q < Qf; ++q) for (int c = 0; c < Q; ++c) It[c * Qf + q] = I[q * Q + c];
-  std::vector<double> B = matmul(It, Lf.M, Q, Qf, Qf);               // Q×Qf = Iᵀ M_f
-  std::vector<double> F = filter_matrix(L, p.filter_alpha, p.filter_s, p.filter_ic);
-  // w̃ weights: v = M_σ⁻¹ e_top, c_l = (Δσ_l/2) M v|_l
-  std::vector<double> cw((size_t)Nz * Q);
-  {
-    std::vector<long double> Ms((size_t)nrow * nrow, 0.0L);
-    for (int l = 0; l < Nz; ++l)
-      for (int a = 0; a < Q; ++a)
-        for (int b = 0; b < Q; ++b) Ms[(size_t)(l * P + a) * nrow + l * P + b] += 0.5L * dsl[l] * L.M[a * Q + b];
-    if (!invert(Ms, nrow)) return fail(SEM_ERR_INVALID_ARG, "sigma mass is singular");
-    for (int l = 0; l < Nz; ++l)
-      for (int b = 0; b < Q; ++b) {
-        long double s = 0.0L;
-        for (int c = 0; c < Q; ++c) s += 0.5L * dsl[l] * L.M[b * Q + c] * Ms[(size_t)(l * P + c) * nrow + (nrow - 1)];
-        cw[(size_t)l * Q + b] = (double)s;
-      }
-  }
-  // static condensation of M' (element scale Δx/2 · M)
-  std::vector<double> Aii((size_t)Pm * Pm), Z((size_t)2 * Pm);
-  long double S00, S01, S11;
-  {
-    std::vector<long double> Mii((size_t)Pm * Pm);
-    for (int i = 0; i < Pm; ++i) for (int k = 0; k < Pm; ++k) Mii[i * Pm + k] = L.M[(i + 1) * Q + (k + 1)];
-    if (!invert(Mii, Pm)) return fail(SEM_ERR_INVALID_ARG, "interior mass is singular");
-    for (int i = 0; i < Pm * Pm; ++i) Aii[i] = (double)Mii[i];
-    const int bn[2] = {0, P};
-    long double Zl[2][kMaxP];
-    for (int s2 = 0; s2 < 2; ++s2)
-      for (int i = 0; i < Pm; ++i) {
-        long double acc = 0.0L;
-        for (int k = 0; k < Pm; ++k) acc += (long double)L.M[bn[s2] * Q + (k + 1)] * Mii[k * Pm + i];
-        Zl[s2][i] = acc;
-        Z[s2 * Pm + i] = (double)acc;
-      }
-    auto sch = [&](int s1, int s2) {
-      long double acc = L.M[bn[s1] * Q + bn[s2]];
-      for (int i = 0; i < Pm; ++i) acc -= Zl[s1][i] * (long double)L.M[(i + 1) * Q + bn[s2]];
-      return acc;
-    };
-    S00 = sch(0, 0); S01 = sch(0, 1); S11 = sch(1, 1);
-  }
+  // M' interface tridiagonal (Thomas factors; Sherman–Morrison closure when periodic)
   const int N = p.periodic ? Nx : Nx + 1;
   std::vector<double> th_e(N, 0.0), th_m(N, 0.0), th_cp(N, 0.0), th_z(N, 0.0);
   double th_vlast = 0.0, th_fac = 0.0;
   {
-    std::vector<long double> d(N, 0.0L), e(N, 0.0L);
+    const double S00 = ct->S00, S01 = ct->S01, S11 = ct->S11;
+    std::vector<double> d(N, 0.0), e(N, 0.0);
     for (int j = 0; j < Nx; ++j) {
       const int jr = (j + 1) % N;
       d[j] += se[j] * S00;
       d[jr] += se[j] * S11;
       e[j] = se[j] * S01;            // coupling j ↔ j+1 (periodic: e[N−1] is the corner)
     }
-    long double gamma = 0.0L, corner = 0.0L;
+    double gamma = 0.0, corner = 0.0;
     if (p.periodic) {
       corner = e[N - 1];
       gamma = -d[0];
       d[0] -= gamma;
       d[N - 1] -= corner * corner / gamma;
     }
-    std::vector<long double> m(N), cp(N, 0.0L);
+    std::vector<double> m(N), cp(N, 0.0);
     for (int j = 0; j < N; ++j) {
-      const long double piv = j == 0 ? d[0] : d[j] - e[j - 1] * cp[j - 1];
-      m[j] = 1.0L / piv;
+      const double piv = j == 0 ? d[0] : d[j] - e[j - 1] * cp[j - 1];
+      m[j] = 1.0 / piv;
       if (j < N - 1) cp[j] = e[j] * m[j];
     }
-    for (int j = 0; j < N; ++j) { th_e[j] = (double)e[j]; th_m[j] = (double)m[j]; th_cp[j] = (double)cp[j]; }
+    th_e = e; th_m = m; th_cp = cp;
     if (p.periodic) {
-      std::vector<long double> u(N, 0.0L), y(N);
+      std::vector<double> u(N, 0.0), y(N);
       u[0] = gamma;
       u[N - 1] = corner;
       for (int j = 0; j < N; ++j) y[j] = (j == 0 ? u[0] : u[j] - e[j - 1] * y[j - 1]) * m[j];
       for (int j = N - 2; j >= 0; --j) y[j] -= cp[j] * y[j + 1];
-      const long double vl = corner / gamma;
-      for (int j = 0; j < N; ++j) th_z[j] = (double)y[j];
-      th_vlast = (double)vl;
-      th_fac = (double)(1.0L / (1.0L + y[0] + vl * y[N - 1]));
+      const double vl = corner / gamma;
+      th_z = y;
+      th_vlast = vl;
+      th_fac = 1.0 / (1.0 + y[0] + vl * y[N - 1]);
     }
   }
-
-  // σ-separable preconditioner: Kσ S = Mσ S Λ on the interior rows (Dirichlet at the surface),
-  // Kσ = Σ_l (2/Δσ_l) Dᵀ W D, Mσ = Σ_l (Δσ_l/2) W (GLL-lumped, as in the stiffness quadrature).
   const int nr = nrow - 1;
-  std::vector<double> Sg((size_t)nr * nr), lam(nr);
-  {
-    std::vector<long double> Ks((size_t)nrow * nrow, 0.0L), Ms(nrow, 0.0L);
-    for (int l = 0; l < Nz; ++l)
-      for (int a = 0; a < Q; ++a) {
-        Ms[l * P + a] += 0.5L * dsl[l] * L.w[a];
-        for (int b = 0; b < Q; ++b) {
-          long double s2 = 0.0L;
-          for (int c = 0; c < Q; ++c) s2 += (long double)L.D[c * Q + a] * L.w[c] * L.D[c * Q + b];
-          Ks[(size_t)(l * P + a) * nrow + l * P + b] += (2.0L / dsl[l]) * s2;
-        }
-      }
-    std::vector<long double> B((size_t)nr * nr), ev, V;
-    for (int i = 0; i < nr; ++i)
-      for (int j = 0; j < nr; ++j) B[(size_t)i * nr + j] = Ks[(size_t)i * nrow + j] / std::sqrt(Ms[i] * Ms[j]);
-    sym_eig(B, nr, ev, V);
-    for (int k = 0; k < nr; ++k) lam[k] = (double)ev[k];
-    for (int j = 0; j < nr; ++j)
-      for (int k = 0; k < nr; ++k) Sg[(size_t)j * nr + k] = (double)(V[(size_t)j * nr + k] / std::sqrt(Ms[j]));
-  }
 
   // ---- device allocation -------------------------------------------------------
   sem_mesh* m = new sem_mesh;
