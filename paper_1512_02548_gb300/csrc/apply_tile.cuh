@@ -37,7 +37,7 @@ struct TileLayout {
   }
   // elements of the dynamic shared memory (of type T)
   __host__ __device__ size_t count(int nrow, int Nz) const {
-    return (size_t)tcols * XS + 3 * (size_t)nline + (size_t)en_max * Q * 4 + (size_t)en_max * Nz * 2 + nrow;
+    return (size_t)tcols * XS + 3 * (size_t)nline + (size_t)en_max * Q * 4 + (size_t)en_max * Nz * 2 + nrow + Q;
   }
 };
 
@@ -57,12 +57,19 @@ __global__ void __launch_bounds__(kThreads) k_apply_tile(DevGeom g, const T* __r
   T* Gs = Ys + L.nline;                     // [en][Q][4] d, 1/d, ∂xh, ∂xd
   T* Cs = Gs + (size_t)L.en_max * Q * 4;    // [en][Nz][2] Δσ/Δx, Δx/Δσ
   T* Ss = Cs + (size_t)L.en_max * Nz * 2;   // [nrow] σ
-  const T* D = CT<T>::D() + d_off(P);
+  T* Ws = Ss + nrow;                        // [Q] GLL weights (indexed per thread)
+  const T* D = CT<T>::D() + d_off(P);       // compile-time indices only: constant operands
   const T* w = CT<T>::w() + w_off(P);
   const T* geo = geo_ptr<T>(g);
   for (int t = threadIdx.x; t < nrow; t += blockDim.x) Ss[t] = (T)g.sig[t];
+  for (int t = threadIdx.x; t < Q; t += blockDim.x) Ws[t] = w[t];
   const int ntiles = (Nx + E - 1) / E;
-  const int lines_per_el = Nz * Q;
+  const int lpe = Nz * Q;                                   // lines per element (x- or σ-lines)
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  // line index li = threadIdx.x + k·blockDim.x as (element, line in element), stepped without
+  // dividing: line 0 of the loop and the step of blockDim.x lines
+  const int le0 = threadIdx.x / lpe, lr0 = threadIdx.x - le0 * lpe;
+  const int lde = blockDim.x / lpe, ldr = blockDim.x - lde * lpe;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int ex0 = tile * E;
     const int ne = min(E, Nx - ex0);
@@ -70,13 +77,13 @@ __global__ void __launch_bounds__(kThreads) k_apply_tile(DevGeom g, const T* __r
     const bool has_left = g.periodic || ex0 > 0;
     const int nc = en * P + 1;
     __syncthreads();                             // the previous tile's readers are done
-    // ---- stage the tile: nodal values, geometry, layer ratios ----
-    for (int t = threadIdx.x; t < nc * nrow; t += blockDim.x) {
-      const int j = t / nrow, r = t - j * nrow;
+    // ---- stage the tile: nodal values (a warp per column), geometry, layer ratios ----
+    for (int j = warp; j < nc; j += nwarps) {
       int gc = (ex0 - 1) * P + j;
       if (gc < 0) gc = g.periodic ? gc + ncol : -1;
       else if (gc >= ncol) gc -= ncol;           // periodic: column Nx·P is column 0
-      Xs[j * XS + r] = gc >= 0 ? __ldg(x + (size_t)gc * nrow + r) : T(0);
+      const T* xc = x + (size_t)(gc < 0 ? 0 : gc) * nrow;
+      for (int r = lane; r < nrow; r += 32) Xs[j * XS + r] = gc >= 0 ? __ldg(xc + r) : T(0);
     }
     for (int t = threadIdx.x; t < en * Q * 4; t += blockDim.x) {
       const int e = t / (Q * 4);
@@ -88,16 +95,15 @@ __global__ void __launch_bounds__(kThreads) k_apply_tile(DevGeom g, const T* __r
       const int e = t / Nz, l = t - e * Nz;
       int ge = ex0 - 1 + e;
       if (ge < 0) ge = g.periodic ? ge + Nx : 0;
-      const double dxe = g.dxe[ge], dsl = g.dsl[l];
-      Cs[2 * t] = (T)(dsl / dxe);
-      Cs[2 * t + 1] = (T)(dxe / dsl);
+      const T dxe = (T)g.dxe[ge], dsl = (T)g.dsl[l];   // ratios in the kernel's own precision
+      Cs[2 * t] = dsl / dxe;
+      Cs[2 * t + 1] = dxe / dsl;
     }
     __syncthreads();
-    const int nlines = en * lines_per_el;
-    const int first = has_left ? 0 : lines_per_el;   // walls: no element left of x = 0
+    const int e_first = has_left ? 0 : 1;        // walls: no element left of x = 0
     // ---- 1. x-lines: u_r ----
-    for (int li = first + threadIdx.x; li < nlines; li += blockDim.x) {
-      const int e = li / lines_per_el, rem = li - e * lines_per_el;
+    for (int e = e_first + le0, rem = lr0; e < en; e += lde, rem += ldr) {
+      if (rem >= lpe) { rem -= lpe; ++e; if (e >= en) break; }
       const int l = rem / Q, b = rem - l * Q;
       const T* X = Xs + (e * P) * XS + l * P + b;
       T u[Q];
@@ -114,8 +120,8 @@ __global__ void __launch_bounds__(kThreads) k_apply_tile(DevGeom g, const T* __r
     }
     __syncthreads();
     // ---- 2. σ-lines: u_t, F1, F2 and the σ part of the transpose ----
-    for (int li = first + threadIdx.x; li < nlines; li += blockDim.x) {
-      const int e = li / lines_per_el, rem = li - e * lines_per_el;
+    for (int e = e_first + le0, rem = lr0; e < en; e += lde, rem += ldr) {
+      if (rem >= lpe) { rem -= lpe; ++e; if (e >= en) break; }
       const int l = rem / Q, a = rem - l * Q;
       const T* X = Xs + (e * P + a) * XS + l * P;
       T u[Q];
@@ -123,9 +129,9 @@ __global__ void __launch_bounds__(kThreads) k_apply_tile(DevGeom g, const T* __r
       for (int c = 0; c < Q; ++c) u[c] = X[c];
       const T* gq = Gs + (e * Q + a) * 4;
       const T c0 = Cs[2 * (e * Nz + l)], c1 = Cs[2 * (e * Nz + l) + 1];
-      const T g11 = w[a] * c0 * gq[0];           // w_a Δσ/Δx d
-      const T g22 = w[a] * c1 * gq[1];           // w_a Δx/Δσ /d
-      const T wa = w[a], hx = gq[2], dxd = gq[3];
+      const T wa = Ws[a], hx = gq[2], dxd = gq[3];
+      const T g11 = wa * c0 * gq[0];             // w_a Δσ/Δx d
+      const T g22 = wa * c1 * gq[1];             // w_a Δx/Δσ /d
       const T* sg = Ss + l * P;
       const int base = (e * Nz + l) * Q;
       T f2[Q];
@@ -151,8 +157,8 @@ __global__ void __launch_bounds__(kThreads) k_apply_tile(DevGeom g, const T* __r
     }
     __syncthreads();
     // ---- 3. x-lines: the element contribution (into the u_r buffer) ----
-    for (int li = first + threadIdx.x; li < nlines; li += blockDim.x) {
-      const int e = li / lines_per_el, rem = li - e * lines_per_el;
+    for (int e = e_first + le0, rem = lr0; e < en; e += lde, rem += ldr) {
+      if (rem >= lpe) { rem -= lpe; ++e; if (e >= en) break; }
       const int l = rem / Q, b = rem - l * Q;
       const int row = ((e * Nz + l) * Q + b) * QP;
       T f1[Q];
@@ -169,23 +175,25 @@ __global__ void __launch_bounds__(kThreads) k_apply_tile(DevGeom g, const T* __r
     __syncthreads();
     // ---- 4. gather: own columns [P, P + ne·P) (plus the last column between walls) ----
     const bool last_wall = !g.periodic && ex0 + ne == Nx;
-    const int nout = (ne * P + (last_wall ? 1 : 0)) * nrow;
+    const int nout = ne * P + (last_wall ? 1 : 0);   // output columns
     T* yt = y + (size_t)ex0 * P * nrow;
-    for (int t = threadIdx.x; t < nout; t += blockDim.x) {
-      const int jj = t / nrow, r = t - jj * nrow;
+    for (int jj = warp; jj < nout; jj += nwarps) {   // a warp per output column
       const int j = P + jj;
       int e = j / P, a = j - e * P;
       if (e == en) { e = en - 1; a = P; }       // right wall column
-      int l = r / P, b = r - l * P;
-      if (l == Nz) { l = Nz - 1; b = P; }       // surface row
       const bool left = a == 0 && (e > 1 || has_left);   // the element left of column j exists
-      T s = Ur[((e * Nz + l) * Q + b) * QP + a];
-      if (left) s += Ur[(((e - 1) * Nz + l) * Q + b) * QP + P];
-      if (b == 0 && l > 0) {
-        s += Ur[((e * Nz + l - 1) * Q + P) * QP + a];
-        if (left) s += Ur[(((e - 1) * Nz + l - 1) * Q + P) * QP + P];
+      T* yc = yt + (size_t)jj * nrow;
+      for (int r = lane; r < nrow; r += 32) {
+        int l = r / P, b = r - l * P;
+        if (l == Nz) { l = Nz - 1; b = P; }     // surface row
+        T s = Ur[((e * Nz + l) * Q + b) * QP + a];
+        if (left) s += Ur[(((e - 1) * Nz + l) * Q + b) * QP + P];
+        if (b == 0 && l > 0) {
+          s += Ur[((e * Nz + l - 1) * Q + P) * QP + a];
+          if (left) s += Ur[(((e - 1) * Nz + l - 1) * Q + P) * QP + P];
+        }
+        yc[r] = -s;
       }
-      yt[t] = -s;
     }
   }
 }

@@ -223,8 +223,23 @@ def _uniform(gen) -> float:
     return (next(gen) >> 11) * (1.0 / (1 << 53))
 
 
+def stable_dt(T: float, P: int, Nx: int, length: float, depth: float, H: float, k: float) -> float:
+    """Explicit RK4 step for a periodic tank: min(T/200, dt_grav, dt_adv).
+
+    Short gravity waves on the smallest GLL spacing Δx_min ≈ (Δx_e/2)(1 − cos π/P) have
+    ω_max = (g π/Δx_min)^½, and RK4 needs ω_max dt ≤ 2.8 on the imaginary axis: dt_grav takes
+    half of that.  The nonlinear terms advect with the surface velocity
+    u_max = (g H k/2ω) cosh(k(h + η_max))/cosh(kh) (linear theory at the crest, 20% margin):
+    dt_adv = Δx_min/(2 u_max), a Courant number of ½ on the finest spacing."""
+    dx_min = 0.5 * (length / Nx) * (1 - math.cos(math.pi / P))
+    om = linear_omega(k, depth)
+    u_max = 1.2 * (G_EARTH * H * k / (2 * om)) * math.cosh(k * (depth + H / 2 + k * H * H / 8)) / math.cosh(k * depth)
+    return min(T / 200, 0.5 * 2.8 / math.sqrt(G_EARTH * math.pi / dx_min), 0.5 * dx_min / u_max)
+
+
 def c3_instances(count: int = 512, seed: int = 0) -> list[Workload]:
-    """Uneven periodic tanks: Nx∈[16,128], Nz∈{1,2,4}, P∈{4..8}, kh∈[0.5,3], H/L∈[0.01,0.09]."""
+    """Uneven periodic tanks: Nx∈[16,128], Nz∈{1,2,4}, P∈{4..8}, kh∈[0.5,3], H/L∈[0.01,0.09];
+    step stable_dt."""
     gen = splitmix64(seed)
     out = []
     for i in range(count):
@@ -236,10 +251,12 @@ def c3_instances(count: int = 512, seed: int = 0) -> list[Workload]:
         k = 1.0
         h = kh / k
         T = 2 * math.pi / linear_omega(k, h)
+        H = HL * 2 * math.pi / k
         out.append(Workload(name=f"C3 tank {i}", P=P, Nx=Nx, Nz=Nz, length=2 * math.pi / k,
                             periodic=True, depth=h, Pf=(3 * P + 1) // 2,
                             filter_alpha=36.0, filter_s=12.0, filter_ic=P - 1,
-                            dt=T / 200, nsteps=1, wave_height=HL * 2 * math.pi / k, wavenumber=k))
+                            dt=stable_dt(T, P, Nx, 2 * math.pi / k, h, H, k), nsteps=1, wave_height=H,
+                            wavenumber=k))
     return out
 
 
@@ -303,9 +320,7 @@ def c5_requests(rate: float, count: int = 2000, seed: int = 0, nmin: float = 1e3
     kh∈[0.5,3] and H/L∈[0.01,0.09] as for the uneven batch.  Returns (kind, arrival s,
     workload, steps) sorted by arrival.
 
-    The step is dt = min(T/200, dt_max): fine meshes resolve short gravity waves, whose
-    frequency ω_max = (g π/Δx_min)^½ on the smallest GLL spacing Δx_min ≈ (Δx_e/2)(1 − cos π/P)
-    must satisfy ω_max dt ≤ 2.8 (RK4 on the imaginary axis); dt_max takes half of that."""
+    The step is stable_dt (T/200, bounded by RK4 stability on the finest GLL spacing)."""
     gen = splitmix64(seed)
     t = 0.0
     out = []
@@ -320,12 +335,11 @@ def c5_requests(rate: float, count: int = 2000, seed: int = 0, nmin: float = 1e3
         HL = 0.01 + 0.08 * _uniform(gen)
         k = 1.0
         T = 2 * math.pi / linear_omega(k, kh / k)
-        dx_min = 0.5 * (2 * math.pi / k / Nx) * (1 - math.cos(math.pi / P))
-        dt_max = 0.5 * 2.8 / math.sqrt(G_EARTH * math.pi / dx_min)
+        H = HL * 2 * math.pi / k
         wl = Workload(name=f"C5 request {i}", P=P, Nx=Nx, Nz=Nz, length=2 * math.pi / k, periodic=True,
                       depth=kh / k, Pf=(3 * P + 1) // 2, filter_alpha=36.0, filter_s=12.0, filter_ic=P - 1,
-                      dt=min(T / 200, dt_max), nsteps=nsteps if kind == "rk4" else 0,
-                      wave_height=HL * 2 * math.pi / k, wavenumber=k)
+                      dt=stable_dt(T, P, Nx, 2 * math.pi / k, kh / k, H, k), nsteps=nsteps if kind == "rk4" else 0,
+                      wave_height=H, wavenumber=k)
         out.append((kind, t, wl, nsteps if kind == "rk4" else 0))
     return out
 

@@ -100,6 +100,11 @@ def test_c5_request_stream_matches_its_recipe():
         dx_min = 0.5 * (wl.length / wl.Nx) * (1 - math.cos(math.pi / wl.P))
         assert wl.dt <= T / 200 * (1 + 1e-12)
         assert math.sqrt(9.81 * math.pi / dx_min) * wl.dt <= 1.4 * (1 + 1e-12)
+        # Courant number ≤ ½ for the surface velocity of linear theory at the crest
+        H, k, h = wl.wave_height, wl.wavenumber, wl.depth
+        om = math.sqrt(9.81 * k * math.tanh(k * h))
+        u = 9.81 * H * k / (2 * om) * math.cosh(k * (h + H / 2)) / math.cosh(k * h)
+        assert u * wl.dt / dx_min <= 0.5
     n = np.array([x[2].n_nodes for x in r])
     assert n.min() > 500 and n.max() < 2.5e5
     # node counts log-uniform: median near the geometric mean of the range
