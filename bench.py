@@ -139,9 +139,15 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+STAGE_SOURCES = ("laplace_device.cuh", "surface_device.cuh", "sem_internal.cuh", "mesh_index.cuh")
+
+
 def kernel_source_hash() -> str:
-    src = os.path.join(ROOT, "paper_1512_02548_gb300", "csrc", "kernels_laplace.cu")
-    return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    """Hash of the device sources the fused stage kernel is compiled from."""
+    h = hashlib.sha256()
+    for f in STAGE_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_1512_02548_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
 
 
 def profiled_traffic(kernel: str):
@@ -510,7 +516,7 @@ def run_gpu(args):
                      "achieved": achieved,
                      "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
                      "peak_source": "nominal GB300 FP64 rate, 1.25 TFLOP/s",
-                     "traffic": profiled_traffic("k_pcg")},
+                     "traffic": profiled_traffic("k_stage")},
         "e2e": e2e,
         "gpu_launches": gpu_launches,
         "clocks": clk,

@@ -31,6 +31,7 @@
 // internal linkage, including each order's copy of the constant tables.
 #pragma once
 #include <cooperative_groups.h>
+#include <mutex>
 
 #include "mesh_index.cuh"
 #include "surface_device.cuh"
@@ -1283,12 +1284,27 @@ cudaError_t launch_apply_tile_impl(int fp32, const DevGeom& g, const void* x, vo
   const size_t smem = apply_tile_smem<P>(E, g.nrow, g.Nz, elem);
   if (smem > (size_t)kMaxDynSmem) return cudaErrorInvalidValue;
   const void* fn = fp32 ? (const void*)k_apply_tile<P, float> : (const void*)k_apply_tile<P, double>;
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
-  if (e != cudaSuccess) return e;
+  // the attribute, the SM count and the occupancy for the last (device, precision, smem) are
+  // kept, so that a repeated apply costs one launch on the host
+  static std::mutex mu;
+  static int last_dev[2] = {-1, -1}, last_sms[2] = {0, 0}, last_per_sm[2] = {0, 0};
+  static size_t last_smem[2] = {0, 0};
   int dev = 0, sms = 0, per_sm = 0;
-  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem)) != cudaSuccess) return e;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    const int k = fp32 ? 1 : 0;
+    if (last_dev[k] != dev || last_smem[k] != smem) {
+      if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem)) != cudaSuccess)
+        return e;
+      if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+      if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem)) != cudaSuccess) return e;
+      last_dev[k] = dev; last_smem[k] = smem; last_sms[k] = sms; last_per_sm[k] = per_sm;
+    }
+    sms = last_sms[k];
+    per_sm = last_per_sm[k];
+  }
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   const long long ntiles = (g.Nx + E - 1) / E;
   const int grid = (int)(ntiles < (long long)per_sm * sms ? ntiles : (long long)per_sm * sms);
