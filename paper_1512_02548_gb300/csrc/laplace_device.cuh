@@ -321,24 +321,44 @@ struct Team {
 
 // Returns false (and sets ST_TIMEOUT) if the other CTAs of the team did not arrive in time;
 // the caller must then return without touching another barrier.
+// Scoped atomics of the barrier (PTX memory model): arrivals are acquire-release RMWs on the
+// counter, the last arrival publishes the next generation with a release, and waiters poll it
+// with acquire loads.  The CTA's own writes are ordered before thread 0's arrival by the
+// __syncthreads that precedes it; after the wait, the closing __syncthreads orders the other
+// CTAs' writes before every thread of this CTA.  No separate fences.
+static __device__ __forceinline__ unsigned bar_arrive(unsigned* p) {
+  unsigned old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(old) : "l"(p) : "memory");
+  return old;
+}
+static __device__ __forceinline__ unsigned bar_load(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+static __device__ __forceinline__ void bar_reset(unsigned* p) {
+  asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" :: "l"(p) : "memory");
+}
+static __device__ __forceinline__ void bar_publish(unsigned* p) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], 1;" :: "l"(p) : "memory");
+}
+
 static __device__ __forceinline__ bool grid_barrier(const Team& tm, int* s_flag) {
   __syncthreads();
   if (tm.size == 1) return true;
   if (threadIdx.x == 0) {
     unsigned int* bar = tm.bar;
-    volatile unsigned int* vgen = bar + 1;
-    const unsigned int gen = *vgen;
-    __threadfence();
-    const unsigned int prev = atomicAdd(bar, 1u);
+    // the generation cannot advance before this CTA arrives, so a plain read suffices
+    const unsigned int gen = bar_load(bar + 1);
+    const unsigned int prev = bar_arrive(bar);
     int ok = 1;
     if (prev == (unsigned int)tm.size - 1) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
+      bar_reset(bar);
+      bar_publish(bar + 1);
     } else {
       const unsigned long long t0 = global_ns();
       unsigned int spins = 0;
-      while (*vgen == gen) {
+      while (bar_load(bar + 1) == gen) {
         if ((++spins & 63u) == 0 && global_ns() - t0 > kBarrierTimeoutNs) {
           atomicOr(tm.status, ST_TIMEOUT);
           ok = 0;
@@ -347,7 +367,6 @@ static __device__ __forceinline__ bool grid_barrier(const Team& tm, int* s_flag)
         __nanosleep(20);
       }
     }
-    __threadfence();
     *s_flag = ok;
   }
   __syncthreads();
