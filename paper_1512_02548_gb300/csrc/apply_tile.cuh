@@ -8,6 +8,13 @@
 // buffer, no second kernel and no atomics.  The left element is recomputed by both
 // neighbouring tiles (1/E extra arithmetic, its x values come from L2).
 //
+// The CTAs are persistent and stage their tiles' nodal values with bulk copies (TMA,
+// cp.async.bulk) into two shared-memory buffers: the copy of the next tile is in flight
+// while the current one is computed.  A tile's values are one contiguous range of x
+// (columns are stored back to back); the copy starts at the 16-byte boundary below the
+// range and the tile is read at the resulting offset.  Tiles whose range wraps around the
+// periodic end, or whose rounded range would pass the end of x, are staged with plain loads.
+//
 // Per tile, with the tile's nodal values staged in shared memory:
 //   1. x-lines (element e, layer l, row b): u_r(a) = Σ_c D_ac u(c,b) for all a, in registers;
 //   2. σ-lines (e, l, column a): u_t(b) = Σ_c D_bc u(a,c); the geometric factors of column a
@@ -23,46 +30,125 @@
 
 namespace semgb {
 
+// ---- bulk copies with mbarrier completion (sm_90+ PTX) ----
+static __device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+static __device__ __forceinline__ void mbar_init(unsigned long long* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(bar)) : "memory");
+}
+static __device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// Generic-proxy accesses of shared memory before this point are ordered before later
+// async-proxy (bulk copy) accesses.
+static __device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+static __device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile(
+      "{\n\t.reg .b64 st;\n\t"
+      "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%3], %2;\n\t"
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n\t}"
+      :: "r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+static __device__ __forceinline__ bool mbar_test(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+  return ok != 0;
+}
+// Wait for a phase of the mbarrier, at most `limit_ns` of wall-clock time.
+static __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity,
+                                                 unsigned long long limit_ns) {
+  if (mbar_test(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (unsigned spins = 1;; ++spins) {
+    if (mbar_test(bar, parity)) return true;
+    if ((spins & 255u) == 0 && global_ns() - t0 > limit_ns) return false;
+  }
+}
+
+constexpr unsigned long long kCopyTimeoutNs = 2000000000ull;   // 2 s
+
 template <int P>
 struct TileLayout {
   static constexpr int Q = P + 1;
   static constexpr int QP = (Q % 2 == 0) ? Q + 1 : Q;   // odd stride of the line buffers
-  int E, en_max, XS, tcols, nline;
-  __host__ __device__ TileLayout(int E_, int nrow, int Nz) {
+  int E, en_max, tcols, xbuf, nline;
+  __host__ __device__ TileLayout(int E_, int nrow, int Nz, int elem) {
     E = E_;
     en_max = E + 1;
-    XS = nrow | 1;
     tcols = en_max * P + 1;
+    // one staging buffer: the tile's columns back to back; the 16-byte-aligned copy adds less
+    // than 16 bytes on each side; rounded up to 16 bytes
+    const int per16 = 16 / elem;
+    xbuf = ((tcols * nrow + 2 * per16 + per16 - 1) / per16) * per16;
     nline = en_max * Nz * Q * QP;
   }
-  // elements of the dynamic shared memory (of type T)
-  __host__ __device__ size_t count(int nrow, int Nz) const {
-    return (size_t)tcols * XS + 3 * (size_t)nline + (size_t)en_max * Q * 4 + (size_t)en_max * Nz * 2 + nrow + Q;
+  // bytes of dynamic shared memory for element size `elem`: two mbarriers (16 B), two staging
+  // buffers, the line buffers and the tile's geometry
+  __host__ __device__ size_t bytes(int nrow, int Nz, int elem) const {
+    return 16 + (size_t)elem * (2 * (size_t)xbuf + 3 * (size_t)nline + (size_t)en_max * Q * 4 +
+                                (size_t)en_max * Nz * 2 + nrow + Q);
   }
 };
 
+// Range of x (in elements of T) that a tile reads: columns (ex0−1)·P … (ex0+ne)·P.
+// Returns true when it can be bulk-copied: no periodic wrap, and the 16-byte-aligned
+// superset [*lo, *lo + *count) stays inside x; *shift is the tile's offset in the copy.
+template <int P, class T>
+static __device__ __forceinline__ bool tile_range(const DevGeom& g, int ex0, int ne, long long* lo, int* count,
+                                                  int* shift) {
+  constexpr int per16 = 16 / (int)sizeof(T);
+  const long long c_lo = (long long)(ex0 - 1) * P, c_hi = (long long)(ex0 + ne) * P;
+  if (c_lo < 0 || c_hi >= g.ncol) return false;
+  const long long first = c_lo * g.nrow, last = (c_hi + 1) * g.nrow;   // [first, last)
+  const long long a = first - first % per16;
+  const long long b = ((last + per16 - 1) / per16) * per16;
+  if (b > (long long)g.ncol * g.nrow) return false;
+  *lo = a;
+  *count = (int)(b - a);
+  *shift = (int)(first - a);
+  return true;
+}
+
+// bulk != 0: x is 16-byte aligned and interior tiles are staged by bulk copies.
 template <int P, class T>
 __global__ void __launch_bounds__(kThreads) k_apply_tile(DevGeom g, const T* __restrict__ x, T* __restrict__ y,
-                                                         int E) {
+                                                         int E, int bulk_ok) {
   constexpr int Q = P + 1;
   constexpr int QP = TileLayout<P>::QP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nrow = g.nrow, Nz = g.Nz, Nx = g.Nx, ncol = g.ncol;
-  const TileLayout<P> L(E, nrow, Nz);
-  const int XS = L.XS;
-  T* Xs = reinterpret_cast<T*>(smem_raw);   // [tcols][XS] nodal values of the tile
-  T* Ur = Xs + (size_t)L.tcols * XS;        // [en][Nz][Q b][QP a] u_r, then the element contributions
+  const TileLayout<P> L(E, nrow, Nz, (int)sizeof(T));
+  unsigned long long* mbar = reinterpret_cast<unsigned long long*>(smem_raw);   // [2]
+  T* Xb[2];
+  Xb[0] = reinterpret_cast<T*>(smem_raw + 16);  // staging buffers (16-byte aligned)
+  Xb[1] = Xb[0] + L.xbuf;
+  T* Ur = Xb[1] + L.xbuf;                   // [en][Nz][Q b][QP a] u_r, then the element contributions
   T* Fs = Ur + L.nline;                     // [en][Nz][Q b][QP a] F1
   T* Ys = Fs + L.nline;                     // [en][Nz][Q b][QP a] σ part of the transpose
   T* Gs = Ys + L.nline;                     // [en][Q][4] d, 1/d, ∂xh, ∂xd
   T* Cs = Gs + (size_t)L.en_max * Q * 4;    // [en][Nz][2] Δσ/Δx, Δx/Δσ
   T* Ss = Cs + (size_t)L.en_max * Nz * 2;   // [nrow] σ
   T* Ws = Ss + nrow;                        // [Q] GLL weights (indexed per thread)
+  __shared__ int s_ok;
   const T* D = CT<T>::D() + d_off(P);       // compile-time indices only: constant operands
   const T* w = CT<T>::w() + w_off(P);
   const T* geo = geo_ptr<T>(g);
   for (int t = threadIdx.x; t < nrow; t += blockDim.x) Ss[t] = (T)g.sig[t];
   for (int t = threadIdx.x; t < Q; t += blockDim.x) Ws[t] = w[t];
+  if (threadIdx.x == 0) {
+    mbar_init(&mbar[0]);
+    mbar_init(&mbar[1]);
+    mbar_init_fence();
+    s_ok = 1;
+  }
+  __syncthreads();
   const int ntiles = (Nx + E - 1) / E;
   const int lpe = Nz * Q;                                   // lines per element (x- or σ-lines)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
@@ -70,20 +156,58 @@ __global__ void __launch_bounds__(kThreads) k_apply_tile(DevGeom g, const T* __r
   // dividing: line 0 of the loop and the step of blockDim.x lines
   const int le0 = threadIdx.x / lpe, lr0 = threadIdx.x - le0 * lpe;
   const int lde = blockDim.x / lpe, ldr = blockDim.x - lde * lpe;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  unsigned parity[2] = {0u, 0u};     // next phase to wait for, per staging buffer (thread 0)
+  int pending[2] = {0, 0};           // a bulk copy is in flight into the buffer (thread 0)
+
+  // thread 0: issue the copy of `tile` into buffer `b` if it can be bulk-copied
+  auto issue = [&](int tile, int b) {
+    const int ex0 = tile * E, ne = min(E, Nx - ex0);
+    long long lo;
+    int count, shift;
+    if (bulk_ok && tile_range<P, T>(g, ex0, ne, &lo, &count, &shift)) {
+      fence_proxy_async_smem();
+      bulk_load(Xb[b], x + lo, (unsigned)(count * sizeof(T)), &mbar[b]);
+      pending[b] = 1;
+    }
+  };
+  if (threadIdx.x == 0 && (int)blockIdx.x < ntiles) issue(blockIdx.x, 0);
+
+  int k = 0;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++k) {
+    const int b = k & 1;
     const int ex0 = tile * E;
     const int ne = min(E, Nx - ex0);
     const int en = ne + 1;                       // local element 0 is the left neighbour
     const bool has_left = g.periodic || ex0 > 0;
     const int nc = en * P + 1;
+    long long lo;
+    int count, shift;
+    const bool bulk = bulk_ok && tile_range<P, T>(g, ex0, ne, &lo, &count, &shift);
     __syncthreads();                             // the previous tile's readers are done
-    // ---- stage the tile: nodal values (a warp per column), geometry, layer ratios ----
-    for (int j = warp; j < nc; j += nwarps) {
-      int gc = (ex0 - 1) * P + j;
-      if (gc < 0) gc = g.periodic ? gc + ncol : -1;
-      else if (gc >= ncol) gc -= ncol;           // periodic: column Nx·P is column 0
-      const T* xc = x + (size_t)(gc < 0 ? 0 : gc) * nrow;
-      for (int r = lane; r < nrow; r += 32) Xs[j * XS + r] = gc >= 0 ? __ldg(xc + r) : T(0);
+    if (threadIdx.x == 0) {
+      // prefetch the next tile into the other buffer, then wait for this one
+      if (tile + (int)gridDim.x < ntiles) issue(tile + gridDim.x, b ^ 1);
+      if (pending[b]) {
+        if (!mbar_wait(&mbar[b], parity[b], kCopyTimeoutNs)) s_ok = 0;
+        else {
+          parity[b] ^= 1u;
+          pending[b] = 0;
+        }
+      }
+    }
+    // ---- stage the tile: nodal values (a warp per column unless bulk-copied), geometry ----
+    T* X;
+    if (bulk) {
+      X = Xb[b] + shift;
+    } else {
+      X = Xb[b];
+      for (int j = warp; j < nc; j += nwarps) {
+        int gc = (ex0 - 1) * P + j;
+        if (gc < 0) gc = g.periodic ? gc + ncol : -1;
+        else if (gc >= ncol) gc -= ncol;         // periodic: column Nx·P is column 0
+        const T* xc = x + (size_t)(gc < 0 ? 0 : gc) * nrow;
+        for (int r = lane; r < nrow; r += 32) X[j * nrow + r] = gc >= 0 ? __ldg(xc + r) : T(0);
+      }
     }
     for (int t = threadIdx.x; t < en * Q * 4; t += blockDim.x) {
       const int e = t / (Q * 4);
@@ -100,16 +224,17 @@ __global__ void __launch_bounds__(kThreads) k_apply_tile(DevGeom g, const T* __r
       Cs[2 * t + 1] = dxe / dsl;
     }
     __syncthreads();
+    if (!s_ok) break;                            // a copy did not complete: stop (status set below)
     const int e_first = has_left ? 0 : 1;        // walls: no element left of x = 0
     // ---- 1. x-lines: u_r ----
     for (int e = e_first + le0, rem = lr0; e < en; e += lde, rem += ldr) {
       if (rem >= lpe) { rem -= lpe; ++e; if (e >= en) break; }
-      const int l = rem / Q, b = rem - l * Q;
-      const T* X = Xs + (e * P) * XS + l * P + b;
+      const int l = rem / Q, bb = rem - l * Q;
+      const T* Xl = X + (e * P) * nrow + l * P + bb;
       T u[Q];
 #pragma unroll
-      for (int c = 0; c < Q; ++c) u[c] = X[c * XS];
-      T* out = Ur + ((e * Nz + l) * Q + b) * QP;
+      for (int c = 0; c < Q; ++c) u[c] = Xl[c * nrow];
+      T* out = Ur + ((e * Nz + l) * Q + bb) * QP;
 #pragma unroll
       for (int a = 0; a < Q; ++a) {
         T s = T(0);
@@ -123,10 +248,10 @@ __global__ void __launch_bounds__(kThreads) k_apply_tile(DevGeom g, const T* __r
     for (int e = e_first + le0, rem = lr0; e < en; e += lde, rem += ldr) {
       if (rem >= lpe) { rem -= lpe; ++e; if (e >= en) break; }
       const int l = rem / Q, a = rem - l * Q;
-      const T* X = Xs + (e * P + a) * XS + l * P;
+      const T* Xl = X + (e * P + a) * nrow + l * P;
       T u[Q];
 #pragma unroll
-      for (int c = 0; c < Q; ++c) u[c] = X[c];
+      for (int c = 0; c < Q; ++c) u[c] = Xl[c];
       const T* gq = Gs + (e * Q + a) * 4;
       const T c0 = Cs[2 * (e * Nz + l)], c1 = Cs[2 * (e * Nz + l) + 1];
       const T wa = Ws[a], hx = gq[2], dxd = gq[3];
@@ -136,31 +261,31 @@ __global__ void __launch_bounds__(kThreads) k_apply_tile(DevGeom g, const T* __r
       const int base = (e * Nz + l) * Q;
       T f2[Q];
 #pragma unroll
-      for (int b = 0; b < Q; ++b) {
+      for (int bb = 0; bb < Q; ++bb) {
         T ut = T(0);
 #pragma unroll
-        for (int c = 0; c < Q; ++c) ut = fmx(D[b * Q + c], u[c], ut);
-        const T ur = Ur[(base + b) * QP + a];
-        const T K12 = fmx(-sg[b], dxd, hx);
-        const T wb = w[b];
+        for (int c = 0; c < Q; ++c) ut = fmx(D[bb * Q + c], u[c], ut);
+        const T ur = Ur[(base + bb) * QP + a];
+        const T K12 = fmx(-sg[bb], dxd, hx);
+        const T wb = w[bb];
         const T G12 = wa * wb * K12;
-        Fs[(base + b) * QP + a] = fmx(g11 * wb, ur, G12 * ut);
-        f2[b] = fmx(G12, ur, g22 * wb * fmx(K12, K12, T(1)) * ut);
+        Fs[(base + bb) * QP + a] = fmx(g11 * wb, ur, G12 * ut);
+        f2[bb] = fmx(G12, ur, g22 * wb * fmx(K12, K12, T(1)) * ut);
       }
 #pragma unroll
-      for (int b = 0; b < Q; ++b) {
+      for (int bb = 0; bb < Q; ++bb) {
         T s = T(0);
 #pragma unroll
-        for (int c = 0; c < Q; ++c) s = fmx(D[c * Q + b], f2[c], s);
-        Ys[(base + b) * QP + a] = s;
+        for (int c = 0; c < Q; ++c) s = fmx(D[c * Q + bb], f2[c], s);
+        Ys[(base + bb) * QP + a] = s;
       }
     }
     __syncthreads();
     // ---- 3. x-lines: the element contribution (into the u_r buffer) ----
     for (int e = e_first + le0, rem = lr0; e < en; e += lde, rem += ldr) {
       if (rem >= lpe) { rem -= lpe; ++e; if (e >= en) break; }
-      const int l = rem / Q, b = rem - l * Q;
-      const int row = ((e * Nz + l) * Q + b) * QP;
+      const int l = rem / Q, bb = rem - l * Q;
+      const int row = ((e * Nz + l) * Q + bb) * QP;
       T f1[Q];
 #pragma unroll
       for (int c = 0; c < Q; ++c) f1[c] = Fs[row + c];
@@ -184,11 +309,11 @@ __global__ void __launch_bounds__(kThreads) k_apply_tile(DevGeom g, const T* __r
       const bool left = a == 0 && (e > 1 || has_left);   // the element left of column j exists
       T* yc = yt + (size_t)jj * nrow;
       for (int r = lane; r < nrow; r += 32) {
-        int l = r / P, b = r - l * P;
-        if (l == Nz) { l = Nz - 1; b = P; }     // surface row
-        T s = Ur[((e * Nz + l) * Q + b) * QP + a];
-        if (left) s += Ur[(((e - 1) * Nz + l) * Q + b) * QP + P];
-        if (b == 0 && l > 0) {
+        int l = r / P, bb = r - l * P;
+        if (l == Nz) { l = Nz - 1; bb = P; }    // surface row
+        T s = Ur[((e * Nz + l) * Q + bb) * QP + a];
+        if (left) s += Ur[(((e - 1) * Nz + l) * Q + bb) * QP + P];
+        if (bb == 0 && l > 0) {
           s += Ur[((e * Nz + l - 1) * Q + P) * QP + a];
           if (left) s += Ur[(((e - 1) * Nz + l - 1) * Q + P) * QP + P];
         }
@@ -196,12 +321,20 @@ __global__ void __launch_bounds__(kThreads) k_apply_tile(DevGeom g, const T* __r
       }
     }
   }
+  // a copy still in flight (after a timeout, or the prefetch of a tile this CTA stopped
+  // before) must land before the CTA's shared memory is released
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (!s_ok) atomicOr(g.status, ST_TIMEOUT);
+    for (int bb = 0; bb < 2; ++bb)
+      if (pending[bb] && !mbar_wait(&mbar[bb], parity[bb], kCopyTimeoutNs)) atomicOr(g.status, ST_TIMEOUT);
+  }
 }
 
 // Dynamic shared memory of the tiled apply for tile width E.
 template <int P>
 size_t apply_tile_smem(int E, int nrow, int Nz, size_t elem) {
-  return TileLayout<P>(E, nrow, Nz).count(nrow, Nz) * elem;
+  return TileLayout<P>(E, nrow, Nz, (int)elem).bytes(nrow, Nz, (int)elem);
 }
 
 }  // namespace semgb

@@ -1292,8 +1292,8 @@ cudaError_t launch_stage_impl(int mixed, const StageArgs& a, int grid, size_t sm
 
 
 // Tiled apply (apply_tile.cuh): widest tile of at most 16 elements whose shared memory keeps
-// four CTAs per SM; one CTA per tile up to the co-resident count, grid-stride beyond.
-constexpr size_t kTileSmemTarget = 56 * 1024;
+// three CTAs per SM; persistent CTAs (at most the co-resident count) stride over the tiles.
+constexpr size_t kTileSmemTarget = 76 * 1024;
 
 template <int P>
 cudaError_t launch_apply_tile_impl(int fp32, const DevGeom& g, const void* x, void* y, cudaStream_t s) {
@@ -1327,10 +1327,11 @@ cudaError_t launch_apply_tile_impl(int fp32, const DevGeom& g, const void* x, vo
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   const long long ntiles = (g.Nx + E - 1) / E;
   const int grid = (int)(ntiles < (long long)per_sm * sms ? ntiles : (long long)per_sm * sms);
+  const int bulk_ok = (reinterpret_cast<uintptr_t>(x) % 16) == 0 ? 1 : 0;   // bulk copies need 16-B alignment
   if (fp32) k_apply_tile<P, float><<<grid, kThreads, smem, s>>>(g, static_cast<const float*>(x),
-                                                               static_cast<float*>(y), E);
+                                                               static_cast<float*>(y), E, bulk_ok);
   else k_apply_tile<P, double><<<grid, kThreads, smem, s>>>(g, static_cast<const double*>(x),
-                                                            static_cast<double*>(y), E);
+                                                            static_cast<double*>(y), E, bulk_ok);
   count_launch();
   return cudaGetLastError();
 }
