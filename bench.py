@@ -368,35 +368,80 @@ def c3_batch(dev, count: int = 512, steps: int = 3):
     return out
 
 
-def c5_serving(rate: float = 1000.0, count: int = 400):
-    """C5: Poisson stream of Laplace solves and 10-step RK4 runs (seed 0) served by the
-    continuous-batching loop (mixed precision and FP64, 150 GB admission budget), against the
-    same requests run one after another on the plain FP64 path.  Wall-clock from the first
-    arrival; latency = completion − arrival."""
+def c4_shoal_run(dev, spinup: int = 600, steps: int = 100):
+    """C4: JONSWAP waves generated over the synthetic shoal (2048×2, P=6, walls, relaxation
+    zones), FP64 and mixed precision.  `spinup` untimed steps from rest let the generated
+    waves fill the first part of the tank; then `steps` RK4 steps are timed with CUDA events.
+    The two precisions are compared at the end (relative L2 of η and φ̃)."""
+    import numpy as np
+    import torch
+    import paper_1512_02548_gb300 as sem
+    from sem_workloads import c4_shoal, depth_columns
+    wl = c4_shoal()
+    h = depth_columns(wl, column_positions(wl))
+    out = {"workload": wl.name, "unknowns": wl.n_unknowns, "dt": wl.dt, "spinup_steps": spinup, "steps": steps}
+    res = {}
+    for prec in ("fp64", "mixed"):
+        m = sem.Mesh.from_workload(wl, h=h, precision=prec, tol=1e-13 if prec == "fp64" else 1e-12)
+        eta = torch.zeros(wl.ncol, dtype=torch.float64, device=dev)
+        phis = torch.zeros_like(eta)
+        t = m.rk4_step(eta, phis, wl.dt, spinup, t=0.0)
+        m.reset_counters()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        m.rk4_step(eta, phis, wl.dt, steps, t=t)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        c = m.counters()
+        out[prec] = {"ms_per_rk4_step": ms, "rk4_steps_per_s": 1e3 / ms,
+                     "laplace_dof_per_s": 4 * wl.n_unknowns / ms * 1e3,
+                     "iterations_per_solve": c.iterations / max(c.solves, 1),
+                     "refinements_per_solve": c.refinements / max(c.solves, 1)}
+        res[prec] = (eta, phis)
+        m.close()
+    out["mixed_vs_fp64_rel_l2"] = max(float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
+                                      for a, b in zip(res["mixed"], res["fp64"]))
+    out["max_abs_eta"] = float(res["fp64"][0].abs().max())
+    return out
+
+
+def c5_serving(rates=(100.0, 1000.0), count: int = 300):
+    """C5: Poisson streams of Laplace solves and 10-step RK4 runs (seed 0) served by the
+    continuous-batching loop in mixed precision (150 GB admission budget), against the same
+    requests run one after another on the plain FP64 single-instance path.  Wall-clock from
+    the first arrival; latency = completion − arrival.  One rate below the loop's capacity and
+    one above it."""
     import numpy as np
     from paper_1512_02548_gb300.serve import GpuExecutor, Request, Server, sequential
     from sem_workloads import c5_requests, initial_state
-    base = []
-    for i, (kind, t, wl, ns) in enumerate(c5_requests(rate, count, 0)):
-        e0, p0 = initial_state(wl, column_positions(wl), np.full(wl.ncol, wl.depth))
-        base.append(Request(i, kind, wl, e0, p0, ns, t))
+    keys = ("p50_ms", "p99_ms", "laplace_dof_per_s", "rk4_steps_per_s", "requests_per_s", "wall_s", "completed",
+            "failed")
+    out = {"requests_per_rate": count, "budget_gb": 150}
+    warm = True
+    for rate in rates:
+        base = []
+        for i, (kind, t, wl, ns) in enumerate(c5_requests(rate, count, 0)):
+            e0, p0 = initial_state(wl, column_positions(wl), np.full(wl.ncol, wl.depth))
+            base.append(Request(i, kind, wl, e0, p0, ns, t))
 
-    def fresh():
-        return [Request(r.rid, r.kind, r.wl, r.eta0, r.phis0, r.nsteps, r.arrival) for r in base]
+        def fresh():
+            return [Request(r.rid, r.kind, r.wl, r.eta0, r.phis0, r.nsteps, r.arrival) for r in base]
 
-    Server(GpuExecutor("mixed"), 150 << 30).run(fresh()[:8])          # warm-up
-    out = {"rate_per_s": rate, "requests": count, "laplace_share": sum(r.kind == "laplace" for r in base) / count,
-           "nodes_total": int(sum(r.wl.n_nodes for r in base))}
-    for prec in ("mixed", "fp64"):
-        s = Server(GpuExecutor(prec), 150 << 30, keep_results=False).run(fresh())
-        out[f"served_{prec}"] = {k: s[k] for k in ("p50_ms", "p99_ms", "laplace_dof_per_s", "rk4_steps_per_s",
-                                                   "requests_per_s", "wall_s", "ticks", "peak_active",
-                                                   "completed", "failed")}
-    s = sequential(fresh(), "fp64")
-    out["sequential_fp64"] = {k: s[k] for k in ("p50_ms", "p99_ms", "laplace_dof_per_s", "rk4_steps_per_s",
-                                               "requests_per_s", "wall_s", "completed", "failed")}
-    out["served_mixed_dof_speedup_vs_sequential_fp64"] = (out["served_mixed"]["laplace_dof_per_s"] /
-                                                          out["sequential_fp64"]["laplace_dof_per_s"])
+        if warm:
+            Server(GpuExecutor("mixed"), 150 << 30).run(fresh()[:8])      # warm-up (module loading)
+            warm = False
+        ent = {"laplace_share": sum(r.kind == "laplace" for r in base) / count,
+               "nodes_total": int(sum(r.wl.n_nodes for r in base))}
+        s = Server(GpuExecutor("mixed"), 150 << 30, keep_results=False).run(fresh())
+        ent["served_mixed"] = {k: s[k] for k in keys + ("ticks", "peak_active")}
+        s = sequential(fresh(), "fp64")
+        ent["sequential_fp64"] = {k: s[k] for k in keys}
+        ent["served_mixed_dof_speedup_vs_sequential_fp64"] = (ent["served_mixed"]["laplace_dof_per_s"] /
+                                                              ent["sequential_fp64"]["laplace_dof_per_s"])
+        out[f"rate_{int(rate)}_per_s"] = ent
     return out
 
 
@@ -525,8 +570,10 @@ def run_gpu(args):
         line["apply_long_tank"] = apply_roofline(dev)
     if not args.no_c3:
         line["c3_uneven_batch"] = c3_batch(dev)
+    if not args.no_c4:
+        line["c4_shoal"] = c4_shoal_run(dev)
     if not args.no_c5:
-        line["c5_serving"] = c5_serving(args.c5_rate, args.c5_requests)
+        line["c5_serving"] = c5_serving(tuple(args.c5_rates), args.c5_requests)
     if rank == 0 and not args.no_cpu_baseline:
         try:
             res = oracle_subprocess(args.cpu_stages)
@@ -574,9 +621,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-apply-roofline", action="store_true")
     ap.add_argument("--no-c3", action="store_true")
+    ap.add_argument("--no-c4", action="store_true")
     ap.add_argument("--no-c5", action="store_true")
-    ap.add_argument("--c5-rate", type=float, default=1000.0)
-    ap.add_argument("--c5-requests", type=int, default=400)
+    ap.add_argument("--c5-rates", type=float, nargs="+", default=[100.0, 1000.0])
+    ap.add_argument("--c5-requests", type=int, default=300)
     ap.add_argument("--apply-only", default=None,
                     help="comma list of fp64_column,fp64_tile,fp32_tile: time only these applies (for profiling)")
     ap.add_argument("--apply-nx", type=int, default=65536)

@@ -1,5 +1,8 @@
-// σ-geometry, the matrix-free Laplace operator and the persistent Krylov solver
-// (§2 and §3.1.2 of arXiv 1512.02548), for sm_103a.
+// Device code of the σ-Laplace path (§2 and §3.1.2 of arXiv 1512.02548), templated on the GLL
+// order P: geometry, the matrix-free operator, the persistent Krylov solver with the σ-separable
+// preconditioner, and the fused RK stage.  Included by kernels_order.cu, which is compiled once
+// per order (-DSEM_ORDER=P) and instantiates the host entry points at the end of this file;
+// everything else here has internal linkage, including each order's copy of the constant tables.
 //
 // Operator.  For element (ex,l) with local nodal values u_ab, a along x and b along
 // σ, GLL collocation gives the gradients u_r = (D⊗I)u, u_t = (I⊗D)u; with weights
@@ -10,25 +13,22 @@
 // with K11 = d, K12 = ∂xh − σ ∂xd, K22 = (1 + K12²)/d evaluated on the fly from four
 // numbers per element-local column.  Nothing is stored per node except the vectors.
 //
-// Work decomposition.  One CTA processes an "element column" (all Nz layers of
-// x-element ex) at a time: its (P+1)·Nrow nodes are staged in shared memory, the
-// layers are summed in shared memory, columns a = 0..P−1 are written straight to
-// the output and column a = P (shared with the next x-element) to an edge buffer
-// that the owner of that column adds after a grid barrier.  All sums are in a fixed
-// order, so results are bitwise reproducible.
+// Work decomposition.  A team of CTAs (the whole grid for one mesh, or the CTAs given to one
+// instance of a batch) splits the x-elements into contiguous ranges; a CTA processes its
+// element columns (all Nz layers of an x-element) in chunks of consecutive columns staged in
+// shared memory.  Columns a = 0..P−1 of an element are written straight to the output and
+// column a = P (shared with the next x-element) to an edge buffer that the owner of that
+// column adds after a team barrier.  All sums are in a fixed order, so results are bitwise
+// reproducible for a given team size.
 //
-// Krylov.  Conjugate gradients on the Dirichlet-eliminated SPD system with the
-// Jacobi preconditioner run inside ONE cooperative persistent kernel: two grid
-// barriers per iteration, deterministic reductions, a double-buffered search
-// direction so each CTA can rebuild its halo column without a third barrier, and a
-// device-side convergence test (no host round trip).  In mixed precision the inner
-// iterations run in FP32 and the kernel refines the FP64 residual.
-//
-// Device code of the σ-Laplace path, templated on the GLL order P: geometry, the matrix-free
-// operator, the persistent Krylov solver with the σ-separable preconditioner, and the fused
-// RK stage.  Included by kernels_order.cu, which is compiled once per order (-DSEM_ORDER=P)
-// and instantiates the host entry points at the end of this file; everything else here has
-// internal linkage, including each order's copy of the constant tables.
+// Krylov.  Preconditioned conjugate gradients (Chronopoulos–Gear form: one reduction per
+// iteration) on the Dirichlet-eliminated SPD system, inside one cooperative persistent kernel:
+// team barriers with acquire/release atomics and a wall-clock limit, deterministic reductions,
+// a halo column per CTA so the preconditioned residual needs no extra barrier, and a
+// device-side convergence test (no host round trip).  The σ-separable preconditioner applies
+// the exact inverse of the operator without its slope coupling (σ-eigenbasis, per-mode 1D
+// condensation and a warp-parallel interface solve).  In mixed precision the inner iterations
+// run in FP32 and the kernel refines the FP64 residual.
 #pragma once
 #include <cooperative_groups.h>
 #include <mutex>
