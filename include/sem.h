@@ -120,7 +120,12 @@ typedef struct sem_mesh sem_mesh;
  * (owned by the mesh).  On failure *out is NULL. */
 int sem_mesh_create(const sem_params* p, const double* x_edges_h, const double* h_h,
                     sem_mesh** out);
+/* Waits for the device to be idle, then returns the mesh's memory to a per-device cache that
+ * later sem_mesh_create / sem_batch_create calls reuse (at most 8 GiB per device is kept;
+ * beyond that, blocks go back to CUDA). */
 void sem_mesh_destroy(sem_mesh* m);
+/* Returns every cached device block to CUDA (see sem_mesh_destroy). */
+void sem_trim_cache(void);
 /* Device memory sem_mesh_create would allocate for these arguments, without allocating
  * (for admission control); same validation and errors as sem_mesh_create. */
 int sem_mesh_footprint(const sem_params* p, const double* x_edges_h, const double* h_h, int64_t* bytes);

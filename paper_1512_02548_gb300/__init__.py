@@ -26,7 +26,7 @@ SEM_ERRORS = {1: "SEM_ERR_INVALID_ARG", 2: "SEM_ERR_OOM", 3: "SEM_ERR_CUDA",
 SEM_PREC_FP64, SEM_PREC_MIXED = 0, 1
 SEM_PRECOND_SEPARABLE, SEM_PRECOND_JACOBI = 0, 1
 
-EXPORTED = ("sem_mesh_create", "sem_mesh_destroy", "sem_mesh_footprint", "sem_mesh_info", "sem_mesh_l2g",
+EXPORTED = ("sem_mesh_create", "sem_mesh_destroy", "sem_trim_cache", "sem_mesh_footprint", "sem_mesh_info", "sem_mesh_l2g",
             "sem_update_geometry", "sem_laplace_apply", "sem_laplace_apply_f32", "sem_laplace_apply_noalloc", "sem_laplace_solve",
             "sem_recover_gradient", "sem_zakharov_rhs", "sem_set_wave_input", "sem_apply_filter", "sem_rk4_step",
             "sem_rk4_step_host", "sem_get_counters", "sem_reset_counters", "sem_enable_timing",
@@ -82,6 +82,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sem_mesh_footprint.argtypes = [ctypes.POINTER(sem_params), dp, dp, ctypes.POINTER(ctypes.c_int64)]
     lib.sem_mesh_destroy.argtypes = [vp]
     lib.sem_mesh_destroy.restype = None
+    lib.sem_trim_cache.argtypes = []
+    lib.sem_trim_cache.restype = None
     lib.sem_mesh_info.argtypes = [vp, ctypes.POINTER(sem_info)]
     lib.sem_mesh_l2g.argtypes = [vp, dp, vp]
     lib.sem_update_geometry.argtypes = [vp, dp, vp]

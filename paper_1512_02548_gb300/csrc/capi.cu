@@ -61,6 +61,60 @@ int ensure_device_tables(int dev) {
   return SEM_OK;
 }
 
+// Device memory of meshes and batches comes from a per-device cache of freed blocks, so that
+// a serving loop that creates and destroys meshes per request does not pay cudaMalloc and
+// cudaFree for each.  A freed block is kept (up to kCacheBytes per device) and handed to a
+// later request of at most its size and at least half of it.  sem_trim_cache returns the
+// cached blocks to CUDA.
+constexpr size_t kCacheBytes = 8ull << 30;
+struct BlockCache {
+  std::multimap<size_t, void*> free;          // size → block
+  std::map<void*, size_t> size_of;            // every block this cache handed out or holds
+  size_t cached = 0;
+};
+std::mutex g_cache_mu;
+BlockCache g_cache[64];
+
+cudaError_t dev_alloc(int dev, size_t bytes, void** p) {
+  {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    BlockCache& c = g_cache[dev];
+    auto it = c.free.lower_bound(bytes);
+    if (it != c.free.end() && it->first <= 2 * bytes) {
+      *p = it->second;
+      c.cached -= it->first;
+      c.free.erase(it);
+      return cudaSuccess;
+    }
+  }
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e == cudaErrorMemoryAllocation) {        // give the cached blocks back and retry once
+    sem_trim_cache();
+    cudaGetLastError();
+    e = cudaMalloc(p, bytes);
+  }
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(g_cache_mu);
+  g_cache[dev].size_of[*p] = bytes;
+  return cudaSuccess;
+}
+
+// The block must have no work in flight; the callers synchronise the device first.
+void dev_free(int dev, void* p) {
+  if (!p) return;
+  std::lock_guard<std::mutex> lk(g_cache_mu);
+  BlockCache& c = g_cache[dev];
+  auto it = c.size_of.find(p);
+  const size_t sz = it == c.size_of.end() ? 0 : it->second;
+  if (sz > 0 && c.cached + sz <= kCacheBytes) {
+    c.free.emplace(sz, p);
+    c.cached += sz;
+  } else {
+    if (it != c.size_of.end()) c.size_of.erase(it);
+    cudaFree(p);
+  }
+}
+
 struct DeviceGuard {
   int prev = -1;
   explicit DeviceGuard(int dev) {
@@ -609,7 +663,7 @@ static int mesh_create_impl(const sem_params* pin, const double* x_edges_h, cons
     return SEM_OK;
   }
   m->pool_bytes = total;
-  cudaError_t ae = cudaMalloc(&m->pool, total);
+  cudaError_t ae = dev_alloc(dev, total, reinterpret_cast<void**>(&m->pool));
   if (ae != cudaSuccess) { delete m; return fail(SEM_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(ae)); }
   auto D_ = [&](size_t o) { return reinterpret_cast<double*>(m->pool + o); };
   auto F_ = [&](size_t o) { return reinterpret_cast<float*>(m->pool + o); };
@@ -642,7 +696,7 @@ static int mesh_create_impl(const sem_params* pin, const double* x_edges_h, cons
     cudaError_t e = cudaMemcpy(m->pool + o_S32, S32.data(), S32.size() * sizeof(float), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) code = fail(SEM_ERR_CUDA, std::string("upload: ") + cudaGetErrorString(e));
   }
-  if (code != SEM_OK) { cudaFree(m->pool); delete m; return code; }
+  if (code != SEM_OK) { dev_free(dev, m->pool); delete m; return code; }
 
   DevGeom& g = m->g;
   g.P = P; g.Nx = Nx; g.Nz = Nz; g.ncol = ncol; g.nrow = nrow; g.periodic = p.periodic ? 1 : 0; g.chunk = chunk;
@@ -704,7 +758,7 @@ static int mesh_create_impl(const sem_params* pin, const double* x_edges_h, cons
     cudaError_t e = stage_occupancy(P, p.precision == SEM_PREC_MIXED, m->stage_smem, &per_sm);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess || per_sm < 1) {
-      cudaFree(m->pool);
+      dev_free(dev, m->pool);
       delete m;
       return fail(SEM_ERR_CUDA, "fused stage kernel does not fit on this device");
     }
@@ -712,7 +766,7 @@ static int mesh_create_impl(const sem_params* pin, const double* x_edges_h, cons
     std::vector<int> zeros(m->grid, 0);
     cudaError_t e2 = cudaMemcpy(m->cta_inst_d, zeros.data(), sizeof(int) * m->grid, cudaMemcpyHostToDevice);
     if (e2 != cudaSuccess) {
-      cudaFree(m->pool);
+      dev_free(dev, m->pool);
       delete m;
       return fail(SEM_ERR_CUDA, std::string("upload: ") + cudaGetErrorString(e2));
     }
@@ -726,7 +780,8 @@ void sem_mesh_destroy(sem_mesh* m) {
   DeviceGuard dg(m->device);
   for (auto& pr : m->events) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
   for (auto e : m->spare) cudaEventDestroy(e);
-  cudaFree(m->pool);
+  cudaDeviceSynchronize();   // no work of this mesh may still run when its memory is reused
+  dev_free(m->device, m->pool);
   delete m;
 }
 
@@ -948,7 +1003,7 @@ int sem_batch_create(sem_mesh* const* meshes, int count, sem_batch** out) {
       b->launches.push_back(std::move(L));
     }
   }
-  cudaError_t ae = cudaMalloc(&b->pool, total + 256);
+  cudaError_t ae = dev_alloc(dev, total + 256, reinterpret_cast<void**>(&b->pool));
   if (ae != cudaSuccess) { delete b; return fail(SEM_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(ae)); }
   size_t off = 0;
   for (auto& L : b->launches) {
@@ -964,7 +1019,7 @@ int sem_batch_create(sem_mesh* const* meshes, int count, sem_batch** out) {
     for (size_t k = 0; k < L.members.size(); ++k)
       for (int c = 0; c < L.nteam[k]; ++c) map[L.team0[k] + c] = (int)k;
     cudaError_t e = cudaMemcpy(L.cta_d, map.data(), sizeof(int) * L.grid, cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) { cudaFree(b->pool); delete b; return fail(SEM_ERR_CUDA, cudaGetErrorString(e)); }
+    if (e != cudaSuccess) { dev_free(dev, b->pool); delete b; return fail(SEM_ERR_CUDA, cudaGetErrorString(e)); }
     L.inst_h.resize(L.members.size());
     L.status_h.resize(L.members.size());
   }
@@ -975,8 +1030,27 @@ int sem_batch_create(sem_mesh* const* meshes, int count, sem_batch** out) {
 void sem_batch_destroy(sem_batch* b) {
   if (!b) return;
   DeviceGuard dg(b->device);
-  cudaFree(b->pool);
+  cudaDeviceSynchronize();   // no work of this batch may still run when its memory is reused
+  dev_free(b->device, b->pool);
   delete b;
+}
+
+void sem_trim_cache(void) {
+  std::lock_guard<std::mutex> lk(g_cache_mu);
+  int prev = -1;
+  cudaGetDevice(&prev);
+  for (int d = 0; d < 64; ++d) {
+    BlockCache& c = g_cache[d];
+    if (c.free.empty()) continue;
+    cudaSetDevice(d);
+    for (auto& kv : c.free) {
+      cudaFree(kv.second);
+      c.size_of.erase(kv.second);
+    }
+    c.free.clear();
+    c.cached = 0;
+  }
+  if (prev >= 0) cudaSetDevice(prev);
 }
 
 int sem_batch_info(const sem_batch* b, int* launches_per_stage, int* ctas) {
