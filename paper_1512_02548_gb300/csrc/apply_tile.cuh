@@ -23,9 +23,8 @@
 //      K12 = ∂xh − σ ∂xd, K22 = (1 + K12²)/d, and the σ part of the transpose,
 //      y_σ(b) = Σ_c D_cb F2(c), in registers;
 //   3. x-lines: y_e(a) = Σ_c D_ca F1(c) + y_σ(a) — the element's contribution to A = −𝓛;
-//   4. the element contributions are added into the tile's nodes in four passes by the
-//      parity of (element, layer), so shared nodes get their ≤ 4 contributions in a fixed
-//      order without atomics; the tile's own columns are written as −sum.
+//   4. every tile node sums the contributions of the ≤ 4 elements that share it (left/right
+//      element, lower/upper layer) in a fixed order and writes −sum.
 // All sums have a fixed order: results are bitwise reproducible.
 #pragma once
 
@@ -282,41 +281,45 @@ __global__ void __launch_bounds__(kThreads) k_apply_tile(DevGeom g, const T* __r
       }
     }
     __syncthreads();
-    // ---- 3. x-lines: element contributions accumulated into the tile's node array ----
-    // The u_r buffer is dead after step 2 and holds the tile's nodes (column-major, like x).
-    // Elements are added in four passes by the parity of (element, layer): within a pass no two
-    // elements share a node, so plain read-add-write is race free, and every node receives its
-    // ≤ 4 contributions in the same order.
-    T* Yt = Ur;
-    for (int t = threadIdx.x; t < nc * nrow; t += blockDim.x) Yt[t] = T(0);
-    __syncthreads();
-#pragma unroll 1
-    for (int pass = 0; pass < 4; ++pass) {
-      for (int e = e_first + le0, rem = lr0; e < en; e += lde, rem += ldr) {
-        if (rem >= lpe) { rem -= lpe; ++e; if (e >= en) break; }
-        const int l = rem / Q, bb = rem - l * Q;
-        if ((e & 1) != (pass & 1) || (l & 1) != (pass >> 1)) continue;
-        const int row = ((e * Nz + l) * Q + bb) * QP;
-        T f1[Q];
+    // ---- 3. x-lines: the element contribution (into the u_r buffer) ----
+    for (int e = e_first + le0, rem = lr0; e < en; e += lde, rem += ldr) {
+      if (rem >= lpe) { rem -= lpe; ++e; if (e >= en) break; }
+      const int l = rem / Q, bb = rem - l * Q;
+      const int row = ((e * Nz + l) * Q + bb) * QP;
+      T f1[Q];
 #pragma unroll
-        for (int c = 0; c < Q; ++c) f1[c] = Fs[row + c];
-        T* yn = Yt + (e * P) * nrow + l * P + bb;   // node (a = 0, b) of this x-line
+      for (int c = 0; c < Q; ++c) f1[c] = Fs[row + c];
 #pragma unroll
-        for (int a = 0; a < Q; ++a) {
-          T s = Ys[row + a];
+      for (int a = 0; a < Q; ++a) {
+        T s = Ys[row + a];
 #pragma unroll
-          for (int c = 0; c < Q; ++c) s = fmx(D[c * Q + a], f1[c], s);
-          yn[a * nrow] += s;
-        }
+        for (int c = 0; c < Q; ++c) s = fmx(D[c * Q + a], f1[c], s);
+        Ur[row + a] = s;
       }
-      __syncthreads();
     }
-    // ---- 4. own columns [P, P + ne·P) (plus the last column between walls), contiguous ----
+    __syncthreads();
+    // ---- 4. gather: own columns [P, P + ne·P) (plus the last column between walls) ----
     const bool last_wall = !g.periodic && ex0 + ne == Nx;
-    const int nout = (ne * P + (last_wall ? 1 : 0)) * nrow;   // output values
+    const int nout = ne * P + (last_wall ? 1 : 0);   // output columns
     T* yt = y + (size_t)ex0 * P * nrow;
-    const T* ys = Yt + P * nrow;
-    for (int t = threadIdx.x; t < nout; t += blockDim.x) yt[t] = -ys[t];
+    for (int jj = warp; jj < nout; jj += nwarps) {   // a warp per output column
+      const int j = P + jj;
+      int e = j / P, a = j - e * P;
+      if (e == en) { e = en - 1; a = P; }       // right wall column
+      const bool left = a == 0 && (e > 1 || has_left);   // the element left of column j exists
+      T* yc = yt + (size_t)jj * nrow;
+      for (int r = lane; r < nrow; r += 32) {
+        int l = r / P, bb = r - l * P;
+        if (l == Nz) { l = Nz - 1; bb = P; }    // surface row
+        T s = Ur[((e * Nz + l) * Q + bb) * QP + a];
+        if (left) s += Ur[(((e - 1) * Nz + l) * Q + bb) * QP + P];
+        if (bb == 0 && l > 0) {
+          s += Ur[((e * Nz + l - 1) * Q + P) * QP + a];
+          if (left) s += Ur[(((e - 1) * Nz + l - 1) * Q + P) * QP + P];
+        }
+        yc[r] = -s;
+      }
+    }
   }
   // a copy still in flight (after a timeout, or the prefetch of a tile this CTA stopped
   // before) must land before the CTA's shared memory is released
