@@ -23,8 +23,9 @@
 //      K12 = ∂xh − σ ∂xd, K22 = (1 + K12²)/d, and the σ part of the transpose,
 //      y_σ(b) = Σ_c D_cb F2(c), in registers;
 //   3. x-lines: y_e(a) = Σ_c D_ca F1(c) + y_σ(a) — the element's contribution to A = −𝓛;
-//   4. every tile node sums the contributions of the ≤ 4 elements that share it (left/right
-//      element, lower/upper layer) in a fixed order and writes −sum.
+//   4. the contributions are stored into the tile's nodes; the nodes shared between layers
+//      and between elements are completed by two small fix-up sweeps in a fixed order (no
+//      atomics), and the tile's own columns are written as −sum with contiguous stores.
 // All sums have a fixed order: results are bitwise reproducible.
 #pragma once
 
@@ -93,7 +94,7 @@ struct TileLayout {
   // buffers, the line buffers and the tile's geometry
   __host__ __device__ size_t bytes(int nrow, int Nz, int elem) const {
     return 16 + (size_t)elem * (2 * (size_t)xbuf + 3 * (size_t)nline + (size_t)en_max * Q * 4 +
-                                (size_t)en_max * Nz * 2 + nrow + Q);
+                                (size_t)en_max * Nz * 2 + nrow + Q + 2 * (size_t)en_max * Nz * Q);
   }
 };
 
@@ -136,6 +137,8 @@ __global__ void __launch_bounds__(kThreads) k_apply_tile(DevGeom g, const T* __r
   T* Cs = Gs + (size_t)L.en_max * Q * 4;    // [en][Nz][2] Δσ/Δx, Δx/Δσ
   T* Ss = Cs + (size_t)L.en_max * Nz * 2;   // [nrow] σ
   T* Ws = Ss + nrow;                        // [Q] GLL weights (indexed per thread)
+  T* Rrow = Ws + Q;                         // [en][Nz][Q] top-row (b = P) contributions, a < P
+  T* Ccol = Rrow + (size_t)L.en_max * Nz * Q;   // [en][Nz][Q] right-column (a = P) contributions
   __shared__ int s_ok;
   const T* D = CT<T>::D() + d_off(P);       // compile-time indices only: constant operands
   const T* w = CT<T>::w() + w_off(P);
@@ -281,7 +284,14 @@ __global__ void __launch_bounds__(kThreads) k_apply_tile(DevGeom g, const T* __r
       }
     }
     __syncthreads();
-    // ---- 3. x-lines: the element contribution (into the u_r buffer) ----
+    // ---- 3. x-lines: element contributions into the tile's nodes ----
+    // The u_r buffer is dead after step 2 and now holds the tile's nodes (column-major, like
+    // x).  A node interior to its element's column range and layer is written by exactly one
+    // x-line.  The shared nodes are completed in a fixed order: the value of the element to the
+    // right (a = 0) and of the layer above (b = 0) is stored; the top row of a layer (b = P)
+    // and the right column of an element (a = P) go to small buffers and are added afterwards,
+    // rows first, then columns.
+    T* Yt = Ur;
     for (int e = e_first + le0, rem = lr0; e < en; e += lde, rem += ldr) {
       if (rem >= lpe) { rem -= lpe; ++e; if (e >= en) break; }
       const int l = rem / Q, bb = rem - l * Q;
@@ -289,37 +299,51 @@ __global__ void __launch_bounds__(kThreads) k_apply_tile(DevGeom g, const T* __r
       T f1[Q];
 #pragma unroll
       for (int c = 0; c < Q; ++c) f1[c] = Fs[row + c];
+      const bool top = bb == P && l < Nz - 1;   // row shared with the layer above
+      T* yn = Yt + (e * P) * nrow + l * P + bb;
 #pragma unroll
       for (int a = 0; a < Q; ++a) {
         T s = Ys[row + a];
 #pragma unroll
         for (int c = 0; c < Q; ++c) s = fmx(D[c * Q + a], f1[c], s);
-        Ur[row + a] = s;
+        if (a == P) Ccol[(e * Nz + l) * Q + bb] = s;
+        else if (top) Rrow[(e * Nz + l) * Q + a] = s;
+        else yn[a * nrow] = s;
       }
     }
     __syncthreads();
-    // ---- 4. gather: own columns [P, P + ne·P) (plus the last column between walls) ----
-    const bool last_wall = !g.periodic && ex0 + ne == Nx;
-    const int nout = ne * P + (last_wall ? 1 : 0);   // output columns
-    T* yt = y + (size_t)ex0 * P * nrow;
-    for (int jj = warp; jj < nout; jj += nwarps) {   // a warp per output column
-      const int j = P + jj;
-      int e = j / P, a = j - e * P;
-      if (e == en) { e = en - 1; a = P; }       // right wall column
-      const bool left = a == 0 && (e > 1 || has_left);   // the element left of column j exists
-      T* yc = yt + (size_t)jj * nrow;
-      for (int r = lane; r < nrow; r += 32) {
-        int l = r / P, bb = r - l * P;
-        if (l == Nz) { l = Nz - 1; bb = P; }    // surface row
-        T s = Ur[((e * Nz + l) * Q + bb) * QP + a];
-        if (left) s += Ur[(((e - 1) * Nz + l) * Q + bb) * QP + P];
-        if (bb == 0 && l > 0) {
-          s += Ur[((e * Nz + l - 1) * Q + P) * QP + a];
-          if (left) s += Ur[(((e - 1) * Nz + l - 1) * Q + P) * QP + P];
-        }
-        yc[r] = -s;
-      }
+    // rows shared between layers: (e, l, a < P) adds to row (l+1)·P
+    for (int t = threadIdx.x; t < en * (Nz - 1) * P; t += blockDim.x) {
+      const int e = t / ((Nz - 1) * P), rem = t - e * ((Nz - 1) * P);
+      const int l = rem / P, a = rem - l * P;
+      if (e < e_first) continue;
+      Yt[(e * P + a) * nrow + (l + 1) * P] += Rrow[(e * Nz + l) * Q + a];
     }
+    __syncthreads();
+    // columns shared between elements: (e, l, b) adds to column (e+1)·P; the layers' top nodes
+    // (b = P, below the top layer) meet the next layer's b = 0 and are added in a second sweep
+    for (int sweep = 0; sweep < 2; ++sweep) {
+      const int per = sweep == 0 ? P : 1;        // b = 0..P−1, then b = P
+      for (int t = threadIdx.x; t < en * Nz * per; t += blockDim.x) {
+        const int e = t / (Nz * per), rem = t - e * (Nz * per);
+        const int l = rem / per, bb = sweep == 0 ? rem - l * per : P;
+        if (e < e_first) continue;
+        T* dst = Yt + ((e + 1) * P) * nrow + l * P + bb;
+        const T v = Ccol[(e * Nz + l) * Q + bb];
+        // the tile's last column has no element to its right: its first contribution is a store
+        // (rows l·P+b, b < P, and the surface node), the layer-top nodes then add
+        const bool first_here = e == en - 1 && (sweep == 0 || l == Nz - 1);
+        if (first_here) *dst = v;
+        else *dst += v;
+      }
+      __syncthreads();
+    }
+    // ---- 4. own columns [P, P + ne·P) (plus the last column between walls), contiguous ----
+    const bool last_wall = !g.periodic && ex0 + ne == Nx;
+    const int nout = (ne * P + (last_wall ? 1 : 0)) * nrow;   // output values
+    T* yt = y + (size_t)ex0 * P * nrow;
+    const T* ys = Yt + P * nrow;
+    for (int t = threadIdx.x; t < nout; t += blockDim.x) yt[t] = -ys[t];
   }
   // a copy still in flight (after a timeout, or the prefetch of a tile this CTA stopped
   // before) must land before the CTA's shared memory is released
