@@ -231,8 +231,8 @@ def run_reference(args):
 # ---------------------------------------------------------------------------------------------
 def apply_roofline(dev, reps: int = 20, Nx: int = 65536, kernels=("fp64_column", "fp64_tile", "fp32_tile")):
     """The operator apply y = 𝓛x on a 65536×4, P=6 periodic tank (9.8 M nodes), three kernels:
-    the FP64 element-column kernel (sem_laplace_apply), the FP64 tiled kernel (same call with
-    SEM_APPLY_KERNEL=tile) and the FP32 tiled kernel of the mixed path (sem_laplace_apply_f32).
+    the FP64 tiled kernel (sem_laplace_apply), the FP64 element-column kernel (same call with
+    SEM_APPLY_KERNEL=column) and the FP32 tiled kernel of the mixed path (sem_laplace_apply_f32).
 
     Algorithmic work per apply: (8(P+1)+7) flops per element-local node; algorithmic bytes:
     read x + write y, 16 B (FP64) or 8 B (FP32) per node.  Design bytes add the per-column
@@ -270,9 +270,9 @@ def apply_roofline(dev, reps: int = 20, Nx: int = 65536, kernels=("fp64_column",
             ts.append(e0.elapsed_time(e1))
         return float(np.median(ts))
 
-    def tile64():
+    def column64():
         old = os.environ.get("SEM_APPLY_KERNEL")
-        os.environ["SEM_APPLY_KERNEL"] = "tile"
+        os.environ["SEM_APPLY_KERNEL"] = "column"
         try:
             mesh.laplace_apply(x, y)
         finally:
@@ -287,7 +287,7 @@ def apply_roofline(dev, reps: int = 20, Nx: int = 65536, kernels=("fp64_column",
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs")
     out = {"workload": wl.name, "n_nodes": mesh.n, "flops_per_apply": flops, "l2_flushed": True}
-    for name, fn, elem in (("fp64_column", lambda: mesh.laplace_apply(x, y), 8), ("fp64_tile", tile64, 8),
+    for name, fn, elem in (("fp64_column", column64, 8), ("fp64_tile", lambda: mesh.laplace_apply(x, y), 8),
                            ("fp32_tile", lambda: mesh.laplace_apply_f32(x32, y32), 4)):
         if name not in kernels:
             continue

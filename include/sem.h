@@ -145,9 +145,10 @@ int sem_update_geometry(sem_mesh* m, const double* eta_d, void* stream);
 
 /* y = 𝓛 x with 𝓛_ij = −Σ_k ∫ (K∇N_j)·∇N_i over the mesh (§3.1.2), matrix-free,
  * all n rows (no Dirichlet modification), for the last sem_update_geometry.
- * x_d, y_d: device, n values, must not overlap.  Environment: SEM_APPLY_KERNEL=tile
- * selects the tiled kernel of sem_laplace_apply_f32 in FP64 (same result up to rounding
- * order); otherwise the element-column kernel with the mesh's edge workspace runs. */
+ * x_d, y_d: device, n values, must not overlap.  Runs the tiled kernel of
+ * sem_laplace_apply_f32 in FP64; the environment variable SEM_APPLY_KERNEL=column selects the
+ * element-column kernel with the mesh's edge workspace instead (same result up to rounding
+ * order). */
 int sem_laplace_apply(sem_mesh* m, const double* x_d, double* y_d, void* stream);
 
 /* The same operator in FP32 (the arithmetic of the mixed-precision inner solve): y = 𝓛 x

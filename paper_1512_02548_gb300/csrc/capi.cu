@@ -815,9 +815,13 @@ int sem_update_geometry(sem_mesh* m, const double* eta_d, void* stream) {
 int sem_laplace_apply(sem_mesh* m, const double* x_d, double* y_d, void* stream) {
   if (!m || !x_d || !y_d || x_d == y_d) return fail(SEM_ERR_INVALID_ARG, "bad pointer");
   DeviceGuard dg(m->device);
-  const char* k = std::getenv("SEM_APPLY_KERNEL");   // "tile": the tiled kernel, else element columns
-  if (k && std::strcmp(k, "tile") == 0) CUDA_TRY(launch_apply_tile(0, m->g, x_d, y_d, (cudaStream_t)stream));
-  else CUDA_TRY(launch_apply(m->g, x_d, y_d, m->qtmp, m->edgetmp, (cudaStream_t)stream));
+  const char* k = std::getenv("SEM_APPLY_KERNEL");   // "column": the element-column kernel, else tiled
+  cudaError_t e = cudaErrorInvalidValue;
+  if (!(k && std::strcmp(k, "column") == 0)) e = launch_apply_tile(0, m->g, x_d, y_d, (cudaStream_t)stream);
+  // the element-column kernel when asked for, or when the FP64 tile does not fit in shared memory
+  // (largest orders with many layers); the tile launcher checks that before launching anything
+  if (e == cudaErrorInvalidValue) e = launch_apply(m->g, x_d, y_d, m->qtmp, m->edgetmp, (cudaStream_t)stream);
+  if (e != cudaSuccess) return fail(SEM_ERR_CUDA, std::string("apply: ") + cudaGetErrorString(e));
   return SEM_OK;
 }
 
