@@ -79,6 +79,9 @@ template <int P>
 struct TileLayout {
   static constexpr int Q = P + 1;
   static constexpr int QP = (Q % 2 == 0) ? Q + 1 : Q;   // odd stride of the line buffers
+  // stride of one (element, layer) block of a line buffer: at least Q·QP and ≡ 8 (mod 16), so
+  // that the σ-lines of consecutive layers (one warp) fall in different shared-memory banks
+  static constexpr int BS = Q * QP + ((8 - (Q * QP) % 16) + 16) % 16;
   int E, en_max, tcols, xbuf, nline;
   __host__ __device__ TileLayout(int E_, int nrow, int Nz, int elem) {
     E = E_;
@@ -88,7 +91,7 @@ struct TileLayout {
     // than 16 bytes on each side; rounded up to 16 bytes
     const int per16 = 16 / elem;
     xbuf = ((tcols * nrow + 2 * per16 + per16 - 1) / per16) * per16;
-    nline = en_max * Nz * Q * QP;
+    nline = en_max * Nz * BS;
   }
   // bytes of dynamic shared memory for element size `elem`: two mbarriers (16 B), two staging
   // buffers, the line buffers and the tile's geometry
@@ -123,6 +126,7 @@ __global__ void __launch_bounds__(kThreads) k_apply_tile(DevGeom g, const T* __r
                                                          int E, int bulk_ok) {
   constexpr int Q = P + 1;
   constexpr int QP = TileLayout<P>::QP;
+  constexpr int BS = TileLayout<P>::BS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nrow = g.nrow, Nz = g.Nz, Nx = g.Nx, ncol = g.ncol;
   const TileLayout<P> L(E, nrow, Nz, (int)sizeof(T));
@@ -237,7 +241,7 @@ __global__ void __launch_bounds__(kThreads) k_apply_tile(DevGeom g, const T* __r
       T u[Q];
 #pragma unroll
       for (int c = 0; c < Q; ++c) u[c] = Xl[c * nrow];
-      T* out = Ur + ((e * Nz + l) * Q + bb) * QP;
+      T* out = Ur + (e * Nz + l) * BS + bb * QP;
 #pragma unroll
       for (int a = 0; a < Q; ++a) {
         T s = T(0);
@@ -261,18 +265,18 @@ __global__ void __launch_bounds__(kThreads) k_apply_tile(DevGeom g, const T* __r
       const T g11 = wa * c0 * gq[0];             // w_a Δσ/Δx d
       const T g22 = wa * c1 * gq[1];             // w_a Δx/Δσ /d
       const T* sg = Ss + l * P;
-      const int base = (e * Nz + l) * Q;
+      const int base = (e * Nz + l) * BS;
       T f2[Q];
 #pragma unroll
       for (int bb = 0; bb < Q; ++bb) {
         T ut = T(0);
 #pragma unroll
         for (int c = 0; c < Q; ++c) ut = fmx(D[bb * Q + c], u[c], ut);
-        const T ur = Ur[(base + bb) * QP + a];
+        const T ur = Ur[base + bb * QP + a];
         const T K12 = fmx(-sg[bb], dxd, hx);
         const T wb = w[bb];
         const T G12 = wa * wb * K12;
-        Fs[(base + bb) * QP + a] = fmx(g11 * wb, ur, G12 * ut);
+        Fs[base + bb * QP + a] = fmx(g11 * wb, ur, G12 * ut);
         f2[bb] = fmx(G12, ur, g22 * wb * fmx(K12, K12, T(1)) * ut);
       }
 #pragma unroll
@@ -280,7 +284,7 @@ __global__ void __launch_bounds__(kThreads) k_apply_tile(DevGeom g, const T* __r
         T s = T(0);
 #pragma unroll
         for (int c = 0; c < Q; ++c) s = fmx(D[c * Q + bb], f2[c], s);
-        Ys[(base + bb) * QP + a] = s;
+        Ys[base + bb * QP + a] = s;
       }
     }
     __syncthreads();
@@ -295,7 +299,7 @@ __global__ void __launch_bounds__(kThreads) k_apply_tile(DevGeom g, const T* __r
     for (int e = e_first + le0, rem = lr0; e < en; e += lde, rem += ldr) {
       if (rem >= lpe) { rem -= lpe; ++e; if (e >= en) break; }
       const int l = rem / Q, bb = rem - l * Q;
-      const int row = ((e * Nz + l) * Q + bb) * QP;
+      const int row = (e * Nz + l) * BS + bb * QP;
       T f1[Q];
 #pragma unroll
       for (int c = 0; c < Q; ++c) f1[c] = Fs[row + c];
