@@ -352,3 +352,29 @@ def test_c4_shoal_full_size_two_steps():
                 e, p = om.rk4_step(e, p, wl.dt, t=1.0 + s * wl.dt)
         assert np.abs(e).max() > 1e-5               # the zone is generating waves
         assert rel(eta, e) < tol and rel(phis, p) < tol
+
+
+def test_mesh_memory_is_reused_and_trimmed():
+    """Destroyed meshes return their device block to the library's cache: creating and destroying
+    many meshes of one size does not grow the device memory in use, a reused block gives the same
+    results, and sem_trim_cache hands the cached blocks back to CUDA."""
+    wl, om, gm = make_pair(P=5, Nx=40, Nz=3)
+    eta, phis = surface(om, seed=5)
+    ref = om.laplace_solve(eta, phis)
+    gm.close()
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(20):
+        m = sem.Mesh.from_workload(wl, h=om.h)
+        m.update_geometry(T(eta))
+        Phi = torch.zeros(om.n, dtype=torch.float64, device=DEV)
+        m.laplace_solve(T(phis), Phi)
+        assert rel(Phi, ref) < TOL_FP64
+        m.close()
+    torch.cuda.synchronize()
+    block = sem.mesh_footprint(sem.mesh_params(wl.P, wl.Nx, wl.Nz, wl.periodic, wl.Pf, wl.filter_alpha,
+                                               wl.filter_s, wl.filter_ic, wl.g), wl.element_edges(), om.h)
+    assert free0 - torch.cuda.mem_get_info()[0] <= 2 * block + (4 << 20)
+    sem.load_library().sem_trim_cache()
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] >= free0 - (4 << 20)
