@@ -320,7 +320,7 @@ int do_rk4_fused(sem_mesh* m, double* eta, double* phis, double t0, double dt, i
         CUDA_TRY(take_event(m, &e1));
         CUDA_TRY(cudaEventRecord(e0, s));
       }
-      CUDA_TRY(launch_stage(m->p.P, mixed, a, m->stage_team, m->stage_smem, s));
+      CUDA_TRY(launch_stage(m->p.P, mixed, 0, a, m->stage_team, m->stage_smem, s));
       if (m->timing) {
         CUDA_TRY(cudaEventRecord(e1, s));
         m->events.emplace_back(e0, e1);
@@ -755,7 +755,7 @@ static int mesh_create_impl(const sem_params* pin, const double* x_edges_h, cons
     m->fused = !(fz && fz[0] == '0') && p.precond == SEM_PRECOND_SEPARABLE;
     m->stage_smem = stage_smem_bytes(P, nrow, Nz, chunk);
     int per_sm = 0, sms = 0;
-    cudaError_t e = stage_occupancy(P, p.precision == SEM_PREC_MIXED, m->stage_smem, &per_sm);
+    cudaError_t e = stage_occupancy(P, p.precision == SEM_PREC_MIXED, 0, m->stage_smem, &per_sm);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess || per_sm < 1) {
       dev_free(dev, m->pool);
@@ -964,7 +964,7 @@ int sem_batch_create(sem_mesh* const* meshes, int count, sem_batch** out) {
     size_t smem = 0;
     for (int i : grp.second) smem = std::max(smem, meshes[i]->stage_smem);
     int per_sm = 0;
-    cudaError_t e = stage_occupancy(grp.first.first, grp.first.second, smem, &per_sm);
+    cudaError_t e = stage_occupancy(grp.first.first, grp.first.second, 1, smem, &per_sm);
     if (e != cudaSuccess || per_sm < 1) { delete b; return fail(SEM_ERR_CUDA, "fused stage kernel does not fit"); }
     const int cap = per_sm * sms;
     // split into launches of at most `cap` instances, then share the CTAs by work
@@ -986,7 +986,7 @@ int sem_batch_create(sem_mesh* const* meshes, int count, sem_batch** out) {
       int used = 0;
       for (size_t k = 0; k < L.members.size(); ++k) {
         const sem_mesh* m = meshes[L.members[k]];
-        const int limit = std::max(1, std::min(m->stage_team, (m->p.Nx + m->g.chunk - 1) / m->g.chunk));
+        const int limit = std::max(1, std::min(m->grid, (m->p.Nx + m->g.chunk - 1) / m->g.chunk));   // ≤ grid: buffer sizes
         c[k] = std::max(1, std::min(limit, (int)((double)cap * w[k] / wsum)));
         used += c[k];
       }
@@ -1092,7 +1092,7 @@ int sem_batch_rk4_step(sem_batch* b, double* const* eta_d, double* const* phis_d
       for (auto& L : b->launches) {
         CUDA_TRY(cudaMemsetAsync(L.bars_d, 0, 2 * sizeof(unsigned int) * L.members.size(), s));
         const StageArgs a{L.inst_d, L.cta_d, L.bars_d, stage, step};
-        CUDA_TRY(launch_stage(L.P, L.mixed, a, L.grid, L.smem, s));
+        CUDA_TRY(launch_stage(L.P, L.mixed, 1, a, L.grid, L.smem, s));
       }
   int rc = batch_status(b, s);
   if (t_h)
@@ -1121,7 +1121,7 @@ int sem_batch_laplace_solve(sem_batch* b, const double* const* eta_d, const doub
   for (auto& L : b->launches) {
     CUDA_TRY(cudaMemsetAsync(L.bars_d, 0, 2 * sizeof(unsigned int) * L.members.size(), s));
     const StageArgs a{L.inst_d, L.cta_d, L.bars_d, 0, 0};
-    CUDA_TRY(launch_stage(L.P, L.mixed, a, L.grid, L.smem, s));
+    CUDA_TRY(launch_stage(L.P, L.mixed, 1, a, L.grid, L.smem, s));
   }
   return batch_status(b, s);
 }

@@ -161,15 +161,15 @@ size_t stage_smem_bytes(int P, int nrow, int Nz, int chunk) {
   return apply_smem_bytes(P, nrow, Nz, chunk, sizeof(double));
 }
 
-cudaError_t stage_occupancy(int P, int mixed, size_t smem, int* per_sm) {
+cudaError_t stage_occupancy(int P, int mixed, int wide, size_t smem, int* per_sm) {
   cudaError_t e = cudaSuccess;
-  SEM_DISPATCH_P(P, (e = stage_occupancy_impl<PP>(mixed, smem, per_sm)));
+  SEM_DISPATCH_P(P, (e = stage_occupancy_impl<PP>(mixed, wide, smem, per_sm)));
   return e;
 }
 
-cudaError_t launch_stage(int P, int mixed, const StageArgs& a, int grid, size_t smem, cudaStream_t s) {
+cudaError_t launch_stage(int P, int mixed, int wide, const StageArgs& a, int grid, size_t smem, cudaStream_t s) {
   cudaError_t e = cudaSuccess;
-  SEM_DISPATCH_P(P, (e = launch_stage_impl<PP>(mixed, a, grid, smem, s)));
+  SEM_DISPATCH_P(P, (e = launch_stage_impl<PP>(mixed, wide, a, grid, smem, s)));
   count_launch();
   return e;
 }

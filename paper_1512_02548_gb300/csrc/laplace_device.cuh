@@ -1178,8 +1178,11 @@ __device__ void stage_body(Instance& I, const Team& tm, int stage, int step, uns
   }
 }
 
-template <int P, bool MIXED>
-__global__ void __launch_bounds__(kThreads) k_stage(StageArgs B) {
+// WIDE = false: one CTA per SM and the full register file, so the stage keeps its values in
+// registers (single meshes: one team, latency bound).  WIDE = true: two CTAs per SM at 128
+// registers, more co-resident teams for batches of many small instances.
+template <int P, bool MIXED, bool WIDE>
+__global__ void __launch_bounds__(kThreads, WIDE ? 2 : 1) k_stage(StageArgs B) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[160];
   __shared__ int s_flag;
@@ -1275,18 +1278,24 @@ cudaError_t launch_prec_setup_impl(const DevGeom& g, const PrecSetup& ps, cudaSt
 }
 
 template <int P>
-cudaError_t stage_occupancy_impl(int mixed, size_t smem, int* per_sm) {
-  const void* fn = mixed ? (const void*)k_stage<P, true> : (const void*)k_stage<P, false>;
+static const void* stage_fn(int mixed, int wide) {
+  if (wide) return mixed ? (const void*)k_stage<P, true, true> : (const void*)k_stage<P, false, true>;
+  return mixed ? (const void*)k_stage<P, true, false> : (const void*)k_stage<P, false, false>;
+}
+
+template <int P>
+cudaError_t stage_occupancy_impl(int mixed, int wide, size_t smem, int* per_sm) {
+  const void* fn = stage_fn<P>(mixed, wide);
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, fn, kThreads, smem);
 }
 
 template <int P>
-cudaError_t launch_stage_impl(int mixed, const StageArgs& a, int grid, size_t smem, cudaStream_t s) {
+cudaError_t launch_stage_impl(int mixed, int wide, const StageArgs& a, int grid, size_t smem, cudaStream_t s) {
   StageArgs aa = a;
   void* args[] = {&aa};
-  const void* fn = mixed ? (const void*)k_stage<P, true> : (const void*)k_stage<P, false>;
+  const void* fn = stage_fn<P>(mixed, wide);
   return cudaLaunchCooperativeKernel(fn, grid, kThreads, args, smem, s);
 }
 

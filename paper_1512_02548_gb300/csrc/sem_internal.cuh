@@ -184,16 +184,17 @@ template <int P> cudaError_t launch_pcg_impl(int mixed, const DevGeom& g, const 
 template <int P> cudaError_t launch_prec_setup_impl(const DevGeom& g, const PrecSetup& ps, cudaStream_t s);
 template <int P> cudaError_t launch_apply_tile_impl(int fp32, const DevGeom& g, const void* x, void* y,
                                                     cudaStream_t s);
-template <int P> cudaError_t stage_occupancy_impl(int mixed, size_t smem, int* per_sm);
-template <int P> cudaError_t launch_stage_impl(int mixed, const StageArgs& a, int grid, size_t smem,
+template <int P> cudaError_t stage_occupancy_impl(int mixed, int wide, size_t smem, int* per_sm);
+template <int P> cudaError_t launch_stage_impl(int mixed, int wide, const StageArgs& a, int grid, size_t smem,
                                                cudaStream_t s);
 
 // ---- launchers (kernels_laplace.cu) ----
 // Fused RK stage for instances of order P: capacity (CTAs per SM) at a given dynamic smem,
-// and the cooperative launch.
-cudaError_t stage_occupancy(int P, int mixed, size_t smem, int* per_sm);
+// and the cooperative launch.  wide = 0: the one-CTA-per-SM variant (single meshes);
+// wide = 1: the two-CTAs-per-SM variant (batches).
+cudaError_t stage_occupancy(int P, int mixed, int wide, size_t smem, int* per_sm);
 size_t stage_smem_bytes(int P, int nrow, int Nz, int chunk);
-cudaError_t launch_stage(int P, int mixed, const StageArgs& a, int grid, size_t smem, cudaStream_t s);
+cudaError_t launch_stage(int P, int mixed, int wide, const StageArgs& a, int grid, size_t smem, cudaStream_t s);
 // out[k] = status word of inst[k]; a nonzero word is cleared after it is read.
 cudaError_t launch_gather_status(const Instance* inst, int n, int* out, cudaStream_t s);
 cudaError_t upload_line_tables(const double* D64, const double* w64);  // packed, all orders
