@@ -29,8 +29,14 @@
  * end to read the mesh's device status word; all others return as soon as
  * the work is enqueued.
  *
- * Tuning.  The environment variable SEM_GRID_LIMIT, read by sem_mesh_create, caps
- * the number of CTAs of the persistent Krylov kernel (default: all co-resident).
+ * Environment (tuning and testing).  Read by sem_mesh_create: SEM_GRID_LIMIT caps the number
+ * of CTAs of the persistent Krylov kernel and of a mesh's fused stage (default: all
+ * co-resident); SEM_FUSED_STAGE=0 makes sem_rk4_step run the multi-kernel path instead of one
+ * fused launch per RK stage.  Read by sem_laplace_apply: SEM_APPLY_KERNEL=column (see there).
+ *
+ * Device memory.  Each mesh and batch owns one device block, taken at creation from a
+ * per-device cache of blocks freed by earlier meshes and batches (or from cudaMalloc) and given
+ * back to that cache at destruction; sem_trim_cache returns the cached blocks to CUDA.
  *
  * Errors.  Every call returns SEM_OK (0) or one of the codes below;
  * sem_last_error() gives a message for the calling thread's last failure.
