@@ -120,15 +120,17 @@ static __device__ __forceinline__ bool tile_range(const DevGeom& g, int ex0, int
   return true;
 }
 
-// bulk != 0: x is 16-byte aligned and interior tiles are staged by bulk copies.
-template <int P, class T>
+// bulk_ok != 0: x is 16-byte aligned and interior tiles are staged by bulk copies.
+// NZC > 0: the layer count is the compile-time constant NZC (= g.Nz), which turns the row
+// arithmetic into constants; NZC = 0 reads it from g.
+template <int P, class T, int NZC>
 __global__ void __launch_bounds__(kThreads) k_apply_tile(DevGeom g, const T* __restrict__ x, T* __restrict__ y,
                                                          int E, int bulk_ok) {
   constexpr int Q = P + 1;
   constexpr int QP = TileLayout<P>::QP;
   constexpr int BS = TileLayout<P>::BS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int nrow = g.nrow, Nz = g.Nz, Nx = g.Nx, ncol = g.ncol;
+  const int nrow = NZC ? NZC * P + 1 : g.nrow, Nz = NZC ? NZC : g.Nz, Nx = g.Nx, ncol = g.ncol;
   const TileLayout<P> L(E, nrow, Nz, (int)sizeof(T));
   unsigned long long* mbar = reinterpret_cast<unsigned long long*>(smem_raw);   // [2]
   T* Xb[2];

@@ -1311,18 +1311,23 @@ cudaError_t launch_apply_tile_impl(int fp32, const DevGeom& g, const void* x, vo
   while (E > 1 && apply_tile_smem<P>(E, g.nrow, g.Nz, elem) > kTileSmemTarget) E >>= 1;
   const size_t smem = apply_tile_smem<P>(E, g.nrow, g.Nz, elem);
   if (smem > (size_t)kMaxDynSmem) return cudaErrorInvalidValue;
-  const void* fn = fp32 ? (const void*)k_apply_tile<P, float> : (const void*)k_apply_tile<P, double>;
-  // the attribute, the SM count and the occupancy for the last (device, precision, smem) are
+  // FP32 kernels specialised on the common layer counts 1, 2 and 4 (constant row arithmetic)
+  const int nzc = fp32 && (g.Nz == 1 || g.Nz == 2 || g.Nz == 4) ? g.Nz : 0;
+  const int k = fp32 ? 1 + (nzc == 4 ? 3 : nzc) : 0;   // kernel variant 0..4
+  const void* fns[5] = {(const void*)k_apply_tile<P, double, 0>, (const void*)k_apply_tile<P, float, 0>,
+                        (const void*)k_apply_tile<P, float, 1>, (const void*)k_apply_tile<P, float, 2>,
+                        (const void*)k_apply_tile<P, float, 4>};
+  const void* fn = fns[k];
+  // the attribute, the SM count and the occupancy for the last (device, smem) of each variant are
   // kept, so that a repeated apply costs one launch on the host
   static std::mutex mu;
-  static int last_dev[2] = {-1, -1}, last_sms[2] = {0, 0}, last_per_sm[2] = {0, 0};
-  static size_t last_smem[2] = {0, 0};
+  static int last_dev[5] = {-1, -1, -1, -1, -1}, last_sms[5] = {0}, last_per_sm[5] = {0};
+  static size_t last_smem[5] = {0};
   int dev = 0, sms = 0, per_sm = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   {
     std::lock_guard<std::mutex> lk(mu);
-    const int k = fp32 ? 1 : 0;
     if (last_dev[k] != dev || last_smem[k] != smem) {
       if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem)) != cudaSuccess)
         return e;
@@ -1337,10 +1342,16 @@ cudaError_t launch_apply_tile_impl(int fp32, const DevGeom& g, const void* x, vo
   const long long ntiles = (g.Nx + E - 1) / E;
   const int grid = (int)(ntiles < (long long)per_sm * sms ? ntiles : (long long)per_sm * sms);
   const int bulk_ok = (reinterpret_cast<uintptr_t>(x) % 16) == 0 ? 1 : 0;   // bulk copies need 16-B alignment
-  if (fp32) k_apply_tile<P, float><<<grid, kThreads, smem, s>>>(g, static_cast<const float*>(x),
-                                                               static_cast<float*>(y), E, bulk_ok);
-  else k_apply_tile<P, double><<<grid, kThreads, smem, s>>>(g, static_cast<const double*>(x),
-                                                            static_cast<double*>(y), E, bulk_ok);
+  const float* xf = static_cast<const float*>(x);
+  float* yf = static_cast<float*>(y);
+  switch (k) {
+    case 0: k_apply_tile<P, double, 0><<<grid, kThreads, smem, s>>>(g, static_cast<const double*>(x),
+                                                                   static_cast<double*>(y), E, bulk_ok); break;
+    case 1: k_apply_tile<P, float, 0><<<grid, kThreads, smem, s>>>(g, xf, yf, E, bulk_ok); break;
+    case 2: k_apply_tile<P, float, 1><<<grid, kThreads, smem, s>>>(g, xf, yf, E, bulk_ok); break;
+    case 3: k_apply_tile<P, float, 2><<<grid, kThreads, smem, s>>>(g, xf, yf, E, bulk_ok); break;
+    default: k_apply_tile<P, float, 4><<<grid, kThreads, smem, s>>>(g, xf, yf, E, bulk_ok); break;
+  }
   count_launch();
   return cudaGetLastError();
 }
