@@ -478,9 +478,9 @@ static __device__ __forceinline__ bool is_halo_col(const DevGeom& g, const Range
 //   s ← w + β s,  r ← r − α s,  p ← u + β p,  x ← x + α p      (first iteration: s ← w, p ← u).
 // With update == false only the preconditioner part runs on r[cur].  Jacobi completes u here;
 // the separable preconditioner transforms the residual to the σ-eigenbasis and condenses.
-template <int P, class T>
+template <int P, class T, class TP>
 __device__ void cg_update(const DevGeom& g, Smem<P, T>& s, const Range& R, const Team& tm,
-                          const PrecView<T>& pv, int precond, const CgVecs<T>& V, int cur, bool update,
+                          const PrecView<TP>& pv, int precond, const CgVecs<T>& V, int cur, bool update,
                           bool first, T alpha, T beta) {
   constexpr int Q = P + 1, Pm = P - 1;
   const int nrow = g.nrow, nr = nrow - 1;
@@ -488,8 +488,10 @@ __device__ void cg_update(const DevGeom& g, Smem<P, T>& s, const Range& R, const
   T* r_new = V.r[cur ^ 1];
   const T* s_old = V.s[cur];
   T* s_new = V.s[cur ^ 1];
-  T* X = s.X;     // [E][Q][nr] residual of the chunk's element columns
-  T* RH = s.F1;   // [E][Q][nr] σ-transformed residual
+  // the preconditioner works in TP (FP32 also under FP64 vectors); its staging buffers reuse
+  // the apply's shared memory, which holds at least as many values of type T
+  TP* X = reinterpret_cast<TP*>(s.X);     // [E][Q][nr] residual of the chunk's element columns
+  TP* RH = reinterpret_cast<TP*>(s.F1);   // [E][Q][nr] σ-transformed residual
   const int E = g.chunk, qn = Q * nr;
   for (int ex0 = R.e0; ex0 < R.e1; ex0 += E) {
     const int ne = min(E, R.e1 - ex0);
@@ -521,7 +523,7 @@ __device__ void cg_update(const DevGeom& g, Smem<P, T>& s, const Range& R, const
         if (own) V.u[i] = uv;
         else if (is_halo_col(g, R, ex, a)) V.uh[(size_t)tm.rank * nrow + j] = uv;
       } else {
-        X[t] = rv;
+        X[t] = (TP)rv;
       }
     }
     if (precond == PREC_JACOBI) continue;
@@ -529,8 +531,8 @@ __device__ void cg_update(const DevGeom& g, Smem<P, T>& s, const Range& R, const
     for (int t = threadIdx.x; t < ne * qn; t += blockDim.x) {
       const int e = t / qn, rem = t - e * qn;
       const int a = rem / nr, k = rem - a * nr, ex = ex0 + e;
-      const T* Xa = X + e * qn + a * nr;
-      T v = 0;
+      const TP* Xa = X + e * qn + a * nr;
+      TP v = 0;
       for (int j = 0; j < nr; ++j) v = fmx(pv.S[j * nr + k], Xa[j], v);
       RH[t] = v;
       if (owns_local_col(g, ex, a)) pv.rhat[(size_t)col_of(g, ex, a) * nr + k] = v;
@@ -538,14 +540,14 @@ __device__ void cg_update(const DevGeom& g, Smem<P, T>& s, const Range& R, const
     __syncthreads();
     for (int t = threadIdx.x; t < ne * nr; t += blockDim.x) {
       const int e = t / nr, k = t - e * nr, ex = ex0 + e;
-      const T* RHe = RH + e * qn;
-      const T* Zk = pv.Z + ((size_t)k * g.Nx + ex) * 2 * Pm;
+      const TP* RHe = RH + e * qn;
+      const TP* Zk = pv.Z + ((size_t)k * g.Nx + ex) * 2 * Pm;
       // the assembled residual at an interface node enters once: with the element that owns
       // that column (its left end), plus the walls' last column with the last element
-      T l = RHe[k], r = owns_local_col(g, ex, P) ? RHe[P * nr + k] : T(0);
+      TP l = RHe[k], r = owns_local_col(g, ex, P) ? RHe[P * nr + k] : TP(0);
 #pragma unroll
       for (int m = 0; m < Pm; ++m) {
-        const T f = RHe[(1 + m) * nr + k];
+        const TP f = RHe[(1 + m) * nr + k];
         l = fmx(-Zk[m], f, l);
         r = fmx(-Zk[Pm + m], f, r);
       }
@@ -577,12 +579,12 @@ __device__ void phase_interface(const DevGeom& g, const PrecView<T>& pv, const T
 
 // Back-substitution of the element interiors, then u = S ẑ on owned columns and on the halo
 // column (whose modal values are interface unknowns, known to every CTA after the solve).
-template <int P, class T>
+template <int P, class T, class TP>
 __device__ void phase_backsub(const DevGeom& g, Smem<P, T>& s, const Range& R, const Team& tm,
-                              const PrecView<T>& pv, const CgVecs<T>& V) {
+                              const PrecView<TP>& pv, const CgVecs<T>& V) {
   constexpr int Q = P + 1, Pm = P - 1;
   const int nrow = g.nrow, nr = pv.nr, N = pv.nif;
-  T* ZH = s.F1;   // [E][Q][nr]
+  TP* ZH = reinterpret_cast<TP*>(s.F1);   // [E][Q][nr]
   const int E = g.chunk, qn = Q * nr;
   for (int ex0 = R.e0; ex0 < R.e1; ex0 += E) {
     const int ne = min(E, R.e1 - ex0);
@@ -590,15 +592,15 @@ __device__ void phase_backsub(const DevGeom& g, Smem<P, T>& s, const Range& R, c
       const int e = t / qn, rem = t - e * qn;
       const int a = rem / nr, k = rem - a * nr, ex = ex0 + e;
       const int jl = ex, jr = (ex + 1 == N) ? 0 : ex + 1;
-      const T zl = ldcg(pv.zb + (size_t)k * N + jl);
-      const T zr = ldcg(pv.zb + (size_t)k * N + jr);
-      T v;
+      const TP zl = ldcg(pv.zb + (size_t)k * N + jl);
+      const TP zr = ldcg(pv.zb + (size_t)k * N + jr);
+      TP v;
       if (a == 0) v = zl;
       else if (a == P) v = zr;
       else {
         const int i = a - 1;
-        const T* Ai = pv.Aii + (((size_t)k * g.Nx + ex) * Pm + i) * Pm;
-        const T* Zk = pv.Z + ((size_t)k * g.Nx + ex) * 2 * Pm;
+        const TP* Ai = pv.Aii + (((size_t)k * g.Nx + ex) * Pm + i) * Pm;
+        const TP* Zk = pv.Z + ((size_t)k * g.Nx + ex) * 2 * Pm;
         v = 0;
 #pragma unroll
         for (int m = 0; m < Pm; ++m) v = fmx(Ai[m], pv.rhat[(size_t)(ex * P + 1 + m) * nr + k], v);
@@ -614,12 +616,12 @@ __device__ void phase_backsub(const DevGeom& g, Smem<P, T>& s, const Range& R, c
       const bool own = owns_local_col(g, ex, a);
       const bool halo = is_halo_col(g, R, ex, a);
       if (!own && !halo) continue;
-      const T* Za = ZH + e * qn + a * nr;
-      const T* Sj = pv.S + j * nr;
-      T v = 0;
+      const TP* Za = ZH + e * qn + a * nr;
+      const TP* Sj = pv.S + j * nr;
+      TP v = 0;
       for (int k = 0; k < nr; ++k) v = fmx(Sj[k], Za[k], v);
-      if (own) V.u[(size_t)col_of(g, ex, a) * nrow + j] = v;
-      else V.uh[(size_t)tm.rank * nrow + j] = v;
+      if (own) V.u[(size_t)col_of(g, ex, a) * nrow + j] = (T)v;
+      else V.uh[(size_t)tm.rank * nrow + j] = (T)v;
     }
     __syncthreads();
   }
@@ -627,14 +629,14 @@ __device__ void phase_backsub(const DevGeom& g, Smem<P, T>& s, const Range& R, c
 
 // Remaining grid phases of u = M⁻¹ r after cg_update (separable: interface solve and
 // back-substitution; Jacobi: nothing but a barrier that protects w and edge).
-template <int P, class T>
+template <int P, class T, class TP>
 __device__ bool finish_precondition(const DevGeom& g, Smem<P, T>& s, const Range& R, const Team& tm,
-                                    const PcgArgs& PA, const PrecView<T>& pv, const CgVecs<T>& V, int* s_flag) {
+                                    const PcgArgs& PA, const PrecView<TP>& pv, const CgVecs<T>& V, int* s_flag) {
   if (PA.precond == PREC_JACOBI) return grid_barrier(tm, s_flag);
   if (!grid_barrier(tm, s_flag)) return false;
-  phase_interface<T>(g, pv, tm);
+  phase_interface<TP>(g, pv, tm);
   if (!grid_barrier(tm, s_flag)) return false;
-  phase_backsub<P, T>(g, s, R, tm, pv, V);
+  phase_backsub<P, T, TP>(g, s, R, tm, pv, V);
   return true;
 }
 
@@ -644,16 +646,16 @@ __device__ bool finish_precondition(const DevGeom& g, Smem<P, T>& s, const Range
 // Starts from V.x with its residual in V.r[0].  Stops when ‖r‖² ≤ target or after max_it
 // iterations.  Returns the iterations, or −1 on a barrier timeout; ‖r‖² of the final residual
 // (on thread 0) in *rr_out.
-template <int P, class T, class A>
+template <int P, class T, class A, class TP>
 __device__ int cg_solve(const DevGeom& g, Smem<P, T>& s, const Range& R, const Team& tm, const PcgArgs& PA,
-                        const PrecView<T>& pv, const CgVecs<T>& V, double target, int max_it, double* red,
+                        const PrecView<TP>& pv, const CgVecs<T>& V, double target, int max_it, double* red,
                         int* s_flag, double* rr_out) {
   const int nrow = g.nrow;
   __shared__ T s_scal[2];
   __shared__ int s_stop;
   int cur = 0;
-  cg_update<P, T>(g, s, R, tm, pv, PA.precond, V, cur, false, true, T(0), T(0));
-  if (!finish_precondition<P, T>(g, s, R, tm, PA, pv, V, s_flag)) return -1;
+  cg_update<P, T, TP>(g, s, R, tm, pv, PA.precond, V, cur, false, true, T(0), T(0));
+  if (!finish_precondition<P, T, TP>(g, s, R, tm, PA, pv, V, s_flag)) return -1;
   int k = 0;
   double gamma_prev = 1.0, alpha_prev = 1.0, rr = 0.0;
   while (true) {
@@ -705,9 +707,9 @@ __device__ int cg_solve(const DevGeom& g, Smem<P, T>& s, const Range& R, const T
     __syncthreads();
     if (s_stop) break;
     const T alpha = s_scal[0], beta = s_scal[1];
-    cg_update<P, T>(g, s, R, tm, pv, PA.precond, V, cur, true, k == 0, alpha, beta);
+    cg_update<P, T, TP>(g, s, R, tm, pv, PA.precond, V, cur, true, k == 0, alpha, beta);
     cur ^= 1;
-    if (!finish_precondition<P, T>(g, s, R, tm, PA, pv, V, s_flag)) return -1;
+    if (!finish_precondition<P, T, TP>(g, s, R, tm, PA, pv, V, s_flag)) return -1;
     ++k;
   }
   *rr_out = rr;
@@ -805,7 +807,10 @@ __device__ bool solve_body(const DevGeom& g, const PcgArgs& A, const Team& tm, u
     const CgVecs<double> V{A.x, {A.r64, A.r64b}, {A.p64b, A.s64b}, A.p64a, A.z64, A.uh64, A.q64, A.edge64,
                            g.invdiag64};
     double rr_out = rr;
-    iters = cg_solve<P, double, double>(g, s64, R, tm, A, A.pv64, V, target, A.max_iter, red, &s_flag, &rr_out);
+    // FP64 vectors, FP32 preconditioner: u = M⁻¹r only steers the search directions, and the
+    // FP32 pipe is 64 times the FP64 pipe on this part
+    iters = cg_solve<P, double, double, float>(g, s64, R, tm, A, A.pv32, V, target, A.max_iter, red, &s_flag,
+                                               &rr_out);
     if (iters < 0) return false;
     rr = rr_out;
   } else {
@@ -840,7 +845,7 @@ __device__ bool solve_body(const DevGeom& g, const PcgArgs& A, const Team& tm, u
       if (!grid_barrier(tm, &s_flag)) return false;
       const double tgt_in = fmax(A.inner_rtol * A.inner_rtol * rr, 0.25 * target);
       double rr_in = rr;
-      const int it = cg_solve<P, float, float>(g, s32, R, tm, A, A.pv32, V, tgt_in, A.max_iter - iters, red,
+      const int it = cg_solve<P, float, float, float>(g, s32, R, tm, A, A.pv32, V, tgt_in, A.max_iter - iters, red,
                                                &s_flag, &rr_in);
       if (it < 0) return false;
       iters += it;
