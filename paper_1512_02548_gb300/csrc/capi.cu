@@ -630,18 +630,14 @@ static int mesh_create_impl(const sem_params* pin, const double* x_edges_h, cons
   const size_t o_s64b = cv.take<double>(n), o_s32b = cv.take<float>(n);
   const size_t o_uh64 = cv.take<double>((size_t)m->grid * nrow), o_uh32 = cv.take<float>((size_t)m->grid * nrow);
   const size_t nEl = (size_t)nr * Nx, nIf = (size_t)nr * N;
-  const size_t o_S64 = cv.take<double>((size_t)nr * nr), o_S32 = cv.take<float>((size_t)nr * nr),
+  const size_t o_S32 = cv.take<float>((size_t)nr * nr),
                o_lam = cv.take<double>(nr), o_schur = cv.take<double>(nEl * 3),
-               o_A64 = cv.take<double>(nEl * Pm * Pm + 1), o_A32 = cv.take<float>(nEl * Pm * Pm + 1),
-               o_Z64 = cv.take<double>(nEl * 2 * Pm + 1), o_Z32 = cv.take<float>(nEl * 2 * Pm + 1),
-               o_te64 = cv.take<double>(nIf), o_tm64 = cv.take<double>(nIf), o_tcp64 = cv.take<double>(nIf),
-               o_tz64 = cv.take<double>(nIf), o_te32 = cv.take<float>(nIf), o_tm32 = cv.take<float>(nIf),
-               o_tcp32 = cv.take<float>(nIf), o_tz32 = cv.take<float>(nIf), o_tvl64 = cv.take<double>(nr),
-               o_tfac64 = cv.take<double>(nr), o_tvl32 = cv.take<float>(nr), o_tfac32 = cv.take<float>(nr),
-               o_gL64 = cv.take<double>(nEl), o_gR64 = cv.take<double>(nEl), o_gL32 = cv.take<float>(nEl),
-               o_gR32 = cv.take<float>(nEl), o_zb64 = cv.take<double>(nIf), o_zb32 = cv.take<float>(nIf),
-               o_rh64 = cv.take<double>((size_t)ncol * nr), o_rh32 = cv.take<float>((size_t)ncol * nr),
-               o_pscr = cv.take<double>(nIf);
+               o_A32 = cv.take<float>(nEl * Pm * Pm + 1), o_Z32 = cv.take<float>(nEl * 2 * Pm + 1),
+               o_te32 = cv.take<float>(nIf), o_tm32 = cv.take<float>(nIf),
+               o_tcp32 = cv.take<float>(nIf), o_tz32 = cv.take<float>(nIf),
+               o_tvl32 = cv.take<float>(nr), o_tfac32 = cv.take<float>(nr),
+               o_gL32 = cv.take<float>(nEl), o_gR32 = cv.take<float>(nEl), o_zb32 = cv.take<float>(nIf),
+               o_rh32 = cv.take<float>((size_t)ncol * nr);
   const size_t o_xcol = cv.take<double>(ncol), o_wave = cv.take<double>(4 * kMaxWaveComp);
   const size_t o_wt = cv.take<double>(ncol), o_etax = cv.take<double>(ncol), o_phisx = cv.take<double>(ncol),
                o_R = cv.take<double>((size_t)2 * Nx * Q), o_scr = cv.take<double>((size_t)4 * Nx + 2 * (N + 1)),
@@ -682,7 +678,7 @@ static int mesh_create_impl(const sem_params* pin, const double* x_edges_h, cons
   up(o_hx, hx_loc); up(o_dxe, dxe); up(o_dsl, dsl); up(o_sig, sig);
   up(o_tD, L.D); up(o_tMD, MD); up(o_tB, B); up(o_tI, I); up(o_tF, F); up(o_tcw, cw);
   up(o_tAii, Aii); up(o_tZ, Z); up(o_tse, se); up(o_te, th_e); up(o_tm, th_m); up(o_tcp, th_cp); up(o_tz, th_z);
-  up(o_S64, Sg); up(o_lam, lam);
+  up(o_lam, lam);
   {
     std::vector<double> xc(ncol);
     for (int c = 0; c < ncol; ++c) {
@@ -720,16 +716,10 @@ static int mesh_create_impl(const sem_params* pin, const double* x_edges_h, cons
   a.precond = p.precond == SEM_PRECOND_JACOBI ? PREC_JACOBI : PREC_SEPARABLE;
   PrecSetup& ps = m->ps;
   ps.nr = nr; ps.nif = N; ps.lam = D_(o_lam); ps.schur = D_(o_schur);
-  ps.Aii64 = D_(o_A64); ps.Z64 = D_(o_Z64); ps.te64 = D_(o_te64); ps.tm64 = D_(o_tm64); ps.tcp64 = D_(o_tcp64);
-  ps.tz64 = D_(o_tz64); ps.tvl64 = D_(o_tvl64); ps.tfac64 = D_(o_tfac64);
   ps.Aii32 = F_(o_A32); ps.Z32 = F_(o_Z32); ps.te32 = F_(o_te32); ps.tm32 = F_(o_tm32); ps.tcp32 = F_(o_tcp32);
   ps.tz32 = F_(o_tz32); ps.tvl32 = F_(o_tvl32); ps.tfac32 = F_(o_tfac32);
-  ps.scratch = D_(o_pscr);
-  ps.v64 = PrecView<double>{nr, N, D_(o_S64), ps.Aii64, ps.Z64, ps.te64, ps.tm64, ps.tcp64, ps.tz64, ps.tvl64,
-                            ps.tfac64, D_(o_gL64), D_(o_gR64), D_(o_zb64), D_(o_rh64)};
   ps.v32 = PrecView<float>{nr, N, F_(o_S32), ps.Aii32, ps.Z32, ps.te32, ps.tm32, ps.tcp32, ps.tz32, ps.tvl32,
                            ps.tfac32, F_(o_gL32), F_(o_gR32), F_(o_zb32), F_(o_rh32)};
-  a.pv64 = ps.v64;
   a.pv32 = ps.v32;
 
   m->Phi = D_(o_Phi); m->qtmp = D_(o_qtmp); m->edgetmp = D_(o_etmp);

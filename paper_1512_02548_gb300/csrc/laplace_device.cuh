@@ -954,16 +954,11 @@ __device__ __forceinline__ void prec_elem_mode(const DevGeom& g, const PrecSetup
     }
   }
   const size_t base = (size_t)k * g.Nx + ex;
-  double* A64 = ps.Aii64 + base * Pm * Pm;
   float* A32 = ps.Aii32 + base * Pm * Pm;
 #pragma unroll
   for (int i = 0; i < Pm; ++i)
 #pragma unroll
-    for (int j = 0; j < Pm; ++j) {
-      const float v = 0.5f * (Ai[i][j] + Ai[j][i]);
-      A32[i * Pm + j] = v;
-      A64[i * Pm + j] = (double)v;
-    }
+    for (int j = 0; j < Pm; ++j) A32[i * Pm + j] = 0.5f * (Ai[i][j] + Ai[j][i]);
   double Z0[Pm], Z1[Pm];
 #pragma unroll
   for (int i = 0; i < Pm; ++i) {
@@ -983,12 +978,11 @@ __device__ __forceinline__ void prec_elem_mode(const DevGeom& g, const PrecSetup
     S01 -= Z0[i] * Kx[(1 + i) * Q + P];
     S11 -= Z1[i] * Kx[(1 + i) * Q + P];
   }
-  double* Z64 = ps.Z64 + base * 2 * Pm;
   float* Z32 = ps.Z32 + base * 2 * Pm;
 #pragma unroll
   for (int i = 0; i < Pm; ++i) {
-    Z64[i] = Z0[i]; Z64[Pm + i] = Z1[i];
-    Z32[i] = (float)Z0[i]; Z32[Pm + i] = (float)Z1[i];
+    Z32[i] = (float)Z0[i];
+    Z32[Pm + i] = (float)Z1[i];
   }
   ps.schur[base * 3 + 0] = S00;
   ps.schur[base * 3 + 1] = S01;
@@ -1021,25 +1015,19 @@ static __device__ void prec_tri_mode(const DevGeom& g, const PrecSetup& ps, int 
   const bool staged = stage_sm != nullptr;
   const int N = ps.nif, Nx = g.Nx;
   const double* sc = ps.schur + (size_t)k * Nx * 3;
-  double* te = ps.te64 + (size_t)k * N;
-  double* tm = ps.tm64 + (size_t)k * N;
-  double* tcp = ps.tcp64 + (size_t)k * N;
-  double* tz = ps.tz64 + (size_t)k * N;
   float* te32 = ps.te32 + (size_t)k * N;
   float* tm32 = ps.tm32 + (size_t)k * N;
   float* tcp32 = ps.tcp32 + (size_t)k * N;
   float* tz32 = ps.tz32 + (size_t)k * N;
   const double corner = g.periodic ? sc[(Nx - 1) * 3 + 1] : 0.0;
-  float* dd = staged ? stage_sm : tm32;     // modified diagonal (FP32)
+  float* dd = staged ? stage_sm : tm32;     // modified diagonal
   float* ee = staged ? dd + N : te32;
   for (int j = (threadIdx.x & 31); j < N; j += 32) {
     double d;
     if (g.periodic) d = sc[j * 3 + 0] + sc[(j == 0 ? Nx - 1 : j - 1) * 3 + 2];
     else d = (j < Nx ? sc[j * 3 + 0] : 0.0) + (j > 0 ? sc[(j - 1) * 3 + 2] : 0.0);
-    const double e = (j < N - 1) ? sc[j * 3 + 1] : 0.0;
-    te[j] = e;
     dd[j] = (float)d;
-    ee[j] = (float)e;
+    ee[j] = (float)((j < N - 1) ? sc[j * 3 + 1] : 0.0);
   }
   __syncwarp();
   const double gamma = g.periodic ? -(double)(sc[0] + sc[(Nx - 1) * 3 + 2]) : 0.0;
@@ -1060,27 +1048,21 @@ static __device__ void prec_tri_mode(const DevGeom& g, const PrecSetup& ps, int 
   __syncwarp();
   for (int j = (threadIdx.x & 31); j < N; j += 32) {
     const float m = dd[j], e32 = ee[j];
-    tm[j] = (double)m;
-    tcp[j] = te[j] * (double)m;
     tm32[j] = m;
     te32[j] = e32;
     tcp32[j] = e32 * m;
   }
   __syncwarp();
   if (g.periodic) {
-    auto u64 = [&](int j) -> double { return j == 0 ? gamma : (j == N - 1 ? corner : 0.0); };
-    warp_tridiag<double>(N, u64, te, tm, tcp, false, (const double*)nullptr, 0.0, 0.0, tz);
     auto u32 = [&](int j) -> float { return j == 0 ? (float)gamma : (j == N - 1 ? (float)corner : 0.f); };
     warp_tridiag<float>(N, u32, te32, tm32, tcp32, false, (const float*)nullptr, 0.f, 0.f, tz32);
     if ((threadIdx.x & 31) == 0) {
       const double vl = corner / gamma;
-      ps.tvl64[k] = vl;
-      ps.tfac64[k] = 1.0 / (1.0 + tz[0] + vl * tz[N - 1]);
       ps.tvl32[k] = (float)vl;
       ps.tfac32[k] = 1.f / (1.f + tz32[0] + (float)vl * tz32[N - 1]);
     }
   } else {
-    for (int j = (threadIdx.x & 31); j < N; j += 32) { tz[j] = 0.0; tz32[j] = 0.f; }
+    for (int j = (threadIdx.x & 31); j < N; j += 32) tz32[j] = 0.f;
   }
 }
 

@@ -77,17 +77,16 @@ struct PrecView {
   T* rhat;                 // [ncol][nr] σ-transformed residual
 };
 
-// Set-up data written per stage by the preconditioner set-up kernels (FP64 masters + FP32 copies).
+// Set-up data written per stage by the preconditioner set-up kernels.  The preconditioner is
+// applied in FP32 by both precisions' solves, so its factors are FP32 (the element Schur
+// complements are formed in FP64 before they are rounded).
 struct PrecSetup {
   int nr, nif;
   const double* lam;       // [nr] σ eigenvalues
   double* schur;           // [nr][Nx][3]  S00, S01, S11 of the condensed element matrix
-  PrecView<double> v64;
   PrecView<float> v32;
   // writable aliases of the factor arrays
-  double *Aii64, *Z64, *te64, *tm64, *tcp64, *tz64, *tvl64, *tfac64;
   float *Aii32, *Z32, *te32, *tm32, *tcp32, *tz32, *tvl32, *tfac32;
-  double* scratch;         // [nr][nif] pivots' right-hand terms when the set-up is not staged
 };
 
 struct PcgArgs {
@@ -107,8 +106,7 @@ struct PcgArgs {
   float* s32b;
   double* uh64;           // preconditioned residual on each CTA's halo column, [grid][nrow]
   float* uh32;
-  PrecView<double> pv64;
-  PrecView<float> pv32;
+  PrecView<float> pv32;    // the preconditioner of both precisions' solves
   int precond;            // PREC_SEPARABLE or PREC_JACOBI
   double tol;
   double inner_rtol;
