@@ -123,8 +123,11 @@ static __device__ __forceinline__ bool tile_range(const DevGeom& g, int ex0, int
 // bulk_ok != 0: x is 16-byte aligned and interior tiles are staged by bulk copies.
 // NZC > 0: the layer count is the compile-time constant NZC (= g.Nz), which turns the row
 // arithmetic into constants; NZC = 0 reads it from g.
+// Minimum of 3 CTAs per SM (at most 85 registers) only for FP32, P = 8, four layers, which the
+// compiler otherwise builds with 96 registers (two CTAs per SM); 0 leaves the choice to it.
 template <int P, class T, int NZC>
-__global__ void __launch_bounds__(kThreads) k_apply_tile(DevGeom g, const T* __restrict__ x, T* __restrict__ y,
+__global__ void __launch_bounds__(kThreads, (sizeof(T) == 4 && P == 8 && NZC == 4) ? 3 : 0)
+    k_apply_tile(DevGeom g, const T* __restrict__ x, T* __restrict__ y,
                                                          int E, int bulk_ok) {
   constexpr int Q = P + 1;
   constexpr int QP = TileLayout<P>::QP;
@@ -133,10 +136,8 @@ __global__ void __launch_bounds__(kThreads) k_apply_tile(DevGeom g, const T* __r
   const int nrow = NZC ? NZC * P + 1 : g.nrow, Nz = NZC ? NZC : g.Nz, Nx = g.Nx, ncol = g.ncol;
   const TileLayout<P> L(E, nrow, Nz, (int)sizeof(T));
   unsigned long long* mbar = reinterpret_cast<unsigned long long*>(smem_raw);   // [2]
-  T* Xb[2];
-  Xb[0] = reinterpret_cast<T*>(smem_raw + 16);  // staging buffers (16-byte aligned)
-  Xb[1] = Xb[0] + L.xbuf;
-  T* Ur = Xb[1] + L.xbuf;                   // [en][Nz][Q b][QP a] u_r, then the element contributions
+  T* const Xb0 = reinterpret_cast<T*>(smem_raw + 16);   // staging buffers b = 0, 1 at Xb0 + b·xbuf
+  T* Ur = Xb0 + 2 * L.xbuf;                 // [en][Nz][Q b][QP a] u_r, then the element contributions
   T* Fs = Ur + L.nline;                     // [en][Nz][Q b][QP a] F1
   T* Ys = Fs + L.nline;                     // [en][Nz][Q b][QP a] σ part of the transpose
   T* Gs = Ys + L.nline;                     // [en][Q][4] d, 1/d, ∂xh, ∂xd
@@ -165,18 +166,19 @@ __global__ void __launch_bounds__(kThreads) k_apply_tile(DevGeom g, const T* __r
   // dividing: line 0 of the loop and the step of blockDim.x lines
   const int le0 = threadIdx.x / lpe, lr0 = threadIdx.x - le0 * lpe;
   const int lde = blockDim.x / lpe, ldr = blockDim.x - lde * lpe;
-  unsigned parity[2] = {0u, 0u};     // next phase to wait for, per staging buffer (thread 0)
-  int pending[2] = {0, 0};           // a bulk copy is in flight into the buffer (thread 0)
+  unsigned parity0 = 0u, parity1 = 0u;   // next phase to wait for, per staging buffer (thread 0)
+  int pending0 = 0, pending1 = 0;        // a bulk copy is in flight into the buffer (thread 0)
 
-  // thread 0: issue the copy of `tile` into buffer `b` if it can be bulk-copied
-  auto issue = [&](int tile, int b) {
+  // thread 0: issue the copy of `tile` into buffer `bf` if it can be bulk-copied
+  auto issue = [&](int tile, int bf) {
     const int ex0 = tile * E, ne = min(E, Nx - ex0);
     long long lo;
     int count, shift;
     if (bulk_ok && tile_range<P, T>(g, ex0, ne, &lo, &count, &shift)) {
       fence_proxy_async_smem();
-      bulk_load(Xb[b], x + lo, (unsigned)(count * sizeof(T)), &mbar[b]);
-      pending[b] = 1;
+      bulk_load(Xb0 + bf * L.xbuf, x + lo, (unsigned)(count * sizeof(T)), &mbar[bf]);
+      if (bf) pending1 = 1;
+      else pending0 = 1;
     }
   };
   if (threadIdx.x == 0 && (int)blockIdx.x < ntiles) issue(blockIdx.x, 0);
@@ -196,20 +198,19 @@ __global__ void __launch_bounds__(kThreads) k_apply_tile(DevGeom g, const T* __r
     if (threadIdx.x == 0) {
       // prefetch the next tile into the other buffer, then wait for this one
       if (tile + (int)gridDim.x < ntiles) issue(tile + gridDim.x, b ^ 1);
-      if (pending[b]) {
-        if (!mbar_wait(&mbar[b], parity[b], kCopyTimeoutNs)) s_ok = 0;
-        else {
-          parity[b] ^= 1u;
-          pending[b] = 0;
-        }
+      const int pend = b ? pending1 : pending0;
+      if (pend) {
+        const unsigned par = b ? parity1 : parity0;
+        if (!mbar_wait(&mbar[b], par, kCopyTimeoutNs)) s_ok = 0;
+        else if (b) { parity1 ^= 1u; pending1 = 0; }
+        else { parity0 ^= 1u; pending0 = 0; }
       }
     }
     // ---- stage the tile: nodal values (a warp per column unless bulk-copied), geometry ----
-    T* X;
+    T* X = Xb0 + b * L.xbuf;
     if (bulk) {
-      X = Xb[b] + shift;
+      X += shift;
     } else {
-      X = Xb[b];
       for (int j = warp; j < nc; j += nwarps) {
         int gc = (ex0 - 1) * P + j;
         if (gc < 0) gc = g.periodic ? gc + ncol : -1;
@@ -319,8 +320,9 @@ __global__ void __launch_bounds__(kThreads) k_apply_tile(DevGeom g, const T* __r
     }
     __syncthreads();
     // rows shared between layers: (e, l, a < P) adds to row (l+1)·P
+    const int rpe = (Nz > 1 ? Nz - 1 : 1) * P;   // shared rows per element (the loop is empty for Nz = 1)
     for (int t = threadIdx.x; t < en * (Nz - 1) * P; t += blockDim.x) {
-      const int e = t / ((Nz - 1) * P), rem = t - e * ((Nz - 1) * P);
+      const int e = t / rpe, rem = t - e * rpe;
       const int l = rem / P, a = rem - l * P;
       if (e < e_first) continue;
       Yt[(e * P + a) * nrow + (l + 1) * P] += Rrow[(e * Nz + l) * Q + a];
@@ -356,8 +358,8 @@ __global__ void __launch_bounds__(kThreads) k_apply_tile(DevGeom g, const T* __r
   __syncthreads();
   if (threadIdx.x == 0) {
     if (!s_ok) atomicOr(g.status, ST_TIMEOUT);
-    for (int bb = 0; bb < 2; ++bb)
-      if (pending[bb] && !mbar_wait(&mbar[bb], parity[bb], kCopyTimeoutNs)) atomicOr(g.status, ST_TIMEOUT);
+    if (pending0 && !mbar_wait(&mbar[0], parity0, kCopyTimeoutNs)) atomicOr(g.status, ST_TIMEOUT);
+    if (pending1 && !mbar_wait(&mbar[1], parity1, kCopyTimeoutNs)) atomicOr(g.status, ST_TIMEOUT);
   }
 }
 
