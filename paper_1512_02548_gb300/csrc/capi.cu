@@ -709,7 +709,7 @@ static int mesh_create_impl(const sem_params* pin, const double* x_edges_h, cons
   a.part = D_(o_part); a.part_stride = m->grid;
   a.bar = reinterpret_cast<unsigned int*>(m->pool + o_bar);
   a.rec = m->rec;
-  a.tol = p.tol; a.inner_rtol = 1e-4; a.max_iter = p.max_iter; a.mixed = p.precision == SEM_PREC_MIXED;
+  a.tol = p.tol; a.inner_rtol = 1e-6; a.max_iter = p.max_iter; a.mixed = p.precision == SEM_PREC_MIXED;
   a.r64b = D_(o_r64b); a.r32b = F_(o_r32b);
   a.s64b = D_(o_s64b); a.s32b = F_(o_s32b);
   a.uh64 = D_(o_uh64); a.uh32 = F_(o_uh32);
