@@ -313,7 +313,7 @@ constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;  // 2 s
 // assigned to one instance of a batch.
 struct Team {
   int rank, size;        // this CTA's index in the team, number of CTAs
-  unsigned int* bar;     // {arrive, generation}, zero at launch
+  unsigned int* bar;     // arrival counter (and one spare word), zero at launch
   int* status;           // device status word of the instance
   double* part;          // reduction partials [4 slots][4 values][stride]
   int stride;
@@ -321,11 +321,13 @@ struct Team {
 
 // Returns false (and sets ST_TIMEOUT) if the other CTAs of the team did not arrive in time;
 // the caller must then return without touching another barrier.
-// Scoped atomics of the barrier (PTX memory model): arrivals are acquire-release RMWs on the
-// counter, the last arrival publishes the next generation with a release, and waiters poll it
-// with acquire loads.  The CTA's own writes are ordered before thread 0's arrival by the
-// __syncthreads that precedes it; after the wait, the closing __syncthreads orders the other
-// CTAs' writes before every thread of this CTA.  No separate fences.
+// The arrival counter only grows during a launch: the n-th barrier of the launch is passed once
+// it reaches n·size, so the last arrival's own increment releases the waiters (one round trip
+// to L2 fewer than a separate generation word).  Arrivals are acquire-release RMWs, waiters poll
+// with acquire loads; successive RMWs extend each arrival's release sequence, so a waiter that
+// reads n·size has acquired every CTA's writes before its arrival.  The CTA's own writes are
+// ordered before thread 0's arrival by the __syncthreads that precedes it; after the wait, the
+// closing __syncthreads orders the other CTAs' writes before every thread of this CTA.
 static __device__ __forceinline__ unsigned bar_arrive(unsigned* p) {
   unsigned old;
   asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(old) : "l"(p) : "memory");
@@ -336,29 +338,19 @@ static __device__ __forceinline__ unsigned bar_load(const unsigned* p) {
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
-static __device__ __forceinline__ void bar_reset(unsigned* p) {
-  asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" :: "l"(p) : "memory");
-}
-static __device__ __forceinline__ void bar_publish(unsigned* p) {
-  asm volatile("red.release.gpu.global.add.u32 [%0], 1;" :: "l"(p) : "memory");
-}
 
 static __device__ __forceinline__ bool grid_barrier(const Team& tm, int* s_flag) {
   __syncthreads();
   if (tm.size == 1) return true;
   if (threadIdx.x == 0) {
-    unsigned int* bar = tm.bar;
-    // the generation cannot advance before this CTA arrives, so a plain read suffices
-    const unsigned int gen = bar_load(bar + 1);
-    const unsigned int prev = bar_arrive(bar);
+    const unsigned size = (unsigned)tm.size;
+    const unsigned prev = bar_arrive(tm.bar);
+    const unsigned target = prev - prev % size + size;   // arrivals that complete this barrier
     int ok = 1;
-    if (prev == (unsigned int)tm.size - 1) {
-      bar_reset(bar);
-      bar_publish(bar + 1);
-    } else {
+    if (prev + 1 != target) {
       const unsigned long long t0 = global_ns();
       unsigned int spins = 0;
-      while (bar_load(bar + 1) == gen) {
+      while (bar_load(tm.bar) < target) {
         if ((++spins & 63u) == 0 && global_ns() - t0 > kBarrierTimeoutNs) {
           atomicOr(tm.status, ST_TIMEOUT);
           ok = 0;
@@ -402,14 +394,23 @@ template <int K>
 __device__ __forceinline__ void grid_sum(const Team& tm, int slot, double (&v)[K], double* red) {
   const int lane = threadIdx.x & 31;
   if (threadIdx.x < 32) {
+    // the K partial loads of a lane are independent: one round trip to L2, not K
+    const double* p = tm.part + (size_t)slot * 4 * tm.stride;
+    double s[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) s[k] = 0.0;
+    for (int c = lane; c < tm.size; c += 32) {
+      double t[K];
+#pragma unroll
+      for (int k = 0; k < K; ++k) t[k] = __ldcg(p + (size_t)k * tm.stride + c);
+#pragma unroll
+      for (int k = 0; k < K; ++k) s[k] += t[k];
+    }
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      const double* p = tm.part + ((size_t)slot * 4 + k) * tm.stride;
-      double s = 0.0;
-      for (int c = lane; c < tm.size; c += 32) s += __ldcg(p + c);
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) red[128 + k] = s;
+      for (int o = 16; o > 0; o >>= 1) s[k] += __shfl_xor_sync(0xffffffffu, s[k], o);
+      if (lane == 0) red[128 + k] = s[k];
     }
   }
   __syncthreads();

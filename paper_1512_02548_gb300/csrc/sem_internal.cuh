@@ -98,7 +98,7 @@ struct PcgArgs {
   float *d32, *r32, *z32, *p32a, *p32b, *q32, *edge32;
   double* part;           // reduction partials [4 slots][4 values][max grid]
   int part_stride;        // max grid
-  unsigned int* bar;      // grid barrier {arrive, generation}
+  unsigned int* bar;      // grid barrier: arrival counter (two words), zero at launch
   SolveRecord* rec;
   double* r64b;           // second residual buffer (double-buffered update)
   float* r32b;
