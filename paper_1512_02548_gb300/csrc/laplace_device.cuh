@@ -365,57 +365,51 @@ static __device__ __forceinline__ bool grid_barrier(const Team& tm, int* s_flag)
   return *s_flag != 0;
 }
 
-// Deterministic block sum of K values of type A (all threads get the result).
+// Shared reduction buffer of the persistent kernels: K·blockDim partials of block_sum, then the
+// block sums and the grid sums.
+constexpr int kRedOut = 4 * kThreads, kRedGrid = kRedOut + 8, kRedSize = kRedGrid + 8;
+
+// Deterministic block sum of K ≤ 4 values of type A (all threads get the result).  The values go
+// to shared memory and warp k adds up value k (lane j: threads j, j + 32, …, then a shuffle
+// tree), so the K sums run on different SM sub-partitions.  FP64 adds issue slowly on this
+// GPU; a shuffle tree in every warp would issue about eight times as many.
 template <int K, class A>
 __device__ __forceinline__ void block_sum(A (&v)[K], double* red) {
-#pragma unroll
-  for (int k = 0; k < K; ++k)
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
   A* rr = reinterpret_cast<A*>(red);
-  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  __syncthreads();
-  if (lane == 0)
+  const int nt = blockDim.x, tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+  __syncthreads();                               // earlier readers of the buffer are done
 #pragma unroll
-    for (int k = 0; k < K; ++k) rr[k * 32 + wid] = v[k];
+  for (int k = 0; k < K; ++k) rr[k * nt + tid] = v[k];
   __syncthreads();
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    A s = lane < nw ? rr[k * 32 + lane] : A(0);
+  if (wid < K) {
+    const A* row = rr + wid * nt;
+    A s = A(0);
+    for (int j = lane; j < nt; j += 32) s += row[j];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    v[k] = s;
+    if (lane == 0) red[kRedOut + wid] = (double)s;
   }
   __syncthreads();
+#pragma unroll
+  for (int k = 0; k < K; ++k) v[k] = (A)red[kRedOut + k];
 }
 
-// Sum of K per-CTA partials part[slot][k][cta] over all CTAs, same order in every CTA.
+// Sum of K per-CTA partials part[slot][k][cta] over all CTAs, same order in every CTA; warp k
+// sums value k.
 template <int K>
 __device__ __forceinline__ void grid_sum(const Team& tm, int slot, double (&v)[K], double* red) {
-  const int lane = threadIdx.x & 31;
-  if (threadIdx.x < 32) {
-    // the K partial loads of a lane are independent: one round trip to L2, not K
-    const double* p = tm.part + (size_t)slot * 4 * tm.stride;
-    double s[K];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (wid < K) {
+    const double* p = tm.part + ((size_t)slot * 4 + wid) * tm.stride;
+    double s = 0.0;
+    for (int c = lane; c < tm.size; c += 32) s += __ldcg(p + c);
 #pragma unroll
-    for (int k = 0; k < K; ++k) s[k] = 0.0;
-    for (int c = lane; c < tm.size; c += 32) {
-      double t[K];
-#pragma unroll
-      for (int k = 0; k < K; ++k) t[k] = __ldcg(p + (size_t)k * tm.stride + c);
-#pragma unroll
-      for (int k = 0; k < K; ++k) s[k] += t[k];
-    }
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s[k] += __shfl_xor_sync(0xffffffffu, s[k], o);
-      if (lane == 0) red[128 + k] = s[k];
-    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) red[kRedGrid + wid] = s;
   }
   __syncthreads();
 #pragma unroll
-  for (int k = 0; k < K; ++k) v[k] = red[128 + k];
+  for (int k = 0; k < K; ++k) v[k] = red[kRedGrid + k];
   __syncthreads();
 }
 
@@ -658,7 +652,7 @@ __device__ int cg_solve(const DevGeom& g, Smem<P, T>& s, const Range& R, const T
   cg_update<P, T, TP>(g, s, R, tm, pv, PA.precond, V, cur, false, true, T(0), T(0));
   if (!finish_precondition<P, T, TP>(g, s, R, tm, PA, pv, V, s_flag)) return -1;
   int k = 0;
-  double gamma_prev = 1.0, alpha_prev = 1.0, rr = 0.0;
+  double inv_gamma_prev = 1.0, inv_alpha_prev = 1.0, rr = 0.0;   // 1/γ and 1/α of the last iteration
   while (true) {
     // w = A u and the three inner products (u on owned columns and the halo column)
     const T* rc = V.r[cur];
@@ -694,12 +688,14 @@ __device__ int cg_solve(const DevGeom& g, Smem<P, T>& s, const Range& R, const T
       if (!(rr == rr) || isinf(rr) || !(sums[1] == sums[1])) { atomicOr(g.status, ST_NONFINITE); stop = 1; }
       else if (rr <= target || k >= max_it) stop = 1;
       if (!stop) {
+        // α = γ/(δ − βγ/α_prev): the two divisions of the next iteration's β and γ/α are taken
+        // beside this one (1/γ, and 1/α = den/γ), not after it
         const double gam = sums[0], del = sums[1];
-        double alpha, beta;
-        if (k == 0) { beta = 0.0; alpha = gam / del; }
-        else { beta = gam / gamma_prev; alpha = gam / (del - beta * gam / alpha_prev); }
-        gamma_prev = gam;
-        alpha_prev = alpha;
+        const double beta = k == 0 ? 0.0 : gam * inv_gamma_prev;
+        const double den = k == 0 ? del : del - beta * gam * inv_alpha_prev;
+        const double alpha = gam / den;
+        inv_gamma_prev = 1.0 / gam;
+        inv_alpha_prev = den * inv_gamma_prev;
         s_scal[0] = (T)alpha;
         s_scal[1] = (T)beta;
       }
@@ -890,7 +886,7 @@ __device__ bool solve_body(const DevGeom& g, const PcgArgs& A, const Team& tm, u
 template <int P, bool MIXED>
 __global__ void __launch_bounds__(kThreads) k_pcg(DevGeom g, PcgArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double red[160];
+  __shared__ double red[kRedSize];
   __shared__ int s_flag;
   const Team tm{(int)blockIdx.x, (int)gridDim.x, A.bar, g.status, A.part, A.part_stride};
   solve_body<P, MIXED>(g, A, tm, smem_raw, red, &s_flag);
@@ -1172,7 +1168,7 @@ __device__ void stage_body(Instance& I, const Team& tm, int stage, int step, uns
 template <int P, bool MIXED, bool WIDE>
 __global__ void __launch_bounds__(kThreads, WIDE ? 2 : 1) k_stage(StageArgs B) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double red[160];
+  __shared__ double red[kRedSize];
   __shared__ int s_flag;
   __shared__ __align__(16) double sh[kStageWarps][kSurfWarpScratch];
   __shared__ double Kx[(P + 1) * (P + 1)];
