@@ -160,6 +160,11 @@ struct sem_mesh {
   double *ke = nullptr, *kp = nullptr, *ae = nullptr, *ap = nullptr, *se = nullptr, *sp = nullptr;
   double *eta_dev = nullptr, *phis_dev = nullptr;
   double *s1e = nullptr, *s1p = nullptr;   // second stage-input pair of the fused RK stage
+  // stage potentials kept for the next stages' initial guesses, and the trajectory they belong
+  // to (the state buffers and dt of the last fused RK call; hist_dt = 0: none)
+  double *Phi1 = nullptr, *Phi3 = nullptr;
+  double hist_dt = 0.0;
+  const double *hist_eta = nullptr, *hist_phis = nullptr;
   // fused-stage launch of this mesh alone: device descriptor, CTA map, barrier pair
   Instance* inst_d = nullptr;
   int* cta_inst_d = nullptr;
@@ -221,6 +226,7 @@ int status_error(int st) {
 // After a failed step the mesh's warm-start potential may hold non-finite values; the next
 // solve on this mesh starts from zero instead.
 cudaError_t reset_warm_start(sem_mesh* m, cudaStream_t s) {
+  m->hist_dt = 0.0;   // the stage potentials kept for initial guesses may be from a failed step
   return cudaMemsetAsync(m->Phi, 0, sizeof(double) * (size_t)m->n, s);
 }
 
@@ -284,6 +290,14 @@ int do_rhs(sem_mesh* m, const double* eta, const double* phis, double time, doub
   return SEM_OK;
 }
 
+// After a fused RK call: the next call continues the trajectory if it steps the same state
+// buffers with the same dt (then its stage 2 may extrapolate from the last stage-3 potential).
+void set_history(sem_mesh* m, const double* eta, const double* phis, double dt) {
+  m->hist_dt = dt;
+  m->hist_eta = eta;
+  m->hist_phis = phis;
+}
+
 Instance make_instance(sem_mesh* m, double* eta, double* phis, double tstart, double dt, int team0,
                        int nteam) {
   Instance I{};
@@ -296,6 +310,8 @@ Instance make_instance(sem_mesh* m, double* eta, double* phis, double tstart, do
   I.s0e = m->se; I.s0p = m->sp; I.s1e = m->s1e; I.s1p = m->s1p;
   I.ke = m->ke; I.kp = m->kp; I.ae = m->ae; I.ap = m->ap;
   I.wt = m->wt; I.etax = m->etax; I.phisx = m->phisx; I.R = m->R; I.scr = m->scr;
+  I.P1 = m->Phi1; I.P3 = m->Phi3;
+  I.hist = (m->hist_dt == dt && m->hist_eta == eta && m->hist_phis == phis) ? 1 : 0;
   I.tstart = tstart; I.dt = dt;
   I.tau = m->p.relax_tau > 0.0 ? m->p.relax_tau : dt;
   I.team0 = team0; I.nteam = nteam;
@@ -326,6 +342,7 @@ int do_rk4_fused(sem_mesh* m, double* eta, double* phis, double t0, double dt, i
         m->events.emplace_back(e0, e1);
       }
     }
+  if (nsteps > 0) set_history(m, eta, phis, dt);
   return SEM_OK;
 }
 
@@ -644,7 +661,8 @@ static int mesh_create_impl(const sem_params* pin, const double* x_edges_h, cons
                o_ke = cv.take<double>(ncol), o_kp = cv.take<double>(ncol), o_ae = cv.take<double>(ncol),
                o_ap = cv.take<double>(ncol), o_se = cv.take<double>(ncol), o_sp = cv.take<double>(ncol),
                o_etad = cv.take<double>(ncol), o_phisd = cv.take<double>(ncol),
-               o_s1e = cv.take<double>(ncol), o_s1p = cv.take<double>(ncol);
+               o_s1e = cv.take<double>(ncol), o_s1p = cv.take<double>(ncol),
+               o_P1 = cv.take<double>(n), o_P3 = cv.take<double>(n);
   const size_t o_inst = cv.take<Instance>(1), o_ctai = cv.take<int>((size_t)m->grid), o_sbar = cv.take<unsigned>(4);
   // surface tables
   const size_t o_tD = cv.take<double>(Q * Q), o_tMD = cv.take<double>(Q * Q), o_tB = cv.take<double>((size_t)Q * Qf),
@@ -727,6 +745,7 @@ static int mesh_create_impl(const sem_params* pin, const double* x_edges_h, cons
   m->ke = D_(o_ke); m->kp = D_(o_kp); m->ae = D_(o_ae); m->ap = D_(o_ap); m->se = D_(o_se); m->sp = D_(o_sp);
   m->eta_dev = D_(o_etad); m->phis_dev = D_(o_phisd);
   m->s1e = D_(o_s1e); m->s1p = D_(o_s1p);
+  m->Phi1 = D_(o_P1); m->Phi3 = D_(o_P3);
   m->inst_d = reinterpret_cast<Instance*>(m->pool + o_inst);
   m->cta_inst_d = reinterpret_cast<int*>(m->pool + o_ctai);
   m->stage_bars = reinterpret_cast<unsigned int*>(m->pool + o_sbar);
@@ -1084,6 +1103,8 @@ int sem_batch_rk4_step(sem_batch* b, double* const* eta_d, double* const* phis_d
         const StageArgs a{L.inst_d, L.cta_d, L.bars_d, stage, step};
         CUDA_TRY(launch_stage(L.P, L.mixed, 1, a, L.grid, L.smem, s));
       }
+  if (nsteps > 0)
+    for (int i = 0; i < n; ++i) set_history(b->meshes[i], eta_d[i], phis_d[i], dt_h[i]);
   int rc = batch_status(b, s);
   if (t_h)
     for (int i = 0; i < n; ++i) t_h[i] += nsteps * dt_h[i];

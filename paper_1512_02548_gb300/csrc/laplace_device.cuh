@@ -1096,6 +1096,16 @@ __device__ void stage_body(Instance& I, const Team& tm, int stage, int step, uns
 
   // σ-geometry of the owned element columns
   for (int q = threadIdx.x; q < ne * Q; q += blockDim.x) geometry_item<P>(g, ein, R.e0 * Q + q);
+  // Initial guess of the stage's Laplace solve.  x holds the previous stage's potential; the
+  // stage states of RK4 lie on lines from y_n, so linear extrapolation in the stage time turns the
+  // first-order starts of stages 2 and 4 into second-order ones: stage 2 (y_n + ½dt k₁) from
+  // 2Φ₁ − Φ₃ of the last step, stage 4 (y_n + dt k₃) from 2Φ₃ − Φ₁.  Owned nodes only; the
+  // barriers below order these writes before any neighbour reads them.
+  if (stage == 4 || (stage == 2 && (step > 0 || I.hist))) {
+    const double* Pold = stage == 2 ? I.P3 : I.P1;
+    double* x = I.pa.x;
+    for (int i = R.c0 * g.nrow + threadIdx.x; i < R.c1 * g.nrow; i += blockDim.x) x[i] = fma(2.0, x[i], -Pold[i]);
+  }
   __syncthreads();
   // preconditioner: condensation of the owned elements for every mode, then interface pivots
   for (int ex = R.e0; ex < R.e1; ++ex) {
@@ -1115,6 +1125,10 @@ __device__ void stage_body(Instance& I, const Team& tm, int stage, int step, uns
   __syncthreads();
   if (!solve_body<P, MIXED>(g, I.pa, tm, smem_raw, red, s_flag)) return;
   if (stage == 0) return;
+  if (stage == 1 || stage == 3) {              // kept for the initial guesses of stages 4 and 2
+    double* Pk = stage == 1 ? I.P1 : I.P3;
+    for (int i = R.c0 * g.nrow + threadIdx.x; i < R.c1 * g.nrow; i += blockDim.x) Pk[i] = I.pa.x[i];
+  }
   // w̃ on owned columns; element S_x of η and φ̃; condensation of M'
   for (int col = R.c0 + warp; col < R.c1; col += nw) wsurf_column(t, I.pa.x, ein, I.wt, col, lane);
   for (int q = threadIdx.x; q < 2 * ne * Q; q += blockDim.x) {

@@ -156,10 +156,11 @@ struct Instance {
   double *s1e, *s1p;
   double *ke, *kp, *ae, *ap;
   double *wt, *etax, *phisx, *R, *scr;
+  double *P1, *P3;       // potentials of stage 1 of this step and of stage 3 of the last step
   double tstart, dt, tau;
   int team0, nteam;      // first CTA and number of CTAs of this instance's team
   int relax;
-  int pad;
+  int hist;              // P3 belongs to the step before this call's first step (same trajectory)
 };
 
 struct StageArgs {
