@@ -162,7 +162,7 @@ struct sem_mesh {
   double *s1e = nullptr, *s1p = nullptr;   // second stage-input pair of the fused RK stage
   // stage potentials kept for the next stages' initial guesses, and the trajectory they belong
   // to (the state buffers and dt of the last fused RK call; hist_dt = 0: none)
-  double *Phi1 = nullptr, *Phi3 = nullptr;
+  double *Phi1 = nullptr, *Phi2 = nullptr, *Phi3 = nullptr, *D32 = nullptr;
   double hist_dt = 0.0;
   const double *hist_eta = nullptr, *hist_phis = nullptr;
   // fused-stage launch of this mesh alone: device descriptor, CTA map, barrier pair
@@ -291,7 +291,8 @@ int do_rhs(sem_mesh* m, const double* eta, const double* phis, double time, doub
 }
 
 // After a fused RK call: the next call continues the trajectory if it steps the same state
-// buffers with the same dt (then its stage 2 may extrapolate from the last stage-3 potential).
+// buffers with the same dt (then its stages 2 and 3 may extrapolate from the last step's stage
+// potentials).
 void set_history(sem_mesh* m, const double* eta, const double* phis, double dt) {
   m->hist_dt = dt;
   m->hist_eta = eta;
@@ -310,7 +311,7 @@ Instance make_instance(sem_mesh* m, double* eta, double* phis, double tstart, do
   I.s0e = m->se; I.s0p = m->sp; I.s1e = m->s1e; I.s1p = m->s1p;
   I.ke = m->ke; I.kp = m->kp; I.ae = m->ae; I.ap = m->ap;
   I.wt = m->wt; I.etax = m->etax; I.phisx = m->phisx; I.R = m->R; I.scr = m->scr;
-  I.P1 = m->Phi1; I.P3 = m->Phi3;
+  I.P1 = m->Phi1; I.P2 = m->Phi2; I.P3 = m->Phi3; I.D32 = m->D32;
   I.hist = (m->hist_dt == dt && m->hist_eta == eta && m->hist_phis == phis) ? 1 : 0;
   I.tstart = tstart; I.dt = dt;
   I.tau = m->p.relax_tau > 0.0 ? m->p.relax_tau : dt;
@@ -662,7 +663,8 @@ static int mesh_create_impl(const sem_params* pin, const double* x_edges_h, cons
                o_ap = cv.take<double>(ncol), o_se = cv.take<double>(ncol), o_sp = cv.take<double>(ncol),
                o_etad = cv.take<double>(ncol), o_phisd = cv.take<double>(ncol),
                o_s1e = cv.take<double>(ncol), o_s1p = cv.take<double>(ncol),
-               o_P1 = cv.take<double>(n), o_P3 = cv.take<double>(n);
+               o_P1 = cv.take<double>(n), o_P2 = cv.take<double>(n), o_P3 = cv.take<double>(n),
+               o_D32 = cv.take<double>(n);
   const size_t o_inst = cv.take<Instance>(1), o_ctai = cv.take<int>((size_t)m->grid), o_sbar = cv.take<unsigned>(4);
   // surface tables
   const size_t o_tD = cv.take<double>(Q * Q), o_tMD = cv.take<double>(Q * Q), o_tB = cv.take<double>((size_t)Q * Qf),
@@ -745,7 +747,7 @@ static int mesh_create_impl(const sem_params* pin, const double* x_edges_h, cons
   m->ke = D_(o_ke); m->kp = D_(o_kp); m->ae = D_(o_ae); m->ap = D_(o_ap); m->se = D_(o_se); m->sp = D_(o_sp);
   m->eta_dev = D_(o_etad); m->phis_dev = D_(o_phisd);
   m->s1e = D_(o_s1e); m->s1p = D_(o_s1p);
-  m->Phi1 = D_(o_P1); m->Phi3 = D_(o_P3);
+  m->Phi1 = D_(o_P1); m->Phi2 = D_(o_P2); m->Phi3 = D_(o_P3); m->D32 = D_(o_D32);
   m->inst_d = reinterpret_cast<Instance*>(m->pool + o_inst);
   m->cta_inst_d = reinterpret_cast<int*>(m->pool + o_ctai);
   m->stage_bars = reinterpret_cast<unsigned int*>(m->pool + o_sbar);

@@ -1099,12 +1099,18 @@ __device__ void stage_body(Instance& I, const Team& tm, int stage, int step, uns
   // Initial guess of the stage's Laplace solve.  x holds the previous stage's potential; the
   // stage states of RK4 lie on lines from y_n, so linear extrapolation in the stage time turns the
   // first-order starts of stages 2 and 4 into second-order ones: stage 2 (y_n + ½dt k₁) from
-  // 2Φ₁ − Φ₃ of the last step, stage 4 (y_n + dt k₃) from 2Φ₃ − Φ₁.  Owned nodes only; the
-  // barriers below order these writes before any neighbour reads them.
-  if (stage == 4 || (stage == 2 && (step > 0 || I.hist))) {
+  // 2Φ₁ − Φ₃ of the last step, stage 4 (y_n + dt k₃) from 2Φ₃ − Φ₁.  Stage 3 (y_n + ½dt k₂)
+  // differs from stage 2 by ¼dt²k₁' + …, which changes little from step to step: Φ₂ + (Φ₃ − Φ₂)
+  // of the last step.  Owned nodes only; the barriers below order these writes before any
+  // neighbour reads them.
+  const bool cont = step > 0 || I.hist;        // the last step belongs to this trajectory
+  if (stage == 4 || (stage == 2 && cont)) {
     const double* Pold = stage == 2 ? I.P3 : I.P1;
     double* x = I.pa.x;
     for (int i = R.c0 * g.nrow + threadIdx.x; i < R.c1 * g.nrow; i += blockDim.x) x[i] = fma(2.0, x[i], -Pold[i]);
+  } else if (stage == 3 && cont) {
+    double* x = I.pa.x;
+    for (int i = R.c0 * g.nrow + threadIdx.x; i < R.c1 * g.nrow; i += blockDim.x) x[i] += I.D32[i];
   }
   __syncthreads();
   // preconditioner: condensation of the owned elements for every mode, then interface pivots
@@ -1125,9 +1131,17 @@ __device__ void stage_body(Instance& I, const Team& tm, int stage, int step, uns
   __syncthreads();
   if (!solve_body<P, MIXED>(g, I.pa, tm, smem_raw, red, s_flag)) return;
   if (stage == 0) return;
-  if (stage == 1 || stage == 3) {              // kept for the initial guesses of stages 4 and 2
-    double* Pk = stage == 1 ? I.P1 : I.P3;
-    for (int i = R.c0 * g.nrow + threadIdx.x; i < R.c1 * g.nrow; i += blockDim.x) Pk[i] = I.pa.x[i];
+  // kept for the initial guesses of the next stages
+  if (stage == 3) {
+    for (int i = R.c0 * g.nrow + threadIdx.x; i < R.c1 * g.nrow; i += blockDim.x) {
+      const double v = I.pa.x[i];
+      I.D32[i] = v - I.P2[i];
+      I.P3[i] = v;
+    }
+  } else {
+    double* Pk = stage == 1 ? I.P1 : (stage == 2 ? I.P2 : nullptr);
+    if (Pk)
+      for (int i = R.c0 * g.nrow + threadIdx.x; i < R.c1 * g.nrow; i += blockDim.x) Pk[i] = I.pa.x[i];
   }
   // w̃ on owned columns; element S_x of η and φ̃; condensation of M'
   for (int col = R.c0 + warp; col < R.c1; col += nw) wsurf_column(t, I.pa.x, ein, I.wt, col, lane);

@@ -156,7 +156,8 @@ struct Instance {
   double *s1e, *s1p;
   double *ke, *kp, *ae, *ap;
   double *wt, *etax, *phisx, *R, *scr;
-  double *P1, *P3;       // potentials of stage 1 of this step and of stage 3 of the last step
+  double *P1, *P2, *P3;  // stage potentials: P1, P2 of this step, P3 of the last stage 3
+  double *D32;           // Φ₃ − Φ₂ of the last step
   double tstart, dt, tau;
   int team0, nteam;      // first CTA and number of CTAs of this instance's team
   int relax;
