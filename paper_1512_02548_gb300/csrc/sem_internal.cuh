@@ -243,6 +243,10 @@ __device__ __forceinline__ float fmx(float a, float b, float c) { return fmaf(a,
 // chunk, the lanes scan the composed maps with shuffles, then each lane replays its chunk.
 // `gfun(j)` returns the right-hand side; `out` (N values, global or shared) receives x.
 // Must be called by all 32 lanes of a warp.
+// Chunks of at most kTridiagRegs values per lane (N ≤ 32·kTridiagRegs) are kept in registers
+// between the passes: the right-hand side and the factors are read once, y never leaves the lane.
+constexpr int kTridiagRegs = 4;
+
 template <class T, class GFun>
 __device__ __forceinline__ void warp_tridiag(int N, GFun gfun, const T* te, const T* tm, const T* tcp,
                                              bool periodic, const T* tz, T tvl, T tfac, T* out) {
@@ -250,6 +254,65 @@ __device__ __forceinline__ void warp_tridiag(int N, GFun gfun, const T* te, cons
   const int c = (N + 31) / 32;
   const int j0 = min(N, lane * c), j1 = min(N, j0 + c);
   const unsigned full = 0xffffffffu;
+  if (c <= kTridiagRegs) {
+    // the same operations in the same order as below, on register copies of the chunk
+    T al[kTridiagRegs], gm[kTridiagRegs], cp[kTridiagRegs], v[kTridiagRegs];
+#pragma unroll
+    for (int q = 0; q < kTridiagRegs; ++q) {
+      const int j = j0 + q;
+      if (j < j1) {
+        const T m = tm[j];
+        al[q] = j > 0 ? -te[j - 1] * m : T(0);
+        gm[q] = gfun(j) * m;
+        cp[q] = tcp[j];
+      }
+    }
+    T A = T(1), B = T(0);
+#pragma unroll
+    for (int q = 0; q < kTridiagRegs; ++q)
+      if (j0 + q < j1) { B = fmx(al[q], B, gm[q]); A = al[q] * A; }
+    for (int o = 1; o < 32; o <<= 1) {
+      const T Ap = __shfl_up_sync(full, A, o), Bp = __shfl_up_sync(full, B, o);
+      if (lane >= o) { B = fmx(A, Bp, B); A = A * Ap; }
+    }
+    T y = __shfl_up_sync(full, B, 1);
+    if (lane == 0) y = T(0);
+#pragma unroll
+    for (int q = 0; q < kTridiagRegs; ++q)
+      if (j0 + q < j1) { y = fmx(al[q], y, gm[q]); v[q] = y; }
+    A = T(1); B = T(0);
+#pragma unroll
+    for (int q = kTridiagRegs - 1; q >= 0; --q)
+      if (j0 + q < j1) { const T ga = -cp[q]; B = fmx(ga, B, v[q]); A = ga * A; }
+    for (int o = 1; o < 32; o <<= 1) {
+      const T An = __shfl_down_sync(full, A, o), Bn = __shfl_down_sync(full, B, o);
+      if (lane + o < 32) { B = fmx(A, Bn, B); A = A * An; }
+    }
+    T x = __shfl_down_sync(full, B, 1);
+    if (lane == 31) x = T(0);
+#pragma unroll
+    for (int q = kTridiagRegs - 1; q >= 0; --q)
+      if (j0 + q < j1) { x = fmx(-cp[q], x, v[q]); v[q] = x; }
+    if (periodic) {
+      // x_0 is on lane 0, x_{N−1} on the lane whose chunk ends at N
+      const T x0 = __shfl_sync(full, v[0], 0);
+      const int ln = (N - 1) / c;
+      T xl = v[0];
+#pragma unroll
+      for (int q = 1; q < kTridiagRegs; ++q)
+        if (j0 + q == N - 1) xl = v[q];
+      const T xN = __shfl_sync(full, xl, ln);
+      const T cc = (x0 + tvl * xN) * tfac;
+#pragma unroll
+      for (int q = 0; q < kTridiagRegs; ++q)
+        if (j0 + q < j1) v[q] = fmx(-cc, tz[j0 + q], v[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < kTridiagRegs; ++q)
+      if (j0 + q < j1) out[j0 + q] = v[q];
+    __syncwarp();
+    return;
+  }
   // forward: y_j = α_j y_{j−1} + β_j, α_j = −e_{j−1} m_j, β_j = g_j m_j
   T A = T(1), B = T(0);
   for (int j = j0; j < j1; ++j) {
