@@ -468,6 +468,22 @@ static __device__ __forceinline__ bool is_halo_col(const DevGeom& g, const Range
   return a == g.P && ex == R.e1 - 1 && !owns_local_col(g, ex, g.P);
 }
 
+// Σ_j a[j·sa] b[j] over j < n with four partial sums (j mod 4), added pairwise at the end: four
+// short dependent chains instead of one of length n.
+template <class TP>
+__device__ __forceinline__ TP dot4(const TP* a, int sa, const TP* b, int n) {
+  TP v0 = TP(0), v1 = TP(0), v2 = TP(0), v3 = TP(0);
+  int j = 0;
+  for (; j + 4 <= n; j += 4) {
+    v0 = fmx(a[j * sa], b[j], v0);
+    v1 = fmx(a[(j + 1) * sa], b[j + 1], v1);
+    v2 = fmx(a[(j + 2) * sa], b[j + 2], v2);
+    v3 = fmx(a[(j + 3) * sa], b[j + 3], v3);
+  }
+  for (; j < n; ++j) v0 = fmx(a[j * sa], b[j], v0);
+  return (v0 + v1) + (v2 + v3);
+}
+
 // Update of the Chronopoulos–Gear recurrences on owned nodes (and, for r, on the halo column),
 // then the first part of u = M⁻¹ r:
 //   s ← w + β s,  r ← r − α s,  p ← u + β p,  x ← x + α p      (first iteration: s ← w, p ← u).
@@ -527,8 +543,7 @@ __device__ void cg_update(const DevGeom& g, Smem<P, T>& s, const Range& R, const
       const int e = t / qn, rem = t - e * qn;
       const int a = rem / nr, k = rem - a * nr, ex = ex0 + e;
       const TP* Xa = X + e * qn + a * nr;
-      TP v = 0;
-      for (int j = 0; j < nr; ++j) v = fmx(pv.S[j * nr + k], Xa[j], v);
+      const TP v = dot4<TP>(pv.S + k, nr, Xa, nr);
       RH[t] = v;
       if (owns_local_col(g, ex, a)) pv.rhat[(size_t)col_of(g, ex, a) * nr + k] = v;
     }
@@ -613,8 +628,7 @@ __device__ void phase_backsub(const DevGeom& g, Smem<P, T>& s, const Range& R, c
       if (!own && !halo) continue;
       const TP* Za = ZH + e * qn + a * nr;
       const TP* Sj = pv.S + j * nr;
-      TP v = 0;
-      for (int k = 0; k < nr; ++k) v = fmx(Sj[k], Za[k], v);
+      const TP v = dot4<TP>(Sj, 1, Za, nr);
       if (own) V.u[(size_t)col_of(g, ex, a) * nrow + j] = (T)v;
       else V.uh[(size_t)tm.rank * nrow + j] = (T)v;
     }
