@@ -33,6 +33,9 @@
  * of CTAs of the persistent Krylov kernel and of a mesh's fused stage (default: all
  * co-resident); SEM_FUSED_STAGE=0 makes sem_rk4_step run the multi-kernel path instead of one
  * fused launch per RK stage.  Read by sem_laplace_apply: SEM_APPLY_KERNEL=column (see there).
+ * Read by sem_batch_create: SEM_BATCH_WIDE=1 (or 0) makes every (order, precision) group of the
+ * batch use the two-CTAs-per-SM build of the fused stage (or the one-CTA-per-SM build); by
+ * default groups of more than 8 instances use the former.
  *
  * Device memory.  Each mesh and batch owns one device block, taken at creation from a
  * per-device cache of blocks freed by earlier meshes and batches (or from cudaMalloc) and given

@@ -182,7 +182,7 @@ struct sem_mesh {
 // A batch: instances grouped by (order, precision) and, within a group, into launches of at
 // most the co-resident capacity; each instance gets a team of CTAs sized to its work.
 struct BatchLaunch {
-  int P = 0, mixed = 0;
+  int P = 0, mixed = 0, wide = 1;
   std::vector<int> members;          // mesh indices
   std::vector<int> team0, nteam;
   int grid = 0;
@@ -943,6 +943,9 @@ int sem_rk4_step_host(sem_mesh* m, double* eta_h, double* phis_h, double* t, dou
   return rc;
 }
 
+// Groups of at most this many instances use the one-CTA-per-SM stage build.
+constexpr int kBatchNarrowMax = 8;
+
 int sem_batch_create(sem_mesh* const* meshes, int count, sem_batch** out) {
   if (!out) return fail(SEM_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
@@ -975,7 +978,12 @@ int sem_batch_create(sem_mesh* const* meshes, int count, sem_batch** out) {
     size_t smem = 0;
     for (int i : grp.second) smem = std::max(smem, meshes[i]->stage_smem);
     int per_sm = 0;
-    cudaError_t e = stage_occupancy(grp.first.first, grp.first.second, 1, smem, &per_sm);
+    // Build of the stage kernel: two CTAs per SM (128 registers) for groups of many instances,
+    // where more co-resident teams pay; one CTA per SM with the full register file (the
+    // single-mesh build, faster per CTA) for a few instances.  SEM_BATCH_WIDE=0/1 forces either.
+    const char* wenv = std::getenv("SEM_BATCH_WIDE");
+    const int wide = wenv ? (std::atoi(wenv) != 0) : (grp.second.size() > (size_t)kBatchNarrowMax ? 1 : 0);
+    cudaError_t e = stage_occupancy(grp.first.first, grp.first.second, wide, smem, &per_sm);
     if (e != cudaSuccess || per_sm < 1) { delete b; return fail(SEM_ERR_CUDA, "fused stage kernel does not fit"); }
     const int cap = per_sm * sms;
     // split into launches of at most `cap` instances, then share the CTAs by work
@@ -983,6 +991,7 @@ int sem_batch_create(sem_mesh* const* meshes, int count, sem_batch** out) {
       BatchLaunch L;
       L.P = grp.first.first;
       L.mixed = grp.first.second;
+      L.wide = wide;
       L.smem = smem;
       const size_t last = std::min(grp.second.size(), first + (size_t)cap);
       L.members.assign(grp.second.begin() + first, grp.second.begin() + last);
@@ -1103,7 +1112,7 @@ int sem_batch_rk4_step(sem_batch* b, double* const* eta_d, double* const* phis_d
       for (auto& L : b->launches) {
         CUDA_TRY(cudaMemsetAsync(L.bars_d, 0, 2 * sizeof(unsigned int) * L.members.size(), s));
         const StageArgs a{L.inst_d, L.cta_d, L.bars_d, stage, step};
-        CUDA_TRY(launch_stage(L.P, L.mixed, 1, a, L.grid, L.smem, s));
+        CUDA_TRY(launch_stage(L.P, L.mixed, L.wide, a, L.grid, L.smem, s));
       }
   if (nsteps > 0)
     for (int i = 0; i < n; ++i) set_history(b->meshes[i], eta_d[i], phis_d[i], dt_h[i]);
@@ -1134,7 +1143,7 @@ int sem_batch_laplace_solve(sem_batch* b, const double* const* eta_d, const doub
   for (auto& L : b->launches) {
     CUDA_TRY(cudaMemsetAsync(L.bars_d, 0, 2 * sizeof(unsigned int) * L.members.size(), s));
     const StageArgs a{L.inst_d, L.cta_d, L.bars_d, 0, 0};
-    CUDA_TRY(launch_stage(L.P, L.mixed, 1, a, L.grid, L.smem, s));
+    CUDA_TRY(launch_stage(L.P, L.mixed, L.wide, a, L.grid, L.smem, s));
   }
   return batch_status(b, s);
 }

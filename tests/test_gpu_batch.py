@@ -4,7 +4,8 @@
   the multi-kernel path (SEM_FUSED_STAGE=0) and as the oracle.
 * A batch of uneven instances (different orders, element counts, layers, ends, relaxation,
   precision) stepped together equals each instance stepped alone, within the stated
-  tolerances (1e-10 FP64, 1e-8 mixed), and an FP64 member equals the oracle.
+  tolerances (1e-10 FP64, 1e-8 mixed), and an FP64 member equals the oracle; with either build of
+  the stage kernel for the batch's groups (SEM_BATCH_WIDE) and the default choice by group size.
 """
 import math
 import os
@@ -90,7 +91,22 @@ def _uneven_instances():
     return cases
 
 
-def test_batch_equals_instances_alone():
+@pytest.fixture(params=["default", "0", "1"], ids=["build-by-size", "one-cta-per-sm", "two-ctas-per-sm"])
+def batch_build(request):
+    """SEM_BATCH_WIDE for the batches created in the test (read by sem_batch_create)."""
+    old = os.environ.get("SEM_BATCH_WIDE")
+    if request.param == "default":
+        os.environ.pop("SEM_BATCH_WIDE", None)
+    else:
+        os.environ["SEM_BATCH_WIDE"] = request.param
+    yield request.param
+    if old is None:
+        os.environ.pop("SEM_BATCH_WIDE", None)
+    else:
+        os.environ["SEM_BATCH_WIDE"] = old
+
+
+def test_batch_equals_instances_alone(batch_build):
     cases = _uneven_instances()
     oms = [osem.mesh_for(wl) for wl, _ in cases]
     states = [state(wl, om, i) for i, ((wl, _), om) in enumerate(zip(cases, oms))]
