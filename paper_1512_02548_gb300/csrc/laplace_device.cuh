@@ -568,12 +568,14 @@ __device__ void cg_update(const DevGeom& g, Smem<P, T>& s, const Range& R, const
   }
 }
 
-// Interface solve per σ-mode: one warp (warp 0 of a CTA) per mode, modes spread over CTAs;
+// Interface solve per σ-mode: one warp (warp 0 of a CTA) per mode, or the whole CTA for long
+// systems, modes spread over CTAs;
 // g_j = gL_j + gR_{j−1} assembled on the fly, then the warp-parallel tridiagonal solve.
 template <class T>
 __device__ void phase_interface(const DevGeom& g, const PrecView<T>& pv, const Team& tm) {
-  if (threadIdx.x >= 32) return;
   const int N = pv.nif, Nx = g.Nx;
+  const bool whole_cta = N > 32 * kTridiagRegs;   // long systems: all warps of the CTA per mode
+  if (!whole_cta && threadIdx.x >= 32) return;
   for (int k = tm.rank; k < pv.nr; k += tm.size) {
     const T* gl = pv.gL + (size_t)k * Nx;
     const T* gr = pv.gR + (size_t)k * Nx;
@@ -581,9 +583,14 @@ __device__ void phase_interface(const DevGeom& g, const PrecView<T>& pv, const T
       if (g.periodic) return ldcg(gl + j) + ldcg(gr + (j == 0 ? Nx - 1 : j - 1));
       return (j < Nx ? ldcg(gl + j) : T(0)) + (j > 0 ? ldcg(gr + j - 1) : T(0));
     };
-    warp_tridiag<T>(N, gfun, pv.te + (size_t)k * N, pv.tm + (size_t)k * N, pv.tcp + (size_t)k * N,
-                    g.periodic != 0, pv.tz + (size_t)k * N, g.periodic ? pv.tvl[k] : T(0),
-                    g.periodic ? pv.tfac[k] : T(0), pv.zb + (size_t)k * N);
+    if (whole_cta)
+      cta_tridiag<T>(N, gfun, pv.te + (size_t)k * N, pv.tm + (size_t)k * N, pv.tcp + (size_t)k * N,
+                     g.periodic != 0, pv.tz + (size_t)k * N, g.periodic ? pv.tvl[k] : T(0),
+                     g.periodic ? pv.tfac[k] : T(0), pv.zb + (size_t)k * N);
+    else
+      warp_tridiag<T>(N, gfun, pv.te + (size_t)k * N, pv.tm + (size_t)k * N, pv.tcp + (size_t)k * N,
+                      g.periodic != 0, pv.tz + (size_t)k * N, g.periodic ? pv.tvl[k] : T(0),
+                      g.periodic ? pv.tfac[k] : T(0), pv.zb + (size_t)k * N);
   }
 }
 
@@ -1169,8 +1176,7 @@ __device__ void stage_body(Instance& I, const Team& tm, int stage, int step, uns
     mass1d_condense(t, I.R, 2, I.scr, rh * t.Nx + ex);
   }
   if (!grid_barrier(tm, s_flag)) return;
-  if (warp == 0)
-    for (int rh = tm.rank; rh < 2; rh += tm.size) mass1d_interface(t, 2, I.scr, rh);
+  for (int rh = tm.rank; rh < 2; rh += tm.size) mass1d_interface_cta(t, 2, I.scr, rh);
   if (!grid_barrier(tm, s_flag)) return;
   for (int q = threadIdx.x; q < 2 * nc; q += blockDim.x) {
     const int rh = q / nc, col = R.c0 + (q - rh * nc);
@@ -1185,8 +1191,7 @@ __device__ void stage_body(Instance& I, const Team& tm, int stage, int step, uns
     mass1d_condense(t, I.R, 2, I.scr, rh * t.Nx + ex);
   }
   if (!grid_barrier(tm, s_flag)) return;
-  if (warp == 0)
-    for (int rh = tm.rank; rh < 2; rh += tm.size) mass1d_interface(t, 2, I.scr, rh);
+  for (int rh = tm.rank; rh < 2; rh += tm.size) mass1d_interface_cta(t, 2, I.scr, rh);
   if (!grid_barrier(tm, s_flag)) return;
   for (int q = threadIdx.x; q < 2 * nc; q += blockDim.x) {
     const int rh = q / nc, col = R.c0 + (q - rh * nc);

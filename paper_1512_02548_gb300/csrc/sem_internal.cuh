@@ -360,6 +360,99 @@ __device__ __forceinline__ void warp_tridiag(int N, GFun gfun, const T* te, cons
   }
 }
 
+// All threads of the CTA solve one tridiagonal system: the factors and recurrences of
+// warp_tridiag, with chunks of ⌈N/blockDim⌉ values per thread and the scan of the composed affine
+// maps across the CTA (shuffles within each warp, the warps' totals scanned by warp 0 through
+// shared memory).  For long systems (N > 32·kTridiagRegs), where a warp alone would walk chunks of
+// N/32 values.  Must be called by every thread of the CTA (it synchronises the CTA).
+template <class T, class GFun>
+__device__ void cta_tridiag(int N, GFun gfun, const T* te, const T* tm, const T* tcp, bool periodic,
+                            const T* tz, T tvl, T tfac, T* out) {
+  __shared__ T sA[32], sB[32];
+  const int nt = blockDim.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  const int c = (N + nt - 1) / nt;
+  const int j0 = min(N, tid * c), j1 = min(N, j0 + c);
+  const unsigned full = 0xffffffffu;
+  // forward: y_j = α_j y_{j−1} + β_j over this thread's chunk
+  T A = T(1), B = T(0);
+  for (int j = j0; j < j1; ++j) {
+    const T m = tm[j];
+    const T al = j > 0 ? -te[j - 1] * m : T(0);
+    B = fmx(al, B, gfun(j) * m);
+    A = al * A;
+  }
+  for (int o = 1; o < 32; o <<= 1) {             // inclusive scan over the lanes
+    const T Ap = __shfl_up_sync(full, A, o), Bp = __shfl_up_sync(full, B, o);
+    if (lane >= o) { B = fmx(A, Bp, B); A = A * Ap; }
+  }
+  __syncthreads();                                // earlier users of sA, sB are done
+  if (lane == 31) { sA[wid] = A; sB[wid] = B; }
+  __syncthreads();
+  if (wid == 0) {                                 // exclusive scan over the warps
+    T a = lane < nw ? sA[lane] : T(1), b = lane < nw ? sB[lane] : T(0);
+    for (int o = 1; o < 32; o <<= 1) {
+      const T ap = __shfl_up_sync(full, a, o), bp = __shfl_up_sync(full, b, o);
+      if (lane >= o) { b = fmx(a, bp, b); a = a * ap; }
+    }
+    T eb = __shfl_up_sync(full, b, 1);
+    if (lane == 0) eb = T(0);
+    if (lane < nw) sB[lane] = eb;                 // y at the end of the warps before
+  }
+  __syncthreads();
+  {
+    T Al = __shfl_up_sync(full, A, 1), Bl = __shfl_up_sync(full, B, 1);
+    if (lane == 0) { Al = T(1); Bl = T(0); }
+    T y = fmx(Al, sB[wid], Bl);                   // y_{j0−1}
+    for (int j = j0; j < j1; ++j) {
+      const T m = tm[j];
+      const T al = j > 0 ? -te[j - 1] * m : T(0);
+      y = fmx(al, y, gfun(j) * m);
+      out[j] = y;
+    }
+  }
+  // backward: x_j = γ_j x_{j+1} + y_j, γ_j = −c'_j (c'_{N−1} = 0), chunks from the top
+  A = T(1); B = T(0);
+  for (int j = j1 - 1; j >= j0; --j) {
+    const T ga = -tcp[j];
+    B = fmx(ga, B, out[j]);
+    A = ga * A;
+  }
+  for (int o = 1; o < 32; o <<= 1) {
+    const T An = __shfl_down_sync(full, A, o), Bn = __shfl_down_sync(full, B, o);
+    if (lane + o < 32) { B = fmx(A, Bn, B); A = A * An; }
+  }
+  __syncthreads();
+  if (lane == 0) { sA[wid] = A; sB[wid] = B; }
+  __syncthreads();
+  if (wid == 0) {
+    T a = lane < nw ? sA[lane] : T(1), b = lane < nw ? sB[lane] : T(0);
+    for (int o = 1; o < 32; o <<= 1) {
+      const T an = __shfl_down_sync(full, a, o), bn = __shfl_down_sync(full, b, o);
+      if (lane + o < 32) { b = fmx(a, bn, b); a = a * an; }
+    }
+    T eb = __shfl_down_sync(full, b, 1);
+    if (lane == 31) eb = T(0);
+    if (lane < nw) sB[lane] = eb;                 // x at the start of the warps after
+  }
+  __syncthreads();
+  {
+    T An = __shfl_down_sync(full, A, 1), Bn = __shfl_down_sync(full, B, 1);
+    if (lane == 31) { An = T(1); Bn = T(0); }
+    T x = fmx(An, sB[wid], Bn);                   // x_{j1}
+    for (int j = j1 - 1; j >= j0; --j) {
+      x = fmx(-tcp[j], x, out[j]);
+      out[j] = x;
+    }
+  }
+  __syncthreads();
+  if (periodic) {
+    const T cc = (out[0] + tvl * out[N - 1]) * tfac;
+    __syncthreads();
+    for (int j = j0; j < j1; ++j) out[j] = fmx(-cc, tz[j], out[j]);
+    __syncthreads();
+  }
+}
+
 // Launch counter (all kernels of this library).
 void count_launch(int k = 1);
 

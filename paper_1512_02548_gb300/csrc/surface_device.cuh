@@ -82,6 +82,25 @@ __device__ __forceinline__ void mass1d_interface(const SurfTables& t, int nrhs, 
   warp_tridiag<double>(N, gfun, t.th_e, t.th_m, t.th_cp, t.periodic != 0, t.th_z, t.th_vlast, t.th_fac, ub);
 }
 
+// The same solve by a whole CTA (every thread must call it): long systems (N > 32·kTridiagRegs)
+// use the CTA-wide scan, short ones warp 0 alone.
+__device__ __forceinline__ void mass1d_interface_cta(const SurfTables& t, int nrhs, double* __restrict__ scr,
+                                                     int rh) {
+  const int Nx = t.Nx, N = t.nif;
+  if (N <= 32 * kTridiagRegs) {
+    if (threadIdx.x < 32) mass1d_interface(t, nrhs, scr, rh);
+    return;
+  }
+  const double* gl = scr + rh * Nx;
+  const double* gr = scr + nrhs * Nx + rh * Nx;
+  double* ub = scr + 2 * nrhs * Nx + rh * N;
+  auto gfun = [&](int j) -> double {
+    if (t.periodic) return __ldcg(gl + j) + __ldcg(gr + (j == 0 ? Nx - 1 : j - 1));
+    return (j < Nx ? __ldcg(gl + j) : 0.0) + (j > 0 ? __ldcg(gr + j - 1) : 0.0);
+  };
+  cta_tridiag<double>(N, gfun, t.th_e, t.th_m, t.th_cp, t.periodic != 0, t.th_z, t.th_vlast, t.th_fac, ub);
+}
+
 // Phase 3, column `col` of right-hand side `rh`: interface value or back-substituted interior.
 __device__ __forceinline__ void mass1d_backsub(const SurfTables& t, const double* __restrict__ R, int nrhs,
                                                double* __restrict__ u, const double* __restrict__ scr,

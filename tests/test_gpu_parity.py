@@ -226,6 +226,20 @@ def test_rk4_steps(case):
     assert rel(eta, e) < TOL_FP64 and rel(phis, p) < TOL_FP64
 
 
+@pytest.mark.parametrize("periodic", [True, False], ids=["periodic", "walls"])
+def test_long_tank_interface_solves(periodic):
+    """More than 128 interface unknowns: the preconditioner's and M''s interface systems are
+    solved by a whole CTA (chunks over all its threads) instead of one warp."""
+    wl, om, gm = make_pair(P=3, Nx=150, Nz=1, periodic=periodic)
+    eta0, phis0 = surface(om, seed=11)
+    eta, phis = T(eta0), T(phis0)
+    gm.rk4_step(eta, phis, wl.dt, 2)
+    e, p = eta0, phis0
+    for _ in range(2):
+        e, p = om.rk4_step(e, p, wl.dt)
+    assert rel(eta, e) < TOL_FP64 and rel(phis, p) < TOL_FP64
+
+
 def test_c1_one_period_matches_oracle():
     wl = c1_linear_standing()
     om = osem.mesh_for(wl)
