@@ -219,7 +219,11 @@ int sem_zakharov_rhs(sem_mesh* m, const double* eta_d, const double* phis_d, dou
  * (1 − γ(x))(q_a − q)/τ is added at the surface nodes, with γ a smooth step ξ²(3−2ξ) across
  * each zone.  Arrays are host, ncomp ≤ 4096 entries each; ncomp = 0 clears the signal.
  * The copy is synchronous and not ordered with `stream` work: call it while no step of
- * this mesh is in flight. */
+ * this mesh is in flight.  It also tabulates cos, sin of k_i x at the left-zone columns
+ * (one more device block of 16·ncomp bytes per zone column, up to 512 MB; larger tables are
+ * skipped): the fused RK stage then evaluates the signal by angle addition, with per-stage
+ * sines of ω_i t + θ_i, spread over all CTAs of the team.  Returns SEM_ERR_OOM if that block
+ * cannot be allocated. */
 int sem_set_wave_input(sem_mesh* m, int ncomp, const double* amp_h, const double* omega_h,
                        const double* k_h, const double* phase_h);
 

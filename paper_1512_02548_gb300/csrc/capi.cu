@@ -163,6 +163,10 @@ struct sem_mesh {
   // stage potentials kept for the next stages' initial guesses, and the trajectory they belong
   // to (the state buffers and dt of the last fused RK call; hist_dt = 0: none)
   double *Phi1 = nullptr, *Phi2 = nullptr, *Phi3 = nullptr, *D32 = nullptr;
+  // column positions on the host, and the cos/sin(k x) table of the left-zone columns for the
+  // generated signal (its own device block, rebuilt by sem_set_wave_input)
+  std::vector<double> xcol_h;
+  double* wkx = nullptr;
   double hist_dt = 0.0;
   const double *hist_eta = nullptr, *hist_phis = nullptr;
   // fused-stage launch of this mesh alone: device descriptor, CTA map, barrier pair
@@ -657,6 +661,8 @@ static int mesh_create_impl(const sem_params* pin, const double* x_edges_h, cons
                o_gL32 = cv.take<float>(nEl), o_gR32 = cv.take<float>(nEl), o_zb32 = cv.take<float>(nIf),
                o_rh32 = cv.take<float>((size_t)ncol * nr);
   const size_t o_xcol = cv.take<double>(ncol), o_wave = cv.take<double>(4 * kMaxWaveComp);
+  const bool zones = p.relax_left > 0.0 || p.relax_right > 0.0;
+  const size_t o_wA = cv.take<double>(zones ? 4 * kMaxWaveComp : 0), o_wEP = cv.take<double>(zones ? 2 * ncol : 0);
   const size_t o_wt = cv.take<double>(ncol), o_etax = cv.take<double>(ncol), o_phisx = cv.take<double>(ncol),
                o_R = cv.take<double>((size_t)2 * Nx * Q), o_scr = cv.take<double>((size_t)4 * Nx + 2 * (N + 1)),
                o_ke = cv.take<double>(ncol), o_kp = cv.take<double>(ncol), o_ae = cv.take<double>(ncol),
@@ -706,6 +712,7 @@ static int mesh_create_impl(const sem_params* pin, const double* x_edges_h, cons
       xc[c] = x_edges_h[e] + 0.5 * (L.r[a] + 1.0) * dxe[e];
     }
     up(o_xcol, xc);
+    m->xcol_h = xc;
   }
   if (code == SEM_OK) {
     std::vector<float> S32(Sg.begin(), Sg.end());
@@ -760,6 +767,9 @@ static int mesh_create_impl(const sem_params* pin, const double* x_edges_h, cons
   t.th_vlast = th_vlast; t.th_fac = th_fac; t.nif = N; t.filter_on = (p.filter_ic >= 0 && p.filter_ic < P) ? 1 : 0;
   t.xcol = D_(o_xcol); t.x0 = x_edges_h[0]; t.x1 = x_edges_h[Nx];
   t.relax_left = p.relax_left; t.relax_right = p.relax_right; t.ncomp = 0; t.wave = D_(o_wave);
+  t.nzl = 0; t.wkx = nullptr;
+  t.wA = zones ? D_(o_wA) : nullptr;
+  t.wEP = zones ? D_(o_wEP) : nullptr;
   // the fused RK stage runs this mesh with one team of CTAs (at most its Krylov grid)
   {
     const char* fz = std::getenv("SEM_FUSED_STAGE");
@@ -792,6 +802,7 @@ void sem_mesh_destroy(sem_mesh* m) {
   for (auto& pr : m->events) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
   for (auto e : m->spare) cudaEventDestroy(e);
   cudaDeviceSynchronize();   // no work of this mesh may still run when its memory is reused
+  if (m->wkx) dev_free(m->device, m->wkx);
   dev_free(m->device, m->pool);
   delete m;
 }
@@ -905,6 +916,32 @@ int sem_set_wave_input(sem_mesh* m, int ncomp, const double* amp_h, const double
   for (int q = 0; q < 4 && ncomp > 0; ++q)
     CUDA_TRY(cudaMemcpy(w + (size_t)q * ncomp, src[q], sizeof(double) * ncomp, cudaMemcpyHostToDevice));
   m->st.ncomp = ncomp;
+  // cos, sin of k x at the left-zone columns (the first nzl columns), for the fused stage's
+  // angle-addition evaluation; left out when there is no left zone or the table would pass 512 MB
+  CUDA_TRY(cudaDeviceSynchronize());
+  if (m->wkx) { dev_free(m->device, m->wkx); m->wkx = nullptr; }
+  m->st.wkx = nullptr;
+  m->st.nzl = 0;
+  int nzl = 0;
+  if (m->p.relax_left > 0.0)
+    while (nzl < m->ncol && m->xcol_h[nzl] < m->st.x0 + m->p.relax_left) ++nzl;
+  const size_t entries = (size_t)nzl * (size_t)ncomp * 2;
+  if (nzl > 0 && ncomp > 0 && m->st.wA && entries * sizeof(double) <= (size_t(512) << 20)) {
+    std::vector<double> tab(entries);
+    for (int c = 0; c < nzl; ++c)
+      for (int i = 0; i < ncomp; ++i) {
+        const double kx = k_h[i] * m->xcol_h[c];
+        tab[((size_t)c * ncomp + i) * 2] = std::cos(kx);
+        tab[((size_t)c * ncomp + i) * 2 + 1] = std::sin(kx);
+      }
+    void* d = nullptr;
+    cudaError_t e = dev_alloc(m->device, entries * sizeof(double), &d);
+    if (e != cudaSuccess) return fail(SEM_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    m->wkx = static_cast<double*>(d);
+    CUDA_TRY(cudaMemcpy(m->wkx, tab.data(), entries * sizeof(double), cudaMemcpyHostToDevice));
+    m->st.wkx = m->wkx;
+    m->st.nzl = nzl;
+  }
   return SEM_OK;
 }
 

@@ -1124,6 +1124,10 @@ __device__ void stage_body(Instance& I, const Team& tm, int stage, int step, uns
   // differs from stage 2 by ¼dt²k₁' + …, which changes little from step to step: Φ₂ + (Φ₃ − Φ₂)
   // of the last step.  Owned nodes only; the barriers below order these writes before any
   // neighbour reads them.
+  // generated signal of the left relaxation zone at this stage's time: component angles now
+  // (all CTAs of the team), the zone columns after the next barrier, read by the relaxation term
+  const bool wave_tab = I.relax && t.wkx != nullptr && t.ncomp > 0 && t.nzl > 0 && stage >= 1;
+  if (wave_tab) wave_angles(t, time, tm.rank * blockDim.x + threadIdx.x, tm.size * blockDim.x);
   const bool cont = step > 0 || I.hist;        // the last step belongs to this trajectory
   if (stage == 4 || (stage == 2 && cont)) {
     const double* Pold = stage == 2 ? I.P3 : I.P1;
@@ -1142,6 +1146,8 @@ __device__ void stage_body(Instance& I, const Team& tm, int stage, int step, uns
     __syncthreads();
   }
   if (!grid_barrier(tm, s_flag)) return;
+  if (wave_tab)
+    for (int col = tm.rank * nw + warp; col < t.nzl; col += tm.size * nw) wave_zone_column(t, col, lane);
   if (warp == 0) {
     float* stg = 2 * I.ps.nif <= 2 * kSurfWarpScratch ? reinterpret_cast<float*>(sh[0]) : nullptr;
     for (int k = tm.rank; k < I.ps.nr; k += tm.size) prec_tri_mode(g, I.ps, k, stg);
@@ -1200,7 +1206,7 @@ __device__ void stage_body(Instance& I, const Team& tm, int stage, int step, uns
   __syncthreads();
   // relaxation source and the RK4 bookkeeping on owned columns
   for (int col = R.c0 + threadIdx.x; col < R.c1; col += blockDim.x) {
-    if (I.relax) relax_column(t, ein, pin, time, 1.0 / I.tau, I.ke, I.kp, col);
+    if (I.relax) relax_column(t, ein, pin, time, 1.0 / I.tau, I.ke, I.kp, col, wave_tab ? t.wEP : nullptr);
     rk4_item(stage, I.dt, I.eta, I.phis, I.ke, I.kp, I.ae, I.ap, eout, pout, col);
   }
   if (stage == 4 && t.filter_on) {

@@ -143,6 +143,13 @@ struct SurfTables {
   double relax_left, relax_right;
   int ncomp;              // components of the generated signal
   const double* wave;     // [4][ncomp]: a, ω, k, θ
+  // the generated signal by angle addition (fused stage): cos(ωt + θ − kx) from cos, sin of
+  // ωt + θ (per stage) and of kx (per column, fixed); nzl = columns of the left zone, which are
+  // the first columns; wkx = nullptr: evaluated directly
+  int nzl;
+  const double* wkx;      // [nzl][ncomp][2]: cos k_i x, sin k_i x
+  double* wA;             // [4][ncomp] per stage: a cos A, a sin A, c sin A, c cos A (A = ωt + θ, c = −g a/ω)
+  double* wEP;            // [nzl][2] per stage: generated η and φ̃ at the left-zone columns
 };
 
 // One instance (mesh + state) of a fused RK stage launch.

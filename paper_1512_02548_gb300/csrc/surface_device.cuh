@@ -199,9 +199,51 @@ __device__ __forceinline__ void filter_element(const SurfTables& t, double* q0, 
 // Embedded penalty forcing of §2.2 at column `col`: q̇ += (1 − γ(x))(q_a(x,t) − q)/τ with
 // γ = ξ²(3 − 2ξ) across each zone (1 outside); q_a is the linear superposition of the wave
 // input in the left zone, rest in the right zone.
+// Per time level, the component factors of the generated signal (§2.2): with A = ωt + θ and
+// c = −g a/ω, wA = (a cos A, a sin A, c sin A, c cos A).  Items i = first, first + stride, ….
+__device__ __forceinline__ void wave_angles(const SurfTables& t, double time, int first, int stride) {
+  const int n = t.ncomp;
+  const double* a = t.wave;
+  const double* om = a + n;
+  const double* th = om + 2 * n;
+  for (int i = first; i < n; i += stride) {
+    double sn, cs;
+    sincos(fma(om[i], time, th[i]), &sn, &cs);
+    const double c = -t.g * a[i] / om[i];
+    t.wA[i] = a[i] * cs;
+    t.wA[n + i] = a[i] * sn;
+    t.wA[2 * n + i] = c * sn;
+    t.wA[3 * n + i] = c * cs;
+  }
+}
+
+// The generated η = Σ a cos(A − kx) and φ̃ = Σ c sin(A − kx) at left-zone column `col`, by one
+// warp (lanes over the components, then a shuffle tree): cos(A − kx) = cos A cos kx + sin A sin kx,
+// sin(A − kx) = sin A cos kx − cos A sin kx.  Written to wEP by lane 0.
+__device__ __forceinline__ void wave_zone_column(const SurfTables& t, int col, int lane) {
+  const int n = t.ncomp;
+  const double* ck = t.wkx + (size_t)col * n * 2;
+  double ea = 0.0, pa = 0.0;
+  for (int i = lane; i < n; i += 32) {
+    const double cb = ck[2 * i], sb = ck[2 * i + 1];
+    ea = fma(t.wA[i], cb, fma(t.wA[n + i], sb, ea));
+    pa = fma(t.wA[2 * n + i], cb, fma(-t.wA[3 * n + i], sb, pa));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    ea += __shfl_xor_sync(0xffffffffu, ea, o);
+    pa += __shfl_xor_sync(0xffffffffu, pa, o);
+  }
+  if (lane == 0) {
+    t.wEP[2 * col] = ea;
+    t.wEP[2 * col + 1] = pa;
+  }
+}
+
+// ep: the generated (η, φ̃) of the left-zone columns for this time (wave_zone_columns), or
+// nullptr to sum the components here.
 __device__ __forceinline__ void relax_column(const SurfTables& t, const double* __restrict__ eta,
                                              const double* __restrict__ phis, double time, double inv_tau,
-                                             double* de, double* dp, int col) {
+                                             double* de, double* dp, int col, const double* ep = nullptr) {
   const double x = t.xcol[col];
   double gam = 1.0;
   const bool left = t.relax_left > 0.0 && x < t.x0 + t.relax_left;
@@ -215,7 +257,10 @@ __device__ __forceinline__ void relax_column(const SurfTables& t, const double* 
   }
   if (gam >= 1.0) return;
   double ea = 0.0, pa = 0.0;
-  if (left) {
+  if (left && ep != nullptr && col < t.nzl) {
+    ea = ep[2 * col];
+    pa = ep[2 * col + 1];
+  } else if (left) {
     const double* a = t.wave;
     const double* om = a + t.ncomp;
     const double* k = om + t.ncomp;
