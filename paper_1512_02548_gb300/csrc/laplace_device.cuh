@@ -925,23 +925,31 @@ __global__ void __launch_bounds__(kThreads) k_pcg(DevGeom g, PcgArgs A) {
 constexpr int kPrecModesPerBlock = 32;
 constexpr size_t kTriStageMax = 160 * 1024;
 
-// Mode-independent part of element ex (all threads of the block, sync after): Kx and the
-// lumped mass weights (Δx/2) w/d.
+// Mode-independent part of element ex: entry t (row-major) of Kx and entry i of the lumped mass
+// weights (Δx/2) w/d; prec_elem_kx fills both with all threads of the block (sync after).
 template <int P>
-__device__ __forceinline__ void prec_elem_kx(const DevGeom& g, int ex, double* Kx, double* mw) {
+__device__ __forceinline__ double prec_kx_entry(const DevGeom& g, int ex, int t) {
   constexpr int Q = P + 1;
   const double* D = c_D64 + d_off(P);
   const double* w = c_w64 + w_off(P);
   const double* geo = g.geo64 + (size_t)ex * Q * 4;
-  const double dxe = g.dxe[ex];
-  for (int t = threadIdx.x; t < Q * Q; t += blockDim.x) {
-    const int i = t / Q, j = t - i * Q;
-    double s = 0.0;
+  const int i = t / Q, j = t - i * Q;
+  double s = 0.0;
 #pragma unroll
-    for (int a = 0; a < Q; ++a) s = fma(D[a * Q + i] * w[a] * geo[a * 4 + 0], D[a * Q + j], s);
-    Kx[t] = (2.0 / dxe) * s;
-  }
-  for (int i = threadIdx.x; i < Q; i += blockDim.x) mw[i] = 0.5 * dxe * w[i] * geo[i * 4 + 1];
+  for (int a = 0; a < Q; ++a) s = fma(D[a * Q + i] * w[a] * geo[a * 4 + 0], D[a * Q + j], s);
+  return (2.0 / g.dxe[ex]) * s;
+}
+template <int P>
+__device__ __forceinline__ double prec_mw_entry(const DevGeom& g, int ex, int i) {
+  constexpr int Q = P + 1;
+  const double* w = c_w64 + w_off(P);
+  return 0.5 * g.dxe[ex] * w[i] * g.geo64[(size_t)ex * Q * 4 + i * 4 + 1];
+}
+template <int P>
+__device__ __forceinline__ void prec_elem_kx(const DevGeom& g, int ex, double* Kx, double* mw) {
+  constexpr int Q = P + 1;
+  for (int t = threadIdx.x; t < Q * Q; t += blockDim.x) Kx[t] = prec_kx_entry<P>(g, ex, t);
+  for (int i = threadIdx.x; i < Q; i += blockDim.x) mw[i] = prec_mw_entry<P>(g, ex, i);
 }
 
 // Mode k of element ex (one thread).
@@ -1138,12 +1146,32 @@ __device__ void stage_body(Instance& I, const Team& tm, int stage, int step, uns
     for (int i = R.c0 * g.nrow + threadIdx.x; i < R.c1 * g.nrow; i += blockDim.x) x[i] += I.D32[i];
   }
   __syncthreads();
-  // preconditioner: condensation of the owned elements for every mode, then interface pivots
-  for (int ex = R.e0; ex < R.e1; ++ex) {
-    prec_elem_kx<P>(g, ex, Kx, mw);
-    __syncthreads();
-    for (int k = threadIdx.x; k < I.ps.nr; k += blockDim.x) prec_elem_mode<P>(g, I.ps, ex, k, Kx, mw);
-    __syncthreads();
+  // preconditioner: condensation of the owned elements for every mode, then interface pivots.
+  // The apply's shared memory is free until the solve: it holds Kx and mw of a batch of elements,
+  // so that all (element, mode) pairs of the batch run at once.
+  {
+    double* kxs = reinterpret_cast<double*>(smem_raw);
+    constexpr int per = Q * Q + Q;
+    const int avail = Q * Q + Q + g.nrow + g.chunk * (2 * g.Nz + 4 * Q + Q * g.nrow + 2 * g.Nz * Q * Q);
+    const int nb_max = max(1, min(ne, avail / per));
+    const int nr = I.ps.nr;
+    for (int e0 = R.e0; e0 < R.e1; e0 += nb_max) {
+      const int nb = min(nb_max, R.e1 - e0);
+      for (int t = threadIdx.x; t < nb * Q * Q; t += blockDim.x) {
+        const int b = t / (Q * Q);
+        kxs[b * per + (t - b * Q * Q)] = prec_kx_entry<P>(g, e0 + b, t - b * Q * Q);
+      }
+      for (int t = threadIdx.x; t < nb * Q; t += blockDim.x) {
+        const int b = t / Q;
+        kxs[b * per + Q * Q + (t - b * Q)] = prec_mw_entry<P>(g, e0 + b, t - b * Q);
+      }
+      __syncthreads();
+      for (int t = threadIdx.x; t < nb * nr; t += blockDim.x) {
+        const int b = t / nr, k = t - b * nr;
+        prec_elem_mode<P>(g, I.ps, e0 + b, k, kxs + b * per, kxs + b * per + Q * Q);
+      }
+      __syncthreads();
+    }
   }
   if (!grid_barrier(tm, s_flag)) return;
   if (wave_tab)
