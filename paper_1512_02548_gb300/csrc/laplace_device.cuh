@@ -1092,6 +1092,125 @@ static __device__ void prec_tri_mode(const DevGeom& g, const PrecSetup& ps, int 
   }
 }
 
+// 2×2 matrix product A·B scaled by a power of two (exact) so that its largest entry lies in
+// [½, 1): the pivot scan below needs only ratios of the entries.
+static __device__ __forceinline__ void mat2_mul_norm(const float (&A)[4], const float (&B)[4], float (&C)[4]) {
+  float c0 = fmaf(A[0], B[0], A[1] * B[2]), c1 = fmaf(A[0], B[1], A[1] * B[3]);
+  float c2 = fmaf(A[2], B[0], A[3] * B[2]), c3 = fmaf(A[2], B[1], A[3] * B[3]);
+  const float mx = fmaxf(fmaxf(fabsf(c0), fabsf(c1)), fmaxf(fabsf(c2), fabsf(c3)));
+  if (mx > 0.f && mx < INFINITY) {
+    int ex;
+    frexpf(mx, &ex);
+    c0 = ldexpf(c0, -ex); c1 = ldexpf(c1, -ex); c2 = ldexpf(c2, -ex); c3 = ldexpf(c3, -ex);
+  }
+  C[0] = c0; C[1] = c1; C[2] = c2; C[3] = c3;
+}
+
+// prec_tri_mode by every thread of the CTA, for long interface systems (N > 32·kTridiagRegs).  The
+// pivots p_j = d_j − e_{j−1}²/p_{j−1} are the ratios of the continuants [u_j; v_j] = M_j [u_{j−1};
+// v_{j−1}], M_j = [[d_j, −e_{j−1}²], [1, 0]], [u_{−1}; v_{−1}] = [1; 0].  Each thread multiplies
+// the M_j of its chunk, a CTA-wide scan of these products gives the continuant before every
+// chunk, and each thread then runs the scalar recurrence of prec_tri_mode from that pivot.
+static __device__ void prec_tri_mode_cta(const DevGeom& g, const PrecSetup& ps, int k) {
+  __shared__ float sM[32][4];
+  const int N = ps.nif, Nx = g.Nx;
+  const int nt = blockDim.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  const unsigned full = 0xffffffffu;
+  const double* sc = ps.schur + (size_t)k * Nx * 3;
+  float* te32 = ps.te32 + (size_t)k * N;
+  float* tm32 = ps.tm32 + (size_t)k * N;
+  float* tcp32 = ps.tcp32 + (size_t)k * N;
+  float* tz32 = ps.tz32 + (size_t)k * N;
+  const double corner = g.periodic ? sc[(Nx - 1) * 3 + 1] : 0.0;
+  const double gamma = g.periodic ? -(double)(sc[0] + sc[(Nx - 1) * 3 + 2]) : 0.0;
+  // diagonal (staged in tm32, replaced by the pivots) and off-diagonal
+  for (int j = tid; j < N; j += nt) {
+    double d;
+    if (g.periodic) d = sc[j * 3 + 0] + sc[(j == 0 ? Nx - 1 : j - 1) * 3 + 2];
+    else d = (j < Nx ? sc[j * 3 + 0] : 0.0) + (j > 0 ? sc[(j - 1) * 3 + 2] : 0.0);
+    if (g.periodic && j == 0) d = 2.0 * (sc[0] + sc[(Nx - 1) * 3 + 2]);
+    tm32[j] = (float)d;
+    te32[j] = (float)((j < N - 1) ? sc[j * 3 + 1] : 0.0);
+  }
+  __syncthreads();
+  if (g.periodic && tid == 0) tm32[N - 1] = (float)((double)tm32[N - 1] - corner * corner / gamma);
+  __syncthreads();
+  const int c = (N + nt - 1) / nt;
+  const int j0 = min(N, tid * c), j1 = min(N, j0 + c);
+  float M[4] = {1.f, 0.f, 0.f, 1.f};
+  for (int j = j0; j < j1; ++j) {
+    const float ej = j > 0 ? te32[j - 1] : 0.f;
+    const float Mj[4] = {tm32[j], -ej * ej, 1.f, 0.f};
+    mat2_mul_norm(Mj, M, M);
+  }
+  for (int o = 1; o < 32; o <<= 1) {               // inclusive scan over the lanes (later on the left)
+    float Mp[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) Mp[q] = __shfl_up_sync(full, M[q], o);
+    if (lane >= o) mat2_mul_norm(M, Mp, M);
+  }
+  if (lane == 31)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) sM[wid][q] = M[q];
+  __syncthreads();
+  if (wid == 0) {                                   // exclusive scan over the warps
+    float W[4] = {1.f, 0.f, 0.f, 1.f};
+    if (lane < nw)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) W[q] = sM[lane][q];
+    for (int o = 1; o < 32; o <<= 1) {
+      float Wp[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) Wp[q] = __shfl_up_sync(full, W[q], o);
+      if (lane >= o) mat2_mul_norm(W, Wp, W);
+    }
+    float E[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) E[q] = __shfl_up_sync(full, W[q], 1);
+    if (lane == 0) { E[0] = 1.f; E[1] = 0.f; E[2] = 0.f; E[3] = 1.f; }
+    __syncwarp();
+    if (lane < nw)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) sM[lane][q] = E[q];
+  }
+  __syncthreads();
+  float Lx[4];                                      // lanes before this one in the warp
+#pragma unroll
+  for (int q = 0; q < 4; ++q) Lx[q] = __shfl_up_sync(full, M[q], 1);
+  if (lane == 0) { Lx[0] = 1.f; Lx[1] = 0.f; Lx[2] = 0.f; Lx[3] = 1.f; }
+  float Ew[4], Pf[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) Ew[q] = sM[wid][q];
+  mat2_mul_norm(Lx, Ew, Pf);                        // continuant map up to the end of the last chunk
+  // the scalar recurrence of prec_tri_mode from the pivot before the chunk
+  float e_prev = 0.f, cp_prev = 0.f;
+  if (j0 > 0 && j0 < j1) {
+    e_prev = te32[j0 - 1];
+    cp_prev = e_prev * (Pf[2] / Pf[0]);             // e_{j0−1} / p_{j0−1}
+  }
+  __syncthreads();                                  // every chunk has read its diagonal
+  for (int j = j0; j < j1; ++j) {
+    const float m = 1.f / (j == 0 ? tm32[0] : fmaf(-e_prev, cp_prev, tm32[j]));
+    const float e = te32[j];
+    tm32[j] = m;
+    tcp32[j] = e * m;
+    cp_prev = e * m;
+    e_prev = e;
+  }
+  __syncthreads();
+  if (g.periodic) {
+    auto u32 = [&](int j) -> float { return j == 0 ? (float)gamma : (j == N - 1 ? (float)corner : 0.f); };
+    cta_tridiag<float>(N, u32, te32, tm32, tcp32, false, (const float*)nullptr, 0.f, 0.f, tz32);
+    if (tid == 0) {
+      const double vl = corner / gamma;
+      ps.tvl32[k] = (float)vl;
+      ps.tfac32[k] = 1.f / (1.f + tz32[0] + (float)vl * tz32[N - 1]);
+    }
+  } else {
+    for (int j = tid; j < N; j += nt) tz32[j] = 0.f;
+  }
+}
+
 static __global__ void __launch_bounds__(32) k_prec_tri(DevGeom g, PrecSetup ps, int staged) {
   extern __shared__ __align__(16) double tri_sm[];
   prec_tri_mode(g, ps, blockIdx.x, staged ? reinterpret_cast<float*>(tri_sm) : nullptr);
@@ -1176,7 +1295,9 @@ __device__ void stage_body(Instance& I, const Team& tm, int stage, int step, uns
   if (!grid_barrier(tm, s_flag)) return;
   if (wave_tab)
     for (int col = tm.rank * nw + warp; col < t.nzl; col += tm.size * nw) wave_zone_column(t, col, lane);
-  if (warp == 0) {
+  if (I.ps.nif > 32 * kTridiagRegs) {             // long systems: the whole CTA per mode
+    for (int k = tm.rank; k < I.ps.nr; k += tm.size) prec_tri_mode_cta(g, I.ps, k);
+  } else if (warp == 0) {
     float* stg = 2 * I.ps.nif <= 2 * kSurfWarpScratch ? reinterpret_cast<float*>(sh[0]) : nullptr;
     for (int k = tm.rank; k < I.ps.nr; k += tm.size) prec_tri_mode(g, I.ps, k, stg);
   }
