@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "sem.h"
+#include "mesh_index.cuh"
 #include "sem_internal.cuh"
 #include "tables.h"
 
@@ -175,7 +176,9 @@ struct sem_mesh {
   unsigned int* stage_bars = nullptr;
   Instance inst_h{};
   int stage_team = 0;
-  size_t stage_smem = 0;
+  size_t stage_smem = 0;         // the mesh's own fused stage launch (with the factor cache)
+  size_t stage_smem_batch = 0;   // in a batch launch (no factor cache)
+  int gcache = 0;                // doubles of the factor cache in the own launch (0 = none)
   bool fused = true;
   // optional event timing of the Krylov kernel
   bool timing = false;
@@ -303,10 +306,12 @@ void set_history(sem_mesh* m, const double* eta, const double* phis, double dt) 
   m->hist_phis = phis;
 }
 
+// own_launch: the mesh's own fused stage launch, whose shared memory holds the factor cache.
 Instance make_instance(sem_mesh* m, double* eta, double* phis, double tstart, double dt, int team0,
-                       int nteam) {
+                       int nteam, bool own_launch = false) {
   Instance I{};
   I.g = m->g;
+  I.g.gcache = own_launch ? m->gcache : 0;
   I.st = m->st;
   I.pa = m->pa;
   I.pa.x = m->Phi;
@@ -326,7 +331,7 @@ Instance make_instance(sem_mesh* m, double* eta, double* phis, double tstart, do
 
 // nsteps RK4 steps of one mesh with the fused stage kernel: one cooperative launch per stage.
 int do_rk4_fused(sem_mesh* m, double* eta, double* phis, double t0, double dt, int nsteps, cudaStream_t s) {
-  m->inst_h = make_instance(m, eta, phis, t0, dt, 0, m->stage_team);
+  m->inst_h = make_instance(m, eta, phis, t0, dt, 0, m->stage_team, true);
   CUDA_TRY(cudaMemcpyAsync(m->inst_d, &m->inst_h, sizeof(Instance), cudaMemcpyHostToDevice, s));
   StageArgs a{m->inst_d, m->cta_inst_d, m->stage_bars, 1, 0};
   const int mixed = m->p.precision == SEM_PREC_MIXED;
@@ -784,6 +789,21 @@ static int mesh_create_impl(const sem_params* pin, const double* x_edges_h, cons
       return fail(SEM_ERR_CUDA, "fused stage kernel does not fit on this device");
     }
     m->stage_team = std::min(m->grid, per_sm * sms);
+    m->stage_smem_batch = m->stage_smem;
+    // room for the solve's geometric factors (3 per element-local node of a CTA's element
+    // columns) after the apply's buffers, if the launch keeps its occupancy
+    {
+      const int Qd = P + 1;
+      const int ne_max = (Nx + m->stage_team - 1) / m->stage_team;
+      const size_t need = (size_t)3 * ne_max * Nz * Qd * Qd;
+      const size_t smem2 = m->stage_smem + need * sizeof(double);
+      int per2 = 0;
+      if (smem2 <= (size_t)kMaxDynSmem &&
+          stage_occupancy(P, p.precision == SEM_PREC_MIXED, 0, smem2, &per2) == cudaSuccess && per2 >= per_sm) {
+        m->stage_smem = smem2;
+        m->gcache = (int)need;
+      }
+    }
     std::vector<int> zeros(m->grid, 0);
     cudaError_t e2 = cudaMemcpy(m->cta_inst_d, zeros.data(), sizeof(int) * m->grid, cudaMemcpyHostToDevice);
     if (e2 != cudaSuccess) {
@@ -1013,7 +1033,7 @@ int sem_batch_create(sem_mesh* const* meshes, int count, sem_batch** out) {
   size_t total = 0;
   for (auto& grp : groups) {
     size_t smem = 0;
-    for (int i : grp.second) smem = std::max(smem, meshes[i]->stage_smem);
+    for (int i : grp.second) smem = std::max(smem, meshes[i]->stage_smem_batch);
     int per_sm = 0;
     // Build of the stage kernel: two CTAs per SM (128 registers) for groups of many instances,
     // where more co-resident teams pay; one CTA per SM with the full register file (the

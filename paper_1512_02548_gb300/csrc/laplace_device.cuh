@@ -190,19 +190,58 @@ template <> __device__ __forceinline__ const float* geo_ptr<float>(const DevGeom
 // input value of local column a, row iz of element column ex; `store(ex,a,iz,y)` receives the
 // element column's contribution.  Returns this thread's share of Σ x·(A_e x) over the chunk
 // (accumulated in T).
+// Geometric factors of the σ-transformed operator at element-local node (a, b) of layer l:
+// G11 = w_a w_b (Δσ/Δx) d, G12 = w_a w_b K12, G22 = w_a w_b (Δx/Δσ) (1 + K12²)/d, K12 = ∂xh − σ ∂xd.
+template <class T>
+__device__ __forceinline__ void geo_factors(T d, T invd, T hx, T dxd, T cz0, T cz1, T wa, T wb, T sig, T& G11,
+                                            T& G12, T& G22) {
+  const T wab = wa * wb;
+  const T K12 = hx - sig * dxd;
+  const T K22 = fmx(K12, K12, (T)1) * invd;
+  G11 = wab * cz0 * d;
+  G12 = wab * K12;
+  G22 = wab * cz1 * K22;
+}
+
+// The factors of every element-local node of the CTA's element columns R.e0..R.e1−1, three per
+// node in the order of the apply's work items; FP64, computed as in apply_element_chunk.
+template <int P>
+__device__ void fill_gcache(const DevGeom& g, int e0, int e1, double* gc) {
+  constexpr int Q = P + 1;
+  const int elsz = g.Nz * Q * Q;
+  const double* w = c_w64 + w_off(P);
+  for (int t = threadIdx.x; t < (e1 - e0) * elsz; t += blockDim.x) {
+    const int e = t / elsz, rem0 = t - e * elsz;
+    const int l = rem0 / (Q * Q), rem = rem0 - l * (Q * Q), a = rem / Q, b = rem - a * Q;
+    const int ge = e0 + e;
+    const double* geo = g.geo64 + (size_t)ge * Q * 4 + a * 4;
+    const double dxe = g.dxe[ge], dsl = g.dsl[l];
+    double G11, G12, G22;
+    geo_factors<double>(geo[0], geo[1], geo[2], geo[3], dsl / dxe, dxe / dsl, w[a], w[b], g.sig[l * P + b], G11,
+                        G12, G22);
+    gc[3 * t] = G11;
+    gc[3 * t + 1] = G12;
+    gc[3 * t + 2] = G22;
+  }
+}
+
+// gc (FP64 only, optional): the chunk's geometric factors from fill_gcache, used instead of
+// staging the geometry and recomputing them.
 template <int P, class T, class LoadX, class Store>
 __device__ __forceinline__ T apply_element_chunk(const DevGeom& g, Smem<P, T>& s, int ex0, int ne,
-                                                 LoadX loadx, Store store) {
+                                                 LoadX loadx, Store store, const double* gc = nullptr) {
   constexpr int Q = P + 1;
   const int nrow = g.nrow, Nz = g.Nz;
   const int colsz = Q * nrow, elsz = Nz * Q * Q;
-  const T* geo = geo_ptr<T>(g) + (size_t)ex0 * Q * 4;
-  for (int t = threadIdx.x; t < ne * 4 * Q; t += blockDim.x) s.geo[t] = geo[t];
-  for (int t = threadIdx.x; t < ne * Nz; t += blockDim.x) {
-    const int e = t / Nz, l = t - e * Nz;
-    const double dxe = g.dxe[ex0 + e], dsl = g.dsl[l];
-    s.cxz[2 * t] = (T)(dsl / dxe);
-    s.cxz[2 * t + 1] = (T)(dxe / dsl);
+  if (gc == nullptr) {
+    const T* geo = geo_ptr<T>(g) + (size_t)ex0 * Q * 4;
+    for (int t = threadIdx.x; t < ne * 4 * Q; t += blockDim.x) s.geo[t] = geo[t];
+    for (int t = threadIdx.x; t < ne * Nz; t += blockDim.x) {
+      const int e = t / Nz, l = t - e * Nz;
+      const double dxe = g.dxe[ex0 + e], dsl = g.dsl[l];
+      s.cxz[2 * t] = (T)(dsl / dxe);
+      s.cxz[2 * t + 1] = (T)(dxe / dsl);
+    }
   }
   for (int t = threadIdx.x; t < ne * colsz; t += blockDim.x) {
     const int e = t / colsz, rem = t - e * colsz;
@@ -224,15 +263,16 @@ __device__ __forceinline__ T apply_element_chunk(const DevGeom& g, Smem<P, T>& s
       ur = fmx(Da[c], Xrow[c * nrow], ur);
       ut = fmx(Db[c], Xcol[c], ut);
     }
-    const T* ge = s.geo + e * 4 * Q + a * 4;
-    const T d = ge[0], invd = ge[1], hx = ge[2], dxd = ge[3];
-    const T* cz = s.cxz + 2 * (e * Nz + l);
-    const T wab = s.w[a] * s.w[b];
-    const T K12 = hx - s.sig[l * P + b] * dxd;
-    const T K22 = fmx(K12, K12, (T)1) * invd;
-    const T G11 = wab * cz[0] * d;
-    const T G12 = wab * K12;
-    const T G22 = wab * cz[1] * K22;
+    T G11, G12, G22;
+    if (gc != nullptr) {
+      G11 = (T)gc[3 * t];
+      G12 = (T)gc[3 * t + 1];
+      G22 = (T)gc[3 * t + 2];
+    } else {
+      const T* ge = s.geo + e * 4 * Q + a * 4;
+      const T* cz = s.cxz + 2 * (e * Nz + l);
+      geo_factors<T>(ge[0], ge[1], ge[2], ge[3], cz[0], cz[1], s.w[a], s.w[b], s.sig[l * P + b], G11, G12, G22);
+    }
     s.F1[t] = fmx(G11, ur, G12 * ut);
     s.F2[t] = fmx(G12, ur, G22 * ut);
   }
@@ -665,7 +705,7 @@ __device__ bool finish_precondition(const DevGeom& g, Smem<P, T>& s, const Range
 template <int P, class T, class A, class TP>
 __device__ int cg_solve(const DevGeom& g, Smem<P, T>& s, const Range& R, const Team& tm, const PcgArgs& PA,
                         const PrecView<TP>& pv, const CgVecs<T>& V, double target, int max_it, double* red,
-                        int* s_flag, double* rr_out) {
+                        int* s_flag, double* rr_out, const double* gc = nullptr) {
   const int nrow = g.nrow;
   __shared__ T s_scal[2];
   __shared__ int s_stop;
@@ -679,6 +719,7 @@ __device__ int cg_solve(const DevGeom& g, Smem<P, T>& s, const Range& R, const T
     const T* rc = V.r[cur];
     A acc[3] = {A(0), A(0), A(0)};   // γ = (r,u), δ = (u,Au), (r,r)
     for (int ex0 = R.e0; ex0 < R.e1; ex0 += g.chunk) {
+      const double* gce = gc ? gc + (size_t)(ex0 - R.e0) * 3 * g.Nz * (P + 1) * (P + 1) : nullptr;
       acc[1] += (A)apply_element_chunk<P, T>(
           g, s, ex0, min(g.chunk, R.e1 - ex0),
           [&](int e, int a, int iz) -> T {
@@ -696,7 +737,8 @@ __device__ int cg_solve(const DevGeom& g, Smem<P, T>& s, const Range& R, const T
           [&](int e, int a, int iz, T y) {
             if (owns_local_col(g, e, a)) V.w[(size_t)col_of(g, e, a) * nrow + iz] = y;
             else V.edge[(size_t)e * nrow + iz] = y;
-          });
+          },
+          gce);
     }
     block_sum<3, A>(acc, red);
     put_partials<3, A>(tm, 2, acc);
@@ -739,14 +781,16 @@ __device__ int cg_solve(const DevGeom& g, Smem<P, T>& s, const Range& R, const T
 template <int P>
 __device__ bool fp64_residual(const DevGeom& g, Smem<P, double>& s, const Range& R, const Team& tm,
                               const PcgArgs& A, bool want_b, double* red, int* s_flag, double& rr, double& bb,
-                              double* dx = nullptr) {
+                              double* dx = nullptr, const double* gc = nullptr) {
   // dx (optional): on entry dx[0] is this thread's partial ‖δ‖² of the last correction; on
   // exit dx[0] = ‖δ‖² and dx[1] = ‖x‖² over the whole team (interior nodes).
   const int nrow = g.nrow;
   const double* x = A.x;
   const double* phis = A.phis;
+  const size_t gstride = (size_t)3 * g.Nz * (g.P + 1) * (g.P + 1);   // cached factors per element
   for (int ex0 = R.e0; ex0 < R.e1; ex0 += g.chunk) {
     const int ne = min(g.chunk, R.e1 - ex0);
+    const double* gce = gc ? gc + (size_t)(ex0 - R.e0) * gstride : nullptr;
     apply_element_chunk<P, double>(
         g, s, ex0, ne,
         [&](int e, int a, int iz) -> double {
@@ -756,7 +800,8 @@ __device__ bool fp64_residual(const DevGeom& g, Smem<P, double>& s, const Range&
         [&](int e, int a, int iz, double y) {
           if (owns_local_col(g, e, a)) A.q64[(size_t)col_of(g, e, a) * nrow + iz] = y;
           else A.edge64[(size_t)e * nrow + iz] = y;
-        });
+        },
+        gce);
     if (want_b)
       apply_element_chunk<P, double>(
           g, s, ex0, ne,
@@ -764,7 +809,8 @@ __device__ bool fp64_residual(const DevGeom& g, Smem<P, double>& s, const Range&
           [&](int e, int a, int iz, double y) {
             if (owns_local_col(g, e, a)) A.q64b[(size_t)col_of(g, e, a) * nrow + iz] = y;
             else A.edge64b[(size_t)e * nrow + iz] = y;
-          });
+          },
+          gce);
   }
   if (!grid_barrier(tm, s_flag)) return false;
   double acc[4] = {0.0, 0.0, dx ? dx[0] : 0.0, 0.0};
@@ -808,8 +854,17 @@ __device__ bool solve_body(const DevGeom& g, const PcgArgs& A, const Team& tm, u
   Smem<P, double> s64;
   s64.carve(smem_raw, nrow, g.Nz, g.chunk);
   s64.load_tables(g);
+  // the geometric factors of the FP64 applies, once per solve, where the launch reserved room
+  // for them after the apply's buffers
+  const double* gc = nullptr;
+  if (g.gcache > 0 && (size_t)3 * (R.e1 - R.e0) * g.Nz * (P + 1) * (P + 1) <= (size_t)g.gcache) {
+    double* c = s64.F2 + (size_t)g.Nz * (P + 1) * (P + 1) * g.chunk;
+    fill_gcache<P>(g, R.e0, R.e1, c);
+    __syncthreads();
+    gc = c;
+  }
   double rr = 0.0, bb = 0.0;
-  if (!fp64_residual<P>(g, s64, R, tm, A, true, red, &s_flag, rr, bb)) return false;
+  if (!fp64_residual<P>(g, s64, R, tm, A, true, red, &s_flag, rr, bb, nullptr, gc)) return false;
   const double target = A.tol * A.tol * bb;
   int iters = 0, refinements = 0;
   bool rr_floor_ok = false;   // stopped at the FP64 residual floor with converged corrections
@@ -828,7 +883,7 @@ __device__ bool solve_body(const DevGeom& g, const PcgArgs& A, const Team& tm, u
     // FP64 vectors, FP32 preconditioner: u = M⁻¹r only steers the search directions, and the
     // FP32 pipe is 64 times the FP64 pipe on this part
     iters = cg_solve<P, double, double, float>(g, s64, R, tm, A, A.pv32, V, target, A.max_iter, red, &s_flag,
-                                               &rr_out);
+                                               &rr_out, gc);
     if (iters < 0) return false;
     rr = rr_out;
   } else {
@@ -882,7 +937,7 @@ __device__ bool solve_body(const DevGeom& g, const PcgArgs& A, const Team& tm, u
       s64.load_tables(g);
       if (!grid_barrier(tm, &s_flag)) return false;
       double dummy_b = 0.0;
-      if (!fp64_residual<P>(g, s64, R, tm, A, false, red, &s_flag, rr, dummy_b, dx)) return false;
+      if (!fp64_residual<P>(g, s64, R, tm, A, false, red, &s_flag, rr, dummy_b, dx, gc)) return false;
       stalled = dx[0] > 0.25 * dd_prev;
       dd_prev = dx[0];
       if (it == 0) break;   // no progress possible

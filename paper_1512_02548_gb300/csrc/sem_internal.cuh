@@ -33,6 +33,8 @@ struct DevGeom {
   double* invdiag64;     // [n] 1 / diag(−𝓛) at interior nodes, 0 at the surface
   float* invdiag32;      // same in FP32
   int* status;           // device status word
+  int gcache;            // doubles of dynamic shared memory after the FP64 apply's buffers that
+                         // hold a solve's geometric factors (single-mesh fused stage; 0 = none)
 };
 
 // Element columns processed together per CTA pass: enough that a pass has ~256–512 work
