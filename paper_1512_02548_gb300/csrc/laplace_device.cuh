@@ -1161,7 +1161,8 @@ static __device__ __forceinline__ void mat2_mul_norm(const float (&A)[4], const 
   C[0] = c0; C[1] = c1; C[2] = c2; C[3] = c3;
 }
 
-// prec_tri_mode by every thread of the CTA, for long interface systems (N > 32·kTridiagRegs).  The
+// prec_tri_mode by every thread of the CTA, for long interface systems between walls
+// (N > 32·kTridiagRegs).  The
 // pivots p_j = d_j − e_{j−1}²/p_{j−1} are the ratios of the continuants [u_j; v_j] = M_j [u_{j−1};
 // v_{j−1}], M_j = [[d_j, −e_{j−1}²], [1, 0]], [u_{−1}; v_{−1}] = [1; 0].  Each thread multiplies
 // the M_j of its chunk, a CTA-wide scan of these products gives the continuant before every
@@ -1350,7 +1351,11 @@ __device__ void stage_body(Instance& I, const Team& tm, int stage, int step, uns
   if (!grid_barrier(tm, s_flag)) return;
   if (wave_tab)
     for (int col = tm.rank * nw + warp; col < t.nzl; col += tm.size * nw) wave_zone_column(t, col, lane);
-  if (I.ps.nif > 32 * kTridiagRegs) {             // long systems: the whole CTA per mode
+  // long systems between walls: the whole CTA per mode.  Periodic systems keep the serial
+  // recurrence: their Sherman–Morrison closure divides by 1 + vᵀT'⁻¹u, which for a nearly
+  // singular lowest mode magnifies any difference in the pivots (a 192 k-node periodic tank
+  // stopped converging with the scanned pivots).
+  if (I.ps.nif > 32 * kTridiagRegs && !g.periodic) {
     for (int k = tm.rank; k < I.ps.nr; k += tm.size) prec_tri_mode_cta(g, I.ps, k);
   } else if (warp == 0) {
     float* stg = 2 * I.ps.nif <= 2 * kSurfWarpScratch ? reinterpret_cast<float*>(sh[0]) : nullptr;

@@ -240,6 +240,39 @@ def test_long_tank_interface_solves(periodic):
     assert rel(eta, e) < TOL_FP64 and rel(phis, p) < TOL_FP64
 
 
+@pytest.mark.slow
+def test_long_periodic_tank_fused_equals_multikernel():
+    """A 192 k-node periodic tank (5352×2, P=4; request 91 of the C5 stream): the fused stage
+    (long-system paths) against the multi-kernel path, two RK4 steps, 1e-10, with every solve
+    converging in a normal number of iterations.  Scanned interface pivots had made this tank's
+    solves stall (its lowest σ-mode is nearly singular in x)."""
+    from sem_workloads import c5_requests
+    wl = c5_requests(100.0, 300, 0)[91][2]
+    assert (wl.P, wl.Nx, wl.Nz, wl.periodic) == (4, 5352, 2, True)
+    x = np.linspace(0.0, wl.length, wl.ncol, endpoint=False)
+    h = np.full(wl.ncol, wl.depth)
+    e0, p0 = initial_state(wl, x, h)
+    res = []
+    for fused in ("1", "0"):
+        old = os.environ.get("SEM_FUSED_STAGE")
+        os.environ["SEM_FUSED_STAGE"] = fused
+        try:
+            gm = sem.Mesh.from_workload(wl, h=h)
+        finally:
+            if old is None:
+                del os.environ["SEM_FUSED_STAGE"]
+            else:
+                os.environ["SEM_FUSED_STAGE"] = old
+        eta, phis = T(e0), T(p0)
+        gm.reset_counters()
+        gm.rk4_step(eta, phis, wl.dt, 2)
+        c = gm.counters()
+        assert c.iterations / c.solves < 20 and c.max_rel_residual <= 1e-13, (fused, c.iterations, c.solves)
+        res.append((eta.cpu().numpy(), phis.cpu().numpy()))
+        gm.close()
+    assert rel(res[0][0], res[1][0]) < TOL_FP64 and rel(res[0][1], res[1][1]) < TOL_FP64
+
+
 def test_c1_one_period_matches_oracle():
     wl = c1_linear_standing()
     om = osem.mesh_for(wl)
