@@ -233,7 +233,11 @@ int sem_apply_filter(sem_mesh* m, double* q_d, void* stream);
 
 /* nsteps classical RK4 steps of size dt on (η, φ̃) in place, each followed by
  * the filter (§3.1.1, §3.4); *t advances by nsteps·dt.  eta_d, phis_d: device,
- * Ncol.  Synchronises once at the end. */
+ * Ncol.  Synchronises once at the end.  Each stage's Laplace solve starts from an
+ * extrapolation of earlier stage potentials kept by the mesh; stages 2 and 3 of the
+ * first step use the previous call's potentials when this call steps the same eta_d,
+ * phis_d with the same dt (a continuing trajectory).  The starting point does not change
+ * the converged result, only the iteration count; a failed step clears the history. */
 int sem_rk4_step(sem_mesh* m, double* eta_d, double* phis_d, double* t, double dt,
                  int nsteps, void* stream);
 

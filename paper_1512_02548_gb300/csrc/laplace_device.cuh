@@ -1283,7 +1283,7 @@ constexpr int kStageWarps = kThreads / 32;
 
 template <int P, bool MIXED>
 __device__ void stage_body(Instance& I, const Team& tm, int stage, int step, unsigned char* smem_raw,
-                           double* red, int* s_flag, double (*sh)[kSurfWarpScratch], double* Kx, double* mw) {
+                           double* red, int* s_flag, double (*sh)[kSurfWarpScratch]) {
   constexpr int Q = P + 1;
   const DevGeom& g = I.g;
   const SurfTables& t = I.st;
@@ -1433,8 +1433,6 @@ __global__ void __launch_bounds__(kThreads, WIDE ? 2 : 1) k_stage(StageArgs B) {
   __shared__ double red[kRedSize];
   __shared__ int s_flag;
   __shared__ __align__(16) double sh[kStageWarps][kSurfWarpScratch];
-  __shared__ double Kx[(P + 1) * (P + 1)];
-  __shared__ double mw[P + 1];
   __shared__ __align__(16) Instance I;
   const int ii = B.cta_inst[blockIdx.x];
   {
@@ -1444,7 +1442,7 @@ __global__ void __launch_bounds__(kThreads, WIDE ? 2 : 1) k_stage(StageArgs B) {
   }
   __syncthreads();
   const Team tm{(int)blockIdx.x - I.team0, I.nteam, B.bars + 2 * ii, I.g.status, I.pa.part, I.pa.part_stride};
-  stage_body<P, MIXED>(I, tm, B.stage, B.step, smem_raw, red, &s_flag, sh, Kx, mw);
+  stage_body<P, MIXED>(I, tm, B.stage, B.step, smem_raw, red, &s_flag, sh);
 }
 
 
