@@ -179,6 +179,7 @@ struct sem_mesh {
   size_t stage_smem = 0;         // the mesh's own fused stage launch (with the factor cache)
   size_t stage_smem_batch = 0;   // in a batch launch (no factor cache)
   int gcache = 0;                // doubles of the factor cache in the own launch (0 = none)
+  int own_chunk = 0;             // element columns per pass in the own launch (g.chunk elsewhere)
   bool fused = true;
   // optional event timing of the Krylov kernel
   bool timing = false;
@@ -312,6 +313,7 @@ Instance make_instance(sem_mesh* m, double* eta, double* phis, double tstart, do
   Instance I{};
   I.g = m->g;
   I.g.gcache = own_launch ? m->gcache : 0;
+  if (own_launch) I.g.chunk = m->own_chunk;
   I.st = m->st;
   I.pa = m->pa;
   I.pa.x = m->Phi;
@@ -790,16 +792,26 @@ static int mesh_create_impl(const sem_params* pin, const double* x_edges_h, cons
     }
     m->stage_team = std::min(m->grid, per_sm * sms);
     m->stage_smem_batch = m->stage_smem;
-    // room for the solve's geometric factors (3 per element-local node of a CTA's element
-    // columns) after the apply's buffers, if the launch keeps its occupancy
+    m->own_chunk = chunk;
+    // The own launch: all of a CTA's element columns in one pass (instead of passes of `chunk`,
+    // each paying its own round trips to L2 and CTA barriers), and room for the solve's
+    // geometric factors (3 per element-local node) after the apply's buffers, each if the
+    // launch keeps its occupancy.
     {
       const int Qd = P + 1;
       const int ne_max = (Nx + m->stage_team - 1) / m->stage_team;
+      const int mixed = p.precision == SEM_PREC_MIXED;
+      int per2 = 0;
+      const size_t smem_wide = stage_smem_bytes(P, nrow, Nz, ne_max);
+      if (ne_max > chunk && smem_wide <= (size_t)kMaxDynSmem &&
+          stage_occupancy(P, mixed, 0, smem_wide, &per2) == cudaSuccess && per2 >= per_sm) {
+        m->own_chunk = ne_max;
+        m->stage_smem = smem_wide;
+      }
       const size_t need = (size_t)3 * ne_max * Nz * Qd * Qd;
       const size_t smem2 = m->stage_smem + need * sizeof(double);
-      int per2 = 0;
       if (smem2 <= (size_t)kMaxDynSmem &&
-          stage_occupancy(P, p.precision == SEM_PREC_MIXED, 0, smem2, &per2) == cudaSuccess && per2 >= per_sm) {
+          stage_occupancy(P, mixed, 0, smem2, &per2) == cudaSuccess && per2 >= per_sm) {
         m->stage_smem = smem2;
         m->gcache = (int)need;
       }
