@@ -193,6 +193,7 @@ struct BatchLaunch {
   int P = 0, mixed = 0, wide = 1;
   std::vector<int> members;          // mesh indices
   std::vector<int> team0, nteam;
+  std::vector<int> chunk;            // element columns per pass of each member
   int grid = 0;
   size_t smem = 0;
   Instance* inst_d = nullptr;
@@ -308,12 +309,14 @@ void set_history(sem_mesh* m, const double* eta, const double* phis, double dt) 
 }
 
 // own_launch: the mesh's own fused stage launch, whose shared memory holds the factor cache.
+// chunk > 0: element columns per pass in a batch launch.
 Instance make_instance(sem_mesh* m, double* eta, double* phis, double tstart, double dt, int team0,
-                       int nteam, bool own_launch = false) {
+                       int nteam, bool own_launch = false, int chunk = 0) {
   Instance I{};
   I.g = m->g;
   I.g.gcache = own_launch ? m->gcache : 0;
   if (own_launch) I.g.chunk = m->own_chunk;
+  else if (chunk > 0) I.g.chunk = chunk;
   I.st = m->st;
   I.pa = m->pa;
   I.pa.x = m->Phi;
@@ -1014,6 +1017,9 @@ int sem_rk4_step_host(sem_mesh* m, double* eta_h, double* phis_h, double* t, dou
 
 // Groups of at most this many instances use the one-CTA-per-SM stage build.
 constexpr int kBatchNarrowMax = 8;
+// Dynamic shared memory per CTA up to which batch members widen their passes (two CTAs per SM,
+// or one).
+constexpr size_t kBatchSmemWide = 88 * 1024, kBatchSmemNarrow = 176 * 1024;
 
 int sem_batch_create(sem_mesh* const* meshes, int count, sem_batch** out) {
   if (!out) return fail(SEM_ERR_INVALID_ARG, "out is NULL");
@@ -1089,6 +1095,27 @@ int sem_batch_create(sem_mesh* const* meshes, int count, sem_batch** out) {
       int acc = 0;
       for (size_t k = 0; k < c.size(); ++k) { L.team0.push_back(acc); L.nteam.push_back(c[k]); acc += c[k]; }
       L.grid = acc;
+      // each member's CTAs take their element columns in as few passes as the launch's shared
+      // memory allows (a budget per CTA that keeps the build's CTAs per SM)
+      {
+        const size_t budget = wide ? kBatchSmemWide : kBatchSmemNarrow;
+        size_t smem_l = smem;
+        for (size_t k = 0; k < L.members.size(); ++k) {
+          const sem_mesh* m = meshes[L.members[k]];
+          const int ne = (m->p.Nx + c[k] - 1) / c[k];
+          int E = m->g.chunk;
+          while (E < ne && stage_smem_bytes(m->p.P, m->nrow, m->p.Nz, E + 1) <= budget) ++E;
+          L.chunk.push_back(E);
+          smem_l = std::max(smem_l, stage_smem_bytes(m->p.P, m->nrow, m->p.Nz, E));
+        }
+        int per2 = 0;
+        if (smem_l > smem &&
+            (stage_occupancy(L.P, L.mixed, wide, smem_l, &per2) != cudaSuccess || per2 < per_sm)) {
+          for (size_t k = 0; k < L.members.size(); ++k) L.chunk[k] = meshes[L.members[k]]->g.chunk;
+          smem_l = smem;
+        }
+        L.smem = smem_l;
+      }
       total += ((sizeof(Instance) * L.members.size() + 255) & ~size_t(255)) +
                ((sizeof(int) * (size_t)L.grid + 255) & ~size_t(255)) +
                ((sizeof(unsigned) * 2 * L.members.size() + 255) & ~size_t(255)) +
@@ -1171,7 +1198,7 @@ int sem_batch_rk4_step(sem_batch* b, double* const* eta_d, double* const* phis_d
     for (size_t k = 0; k < L.members.size(); ++k) {
       const int i = L.members[k];
       L.inst_h[k] = make_instance(b->meshes[i], eta_d[i], phis_d[i], t_h ? t_h[i] : 0.0, dt_h[i], L.team0[k],
-                                  L.nteam[k]);
+                                  L.nteam[k], false, L.chunk[k]);
     }
     CUDA_TRY(cudaMemcpyAsync(L.inst_d, L.inst_h.data(), sizeof(Instance) * L.members.size(),
                              cudaMemcpyHostToDevice, s));
@@ -1203,7 +1230,7 @@ int sem_batch_laplace_solve(sem_batch* b, const double* const* eta_d, const doub
     for (size_t k = 0; k < L.members.size(); ++k) {
       const int i = L.members[k];
       L.inst_h[k] = make_instance(b->meshes[i], const_cast<double*>(eta_d[i]), const_cast<double*>(phis_d[i]),
-                                  0.0, 1.0, L.team0[k], L.nteam[k]);
+                                  0.0, 1.0, L.team0[k], L.nteam[k], false, L.chunk[k]);
       L.inst_h[k].pa.x = Phi_d[i];
     }
     CUDA_TRY(cudaMemcpyAsync(L.inst_d, L.inst_h.data(), sizeof(Instance) * L.members.size(),
