@@ -26,6 +26,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -98,7 +99,9 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        # the samples are read back by this process only; SEM_CLOCKS_DIR keeps them elsewhere
+        self.path = os.path.join(os.environ.get("SEM_CLOCKS_DIR", tempfile.gettempdir()),
+                                 f"sem_clocks_rank{gpu_index}_{os.getpid()}.csv")
 
     def start(self):
         try:
