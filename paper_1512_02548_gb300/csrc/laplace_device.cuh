@@ -611,7 +611,7 @@ __device__ void cg_update(const DevGeom& g, Smem<P, T>& s, const Range& R, const
 // Interface solve per σ-mode: one warp (warp 0 of a CTA) per mode, or the whole CTA for long
 // systems, modes spread over CTAs;
 // g_j = gL_j + gR_{j−1} assembled on the fly, then the warp-parallel tridiagonal solve.
-template <class T>
+template <class T, bool CACHE = false>
 __device__ void phase_interface(const DevGeom& g, const PrecView<T>& pv, const Team& tm) {
   const int N = pv.nif, Nx = g.Nx;
   const bool whole_cta = N > 32 * kTridiagRegs;   // long systems: all warps of the CTA per mode
@@ -624,7 +624,7 @@ __device__ void phase_interface(const DevGeom& g, const PrecView<T>& pv, const T
       return (j < Nx ? ldcg(gl + j) : T(0)) + (j > 0 ? ldcg(gr + j - 1) : T(0));
     };
     if (whole_cta)
-      cta_tridiag<T>(N, gfun, pv.te + (size_t)k * N, pv.tm + (size_t)k * N, pv.tcp + (size_t)k * N,
+      cta_tridiag<T, decltype(gfun), CACHE>(N, gfun, pv.te + (size_t)k * N, pv.tm + (size_t)k * N, pv.tcp + (size_t)k * N,
                      g.periodic != 0, pv.tz + (size_t)k * N, g.periodic ? pv.tvl[k] : T(0),
                      g.periodic ? pv.tfac[k] : T(0), pv.zb + (size_t)k * N);
     else
@@ -685,12 +685,12 @@ __device__ void phase_backsub(const DevGeom& g, Smem<P, T>& s, const Range& R, c
 
 // Remaining grid phases of u = M⁻¹ r after cg_update (separable: interface solve and
 // back-substitution; Jacobi: nothing but a barrier that protects w and edge).
-template <int P, class T, class TP>
+template <int P, class T, class TP, bool CACHE = false>
 __device__ bool finish_precondition(const DevGeom& g, Smem<P, T>& s, const Range& R, const Team& tm,
                                     const PcgArgs& PA, const PrecView<TP>& pv, const CgVecs<T>& V, int* s_flag) {
   if (PA.precond == PREC_JACOBI) return grid_barrier(tm, s_flag);
   if (!grid_barrier(tm, s_flag)) return false;
-  phase_interface<TP>(g, pv, tm);
+  phase_interface<TP, CACHE>(g, pv, tm);
   if (!grid_barrier(tm, s_flag)) return false;
   phase_backsub<P, T, TP>(g, s, R, tm, pv, V);
   return true;
@@ -702,7 +702,7 @@ __device__ bool finish_precondition(const DevGeom& g, Smem<P, T>& s, const Range
 // Starts from V.x with its residual in V.r[0].  Stops when ‖r‖² ≤ target or after max_it
 // iterations.  Returns the iterations, or −1 on a barrier timeout; ‖r‖² of the final residual
 // (on thread 0) in *rr_out.
-template <int P, class T, class A, class TP>
+template <int P, class T, class A, class TP, bool CACHE = false>
 __device__ int cg_solve(const DevGeom& g, Smem<P, T>& s, const Range& R, const Team& tm, const PcgArgs& PA,
                         const PrecView<TP>& pv, const CgVecs<T>& V, double target, int max_it, double* red,
                         int* s_flag, double* rr_out, const double* gc = nullptr) {
@@ -711,7 +711,7 @@ __device__ int cg_solve(const DevGeom& g, Smem<P, T>& s, const Range& R, const T
   __shared__ int s_stop;
   int cur = 0;
   cg_update<P, T, TP>(g, s, R, tm, pv, PA.precond, V, cur, false, true, T(0), T(0));
-  if (!finish_precondition<P, T, TP>(g, s, R, tm, PA, pv, V, s_flag)) return -1;
+  if (!finish_precondition<P, T, TP, CACHE>(g, s, R, tm, PA, pv, V, s_flag)) return -1;
   int k = 0;
   double inv_gamma_prev = 1.0, inv_alpha_prev = 1.0, rr = 0.0;   // 1/γ and 1/α of the last iteration
   while (true) {
@@ -769,7 +769,7 @@ __device__ int cg_solve(const DevGeom& g, Smem<P, T>& s, const Range& R, const T
     const T alpha = s_scal[0], beta = s_scal[1];
     cg_update<P, T, TP>(g, s, R, tm, pv, PA.precond, V, cur, true, k == 0, alpha, beta);
     cur ^= 1;
-    if (!finish_precondition<P, T, TP>(g, s, R, tm, PA, pv, V, s_flag)) return -1;
+    if (!finish_precondition<P, T, TP, CACHE>(g, s, R, tm, PA, pv, V, s_flag)) return -1;
     ++k;
   }
   *rr_out = rr;
@@ -845,7 +845,7 @@ __device__ bool fp64_residual(const DevGeom& g, Smem<P, double>& s, const Range&
 
 // One Laplace solve by a team of CTAs: FP64 residual of the lifted system, then PCG in FP64, or
 // FP32 inner PCG with FP64 residual refinement (MIXED).  Returns false after a barrier timeout.
-template <int P, bool MIXED>
+template <int P, bool MIXED, bool CACHE = false>
 __device__ bool solve_body(const DevGeom& g, const PcgArgs& A, const Team& tm, unsigned char* smem_raw,
                            double* red, int* s_flag_p) {
   int& s_flag = *s_flag_p;
@@ -882,7 +882,7 @@ __device__ bool solve_body(const DevGeom& g, const PcgArgs& A, const Team& tm, u
     double rr_out = rr;
     // FP64 vectors, FP32 preconditioner: u = M⁻¹r only steers the search directions, and the
     // FP32 pipe is 64 times the FP64 pipe on this part
-    iters = cg_solve<P, double, double, float>(g, s64, R, tm, A, A.pv32, V, target, A.max_iter, red, &s_flag,
+    iters = cg_solve<P, double, double, float, CACHE>(g, s64, R, tm, A, A.pv32, V, target, A.max_iter, red, &s_flag,
                                                &rr_out, gc);
     if (iters < 0) return false;
     rr = rr_out;
@@ -918,7 +918,7 @@ __device__ bool solve_body(const DevGeom& g, const PcgArgs& A, const Team& tm, u
       if (!grid_barrier(tm, &s_flag)) return false;
       const double tgt_in = fmax(A.inner_rtol * A.inner_rtol * rr, 0.25 * target);
       double rr_in = rr;
-      const int it = cg_solve<P, float, float, float>(g, s32, R, tm, A, A.pv32, V, tgt_in, A.max_iter - iters, red,
+      const int it = cg_solve<P, float, float, float, CACHE>(g, s32, R, tm, A, A.pv32, V, tgt_in, A.max_iter - iters, red,
                                                &s_flag, &rr_in);
       if (it < 0) return false;
       iters += it;
@@ -1281,7 +1281,7 @@ static __global__ void __launch_bounds__(32) k_prec_tri(DevGeom g, PrecSetup ps,
 // ------------------------------------------------------------------------------------
 constexpr int kStageWarps = kThreads / 32;
 
-template <int P, bool MIXED>
+template <int P, bool MIXED, bool CACHE = false>
 __device__ void stage_body(Instance& I, const Team& tm, int stage, int step, unsigned char* smem_raw,
                            double* red, int* s_flag, double (*sh)[kSurfWarpScratch]) {
   constexpr int Q = P + 1;
@@ -1365,7 +1365,7 @@ __device__ void stage_body(Instance& I, const Team& tm, int stage, int step, uns
   // Laplace solve, warm-started from the previous stage's potential
   if (threadIdx.x == 0) I.pa.phis = pin;
   __syncthreads();
-  if (!solve_body<P, MIXED>(g, I.pa, tm, smem_raw, red, s_flag)) return;
+  if (!solve_body<P, MIXED, CACHE>(g, I.pa, tm, smem_raw, red, s_flag)) return;
   if (stage == 0) return;
   // kept for the initial guesses of the next stages
   if (stage == 3) {
@@ -1391,7 +1391,7 @@ __device__ void stage_body(Instance& I, const Team& tm, int stage, int step, uns
     mass1d_condense(t, I.R, 2, I.scr, rh * t.Nx + ex);
   }
   if (!grid_barrier(tm, s_flag)) return;
-  for (int rh = tm.rank; rh < 2; rh += tm.size) mass1d_interface_cta(t, 2, I.scr, rh);
+  for (int rh = tm.rank; rh < 2; rh += tm.size) mass1d_interface_cta<CACHE>(t, 2, I.scr, rh);
   if (!grid_barrier(tm, s_flag)) return;
   for (int q = threadIdx.x; q < 2 * nc; q += blockDim.x) {
     const int rh = q / nc, col = R.c0 + (q - rh * nc);
@@ -1406,7 +1406,7 @@ __device__ void stage_body(Instance& I, const Team& tm, int stage, int step, uns
     mass1d_condense(t, I.R, 2, I.scr, rh * t.Nx + ex);
   }
   if (!grid_barrier(tm, s_flag)) return;
-  for (int rh = tm.rank; rh < 2; rh += tm.size) mass1d_interface_cta(t, 2, I.scr, rh);
+  for (int rh = tm.rank; rh < 2; rh += tm.size) mass1d_interface_cta<CACHE>(t, 2, I.scr, rh);
   if (!grid_barrier(tm, s_flag)) return;
   for (int q = threadIdx.x; q < 2 * nc; q += blockDim.x) {
     const int rh = q / nc, col = R.c0 + (q - rh * nc);
@@ -1442,7 +1442,7 @@ __global__ void __launch_bounds__(kThreads, WIDE ? 2 : 1) k_stage(StageArgs B) {
   }
   __syncthreads();
   const Team tm{(int)blockIdx.x - I.team0, I.nteam, B.bars + 2 * ii, I.g.status, I.pa.part, I.pa.part_stride};
-  stage_body<P, MIXED>(I, tm, B.stage, B.step, smem_raw, red, &s_flag, sh);
+  stage_body<P, MIXED, !WIDE>(I, tm, B.stage, B.step, smem_raw, red, &s_flag, sh);
 }
 
 

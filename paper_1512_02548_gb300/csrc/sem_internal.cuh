@@ -374,7 +374,12 @@ __device__ __forceinline__ void warp_tridiag(int N, GFun gfun, const T* te, cons
 // maps across the CTA (shuffles within each warp, the warps' totals scanned by warp 0 through
 // shared memory).  For long systems (N > 32·kTridiagRegs), where a warp alone would walk chunks of
 // N/32 values.  Must be called by every thread of the CTA (it synchronises the CTA).
-template <class T, class GFun>
+// Chunks of at most kCtaRegs values per thread keep the right-hand side and y in registers
+// between the passes of cta_tridiag (N ≤ kCtaRegs·blockDim).
+constexpr int kCtaRegs = 12;
+
+// CACHE (compile time): keep the chunk in registers (the one-CTA-per-SM build, which has the registers).
+template <class T, class GFun, bool CACHE = false>
 __device__ void cta_tridiag(int N, GFun gfun, const T* te, const T* tm, const T* tcp, bool periodic,
                             const T* tz, T tvl, T tfac, T* out) {
   __shared__ T sA[32], sB[32];
@@ -382,13 +387,29 @@ __device__ void cta_tridiag(int N, GFun gfun, const T* te, const T* tm, const T*
   const int c = (N + nt - 1) / nt;
   const int j0 = min(N, tid * c), j1 = min(N, j0 + c);
   const unsigned full = 0xffffffffu;
+  const bool regs = CACHE && c <= kCtaRegs;
+  T gr[kCtaRegs], vr[kCtaRegs];                   // g_j m_j, then y_j and x_j, of this chunk
   // forward: y_j = α_j y_{j−1} + β_j over this thread's chunk
   T A = T(1), B = T(0);
-  for (int j = j0; j < j1; ++j) {
-    const T m = tm[j];
-    const T al = j > 0 ? -te[j - 1] * m : T(0);
-    B = fmx(al, B, gfun(j) * m);
-    A = al * A;
+  if (regs) {
+#pragma unroll
+    for (int q = 0; q < kCtaRegs; ++q) {
+      const int j = j0 + q;
+      if (j < j1) {
+        const T m = tm[j];
+        const T al = j > 0 ? -te[j - 1] * m : T(0);
+        gr[q] = gfun(j) * m;
+        B = fmx(al, B, gr[q]);
+        A = al * A;
+      }
+    }
+  } else {
+    for (int j = j0; j < j1; ++j) {
+      const T m = tm[j];
+      const T al = j > 0 ? -te[j - 1] * m : T(0);
+      B = fmx(al, B, gfun(j) * m);
+      A = al * A;
+    }
   }
   for (int o = 1; o < 32; o <<= 1) {             // inclusive scan over the lanes
     const T Ap = __shfl_up_sync(full, A, o), Bp = __shfl_up_sync(full, B, o);
@@ -412,19 +433,43 @@ __device__ void cta_tridiag(int N, GFun gfun, const T* te, const T* tm, const T*
     T Al = __shfl_up_sync(full, A, 1), Bl = __shfl_up_sync(full, B, 1);
     if (lane == 0) { Al = T(1); Bl = T(0); }
     T y = fmx(Al, sB[wid], Bl);                   // y_{j0−1}
-    for (int j = j0; j < j1; ++j) {
-      const T m = tm[j];
-      const T al = j > 0 ? -te[j - 1] * m : T(0);
-      y = fmx(al, y, gfun(j) * m);
-      out[j] = y;
+    if (regs) {
+#pragma unroll
+      for (int q = 0; q < kCtaRegs; ++q) {
+        const int j = j0 + q;
+        if (j < j1) {
+          const T al = j > 0 ? -te[j - 1] * tm[j] : T(0);
+          y = fmx(al, y, gr[q]);
+          vr[q] = y;
+        }
+      }
+    } else {
+      for (int j = j0; j < j1; ++j) {
+        const T m = tm[j];
+        const T al = j > 0 ? -te[j - 1] * m : T(0);
+        y = fmx(al, y, gfun(j) * m);
+        out[j] = y;
+      }
     }
   }
   // backward: x_j = γ_j x_{j+1} + y_j, γ_j = −c'_j (c'_{N−1} = 0), chunks from the top
   A = T(1); B = T(0);
-  for (int j = j1 - 1; j >= j0; --j) {
-    const T ga = -tcp[j];
-    B = fmx(ga, B, out[j]);
-    A = ga * A;
+  if (regs) {
+#pragma unroll
+    for (int q = kCtaRegs - 1; q >= 0; --q) {
+      const int j = j0 + q;
+      if (j < j1) {
+        const T ga = -tcp[j];
+        B = fmx(ga, B, vr[q]);
+        A = ga * A;
+      }
+    }
+  } else {
+    for (int j = j1 - 1; j >= j0; --j) {
+      const T ga = -tcp[j];
+      B = fmx(ga, B, out[j]);
+      A = ga * A;
+    }
   }
   for (int o = 1; o < 32; o <<= 1) {
     const T An = __shfl_down_sync(full, A, o), Bn = __shfl_down_sync(full, B, o);
@@ -448,9 +493,21 @@ __device__ void cta_tridiag(int N, GFun gfun, const T* te, const T* tm, const T*
     T An = __shfl_down_sync(full, A, 1), Bn = __shfl_down_sync(full, B, 1);
     if (lane == 31) { An = T(1); Bn = T(0); }
     T x = fmx(An, sB[wid], Bn);                   // x_{j1}
-    for (int j = j1 - 1; j >= j0; --j) {
-      x = fmx(-tcp[j], x, out[j]);
-      out[j] = x;
+    if (regs) {
+#pragma unroll
+      for (int q = kCtaRegs - 1; q >= 0; --q) {
+        const int j = j0 + q;
+        if (j < j1) {
+          x = fmx(-tcp[j], x, vr[q]);
+          vr[q] = x;
+          out[j] = x;
+        }
+      }
+    } else {
+      for (int j = j1 - 1; j >= j0; --j) {
+        x = fmx(-tcp[j], x, out[j]);
+        out[j] = x;
+      }
     }
   }
   __syncthreads();

@@ -83,7 +83,8 @@ __device__ __forceinline__ void mass1d_interface(const SurfTables& t, int nrhs, 
 }
 
 // The same solve by a whole CTA (every thread must call it): long systems (N > 32·kTridiagRegs)
-// use the CTA-wide scan, short ones warp 0 alone.
+// use the CTA-wide scan (CACHE: with register-held chunks), short ones warp 0 alone.
+template <bool CACHE = false>
 __device__ __forceinline__ void mass1d_interface_cta(const SurfTables& t, int nrhs, double* __restrict__ scr,
                                                      int rh) {
   const int Nx = t.Nx, N = t.nif;
@@ -98,7 +99,8 @@ __device__ __forceinline__ void mass1d_interface_cta(const SurfTables& t, int nr
     if (t.periodic) return __ldcg(gl + j) + __ldcg(gr + (j == 0 ? Nx - 1 : j - 1));
     return (j < Nx ? __ldcg(gl + j) : 0.0) + (j > 0 ? __ldcg(gr + j - 1) : 0.0);
   };
-  cta_tridiag<double>(N, gfun, t.th_e, t.th_m, t.th_cp, t.periodic != 0, t.th_z, t.th_vlast, t.th_fac, ub);
+  cta_tridiag<double, decltype(gfun), CACHE>(N, gfun, t.th_e, t.th_m, t.th_cp, t.periodic != 0, t.th_z, t.th_vlast,
+                                             t.th_fac, ub);
 }
 
 // Phase 3, column `col` of right-hand side `rh`: interface value or back-substituted interior.
