@@ -713,7 +713,10 @@ __device__ int cg_solve(const DevGeom& g, Smem<P, T>& s, const Range& R, const T
   cg_update<P, T, TP>(g, s, R, tm, pv, PA.precond, V, cur, false, true, T(0), T(0));
   if (!finish_precondition<P, T, TP, CACHE>(g, s, R, tm, PA, pv, V, s_flag)) return -1;
   int k = 0;
-  double inv_gamma_prev = 1.0, inv_alpha_prev = 1.0, rr = 0.0;   // 1/γ and 1/α of the last iteration
+  double rr = 0.0;
+  // 1/γ and 1/α of the last iteration, double-buffered by iteration parity: thread 32 (another SM
+  // sub-partition, so another FP64 pipe) divides for the next iteration while thread 0 divides for α
+  __shared__ double s_inv[2][2];
   while (true) {
     // w = A u and the three inner products (u on owned columns and the halo column)
     const T* rc = V.r[cur];
@@ -745,20 +748,27 @@ __device__ int cg_solve(const DevGeom& g, Smem<P, T>& s, const Range& R, const T
     if (!grid_barrier(tm, s_flag)) return -1;
     double sums[3];
     grid_sum<3>(tm, 2, sums, red);
+    if (threadIdx.x == 32) {
+      const double gam = sums[0], del = sums[1];
+      const double* ip = s_inv[(k + 1) & 1];
+      const double beta = k == 0 ? 0.0 : gam * ip[0];
+      const double den = k == 0 ? del : del - beta * gam * ip[1];
+      const double ig = 1.0 / gam;
+      s_inv[k & 1][0] = ig;
+      s_inv[k & 1][1] = den * ig;
+    }
     if (threadIdx.x == 0) {
       rr = sums[2];
       int stop = 0;
       if (!(rr == rr) || isinf(rr) || !(sums[1] == sums[1])) { atomicOr(g.status, ST_NONFINITE); stop = 1; }
       else if (rr <= target || k >= max_it) stop = 1;
       if (!stop) {
-        // α = γ/(δ − βγ/α_prev): the two divisions of the next iteration's β and γ/α are taken
-        // beside this one (1/γ, and 1/α = den/γ), not after it
+        // α = γ/(δ − βγ/α_prev); thread 32 takes the next iteration's 1/γ and 1/α = den/γ
         const double gam = sums[0], del = sums[1];
-        const double beta = k == 0 ? 0.0 : gam * inv_gamma_prev;
-        const double den = k == 0 ? del : del - beta * gam * inv_alpha_prev;
+        const double* ip = s_inv[(k + 1) & 1];
+        const double beta = k == 0 ? 0.0 : gam * ip[0];
+        const double den = k == 0 ? del : del - beta * gam * ip[1];
         const double alpha = gam / den;
-        inv_gamma_prev = 1.0 / gam;
-        inv_alpha_prev = den * inv_gamma_prev;
         s_scal[0] = (T)alpha;
         s_scal[1] = (T)beta;
       }
