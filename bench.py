@@ -1,20 +1,27 @@
 """Benchmark: Laplace DOF/s and RK4 steps/s of the σ-transformed SEM wave model on GB300.
 
-Workload (one "step"): one classical RK4 step of the steep periodic nonlinear wave
-(64×4 elements, P=6, P_f=9, filter (36,12,P-1), kh=1, H/L=0.08, dt=T/200) —
-four σ-geometry updates, four Dirichlet-lifted Laplace solves (persistent PCG),
-four gradient recoveries, four over-integrated Zakharov right-hand sides, the RK4
-combination and the modal filter, all in the library's CUDA kernels.
+Workload (one "step"): one classical RK4 step of every tank of the uneven batch — 512
+independent periodic tanks from seed 0 (Nx ∈ [16,128], Nz ∈ {1,2,4}, P ∈ {4..8},
+kh ∈ [0.5,3], H/L ∈ [0.01,0.09], 3.18 M Laplace unknowns) — each RK4 step being four
+σ-geometry updates, four Dirichlet-lifted Laplace solves, four gradient recoveries, four
+over-integrated Zakharov right-hand sides, the RK4 combination and the modal filter per tank,
+run as one fused launch per RK stage and (order, precision) group, all in the library's
+CUDA kernels.
 
-value   = Laplace DOF/s = 4 · n_unknowns · steps / device time (FP64 path);
-e2e     = the same metric through sem_rk4_step_host (pinned host buffers,
-          host↔device copies of (η, φ̃) inside the timed region);
-roofline: dominant kernel = the persistent Krylov kernel, FP64-ALU bound;
-cpu_baseline: the CPU oracle on a bounded sample of the same workload.
+value   = Laplace DOF/s of the batched plain FP64 path = 4 · Σ unknowns · steps / device time;
+          the batched mixed-precision path (FP32 inner, FP64 refinement), the same tanks one
+          after another on the plain FP64 single-mesh path, and each path's relative L² error
+          against the CPU oracle on a seeded sample of tanks are reported beside it;
+e2e     = the same metric through sem_batch_rk4_step_host (packed pinned host buffers, the
+          host↔device copies of every tank's (η, φ̃) inside the timed region);
+roofline: the fused stage kernel of the batch, FP64-ALU bound (FP64 Krylov work counted);
+cpu_baseline: the CPU oracle on a bounded sample of the same tanks, on all host cores.
+Extras: the C2 steep wave, the C4 shoal and the C5 request stream (mixed vs FP64, each with
+its error against the oracle), and the operator apply on a long tank (HBM roofline).
 
-`--impl reference` times the CPU oracle itself (the reference arm).  Under
-torchrun each rank runs an independent replica of the tank (weak scaling, no
-data-path collective); rank 0 prints the JSON line.
+`--impl reference` times the CPU oracle itself (the reference arm).  Under torchrun each rank
+runs an independent replica of the batch (weak scaling, no data-path collective); rank 0
+prints the JSON line.
 """
 from __future__ import annotations
 
@@ -32,37 +39,29 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "Laplace DOF/s (RK4 steps/s alongside)"
+METRIC = "Laplace DOF/s (tank RK4 steps/s alongside), batched FP64; mixed precision beside it"
 UNIT = "DOF/s"
-# Algorithmic FP64 work of one Krylov iteration (per-unit figures stated in the design notes):
+C3_NAME = ("C3 512 uneven periodic tanks (seed 0): Nx 16-128, Nz 1/2/4, P 4-8, kh 0.5-3, H/L 0.01-0.09; "
+           "one RK4 step of every tank per step")
+# Algorithmic FP64 work (per-unit figures stated in the design notes):
 #   operator apply: 8(P+1)+7 flops per element-local node (gradients, fluxes, transposed sums)
-#   vector updates and dots: 13 flops per unknown
-#   σ-separable preconditioner: see flops_per_precond
+#   Krylov vector updates and dots: 13 flops per unknown and iteration
+# The σ-separable preconditioner runs in FP32 in both precisions and is not counted.
 FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 rate (vector and tensor alike)
-
-
-def workload():
-    from sem_workloads import c2_steep_periodic
-    return c2_steep_periodic()
-
-
-def flops_per_precond(wl) -> float:
-    """σ-separable preconditioner: two σ-transforms (nr² FMAs per column each), per-(mode,
-    element) condensation and back-substitution ((P−1)² + 4(P−1) FMAs), interface solve."""
-    P, nr = wl.P, wl.nrow - 1
-    nif = wl.Nx if wl.periodic else wl.Nx + 1
-    return 4 * wl.ncol * nr * nr + 2 * nr * wl.Nx * ((P - 1) ** 2 + 4 * (P - 1)) + 6 * nr * nif
-
-
-def flops_per_iteration(wl) -> float:
-    P = wl.P
-    return (wl.Nx * wl.Nz * (P + 1) ** 2 * (8 * (P + 1) + 7) + 13 * wl.n_unknowns
-            + flops_per_precond(wl))
 
 
 def flops_per_apply(wl) -> float:
     P = wl.P
     return wl.Nx * wl.Nz * (P + 1) ** 2 * (8 * (P + 1) + 7)
+
+
+def fp64_solver_flops(wl, solves: int, iterations: int, refinements: int, mixed: bool) -> float:
+    """FP64 algorithmic flops of `solves` Laplace solves: two applies per solve for the lifted
+    right-hand side and the initial residual, one per Krylov iteration with its vector work
+    (plain FP64), or one per refinement (mixed: its inner iterations run in FP32)."""
+    if mixed:
+        return (2 * solves + refinements) * flops_per_apply(wl)
+    return (2 * solves + iterations) * flops_per_apply(wl) + iterations * 13 * wl.n_unknowns
 
 
 def max_over_ranks(value: float, device=None) -> float:
@@ -169,60 +168,123 @@ def profiled_traffic(kernel: str):
 # ---------------------------------------------------------------------------------------------
 # CPU oracle timing (reference arm and cpu_baseline)
 # ---------------------------------------------------------------------------------------------
-def oracle_stage_sample(n_stages: int):
-    """Run n_stages RK4 stages of the oracle on the bench workload; returns (seconds, DOF)."""
+def _oracle_init():
+    """Worker initialiser of the oracle pool (spawned processes, one BLAS thread each)."""
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        os.environ[k] = "1"
+
+
+def oracle_job(job):
+    """One oracle run in a worker: job = (kind, key, eta0, phis0, nsteps, t0) with kind "c3" (key =
+    tank index), "c2", "c4" or "c5" (key = (rate, count, request index)); nsteps = 0 means one
+    Laplace solve (returns Φ).  Returns (key, results, seconds, Laplace unknowns solved)."""
     import numpy as np
     from oracle import sem as osem
-    from sem_workloads import initial_state
-    wl = workload()
-    om = osem.mesh_for(wl)
-    eta, phis = initial_state(wl, om.xcol, om.h)
-    om.surface_mass()
-    om.mass2d()
-    om.laplace_solve(eta, phis)          # RCM ordering and mass factors are set-up, not timed
+    from sem_workloads import c2_steep_periodic, c3_instances, c4_shoal, c5_requests, depth_columns
+    kind, key, eta, phis, nsteps, t = job
+    if kind == "c3":
+        wl = c3_instances(512)[key]
+    elif kind == "c2":
+        wl = c2_steep_periodic()
+    elif kind == "c4":
+        wl = c4_shoal()
+    else:
+        wl = c5_requests(key[0], key[1], 0)[key[2]][2]
+    h = depth_columns(wl, column_positions(wl)) if wl.bathymetry == "shoal" else np.full(wl.ncol, wl.depth)
+    om = osem.mesh_for(wl, h_col=h)
     t0 = time.perf_counter()
-    for _ in range(n_stages):
-        de, dp = om.zakharov_rhs(eta, phis)
-        eta = eta + 0.5 * wl.dt * de
-        phis = phis + 0.5 * wl.dt * dp
-    dt = time.perf_counter() - t0
-    assert np.all(np.isfinite(eta))
-    return dt, n_stages * wl.n_unknowns
+    if nsteps == 0:
+        out = (om.laplace_solve(eta, phis),)
+        dof = wl.n_unknowns
+    else:
+        for _ in range(nsteps):
+            eta, phis = om.rk4_step(eta, phis, wl.dt, t)
+            t += wl.dt
+        out = (eta, phis)
+        dof = 4 * nsteps * wl.n_unknowns
+    return key, out, time.perf_counter() - t0, dof
 
 
-def oracle_subprocess(n_stages: int) -> dict:
-    env = dict(os.environ)
-    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
-        env[k] = "1"
-    env["CUDA_VISIBLE_DEVICES"] = ""
-    code = ("import json,sys; sys.path.insert(0, %r); import bench; "
-            "t, dof = bench.oracle_stage_sample(%d); print(json.dumps({'t': t, 'dof': dof}))" % (ROOT, n_stages))
-    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=900)
-    if out.returncode != 0:
-        raise RuntimeError(out.stderr[-2000:])
-    return json.loads(out.stdout.strip().splitlines()[-1])
+def oracle_pool(n: int):
+    """A pool of `n` spawned oracle processes (safe after CUDA is initialised in this one)."""
+    import multiprocessing as mp
+    names = ("CUDA_VISIBLE_DEVICES", "OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS")
+    env_keep = {k: os.environ.get(k) for k in names}
+    for k in names:
+        os.environ[k] = "" if k == "CUDA_VISIBLE_DEVICES" else "1"
+    try:
+        pool = mp.get_context("spawn").Pool(n, initializer=_oracle_init)
+    finally:
+        for k, v in env_keep.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return pool
+
+
+def c3_sample(count: int, seed: int = 7):
+    """A seeded sample of C3 tank indices (splitmix64 keys, sorted order of the keys)."""
+    from sem_workloads import splitmix64
+    gen = splitmix64(seed)
+    keys = [next(gen) for _ in range(512)]
+    return sorted(range(512), key=lambda i: keys[i])[:count]
+
+
+def c3_initial(i: int):
+    import numpy as np
+    from sem_workloads import c3_instances, initial_state
+    wl = c3_instances(512)[i]
+    return initial_state(wl, column_positions(wl), np.full(wl.ncol, wl.depth))
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
 
 
 def run_reference(args):
+    """Reference arm: the CPU oracle on the headline workload.  One step = one RK4 step of
+    `cores` C3 tanks (a seeded rotation through the 512), one tank per host core, each
+    single-threaded; value = Laplace unknowns solved (4 per tank and step) / wall time."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    wl = workload()
-    # warm-up stages, then K timed stages: one "step" = one RK4 stage (one Laplace solve)
-    oracle_subprocess(max(1, min(args.warmup, 1)))
-    res = oracle_subprocess(args.steps)
-    value = res["dof"] / res["t"]
+    cores = host_cores()
+    order = c3_sample(512)
+    pool = oracle_pool(cores)
+    try:
+        def one(k):
+            idx = [order[(k * cores + j) % 512] for j in range(cores)]
+            jobs = [("c3", i, *c3_initial(i), 1, 0.0) for i in idx]
+            t0 = time.perf_counter()
+            res = pool.map(oracle_job, jobs, chunksize=1)
+            return time.perf_counter() - t0, sum(r[3] for r in res)
+        for k in range(args.warmup):
+            one(k)
+        wall, dof = 0.0, 0
+        for k in range(args.warmup, args.warmup + args.steps):
+            w, d = one(k)
+            wall += w
+            dof += d
+    finally:
+        pool.close()
+        pool.join()
+    value = dof / wall
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * res["t"] / args.steps,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": wl.name, "Nx": wl.Nx, "Nz": wl.Nz, "P": wl.P, "Pf": wl.Pf,
-                   "n_unknowns": wl.n_unknowns, "step": "one RK4 stage of the CPU oracle",
+        "config": {"workload": C3_NAME, "instances": 512, "precision": "fp64",
+                   "step": f"one RK4 step of {cores} of the tanks (seeded rotation) on the CPU oracle",
                    "parallelism": "replicas"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{args.steps} RK4 stages of the C2 tank (one banded-Cholesky "
-                                   f"Laplace solve each), single thread"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{args.steps} steps of {cores} C3 tanks each, one RK4 step (four "
+                                   f"banded-Cholesky Laplace solves) per tank, one process per core, "
+                                   f"nproc = {os.cpu_count()}"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -310,73 +372,170 @@ def apply_roofline(dev, reps: int = 20, Nx: int = 65536, kernels=("fp64_column",
     return out
 
 
-def c3_batch(dev, count: int = 512, steps: int = 3):
-    """C3: uneven periodic tanks (seed 0) stepped together, mixed precision and FP64, against the
-    same tanks stepped one after another on the plain FP64 path.  Laplace DOF/s = 4·Σ unknowns
-    per RK4 step / time; the mixed path is checked against the FP64 batch (≤1e-8 rel)."""
+def rel_l2(a, b) -> float:
+    import numpy as np
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300))
+
+
+def c3_run(dev, prec: str, wls, init, steps: int, warmup: int, keep=(), flush=None, timing=False, clocks=None,
+           world: int = 1):
+    """C3 batch in one precision: `warmup` untimed steps (the state after the first is kept for the
+    tanks in `keep`), then `steps` steps, each timed alone with CUDA events on the stream, L2
+    flushed before each (clocks sampled and library launches counted over the timed steps).
+    Returns (figures, kept states, per-tank counters, stage-launch timing, final states)."""
+    import torch
+    import paper_1512_02548_gb300 as sem
+    meshes = [sem.Mesh.from_workload(wl, precision=prec, tol=1e-13 if prec == "fp64" else 1e-12) for wl in wls]
+    batch = sem.Batch(meshes)
+    etas = [torch.tensor(e, device=dev) for e, _ in init]
+    phis = [torch.tensor(p, device=dev) for _, p in init]
+    dts = [wl.dt for wl in wls]
+    kept = {}
+    for k in range(max(1, warmup)):
+        batch.rk4_step(etas, phis, dts, 1)
+        if k == 0:
+            kept = {i: (etas[i].cpu().numpy(), phis[i].cpu().numpy()) for i in keep}
+    torch.cuda.synchronize()
+    for m in meshes:
+        m.reset_counters()
+    batch.timing()
+    batch.enable_timing(timing)
+    stream = torch.cuda.current_stream()
+    total = 0.0
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    if clocks is not None:
+        clocks.start()
+    launches0 = sem.launch_count()
+    for _ in range(steps):
+        if flush is not None:
+            flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        batch.rk4_step(etas, phis, dts, 1)                 # synchronises (status check)
+        e1.record(stream)
+        e1.synchronize()
+        total += e0.elapsed_time(e1)
+    torch.cuda.synchronize()
+    launches = sem.launch_count() - launches0
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop() if clocks is not None else None
+    batch.enable_timing(False)
+    tm = batch.timing()
+    cnt = [m.counters() for m in meshes]
+    info = batch.info()
+    dof_step = 4 * sum(wl.n_unknowns for wl in wls)
+    ms = total / steps
+    fig = {"ms_per_rk4_step": ms, "laplace_dof_per_s": dof_step / ms * 1e3,
+           "tank_steps_per_s": len(wls) / ms * 1e3, **info, "total_ms": total, "launches": launches,
+           "clocks": clk,
+           "iterations_per_solve": sum(c.iterations for c in cnt) / max(1, sum(c.solves for c in cnt)),
+           "refinements_per_solve": sum(c.refinements for c in cnt) / max(1, sum(c.solves for c in cnt)),
+           "max_rel_residual": max(c.max_rel_residual for c in cnt)}
+    final = [(e.cpu().numpy(), p.cpu().numpy()) for e, p in zip(etas, phis)]
+    batch.close()
+    for m in meshes:
+        m.close()
+    return fig, kept, cnt, tm, final
+
+
+def c3_e2e(dev, wls, init, steps: int, warmup: int):
+    """The batched FP64 step through sem_batch_rk4_step_host: every step copies all tanks' (η, φ̃)
+    from packed pinned host buffers to the device and back (inside the timed region)."""
     import numpy as np
     import torch
     import paper_1512_02548_gb300 as sem
-    from sem_workloads import c3_instances, initial_state
-    wls = c3_instances(count)
-    out = {"instances": count, "unknowns": int(sum(w.n_unknowns for w in wls))}
-    dof_step = 4 * out["unknowns"]
-    init = []
-    for wl in wls:
-        xcol = column_positions(wl)
-        init.append(initial_state(wl, xcol, np.full(wl.ncol, wl.depth)))
+    meshes = [sem.Mesh.from_workload(wl, tol=1e-13) for wl in wls]
+    batch = sem.Batch(meshes)
+    eta_h = torch.tensor(np.concatenate([e for e, _ in init])).pin_memory()
+    phis_h = torch.tensor(np.concatenate([p for _, p in init])).pin_memory()
     dts = [wl.dt for wl in wls]
-    results = {}
-    for prec in ("fp64", "mixed"):
-        meshes = [sem.Mesh.from_workload(wl, precision=prec, tol=1e-13 if prec == "fp64" else 1e-12) for wl in wls]
-        batch = sem.Batch(meshes)
-        etas = [torch.tensor(e, device=dev) for e, _ in init]
-        phis = [torch.tensor(p, device=dev) for _, p in init]
-        batch.rk4_step(etas, phis, dts, 1)                       # warm-up step
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        batch.rk4_step(etas, phis, dts, steps)
-        e1.record()
-        e1.synchronize()
-        ms = e0.elapsed_time(e1) / steps
-        info = batch.info()
-        results[prec] = (etas, phis)
-        out[f"batched_{prec}"] = {"ms_per_rk4_step": ms, "laplace_dof_per_s": dof_step / ms * 1e3,
-                                  "tank_steps_per_s": count / ms * 1e3, **info}
-        batch.close()
-        for m in meshes:
-            m.close()
-    err = max(float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
-              for a, b in zip(results["mixed"][0] + results["mixed"][1], results["fp64"][0] + results["fp64"][1]))
-    out["mixed_vs_fp64_max_rel_l2"] = err
-    # sequential plain FP64: one mesh after another, same steps
+    for _ in range(max(1, warmup)):
+        batch.rk4_step_host(eta_h, phis_h, dts, 1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        batch.rk4_step_host(eta_h, phis_h, dts, 1)
+    wall = time.perf_counter() - t0
+    batch.close()
+    for m in meshes:
+        m.close()
+    return wall, 2 * 8 * int(eta_h.numel())
+
+
+def c3_sequential(dev, wls, init, steps: int):
+    """The same tanks one after another on the plain FP64 single-mesh path (sem_rk4_step)."""
+    import torch
+    import paper_1512_02548_gb300 as sem
     meshes = [sem.Mesh.from_workload(wl) for wl in wls]
     etas = [torch.tensor(e, device=dev) for e, _ in init]
     phis = [torch.tensor(p, device=dev) for _, p in init]
-    for m, e, p, dt in zip(meshes, etas, phis, dts):
-        m.rk4_step(e, p, dt, 1)
+    for m, e, p, wl in zip(meshes, etas, phis, wls):
+        m.rk4_step(e, p, wl.dt, 1)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for m, e, p, dt in zip(meshes, etas, phis, dts):
-        m.rk4_step(e, p, dt, steps)
+    for m, e, p, wl in zip(meshes, etas, phis, wls):
+        m.rk4_step(e, p, wl.dt, steps)
     torch.cuda.synchronize()
     ms = (time.perf_counter() - t0) * 1e3 / steps
-    out["sequential_fp64"] = {"ms_per_rk4_step": ms, "laplace_dof_per_s": dof_step / ms * 1e3}
     for m in meshes:
         m.close()
-    out["mixed_batched_speedup_vs_sequential_fp64"] = out["sequential_fp64"]["ms_per_rk4_step"] / \
-        out["batched_mixed"]["ms_per_rk4_step"]
-    return out
+    return {"ms_per_rk4_step": ms, "laplace_dof_per_s": 4 * sum(wl.n_unknowns for wl in wls) / ms * 1e3}
+
+
+def c2_run(dev, steps: int, warmup: int, flush):
+    """C2 steep periodic wave (64×4, P=6, P_f=9, filter (36,12,5), dt=T/200) on the single-mesh
+    fused path, FP64 and mixed: `steps` RK4 steps each timed with CUDA events (L2 flushed before
+    each), and the state after one step from the initial state for the oracle check."""
+    import numpy as np
+    import torch
+    import paper_1512_02548_gb300 as sem
+    from sem_workloads import c2_steep_periodic, initial_state
+    wl = c2_steep_periodic()
+    h = np.full(wl.ncol, wl.depth)
+    e0, p0 = initial_state(wl, column_positions(wl), h)
+    out = {"workload": wl.name, "unknowns": wl.n_unknowns, "dt": wl.dt}
+    one = {}
+    stream = torch.cuda.current_stream()
+    for prec in ("fp64", "mixed"):
+        m = sem.Mesh.from_workload(wl, h=h, precision=prec)
+        eta, phis = torch.tensor(e0, device=dev), torch.tensor(p0, device=dev)
+        m.rk4_step(eta, phis, wl.dt, 1)
+        one[prec] = (eta.cpu().numpy(), phis.cpu().numpy())
+        for _ in range(warmup - 1):
+            m.rk4_step(eta, phis, wl.dt, 1)
+        torch.cuda.synchronize()
+        m.reset_counters()
+        total = 0.0
+        for _ in range(steps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            m.rk4_step(eta, phis, wl.dt, 1)
+            b.record(stream)
+            b.synchronize()
+            total += a.elapsed_time(b)
+        c = m.counters()
+        ms = total / steps
+        out[prec] = {"ms_per_rk4_step": ms, "rk4_steps_per_s": 1e3 / ms,
+                     "laplace_dof_per_s": 4 * wl.n_unknowns / ms * 1e3,
+                     "iterations_per_solve": c.iterations / max(c.solves, 1),
+                     "refinements_per_solve": c.refinements / max(c.solves, 1)}
+        m.close()
+    out["mixed_over_fp64"] = out["mixed"]["laplace_dof_per_s"] / out["fp64"]["laplace_dof_per_s"]
+    return out, (e0, p0), one
 
 
 def c4_shoal_run(dev, spinup: int = 600, steps: int = 100):
     """C4: JONSWAP waves generated over the synthetic shoal (2048×2, P=6, walls, relaxation
     zones), FP64 and mixed precision.  `spinup` untimed steps from rest let the generated
     waves fill the first part of the tank; then `steps` RK4 steps are timed with CUDA events.
-    The two precisions are compared at the end (relative L2 of η and φ̃)."""
-    import numpy as np
+    For the oracle check, one more step of each precision starts from the FP64 spun-up state."""
     import torch
     import paper_1512_02548_gb300 as sem
     from sem_workloads import c4_shoal, depth_columns
@@ -384,11 +543,14 @@ def c4_shoal_run(dev, spinup: int = 600, steps: int = 100):
     h = depth_columns(wl, column_positions(wl))
     out = {"workload": wl.name, "unknowns": wl.n_unknowns, "dt": wl.dt, "spinup_steps": spinup, "steps": steps}
     res = {}
+    start = None
     for prec in ("fp64", "mixed"):
         m = sem.Mesh.from_workload(wl, h=h, precision=prec, tol=1e-13 if prec == "fp64" else 1e-12)
         eta = torch.zeros(wl.ncol, dtype=torch.float64, device=dev)
         phis = torch.zeros_like(eta)
         t = m.rk4_step(eta, phis, wl.dt, spinup, t=0.0)
+        if prec == "fp64":
+            start = (eta.cpu().numpy(), phis.cpu().numpy(), t)
         m.reset_counters()
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -407,45 +569,67 @@ def c4_shoal_run(dev, spinup: int = 600, steps: int = 100):
         m.close()
     out["mixed_vs_fp64_rel_l2"] = max(float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
                                       for a, b in zip(res["mixed"], res["fp64"]))
+    out["mixed_over_fp64"] = out["mixed"]["rk4_steps_per_s"] / out["fp64"]["rk4_steps_per_s"]
     out["max_abs_eta"] = float(res["fp64"][0].abs().max())
-    return out
+    one = {}
+    for prec in ("fp64", "mixed"):
+        m = sem.Mesh.from_workload(wl, h=h, precision=prec, tol=1e-13 if prec == "fp64" else 1e-12)
+        eta = torch.tensor(start[0], device=dev)
+        phis = torch.tensor(start[1], device=dev)
+        m.rk4_step(eta, phis, wl.dt, 1, t=start[2])
+        one[prec] = (eta.cpu().numpy(), phis.cpu().numpy())
+        m.close()
+    return out, start, one
 
 
-def c5_serving(rates=(100.0, 1000.0), count: int = 300):
+def c5_serving(rates=(100.0, 1000.0), count: int = 1000, sample: int = 4):
     """C5: Poisson streams of Laplace solves and 10-step RK4 runs (seed 0) served by the
     continuous-batching loop in mixed precision (150 GB admission budget), against the same
     requests run one after another on the plain FP64 single-instance path.  Wall-clock from
-    the first arrival; latency = completion − arrival.  One rate below the loop's capacity and
-    one above it."""
+    the first arrival; latency = completion − arrival.  The served results of a seeded sample
+    of small requests at the first rate are kept for the oracle check."""
     import numpy as np
     from paper_1512_02548_gb300.serve import GpuExecutor, Request, Server, sequential
-    from sem_workloads import c5_requests, initial_state
+    from sem_workloads import c5_requests, initial_state, splitmix64
     keys = ("p50_ms", "p99_ms", "laplace_dof_per_s", "rk4_steps_per_s", "requests_per_s", "wall_s", "completed",
             "failed")
     out = {"requests_per_rate": count, "budget_gb": 150}
     warm = True
-    for rate in rates:
+    checks = []
+    for ri, rate in enumerate(rates):
+        stream = c5_requests(rate, count, 0)
         base = []
-        for i, (kind, t, wl, ns) in enumerate(c5_requests(rate, count, 0)):
+        for i, (kind, t, wl, ns) in enumerate(stream):
             e0, p0 = initial_state(wl, column_positions(wl), np.full(wl.ncol, wl.depth))
             base.append(Request(i, kind, wl, e0, p0, ns, t))
 
         def fresh():
             return [Request(r.rid, r.kind, r.wl, r.eta0, r.phis0, r.nsteps, r.arrival) for r in base]
 
+        keep = set()
+        if ri == 0:
+            gen = splitmix64(11)
+            small = sorted((r.rid for r in base if r.wl.n_nodes <= 12000), key=lambda i: next(gen))
+            lap = [i for i in small if base[i].kind == "laplace"][: sample // 2]
+            rk = [i for i in small if base[i].kind == "rk4"][: sample - len(lap)]
+            keep = set(lap + rk)
         if warm:
             Server(GpuExecutor("mixed"), 150 << 30).run(fresh()[:8])      # warm-up (module loading)
             warm = False
         ent = {"laplace_share": sum(r.kind == "laplace" for r in base) / count,
                "nodes_total": int(sum(r.wl.n_nodes for r in base))}
-        s = Server(GpuExecutor("mixed"), 150 << 30, keep_results=False).run(fresh())
+        reqs = fresh()
+        s = Server(GpuExecutor("mixed"), 150 << 30, keep_results=keep).run(reqs)
         ent["served_mixed"] = {k: s[k] for k in keys + ("ticks", "peak_active")}
+        for r in reqs:
+            if r.rid in keep and r.error is None:
+                checks.append((rate, count, r.rid, r.kind, r.eta0, r.phis0, r.nsteps, r.result))
         s = sequential(fresh(), "fp64")
         ent["sequential_fp64"] = {k: s[k] for k in keys}
         ent["served_mixed_dof_speedup_vs_sequential_fp64"] = (ent["served_mixed"]["laplace_dof_per_s"] /
                                                               ent["sequential_fp64"]["laplace_dof_per_s"])
         out[f"rate_{int(rate)}_per_s"] = ent
-    return out
+    return out, checks
 
 
 def measured_peaks() -> dict:
@@ -463,7 +647,7 @@ def run_gpu(args):
     import torch
 
     import paper_1512_02548_gb300 as sem
-    from sem_workloads import initial_state
+    from sem_workloads import c3_instances
 
     rank, world, local = dist_env()
     if world > 1:
@@ -472,127 +656,162 @@ def run_gpu(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     sem.load_library()
+    lead = rank == 0
+    check = lead and world == 1 and not args.no_oracle
 
-    wl = workload()
-    # column positions need GLL nodes; take them from a throw-away oracle-free formula:
-    # the library only needs edges and depth, initial data are sampled at the columns.
-    h = np.full(wl.ncol, wl.depth)
-    mesh = sem.Mesh.from_workload(wl, h=h, precision=args.precision)
-    xcol = column_positions(wl)
-    eta0, phis0 = initial_state(wl, xcol, h)
-    eta = torch.tensor(eta0, device=dev)
-    phis = torch.tensor(phis0, device=dev)
+    wls = c3_instances(512)
+    init = [c3_initial(i) for i in range(512)]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > 129 MB L2
-    stream = torch.cuda.current_stream()
+    sample = c3_sample(max(args.oracle_tanks, 2 * host_cores())) if check else []
+    dof_step = 4 * sum(wl.n_unknowns for wl in wls)
 
-    for _ in range(args.warmup):
-        mesh.rk4_step(eta, phis, wl.dt, 1)
-    torch.cuda.synchronize()
-    mesh.reset_counters()
-    mesh.timing()                                   # discard
-    mesh.enable_timing(True)
-    launches0 = sem.launch_count()
+    # ---- headline: C3 batched plain FP64 --------------------------------------------------
     clocks = ClockSampler(local)
-    clocks.start()
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    total_ms = 0.0
-    for _ in range(args.steps):
-        flush.zero_()                               # evict L2 between timed steps (not timed)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        mesh.rk4_step(eta, phis, wl.dt, 1)          # synchronises at its end (status check)
-        e1.record(stream)
-        e1.synchronize()
-        total_ms += e0.elapsed_time(e1)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    clk = clocks.stop()
-    gpu_launches = sem.launch_count() - launches0
-    mesh.enable_timing(False)
-    tm = mesh.timing()
-    cnt = mesh.counters()
-    t_max = max_over_ranks(total_ms, dev)
-    dof_per_step = 4 * wl.n_unknowns
-    value = job_throughput(world, args.steps, dof_per_step, t_max)
-    steps_per_s = job_throughput(world, args.steps, 1, t_max)
+    f64, kept64, cnt64, tm64, _ = c3_run(dev, "fp64", wls, init, args.steps, args.warmup, keep=sample,
+                                         flush=flush, timing=True, clocks=clocks, world=world)
+    t_max = max_over_ranks(f64["total_ms"], dev)
+    value = job_throughput(world, args.steps, dof_step, t_max)
+    tank_steps = job_throughput(world, args.steps, len(wls), t_max)
+    mix, keptmx, cntmx, tmmx, _ = c3_run(dev, "mixed", wls, init, args.steps, args.warmup, keep=sample,
+                                         flush=flush, timing=True, world=world)
+    seq = c3_sequential(dev, wls, init, max(1, min(2, args.steps))) if lead else None
 
-    # roofline of the dominant kernel: the fused RK-stage kernel (Laplace solve inside), FP64 ALU
-    # bound; its algorithmic work is counted from the Krylov part only (a lower bound)
-    solves = max(cnt.solves, 1)
-    # per solve: 2 FP64 applies for r0 and b, one preconditioner application per start
-    # (1 in FP64, one per refinement in mixed), one FP64 apply per refinement
-    extra_applies = 2 * cnt.solves + cnt.refinements
-    starts = cnt.refinements if args.precision == "mixed" else cnt.solves
-    flops = (cnt.iterations * flops_per_iteration(wl) + extra_applies * flops_per_apply(wl)
-             + starts * flops_per_precond(wl))
-    avg_launch_ms = tm.krylov_ms / max(tm.krylov_launches, 1)
-    flops_per_launch = flops / max(tm.krylov_launches, 1)
-    achieved = flops_per_launch / (avg_launch_ms / 1e3) / 1e12
-    krylov_share = tm.krylov_ms / total_ms if total_ms > 0 else None
+    # roofline of the batched fused stage kernel: FP64 Krylov work per launch / event-timed launch
+    flops = sum(fp64_solver_flops(wl, c.solves, c.iterations, c.refinements, False) for wl, c in zip(wls, cnt64))
+    launches = max(tm64.krylov_launches, 1)
+    avg_launch_ms = tm64.krylov_ms / launches
+    achieved = flops / launches / (avg_launch_ms / 1e3) / 1e12
+    flops_mx = sum(fp64_solver_flops(wl, c.solves, c.iterations, c.refinements, True) for wl, c in zip(wls, cntmx))
 
-    # end to end through the host-buffer entry point
-    he = torch.tensor(eta0).pin_memory().numpy()
-    hp = torch.tensor(phis0).pin_memory().numpy()
-    for _ in range(2):
-        mesh.rk4_step_host(he, hp, wl.dt, 1)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        mesh.rk4_step_host(he, hp, wl.dt, 1)
-    e2e_s = max_over_ranks(time.perf_counter() - t0, dev)
-    e2e = {"value": job_throughput(world, args.steps, dof_per_step, 1e3 * e2e_s), "unit": UNIT,
-           "h2d_bytes_per_step": 2 * 8 * wl.ncol, "d2h_bytes_per_step": 2 * 8 * wl.ncol}
+    # end to end through the host-buffer batch call
+    e2e_wall, e2e_bytes = c3_e2e(dev, wls, init, args.steps, args.warmup)
+    e2e_s = max_over_ranks(e2e_wall, dev)
+    e2e = {"value": job_throughput(world, args.steps, dof_step, 1e3 * e2e_s), "unit": UNIT,
+           "h2d_bytes_per_step": e2e_bytes, "d2h_bytes_per_step": e2e_bytes,
+           "call": "sem_batch_rk4_step_host (packed pinned host buffers)"}
+
+    c3 = {"instances": len(wls), "unknowns": dof_step // 4,
+          "batched_fp64": {k: v for k, v in f64.items() if k not in ("total_ms", "clocks")},
+          "batched_mixed": {k: v for k, v in mix.items() if k not in ("total_ms", "clocks")},
+          "sequential_fp64": seq,
+          "mixed_over_batched_fp64": mix["laplace_dof_per_s"] / f64["laplace_dof_per_s"],
+          "mixed_over_sequential_fp64": (mix["laplace_dof_per_s"] / seq["laplace_dof_per_s"]) if seq else None,
+          "batched_fp64_over_sequential_fp64": (f64["laplace_dof_per_s"] / seq["laplace_dof_per_s"]) if seq else None,
+          "fp64_work_per_launch_mflop": {"fp64": flops / launches / 1e6,
+                                         "mixed": flops_mx / max(tmmx.krylov_launches, 1) / 1e6},
+          "stage_launch_ms": {"fp64": avg_launch_ms, "mixed": tmmx.krylov_ms / max(tmmx.krylov_launches, 1)}}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
-        "data": "synthetic",
-        "config": {"workload": wl.name, "Nx": wl.Nx, "Nz": wl.Nz, "P": wl.P, "Pf": wl.Pf,
-                   "n_unknowns": wl.n_unknowns, "dt": wl.dt, "precision": args.precision,
-                   "l2": "flushed between timed steps (256 MB write, untimed)",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": C3_NAME, "instances": len(wls), "n_unknowns": dof_step // 4, "precision": "fp64",
+                   "tol": "relative residual 1e-13 (FP64), 1e-12 with refinement (mixed)",
+                   "l2": "flushed between timed steps (256 MB write, untimed); working set above L2",
                    "parallelism": "replicas" if world > 1 else "single"},
-        "rk4_steps_per_s": steps_per_s,
-        "krylov": {"solves": cnt.solves, "iterations_per_solve": cnt.iterations / solves,
-                   "refinements": cnt.refinements, "max_rel_residual": cnt.max_rel_residual,
-                   "stage_kernel_share_of_step_time": krylov_share},
-        "roofline": {"bound": "alu", "kernel": "k_stage (fused RK stage, Krylov work counted)",
-                     "achieved": achieved,
-                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                     "peak_source": "nominal GB300 FP64 rate, 1.25 TFLOP/s",
-                     "traffic": profiled_traffic("k_stage")},
+        "rk4_steps_per_s": tank_steps,
+        "mixed": {"value": mix["laplace_dof_per_s"] * world, "dtype": "f32+f64",
+                  "over_batched_fp64": c3["mixed_over_batched_fp64"],
+                  "over_sequential_fp64": c3["mixed_over_sequential_fp64"],
+                  "tank_steps_per_s": mix["tank_steps_per_s"] * world},
+        "c3_uneven_batch": c3,
+        "roofline": {"bound": "alu", "kernel": "k_stage, batched build (fused RK stage; FP64 Krylov work counted: "
+                                               "applies and vector updates, FP32 preconditioner left out)",
+                     "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP64_PEAK_TFLOPS,
+                     "peak_source": "nominal GB300 FP64 rate, 1.25 TFLOP/s (no measured FP64 peak)",
+                     "launches": tm64.krylov_launches, "avg_launch_ms": avg_launch_ms,
+                     "flops_per_launch": flops / launches,
+                     "traffic": profiled_traffic("k_stage_batch")},
         "e2e": e2e,
-        "gpu_launches": gpu_launches,
-        "clocks": clk,
+        "gpu_launches": f64["launches"],
+        "clocks": f64["clocks"],
     }
-    if not args.no_apply_roofline:
+
+    extras = {}
+    if lead and not args.no_c2:
+        c2, c2_init, c2_one = c2_run(dev, args.steps, args.warmup, flush)
+        line["c2_steep_wave"] = c2
+        extras["c2"] = (c2_init, c2_one)
+    if lead and not args.no_c4:
+        c4, c4_start, c4_one = c4_shoal_run(dev)
+        line["c4_shoal"] = c4
+        extras["c4"] = (c4_start, c4_one)
+    if lead and not args.no_c5:
+        c5, c5_checks = c5_serving(tuple(args.c5_rates), args.c5_requests)
+        line["c5_serving"] = c5
+        extras["c5"] = c5_checks
+    if lead and not args.no_apply_roofline:
         line["apply_long_tank"] = apply_roofline(dev)
-    if not args.no_c3:
-        line["c3_uneven_batch"] = c3_batch(dev)
-    if not args.no_c4:
-        line["c4_shoal"] = c4_shoal_run(dev)
-    if not args.no_c5:
-        line["c5_serving"] = c5_serving(tuple(args.c5_rates), args.c5_requests)
-    if rank == 0 and not args.no_cpu_baseline:
-        try:
-            res = oracle_subprocess(args.cpu_stages)
-            line["cpu_baseline"] = {"value": res["dof"] / res["t"], "unit": UNIT, "cores": 1, "kind": "oracle",
-                                    "sample": f"{args.cpu_stages} RK4 stages of the same tank (one banded-"
-                                              f"Cholesky Laplace solve each), single thread, "
-                                              f"{res['t']:.1f} s"}
-        except Exception as e:  # the GPU number stands on its own
-            line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                    "sample": f"failed: {str(e)[-200:]}"}
-    if rank == 0:
+
+    if check:
+        oracle_checks(line, sample, init, kept64, keptmx, extras)
+    if world > 1:
+        dist.barrier()
+    if lead:
         print(json.dumps(line))
-    mesh.close()
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def oracle_checks(line, sample, init, kept64, keptmx, extras):
+    """The CPU oracle on all host cores: one RK4 step of each sampled C3 tank (timed: the
+    cpu_baseline), then the oracle runs behind the C2, C4 and C5 error figures.  Each GPU
+    result's relative L² error against the oracle is added to its section."""
+    import numpy as np
+    cores = host_cores()
+    pool = oracle_pool(cores)
+    try:
+        jobs = [("c3", i, init[i][0], init[i][1], 1, 0.0) for i in sample]
+        t0 = time.perf_counter()
+        res = pool.map(oracle_job, jobs, chunksize=1)
+        wall = time.perf_counter() - t0
+        dof = sum(r[3] for r in res)
+        cpu_s = sum(r[2] for r in res)
+        err64 = max(max(rel_l2(kept64[i][0], r[1][0]), rel_l2(kept64[i][1], r[1][1])) for i, r in zip(sample, res))
+        errmx = max(max(rel_l2(keptmx[i][0], r[1][0]), rel_l2(keptmx[i][1], r[1][1])) for i, r in zip(sample, res))
+        line["cpu_baseline"] = {"value": dof / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"one RK4 step (four banded-Cholesky Laplace solves) of each of {len(sample)} "
+                                          f"seeded C3 tanks, one process per core on {cores} cores (nproc = "
+                                          f"{os.cpu_count()}): {wall:.1f} s wall, {cpu_s:.1f} s of CPU work"}
+        c3 = line["c3_uneven_batch"]
+        c3["oracle_check"] = {"tanks": list(sample), "steps": 1, "fp64_max_rel_l2": err64, "mixed_max_rel_l2": errmx,
+                              "tolerance": {"fp64": 1e-10, "mixed": 1e-8}}
+        line["mixed"]["max_rel_l2_vs_oracle"] = errmx
+        line["max_rel_l2_vs_oracle"] = err64
+        pending = []
+        if "c2" in extras:
+            (e0, p0), one = extras["c2"]
+            pending.append(("c2", pool.apply_async(oracle_job, (("c2", 0, e0, p0, 1, 0.0),)), one))
+        if "c4" in extras:
+            (e0, p0, t), one = extras["c4"]
+            pending.append(("c4", pool.apply_async(oracle_job, (("c4", 0, e0, p0, 1, t),)), one))
+        for rate, count, rid, kind, e0, p0, ns, result in extras.get("c5", []):
+            pending.append((("c5", kind, rid),
+                            pool.apply_async(oracle_job, (("c5", (rate, count, rid), e0, p0, ns, 0.0),)), result))
+        c5err = []
+        for tag, fut, gpu in pending:
+            _, ref, _, _ = fut.get()
+            if tag == "c2":
+                sec = line["c2_steep_wave"]
+                for prec in ("fp64", "mixed"):
+                    sec[prec]["rel_l2_vs_oracle_one_step"] = max(rel_l2(gpu[prec][0], ref[0]), rel_l2(gpu[prec][1], ref[1]))
+            elif tag == "c4":
+                sec = line["c4_shoal"]
+                for prec in ("fp64", "mixed"):
+                    sec[prec]["rel_l2_vs_oracle_one_step"] = max(rel_l2(gpu[prec][0], ref[0]), rel_l2(gpu[prec][1], ref[1]))
+                sec["oracle_check"] = "one RK4 step from the FP64 state after the spin-up"
+            else:
+                err = rel_l2(gpu["Phi"], ref[0]) if tag[1] == "laplace" else \
+                    max(rel_l2(gpu["eta"], ref[0]), rel_l2(gpu["phis"], ref[1]))
+                c5err.append({"request": tag[2], "kind": tag[1], "rel_l2_vs_oracle": err})
+        if c5err:
+            line["c5_serving"]["oracle_check"] = {"served_mixed": c5err,
+                                                  "max_rel_l2": max(e["rel_l2_vs_oracle"] for e in c5err)}
+    finally:
+        pool.close()
+        pool.join()
 
 
 def column_positions(wl):
@@ -619,15 +838,14 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
-    ap.add_argument("--cpu-stages", type=int, default=8)
-    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--oracle-tanks", type=int, default=16, help="C3 tanks checked against the oracle (at least)")
+    ap.add_argument("--no-oracle", action="store_true", help="skip the oracle checks and the cpu_baseline")
     ap.add_argument("--no-apply-roofline", action="store_true")
-    ap.add_argument("--no-c3", action="store_true")
+    ap.add_argument("--no-c2", action="store_true")
     ap.add_argument("--no-c4", action="store_true")
     ap.add_argument("--no-c5", action="store_true")
     ap.add_argument("--c5-rates", type=float, nargs="+", default=[100.0, 1000.0])
-    ap.add_argument("--c5-requests", type=int, default=300)
+    ap.add_argument("--c5-requests", type=int, default=1000)
     ap.add_argument("--apply-only", default=None,
                     help="comma list of fp64_column,fp64_tile,fp32_tile: time only these applies (for profiling)")
     ap.add_argument("--apply-nx", type=int, default=65536)

@@ -168,20 +168,21 @@ int sem_laplace_apply(sem_mesh* m, const double* x_d, double* y_d, void* stream)
 int sem_laplace_apply_f32(const sem_mesh* m, const float* x_d, float* y_d, void* stream);
 
 /* Allocation-free form of sem_laplace_apply (the paper has no counterpart; this is a
- * service of the library).  For callers that may not allocate device memory at the time
- * of the call: code recording a CUDA graph by stream capture (allocation is not allowed
- * inside a capture), real-time loops that forbid allocator calls, and hosts whose own
- * memory manager owns the device and rejects raw cudaMalloc.  It computes y = 𝓛x
- * exactly as sem_laplace_apply does, for the last sem_update_geometry, but touches no
- * workspace of the mesh and calls no allocator: y receives partial sums first, and the
- * one temporary the apply needs (the shared x-interface column of every element column,
- * Nx·Nrow values) lives in a static device array of 2^20 doubles (8 MiB) that every
- * device which loads the library holds until the process exits.  Nx·Nrow above 2^20 is
- * rejected with SEM_ERR_INVALID_ARG.  The first call on a device looks up the array's
- * device address; make that first call before any stream capture.  All calls on a
- * device share the array, so calls that can overlap on the GPU (other streams, other
- * meshes) race and must be serialised by the caller.  x_d, y_d: device, n values, must
- * not overlap. */
+ * service of the library).  For callers that must not allocate device memory at the time
+ * of the call: real-time or latency-bound loops that forbid allocator calls (cudaMalloc
+ * and cudaFree can synchronise the device and take unbounded time), and hosts whose own
+ * memory manager owns the device's memory (a caching allocator that has reserved it, so a
+ * raw cudaMalloc fails or fragments its pool).  It computes y = 𝓛x exactly as
+ * sem_laplace_apply does, for the last sem_update_geometry, but touches no workspace of the
+ * mesh and calls no allocator: y receives partial sums first, and the one temporary the
+ * apply needs (the shared x-interface column of every element column, Nx·Nrow values) lives
+ * in a static device array of 2^20 doubles (8 MiB) that every device which loads the library
+ * holds until the process exits.  Nx·Nrow above 2^20 is rejected with SEM_ERR_INVALID_ARG.
+ * The first call on a device (and the first after that device's context was reset) looks up
+ * the array's device address.  All calls on a device share the array and it keeps the last
+ * call's contents (every entry a call reads is written earlier in that call, so nothing needs
+ * clearing); calls that can overlap on the GPU (other streams, other meshes) race on it and
+ * must be serialised by the caller.  x_d, y_d: device, n values, must not overlap. */
 int sem_laplace_apply_noalloc(const sem_mesh* m, const double* x_d, double* y_d, void* stream);
 
 /* Laplace problem of eq. (laplaceproblem) for the last sem_update_geometry:
@@ -273,6 +274,14 @@ int sem_batch_rk4_step(sem_batch* b, double* const* eta_d, double* const* phis_d
  * instance's error is returned (its index in the message). */
 int sem_batch_laplace_solve(sem_batch* b, const double* const* eta_d, const double* const* phis_d,
                             double* const* Phi_d, void* stream);
+/* As sem_batch_rk4_step for callers holding every instance's state in host memory (pinned
+ * memory recommended): eta_h and phis_h are packed, instance i's Ncol_i values following those
+ * of instances 0..i-1 (Σ Ncol_i values each).  Two host→device copies, the steps, two
+ * device→host copies, on `stream`, into a packed device copy that the batch owns.  Synchronises.
+ * The state of every instance comes back, a failed instance's included (sem_batch_status says
+ * which failed); the first failing instance's error is returned. */
+int sem_batch_rk4_step_host(sem_batch* b, double* eta_h, double* phis_h, double* t_h, const double* dt_h,
+                            int nsteps, void* stream);
 /* Per-instance result of the last sem_batch_rk4_step or sem_batch_laplace_solve:
  * codes_h[i] (host, one per instance) = SEM_OK or the instance's own error code, so a caller
  * can fail one instance and keep the others (each instance's state is advanced or solved
@@ -293,6 +302,21 @@ typedef struct sem_timing {
 } sem_timing;
 int sem_enable_timing(sem_mesh* m, int on);
 int sem_get_timing(sem_mesh* m, sem_timing* t);
+
+/* The same timing for the fused stage launches of a batch (one record per (order, precision)
+ * group and stage). */
+int sem_batch_enable_timing(sem_batch* b, int on);
+int sem_batch_get_timing(sem_batch* b, sem_timing* t);
+
+/* Testing hook for the bounded team barriers (a barrier that gives up reports
+ * SEM_ERR_TIMEOUT).  Every wait of a team barrier is limited to timeout_ms of wall-clock
+ * time (0: the default, 2000 ms; at most 2000).  drop_rank ≥ 0 makes the CTA of that rank in the
+ * mesh's team return at the start of each later Krylov or fused stage launch of this mesh (alone
+ * or in a batch), before its first barrier, so that the other CTAs' waits run out: the launch
+ * ends within about timeout_ms, the status word carries the timeout and the next synchronising
+ * call returns SEM_ERR_TIMEOUT.  A team of one CTA has no barrier to miss (drop_rank 0 then
+ * skips the work, with no error).  drop_rank = -1 restores normal launches. */
+int sem_set_barrier_test(sem_mesh* m, int drop_rank, double timeout_ms);
 
 /* Number of kernels this library has launched in the calling process. */
 int64_t sem_launch_count(void);

@@ -31,7 +31,9 @@ EXPORTED = ("sem_mesh_create", "sem_mesh_destroy", "sem_trim_cache", "sem_mesh_f
             "sem_recover_gradient", "sem_zakharov_rhs", "sem_set_wave_input", "sem_apply_filter", "sem_rk4_step",
             "sem_rk4_step_host", "sem_get_counters", "sem_reset_counters", "sem_enable_timing",
             "sem_get_timing", "sem_batch_create", "sem_batch_destroy", "sem_batch_info",
-            "sem_batch_rk4_step", "sem_batch_laplace_solve", "sem_batch_status", "sem_launch_count", "sem_last_error")
+            "sem_batch_rk4_step", "sem_batch_rk4_step_host", "sem_batch_laplace_solve", "sem_batch_status",
+            "sem_batch_enable_timing", "sem_batch_get_timing", "sem_set_barrier_test", "sem_launch_count",
+            "sem_last_error")
 
 
 class sem_params(ctypes.Structure):
@@ -107,7 +109,12 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sem_batch_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     lib.sem_batch_rk4_step.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_double), ip, vp]
+    lib.sem_batch_rk4_step_host.argtypes = [vp, dp, dp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                            ip, vp]
     lib.sem_batch_laplace_solve.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
+    lib.sem_batch_enable_timing.argtypes = [vp, ip]
+    lib.sem_batch_get_timing.argtypes = [vp, ctypes.POINTER(sem_timing)]
+    lib.sem_set_barrier_test.argtypes = [vp, ip, ctypes.c_double]
     lib.sem_batch_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     lib.sem_launch_count.restype = ctypes.c_int64
     lib.sem_launch_count.argtypes = []
@@ -308,6 +315,11 @@ class Mesh:
         _check(load_library().sem_get_timing(self._h, ctypes.byref(t)))
         return t
 
+    def set_barrier_test(self, drop_rank: int = -1, timeout_ms: float = 0.0):
+        """Testing hook (sem_set_barrier_test): shorten the team barrier limit and make one CTA
+        leave the next launches before its first barrier; (-1, 0) restores normal launches."""
+        _check(load_library().sem_set_barrier_test(self._h, int(drop_rank), ctypes.c_double(timeout_ms)))
+
 
 class Batch:
     """Many meshes stepped or solved together (``sem_batch``): one fused launch per RK stage and order."""
@@ -333,6 +345,31 @@ class Batch:
         t = (ctypes.c_double * n)(*(ts if ts is not None else [0.0] * n))
         _check(load_library().sem_batch_rk4_step(self._h, e, p, t, d, int(nsteps), _stream()))
         return list(t)
+
+    def rk4_step_host(self, eta_h, phis_h, dts, nsteps: int = 1, ts=None):
+        """sem_batch_rk4_step_host: eta_h, phis_h are packed host float64 arrays (instance i's
+        columns after those of instances 0..i-1), numpy or pinned CPU tensors, updated in place."""
+        def hp(a):
+            if isinstance(a, np.ndarray):
+                if a.dtype != np.float64 or not a.flags.c_contiguous:
+                    raise ValueError("expected a contiguous float64 array")
+                return a.ctypes.data_as(ctypes.c_void_p)
+            return ctypes.c_void_p(a.data_ptr())
+        n = len(self.meshes)
+        d = (ctypes.c_double * n)(*dts)
+        t = (ctypes.c_double * n)(*(ts if ts is not None else [0.0] * n))
+        _check(load_library().sem_batch_rk4_step_host(self._h, hp(eta_h), hp(phis_h), t, d, int(nsteps),
+                                                      _stream()))
+        return list(t)
+
+    def enable_timing(self, on: bool = True):
+        _check(load_library().sem_batch_enable_timing(self._h, int(bool(on))))
+
+    def timing(self) -> sem_timing:
+        """Launches and summed device time (ms) of the stage launches since the last call."""
+        t = sem_timing()
+        _check(load_library().sem_batch_get_timing(self._h, ctypes.byref(t)))
+        return t
 
     def laplace_solve(self, etas, phises, Phis):
         """One Laplace solve per instance (geometry rebuilt for etas[i]); Phis[i] in/out."""

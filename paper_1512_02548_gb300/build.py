@@ -36,20 +36,23 @@ def _run(cmd):
     return res.stdout + res.stderr
 
 
-def build_library(verbose: bool = False, ptxas_info: bool = False) -> str:
+def build_library(verbose: bool = False, ptxas_info: bool = False, defines=(), lib_path: str = LIB,
+                  build_dir: str = BUILD) -> str:
+    """Compile and link the library.  `defines` (e.g. ["SEM_TRACE"]) builds a diagnostic variant,
+    normally with its own `lib_path` and `build_dir`."""
     nvcc = _nvcc()
-    os.makedirs(BUILD, exist_ok=True)
-    inc = ["-I", CSRC, "-I", os.path.join(os.path.dirname(HERE), "include")]
+    os.makedirs(build_dir, exist_ok=True)
+    inc = ["-I", CSRC, "-I", os.path.join(os.path.dirname(HERE), "include")] + [f"-D{d}" for d in defines]
     jobs = []
     for src in CU_SOURCES:
-        obj = os.path.join(BUILD, src + ".o")
+        obj = os.path.join(build_dir, src + ".o")
         cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                "--expt-relaxed-constexpr", *inc, "-c", os.path.join(CSRC, src), "-o", obj]
         if ptxas_info:
             cmd.insert(1, "-Xptxas=-v")
         jobs.append((cmd, obj))
     for P in ORDERS:
-        obj = os.path.join(BUILD, f"kernels_order_p{P}.o")
+        obj = os.path.join(build_dir, f"kernels_order_p{P}.o")
         cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                "--expt-relaxed-constexpr", f"-DSEM_ORDER={P}", *inc, "-c",
                os.path.join(CSRC, "kernels_order.cu"), "-o", obj]
@@ -57,7 +60,7 @@ def build_library(verbose: bool = False, ptxas_info: bool = False) -> str:
             cmd.insert(1, "-Xptxas=-v")
         jobs.append((cmd, obj))
     for src in CXX_SOURCES:
-        obj = os.path.join(BUILD, src + ".o")
+        obj = os.path.join(build_dir, src + ".o")
         cmd = ["g++", "-O2", "-std=c++17", "-fPIC", *inc, "-c", os.path.join(CSRC, src), "-o", obj]
         jobs.append((cmd, obj))
     with ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
@@ -66,10 +69,10 @@ def build_library(verbose: bool = False, ptxas_info: bool = False) -> str:
         for o in outs:
             if o.strip():
                 print(o)
-    tmp = LIB + ".tmp"
+    tmp = lib_path + ".tmp"
     _run([nvcc, *ARCH, "-shared", "-o", tmp, *[o for _, o in jobs], "-lcudart_static", "-lrt", "-ldl", "-lpthread"])
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":

@@ -8,6 +8,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <queue>
 #include <mutex>
 #include <tuple>
 #include <memory>
@@ -210,6 +211,15 @@ struct sem_batch {
   std::vector<BatchLaunch> launches;
   int device = 0;
   unsigned char* pool = nullptr;
+  // packed device copy of every member's (η, φ̃) for sem_batch_rk4_step_host: η of member i at
+  // state + off[i], φ̃ at state + ncol_total + off[i]
+  double* state = nullptr;
+  std::vector<size_t> off;
+  size_t ncol_total = 0;
+  // optional event timing of the stage launches
+  bool timing = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
+  std::vector<cudaEvent_t> spare;
 };
 
 namespace {
@@ -402,7 +412,7 @@ int64_t sem_launch_count(void) { return g_launches.load(); }
 // Host tables of one (P, Nz, Pf, filter) combination, shared by every mesh that has it.
 struct ColumnTables {
   Line L;
-  std::vector<double> MD, I, B, F, cw, Aii, Z, Sg, lam, dsl, sig;
+  std::vector<double> MD, I, B, F, wrow, Aii, Z, Sg, lam, dsl, sig;
   long double S00 = 0, S01 = 0, S11 = 0;
 };
 
@@ -441,9 +451,11 @@ static int column_tables(const sem_params& p, std::shared_ptr<const ColumnTables
   for (int q = 0; q < Qf; ++q) for (int c = 0; c < Q; ++c) It[c * Qf + q] = t->I[q * Q + c];
   t->B = matmul(It, Lf.M, Q, Qf, Qf);                                 // Q×Qf = Iᵀ M_f
   t->F = filter_matrix(L, p.filter_alpha, p.filter_s, p.filter_ic);
-  // w̃ weights: v = M_σ⁻¹ e_top, c_l = (Δσ_l/2) M v|_l
-  t->cw.assign((size_t)Nz * Q, 0.0);
+  // w̃ weights: v = M_σ⁻¹ e_top, c_l = (Δσ_l/2) M v|_l, contracted with the layer's σ-derivative
+  // (2/Δσ_l) D into one weight per row: w̃ d = Σ_iz wrow_iz Φ_iz
+  t->wrow.assign((size_t)nrow, 0.0);
   {
+    std::vector<long double> wr((size_t)nrow, 0.0L);
     std::vector<long double> Ms((size_t)nrow * nrow, 0.0L);
     for (int l = 0; l < Nz; ++l)
       for (int a = 0; a < Q; ++a)
@@ -453,8 +465,9 @@ static int column_tables(const sem_params& p, std::shared_ptr<const ColumnTables
       for (int b = 0; b < Q; ++b) {
         long double s = 0.0L;
         for (int c = 0; c < Q; ++c) s += 0.5L * dsl[l] * L.M[b * Q + c] * Ms[(size_t)(l * P + c) * nrow + (nrow - 1)];
-        t->cw[(size_t)l * Q + b] = (double)s;
+        for (int c = 0; c < Q; ++c) wr[(size_t)l * P + c] += s * (2.0L / dsl[l]) * L.D[b * Q + c];
       }
+    for (int iz = 0; iz < nrow; ++iz) t->wrow[iz] = (double)wr[iz];
   }
   // static condensation of M' (element scale Δx/2 · M)
   t->Aii.assign((size_t)Pm * Pm, 0.0);
@@ -573,7 +586,7 @@ static int mesh_create_impl(const sem_params* pin, const double* x_edges_h, cons
   const std::vector<double>& I = ct->I;
   const std::vector<double>& B = ct->B;
   const std::vector<double>& F = ct->F;
-  const std::vector<double>& cw = ct->cw;
+  const std::vector<double>& wrow = ct->wrow;
   const std::vector<double>& Aii = ct->Aii;
   const std::vector<double>& Z = ct->Z;
   const std::vector<double>& Sg = ct->Sg;
@@ -681,10 +694,11 @@ static int mesh_create_impl(const sem_params* pin, const double* x_edges_h, cons
                o_s1e = cv.take<double>(ncol), o_s1p = cv.take<double>(ncol),
                o_P1 = cv.take<double>(n), o_P2 = cv.take<double>(n), o_P3 = cv.take<double>(n),
                o_D32 = cv.take<double>(n);
+  const size_t o_gglob = cv.take<double>((size_t)3 * Nx * Nz * Q * Q);
   const size_t o_inst = cv.take<Instance>(1), o_ctai = cv.take<int>((size_t)m->grid), o_sbar = cv.take<unsigned>(4);
   // surface tables
   const size_t o_tD = cv.take<double>(Q * Q), o_tMD = cv.take<double>(Q * Q), o_tB = cv.take<double>((size_t)Q * Qf),
-               o_tI = cv.take<double>((size_t)Qf * Q), o_tF = cv.take<double>(Q * Q), o_tcw = cv.take<double>((size_t)Nz * Q),
+               o_tI = cv.take<double>((size_t)Qf * Q), o_tF = cv.take<double>(Q * Q), o_twr = cv.take<double>((size_t)nrow),
                o_tAii = cv.take<double>((size_t)Pm * Pm + 1), o_tZ = cv.take<double>((size_t)2 * Pm + 1),
                o_tse = cv.take<double>(Nx), o_te = cv.take<double>(N), o_tm = cv.take<double>(N),
                o_tcp = cv.take<double>(N), o_tz = cv.take<double>(N);
@@ -712,7 +726,7 @@ static int mesh_create_impl(const sem_params* pin, const double* x_edges_h, cons
   }
   up(o_h, std::vector<double>(h_h, h_h + ncol));
   up(o_hx, hx_loc); up(o_dxe, dxe); up(o_dsl, dsl); up(o_sig, sig);
-  up(o_tD, L.D); up(o_tMD, MD); up(o_tB, B); up(o_tI, I); up(o_tF, F); up(o_tcw, cw);
+  up(o_tD, L.D); up(o_tMD, MD); up(o_tB, B); up(o_tI, I); up(o_tF, F); up(o_twr, wrow);
   up(o_tAii, Aii); up(o_tZ, Z); up(o_tse, se); up(o_te, th_e); up(o_tm, th_m); up(o_tcp, th_cp); up(o_tz, th_z);
   up(o_lam, lam);
   {
@@ -736,6 +750,15 @@ static int mesh_create_impl(const sem_params* pin, const double* x_edges_h, cons
   g.h = D_(o_h); g.hx_loc = D_(o_hx); g.dxe = D_(o_dxe); g.dsl = D_(o_dsl); g.sig = D_(o_sig);
   g.geo64 = D_(o_geo64); g.geo32 = F_(o_geo32); g.invdiag64 = D_(o_id64); g.invdiag32 = F_(o_id32);
   g.status = reinterpret_cast<int*>(m->pool + o_status);
+  g.gglob = D_(o_gglob);
+  g.bar_timeout_ns = kBarrierTimeoutNs;
+  g.drop_rank = -1;
+  g.trace = nullptr;
+#ifdef SEM_TRACE
+  if (cudaMalloc(reinterpret_cast<void**>(&g.trace), sizeof(unsigned long long) * (1 + 2 * kTraceMax)) != cudaSuccess ||
+      cudaMemset(g.trace, 0, sizeof(unsigned long long)) != cudaSuccess)
+    g.trace = nullptr;
+#endif
   m->rec = reinterpret_cast<SolveRecord*>(m->pool + o_rec);
 
   PcgArgs& a = m->pa;
@@ -771,7 +794,7 @@ static int mesh_create_impl(const sem_params* pin, const double* x_edges_h, cons
 
   SurfTables& t = m->st;
   t.P = P; t.Pf = p.Pf; t.Nx = Nx; t.Nz = Nz; t.ncol = ncol; t.nrow = nrow; t.periodic = g.periodic; t.g = p.g;
-  t.D = D_(o_tD); t.MD = D_(o_tMD); t.B = D_(o_tB); t.I = D_(o_tI); t.F = D_(o_tF); t.cw = D_(o_tcw);
+  t.D = D_(o_tD); t.MD = D_(o_tMD); t.B = D_(o_tB); t.I = D_(o_tI); t.F = D_(o_tF); t.wrow = D_(o_twr);
   t.Aii = D_(o_tAii); t.Z = D_(o_tZ); t.se = D_(o_tse); t.dsl = g.dsl; t.h = g.h;
   t.th_e = D_(o_te); t.th_m = D_(o_tm); t.th_cp = D_(o_tcp); t.th_z = D_(o_tz);
   t.th_vlast = th_vlast; t.th_fac = th_fac; t.nif = N; t.filter_on = (p.filter_ic >= 0 && p.filter_ic < P) ? 1 : 0;
@@ -1015,6 +1038,9 @@ int sem_rk4_step_host(sem_mesh* m, double* eta_h, double* phis_h, double* t, dou
   return rc;
 }
 
+// Cost of a team's barriers and cross-CTA round trips per stage, in element-local nodes of work
+// (team sizing in sem_batch_create).
+constexpr double kTeamSyncNodes = 256.0;
 // Groups of at most this many instances use the one-CTA-per-SM stage build.
 constexpr int kBatchNarrowMax = 8;
 // Dynamic shared memory per CTA up to which batch members widen their passes (two CTAs per SM,
@@ -1077,20 +1103,29 @@ int sem_batch_create(sem_mesh* const* meshes, int count, sem_batch** out) {
         w.push_back((double)m->p.Nx * m->p.Nz * (m->p.P + 1) * (m->p.P + 1));
         wsum += w.back();
       }
-      std::vector<int> c(L.members.size());
-      int used = 0;
+      // Team sizes: a launch lasts as long as its slowest team, so the CTAs go one at a time to the
+      // team whose estimated stage time is the largest, while that lowers it: the time of a team
+      // of c CTAs is taken as w/c (element-local nodes per CTA) plus kTeamSyncNodes when c > 1
+      // (the team barriers and cross-CTA round trips, in the same units).
+      (void)wsum;
+      std::vector<int> c(L.members.size(), 1), limit(L.members.size());
       for (size_t k = 0; k < L.members.size(); ++k) {
         const sem_mesh* m = meshes[L.members[k]];
-        const int limit = std::max(1, std::min(m->grid, (m->p.Nx + m->g.chunk - 1) / m->g.chunk));   // ≤ grid: buffer sizes
-        c[k] = std::max(1, std::min(limit, (int)((double)cap * w[k] / wsum)));
-        used += c[k];
+        limit[k] = std::max(1, std::min(m->grid, (m->p.Nx + m->g.chunk - 1) / m->g.chunk));   // ≤ grid: buffer sizes
       }
-      while (used > cap) {   // trim the largest teams
-        size_t kmax = 0;
-        for (size_t k = 1; k < c.size(); ++k) if (c[k] > c[kmax]) kmax = k;
-        if (c[kmax] == 1) break;
-        --c[kmax];
-        --used;
+      auto est = [&](size_t k, int ck) { return w[k] / ck + (ck > 1 ? kTeamSyncNodes : 0.0); };
+      {
+        std::priority_queue<std::pair<double, size_t>> pq;
+        for (size_t k = 0; k < c.size(); ++k) pq.push({est(k, 1), k});
+        int used = (int)c.size();
+        while (used < cap && !pq.empty()) {
+          const size_t k = pq.top().second;
+          pq.pop();
+          if (c[k] >= limit[k] || est(k, c[k] + 1) >= est(k, c[k])) continue;   // this team is done
+          ++c[k];
+          ++used;
+          pq.push({est(k, c[k]), k});
+        }
       }
       int acc = 0;
       for (size_t k = 0; k < c.size(); ++k) { L.team0.push_back(acc); L.nteam.push_back(c[k]); acc += c[k]; }
@@ -1123,9 +1158,15 @@ int sem_batch_create(sem_mesh* const* meshes, int count, sem_batch** out) {
       b->launches.push_back(std::move(L));
     }
   }
+  for (int i = 0; i < count; ++i) {
+    b->off.push_back(b->ncol_total);
+    b->ncol_total += (size_t)meshes[i]->ncol;
+  }
+  total += (2 * b->ncol_total * sizeof(double) + 255) & ~size_t(255);
   cudaError_t ae = dev_alloc(dev, total + 256, reinterpret_cast<void**>(&b->pool));
   if (ae != cudaSuccess) { delete b; return fail(SEM_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(ae)); }
-  size_t off = 0;
+  b->state = reinterpret_cast<double*>(b->pool);
+  size_t off = (2 * b->ncol_total * sizeof(double) + 255) & ~size_t(255);
   for (auto& L : b->launches) {
     L.inst_d = reinterpret_cast<Instance*>(b->pool + off);
     off += (sizeof(Instance) * L.members.size() + 255) & ~size_t(255);
@@ -1151,6 +1192,8 @@ void sem_batch_destroy(sem_batch* b) {
   if (!b) return;
   DeviceGuard dg(b->device);
   cudaDeviceSynchronize();   // no work of this batch may still run when its memory is reused
+  for (auto& pr : b->events) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
+  for (cudaEvent_t e : b->spare) cudaEventDestroy(e);
   dev_free(b->device, b->pool);
   delete b;
 }
@@ -1184,6 +1227,28 @@ int sem_batch_info(const sem_batch* b, int* launches_per_stage, int* ctas) {
 
 namespace {
 int batch_status(sem_batch* b, cudaStream_t s);
+
+cudaError_t take_batch_event(sem_batch* b, cudaEvent_t* ev) {
+  if (!b->spare.empty()) { *ev = b->spare.back(); b->spare.pop_back(); return cudaSuccess; }
+  return cudaEventCreate(ev);
+}
+
+// One stage launch of a batch group, bracketed by events while timing is on.
+cudaError_t batch_launch(sem_batch* b, const BatchLaunch& L, const StageArgs& a, cudaStream_t s) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e;
+  if (b->timing) {
+    if ((e = take_batch_event(b, &e0)) != cudaSuccess) return e;
+    if ((e = take_batch_event(b, &e1)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(e0, s)) != cudaSuccess) return e;
+  }
+  if ((e = launch_stage(L.P, L.mixed, L.wide, a, L.grid, L.smem, s)) != cudaSuccess) return e;
+  if (b->timing) {
+    if ((e = cudaEventRecord(e1, s)) != cudaSuccess) return e;
+    b->events.emplace_back(e0, e1);
+  }
+  return cudaSuccess;
+}
 }  // namespace
 
 int sem_batch_rk4_step(sem_batch* b, double* const* eta_d, double* const* phis_d, double* t_h, const double* dt_h,
@@ -1208,7 +1273,7 @@ int sem_batch_rk4_step(sem_batch* b, double* const* eta_d, double* const* phis_d
       for (auto& L : b->launches) {
         CUDA_TRY(cudaMemsetAsync(L.bars_d, 0, 2 * sizeof(unsigned int) * L.members.size(), s));
         const StageArgs a{L.inst_d, L.cta_d, L.bars_d, stage, step};
-        CUDA_TRY(launch_stage(L.P, L.mixed, L.wide, a, L.grid, L.smem, s));
+        CUDA_TRY(batch_launch(b, L, a, s));
       }
   if (nsteps > 0)
     for (int i = 0; i < n; ++i) set_history(b->meshes[i], eta_d[i], phis_d[i], dt_h[i]);
@@ -1239,9 +1304,56 @@ int sem_batch_laplace_solve(sem_batch* b, const double* const* eta_d, const doub
   for (auto& L : b->launches) {
     CUDA_TRY(cudaMemsetAsync(L.bars_d, 0, 2 * sizeof(unsigned int) * L.members.size(), s));
     const StageArgs a{L.inst_d, L.cta_d, L.bars_d, 0, 0};
-    CUDA_TRY(launch_stage(L.P, L.mixed, L.wide, a, L.grid, L.smem, s));
+    CUDA_TRY(batch_launch(b, L, a, s));
   }
   return batch_status(b, s);
+}
+
+int sem_batch_rk4_step_host(sem_batch* b, double* eta_h, double* phis_h, double* t_h, const double* dt_h,
+                            int nsteps, void* stream) {
+  if (!b || !eta_h || !phis_h || !dt_h || nsteps < 0) return fail(SEM_ERR_INVALID_ARG, "bad argument");
+  DeviceGuard dg(b->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t n = b->meshes.size(), bytes = sizeof(double) * b->ncol_total;
+  double* eta_d = b->state;
+  double* phis_d = b->state + b->ncol_total;
+  CUDA_TRY(cudaMemcpyAsync(eta_d, eta_h, bytes, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(phis_d, phis_h, bytes, cudaMemcpyHostToDevice, s));
+  std::vector<double*> ep(n), pp(n);
+  for (size_t i = 0; i < n; ++i) { ep[i] = eta_d + b->off[i]; pp[i] = phis_d + b->off[i]; }
+  const int rc = sem_batch_rk4_step(b, ep.data(), pp.data(), t_h, dt_h, nsteps, stream);
+  if (rc != SEM_OK && rc != SEM_ERR_NOT_CONVERGED && rc != SEM_ERR_NONFINITE && rc != SEM_ERR_TIMEOUT) return rc;
+  // every member's state comes back, failed members' included (their codes say which)
+  const std::string err = t_err;
+  CUDA_TRY(cudaMemcpyAsync(eta_h, eta_d, bytes, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaMemcpyAsync(phis_h, phis_d, bytes, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if (rc != SEM_OK) t_err = err;
+  return rc;
+}
+
+int sem_batch_enable_timing(sem_batch* b, int on) {
+  if (!b) return fail(SEM_ERR_INVALID_ARG, "NULL batch");
+  b->timing = on != 0;
+  return SEM_OK;
+}
+
+int sem_batch_get_timing(sem_batch* b, sem_timing* t) {
+  if (!b || !t) return fail(SEM_ERR_INVALID_ARG, "NULL argument");
+  DeviceGuard dg(b->device);
+  double total = 0.0;
+  for (auto& pr : b->events) {
+    CUDA_TRY(cudaEventSynchronize(pr.second));
+    float ms = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&ms, pr.first, pr.second));
+    total += ms;
+    b->spare.push_back(pr.first);
+    b->spare.push_back(pr.second);
+  }
+  t->krylov_launches = (int64_t)b->events.size();
+  t->krylov_ms = total;
+  b->events.clear();
+  return SEM_OK;
 }
 
 namespace {
@@ -1317,6 +1429,30 @@ int sem_get_timing(sem_mesh* m, sem_timing* t) {
   t->krylov_launches = (int64_t)m->events.size();
   t->krylov_ms = total;
   m->events.clear();
+  return SEM_OK;
+}
+
+#ifdef SEM_TRACE
+// Diagnostic builds only (not part of sem.h): copies the phase trace of the mesh's last launches
+// ([0] = marks, then (tag, ns) pairs) to out_h and clears it.
+int sem_trace_read(sem_mesh* m, unsigned long long* out_h, int max_words) {
+  if (!m || !out_h || !m->g.trace) return fail(SEM_ERR_INVALID_ARG, "no trace");
+  DeviceGuard dg(m->device);
+  CUDA_TRY(cudaDeviceSynchronize());
+  const int words = std::min(max_words, 1 + 2 * kTraceMax);
+  CUDA_TRY(cudaMemcpy(out_h, m->g.trace, sizeof(unsigned long long) * words, cudaMemcpyDeviceToHost));
+  CUDA_TRY(cudaMemset(m->g.trace, 0, sizeof(unsigned long long)));
+  return SEM_OK;
+}
+#endif
+
+int sem_set_barrier_test(sem_mesh* m, int drop_rank, double timeout_ms) {
+  if (!m) return fail(SEM_ERR_INVALID_ARG, "NULL mesh");
+  if (drop_rank < -1) return fail(SEM_ERR_INVALID_ARG, "drop_rank must be -1 or a team rank");
+  if (!(timeout_ms >= 0.0) || timeout_ms > 1e-6 * (double)kBarrierTimeoutNs)
+    return fail(SEM_ERR_INVALID_ARG, "timeout_ms must be in [0, 2000]");
+  m->g.drop_rank = drop_rank;
+  m->g.bar_timeout_ns = timeout_ms > 0.0 ? (unsigned long long)(timeout_ms * 1e6) : kBarrierTimeoutNs;
   return SEM_OK;
 }
 

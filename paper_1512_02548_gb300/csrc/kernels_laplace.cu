@@ -1,6 +1,7 @@
 // Run-time dispatch of the σ-Laplace launchers on the GLL order, the element-to-global map,
 // the apply's edge pass, and the allocation-free apply (arXiv 1512.02548, §3.1.2).  The
 // order-templated kernels live in laplace_device.cuh and are compiled once per order.
+#include <dlfcn.h>
 #include <mutex>
 
 #include "mesh_index.cuh"
@@ -86,23 +87,43 @@ cudaError_t launch_apply(const DevGeom& g, const double* x, double* y, double* q
 // ------------------------------------------------------------------------------------
 static __device__ __align__(256) double g_noalloc_edge[kNoAllocEdgeMax];
 
+// Device address of g_noalloc_edge, looked up with cudaGetSymbolAddress at the first call on a
+// device (with that device current) and kept for later calls.  The address belongs to the CUDA
+// context that loaded this module, so the cache is keyed on that context as well: after
+// cudaDeviceReset a new primary context may load the module at another address, and the next
+// call looks it up again.  The context handle comes from the driver's cuCtxGetCurrent, found
+// in the already loaded driver library; without it the key is the device alone.
 static std::mutex g_noalloc_mu;
-static double* g_noalloc_ptr[64] = {nullptr};
+struct NoallocSlot { void* ctx; double* ptr; };
+static NoallocSlot g_noalloc_slot[64] = {};
 
-// Device address of g_noalloc_edge for the current device, looked up once per device.
+static void* current_context() {
+  using GetCurrent = int (*)(void**);
+  static GetCurrent fn = []() -> GetCurrent {
+    void* h = dlopen("libcuda.so.1", RTLD_NOW | RTLD_NOLOAD);
+    return h ? reinterpret_cast<GetCurrent>(dlsym(h, "cuCtxGetCurrent")) : nullptr;
+  }();
+  void* ctx = nullptr;
+  if (fn && fn(&ctx) != 0) ctx = nullptr;
+  return ctx;
+}
+
 static cudaError_t noalloc_edge_address(double** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  void* ctx = current_context();   // null on a thread the runtime has not bound yet
   std::lock_guard<std::mutex> lk(g_noalloc_mu);
-  if (!g_noalloc_ptr[dev]) {
+  NoallocSlot& sl = g_noalloc_slot[dev];
+  if (!sl.ptr || sl.ctx != ctx) {
     double* p = nullptr;
     e = cudaGetSymbolAddress(reinterpret_cast<void**>(&p), g_noalloc_edge);
     if (e != cudaSuccess) return e;
-    g_noalloc_ptr[dev] = p;
+    sl.ptr = p;
+    sl.ctx = current_context();      // the lookup has bound the device's context to this thread
   }
-  *out = g_noalloc_ptr[dev];
+  *out = sl.ptr;
   return cudaSuccess;
 }
 

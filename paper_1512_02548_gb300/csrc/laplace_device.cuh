@@ -347,8 +347,6 @@ namespace semgb {
 // Grid barrier for the cooperative kernel, with a wall-clock limit.
 // ------------------------------------------------------------------------------------
 
-constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;  // 2 s
-
 // A team of CTAs that synchronise among themselves: the whole grid for one mesh, or the CTAs
 // assigned to one instance of a batch.
 struct Team {
@@ -357,6 +355,7 @@ struct Team {
   int* status;           // device status word of the instance
   double* part;          // reduction partials [4 slots][4 values][stride]
   int stride;
+  unsigned long long timeout_ns;   // limit of each barrier wait (2 s unless a test sets it)
 };
 
 // Returns false (and sets ST_TIMEOUT) if the other CTAs of the team did not arrive in time;
@@ -379,6 +378,22 @@ static __device__ __forceinline__ unsigned bar_load(const unsigned* p) {
   return v;
 }
 
+#ifdef SEM_TRACE
+static __device__ __forceinline__ void trace_mark(const DevGeom& g, const Team& tm, int tag) {
+  if (threadIdx.x == 0 && tm.rank == 0 && g.trace) {
+    const unsigned long long n = g.trace[0];
+    if (n < (unsigned long long)kTraceMax) {
+      g.trace[1 + 2 * n] = (unsigned long long)tag;
+      g.trace[2 + 2 * n] = global_ns();
+      g.trace[0] = n + 1;
+    }
+  }
+}
+#define SEM_MARK(g, tm, tag) trace_mark(g, tm, tag)
+#else
+#define SEM_MARK(g, tm, tag) ((void)0)
+#endif
+
 static __device__ __forceinline__ bool grid_barrier(const Team& tm, int* s_flag) {
   __syncthreads();
   if (tm.size == 1) return true;
@@ -391,7 +406,7 @@ static __device__ __forceinline__ bool grid_barrier(const Team& tm, int* s_flag)
       const unsigned long long t0 = global_ns();
       unsigned int spins = 0;
       while (bar_load(tm.bar) < target) {
-        if ((++spins & 63u) == 0 && global_ns() - t0 > kBarrierTimeoutNs) {
+        if ((++spins & 63u) == 0 && global_ns() - t0 > tm.timeout_ns) {
           atomicOr(tm.status, ST_TIMEOUT);
           ok = 0;
           break;
@@ -615,8 +630,9 @@ template <class T, bool CACHE = false>
 __device__ void phase_interface(const DevGeom& g, const PrecView<T>& pv, const Team& tm) {
   const int N = pv.nif, Nx = g.Nx;
   const bool whole_cta = N > 32 * kTridiagRegs;   // long systems: all warps of the CTA per mode
-  if (!whole_cta && threadIdx.x >= 32) return;
-  for (int k = tm.rank; k < pv.nr; k += tm.size) {
+  // short systems: one warp per mode, the modes spread over the team's CTAs and their warps
+  const int w = whole_cta ? 0 : (int)(threadIdx.x >> 5), nw = whole_cta ? 1 : (int)(blockDim.x >> 5);
+  for (int k = tm.rank + tm.size * w; k < pv.nr; k += tm.size * nw) {
     const T* gl = pv.gL + (size_t)k * Nx;
     const T* gr = pv.gR + (size_t)k * Nx;
     auto gfun = [&](int j) -> T {
@@ -690,8 +706,11 @@ __device__ bool finish_precondition(const DevGeom& g, Smem<P, T>& s, const Range
                                     const PcgArgs& PA, const PrecView<TP>& pv, const CgVecs<T>& V, int* s_flag) {
   if (PA.precond == PREC_JACOBI) return grid_barrier(tm, s_flag);
   if (!grid_barrier(tm, s_flag)) return false;
+  SEM_MARK(g, tm, TR_IT_BAR2);
   phase_interface<TP, CACHE>(g, pv, tm);
+  SEM_MARK(g, tm, TR_IT_INTERFACE);
   if (!grid_barrier(tm, s_flag)) return false;
+  SEM_MARK(g, tm, TR_IT_BAR3);
   phase_backsub<P, T, TP>(g, s, R, tm, pv, V);
   return true;
 }
@@ -710,8 +729,10 @@ __device__ int cg_solve(const DevGeom& g, Smem<P, T>& s, const Range& R, const T
   __shared__ T s_scal[2];
   __shared__ int s_stop;
   int cur = 0;
+  SEM_MARK(g, tm, TR_CG_START);
   cg_update<P, T, TP>(g, s, R, tm, pv, PA.precond, V, cur, false, true, T(0), T(0));
   if (!finish_precondition<P, T, TP, CACHE>(g, s, R, tm, PA, pv, V, s_flag)) return -1;
+  SEM_MARK(g, tm, TR_IT_BACKSUB);
   int k = 0;
   double rr = 0.0;
   // 1/γ and 1/α of the last iteration, double-buffered by iteration parity: thread 32 (another SM
@@ -745,7 +766,9 @@ __device__ int cg_solve(const DevGeom& g, Smem<P, T>& s, const Range& R, const T
     }
     block_sum<3, A>(acc, red);
     put_partials<3, A>(tm, 2, acc);
+    SEM_MARK(g, tm, TR_IT_APPLY);
     if (!grid_barrier(tm, s_flag)) return -1;
+    SEM_MARK(g, tm, TR_IT_BAR1);
     double sums[3];
     grid_sum<3>(tm, 2, sums, red);
     if (threadIdx.x == 32) {
@@ -775,13 +798,17 @@ __device__ int cg_solve(const DevGeom& g, Smem<P, T>& s, const Range& R, const T
       s_stop = stop;
     }
     __syncthreads();
+    SEM_MARK(g, tm, TR_IT_SCALARS);
     if (s_stop) break;
     const T alpha = s_scal[0], beta = s_scal[1];
     cg_update<P, T, TP>(g, s, R, tm, pv, PA.precond, V, cur, true, k == 0, alpha, beta);
     cur ^= 1;
+    SEM_MARK(g, tm, TR_IT_UPDATE);
     if (!finish_precondition<P, T, TP, CACHE>(g, s, R, tm, PA, pv, V, s_flag)) return -1;
+    SEM_MARK(g, tm, TR_IT_BACKSUB);
     ++k;
   }
+  SEM_MARK(g, tm, TR_CG_END);
   *rr_out = rr;
   return k;
 }
@@ -866,15 +893,23 @@ __device__ bool solve_body(const DevGeom& g, const PcgArgs& A, const Team& tm, u
   s64.load_tables(g);
   // the geometric factors of the FP64 applies, once per solve, where the launch reserved room
   // for them after the apply's buffers
+  // (in shared memory where the launch reserved room, else in the mesh's global array)
   const double* gc = nullptr;
-  if (g.gcache > 0 && (size_t)3 * (R.e1 - R.e0) * g.Nz * (P + 1) * (P + 1) <= (size_t)g.gcache) {
+  const size_t per_e = (size_t)3 * g.Nz * (P + 1) * (P + 1);
+  if (g.gcache > 0 && per_e * (R.e1 - R.e0) <= (size_t)g.gcache) {
     double* c = s64.F2 + (size_t)g.Nz * (P + 1) * (P + 1) * g.chunk;
+    fill_gcache<P>(g, R.e0, R.e1, c);
+    __syncthreads();
+    gc = c;
+  } else if (g.gglob != nullptr) {
+    double* c = g.gglob + (size_t)R.e0 * per_e;
     fill_gcache<P>(g, R.e0, R.e1, c);
     __syncthreads();
     gc = c;
   }
   double rr = 0.0, bb = 0.0;
   if (!fp64_residual<P>(g, s64, R, tm, A, true, red, &s_flag, rr, bb, nullptr, gc)) return false;
+  SEM_MARK(g, tm, TR_RESIDUAL);
   const double target = A.tol * A.tol * bb;
   int iters = 0, refinements = 0;
   bool rr_floor_ok = false;   // stopped at the FP64 residual floor with converged corrections
@@ -948,6 +983,7 @@ __device__ bool solve_body(const DevGeom& g, const PcgArgs& A, const Team& tm, u
       if (!grid_barrier(tm, &s_flag)) return false;
       double dummy_b = 0.0;
       if (!fp64_residual<P>(g, s64, R, tm, A, false, red, &s_flag, rr, dummy_b, dx, gc)) return false;
+      SEM_MARK(g, tm, TR_REFINE);
       stalled = dx[0] > 0.25 * dd_prev;
       dd_prev = dx[0];
       if (it == 0) break;   // no progress possible
@@ -974,7 +1010,8 @@ __global__ void __launch_bounds__(kThreads) k_pcg(DevGeom g, PcgArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[kRedSize];
   __shared__ int s_flag;
-  const Team tm{(int)blockIdx.x, (int)gridDim.x, A.bar, g.status, A.part, A.part_stride};
+  const Team tm{(int)blockIdx.x, (int)gridDim.x, A.bar, g.status, A.part, A.part_stride, g.bar_timeout_ns};
+  if (tm.rank == g.drop_rank) return;   // testing hook: see sem_set_barrier_test
   solve_body<P, MIXED>(g, A, tm, smem_raw, red, &s_flag);
 }
 
@@ -1291,6 +1328,23 @@ static __global__ void __launch_bounds__(32) k_prec_tri(DevGeom g, PrecSetup ps,
 // ------------------------------------------------------------------------------------
 constexpr int kStageWarps = kThreads / 32;
 
+// The interface systems of the two right-hand sides (η, φ̃) of an M' solve: short systems on one
+// warp each (warps 0 and 1 of a one-CTA team, warp 0 of ranks 0 and 1 otherwise), long ones on a
+// whole CTA each.  Every thread of the CTA calls it.
+template <bool CACHE>
+__device__ __forceinline__ void mass1d_interfaces(const SurfTables& t, const Team& tm, double* scr) {
+  if (t.nif <= 32 * kTridiagRegs) {
+    const int warp = threadIdx.x >> 5;
+    if (tm.size == 1) {
+      if (warp < 2) mass1d_interface(t, 2, scr, warp);
+    } else if (tm.rank < 2 && warp == 0) {
+      mass1d_interface(t, 2, scr, tm.rank);
+    }
+    return;
+  }
+  for (int rh = tm.rank; rh < 2; rh += tm.size) mass1d_interface_cta<CACHE>(t, 2, scr, rh);
+}
+
 template <int P, bool MIXED, bool CACHE = false>
 __device__ void stage_body(Instance& I, const Team& tm, int stage, int step, unsigned char* smem_raw,
                            double* red, int* s_flag, double (*sh)[kSurfWarpScratch]) {
@@ -1307,6 +1361,7 @@ __device__ void stage_body(Instance& I, const Team& tm, int stage, int step, uns
   const double t0 = I.tstart + step * I.dt;
   const double time = t0 + (stage == 1 ? 0.0 : (stage == 4 ? I.dt : 0.5 * I.dt));
   const int ne = R.e1 - R.e0, nc = R.c1 - R.c0;
+  SEM_MARK(g, tm, TR_START);
 
   // σ-geometry of the owned element columns
   for (int q = threadIdx.x; q < ne * Q; q += blockDim.x) geometry_item<P>(g, ein, R.e0 * Q + q);
@@ -1358,7 +1413,9 @@ __device__ void stage_body(Instance& I, const Team& tm, int stage, int step, uns
       __syncthreads();
     }
   }
+  SEM_MARK(g, tm, TR_SETUP);
   if (!grid_barrier(tm, s_flag)) return;
+  SEM_MARK(g, tm, TR_BAR_SETUP);
   if (wave_tab)
     for (int col = tm.rank * nw + warp; col < t.nzl; col += tm.size * nw) wave_zone_column(t, col, lane);
   // long systems between walls: the whole CTA per mode.  Periodic systems keep the serial
@@ -1367,15 +1424,18 @@ __device__ void stage_body(Instance& I, const Team& tm, int stage, int step, uns
   // stopped converging with the scanned pivots).
   if (I.ps.nif > 32 * kTridiagRegs && !g.periodic) {
     for (int k = tm.rank; k < I.ps.nr; k += tm.size) prec_tri_mode_cta(g, I.ps, k);
-  } else if (warp == 0) {
-    float* stg = 2 * I.ps.nif <= 2 * kSurfWarpScratch ? reinterpret_cast<float*>(sh[0]) : nullptr;
-    for (int k = tm.rank; k < I.ps.nr; k += tm.size) prec_tri_mode(g, I.ps, k, stg);
+  } else {
+    // one warp per mode, the modes spread over the team's CTAs and their warps
+    float* stg = 2 * I.ps.nif <= 2 * kSurfWarpScratch ? reinterpret_cast<float*>(sh[warp]) : nullptr;
+    for (int k = tm.rank + tm.size * warp; k < I.ps.nr; k += tm.size * nw) prec_tri_mode(g, I.ps, k, stg);
   }
   if (!grid_barrier(tm, s_flag)) return;
+  SEM_MARK(g, tm, TR_PIVOTS);
   // Laplace solve, warm-started from the previous stage's potential
   if (threadIdx.x == 0) I.pa.phis = pin;
   __syncthreads();
   if (!solve_body<P, MIXED, CACHE>(g, I.pa, tm, smem_raw, red, s_flag)) return;
+  SEM_MARK(g, tm, TR_SOLVED);
   if (stage == 0) return;
   // kept for the initial guesses of the next stages
   if (stage == 3) {
@@ -1400,14 +1460,17 @@ __device__ void stage_body(Instance& I, const Team& tm, int stage, int step, uns
     const int rh = q / ne, ex = R.e0 + (q - rh * ne);
     mass1d_condense(t, I.R, 2, I.scr, rh * t.Nx + ex);
   }
+  SEM_MARK(g, tm, TR_WSX);
   if (!grid_barrier(tm, s_flag)) return;
-  for (int rh = tm.rank; rh < 2; rh += tm.size) mass1d_interface_cta<CACHE>(t, 2, I.scr, rh);
+  mass1d_interfaces<CACHE>(t, tm, I.scr);
   if (!grid_barrier(tm, s_flag)) return;
+  SEM_MARK(g, tm, TR_MINT1);
   for (int q = threadIdx.x; q < 2 * nc; q += blockDim.x) {
     const int rh = q / nc, col = R.c0 + (q - rh * nc);
     mass1d_backsub(t, I.R, 2, rh == 0 ? I.etax : I.phisx, I.scr, rh, col);
   }
   if (!grid_barrier(tm, s_flag)) return;
+  SEM_MARK(g, tm, TR_MBACK1);
   // over-integrated Zakharov right-hand side of the owned elements and its M' solve
   for (int ex = R.e0 + warp; ex < R.e1; ex += nw) zak_element(t, ein, I.etax, I.phisx, I.wt, I.R, ex, lane, sh[warp]);
   __syncthreads();
@@ -1415,9 +1478,11 @@ __device__ void stage_body(Instance& I, const Team& tm, int stage, int step, uns
     const int rh = q / ne, ex = R.e0 + (q - rh * ne);
     mass1d_condense(t, I.R, 2, I.scr, rh * t.Nx + ex);
   }
+  SEM_MARK(g, tm, TR_ZAK);
   if (!grid_barrier(tm, s_flag)) return;
-  for (int rh = tm.rank; rh < 2; rh += tm.size) mass1d_interface_cta<CACHE>(t, 2, I.scr, rh);
+  mass1d_interfaces<CACHE>(t, tm, I.scr);
   if (!grid_barrier(tm, s_flag)) return;
+  SEM_MARK(g, tm, TR_MINT2);
   for (int q = threadIdx.x; q < 2 * nc; q += blockDim.x) {
     const int rh = q / nc, col = R.c0 + (q - rh * nc);
     mass1d_backsub(t, I.R, 2, rh == 0 ? I.ke : I.kp, I.scr, rh, col);
@@ -1428,9 +1493,11 @@ __device__ void stage_body(Instance& I, const Team& tm, int stage, int step, uns
     if (I.relax) relax_column(t, ein, pin, time, 1.0 / I.tau, I.ke, I.kp, col, wave_tab ? t.wEP : nullptr);
     rk4_item(stage, I.dt, I.eta, I.phis, I.ke, I.kp, I.ae, I.ap, eout, pout, col);
   }
+  SEM_MARK(g, tm, TR_RK4);
   if (stage == 4 && t.filter_on) {
     if (!grid_barrier(tm, s_flag)) return;
     for (int ex = R.e0 + warp; ex < R.e1; ex += nw) filter_element(t, I.eta, I.phis, ex, lane, sh[warp]);
+    SEM_MARK(g, tm, TR_FILTER);
   }
 }
 
@@ -1451,7 +1518,9 @@ __global__ void __launch_bounds__(kThreads, WIDE ? 2 : 1) k_stage(StageArgs B) {
     for (int q = threadIdx.x; q < (int)(sizeof(Instance) / 4); q += blockDim.x) dst[q] = src[q];
   }
   __syncthreads();
-  const Team tm{(int)blockIdx.x - I.team0, I.nteam, B.bars + 2 * ii, I.g.status, I.pa.part, I.pa.part_stride};
+  const Team tm{(int)blockIdx.x - I.team0, I.nteam, B.bars + 2 * ii, I.g.status, I.pa.part, I.pa.part_stride,
+                I.g.bar_timeout_ns};
+  if (tm.rank == I.g.drop_rank) return;   // testing hook: see sem_set_barrier_test
   stage_body<P, MIXED, !WIDE>(I, tm, B.stage, B.step, smem_raw, red, &s_flag, sh);
 }
 

@@ -16,6 +16,9 @@ __host__ __device__ constexpr int w_off(int P) { return P * (P + 1) / 2 - 1; }
 constexpr int kDTotal = d_off(kMaxP + 1);
 constexpr int kWTotal = w_off(kMaxP + 1);
 
+// Wall-clock limit of a team barrier wait (sem_set_barrier_test can shorten it).
+constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;   // 2 s
+
 // Device status bits (OR-ed into the mesh's status word).
 enum : int { ST_NOT_CONVERGED = 1, ST_NONFINITE = 2, ST_TIMEOUT = 4, ST_BAD_DEPTH = 8 };
 
@@ -35,6 +38,24 @@ struct DevGeom {
   int* status;           // device status word
   int gcache;            // doubles of dynamic shared memory after the FP64 apply's buffers that
                          // hold a solve's geometric factors (single-mesh fused stage; 0 = none)
+  double* gglob;         // [Nx][Nz][(P+1)²][3] geometric factors of the FP64 applies of a solve,
+                         // when they do not fit in shared memory (each CTA fills its own elements)
+  unsigned long long bar_timeout_ns;   // wall-clock limit of every team barrier wait
+  int drop_rank;         // testing: this team rank leaves the next launch before its first
+                         // barrier, so the others' bounded waits run out (−1: none)
+  unsigned long long* trace;   // phase trace of builds compiled with -DSEM_TRACE (else unused):
+                               // [0] = marks so far, then (tag, %globaltimer) pairs
+};
+
+// Phase trace (diagnostic builds only, compiled with -DSEM_TRACE): thread 0 of team rank 0
+// stamps %globaltimer with a tag at the phase boundaries of the Krylov and fused stage kernels.
+constexpr int kTraceMax = 4096;
+enum : int {
+  TR_START = 1, TR_SETUP = 2, TR_BAR_SETUP = 3, TR_PIVOTS = 4, TR_RESIDUAL = 5,
+  TR_IT_APPLY = 10, TR_IT_BAR1 = 11, TR_IT_SCALARS = 12, TR_IT_UPDATE = 13, TR_IT_BAR2 = 14,
+  TR_IT_INTERFACE = 15, TR_IT_BAR3 = 16, TR_IT_BACKSUB = 17, TR_CG_START = 18, TR_CG_END = 19,
+  TR_REFINE = 20, TR_SOLVED = 30, TR_WSX = 31, TR_MINT1 = 32, TR_MBACK1 = 33, TR_ZAK = 34, TR_MINT2 = 35,
+  TR_RK4 = 36, TR_FILTER = 37, TR_END = 38
 };
 
 // Element columns processed together per CTA pass: enough that a pass has ~256–512 work
@@ -125,7 +146,7 @@ struct SurfTables {
   const double* B;        // (P+1)×(Pf+1)  Iᵀ M_f (over-integration projection)
   const double* I;        // (Pf+1)×(P+1)  interpolation to the fine nodes
   const double* F;        // (P+1)²  modal filter
-  const double* cw;       // Nz×(P+1) σ-contraction weights of the w̃ projection
+  const double* wrow;     // [nrow] row weights of the w̃ projection: w̃ d = Σ_iz wrow_iz Φ_iz
   const double* Aii;      // (P−1)²  inverse interior block of M
   const double* Z;        // 2×(P−1) M_bi M_ii⁻¹
   const double* se;       // [Nx] Δx_e / 2

@@ -19,22 +19,15 @@ __device__ __forceinline__ int scol(const SurfTables& t, int ex, int a) {
 // w̃ at column `col` (one warp).  On the tensor-product mesh the 2D mass is M_x ⊗ M_σ and the
 // σ-derivative (1/d)∂σΦ is continuous across x-element edges, so the surface row of
 // M⁻¹S_zΦ (eq. velocpot2) is the per-column contraction
-//     w̃ = Σ_l Σ_b c_{l,b} (1/d) (2/Δσ_l) (D Φ_l)_b,  c_l = (Δσ_l/2) M (M_σ⁻¹ e_top)|_l.
-// Lanes take (layer, row) pairs; the warp sums.
+//     w̃ = (1/d) Σ_l Σ_b c_{l,b} (2/Δσ_l) (D Φ_l)_b,  c_l = (Δσ_l/2) M (M_σ⁻¹ e_top)|_l,
+// whose weights are folded on the host into one weight per row, w̃ = (1/d) Σ_iz wrow_iz Φ_iz.
+// Lanes take rows; the warp sums.
 __device__ __forceinline__ void wsurf_column(const SurfTables& t, const double* __restrict__ Phi,
                                              const double* __restrict__ eta, double* __restrict__ w,
                                              int col, int lane) {
-  const int P = t.P, Q = P + 1;
   const double* phi = Phi + (size_t)col * t.nrow;
   double acc = 0.0;
-  for (int lb = lane; lb < t.Nz * Q; lb += 32) {
-    const int l = lb / Q, b = lb - l * Q;
-    const double* pl = phi + l * P;
-    const double* Db = t.D + b * Q;
-    double d = 0.0;
-    for (int c = 0; c < Q; ++c) d = fma(Db[c], pl[c], d);
-    acc = fma(t.cw[lb] * (2.0 / t.dsl[l]), d, acc);
-  }
+  for (int iz = lane; iz < t.nrow; iz += 32) acc = fma(t.wrow[iz], phi[iz], acc);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if (lane == 0) w[col] = acc / (eta[col] + t.h[col]);

@@ -140,7 +140,9 @@ class Server:
     """Budgeted admission in arrival order and one batched tick at a time."""
 
     def __init__(self, executor, hbm_budget: int, clock=time.perf_counter, sleep=time.sleep,
-                 keep_results: bool = True):
+                 keep_results=True):
+        """keep_results: True (every request's result is copied back), False, or a set of
+        request ids whose results are kept."""
         self.ex = executor
         self.budget = int(hbm_budget)
         self.clock = clock
@@ -165,7 +167,8 @@ class Server:
         def finish(r: Request, error: str | None = None):
             nonlocal used
             r.error = error
-            r.result = self.ex.release(r, keep_result=self.keep and error is None)
+            keep = self.keep if isinstance(self.keep, bool) else r.rid in self.keep
+            r.result = self.ex.release(r, keep_result=keep and error is None)
             r.finished = self.clock() - t0
             used -= fp[r.rid]
             del active[r.rid]

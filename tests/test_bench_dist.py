@@ -61,3 +61,35 @@ def test_reference_arm_other_ranks_exit_without_work():
     out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
                           "--steps", "1", "--warmup", "3"], env=env, capture_output=True, text=True, timeout=120)
     assert out.returncode == 0 and out.stdout.strip() == ""
+
+
+def test_c3_sample_is_seeded_and_distinct():
+    sys.path.insert(0, ROOT)
+    import bench
+    a, b = bench.c3_sample(32), bench.c3_sample(32)
+    assert a == b and len(set(a)) == 32 and all(0 <= i < 512 for i in a)
+    assert bench.c3_sample(8) == a[:8]
+
+
+def test_oracle_pool_runs_one_step_per_tank():
+    """The spawned oracle pool of the cpu_baseline and the reference arm: one RK4 step of two small
+    C3 tanks, each equal to the oracle run in this process, with four Laplace solves per tank."""
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import bench
+    from oracle import sem as osem
+    from sem_workloads import c3_instances
+    wls = c3_instances(512)
+    small = sorted(range(512), key=lambda i: wls[i].n_unknowns)[:2]
+    pool = bench.oracle_pool(2)
+    try:
+        res = pool.map(bench.oracle_job, [("c3", i, *bench.c3_initial(i), 1, 0.0) for i in small])
+    finally:
+        pool.close()
+        pool.join()
+    for i, (key, (eta, phis), secs, dof) in zip(small, res):
+        wl = wls[i]
+        assert key == i and dof == 4 * wl.n_unknowns and secs > 0
+        om = osem.mesh_for(wl, h_col=np.full(wl.ncol, wl.depth))
+        e, p = om.rk4_step(*bench.c3_initial(i), wl.dt)
+        assert np.array_equal(e, eta) and np.array_equal(p, phis)

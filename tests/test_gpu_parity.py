@@ -226,11 +226,18 @@ def test_rk4_steps(case):
     assert rel(eta, e) < TOL_FP64 and rel(phis, p) < TOL_FP64
 
 
+@pytest.mark.parametrize("Nx", [150, 1500])
 @pytest.mark.parametrize("periodic", [True, False], ids=["periodic", "walls"])
-def test_long_tank_interface_solves(periodic):
+def test_long_tank_interface_solves(periodic, Nx):
     """More than 128 interface unknowns: the preconditioner's and M''s interface systems are
-    solved by a whole CTA (chunks over all its threads) instead of one warp."""
-    wl, om, gm = make_pair(P=3, Nx=150, Nz=1, periodic=periodic)
+    solved by a whole CTA (chunks over all its threads) instead of one warp.  Nx = 150 gives one
+    value per thread; Nx = 1500 gives chunks of 6, which the single-mesh stage build keeps in
+    registers between the passes of the solve."""
+    import dataclasses
+    # the tank grows with Nx, so that the elements keep the aspect ratio of the Nx = 150 case
+    wl = dataclasses.replace(small_case(P=3, Nx=Nx, Nz=1, periodic=periodic), length=2 * math.pi * Nx / 150)
+    om = osem.mesh_for(wl)
+    gm = sem.Mesh.from_workload(wl, h=om.h)
     eta0, phis0 = surface(om, seed=11)
     eta, phis = T(eta0), T(phis0)
     gm.rk4_step(eta, phis, wl.dt, 2)

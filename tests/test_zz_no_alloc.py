@@ -1,9 +1,9 @@
 """Allocation-free operator apply (sem_laplace_apply_noalloc) against the regular apply.
 
-Some callers cannot allocate device memory when they call the library: a stream that
-is being captured into a CUDA graph, a real-time loop that forbids allocator calls, or
-a host whose memory manager owns the GPU and refuses raw cudaMalloc.  For them the
-library offers an apply whose only temporary lives in a static device array.  This
+Some callers cannot allocate device memory when they call the library: a real-time loop
+that forbids allocator calls (cudaMalloc and cudaFree can synchronise the device), or a
+host whose own memory manager owns the GPU's memory and refuses raw cudaMalloc.  For
+them the library offers an apply whose only temporary lives in a static device array.  This
 test calls it through the C ABI twice in a row (the array keeps the first call's
 contents) and checks each result against sem_laplace_apply at the tolerance of the
 other operator tests; it also checks that a mesh too large for the array is refused.
