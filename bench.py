@@ -176,8 +176,10 @@ def _oracle_init():
 
 def oracle_job(job):
     """One oracle run in a worker: job = (kind, key, eta0, phis0, nsteps, t0) with kind "c3" (key =
-    tank index), "c2", "c4" or "c5" (key = (rate, count, request index)); nsteps = 0 means one
-    Laplace solve (returns Φ).  Returns (key, results, seconds, Laplace unknowns solved)."""
+    tank index), "c2" (key = H/L, 0 for the configured 0.08), "c4" or "c5" (key = (rate, count,
+    request index)); nsteps = 0 means one Laplace solve (returns Φ), nsteps < 0 the displaced volume
+    1ᵀM'η and energy ½Φᵀ(−𝓛)Φ + ½gηᵀM'η of the state.  Returns (key, results, seconds, Laplace
+    unknowns solved)."""
     import numpy as np
     from oracle import sem as osem
     from sem_workloads import c2_steep_periodic, c3_instances, c4_shoal, c5_requests, depth_columns
@@ -186,6 +188,9 @@ def oracle_job(job):
         wl = c3_instances(512)[key]
     elif kind == "c2":
         wl = c2_steep_periodic()
+        if key:                                   # another wave steepness H/L
+            import dataclasses
+            wl = dataclasses.replace(wl, wave_height=key * wl.length)
     elif kind == "c4":
         wl = c4_shoal()
     else:
@@ -193,7 +198,10 @@ def oracle_job(job):
     h = depth_columns(wl, column_positions(wl)) if wl.bathymetry == "shoal" else np.full(wl.ncol, wl.depth)
     om = osem.mesh_for(wl, h_col=h)
     t0 = time.perf_counter()
-    if nsteps == 0:
+    if nsteps < 0:                                # diagnostics of a state: displaced volume, energy
+        out = (om.mass(eta), om.energy(eta, phis))
+        dof = wl.n_unknowns
+    elif nsteps == 0:
         out = (om.laplace_solve(eta, phis),)
         dof = wl.n_unknowns
     else:
@@ -632,6 +640,100 @@ def c5_serving(rates=(100.0, 1000.0), count: int = 1000, sample: int = 4):
     return out, checks
 
 
+def long_runs(dev, cores: int):
+    """The full-length runs of C2 and C4 with their conservation diagnostics, computed by the oracle
+    (all host cores) from GPU states:
+      * C2 as configured (H/L = 0.08): FP64 steps until the library reports that the state is no
+        longer regular (the wave, started from linear theory at this steepness, breaks), with the
+        displaced volume and energy every 10 steps up to there;
+      * C2 at H/L = 0.055, the steepest of the same family of initial states that runs 100 periods
+        (20 000 steps, FP64 and mixed): volume and energy every 5 periods, and the drift;
+      * C4 (5 000 steps, FP64 and mixed): volume and energy every 500 steps (the zones generate and
+        absorb waves, so neither is conserved there).
+    Returns a dict of series and summaries."""
+    import numpy as np
+    import torch
+    import paper_1512_02548_gb300 as sem
+    from sem_workloads import c2_steep_periodic, c4_shoal, depth_columns, initial_state
+    pool = oracle_pool(cores)
+    out = {}
+    try:
+        def diag(kind, key, states):
+            futs = [(s, pool.apply_async(oracle_job, ((kind, key, e, p, -1, 0.0),))) for s, e, p in states]
+            rows = [(s,) + tuple(f.get()[1]) for s, f in futs]
+            return [{"step": s, "mass": m, "energy": en} for s, m, en in rows]
+
+        # C2 as configured, until it stops
+        wl = c2_steep_periodic()
+        h = np.full(wl.ncol, wl.depth)
+        e0, p0 = initial_state(wl, column_positions(wl), h)
+        m = sem.Mesh.from_workload(wl, h=h)
+        eta, phis = torch.tensor(e0, device=dev), torch.tensor(p0, device=dev)
+        states, fail, err = [(0, e0, p0)], None, None
+        for step in range(1, wl.nsteps + 1):
+            try:
+                m.rk4_step(eta, phis, wl.dt, 1)
+            except sem.SemError as ex:
+                fail, err = step, str(ex)
+                break
+            if step % 10 == 0:
+                states.append((step, eta.cpu().numpy(), phis.cpu().numpy()))
+        m.close()
+        ser = diag("c2", 0, states)
+        out["c2_as_configured"] = {"H_over_L": 0.08, "dt": wl.dt, "failed_at_step": fail, "error": err,
+                                   "periods_run": (fail - 1 if fail else wl.nsteps) / 200.0, "series": ser}
+        # C2 at H/L = 0.055 for 100 periods
+        import dataclasses
+        wl = dataclasses.replace(c2_steep_periodic(), wave_height=0.055 * c2_steep_periodic().length)
+        e0, p0 = initial_state(wl, column_positions(wl), h)
+        finals = {}
+        for prec in ("fp64", "mixed"):
+            m = sem.Mesh.from_workload(wl, h=h, precision=prec, tol=1e-13 if prec == "fp64" else 1e-12)
+            eta, phis = torch.tensor(e0, device=dev), torch.tensor(p0, device=dev)
+            states = [(0, e0, p0)]
+            t0 = time.perf_counter()
+            for k in range(1, 21):
+                m.rk4_step(eta, phis, wl.dt, 1000)
+                states.append((1000 * k, eta.cpu().numpy(), phis.cpu().numpy()))
+            wall = time.perf_counter() - t0
+            m.close()
+            ser = diag("c2", 0.055, states)
+            m0, E0 = ser[0]["mass"], ser[0]["energy"]
+            scale = 0.5 * wl.wave_height * wl.length
+            out[f"c2_hl0055_{prec}"] = {
+                "steps": 20000, "periods": 100, "wall_s": wall, "series": ser,
+                "max_abs_mass_drift_rel_to_HL2": max(abs(r["mass"] - m0) for r in ser) / scale,
+                "energy_rel_change": (ser[-1]["energy"] - E0) / E0,
+                "energy_increases": sum(1 for a, b in zip(ser, ser[1:]) if b["energy"] > a["energy"])}
+            finals[prec] = states[-1]
+        out["c2_hl0055_mixed_vs_fp64_rel_l2"] = max(rel_l2(finals["mixed"][1], finals["fp64"][1]),
+                                                    rel_l2(finals["mixed"][2], finals["fp64"][2]))
+        # C4, 5000 steps
+        wl = c4_shoal()
+        h = depth_columns(wl, column_positions(wl))
+        finals = {}
+        for prec in ("fp64", "mixed"):
+            m = sem.Mesh.from_workload(wl, h=h, precision=prec, tol=1e-13 if prec == "fp64" else 1e-12)
+            eta = torch.zeros(wl.ncol, dtype=torch.float64, device=dev)
+            phis = torch.zeros_like(eta)
+            t, states = 0.0, []
+            t0 = time.perf_counter()
+            for k in range(1, 11):
+                t = m.rk4_step(eta, phis, wl.dt, 500, t=t)
+                states.append((500 * k, eta.cpu().numpy(), phis.cpu().numpy()))
+            wall = time.perf_counter() - t0
+            m.close()
+            out[f"c4_{prec}"] = {"steps": wl.nsteps, "wall_s": wall, "series": diag("c4", 0, states),
+                                 "max_abs_eta": float(np.abs(states[-1][1]).max())}
+            finals[prec] = states[-1]
+        out["c4_mixed_vs_fp64_rel_l2"] = max(rel_l2(finals["mixed"][1], finals["fp64"][1]),
+                                             rel_l2(finals["mixed"][2], finals["fp64"][2]))
+    finally:
+        pool.close()
+        pool.join()
+    return out
+
+
 def measured_peaks() -> dict:
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -846,6 +948,8 @@ def main():
     ap.add_argument("--no-c5", action="store_true")
     ap.add_argument("--c5-rates", type=float, nargs="+", default=[100.0, 1000.0])
     ap.add_argument("--c5-requests", type=int, default=1000)
+    ap.add_argument("--long-runs", action="store_true",
+                    help="only the full-length C2 and C4 runs with the oracle's volume and energy diagnostics")
     ap.add_argument("--apply-only", default=None,
                     help="comma list of fp64_column,fp64_tile,fp32_tile: time only these applies (for profiling)")
     ap.add_argument("--apply-nx", type=int, default=65536)
@@ -855,6 +959,12 @@ def main():
         import torch
         print(json.dumps(apply_roofline(torch.device("cuda", 0), args.apply_reps, args.apply_nx,
                                         tuple(args.apply_only.split(",")))))
+        return 0
+    if args.long_runs:
+        import torch
+        import paper_1512_02548_gb300 as sem
+        sem.load_library()
+        print(json.dumps({"long_runs": long_runs(torch.device("cuda", 0), host_cores())}))
         return 0
     if args.warmup < 3:
         args.warmup = 3

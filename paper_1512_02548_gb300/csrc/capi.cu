@@ -2,6 +2,7 @@
 // the orchestration of the kernels for one Laplace solve, the recovery, the Zakharov
 // right-hand side and RK4 (§2–§3 of arXiv 1512.02548).
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <cmath>
 #include <cstdio>
@@ -192,6 +193,7 @@ struct sem_mesh {
 // most the co-resident capacity; each instance gets a team of CTAs sized to its work.
 struct BatchLaunch {
   int P = 0, mixed = 0, wide = 1;
+  int csize = 0;                     // cluster teams of csize CTAs each (0: one cooperative launch)
   std::vector<int> members;          // mesh indices
   std::vector<int> team0, nteam;
   std::vector<int> chunk;            // element columns per pass of each member
@@ -203,12 +205,16 @@ struct BatchLaunch {
   int* status_d = nullptr;           // gathered status words of the members
   std::vector<Instance> inst_h;
   std::vector<int> status_h;
+  cudaStream_t stream = nullptr;     // cluster launches: the launch's own stream
+  cudaEvent_t done = nullptr;        // ... and the event that joins it back to the caller's stream
 };
 
 struct sem_batch {
   std::vector<sem_mesh*> meshes;
   std::vector<int> codes;            // per-instance error code of the last step or solve
-  std::vector<BatchLaunch> launches;
+  std::vector<BatchLaunch> launches;     // cooperative plan: one launch per RK stage and group
+  std::vector<BatchLaunch> cl_launches;  // cluster plan: launches on streams of their own (empty: none)
+  cudaEvent_t fork = nullptr;
   int device = 0;
   unsigned char* pool = nullptr;
   // packed device copy of every member's (η, φ̃) for sem_batch_rk4_step_host: η of member i at
@@ -751,6 +757,11 @@ static int mesh_create_impl(const sem_params* pin, const double* x_edges_h, cons
   g.geo64 = D_(o_geo64); g.geo32 = F_(o_geo32); g.invdiag64 = D_(o_id64); g.invdiag32 = F_(o_id32);
   g.status = reinterpret_cast<int*>(m->pool + o_status);
   g.gglob = D_(o_gglob);
+  g.dv_nrow = FastDiv::make(nrow);
+  g.dv_nr = FastDiv::make(nrow - 1);
+  g.dv_colsz = FastDiv::make(Q * nrow);
+  g.dv_elsz = FastDiv::make(Nz * Q * Q);
+  g.dv_qn = FastDiv::make(Q * (nrow - 1));
   g.bar_timeout_ns = kBarrierTimeoutNs;
   g.drop_rank = -1;
   g.trace = nullptr;
@@ -1039,13 +1050,226 @@ int sem_rk4_step_host(sem_mesh* m, double* eta_h, double* phis_h, double* t, dou
 }
 
 // Cost of a team's barriers and cross-CTA round trips per stage, in element-local nodes of work
-// (team sizing in sem_batch_create).
+// (team sizing of the cooperative plan).
 constexpr double kTeamSyncNodes = 256.0;
 // Groups of at most this many instances use the one-CTA-per-SM stage build.
 constexpr int kBatchNarrowMax = 8;
 // Dynamic shared memory per CTA up to which batch members widen their passes (two CTAs per SM,
 // or one).
 constexpr size_t kBatchSmemWide = 88 * 1024, kBatchSmemNarrow = 176 * 1024;
+// Largest thread-block cluster (the non-portable limit of this architecture).
+constexpr int kMaxCluster = 16;
+
+}  // extern "C"
+
+namespace {
+
+int batch_wide(size_t group_size) {
+  const char* wenv = std::getenv("SEM_BATCH_WIDE");
+  return wenv ? (std::atoi(wenv) != 0) : (group_size > (size_t)kBatchNarrowMax ? 1 : 0);
+}
+
+int batch_limit(const sem_mesh* m) {   // ≤ grid: the halo and reduction buffers are sized by it
+  return std::max(1, std::min(m->grid, (m->p.Nx + m->g.chunk - 1) / m->g.chunk));
+}
+
+// Each member's CTAs take their element columns in as few passes as the launch's shared memory
+// allows: a budget per CTA that keeps the build's CTAs per SM.  Returns the launch's dynamic
+// shared memory.
+size_t widen_passes(BatchLaunch& L, sem_mesh* const* meshes, size_t smem) {
+  const size_t budget = L.wide ? kBatchSmemWide : kBatchSmemNarrow;
+  size_t smem_l = smem;
+  L.chunk.clear();
+  for (size_t k = 0; k < L.members.size(); ++k) {
+    const sem_mesh* m = meshes[L.members[k]];
+    const int ne = (m->p.Nx + L.nteam[k] - 1) / L.nteam[k];
+    int E = m->g.chunk;
+    while (E < ne && stage_smem_bytes(m->p.P, m->nrow, m->p.Nz, E + 1) <= budget) ++E;
+    L.chunk.push_back(E);
+    smem_l = std::max(smem_l, stage_smem_bytes(m->p.P, m->nrow, m->p.Nz, E));
+  }
+  return smem_l;
+}
+
+// Cooperative plan: instances grouped by (order, precision), each group split into launches of at
+// most the co-resident CTA count; a launch lasts as long as its slowest team, so the CTAs go one at
+// a time to the team whose estimated stage time is the largest, while that lowers it (the time of a
+// team of c CTAs is taken as w/c element-local nodes per CTA, plus kTeamSyncNodes when c > 1).
+int plan_cooperative(sem_batch* b, sem_mesh* const* meshes, int count, int sms) {
+  std::vector<std::pair<std::pair<int, int>, std::vector<int>>> groups;
+  for (int i = 0; i < count; ++i) {
+    const std::pair<int, int> key(meshes[i]->p.P, meshes[i]->p.precision == SEM_PREC_MIXED ? 1 : 0);
+    auto it = std::find_if(groups.begin(), groups.end(), [&](const auto& g) { return g.first == key; });
+    if (it == groups.end()) groups.push_back({key, {i}});
+    else it->second.push_back(i);
+  }
+  for (auto& grp : groups) {
+    size_t smem = 0;
+    for (int i : grp.second) smem = std::max(smem, meshes[i]->stage_smem_batch);
+    int per_sm = 0;
+    // Build of the stage kernel: two CTAs per SM (128 registers) for groups of many instances,
+    // where more co-resident teams pay; one CTA per SM with the full register file (the
+    // single-mesh build, faster per CTA) for a few instances.  SEM_BATCH_WIDE=0/1 forces either.
+    const int wide = batch_wide(grp.second.size());
+    cudaError_t e = stage_occupancy(grp.first.first, grp.first.second, wide, smem, &per_sm);
+    if (e != cudaSuccess || per_sm < 1) return fail(SEM_ERR_CUDA, "fused stage kernel does not fit");
+    const int cap = per_sm * sms;
+    for (size_t first = 0; first < grp.second.size(); first += cap) {
+      BatchLaunch L;
+      L.P = grp.first.first;
+      L.mixed = grp.first.second;
+      L.wide = wide;
+      const size_t last = std::min(grp.second.size(), first + (size_t)cap);
+      L.members.assign(grp.second.begin() + first, grp.second.begin() + last);
+      std::vector<double> w;
+      for (int i : L.members) {
+        const sem_mesh* m = meshes[i];
+        w.push_back((double)m->p.Nx * m->p.Nz * (m->p.P + 1) * (m->p.P + 1));
+      }
+      std::vector<int> c(L.members.size(), 1), limit(L.members.size());
+      for (size_t k = 0; k < L.members.size(); ++k) limit[k] = batch_limit(meshes[L.members[k]]);
+      auto est = [&](size_t k, int ck) { return w[k] / ck + (ck > 1 ? kTeamSyncNodes : 0.0); };
+      {
+        std::priority_queue<std::pair<double, size_t>> pq;
+        for (size_t k = 0; k < c.size(); ++k) pq.push({est(k, 1), k});
+        int used = (int)c.size();
+        while (used < cap && !pq.empty()) {
+          const size_t k = pq.top().second;
+          pq.pop();
+          if (c[k] >= limit[k] || est(k, c[k] + 1) >= est(k, c[k])) continue;   // this team is done
+          ++c[k];
+          ++used;
+          pq.push({est(k, c[k]), k});
+        }
+      }
+      int acc = 0;
+      for (size_t k = 0; k < c.size(); ++k) { L.team0.push_back(acc); L.nteam.push_back(c[k]); acc += c[k]; }
+      L.grid = acc;
+      size_t smem_l = widen_passes(L, meshes, smem);
+      int per2 = 0;
+      if (smem_l > smem && (stage_occupancy(L.P, L.mixed, wide, smem_l, &per2) != cudaSuccess || per2 < per_sm)) {
+        for (size_t k = 0; k < L.members.size(); ++k) L.chunk[k] = meshes[L.members[k]]->g.chunk;
+        smem_l = smem;
+      }
+      L.smem = smem_l;
+      b->launches.push_back(std::move(L));
+    }
+  }
+  return SEM_OK;
+}
+
+// Cluster plan: each member's team is one thread-block cluster, so no CTA waits on a CTA outside
+// its cluster; the launches need no co-residency, the hardware starts clusters as CTA slots free
+// up, and the launches of all groups run at the same time on streams of their own.  A step then
+// lasts about the larger of the total work per CTA slot and the longest team's time, so a member's
+// team is the smallest power of two c ≤ 16 (and ≤ its buffer limit) whose work per CTA is at most
+// half the total work per CTA slot (work: element-local nodes × the apply's flops per node).
+// Members are grouped by (order, precision, c), the largest first within a launch.  Returns
+// false (and builds nothing) when some group's cluster does not fit on the device.
+bool plan_clusters(sem_batch* b, sem_mesh* const* meshes, int count, int sms) {
+  std::vector<double> w(count);
+  double total = 0.0;
+  for (int i = 0; i < count; ++i) {
+    const sem_mesh* m = meshes[i];
+    const int Q = m->p.P + 1;
+    w[i] = (double)m->p.Nx * m->p.Nz * Q * Q * (8.0 * Q + 7.0);
+    total += w[i];
+  }
+  const double slots = 2.0 * sms;
+  const double per_cta = 0.5 * total / slots;
+  std::vector<std::pair<std::array<int, 3>, std::vector<int>>> groups;
+  for (int i = 0; i < count; ++i) {
+    const int cmax = std::min(kMaxCluster, batch_limit(meshes[i]));
+    const double want = per_cta > 0.0 ? w[i] / per_cta : 1.0;
+    int c = 1;
+    while (c < want && 2 * c <= cmax) c *= 2;
+    const std::array<int, 3> key{meshes[i]->p.P, meshes[i]->p.precision == SEM_PREC_MIXED ? 1 : 0, c};
+    auto it = std::find_if(groups.begin(), groups.end(), [&](const auto& g) { return g.first == key; });
+    if (it == groups.end()) groups.push_back({key, {i}});
+    else it->second.push_back(i);
+  }
+  std::vector<BatchLaunch> out;
+  for (auto& grp : groups) {
+    BatchLaunch L;
+    L.P = grp.first[0];
+    L.mixed = grp.first[1];
+    L.csize = grp.first[2];
+    L.wide = batch_wide(grp.second.size());
+    L.members = grp.second;
+    std::stable_sort(L.members.begin(), L.members.end(), [&](int a, int c) { return w[a] > w[c]; });
+    size_t smem = 0;
+    for (int i : L.members) smem = std::max(smem, meshes[i]->stage_smem_batch);
+    for (size_t k = 0; k < L.members.size(); ++k) {
+      L.team0.push_back((int)k * L.csize);
+      L.nteam.push_back(L.csize);
+    }
+    L.grid = (int)L.members.size() * L.csize;
+    int fit = 0;
+    if (cluster_fit(L.P, L.mixed, L.wide, L.csize, smem, &fit) != cudaSuccess || fit < 1) {
+      cudaGetLastError();
+      return false;
+    }
+    size_t smem_l = widen_passes(L, meshes, smem);
+    int fit2 = 0;
+    if (smem_l > smem && (cluster_fit(L.P, L.mixed, L.wide, L.csize, smem_l, &fit2) != cudaSuccess || fit2 < fit)) {
+      cudaGetLastError();
+      for (size_t k = 0; k < L.members.size(); ++k) L.chunk[k] = meshes[L.members[k]]->g.chunk;
+      smem_l = smem;
+    }
+    L.smem = smem_l;
+    out.push_back(std::move(L));
+  }
+  b->cl_launches = std::move(out);
+  return true;
+}
+
+// A plan's device arrays (descriptors, CTA map, barrier words, gathered status) from the pool.
+int carve_plan(sem_batch* b, std::vector<BatchLaunch>& plan, size_t& off) {
+  for (auto& L : plan) {
+    L.inst_d = reinterpret_cast<Instance*>(b->pool + off);
+    off += (sizeof(Instance) * L.members.size() + 255) & ~size_t(255);
+    L.cta_d = reinterpret_cast<int*>(b->pool + off);
+    off += (sizeof(int) * (size_t)L.grid + 255) & ~size_t(255);
+    L.bars_d = reinterpret_cast<unsigned int*>(b->pool + off);
+    off += (sizeof(unsigned) * 2 * L.members.size() + 255) & ~size_t(255);
+    L.status_d = reinterpret_cast<int*>(b->pool + off);
+    off += (sizeof(int) * L.members.size() + 255) & ~size_t(255);
+    std::vector<int> map(L.grid);
+    for (size_t k = 0; k < L.members.size(); ++k)
+      for (int c = 0; c < L.nteam[k]; ++c) map[L.team0[k] + c] = (int)k;
+    CUDA_TRY(cudaMemcpy(L.cta_d, map.data(), sizeof(int) * L.grid, cudaMemcpyHostToDevice));
+    L.inst_h.resize(L.members.size());
+    L.status_h.resize(L.members.size());
+    if (L.csize > 0) {
+      CUDA_TRY(cudaStreamCreateWithFlags(&L.stream, cudaStreamNonBlocking));
+      CUDA_TRY(cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming));
+    }
+  }
+  return SEM_OK;
+}
+
+size_t plan_bytes(const std::vector<BatchLaunch>& plan) {
+  size_t total = 0;
+  for (const auto& L : plan)
+    total += ((sizeof(Instance) * L.members.size() + 255) & ~size_t(255)) +
+             ((sizeof(int) * (size_t)L.grid + 255) & ~size_t(255)) +
+             ((sizeof(unsigned) * 2 * L.members.size() + 255) & ~size_t(255)) +
+             ((sizeof(int) * L.members.size() + 255) & ~size_t(255));
+  return total;
+}
+
+void release_plan(std::vector<BatchLaunch>& plan) {
+  for (auto& L : plan) {
+    if (L.stream) cudaStreamDestroy(L.stream);
+    if (L.done) cudaEventDestroy(L.done);
+    L.stream = nullptr;
+    L.done = nullptr;
+  }
+}
+
+}  // namespace
+
+extern "C" {
 
 int sem_batch_create(sem_mesh* const* meshes, int count, sem_batch** out) {
   if (!out) return fail(SEM_ERR_INVALID_ARG, "out is NULL");
@@ -1066,123 +1290,29 @@ int sem_batch_create(sem_mesh* const* meshes, int count, sem_batch** out) {
   sem_batch* b = new sem_batch;
   b->device = dev;
   b->meshes.assign(meshes, meshes + count);
-  // group by (order, precision)
-  std::vector<std::pair<std::pair<int, int>, std::vector<int>>> groups;
-  for (int i = 0; i < count; ++i) {
-    const std::pair<int, int> key(meshes[i]->p.P, meshes[i]->p.precision == SEM_PREC_MIXED ? 1 : 0);
-    auto it = std::find_if(groups.begin(), groups.end(), [&](const auto& g) { return g.first == key; });
-    if (it == groups.end()) groups.push_back({key, {i}});
-    else it->second.push_back(i);
-  }
-  size_t total = 0;
-  for (auto& grp : groups) {
-    size_t smem = 0;
-    for (int i : grp.second) smem = std::max(smem, meshes[i]->stage_smem_batch);
-    int per_sm = 0;
-    // Build of the stage kernel: two CTAs per SM (128 registers) for groups of many instances,
-    // where more co-resident teams pay; one CTA per SM with the full register file (the
-    // single-mesh build, faster per CTA) for a few instances.  SEM_BATCH_WIDE=0/1 forces either.
-    const char* wenv = std::getenv("SEM_BATCH_WIDE");
-    const int wide = wenv ? (std::atoi(wenv) != 0) : (grp.second.size() > (size_t)kBatchNarrowMax ? 1 : 0);
-    cudaError_t e = stage_occupancy(grp.first.first, grp.first.second, wide, smem, &per_sm);
-    if (e != cudaSuccess || per_sm < 1) { delete b; return fail(SEM_ERR_CUDA, "fused stage kernel does not fit"); }
-    const int cap = per_sm * sms;
-    // split into launches of at most `cap` instances, then share the CTAs by work
-    for (size_t first = 0; first < grp.second.size(); first += cap) {
-      BatchLaunch L;
-      L.P = grp.first.first;
-      L.mixed = grp.first.second;
-      L.wide = wide;
-      L.smem = smem;
-      const size_t last = std::min(grp.second.size(), first + (size_t)cap);
-      L.members.assign(grp.second.begin() + first, grp.second.begin() + last);
-      double wsum = 0.0;
-      std::vector<double> w;
-      for (int i : L.members) {
-        const sem_mesh* m = meshes[i];
-        w.push_back((double)m->p.Nx * m->p.Nz * (m->p.P + 1) * (m->p.P + 1));
-        wsum += w.back();
-      }
-      // Team sizes: a launch lasts as long as its slowest team, so the CTAs go one at a time to the
-      // team whose estimated stage time is the largest, while that lowers it: the time of a team
-      // of c CTAs is taken as w/c (element-local nodes per CTA) plus kTeamSyncNodes when c > 1
-      // (the team barriers and cross-CTA round trips, in the same units).
-      (void)wsum;
-      std::vector<int> c(L.members.size(), 1), limit(L.members.size());
-      for (size_t k = 0; k < L.members.size(); ++k) {
-        const sem_mesh* m = meshes[L.members[k]];
-        limit[k] = std::max(1, std::min(m->grid, (m->p.Nx + m->g.chunk - 1) / m->g.chunk));   // ≤ grid: buffer sizes
-      }
-      auto est = [&](size_t k, int ck) { return w[k] / ck + (ck > 1 ? kTeamSyncNodes : 0.0); };
-      {
-        std::priority_queue<std::pair<double, size_t>> pq;
-        for (size_t k = 0; k < c.size(); ++k) pq.push({est(k, 1), k});
-        int used = (int)c.size();
-        while (used < cap && !pq.empty()) {
-          const size_t k = pq.top().second;
-          pq.pop();
-          if (c[k] >= limit[k] || est(k, c[k] + 1) >= est(k, c[k])) continue;   // this team is done
-          ++c[k];
-          ++used;
-          pq.push({est(k, c[k]), k});
-        }
-      }
-      int acc = 0;
-      for (size_t k = 0; k < c.size(); ++k) { L.team0.push_back(acc); L.nteam.push_back(c[k]); acc += c[k]; }
-      L.grid = acc;
-      // each member's CTAs take their element columns in as few passes as the launch's shared
-      // memory allows (a budget per CTA that keeps the build's CTAs per SM)
-      {
-        const size_t budget = wide ? kBatchSmemWide : kBatchSmemNarrow;
-        size_t smem_l = smem;
-        for (size_t k = 0; k < L.members.size(); ++k) {
-          const sem_mesh* m = meshes[L.members[k]];
-          const int ne = (m->p.Nx + c[k] - 1) / c[k];
-          int E = m->g.chunk;
-          while (E < ne && stage_smem_bytes(m->p.P, m->nrow, m->p.Nz, E + 1) <= budget) ++E;
-          L.chunk.push_back(E);
-          smem_l = std::max(smem_l, stage_smem_bytes(m->p.P, m->nrow, m->p.Nz, E));
-        }
-        int per2 = 0;
-        if (smem_l > smem &&
-            (stage_occupancy(L.P, L.mixed, wide, smem_l, &per2) != cudaSuccess || per2 < per_sm)) {
-          for (size_t k = 0; k < L.members.size(); ++k) L.chunk[k] = meshes[L.members[k]]->g.chunk;
-          smem_l = smem;
-        }
-        L.smem = smem_l;
-      }
-      total += ((sizeof(Instance) * L.members.size() + 255) & ~size_t(255)) +
-               ((sizeof(int) * (size_t)L.grid + 255) & ~size_t(255)) +
-               ((sizeof(unsigned) * 2 * L.members.size() + 255) & ~size_t(255)) +
-               ((sizeof(int) * L.members.size() + 255) & ~size_t(255));
-      b->launches.push_back(std::move(L));
-    }
-  }
+  int rc = plan_cooperative(b, meshes, count, sms);
+  if (rc) { delete b; return rc; }
+  const char* cenv = std::getenv("SEM_BATCH_CLUSTER");   // 0: cooperative launches only
+  if (!(cenv && std::atoi(cenv) == 0)) plan_clusters(b, meshes, count, sms);
   for (int i = 0; i < count; ++i) {
     b->off.push_back(b->ncol_total);
     b->ncol_total += (size_t)meshes[i]->ncol;
   }
-  total += (2 * b->ncol_total * sizeof(double) + 255) & ~size_t(255);
+  const size_t state_bytes = (2 * b->ncol_total * sizeof(double) + 255) & ~size_t(255);
+  const size_t total = state_bytes + plan_bytes(b->launches) + plan_bytes(b->cl_launches);
   cudaError_t ae = dev_alloc(dev, total + 256, reinterpret_cast<void**>(&b->pool));
   if (ae != cudaSuccess) { delete b; return fail(SEM_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(ae)); }
   b->state = reinterpret_cast<double*>(b->pool);
-  size_t off = (2 * b->ncol_total * sizeof(double) + 255) & ~size_t(255);
-  for (auto& L : b->launches) {
-    L.inst_d = reinterpret_cast<Instance*>(b->pool + off);
-    off += (sizeof(Instance) * L.members.size() + 255) & ~size_t(255);
-    L.cta_d = reinterpret_cast<int*>(b->pool + off);
-    off += (sizeof(int) * (size_t)L.grid + 255) & ~size_t(255);
-    L.bars_d = reinterpret_cast<unsigned int*>(b->pool + off);
-    off += (sizeof(unsigned) * 2 * L.members.size() + 255) & ~size_t(255);
-    L.status_d = reinterpret_cast<int*>(b->pool + off);
-    off += (sizeof(int) * L.members.size() + 255) & ~size_t(255);
-    std::vector<int> map(L.grid);
-    for (size_t k = 0; k < L.members.size(); ++k)
-      for (int c = 0; c < L.nteam[k]; ++c) map[L.team0[k] + c] = (int)k;
-    cudaError_t e = cudaMemcpy(L.cta_d, map.data(), sizeof(int) * L.grid, cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) { dev_free(dev, b->pool); delete b; return fail(SEM_ERR_CUDA, cudaGetErrorString(e)); }
-    L.inst_h.resize(L.members.size());
-    L.status_h.resize(L.members.size());
+  size_t off = state_bytes;
+  rc = carve_plan(b, b->launches, off);
+  if (!rc) rc = carve_plan(b, b->cl_launches, off);
+  if (!rc && !b->cl_launches.empty() && cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess)
+    rc = fail(SEM_ERR_CUDA, "event creation failed");
+  if (rc) {
+    release_plan(b->cl_launches);
+    dev_free(dev, b->pool);
+    delete b;
+    return rc;
   }
   *out = b;
   return SEM_OK;
@@ -1192,6 +1322,8 @@ void sem_batch_destroy(sem_batch* b) {
   if (!b) return;
   DeviceGuard dg(b->device);
   cudaDeviceSynchronize();   // no work of this batch may still run when its memory is reused
+  release_plan(b->cl_launches);
+  if (b->fork) cudaEventDestroy(b->fork);
   for (auto& pr : b->events) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
   for (cudaEvent_t e : b->spare) cudaEventDestroy(e);
   dev_free(b->device, b->pool);
@@ -1218,22 +1350,34 @@ void sem_trim_cache(void) {
 
 int sem_batch_info(const sem_batch* b, int* launches_per_stage, int* ctas) {
   if (!b) return fail(SEM_ERR_INVALID_ARG, "NULL batch");
+  const auto& plan = b->cl_launches.empty() ? b->launches : b->cl_launches;
   int tot = 0;
-  for (const auto& L : b->launches) tot += L.grid;
-  if (launches_per_stage) *launches_per_stage = (int)b->launches.size();
+  for (const auto& L : plan) tot += L.grid;
+  if (launches_per_stage) *launches_per_stage = (int)plan.size();
   if (ctas) *ctas = tot;
   return SEM_OK;
 }
 
+}  // extern "C"
+
 namespace {
-int batch_status(sem_batch* b, cudaStream_t s);
+int batch_status(sem_batch* b, std::vector<BatchLaunch>& plan, cudaStream_t s);
+
+// The cluster plan serves a call unless a member carries the barrier testing hook, whose early
+// CTA exit only the cooperative launches' bounded barriers turn into an error.
+bool use_clusters(const sem_batch* b) {
+  if (b->cl_launches.empty()) return false;
+  for (const sem_mesh* m : b->meshes)
+    if (m->g.drop_rank >= 0 || m->g.bar_timeout_ns != kBarrierTimeoutNs) return false;
+  return true;
+}
 
 cudaError_t take_batch_event(sem_batch* b, cudaEvent_t* ev) {
   if (!b->spare.empty()) { *ev = b->spare.back(); b->spare.pop_back(); return cudaSuccess; }
   return cudaEventCreate(ev);
 }
 
-// One stage launch of a batch group, bracketed by events while timing is on.
+// One stage launch of a batch group on stream s, bracketed by events while timing is on.
 cudaError_t batch_launch(sem_batch* b, const BatchLaunch& L, const StageArgs& a, cudaStream_t s) {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaError_t e;
@@ -1242,14 +1386,38 @@ cudaError_t batch_launch(sem_batch* b, const BatchLaunch& L, const StageArgs& a,
     if ((e = take_batch_event(b, &e1)) != cudaSuccess) return e;
     if ((e = cudaEventRecord(e0, s)) != cudaSuccess) return e;
   }
-  if ((e = launch_stage(L.P, L.mixed, L.wide, a, L.grid, L.smem, s)) != cudaSuccess) return e;
+  if (L.csize > 0) e = launch_stage_cluster(L.P, L.mixed, L.wide, a, L.grid, L.csize, L.smem, s);
+  else e = launch_stage(L.P, L.mixed, L.wide, a, L.grid, L.smem, s);
+  if (e != cudaSuccess) return e;
   if (b->timing) {
     if ((e = cudaEventRecord(e1, s)) != cudaSuccess) return e;
     b->events.emplace_back(e0, e1);
   }
   return cudaSuccess;
 }
+
+// The cluster plan: each group's stage launches in order on the group's own stream, the streams
+// forked from and joined back to s.  stage 0: the Laplace solve alone; else nsteps RK4 steps.
+cudaError_t run_clusters(sem_batch* b, int stage, int nsteps, cudaStream_t s) {
+  cudaError_t e;
+  if ((e = cudaEventRecord(b->fork, s)) != cudaSuccess) return e;
+  for (auto& L : b->cl_launches)
+    if ((e = cudaStreamWaitEvent(L.stream, b->fork, 0)) != cudaSuccess) return e;
+  for (int step = 0; step < (stage == 0 ? 1 : nsteps); ++step)
+    for (int st = (stage == 0 ? 0 : 1); st <= (stage == 0 ? 0 : 4); ++st)
+      for (auto& L : b->cl_launches) {
+        const StageArgs a{L.inst_d, L.cta_d, nullptr, st, step};
+        if ((e = batch_launch(b, L, a, L.stream)) != cudaSuccess) return e;
+      }
+  for (auto& L : b->cl_launches) {
+    if ((e = cudaEventRecord(L.done, L.stream)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(s, L.done, 0)) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
 }  // namespace
+
+extern "C" {
 
 int sem_batch_rk4_step(sem_batch* b, double* const* eta_d, double* const* phis_d, double* t_h, const double* dt_h,
                        int nsteps, void* stream) {
@@ -1259,7 +1427,9 @@ int sem_batch_rk4_step(sem_batch* b, double* const* eta_d, double* const* phis_d
     if (!eta_d[i] || !phis_d[i] || !(dt_h[i] > 0.0)) return fail(SEM_ERR_INVALID_ARG, "bad instance state");
   DeviceGuard dg(b->device);
   cudaStream_t s = (cudaStream_t)stream;
-  for (auto& L : b->launches) {
+  const bool cl = use_clusters(b);
+  auto& plan = cl ? b->cl_launches : b->launches;
+  for (auto& L : plan) {
     for (size_t k = 0; k < L.members.size(); ++k) {
       const int i = L.members[k];
       L.inst_h[k] = make_instance(b->meshes[i], eta_d[i], phis_d[i], t_h ? t_h[i] : 0.0, dt_h[i], L.team0[k],
@@ -1268,16 +1438,20 @@ int sem_batch_rk4_step(sem_batch* b, double* const* eta_d, double* const* phis_d
     CUDA_TRY(cudaMemcpyAsync(L.inst_d, L.inst_h.data(), sizeof(Instance) * L.members.size(),
                              cudaMemcpyHostToDevice, s));
   }
-  for (int step = 0; step < nsteps; ++step)
-    for (int stage = 1; stage <= 4; ++stage)
-      for (auto& L : b->launches) {
-        CUDA_TRY(cudaMemsetAsync(L.bars_d, 0, 2 * sizeof(unsigned int) * L.members.size(), s));
-        const StageArgs a{L.inst_d, L.cta_d, L.bars_d, stage, step};
-        CUDA_TRY(batch_launch(b, L, a, s));
-      }
+  if (cl) {
+    if (nsteps > 0) CUDA_TRY(run_clusters(b, 1, nsteps, s));
+  } else {
+    for (int step = 0; step < nsteps; ++step)
+      for (int stage = 1; stage <= 4; ++stage)
+        for (auto& L : plan) {
+          CUDA_TRY(cudaMemsetAsync(L.bars_d, 0, 2 * sizeof(unsigned int) * L.members.size(), s));
+          const StageArgs a{L.inst_d, L.cta_d, L.bars_d, stage, step};
+          CUDA_TRY(batch_launch(b, L, a, s));
+        }
+  }
   if (nsteps > 0)
     for (int i = 0; i < n; ++i) set_history(b->meshes[i], eta_d[i], phis_d[i], dt_h[i]);
-  int rc = batch_status(b, s);
+  int rc = batch_status(b, plan, s);
   if (t_h)
     for (int i = 0; i < n; ++i) t_h[i] += nsteps * dt_h[i];
   return rc;
@@ -1291,7 +1465,9 @@ int sem_batch_laplace_solve(sem_batch* b, const double* const* eta_d, const doub
     if (!eta_d[i] || !phis_d[i] || !Phi_d[i]) return fail(SEM_ERR_INVALID_ARG, "bad instance state");
   DeviceGuard dg(b->device);
   cudaStream_t s = (cudaStream_t)stream;
-  for (auto& L : b->launches) {
+  const bool cl = use_clusters(b);
+  auto& plan = cl ? b->cl_launches : b->launches;
+  for (auto& L : plan) {
     for (size_t k = 0; k < L.members.size(); ++k) {
       const int i = L.members[k];
       L.inst_h[k] = make_instance(b->meshes[i], const_cast<double*>(eta_d[i]), const_cast<double*>(phis_d[i]),
@@ -1301,12 +1477,16 @@ int sem_batch_laplace_solve(sem_batch* b, const double* const* eta_d, const doub
     CUDA_TRY(cudaMemcpyAsync(L.inst_d, L.inst_h.data(), sizeof(Instance) * L.members.size(),
                              cudaMemcpyHostToDevice, s));
   }
-  for (auto& L : b->launches) {
-    CUDA_TRY(cudaMemsetAsync(L.bars_d, 0, 2 * sizeof(unsigned int) * L.members.size(), s));
-    const StageArgs a{L.inst_d, L.cta_d, L.bars_d, 0, 0};
-    CUDA_TRY(batch_launch(b, L, a, s));
+  if (cl) {
+    CUDA_TRY(run_clusters(b, 0, 0, s));
+  } else {
+    for (auto& L : plan) {
+      CUDA_TRY(cudaMemsetAsync(L.bars_d, 0, 2 * sizeof(unsigned int) * L.members.size(), s));
+      const StageArgs a{L.inst_d, L.cta_d, L.bars_d, 0, 0};
+      CUDA_TRY(batch_launch(b, L, a, s));
+    }
   }
-  return batch_status(b, s);
+  return batch_status(b, plan, s);
 }
 
 int sem_batch_rk4_step_host(sem_batch* b, double* eta_h, double* phis_h, double* t_h, const double* dt_h,
@@ -1356,12 +1536,14 @@ int sem_batch_get_timing(sem_batch* b, sem_timing* t) {
   return SEM_OK;
 }
 
+}  // extern "C"
+
 namespace {
 // One gather of every member's status word and one copy per launch group; returns the
 // first failing instance's error.
-int batch_status(sem_batch* b, cudaStream_t s) {
+int batch_status(sem_batch* b, std::vector<BatchLaunch>& plan, cudaStream_t s) {
   const int n = (int)b->meshes.size();
-  for (auto& L : b->launches) {
+  for (auto& L : plan) {
     CUDA_TRY(launch_gather_status(L.inst_d, (int)L.members.size(), L.status_d, s));
     CUDA_TRY(cudaMemcpyAsync(L.status_h.data(), L.status_d, sizeof(int) * L.members.size(),
                              cudaMemcpyDeviceToHost, s));
@@ -1369,7 +1551,7 @@ int batch_status(sem_batch* b, cudaStream_t s) {
   CUDA_TRY(cudaStreamSynchronize(s));
   int rc = SEM_OK, first = n;
   b->codes.assign(n, SEM_OK);
-  for (const auto& L : b->launches)
+  for (const auto& L : plan)
     for (size_t k = 0; k < L.members.size(); ++k) {
       b->codes[L.members[k]] = status_code(L.status_h[k]);
       if (L.status_h[k] && L.members[k] < first) {
@@ -1387,6 +1569,8 @@ int batch_status(sem_batch* b, cudaStream_t s) {
   return rc;
 }
 }  // namespace
+
+extern "C" {
 
 int sem_batch_status(const sem_batch* b, int* codes_h) {
   if (!b || !codes_h) return fail(SEM_ERR_INVALID_ARG, "NULL argument");

@@ -195,6 +195,20 @@ cudaError_t launch_stage(int P, int mixed, int wide, const StageArgs& a, int gri
   return e;
 }
 
+cudaError_t cluster_fit(int P, int mixed, int wide, int csize, size_t smem, int* active_clusters) {
+  cudaError_t e = cudaSuccess;
+  SEM_DISPATCH_P(P, (e = cluster_fit_impl<PP>(mixed, wide, csize, smem, active_clusters)));
+  return e;
+}
+
+cudaError_t launch_stage_cluster(int P, int mixed, int wide, const StageArgs& a, int grid, int csize, size_t smem,
+                                 cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  SEM_DISPATCH_P(P, (e = launch_stage_cluster_impl<PP>(mixed, wide, a, grid, csize, smem, s)));
+  count_launch();
+  return e;
+}
+
 __global__ void k_gather_status(const Instance* __restrict__ inst, int n, int* __restrict__ out) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;

@@ -17,4 +17,6 @@ template cudaError_t launch_prec_setup_impl<SEM_ORDER>(const DevGeom&, const Pre
 template cudaError_t launch_apply_tile_impl<SEM_ORDER>(int, const DevGeom&, const void*, void*, cudaStream_t);
 template cudaError_t stage_occupancy_impl<SEM_ORDER>(int, int, size_t, int*);
 template cudaError_t launch_stage_impl<SEM_ORDER>(int, int, const StageArgs&, int, size_t, cudaStream_t);
+template cudaError_t cluster_fit_impl<SEM_ORDER>(int, int, int, size_t, int*);
+template cudaError_t launch_stage_cluster_impl<SEM_ORDER>(int, int, const StageArgs&, int, int, size_t, cudaStream_t);
 }  // namespace semgb

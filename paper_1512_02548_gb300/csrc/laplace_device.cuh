@@ -211,7 +211,7 @@ __device__ void fill_gcache(const DevGeom& g, int e0, int e1, double* gc) {
   const int elsz = g.Nz * Q * Q;
   const double* w = c_w64 + w_off(P);
   for (int t = threadIdx.x; t < (e1 - e0) * elsz; t += blockDim.x) {
-    const int e = t / elsz, rem0 = t - e * elsz;
+    const int e = g.dv_elsz.div(t), rem0 = t - e * elsz;
     const int l = rem0 / (Q * Q), rem = rem0 - l * (Q * Q), a = rem / Q, b = rem - a * Q;
     const int ge = e0 + e;
     const double* geo = g.geo64 + (size_t)ge * Q * 4 + a * 4;
@@ -244,13 +244,13 @@ __device__ __forceinline__ T apply_element_chunk(const DevGeom& g, Smem<P, T>& s
     }
   }
   for (int t = threadIdx.x; t < ne * colsz; t += blockDim.x) {
-    const int e = t / colsz, rem = t - e * colsz;
-    const int a = rem / nrow, iz = rem - a * nrow;
+    const int e = g.dv_colsz.div(t), rem = t - e * colsz;
+    const int a = g.dv_nrow.div(rem), iz = rem - a * nrow;
     s.X[t] = loadx(ex0 + e, a, iz);
   }
   __syncthreads();
   for (int t = threadIdx.x; t < ne * elsz; t += blockDim.x) {
-    const int e = t / elsz, rem0 = t - e * elsz;
+    const int e = g.dv_elsz.div(t), rem0 = t - e * elsz;
     const int l = rem0 / (Q * Q), rem = rem0 - l * (Q * Q), a = rem / Q, b = rem - a * Q;
     const T* Xe = s.X + e * colsz;
     const T* Xrow = Xe + l * P + b;              // Xrow[c*nrow]: row l·P+b, column c
@@ -279,8 +279,8 @@ __device__ __forceinline__ T apply_element_chunk(const DevGeom& g, Smem<P, T>& s
   __syncthreads();
   T part = 0;
   for (int t = threadIdx.x; t < ne * colsz; t += blockDim.x) {
-    const int e = t / colsz, rem = t - e * colsz;
-    const int a = rem / nrow, iz = rem - a * nrow;
+    const int e = g.dv_colsz.div(t), rem = t - e * colsz;
+    const int a = g.dv_nrow.div(rem), iz = rem - a * nrow;
     const int l = iz / P, b = iz - l * P;
     const T* F1e = s.F1 + e * elsz;
     const T* F2e = s.F2 + e * elsz;
@@ -356,7 +356,15 @@ struct Team {
   double* part;          // reduction partials [4 slots][4 values][stride]
   int stride;
   unsigned long long timeout_ns;   // limit of each barrier wait (2 s unless a test sets it)
+  int cluster;           // 1: the team is one thread-block cluster (hardware cluster barrier)
 };
+
+// Barrier of every thread of a thread-block cluster, with release/acquire at cluster scope: the
+// writes of every CTA of the cluster before it (global and shared memory) are visible to every
+// CTA after it.  Executed by all threads of every CTA of the cluster.
+static __device__ __forceinline__ void cluster_barrier() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
 
 // Returns false (and sets ST_TIMEOUT) if the other CTAs of the team did not arrive in time;
 // the caller must then return without touching another barrier.
@@ -395,6 +403,10 @@ static __device__ __forceinline__ void trace_mark(const DevGeom& g, const Team& 
 #endif
 
 static __device__ __forceinline__ bool grid_barrier(const Team& tm, int* s_flag) {
+  if (tm.cluster && tm.size > 1) {
+    cluster_barrier();
+    return true;
+  }
   __syncthreads();
   if (tm.size == 1) return true;
   if (threadIdx.x == 0) {
@@ -562,15 +574,15 @@ __device__ void cg_update(const DevGeom& g, Smem<P, T>& s, const Range& R, const
   for (int ex0 = R.e0; ex0 < R.e1; ex0 += E) {
     const int ne = min(E, R.e1 - ex0);
     for (int t = threadIdx.x; t < ne * qn; t += blockDim.x) {
-      const int e = t / qn, rem = t - e * qn;
-      const int a = rem / nr, j = rem - a * nr, ex = ex0 + e;
+      const int e = g.dv_qn.div(t), rem = t - e * qn;
+      const int a = g.dv_nr.div(rem), j = rem - a * nr, ex = ex0 + e;
       const int col = col_of(g, ex, a);
       const size_t i = (size_t)col * nrow + j;
       const bool own = owns_local_col(g, ex, a);
       T rv;
       if (update) {
         T wv = ldcg(V.w + i);
-        if (has_left_edge(g, col)) wv += ldcg(V.edge + (size_t)left_element(g, col) * nrow + j);
+        if (has_left_edge_p<P>(g, col)) wv += ldcg(V.edge + (size_t)left_element_p<P>(g, col) * nrow + j);
         const T sv = first ? wv : fmx(beta, ldcg(s_old + i), wv);
         rv = fmx(-alpha, sv, ldcg(r_old + i));
         if (own) {
@@ -595,8 +607,8 @@ __device__ void cg_update(const DevGeom& g, Smem<P, T>& s, const Range& R, const
     if (precond == PREC_JACOBI) continue;
     __syncthreads();
     for (int t = threadIdx.x; t < ne * qn; t += blockDim.x) {
-      const int e = t / qn, rem = t - e * qn;
-      const int a = rem / nr, k = rem - a * nr, ex = ex0 + e;
+      const int e = g.dv_qn.div(t), rem = t - e * qn;
+      const int a = g.dv_nr.div(rem), k = rem - a * nr, ex = ex0 + e;
       const TP* Xa = X + e * qn + a * nr;
       const TP v = dot4<TP>(pv.S + k, nr, Xa, nr);
       RH[t] = v;
@@ -604,7 +616,7 @@ __device__ void cg_update(const DevGeom& g, Smem<P, T>& s, const Range& R, const
     }
     __syncthreads();
     for (int t = threadIdx.x; t < ne * nr; t += blockDim.x) {
-      const int e = t / nr, k = t - e * nr, ex = ex0 + e;
+      const int e = g.dv_nr.div(t), k = t - e * nr, ex = ex0 + e;
       const TP* RHe = RH + e * qn;
       const TP* Zk = pv.Z + ((size_t)k * g.Nx + ex) * 2 * Pm;
       // the assembled residual at an interface node enters once: with the element that owns
@@ -662,8 +674,8 @@ __device__ void phase_backsub(const DevGeom& g, Smem<P, T>& s, const Range& R, c
   for (int ex0 = R.e0; ex0 < R.e1; ex0 += E) {
     const int ne = min(E, R.e1 - ex0);
     for (int t = threadIdx.x; t < ne * qn; t += blockDim.x) {
-      const int e = t / qn, rem = t - e * qn;
-      const int a = rem / nr, k = rem - a * nr, ex = ex0 + e;
+      const int e = g.dv_qn.div(t), rem = t - e * qn;
+      const int a = g.dv_nr.div(rem), k = rem - a * nr, ex = ex0 + e;
       const int jl = ex, jr = (ex + 1 == N) ? 0 : ex + 1;
       const TP zl = ldcg(pv.zb + (size_t)k * N + jl);
       const TP zr = ldcg(pv.zb + (size_t)k * N + jr);
@@ -684,8 +696,8 @@ __device__ void phase_backsub(const DevGeom& g, Smem<P, T>& s, const Range& R, c
     }
     __syncthreads();
     for (int t = threadIdx.x; t < ne * qn; t += blockDim.x) {
-      const int e = t / qn, rem = t - e * qn;
-      const int a = rem / nr, j = rem - a * nr, ex = ex0 + e;
+      const int e = g.dv_qn.div(t), rem = t - e * qn;
+      const int a = g.dv_nr.div(rem), j = rem - a * nr, ex = ex0 + e;
       const bool own = owns_local_col(g, ex, a);
       const bool halo = is_halo_col(g, R, ex, a);
       if (!own && !halo) continue;
@@ -839,26 +851,34 @@ __device__ bool fp64_residual(const DevGeom& g, Smem<P, double>& s, const Range&
           else A.edge64[(size_t)e * nrow + iz] = y;
         },
         gce);
-    if (want_b)
-      apply_element_chunk<P, double>(
-          g, s, ex0, ne,
-          [&](int e, int a, int iz) -> double { return iz == nrow - 1 ? phis[col_of(g, e, a)] : 0.0; },
-          [&](int e, int a, int iz, double y) {
-            if (owns_local_col(g, e, a)) A.q64b[(size_t)col_of(g, e, a) * nrow + iz] = y;
-            else A.edge64b[(size_t)e * nrow + iz] = y;
-          },
-          gce);
+  }
+  if (want_b) {
+    // b = −(A[0; φ̃])_I enters only through ‖b‖, the scale of the stopping test, which FP32 gives to
+    // far better than the tolerance needs: an FP32 apply on the same shared memory (the FP64
+    // tables are reloaded after it)
+    Smem<P, float> s32;
+    s32.carve(reinterpret_cast<unsigned char*>(s.D), nrow, g.Nz, g.chunk);
+    s32.load_tables(g);
+    for (int ex0 = R.e0; ex0 < R.e1; ex0 += g.chunk)
+      apply_element_chunk<P, float>(
+          g, s32, ex0, min(g.chunk, R.e1 - ex0),
+          [&](int e, int a, int iz) -> float { return iz == nrow - 1 ? (float)phis[col_of(g, e, a)] : 0.f; },
+          [&](int e, int a, int iz, float y) {
+            if (owns_local_col(g, e, a)) A.q64b[(size_t)col_of(g, e, a) * nrow + iz] = (double)y;
+            else A.edge64b[(size_t)e * nrow + iz] = (double)y;
+          });
+    s.load_tables(g);
   }
   if (!grid_barrier(tm, s_flag)) return false;
   double acc[4] = {0.0, 0.0, dx ? dx[0] : 0.0, 0.0};
   const int ncols = R.c1 - R.c0;
   for (int t = threadIdx.x; t < ncols * nrow; t += blockDim.x) {
-    const int col = R.c0 + t / nrow, iz = t - (t / nrow) * nrow;
+    const int cq = g.dv_nrow.div(t), col = R.c0 + cq, iz = t - cq * nrow;
     const size_t i = (size_t)col * nrow + iz;
     if (iz == nrow - 1) { A.x[i] = phis[col]; continue; }
     if (dx) acc[3] += A.x[i] * A.x[i];
-    const bool le = has_left_edge(g, col);
-    const size_t ie = le ? (size_t)left_element(g, col) * nrow + iz : 0;
+    const bool le = has_left_edge_p<P>(g, col);
+    const size_t ie = le ? (size_t)left_element_p<P>(g, col) * nrow + iz : 0;
     double qv = A.q64[i];
     if (le) qv += ldcg(A.edge64 + ie);
     const double rv = -qv;
@@ -917,7 +937,7 @@ __device__ bool solve_body(const DevGeom& g, const PcgArgs& A, const Team& tm, u
     // φ̃ ≡ 0 on the surface: Φ = 0 is the solution.
     const int ncols = R.c1 - R.c0;
     for (int t = threadIdx.x; t < ncols * nrow; t += blockDim.x) {
-      const int col = R.c0 + t / nrow, iz = t - (t / nrow) * nrow;
+      const int cq = g.dv_nrow.div(t), col = R.c0 + cq, iz = t - cq * nrow;
       if (iz != nrow - 1) A.x[(size_t)col * nrow + iz] = 0.0;
     }
     rr = 0.0;
@@ -955,7 +975,7 @@ __device__ bool solve_body(const DevGeom& g, const PcgArgs& A, const Team& tm, u
       // inner: A δ = r in FP32 from δ = 0, to a relative residual inner_rtol (or the outer target)
       const int ncols = R.c1 - R.c0;
       for (int t = threadIdx.x; t < ncols * nrow; t += blockDim.x) {
-        const int col = R.c0 + t / nrow, iz = t - (t / nrow) * nrow;
+        const int cq = g.dv_nrow.div(t), col = R.c0 + cq, iz = t - cq * nrow;
         const size_t i = (size_t)col * nrow + iz;
         A.d32[i] = 0.f;
         A.r32[i] = iz == nrow - 1 ? 0.f : (float)A.r64[i];
@@ -971,7 +991,7 @@ __device__ bool solve_body(const DevGeom& g, const PcgArgs& A, const Team& tm, u
       // x += δ (FP64), then the true FP64 residual
       dx[0] = 0.0;
       for (int t = threadIdx.x; t < ncols * nrow; t += blockDim.x) {
-        const int col = R.c0 + t / nrow, iz = t - (t / nrow) * nrow;
+        const int cq = g.dv_nrow.div(t), col = R.c0 + cq, iz = t - cq * nrow;
         if (iz == nrow - 1) continue;
         const size_t i = (size_t)col * nrow + iz;
         const double d = (double)A.d32[i];
@@ -1010,7 +1030,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg(DevGeom g, PcgArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[kRedSize];
   __shared__ int s_flag;
-  const Team tm{(int)blockIdx.x, (int)gridDim.x, A.bar, g.status, A.part, A.part_stride, g.bar_timeout_ns};
+  const Team tm{(int)blockIdx.x, (int)gridDim.x, A.bar, g.status, A.part, A.part_stride, g.bar_timeout_ns, 0};
   if (tm.rank == g.drop_rank) return;   // testing hook: see sem_set_barrier_test
   solve_body<P, MIXED>(g, A, tm, smem_raw, red, &s_flag);
 }
@@ -1407,7 +1427,7 @@ __device__ void stage_body(Instance& I, const Team& tm, int stage, int step, uns
       }
       __syncthreads();
       for (int t = threadIdx.x; t < nb * nr; t += blockDim.x) {
-        const int b = t / nr, k = t - b * nr;
+        const int b = g.dv_nr.div(t), k = t - b * nr;
         prec_elem_mode<P>(g, I.ps, e0 + b, k, kxs + b * per, kxs + b * per + Q * Q);
       }
       __syncthreads();
@@ -1519,8 +1539,34 @@ __global__ void __launch_bounds__(kThreads, WIDE ? 2 : 1) k_stage(StageArgs B) {
   }
   __syncthreads();
   const Team tm{(int)blockIdx.x - I.team0, I.nteam, B.bars + 2 * ii, I.g.status, I.pa.part, I.pa.part_stride,
-                I.g.bar_timeout_ns};
+                I.g.bar_timeout_ns, 0};
   if (tm.rank == I.g.drop_rank) return;   // testing hook: see sem_set_barrier_test
+  stage_body<P, MIXED, !WIDE>(I, tm, B.stage, B.step, smem_raw, red, &s_flag, sh);
+}
+
+// The same stage body with cluster teams: the CTAs of an instance are one thread-block cluster
+// (team0 is a multiple of the cluster size) and the team barrier is the hardware cluster barrier.
+// No CTA waits on a CTA of another cluster, so the launch needs no co-residency and launches of
+// other groups may run at the same time.  Every CTA of a cluster runs the same sequence of
+// barriers: no control path leaves the kernel early in one CTA only.  (A loop over the four
+// stages inside one launch kept the body's loop-invariant values live across it and spilled
+// registers, so a launch runs one stage.)
+template <int P, bool MIXED, bool WIDE>
+__global__ void __launch_bounds__(kThreads, WIDE ? 2 : 1) k_stage_cl(StageArgs B) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[kRedSize];
+  __shared__ int s_flag;
+  __shared__ __align__(16) double sh[kStageWarps][kSurfWarpScratch];
+  __shared__ __align__(16) Instance I;
+  const int ii = B.cta_inst[blockIdx.x];
+  {
+    const unsigned int* src = reinterpret_cast<const unsigned int*>(B.inst + ii);
+    unsigned int* dst = reinterpret_cast<unsigned int*>(&I);
+    for (int q = threadIdx.x; q < (int)(sizeof(Instance) / 4); q += blockDim.x) dst[q] = src[q];
+  }
+  __syncthreads();
+  const Team tm{(int)blockIdx.x - I.team0, I.nteam, nullptr, I.g.status, I.pa.part, I.pa.part_stride,
+                I.g.bar_timeout_ns, 1};
   stage_body<P, MIXED, !WIDE>(I, tm, B.stage, B.step, smem_raw, red, &s_flag, sh);
 }
 
@@ -1622,6 +1668,49 @@ cudaError_t launch_stage_impl(int mixed, int wide, const StageArgs& a, int grid,
   return cudaLaunchCooperativeKernel(fn, grid, kThreads, args, smem, s);
 }
 
+
+template <int P>
+static const void* stage_cl_fn(int mixed, int wide) {
+  if (wide) return mixed ? (const void*)k_stage_cl<P, true, true> : (const void*)k_stage_cl<P, false, true>;
+  return mixed ? (const void*)k_stage_cl<P, true, false> : (const void*)k_stage_cl<P, false, false>;
+}
+
+template <int P>
+static cudaLaunchConfig_t cluster_config(int grid, int csize, size_t smem, cudaStream_t s, cudaLaunchAttribute* attr) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)csize;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cfg;
+}
+
+template <int P>
+cudaError_t cluster_fit_impl(int mixed, int wide, int csize, size_t smem, int* active_clusters) {
+  const void* fn = stage_cl_fn<P>(mixed, wide);
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) != cudaSuccess) return e;
+  cudaLaunchAttribute attr[1];
+  const cudaLaunchConfig_t cfg = cluster_config<P>(csize, csize, smem, nullptr, attr);
+  return cudaOccupancyMaxActiveClusters(active_clusters, fn, &cfg);
+}
+
+template <int P>
+cudaError_t launch_stage_cluster_impl(int mixed, int wide, const StageArgs& a, int grid, int csize, size_t smem,
+                                      cudaStream_t s) {
+  cudaLaunchAttribute attr[1];
+  const cudaLaunchConfig_t cfg = cluster_config<P>(grid, csize, smem, s, attr);
+  StageArgs aa = a;
+  void* args[] = {&aa};
+  return cudaLaunchKernelExC(&cfg, stage_cl_fn<P>(mixed, wide), args);
+}
 
 // Tiled apply (apply_tile.cuh): widest tile of at most 16 elements whose shared memory keeps
 // three CTAs per SM; persistent CTAs (at most the co-resident count) stride over the tiles.

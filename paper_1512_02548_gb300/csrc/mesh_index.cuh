@@ -26,6 +26,19 @@ static __device__ __forceinline__ int left_element(const DevGeom& g, int col) {
   return ex == 0 ? g.Nx - 1 : ex - 1;
 }
 
+// The same with the order known at compile time (no run-time division).
+template <int P>
+static __device__ __forceinline__ bool has_left_edge_p(const DevGeom& g, int col) {
+  if (col % P != 0) return false;
+  if (g.periodic) return true;
+  return col > 0 && col < g.Nx * P;
+}
+template <int P>
+static __device__ __forceinline__ int left_element_p(const DevGeom& g, int col) {
+  const int ex = col / P;
+  return ex == 0 ? g.Nx - 1 : ex - 1;
+}
+
 static __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));

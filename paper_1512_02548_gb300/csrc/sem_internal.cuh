@@ -22,6 +22,16 @@ constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;   // 2 s
 // Device status bits (OR-ed into the mesh's status word).
 enum : int { ST_NOT_CONVERGED = 1, ST_NONFINITE = 2, ST_TIMEOUT = 4, ST_BAD_DEPTH = 8 };
 
+// Division by a divisor fixed per mesh, for the work-item decompositions of the kernels (an
+// integer division by a run-time value costs tens of instructions): ⌊n/d⌋ = umulhi(n, ⌈2³²/d⌉),
+// exact for 0 ≤ n < 2³²/d (d ≥ 2).
+struct FastDiv {
+  unsigned m;
+  int d;
+  static FastDiv make(int dd) { return FastDiv{(unsigned)((0x100000000ull + (unsigned)dd - 1) / (unsigned)dd), dd}; }
+  __device__ __forceinline__ int div(int n) const { return (int)__umulhi((unsigned)n, m); }
+};
+
 // Read-only view of a mesh for the volume kernels.
 struct DevGeom {
   int P, Nx, Nz, ncol, nrow, periodic;
@@ -43,6 +53,7 @@ struct DevGeom {
   unsigned long long bar_timeout_ns;   // wall-clock limit of every team barrier wait
   int drop_rank;         // testing: this team rank leaves the next launch before its first
                          // barrier, so the others' bounded waits run out (−1: none)
+  FastDiv dv_nrow, dv_nr, dv_colsz, dv_elsz, dv_qn;   // Nrow, Nrow−1, (P+1)Nrow, Nz(P+1)², (P+1)(Nrow−1)
   unsigned long long* trace;   // phase trace of builds compiled with -DSEM_TRACE (else unused):
                                // [0] = marks so far, then (tag, %globaltimer) pairs
 };
@@ -197,7 +208,7 @@ struct Instance {
 struct StageArgs {
   const Instance* inst;  // device array
   const int* cta_inst;   // CTA → instance
-  unsigned int* bars;    // 2 per instance, zero at launch
+  unsigned int* bars;    // 2 per instance, zero at launch (cooperative launches)
   int stage;             // 1..4; 0 = Laplace solve only
   int step;              // steps since tstart
 };
@@ -217,6 +228,9 @@ template <int P> cudaError_t launch_apply_tile_impl(int fp32, const DevGeom& g, 
 template <int P> cudaError_t stage_occupancy_impl(int mixed, int wide, size_t smem, int* per_sm);
 template <int P> cudaError_t launch_stage_impl(int mixed, int wide, const StageArgs& a, int grid, size_t smem,
                                                cudaStream_t s);
+template <int P> cudaError_t cluster_fit_impl(int mixed, int wide, int csize, size_t smem, int* active_clusters);
+template <int P> cudaError_t launch_stage_cluster_impl(int mixed, int wide, const StageArgs& a, int grid, int csize,
+                                                       size_t smem, cudaStream_t s);
 
 // ---- launchers (kernels_laplace.cu) ----
 // Fused RK stage for instances of order P: capacity (CTAs per SM) at a given dynamic smem,
@@ -225,6 +239,12 @@ template <int P> cudaError_t launch_stage_impl(int mixed, int wide, const StageA
 cudaError_t stage_occupancy(int P, int mixed, int wide, size_t smem, int* per_sm);
 size_t stage_smem_bytes(int P, int nrow, int Nz, int chunk);
 cudaError_t launch_stage(int P, int mixed, int wide, const StageArgs& a, int grid, size_t smem, cudaStream_t s);
+// Cluster teams (every instance's CTAs form one thread-block cluster of csize CTAs, grid = members ×
+// csize): no cooperative launch, so launches of different groups may run at once.  cluster_fit
+// gives how many such clusters can be resident at once (0: the cluster size does not fit).
+cudaError_t cluster_fit(int P, int mixed, int wide, int csize, size_t smem, int* active_clusters);
+cudaError_t launch_stage_cluster(int P, int mixed, int wide, const StageArgs& a, int grid, int csize, size_t smem,
+                                 cudaStream_t s);
 // out[k] = status word of inst[k]; a nonzero word is cleared after it is read.
 cudaError_t launch_gather_status(const Instance* inst, int n, int* out, cudaStream_t s);
 cudaError_t upload_line_tables(const double* D64, const double* w64);  // packed, all orders

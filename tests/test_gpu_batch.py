@@ -4,8 +4,9 @@
   the multi-kernel path (SEM_FUSED_STAGE=0) and as the oracle.
 * A batch of uneven instances (different orders, element counts, layers, ends, relaxation,
   precision) stepped together equals each instance stepped alone, within the stated
-  tolerances (1e-10 FP64, 1e-8 mixed), and an FP64 member equals the oracle; with either build of
-  the stage kernel for the batch's groups (SEM_BATCH_WIDE) and the default choice by group size.
+  tolerances (1e-10 FP64, 1e-8 mixed), and an FP64 member equals the oracle; with cluster teams
+  (the default) and with cooperative launches (SEM_BATCH_CLUSTER=0), and with either build of the
+  stage kernel for the batch's groups (SEM_BATCH_WIDE) or the default choice by group size.
 """
 import math
 import os
@@ -91,19 +92,31 @@ def _uneven_instances():
     return cases
 
 
-@pytest.fixture(params=["default", "0", "1"], ids=["build-by-size", "one-cta-per-sm", "two-ctas-per-sm"])
+BUILDS = {
+    "clusters-build-by-size": {},
+    "clusters-one-cta-per-sm": {"SEM_BATCH_WIDE": "0"},
+    "clusters-two-ctas-per-sm": {"SEM_BATCH_WIDE": "1"},
+    "cooperative-build-by-size": {"SEM_BATCH_CLUSTER": "0"},
+    "cooperative-two-ctas-per-sm": {"SEM_BATCH_CLUSTER": "0", "SEM_BATCH_WIDE": "1"},
+}
+
+
+@pytest.fixture(params=list(BUILDS), ids=list(BUILDS))
 def batch_build(request):
-    """SEM_BATCH_WIDE for the batches created in the test (read by sem_batch_create)."""
-    old = os.environ.get("SEM_BATCH_WIDE")
-    if request.param == "default":
-        os.environ.pop("SEM_BATCH_WIDE", None)
-    else:
-        os.environ["SEM_BATCH_WIDE"] = request.param
+    """SEM_BATCH_CLUSTER (cluster teams on streams, or one cooperative launch per stage and
+    group) and SEM_BATCH_WIDE (build of the stage kernel) for the batches created in the test;
+    both are read by sem_batch_create."""
+    names = ("SEM_BATCH_WIDE", "SEM_BATCH_CLUSTER")
+    old = {k: os.environ.get(k) for k in names}
+    for k in names:
+        os.environ.pop(k, None)
+    os.environ.update(BUILDS[request.param])
     yield request.param
-    if old is None:
-        os.environ.pop("SEM_BATCH_WIDE", None)
-    else:
-        os.environ["SEM_BATCH_WIDE"] = old
+    for k, v in old.items():
+        if v is None:
+            os.environ.pop(k, None)
+        else:
+            os.environ[k] = v
 
 
 def test_batch_equals_instances_alone(batch_build):
