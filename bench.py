@@ -590,12 +590,13 @@ def c4_shoal_run(dev, spinup: int = 600, steps: int = 100):
     return out, start, one
 
 
-def c5_serving(rates=(100.0, 1000.0), count: int = 1000, sample: int = 4):
+def c5_serving(rates=(100.0, 1000.0), count: int = 1000, sample: int = 4, steps_per_tick: int = 1):
     """C5: Poisson streams of Laplace solves and 10-step RK4 runs (seed 0) served by the
-    continuous-batching loop in mixed precision (150 GB admission budget), against the same
-    requests run one after another on the plain FP64 single-instance path.  Wall-clock from
-    the first arrival; latency = completion − arrival.  The served results of a seeded sample
-    of small requests at the first rate are kept for the oracle check."""
+    continuous-batching loop in mixed precision (150 GB admission budget; `steps_per_tick` > 1 lets
+    a tick run several RK4 steps while nothing waits), against the same requests run one after
+    another on the plain FP64 single-instance path.  Wall-clock from the first arrival; latency
+    = completion − arrival.  The served results of a seeded sample of small requests at the
+    first rate are kept for the oracle check."""
     import numpy as np
     from paper_1512_02548_gb300.serve import GpuExecutor, Request, Server, sequential
     from sem_workloads import c5_requests, initial_state, splitmix64
@@ -627,7 +628,7 @@ def c5_serving(rates=(100.0, 1000.0), count: int = 1000, sample: int = 4):
         ent = {"laplace_share": sum(r.kind == "laplace" for r in base) / count,
                "nodes_total": int(sum(r.wl.n_nodes for r in base))}
         reqs = fresh()
-        s = Server(GpuExecutor("mixed"), 150 << 30, keep_results=keep).run(reqs)
+        s = Server(GpuExecutor("mixed"), 150 << 30, keep_results=keep, max_steps_per_tick=steps_per_tick).run(reqs)
         ent["served_mixed"] = {k: s[k] for k in keys + ("ticks", "peak_active")}
         for r in reqs:
             if r.rid in keep and r.error is None:
@@ -778,11 +779,13 @@ def run_gpu(args):
                                          flush=flush, timing=True, world=world)
     seq = c3_sequential(dev, wls, init, max(1, min(2, args.steps))) if lead else None
 
-    # roofline of the batched fused stage kernel: FP64 Krylov work per launch / event-timed launch
+    # roofline of the batched fused stage kernel.  The launches of the (order, precision, cluster
+    # size) groups run at the same time on their own streams, so the unit is the whole step: FP64
+    # Krylov work of all timed steps / their event-timed device time (the stage launches fill it)
     flops = sum(fp64_solver_flops(wl, c.solves, c.iterations, c.refinements, False) for wl, c in zip(wls, cnt64))
     launches = max(tm64.krylov_launches, 1)
     avg_launch_ms = tm64.krylov_ms / launches
-    achieved = flops / launches / (avg_launch_ms / 1e3) / 1e12
+    achieved = flops / (f64["total_ms"] / 1e3) / 1e12
     flops_mx = sum(fp64_solver_flops(wl, c.solves, c.iterations, c.refinements, True) for wl, c in zip(wls, cntmx))
 
     # end to end through the host-buffer batch call
@@ -799,8 +802,7 @@ def run_gpu(args):
           "mixed_over_batched_fp64": mix["laplace_dof_per_s"] / f64["laplace_dof_per_s"],
           "mixed_over_sequential_fp64": (mix["laplace_dof_per_s"] / seq["laplace_dof_per_s"]) if seq else None,
           "batched_fp64_over_sequential_fp64": (f64["laplace_dof_per_s"] / seq["laplace_dof_per_s"]) if seq else None,
-          "fp64_work_per_launch_mflop": {"fp64": flops / launches / 1e6,
-                                         "mixed": flops_mx / max(tmmx.krylov_launches, 1) / 1e6},
+          "fp64_work_per_step_gflop": {"fp64": flops / args.steps / 1e9, "mixed": flops_mx / args.steps / 1e9},
           "stage_launch_ms": {"fp64": avg_launch_ms, "mixed": tmmx.krylov_ms / max(tmmx.krylov_launches, 1)}}
 
     line = {
@@ -817,13 +819,15 @@ def run_gpu(args):
                   "over_sequential_fp64": c3["mixed_over_sequential_fp64"],
                   "tank_steps_per_s": mix["tank_steps_per_s"] * world},
         "c3_uneven_batch": c3,
-        "roofline": {"bound": "alu", "kernel": "k_stage, batched build (fused RK stage; FP64 Krylov work counted: "
-                                               "applies and vector updates, FP32 preconditioner left out)",
+        "roofline": {"bound": "alu", "kernel": "k_stage, batched fused RK stage with cluster teams, all "
+                                               "concurrent launches of a step (FP64 Krylov work counted: applies "
+                                               "and vector updates; the FP32 preconditioner left out)",
                      "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP64_PEAK_TFLOPS,
                      "peak_source": "nominal GB300 FP64 rate, 1.25 TFLOP/s (no measured FP64 peak)",
+                     "unit_of_time": "event-timed device time of the timed steps",
                      "launches": tm64.krylov_launches, "avg_launch_ms": avg_launch_ms,
-                     "flops_per_launch": flops / launches,
+                     "flops_per_step": flops / args.steps,
                      "traffic": profiled_traffic("k_stage_batch")},
         "e2e": e2e,
         "gpu_launches": f64["launches"],
@@ -840,7 +844,7 @@ def run_gpu(args):
         line["c4_shoal"] = c4
         extras["c4"] = (c4_start, c4_one)
     if lead and not args.no_c5:
-        c5, c5_checks = c5_serving(tuple(args.c5_rates), args.c5_requests)
+        c5, c5_checks = c5_serving(tuple(args.c5_rates), args.c5_requests, steps_per_tick=args.c5_steps_per_tick)
         line["c5_serving"] = c5
         extras["c5"] = c5_checks
     if lead and not args.no_apply_roofline:
@@ -948,6 +952,9 @@ def main():
     ap.add_argument("--no-c5", action="store_true")
     ap.add_argument("--c5-rates", type=float, nargs="+", default=[100.0, 1000.0])
     ap.add_argument("--c5-requests", type=int, default=1000)
+    ap.add_argument("--c5-steps-per-tick", type=int, default=1)
+    ap.add_argument("--c5-sweep", action="store_true",
+                    help="only the serving sweep: rates 10, 30, 100, 300, 1000, 2000 per s, 2000 requests each")
     ap.add_argument("--long-runs", action="store_true",
                     help="only the full-length C2 and C4 runs with the oracle's volume and energy diagnostics")
     ap.add_argument("--apply-only", default=None,
@@ -959,6 +966,12 @@ def main():
         import torch
         print(json.dumps(apply_roofline(torch.device("cuda", 0), args.apply_reps, args.apply_nx,
                                         tuple(args.apply_only.split(",")))))
+        return 0
+    if args.c5_sweep:
+        import paper_1512_02548_gb300 as sem
+        sem.load_library()
+        out, _ = c5_serving((10.0, 30.0, 100.0, 300.0, 1000.0, 2000.0), 2000, steps_per_tick=args.c5_steps_per_tick)
+        print(json.dumps({"c5_sweep": out}))
         return 0
     if args.long_runs:
         import torch

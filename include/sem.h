@@ -33,9 +33,12 @@
  * of CTAs of the persistent Krylov kernel and of a mesh's fused stage (default: all
  * co-resident); SEM_FUSED_STAGE=0 makes sem_rk4_step run the multi-kernel path instead of one
  * fused launch per RK stage.  Read by sem_laplace_apply: SEM_APPLY_KERNEL=column (see there).
- * Read by sem_batch_create: SEM_BATCH_WIDE=1 (or 0) makes every (order, precision) group of the
- * batch use the two-CTAs-per-SM build of the fused stage (or the one-CTA-per-SM build); by
- * default groups of more than 8 instances use the former.
+ * Read by sem_batch_create: SEM_BATCH_WIDE=1 (or 0) makes every group of the batch use the
+ * two-CTAs-per-SM build of the fused stage (or the one-CTA-per-SM build); by default groups of
+ * more than 8 instances use the former.  SEM_BATCH_CLUSTER=1 (or 0) makes the batch run its
+ * instances as thread-block-cluster teams on concurrent streams (or as cooperative launches, one
+ * per RK stage and (order, precision) group); by default the batch takes the plan it estimates
+ * faster.
  *
  * Device memory.  Each mesh and batch owns one device block, taken at creation from a
  * per-device cache of blocks freed by earlier meshes and batches (or from cudaMalloc) and given
@@ -248,11 +251,15 @@ int sem_rk4_step(sem_mesh* m, double* eta_d, double* phis_d, double* t, double d
 int sem_rk4_step_host(sem_mesh* m, double* eta_h, double* phis_h, double* t, double dt,
                       int nsteps, void* stream);
 
-/* Batched instances (many tanks stepped together).  One cooperative launch per RK stage
- * and per (order P, precision) group runs every instance of the group; each instance is
- * served by its own team of CTAs, sized to its element count, with its own grid barriers
- * and reductions, so results equal the instance run alone up to the summation order of the
- * team's reductions.  The meshes stay owned by the caller and must outlive the batch; they
+/* Batched instances (many tanks stepped together).  Each instance is served by its own team of
+ * CTAs, sized to its work, with its own barriers and reductions, so results equal the instance
+ * run alone up to the summation order of the team's reductions.  Two execution plans: every
+ * team one thread-block cluster (at most 16 CTAs), the launches of all (order, precision, team
+ * size) groups on streams of their own that run at the same time; or one cooperative launch per
+ * RK stage and (order P, precision) group, teams sized to fill the co-resident CTAs.  A batch
+ * takes the plan it estimates faster (the cooperative one when a few large instances would need
+ * more CTAs than a cluster holds); instances carrying the barrier testing hook force the
+ * cooperative plan.  The meshes stay owned by the caller and must outlive the batch; they
  * must share one device and use the separable preconditioner.  Stepping a batch uses each
  * mesh's workspace, so a mesh may not be stepped elsewhere concurrently. */
 typedef struct sem_batch sem_batch;
@@ -282,6 +289,22 @@ int sem_batch_laplace_solve(sem_batch* b, const double* const* eta_d, const doub
  * which failed); the first failing instance's error is returned. */
 int sem_batch_rk4_step_host(sem_batch* b, double* eta_h, double* phis_h, double* t_h, const double* dt_h,
                             int nsteps, void* stream);
+/* Planning parameters of later sem_batch_create calls (process-wide; written by the autotuner
+ * paper_1512_02548_gb300/autotune.py from measurements on the device, NULL restores the defaults).
+ * The environment variables SEM_BATCH_WIDE and SEM_BATCH_CLUSTER still take precedence. */
+typedef struct sem_batch_tuning {
+  double cluster_share;  /* cluster plan: a team is the smallest power of two of CTAs whose work per
+                            CTA is at most this fraction of the batch's work per CTA slot (0.5)   */
+  int max_cluster;       /* largest cluster team, a power of two in 1..16 (16)                   */
+  int narrow_max;        /* groups of at most this many instances use the one-CTA-per-SM build (8) */
+  int plan;              /* -1: the plan estimated faster; 0: cooperative; 1: clusters (-1)       */
+} sem_batch_tuning;
+int sem_set_batch_tuning(const sem_batch_tuning* t);
+int sem_get_batch_tuning(sem_batch_tuning* t);
+/* Tile width (elements per tile, 1..16) of the tiled apply for order P and Nz layers, as measured by
+ * the autotuner; 0 restores the default (the widest tile that keeps three CTAs per SM).  Process-wide. */
+int sem_set_apply_tile_width(int P, int Nz, int E);
+
 /* Per-instance result of the last sem_batch_rk4_step or sem_batch_laplace_solve:
  * codes_h[i] (host, one per instance) = SEM_OK or the instance's own error code, so a caller
  * can fail one instance and keep the others (each instance's state is advanced or solved

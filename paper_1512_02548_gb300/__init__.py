@@ -32,8 +32,8 @@ EXPORTED = ("sem_mesh_create", "sem_mesh_destroy", "sem_trim_cache", "sem_mesh_f
             "sem_rk4_step_host", "sem_get_counters", "sem_reset_counters", "sem_enable_timing",
             "sem_get_timing", "sem_batch_create", "sem_batch_destroy", "sem_batch_info",
             "sem_batch_rk4_step", "sem_batch_rk4_step_host", "sem_batch_laplace_solve", "sem_batch_status",
-            "sem_batch_enable_timing", "sem_batch_get_timing", "sem_set_barrier_test", "sem_launch_count",
-            "sem_last_error")
+            "sem_batch_enable_timing", "sem_batch_get_timing", "sem_set_batch_tuning", "sem_get_batch_tuning",
+            "sem_set_apply_tile_width", "sem_set_barrier_test", "sem_launch_count", "sem_last_error")
 
 
 class sem_params(ctypes.Structure):
@@ -57,6 +57,11 @@ class sem_info(ctypes.Structure):
 class sem_solve_stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("refinements", ctypes.c_int),
                 ("rel_residual", ctypes.c_double)]
+
+
+class sem_batch_tuning(ctypes.Structure):
+    _fields_ = [("cluster_share", ctypes.c_double), ("max_cluster", ctypes.c_int), ("narrow_max", ctypes.c_int),
+                ("plan", ctypes.c_int)]
 
 
 class sem_counters(ctypes.Structure):
@@ -115,6 +120,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sem_batch_enable_timing.argtypes = [vp, ip]
     lib.sem_batch_get_timing.argtypes = [vp, ctypes.POINTER(sem_timing)]
     lib.sem_set_barrier_test.argtypes = [vp, ip, ctypes.c_double]
+    lib.sem_set_batch_tuning.argtypes = [ctypes.POINTER(sem_batch_tuning)]
+    lib.sem_get_batch_tuning.argtypes = [ctypes.POINTER(sem_batch_tuning)]
+    lib.sem_set_apply_tile_width.argtypes = [ip, ip, ip]
     lib.sem_batch_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     lib.sem_launch_count.restype = ctypes.c_int64
     lib.sem_launch_count.argtypes = []
@@ -159,6 +167,34 @@ def _ptr(t, dtype=None):
 
 def launch_count() -> int:
     return int(load_library().sem_launch_count())
+
+
+def set_batch_tuning(cluster_share: float | None = None, max_cluster: int | None = None,
+                     narrow_max: int | None = None, plan: int | None = None, reset: bool = False):
+    """Process-wide batch planning parameters (sem_set_batch_tuning); unset fields keep their value,
+    reset=True restores the defaults first."""
+    lib = load_library()
+    if reset:
+        _check(lib.sem_set_batch_tuning(None))
+    t = sem_batch_tuning()
+    _check(lib.sem_get_batch_tuning(ctypes.byref(t)))
+    for name, v in (("cluster_share", cluster_share), ("max_cluster", max_cluster), ("narrow_max", narrow_max),
+                    ("plan", plan)):
+        if v is not None:
+            setattr(t, name, v)
+    _check(lib.sem_set_batch_tuning(ctypes.byref(t)))
+    return t
+
+
+def get_batch_tuning() -> dict:
+    t = sem_batch_tuning()
+    _check(load_library().sem_get_batch_tuning(ctypes.byref(t)))
+    return {"cluster_share": t.cluster_share, "max_cluster": t.max_cluster, "narrow_max": t.narrow_max, "plan": t.plan}
+
+
+def set_apply_tile_width(P: int, Nz: int, E: int):
+    """Tile width of the tiled apply for (P, Nz) (sem_set_apply_tile_width); 0 = default."""
+    _check(load_library().sem_set_apply_tile_width(int(P), int(Nz), int(E)))
 
 
 def mesh_params(P, Nx, Nz, periodic=True, Pf=0, filter_alpha=0.0, filter_s=0.0, filter_ic=-1, g=9.81,

@@ -354,7 +354,7 @@ Instance make_instance(sem_mesh* m, double* eta, double* phis, double tstart, do
 int do_rk4_fused(sem_mesh* m, double* eta, double* phis, double t0, double dt, int nsteps, cudaStream_t s) {
   m->inst_h = make_instance(m, eta, phis, t0, dt, 0, m->stage_team, true);
   CUDA_TRY(cudaMemcpyAsync(m->inst_d, &m->inst_h, sizeof(Instance), cudaMemcpyHostToDevice, s));
-  StageArgs a{m->inst_d, m->cta_inst_d, m->stage_bars, 1, 0};
+  StageArgs a{m->inst_d, m->cta_inst_d, m->stage_bars, 1, 0, 0};
   const int mixed = m->p.precision == SEM_PREC_MIXED;
   for (int step = 0; step < nsteps; ++step)
     for (int stage = 1; stage <= 4; ++stage) {
@@ -1052,13 +1052,45 @@ int sem_rk4_step_host(sem_mesh* m, double* eta_h, double* phis_h, double* t, dou
 // Cost of a team's barriers and cross-CTA round trips per stage, in element-local nodes of work
 // (team sizing of the cooperative plan).
 constexpr double kTeamSyncNodes = 256.0;
-// Groups of at most this many instances use the one-CTA-per-SM stage build.
-constexpr int kBatchNarrowMax = 8;
+// Batch planning parameters (sem_set_batch_tuning; the defaults are the untuned rules).
+static std::mutex g_tune_mu;
+static sem_batch_tuning g_tune{0.5, 16, 8, -1};
+
+static sem_batch_tuning batch_tuning() {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  return g_tune;
+}
 // Dynamic shared memory per CTA up to which batch members widen their passes (two CTAs per SM,
 // or one).
 constexpr size_t kBatchSmemWide = 88 * 1024, kBatchSmemNarrow = 176 * 1024;
 // Largest thread-block cluster (the non-portable limit of this architecture).
 constexpr int kMaxCluster = 16;
+
+int sem_set_batch_tuning(const sem_batch_tuning* t) {
+  sem_batch_tuning v{0.5, 16, 8, -1};
+  if (t) {
+    if (!(t->cluster_share > 0.0) || t->cluster_share > 64.0 || t->max_cluster < 1 || t->max_cluster > kMaxCluster ||
+        (t->max_cluster & (t->max_cluster - 1)) != 0 || t->narrow_max < 0 || t->plan < -1 || t->plan > 1)
+      return fail(SEM_ERR_INVALID_ARG, "batch tuning out of range");
+    v = *t;
+  }
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune = v;
+  return SEM_OK;
+}
+
+int sem_get_batch_tuning(sem_batch_tuning* t) {
+  if (!t) return fail(SEM_ERR_INVALID_ARG, "NULL argument");
+  *t = batch_tuning();
+  return SEM_OK;
+}
+
+int sem_set_apply_tile_width(int P, int Nz, int E) {
+  if (P < 2 || P > kMaxP || Nz < 1 || Nz > kMaxNz || E < 0 || E > 16)
+    return fail(SEM_ERR_INVALID_ARG, "tile width out of range");
+  set_apply_tile_width(P, Nz, E);
+  return SEM_OK;
+}
 
 }  // extern "C"
 
@@ -1066,7 +1098,7 @@ namespace {
 
 int batch_wide(size_t group_size) {
   const char* wenv = std::getenv("SEM_BATCH_WIDE");
-  return wenv ? (std::atoi(wenv) != 0) : (group_size > (size_t)kBatchNarrowMax ? 1 : 0);
+  return wenv ? (std::atoi(wenv) != 0) : (group_size > (size_t)batch_tuning().narrow_max ? 1 : 0);
 }
 
 int batch_limit(const sem_mesh* m) {   // ≤ grid: the halo and reduction buffers are sized by it
@@ -1166,20 +1198,49 @@ int plan_cooperative(sem_batch* b, sem_mesh* const* meshes, int count, int sms) 
 // half the total work per CTA slot (work: element-local nodes × the apply's flops per node).
 // Members are grouped by (order, precision, c), the largest first within a launch.  Returns
 // false (and builds nothing) when some group's cluster does not fit on the device.
+double member_work(const sem_mesh* m) {
+  const int Q = m->p.P + 1;
+  return (double)m->p.Nx * m->p.Nz * Q * Q * (8.0 * Q + 7.0);
+}
+
+// Estimated step time of each plan, in units of work per CTA: the cluster plan's launches share the
+// GPU, so it takes about the larger of the total work per CTA slot and its longest team; the
+// cooperative plan's launches run one after another, each as long as its slowest team.
+double estimate_clusters(const sem_batch* b, double slots) {
+  double total = 0.0, longest = 0.0;
+  for (const auto& L : b->cl_launches)
+    for (size_t k = 0; k < L.members.size(); ++k) {
+      const double w = member_work(b->meshes[L.members[k]]);
+      total += w;
+      longest = std::max(longest, w / L.nteam[k]);
+    }
+  return std::max(total / slots, longest);
+}
+
+double estimate_cooperative(const sem_batch* b) {
+  double t = 0.0;
+  for (const auto& L : b->launches) {
+    double worst = 0.0;
+    for (size_t k = 0; k < L.members.size(); ++k)
+      worst = std::max(worst, member_work(b->meshes[L.members[k]]) / L.nteam[k]);
+    t += worst;
+  }
+  return t;
+}
+
 bool plan_clusters(sem_batch* b, sem_mesh* const* meshes, int count, int sms) {
   std::vector<double> w(count);
   double total = 0.0;
   for (int i = 0; i < count; ++i) {
-    const sem_mesh* m = meshes[i];
-    const int Q = m->p.P + 1;
-    w[i] = (double)m->p.Nx * m->p.Nz * Q * Q * (8.0 * Q + 7.0);
+    w[i] = member_work(meshes[i]);
     total += w[i];
   }
+  const sem_batch_tuning tune = batch_tuning();
   const double slots = 2.0 * sms;
-  const double per_cta = 0.5 * total / slots;
+  const double per_cta = tune.cluster_share * total / slots;
   std::vector<std::pair<std::array<int, 3>, std::vector<int>>> groups;
   for (int i = 0; i < count; ++i) {
-    const int cmax = std::min(kMaxCluster, batch_limit(meshes[i]));
+    const int cmax = std::min(tune.max_cluster, batch_limit(meshes[i]));
     const double want = per_cta > 0.0 ? w[i] / per_cta : 1.0;
     int c = 1;
     while (c < want && 2 * c <= cmax) c *= 2;
@@ -1223,6 +1284,36 @@ bool plan_clusters(sem_batch* b, sem_mesh* const* meshes, int count, int sms) {
   return true;
 }
 
+// Streams and events of cluster launches are kept per device after a batch is destroyed and
+// handed to later batches (the serving loop creates batches every tick).
+std::mutex g_sp_mu;
+std::vector<std::pair<cudaStream_t, cudaEvent_t>> g_stream_pool[64];
+
+cudaError_t take_stream(int dev, cudaStream_t* st, cudaEvent_t* ev) {
+  {
+    std::lock_guard<std::mutex> lk(g_sp_mu);
+    if (dev >= 0 && dev < 64 && !g_stream_pool[dev].empty()) {
+      *st = g_stream_pool[dev].back().first;
+      *ev = g_stream_pool[dev].back().second;
+      g_stream_pool[dev].pop_back();
+      return cudaSuccess;
+    }
+  }
+  cudaError_t e = cudaStreamCreateWithFlags(st, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return e;
+  return cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+}
+
+void release_plan(std::vector<BatchLaunch>& plan, int dev) {
+  std::lock_guard<std::mutex> lk(g_sp_mu);
+  for (auto& L : plan) {
+    if (L.stream && L.done && dev >= 0 && dev < 64) g_stream_pool[dev].emplace_back(L.stream, L.done);
+    L.stream = nullptr;
+    L.done = nullptr;
+  }
+}
+
+
 // A plan's device arrays (descriptors, CTA map, barrier words, gathered status) from the pool.
 int carve_plan(sem_batch* b, std::vector<BatchLaunch>& plan, size_t& off) {
   for (auto& L : plan) {
@@ -1240,10 +1331,7 @@ int carve_plan(sem_batch* b, std::vector<BatchLaunch>& plan, size_t& off) {
     CUDA_TRY(cudaMemcpy(L.cta_d, map.data(), sizeof(int) * L.grid, cudaMemcpyHostToDevice));
     L.inst_h.resize(L.members.size());
     L.status_h.resize(L.members.size());
-    if (L.csize > 0) {
-      CUDA_TRY(cudaStreamCreateWithFlags(&L.stream, cudaStreamNonBlocking));
-      CUDA_TRY(cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming));
-    }
+    if (L.csize > 0) CUDA_TRY(take_stream(b->device, &L.stream, &L.done));
   }
   return SEM_OK;
 }
@@ -1256,15 +1344,6 @@ size_t plan_bytes(const std::vector<BatchLaunch>& plan) {
              ((sizeof(unsigned) * 2 * L.members.size() + 255) & ~size_t(255)) +
              ((sizeof(int) * L.members.size() + 255) & ~size_t(255));
   return total;
-}
-
-void release_plan(std::vector<BatchLaunch>& plan) {
-  for (auto& L : plan) {
-    if (L.stream) cudaStreamDestroy(L.stream);
-    if (L.done) cudaEventDestroy(L.done);
-    L.stream = nullptr;
-    L.done = nullptr;
-  }
 }
 
 }  // namespace
@@ -1292,8 +1371,14 @@ int sem_batch_create(sem_mesh* const* meshes, int count, sem_batch** out) {
   b->meshes.assign(meshes, meshes + count);
   int rc = plan_cooperative(b, meshes, count, sms);
   if (rc) { delete b; return rc; }
-  const char* cenv = std::getenv("SEM_BATCH_CLUSTER");   // 0: cooperative launches only
-  if (!(cenv && std::atoi(cenv) == 0)) plan_clusters(b, meshes, count, sms);
+  // The cluster plan is kept where it is estimated faster than the cooperative one (it is not
+  // when a few large members would need more CTAs than a cluster holds); SEM_BATCH_CLUSTER=0 or 1
+  // forces either plan.
+  const char* cenv = std::getenv("SEM_BATCH_CLUSTER");
+  const int force = cenv ? (std::atoi(cenv) != 0 ? 1 : 0) : batch_tuning().plan;
+  if (force != 0 && plan_clusters(b, meshes, count, sms) && force < 0 &&
+      estimate_clusters(b, 2.0 * sms) > estimate_cooperative(b))
+    b->cl_launches.clear();
   for (int i = 0; i < count; ++i) {
     b->off.push_back(b->ncol_total);
     b->ncol_total += (size_t)meshes[i]->ncol;
@@ -1309,7 +1394,7 @@ int sem_batch_create(sem_mesh* const* meshes, int count, sem_batch** out) {
   if (!rc && !b->cl_launches.empty() && cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess)
     rc = fail(SEM_ERR_CUDA, "event creation failed");
   if (rc) {
-    release_plan(b->cl_launches);
+    release_plan(b->cl_launches, dev);
     dev_free(dev, b->pool);
     delete b;
     return rc;
@@ -1322,7 +1407,7 @@ void sem_batch_destroy(sem_batch* b) {
   if (!b) return;
   DeviceGuard dg(b->device);
   cudaDeviceSynchronize();   // no work of this batch may still run when its memory is reused
-  release_plan(b->cl_launches);
+  release_plan(b->cl_launches, b->device);
   if (b->fork) cudaEventDestroy(b->fork);
   for (auto& pr : b->events) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
   for (cudaEvent_t e : b->spare) cudaEventDestroy(e);
@@ -1406,7 +1491,7 @@ cudaError_t run_clusters(sem_batch* b, int stage, int nsteps, cudaStream_t s) {
   for (int step = 0; step < (stage == 0 ? 1 : nsteps); ++step)
     for (int st = (stage == 0 ? 0 : 1); st <= (stage == 0 ? 0 : 4); ++st)
       for (auto& L : b->cl_launches) {
-        const StageArgs a{L.inst_d, L.cta_d, nullptr, st, step};
+        const StageArgs a{L.inst_d, L.cta_d, nullptr, st, step, 1};
         if ((e = batch_launch(b, L, a, L.stream)) != cudaSuccess) return e;
       }
   for (auto& L : b->cl_launches) {
@@ -1445,7 +1530,7 @@ int sem_batch_rk4_step(sem_batch* b, double* const* eta_d, double* const* phis_d
       for (int stage = 1; stage <= 4; ++stage)
         for (auto& L : plan) {
           CUDA_TRY(cudaMemsetAsync(L.bars_d, 0, 2 * sizeof(unsigned int) * L.members.size(), s));
-          const StageArgs a{L.inst_d, L.cta_d, L.bars_d, stage, step};
+          const StageArgs a{L.inst_d, L.cta_d, L.bars_d, stage, step, 0};
           CUDA_TRY(batch_launch(b, L, a, s));
         }
   }
@@ -1482,7 +1567,7 @@ int sem_batch_laplace_solve(sem_batch* b, const double* const* eta_d, const doub
   } else {
     for (auto& L : plan) {
       CUDA_TRY(cudaMemsetAsync(L.bars_d, 0, 2 * sizeof(unsigned int) * L.members.size(), s));
-      const StageArgs a{L.inst_d, L.cta_d, L.bars_d, 0, 0};
+      const StageArgs a{L.inst_d, L.cta_d, L.bars_d, 0, 0, 0};
       CUDA_TRY(batch_launch(b, L, a, s));
     }
   }

@@ -2,6 +2,11 @@
 // the apply's edge pass, and the allocation-free apply (arXiv 1512.02548, §3.1.2).  The
 // order-templated kernels live in laplace_device.cuh and are compiled once per order.
 #include <dlfcn.h>
+
+#include <array>
+#include <atomic>
+#include <functional>
+#include <map>
 #include <mutex>
 
 #include "mesh_index.cuh"
@@ -151,6 +156,13 @@ cudaError_t launch_apply_noalloc(const DevGeom& g, const double* x, double* y, c
   return cudaGetLastError();
 }
 
+static std::atomic<int> g_tile_width[kMaxP + 1][kMaxNz + 1];
+
+void set_apply_tile_width(int P, int Nz, int E) { g_tile_width[P][Nz].store(E, std::memory_order_relaxed); }
+int apply_tile_width(int P, int Nz) {
+  return (P >= 0 && P <= kMaxP && Nz >= 0 && Nz <= kMaxNz) ? g_tile_width[P][Nz].load(std::memory_order_relaxed) : 0;
+}
+
 cudaError_t launch_apply_tile(int fp32, const DevGeom& g, const void* x, void* y, cudaStream_t s) {
   cudaError_t e = cudaSuccess;
   SEM_DISPATCH_P(g.P, (e = launch_apply_tile_impl<PP>(fp32, g, x, y, s)));
@@ -182,10 +194,33 @@ size_t stage_smem_bytes(int P, int nrow, int Nz, int chunk) {
   return apply_smem_bytes(P, nrow, Nz, chunk, sizeof(double));
 }
 
+// Occupancy queries are answered once per (device, kernel variant, shared memory) and kept: the
+// serving loop creates batches every tick.
+static std::mutex g_occ_mu;
+static std::map<std::array<long long, 6>, int> g_occ;
+
+static cudaError_t cached_query(std::array<long long, 6> key, int* out, const std::function<cudaError_t(int*)>& q) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  key[0] = dev;
+  {
+    std::lock_guard<std::mutex> lk(g_occ_mu);
+    auto it = g_occ.find(key);
+    if (it != g_occ.end()) { *out = it->second; return cudaSuccess; }
+  }
+  if ((e = q(out)) != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(g_occ_mu);
+  g_occ[key] = *out;
+  return cudaSuccess;
+}
+
 cudaError_t stage_occupancy(int P, int mixed, int wide, size_t smem, int* per_sm) {
-  cudaError_t e = cudaSuccess;
-  SEM_DISPATCH_P(P, (e = stage_occupancy_impl<PP>(mixed, wide, smem, per_sm)));
-  return e;
+  return cached_query({0, P, mixed, wide, 0, (long long)smem}, per_sm, [&](int* o) {
+    cudaError_t e = cudaSuccess;
+    SEM_DISPATCH_P(P, (e = stage_occupancy_impl<PP>(mixed, wide, smem, o)));
+    return e;
+  });
 }
 
 cudaError_t launch_stage(int P, int mixed, int wide, const StageArgs& a, int grid, size_t smem, cudaStream_t s) {
@@ -196,9 +231,11 @@ cudaError_t launch_stage(int P, int mixed, int wide, const StageArgs& a, int gri
 }
 
 cudaError_t cluster_fit(int P, int mixed, int wide, int csize, size_t smem, int* active_clusters) {
-  cudaError_t e = cudaSuccess;
-  SEM_DISPATCH_P(P, (e = cluster_fit_impl<PP>(mixed, wide, csize, smem, active_clusters)));
-  return e;
+  return cached_query({0, P, mixed, wide, csize, (long long)smem}, active_clusters, [&](int* o) {
+    cudaError_t e = cudaSuccess;
+    SEM_DISPATCH_P(P, (e = cluster_fit_impl<PP>(mixed, wide, csize, smem, o)));
+    return e;
+  });
 }
 
 cudaError_t launch_stage_cluster(int P, int mixed, int wide, const StageArgs& a, int grid, int csize, size_t smem,

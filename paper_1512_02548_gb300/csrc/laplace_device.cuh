@@ -571,37 +571,63 @@ __device__ void cg_update(const DevGeom& g, Smem<P, T>& s, const Range& R, const
   TP* X = reinterpret_cast<TP*>(s.X);     // [E][Q][nr] residual of the chunk's element columns
   TP* RH = reinterpret_cast<TP*>(s.F1);   // [E][Q][nr] σ-transformed residual
   const int E = g.chunk, qn = Q * nr;
+  // U items per thread and pass: all their loads are issued before any of their stores, so that
+  // the L2 round trips of consecutive items overlap (a store to the vectors could alias the next
+  // item's loads, which the compiler would otherwise leave behind it)
+  constexpr int U = 2;
   for (int ex0 = R.e0; ex0 < R.e1; ex0 += E) {
-    const int ne = min(E, R.e1 - ex0);
-    for (int t = threadIdx.x; t < ne * qn; t += blockDim.x) {
-      const int e = g.dv_qn.div(t), rem = t - e * qn;
-      const int a = g.dv_nr.div(rem), j = rem - a * nr, ex = ex0 + e;
-      const int col = col_of(g, ex, a);
-      const size_t i = (size_t)col * nrow + j;
-      const bool own = owns_local_col(g, ex, a);
-      T rv;
-      if (update) {
-        T wv = ldcg(V.w + i);
-        if (has_left_edge_p<P>(g, col)) wv += ldcg(V.edge + (size_t)left_element_p<P>(g, col) * nrow + j);
-        const T sv = first ? wv : fmx(beta, ldcg(s_old + i), wv);
-        rv = fmx(-alpha, sv, ldcg(r_old + i));
-        if (own) {
-          s_new[i] = sv;
-          r_new[i] = rv;
-          const T uo = V.u[i];
-          const T pn = first ? uo : fmx(beta, V.p[i], uo);
-          V.p[i] = pn;
-          V.x[i] = fmx(alpha, pn, V.x[i]);
+    const int ne = min(E, R.e1 - ex0), nt = ne * qn;
+    for (int t0 = threadIdx.x; t0 < nt; t0 += U * blockDim.x) {
+      T wv[U], so[U], ro[U], uo[U], po[U], xo[U];
+      int ia[U];                                   // the item's (e, a, j), packed
+      bool own[U];
+#pragma unroll
+      for (int q = 0; q < U; ++q) {
+        const int t = t0 + q * blockDim.x;
+        if (t >= nt) continue;
+        const int e = g.dv_qn.div(t), rem = t - e * qn;
+        const int a = g.dv_nr.div(rem), j = rem - a * nr, ex = ex0 + e;
+        const int col = col_of(g, ex, a);
+        const size_t i = (size_t)col * nrow + j;
+        ia[q] = rem;
+        own[q] = owns_local_col(g, ex, a);
+        ro[q] = ldcg(r_old + i);
+        if (update) {
+          wv[q] = ldcg(V.w + i);
+          if (has_left_edge_p<P>(g, col)) wv[q] += ldcg(V.edge + (size_t)left_element_p<P>(g, col) * nrow + j);
+          so[q] = first ? T(0) : ldcg(s_old + i);
+          if (own[q]) {
+            uo[q] = V.u[i];
+            po[q] = first ? T(0) : V.p[i];
+            xo[q] = V.x[i];
+          }
         }
-      } else {
-        rv = ldcg(r_old + i);
       }
-      if (precond == PREC_JACOBI) {
-        const T uv = rv * V.invdiag[i];
-        if (own) V.u[i] = uv;
-        else if (is_halo_col(g, R, ex, a)) V.uh[(size_t)tm.rank * nrow + j] = uv;
-      } else {
-        X[t] = (TP)rv;
+#pragma unroll
+      for (int q = 0; q < U; ++q) {
+        const int t = t0 + q * blockDim.x;
+        if (t >= nt) continue;
+        const int e = g.dv_qn.div(t), a = g.dv_nr.div(ia[q]), j = ia[q] - a * nr, ex = ex0 + e;
+        const size_t i = (size_t)col_of(g, ex, a) * nrow + j;
+        T rv = ro[q];
+        if (update) {
+          const T sv = first ? wv[q] : fmx(beta, so[q], wv[q]);
+          rv = fmx(-alpha, sv, ro[q]);
+          if (own[q]) {
+            s_new[i] = sv;
+            r_new[i] = rv;
+            const T pn = first ? uo[q] : fmx(beta, po[q], uo[q]);
+            V.p[i] = pn;
+            V.x[i] = fmx(alpha, pn, xo[q]);
+          }
+        }
+        if (precond == PREC_JACOBI) {
+          const T uv = rv * V.invdiag[i];
+          if (own[q]) V.u[i] = uv;
+          else if (is_halo_col(g, R, ex, a)) V.uh[(size_t)tm.rank * nrow + j] = uv;
+        } else {
+          X[t] = (TP)rv;
+        }
       }
     }
     if (precond == PREC_JACOBI) continue;
@@ -673,26 +699,42 @@ __device__ void phase_backsub(const DevGeom& g, Smem<P, T>& s, const Range& R, c
   const int E = g.chunk, qn = Q * nr;
   for (int ex0 = R.e0; ex0 < R.e1; ex0 += E) {
     const int ne = min(E, R.e1 - ex0);
-    for (int t = threadIdx.x; t < ne * qn; t += blockDim.x) {
-      const int e = g.dv_qn.div(t), rem = t - e * qn;
-      const int a = g.dv_nr.div(rem), k = rem - a * nr, ex = ex0 + e;
-      const int jl = ex, jr = (ex + 1 == N) ? 0 : ex + 1;
-      const TP zl = ldcg(pv.zb + (size_t)k * N + jl);
-      const TP zr = ldcg(pv.zb + (size_t)k * N + jr);
-      TP v;
-      if (a == 0) v = zl;
-      else if (a == P) v = zr;
-      else {
-        const int i = a - 1;
-        const TP* Ai = pv.Aii + (((size_t)k * g.Nx + ex) * Pm + i) * Pm;
-        const TP* Zk = pv.Z + ((size_t)k * g.Nx + ex) * 2 * Pm;
-        v = 0;
+    // two items per thread and pass, their interface values loaded together (L2 round trips)
+    const int nt = ne * qn;
+    for (int t0 = threadIdx.x; t0 < nt; t0 += 2 * blockDim.x) {
+      TP zl[2], zr[2];
+      int kk[2], aa[2], ee[2];
 #pragma unroll
-        for (int m = 0; m < Pm; ++m) v = fmx(Ai[m], pv.rhat[(size_t)(ex * P + 1 + m) * nr + k], v);
-        v = fmx(-Zk[i], zl, v);
-        v = fmx(-Zk[Pm + i], zr, v);
+      for (int q = 0; q < 2; ++q) {
+        const int t = t0 + q * blockDim.x;
+        if (t >= nt) continue;
+        const int e = g.dv_qn.div(t), rem = t - e * qn;
+        const int a = g.dv_nr.div(rem), k = rem - a * nr, ex = ex0 + e;
+        const int jl = ex, jr = (ex + 1 == N) ? 0 : ex + 1;
+        zl[q] = ldcg(pv.zb + (size_t)k * N + jl);
+        zr[q] = ldcg(pv.zb + (size_t)k * N + jr);
+        kk[q] = k; aa[q] = a; ee[q] = ex;
       }
-      ZH[t] = v;
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int t = t0 + q * blockDim.x;
+        if (t >= nt) continue;
+        const int a = aa[q], k = kk[q], ex = ee[q];
+        TP v;
+        if (a == 0) v = zl[q];
+        else if (a == P) v = zr[q];
+        else {
+          const int i = a - 1;
+          const TP* Ai = pv.Aii + (((size_t)k * g.Nx + ex) * Pm + i) * Pm;
+          const TP* Zk = pv.Z + ((size_t)k * g.Nx + ex) * 2 * Pm;
+          v = 0;
+#pragma unroll
+          for (int m = 0; m < Pm; ++m) v = fmx(Ai[m], pv.rhat[(size_t)(ex * P + 1 + m) * nr + k], v);
+          v = fmx(-Zk[i], zl[q], v);
+          v = fmx(-Zk[Pm + i], zr[q], v);
+        }
+        ZH[t] = v;
+      }
     }
     __syncthreads();
     for (int t = threadIdx.x; t < ne * qn; t += blockDim.x) {
@@ -1524,6 +1566,12 @@ __device__ void stage_body(Instance& I, const Team& tm, int stage, int step, uns
 // WIDE = false: one CTA per SM and the full register file, so the stage keeps its values in
 // registers (single meshes: one team, latency bound).  WIDE = true: two CTAs per SM at 128
 // registers, more co-resident teams for batches of many small instances.
+// Two launch forms.  Cooperative (B.cluster = 0): the grid is co-resident and a team's barrier is
+// the bounded global one.  Cluster teams (B.cluster = 1): every instance's CTAs are one thread-block
+// cluster (team0 a multiple of the cluster size) and the team barrier is the hardware cluster
+// barrier; no CTA waits on a CTA of another cluster, so the launch needs no co-residency and the
+// launches of other groups may run at the same time.  Every CTA of a cluster takes the same
+// sequence of barriers: no control path leaves the kernel early in one CTA only.
 template <int P, bool MIXED, bool WIDE>
 __global__ void __launch_bounds__(kThreads, WIDE ? 2 : 1) k_stage(StageArgs B) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1539,37 +1587,11 @@ __global__ void __launch_bounds__(kThreads, WIDE ? 2 : 1) k_stage(StageArgs B) {
   }
   __syncthreads();
   const Team tm{(int)blockIdx.x - I.team0, I.nteam, B.bars + 2 * ii, I.g.status, I.pa.part, I.pa.part_stride,
-                I.g.bar_timeout_ns, 0};
-  if (tm.rank == I.g.drop_rank) return;   // testing hook: see sem_set_barrier_test
+                I.g.bar_timeout_ns, B.cluster};
+  // testing hook (see sem_set_barrier_test); the cluster plan never serves a mesh that carries it
+  if (!B.cluster && tm.rank == I.g.drop_rank) return;
   stage_body<P, MIXED, !WIDE>(I, tm, B.stage, B.step, smem_raw, red, &s_flag, sh);
 }
-
-// The same stage body with cluster teams: the CTAs of an instance are one thread-block cluster
-// (team0 is a multiple of the cluster size) and the team barrier is the hardware cluster barrier.
-// No CTA waits on a CTA of another cluster, so the launch needs no co-residency and launches of
-// other groups may run at the same time.  Every CTA of a cluster runs the same sequence of
-// barriers: no control path leaves the kernel early in one CTA only.  (A loop over the four
-// stages inside one launch kept the body's loop-invariant values live across it and spilled
-// registers, so a launch runs one stage.)
-template <int P, bool MIXED, bool WIDE>
-__global__ void __launch_bounds__(kThreads, WIDE ? 2 : 1) k_stage_cl(StageArgs B) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double red[kRedSize];
-  __shared__ int s_flag;
-  __shared__ __align__(16) double sh[kStageWarps][kSurfWarpScratch];
-  __shared__ __align__(16) Instance I;
-  const int ii = B.cta_inst[blockIdx.x];
-  {
-    const unsigned int* src = reinterpret_cast<const unsigned int*>(B.inst + ii);
-    unsigned int* dst = reinterpret_cast<unsigned int*>(&I);
-    for (int q = threadIdx.x; q < (int)(sizeof(Instance) / 4); q += blockDim.x) dst[q] = src[q];
-  }
-  __syncthreads();
-  const Team tm{(int)blockIdx.x - I.team0, I.nteam, nullptr, I.g.status, I.pa.part, I.pa.part_stride,
-                I.g.bar_timeout_ns, 1};
-  stage_body<P, MIXED, !WIDE>(I, tm, B.stage, B.step, smem_raw, red, &s_flag, sh);
-}
-
 
 // ------------------------------------------------------------------------------------
 // Host entry points for one order P (explicitly instantiated per order in kernels_order.cu).
@@ -1670,12 +1692,6 @@ cudaError_t launch_stage_impl(int mixed, int wide, const StageArgs& a, int grid,
 
 
 template <int P>
-static const void* stage_cl_fn(int mixed, int wide) {
-  if (wide) return mixed ? (const void*)k_stage_cl<P, true, true> : (const void*)k_stage_cl<P, false, true>;
-  return mixed ? (const void*)k_stage_cl<P, true, false> : (const void*)k_stage_cl<P, false, false>;
-}
-
-template <int P>
 static cudaLaunchConfig_t cluster_config(int grid, int csize, size_t smem, cudaStream_t s, cudaLaunchAttribute* attr) {
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3((unsigned)grid);
@@ -1693,7 +1709,7 @@ static cudaLaunchConfig_t cluster_config(int grid, int csize, size_t smem, cudaS
 
 template <int P>
 cudaError_t cluster_fit_impl(int mixed, int wide, int csize, size_t smem, int* active_clusters) {
-  const void* fn = stage_cl_fn<P>(mixed, wide);
+  const void* fn = stage_fn<P>(mixed, wide);
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
   if (e != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) != cudaSuccess) return e;
@@ -1709,7 +1725,7 @@ cudaError_t launch_stage_cluster_impl(int mixed, int wide, const StageArgs& a, i
   const cudaLaunchConfig_t cfg = cluster_config<P>(grid, csize, smem, s, attr);
   StageArgs aa = a;
   void* args[] = {&aa};
-  return cudaLaunchKernelExC(&cfg, stage_cl_fn<P>(mixed, wide), args);
+  return cudaLaunchKernelExC(&cfg, stage_fn<P>(mixed, wide), args);
 }
 
 // Tiled apply (apply_tile.cuh): widest tile of at most 16 elements whose shared memory keeps
@@ -1721,6 +1737,8 @@ cudaError_t launch_apply_tile_impl(int fp32, const DevGeom& g, const void* x, vo
   const size_t elem = fp32 ? sizeof(float) : sizeof(double);
   int E = 16;
   while (E > 1 && apply_tile_smem<P>(E, g.nrow, g.Nz, elem) > kTileSmemTarget) E >>= 1;
+  const int Et = apply_tile_width(P, g.Nz);   // a measured width (autotuner), if one is set
+  if (Et > 0 && apply_tile_smem<P>(Et, g.nrow, g.Nz, elem) <= (size_t)kMaxDynSmem) E = Et;
   const size_t smem = apply_tile_smem<P>(E, g.nrow, g.Nz, elem);
   if (smem > (size_t)kMaxDynSmem) return cudaErrorInvalidValue;
   // FP32 kernels specialised on the common layer counts 1, 2 and 4 (constant row arithmetic)

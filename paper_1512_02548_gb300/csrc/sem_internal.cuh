@@ -211,6 +211,7 @@ struct StageArgs {
   unsigned int* bars;    // 2 per instance, zero at launch (cooperative launches)
   int stage;             // 1..4; 0 = Laplace solve only
   int step;              // steps since tstart
+  int cluster;           // 1: cluster-team launch (each instance's CTAs are one cluster)
 };
 
 // ---- per-order entry points (laplace_device.cuh, instantiated in kernels_order.cu) ----
@@ -256,6 +257,9 @@ cudaError_t launch_l2g(const DevGeom& g, int32_t* l2g, cudaStream_t s);
 // Tiled apply y = 𝓛x at every node in FP32 (fp32 = 1, x, y float) or FP64 (x, y double), from the
 // geometry of the last launch_geometry; x and y must not overlap.  No workspace.
 cudaError_t launch_apply_tile(int fp32, const DevGeom& g, const void* x, void* y, cudaStream_t s);
+// Tile width of the tiled apply for (P, Nz): 0 = the widest that keeps three CTAs per SM.
+void set_apply_tile_width(int P, int Nz, int E);
+int apply_tile_width(int P, int Nz);
 // Allocation-free apply (scratch in a static device array of kNoAllocEdgeMax doubles).
 constexpr size_t kNoAllocEdgeMax = size_t(1) << 20;
 cudaError_t launch_apply_noalloc(const DevGeom& g, const double* x, double* y, cudaStream_t s);

@@ -108,15 +108,15 @@ class GpuExecutor:
             b.close()
         return dict(zip(rids, codes))
 
-    def step(self, rids) -> dict[int, int]:
-        """One RK4 step of every listed request in one batched call; rid → error code."""
+    def step(self, rids, nsteps: int = 1) -> dict[int, int]:
+        """`nsteps` RK4 steps of every listed request in one batched call; rid → error code."""
         b = self._batch_for(rids)
         sl = [self.slots[r] for r in rids]
         codes = self._run(b, lambda: b.rk4_step([s["eta"] for s in sl], [s["phis"] for s in sl],
-                                                [s["dt"] for s in sl], 1, ts=[s["t"] for s in sl]))
+                                                [s["dt"] for s in sl], nsteps, ts=[s["t"] for s in sl]))
         for s in sl:
-            s["t"] += s["dt"]
-            s["left"] -= 1
+            s["t"] += nsteps * s["dt"]
+            s["left"] -= nsteps
         return dict(zip(rids, codes))
 
     def steps_left(self, rid) -> int:
@@ -140,14 +140,19 @@ class Server:
     """Budgeted admission in arrival order and one batched tick at a time."""
 
     def __init__(self, executor, hbm_budget: int, clock=time.perf_counter, sleep=time.sleep,
-                 keep_results=True):
+                 keep_results=True, max_steps_per_tick: int = 1):
         """keep_results: True (every request's result is copied back), False, or a set of
-        request ids whose results are kept."""
+        request ids whose results are kept.  max_steps_per_tick > 1: while no request waits for
+        admission, a tick may advance the RK4 requests by several steps in one batched call, up
+        to the fewest steps any of them has left and to the steps that fit before the next
+        arrival (at the measured time per step), so that a lightly loaded loop does not pay a
+        tick per step; requests that arrive meanwhile join the next tick as before."""
         self.ex = executor
         self.budget = int(hbm_budget)
         self.clock = clock
         self.sleep = sleep
         self.keep = keep_results
+        self.max_steps = max(1, int(max_steps_per_tick))
 
     def run(self, requests: list[Request], cancel: dict[int, float] | None = None) -> dict:
         """Serve ``requests``; ``cancel`` maps rid → time after which the request is dropped
@@ -163,6 +168,7 @@ class Server:
         fp: dict[int, int] = {}
         t0 = self.clock()
         ticks = peak_active = peak_bytes = 0
+        per_step = 0.0                  # measured time of one RK4 step of a tick (running mean)
 
         def finish(r: Request, error: str | None = None):
             nonlocal used
@@ -221,7 +227,16 @@ class Server:
                 fresh = []
             rk = [rid for rid, r in active.items() if r.kind == "rk4"]
             if rk:
-                codes = self.ex.step(rk)
+                k = 1
+                if self.max_steps > 1 and not waiting:
+                    k = min([self.max_steps] + [self.ex.steps_left(rid) for rid in rk])
+                    if pending:
+                        gap = pending[0].arrival - (self.clock() - t0)
+                        k = max(1, min(k, int(gap / per_step))) if per_step > 0 else 1
+                tk = self.clock()
+                codes = self.ex.step(rk, k) if k > 1 else self.ex.step(rk)
+                dt_step = (self.clock() - tk) / k
+                per_step = dt_step if per_step <= 0 else 0.5 * (per_step + dt_step)
                 for rid in rk:
                     if codes[rid] != 0:
                         finish(active[rid], f"error code {codes[rid]}")

@@ -4,9 +4,10 @@
   the multi-kernel path (SEM_FUSED_STAGE=0) and as the oracle.
 * A batch of uneven instances (different orders, element counts, layers, ends, relaxation,
   precision) stepped together equals each instance stepped alone, within the stated
-  tolerances (1e-10 FP64, 1e-8 mixed), and an FP64 member equals the oracle; with cluster teams
-  (the default) and with cooperative launches (SEM_BATCH_CLUSTER=0), and with either build of the
-  stage kernel for the batch's groups (SEM_BATCH_WIDE) or the default choice by group size.
+  tolerances (1e-10 FP64, 1e-8 mixed), and an FP64 member equals the oracle; with the plan the
+  batch estimates faster, with cluster teams (SEM_BATCH_CLUSTER=1) and with cooperative launches
+  (SEM_BATCH_CLUSTER=0), and with either build of the stage kernel for the batch's groups
+  (SEM_BATCH_WIDE) or the default choice by group size.
 """
 import math
 import os
@@ -93,9 +94,10 @@ def _uneven_instances():
 
 
 BUILDS = {
-    "clusters-build-by-size": {},
-    "clusters-one-cta-per-sm": {"SEM_BATCH_WIDE": "0"},
-    "clusters-two-ctas-per-sm": {"SEM_BATCH_WIDE": "1"},
+    "plan-by-estimate": {},
+    "clusters-build-by-size": {"SEM_BATCH_CLUSTER": "1"},
+    "clusters-one-cta-per-sm": {"SEM_BATCH_CLUSTER": "1", "SEM_BATCH_WIDE": "0"},
+    "clusters-two-ctas-per-sm": {"SEM_BATCH_CLUSTER": "1", "SEM_BATCH_WIDE": "1"},
     "cooperative-build-by-size": {"SEM_BATCH_CLUSTER": "0"},
     "cooperative-two-ctas-per-sm": {"SEM_BATCH_CLUSTER": "0", "SEM_BATCH_WIDE": "1"},
 }

@@ -46,14 +46,15 @@ class FakeExecutor:
         self.calls.append(("solve", tuple(rids)))
         return {r: (5 if self.slots[r]["bad"] else 0) for r in rids}
 
-    def step(self, rids):
-        self.clock.t += self.tick_s
-        self.calls.append(("step", tuple(rids)))
+    def step(self, rids, nsteps=1):
+        self.clock.t += self.tick_s * nsteps
+        self.calls.append(("step", tuple(rids), nsteps))
         out = {}
         for r in rids:
             s = self.slots[r]
-            s["left"] -= 1
-            s["steps"] += 1
+            assert s["left"] >= nsteps           # no request is stepped past its end
+            s["left"] -= nsteps
+            s["steps"] += nsteps
             out[r] = 5 if s["bad"] else 0
         return out
 
@@ -121,8 +122,8 @@ def test_every_request_completes_once_in_arrival_order():
         if r.kind == "rk4":
             assert r.result["steps"] == r.nsteps
     # each Laplace request is in exactly one solve call, each RK4 request in exactly nsteps steps
-    solved = [rid for kind, rids in ex.calls if kind == "solve" for rid in rids]
-    stepped = [rid for kind, rids in ex.calls if kind == "step" for rid in rids]
+    solved = [rid for c in ex.calls if c[0] == "solve" for rid in c[1]]
+    stepped = [rid for c in ex.calls if c[0] == "step" for rid in c[1]]
     assert sorted(solved) == sorted(r.rid for r in reqs if r.kind == "laplace")
     for r in reqs:
         if r.kind == "rk4":
@@ -132,7 +133,7 @@ def test_every_request_completes_once_in_arrival_order():
 def test_requests_arriving_while_others_run_join_the_next_tick():
     reqs = requests(rate=5000.0, count=40)
     ex, s = serve(reqs, budget=1 << 60, tick_s=2e-3)
-    steps = [rids for kind, rids in ex.calls if kind == "step"]
+    steps = [c[1] for c in ex.calls if c[0] == "step"]
     assert max(len(x) for x in steps) > 1           # batched across requests
     # some RK4 request was admitted while another RK4 request was part-way through its steps
     joined = False
@@ -212,3 +213,21 @@ def test_summary_latency_and_throughput():
     assert s["p99_ms"] == pytest.approx(1e3 * np.percentile(0.01 * np.arange(1, 11), 99))
     dofs = sum(r.wl.n_unknowns * (40 if r.kind == "rk4" else 1) for r in reqs)
     assert s["laplace_dof_per_s"] == pytest.approx(dofs / 0.1)
+
+
+def test_multi_step_ticks_when_nothing_waits():
+    """With max_steps_per_tick, a lightly loaded loop advances its RK4 requests by several steps
+    per call, never past a request's last step, and only while no request waits for admission;
+    every request still gets exactly its steps."""
+    reqs = requests(rate=50.0, count=40)
+    clk = Clock()
+    ex = FakeExecutor(clk, 1e-3)
+    s = Server(ex, 1 << 60, clock=clk, sleep=clk.sleep, max_steps_per_tick=8).run(reqs)
+    assert s["completed"] == len(reqs) and s["failed"] == 0
+    for r in reqs:
+        if r.kind == "rk4":
+            assert r.result["steps"] == r.nsteps
+    multi = [c for c in ex.calls if c[0] == "step" and c[2] > 1]
+    assert multi and all(c[2] <= 8 for c in multi)
+    one = serve(requests(rate=50.0, count=40), budget=1 << 60)[0]
+    assert sum(1 for c in ex.calls if c[0] == "step") < sum(1 for c in one.calls if c[0] == "step")
