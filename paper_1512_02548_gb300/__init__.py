@@ -360,8 +360,13 @@ class Mesh:
 class Batch:
     """Many meshes stepped or solved together (``sem_batch``): one fused launch per RK stage and order."""
 
-    def __init__(self, meshes):
+    def __init__(self, meshes, tuned: bool = True):
+        """tuned: hand the autotuner's measured planning parameters (tuning.json, if measured on
+        this GPU) to the library before the first batch of the process."""
         lib = load_library()
+        if tuned:
+            from .autotune import apply_tuning
+            apply_tuning()
         self.meshes = list(meshes)
         arr = (ctypes.c_void_p * len(self.meshes))(*[m._h.value for m in self.meshes])
         handle = ctypes.c_void_p()

@@ -681,7 +681,7 @@ static int mesh_create_impl(const sem_params* pin, const double* x_edges_h, cons
   const size_t o_s64b = cv.take<double>(n), o_s32b = cv.take<float>(n);
   const size_t o_uh64 = cv.take<double>((size_t)m->grid * nrow), o_uh32 = cv.take<float>((size_t)m->grid * nrow);
   const size_t nEl = (size_t)nr * Nx, nIf = (size_t)nr * N;
-  const size_t o_S32 = cv.take<float>((size_t)nr * nr),
+  const size_t o_S32 = cv.take<float>((size_t)nr * nr), o_ST32 = cv.take<float>((size_t)nr * nr),
                o_lam = cv.take<double>(nr), o_schur = cv.take<double>(nEl * 3),
                o_A32 = cv.take<float>(nEl * Pm * Pm + 1), o_Z32 = cv.take<float>(nEl * 2 * Pm + 1),
                o_te32 = cv.take<float>(nIf), o_tm32 = cv.take<float>(nIf),
@@ -745,8 +745,12 @@ static int mesh_create_impl(const sem_params* pin, const double* x_edges_h, cons
     m->xcol_h = xc;
   }
   if (code == SEM_OK) {
-    std::vector<float> S32(Sg.begin(), Sg.end());
+    std::vector<float> S32(Sg.begin(), Sg.end()), ST32(S32.size());
+    for (int j = 0; j < nr; ++j)
+      for (int k = 0; k < nr; ++k) ST32[(size_t)k * nr + j] = S32[(size_t)j * nr + k];
     cudaError_t e = cudaMemcpy(m->pool + o_S32, S32.data(), S32.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(m->pool + o_ST32, ST32.data(), ST32.size() * sizeof(float), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) code = fail(SEM_ERR_CUDA, std::string("upload: ") + cudaGetErrorString(e));
   }
   if (code != SEM_OK) { dev_free(dev, m->pool); delete m; return code; }
@@ -789,7 +793,7 @@ static int mesh_create_impl(const sem_params* pin, const double* x_edges_h, cons
   ps.nr = nr; ps.nif = N; ps.lam = D_(o_lam); ps.schur = D_(o_schur);
   ps.Aii32 = F_(o_A32); ps.Z32 = F_(o_Z32); ps.te32 = F_(o_te32); ps.tm32 = F_(o_tm32); ps.tcp32 = F_(o_tcp32);
   ps.tz32 = F_(o_tz32); ps.tvl32 = F_(o_tvl32); ps.tfac32 = F_(o_tfac32);
-  ps.v32 = PrecView<float>{nr, N, F_(o_S32), ps.Aii32, ps.Z32, ps.te32, ps.tm32, ps.tcp32, ps.tz32, ps.tvl32,
+  ps.v32 = PrecView<float>{nr, N, F_(o_S32), F_(o_ST32), ps.Aii32, ps.Z32, ps.te32, ps.tm32, ps.tcp32, ps.tz32, ps.tvl32,
                            ps.tfac32, F_(o_gL32), F_(o_gR32), F_(o_zb32), F_(o_rh32)};
   a.pv32 = ps.v32;
 

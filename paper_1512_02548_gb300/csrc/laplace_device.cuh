@@ -556,7 +556,9 @@ __device__ __forceinline__ TP dot4(const TP* a, int sa, const TP* b, int n) {
 //   s ← w + β s,  r ← r − α s,  p ← u + β p,  x ← x + α p      (first iteration: s ← w, p ← u).
 // With update == false only the preconditioner part runs on r[cur].  Jacobi completes u here;
 // the separable preconditioner transforms the residual to the σ-eigenbasis and condenses.
-template <int P, class T, class TP>
+// ILP (compile time, the one-CTA-per-SM build, which has the registers): two items per thread
+// and pass with their loads issued together.
+template <int P, class T, class TP, bool ILP = false>
 __device__ void cg_update(const DevGeom& g, Smem<P, T>& s, const Range& R, const Team& tm,
                           const PrecView<TP>& pv, int precond, const CgVecs<T>& V, int cur, bool update,
                           bool first, T alpha, T beta) {
@@ -574,7 +576,7 @@ __device__ void cg_update(const DevGeom& g, Smem<P, T>& s, const Range& R, const
   // U items per thread and pass: all their loads are issued before any of their stores, so that
   // the L2 round trips of consecutive items overlap (a store to the vectors could alias the next
   // item's loads, which the compiler would otherwise leave behind it)
-  constexpr int U = 2;
+  constexpr int U = ILP ? 2 : 1;
   for (int ex0 = R.e0; ex0 < R.e1; ex0 += E) {
     const int ne = min(E, R.e1 - ex0), nt = ne * qn;
     for (int t0 = threadIdx.x; t0 < nt; t0 += U * blockDim.x) {
@@ -632,6 +634,7 @@ __device__ void cg_update(const DevGeom& g, Smem<P, T>& s, const Range& R, const
     }
     if (precond == PREC_JACOBI) continue;
     __syncthreads();
+    SEM_MARK(g, tm, TR_UPD_VEC);
     for (int t = threadIdx.x; t < ne * qn; t += blockDim.x) {
       const int e = g.dv_qn.div(t), rem = t - e * qn;
       const int a = g.dv_nr.div(rem), k = rem - a * nr, ex = ex0 + e;
@@ -641,23 +644,25 @@ __device__ void cg_update(const DevGeom& g, Smem<P, T>& s, const Range& R, const
       if (owns_local_col(g, ex, a)) pv.rhat[(size_t)col_of(g, ex, a) * nr + k] = v;
     }
     __syncthreads();
+    SEM_MARK(g, tm, TR_UPD_SIGMA);
     for (int t = threadIdx.x; t < ne * nr; t += blockDim.x) {
       const int e = g.dv_nr.div(t), k = t - e * nr, ex = ex0 + e;
       const TP* RHe = RH + e * qn;
-      const TP* Zk = pv.Z + ((size_t)k * g.Nx + ex) * 2 * Pm;
+      const TP* Zl = pv.Z + (size_t)ex * 2 * Pm * nr + k;   // Zl[m·nr]: left row, Zl[(Pm + m)·nr]: right
       // the assembled residual at an interface node enters once: with the element that owns
       // that column (its left end), plus the walls' last column with the last element
       TP l = RHe[k], r = owns_local_col(g, ex, P) ? RHe[P * nr + k] : TP(0);
 #pragma unroll
       for (int m = 0; m < Pm; ++m) {
         const TP f = RHe[(1 + m) * nr + k];
-        l = fmx(-Zk[m], f, l);
-        r = fmx(-Zk[Pm + m], f, r);
+        l = fmx(-Zl[m * nr], f, l);
+        r = fmx(-Zl[(Pm + m) * nr], f, r);
       }
       pv.gL[(size_t)k * g.Nx + ex] = l;
       pv.gR[(size_t)k * g.Nx + ex] = r;
     }
     __syncthreads();
+    SEM_MARK(g, tm, TR_UPD_COND);
   }
 }
 
@@ -690,7 +695,7 @@ __device__ void phase_interface(const DevGeom& g, const PrecView<T>& pv, const T
 
 // Back-substitution of the element interiors, then u = S ẑ on owned columns and on the halo
 // column (whose modal values are interface unknowns, known to every CTA after the solve).
-template <int P, class T, class TP>
+template <int P, class T, class TP, bool ILP = false>
 __device__ void phase_backsub(const DevGeom& g, Smem<P, T>& s, const Range& R, const Team& tm,
                               const PrecView<TP>& pv, const CgVecs<T>& V) {
   constexpr int Q = P + 1, Pm = P - 1;
@@ -699,13 +704,14 @@ __device__ void phase_backsub(const DevGeom& g, Smem<P, T>& s, const Range& R, c
   const int E = g.chunk, qn = Q * nr;
   for (int ex0 = R.e0; ex0 < R.e1; ex0 += E) {
     const int ne = min(E, R.e1 - ex0);
-    // two items per thread and pass, their interface values loaded together (L2 round trips)
+    // (ILP: two items per thread and pass, their interface values loaded together)
+    constexpr int UB = ILP ? 2 : 1;
     const int nt = ne * qn;
-    for (int t0 = threadIdx.x; t0 < nt; t0 += 2 * blockDim.x) {
-      TP zl[2], zr[2];
-      int kk[2], aa[2], ee[2];
+    for (int t0 = threadIdx.x; t0 < nt; t0 += UB * blockDim.x) {
+      TP zl[UB], zr[UB];
+      int kk[UB], aa[UB], ee[UB];
 #pragma unroll
-      for (int q = 0; q < 2; ++q) {
+      for (int q = 0; q < UB; ++q) {
         const int t = t0 + q * blockDim.x;
         if (t >= nt) continue;
         const int e = g.dv_qn.div(t), rem = t - e * qn;
@@ -716,7 +722,7 @@ __device__ void phase_backsub(const DevGeom& g, Smem<P, T>& s, const Range& R, c
         kk[q] = k; aa[q] = a; ee[q] = ex;
       }
 #pragma unroll
-      for (int q = 0; q < 2; ++q) {
+      for (int q = 0; q < UB; ++q) {
         const int t = t0 + q * blockDim.x;
         if (t >= nt) continue;
         const int a = aa[q], k = kk[q], ex = ee[q];
@@ -725,18 +731,19 @@ __device__ void phase_backsub(const DevGeom& g, Smem<P, T>& s, const Range& R, c
         else if (a == P) v = zr[q];
         else {
           const int i = a - 1;
-          const TP* Ai = pv.Aii + (((size_t)k * g.Nx + ex) * Pm + i) * Pm;
-          const TP* Zk = pv.Z + ((size_t)k * g.Nx + ex) * 2 * Pm;
+          const TP* Ai = pv.Aii + ((size_t)ex * Pm + i) * Pm * nr + k;   // Ai[m·nr]
+          const TP* Zl = pv.Z + (size_t)ex * 2 * Pm * nr + k;
           v = 0;
 #pragma unroll
-          for (int m = 0; m < Pm; ++m) v = fmx(Ai[m], pv.rhat[(size_t)(ex * P + 1 + m) * nr + k], v);
-          v = fmx(-Zk[i], zl[q], v);
-          v = fmx(-Zk[Pm + i], zr[q], v);
+          for (int m = 0; m < Pm; ++m) v = fmx(Ai[m * nr], pv.rhat[(size_t)(ex * P + 1 + m) * nr + k], v);
+          v = fmx(-Zl[i * nr], zl[q], v);
+          v = fmx(-Zl[(Pm + i) * nr], zr[q], v);
         }
         ZH[t] = v;
       }
     }
     __syncthreads();
+    SEM_MARK(g, tm, TR_BS_INTERIOR);
     for (int t = threadIdx.x; t < ne * qn; t += blockDim.x) {
       const int e = g.dv_qn.div(t), rem = t - e * qn;
       const int a = g.dv_nr.div(rem), j = rem - a * nr, ex = ex0 + e;
@@ -744,12 +751,12 @@ __device__ void phase_backsub(const DevGeom& g, Smem<P, T>& s, const Range& R, c
       const bool halo = is_halo_col(g, R, ex, a);
       if (!own && !halo) continue;
       const TP* Za = ZH + e * qn + a * nr;
-      const TP* Sj = pv.S + j * nr;
-      const TP v = dot4<TP>(Sj, 1, Za, nr);
+      const TP v = dot4<TP>(pv.ST + j, nr, Za, nr);   // threads of consecutive j read consecutive words
       if (own) V.u[(size_t)col_of(g, ex, a) * nrow + j] = (T)v;
       else V.uh[(size_t)tm.rank * nrow + j] = (T)v;
     }
     __syncthreads();
+    SEM_MARK(g, tm, TR_BS_SIGMA);
   }
 }
 
@@ -765,7 +772,7 @@ __device__ bool finish_precondition(const DevGeom& g, Smem<P, T>& s, const Range
   SEM_MARK(g, tm, TR_IT_INTERFACE);
   if (!grid_barrier(tm, s_flag)) return false;
   SEM_MARK(g, tm, TR_IT_BAR3);
-  phase_backsub<P, T, TP>(g, s, R, tm, pv, V);
+  phase_backsub<P, T, TP, CACHE>(g, s, R, tm, pv, V);
   return true;
 }
 
@@ -784,7 +791,7 @@ __device__ int cg_solve(const DevGeom& g, Smem<P, T>& s, const Range& R, const T
   __shared__ int s_stop;
   int cur = 0;
   SEM_MARK(g, tm, TR_CG_START);
-  cg_update<P, T, TP>(g, s, R, tm, pv, PA.precond, V, cur, false, true, T(0), T(0));
+  cg_update<P, T, TP, CACHE>(g, s, R, tm, pv, PA.precond, V, cur, false, true, T(0), T(0));
   if (!finish_precondition<P, T, TP, CACHE>(g, s, R, tm, PA, pv, V, s_flag)) return -1;
   SEM_MARK(g, tm, TR_IT_BACKSUB);
   int k = 0;
@@ -855,7 +862,7 @@ __device__ int cg_solve(const DevGeom& g, Smem<P, T>& s, const Range& R, const T
     SEM_MARK(g, tm, TR_IT_SCALARS);
     if (s_stop) break;
     const T alpha = s_scal[0], beta = s_scal[1];
-    cg_update<P, T, TP>(g, s, R, tm, pv, PA.precond, V, cur, true, k == 0, alpha, beta);
+    cg_update<P, T, TP, CACHE>(g, s, R, tm, pv, PA.precond, V, cur, true, k == 0, alpha, beta);
     cur ^= 1;
     SEM_MARK(g, tm, TR_IT_UPDATE);
     if (!finish_precondition<P, T, TP, CACHE>(g, s, R, tm, PA, pv, V, s_flag)) return -1;
@@ -1144,11 +1151,12 @@ __device__ __forceinline__ void prec_elem_mode(const DevGeom& g, const PrecSetup
     }
   }
   const size_t base = (size_t)k * g.Nx + ex;
-  float* A32 = ps.Aii32 + base * Pm * Pm;
+  const int nr = ps.nr;
+  float* A32 = ps.Aii32 + (size_t)ex * Pm * Pm * nr + k;   // mode-fastest: A32[(i·Pm + j)·nr]
 #pragma unroll
   for (int i = 0; i < Pm; ++i)
 #pragma unroll
-    for (int j = 0; j < Pm; ++j) A32[i * Pm + j] = 0.5f * (Ai[i][j] + Ai[j][i]);
+    for (int j = 0; j < Pm; ++j) A32[(i * Pm + j) * nr] = 0.5f * (Ai[i][j] + Ai[j][i]);
   double Z0[Pm], Z1[Pm];
 #pragma unroll
   for (int i = 0; i < Pm; ++i) {
@@ -1168,11 +1176,11 @@ __device__ __forceinline__ void prec_elem_mode(const DevGeom& g, const PrecSetup
     S01 -= Z0[i] * Kx[(1 + i) * Q + P];
     S11 -= Z1[i] * Kx[(1 + i) * Q + P];
   }
-  float* Z32 = ps.Z32 + base * 2 * Pm;
+  float* Z32 = ps.Z32 + (size_t)ex * 2 * Pm * nr + k;      // mode-fastest: Z32[(s·Pm + i)·nr]
 #pragma unroll
   for (int i = 0; i < Pm; ++i) {
-    Z32[i] = (float)Z0[i];
-    Z32[Pm + i] = (float)Z1[i];
+    Z32[i * nr] = (float)Z0[i];
+    Z32[(Pm + i) * nr] = (float)Z1[i];
   }
   ps.schur[base * 3 + 0] = S00;
   ps.schur[base * 3 + 1] = S01;

@@ -66,7 +66,9 @@ enum : int {
   TR_IT_APPLY = 10, TR_IT_BAR1 = 11, TR_IT_SCALARS = 12, TR_IT_UPDATE = 13, TR_IT_BAR2 = 14,
   TR_IT_INTERFACE = 15, TR_IT_BAR3 = 16, TR_IT_BACKSUB = 17, TR_CG_START = 18, TR_CG_END = 19,
   TR_REFINE = 20, TR_SOLVED = 30, TR_WSX = 31, TR_MINT1 = 32, TR_MBACK1 = 33, TR_ZAK = 34, TR_MINT2 = 35,
-  TR_RK4 = 36, TR_FILTER = 37, TR_END = 38
+  TR_RK4 = 36, TR_FILTER = 37, TR_END = 38,
+  TR_UPD_VEC = 40, TR_UPD_SIGMA = 41, TR_UPD_COND = 42, TR_BS_INTERIOR = 43, TR_BS_SIGMA = 44,
+  TR_AP_LOAD = 45, TR_AP_F = 46, TR_AP_Y = 47
 };
 
 // Element columns processed together per CTA pass: enough that a pass has ~256–512 work
@@ -97,8 +99,11 @@ struct PrecView {
   int nr;                  // σ modes = interior rows (Nrow − 1)
   int nif;                 // interface unknowns per mode (Nx periodic, Nx+1 walls)
   const T* S;              // [nr*nr]   S[j*nr + k]: σ-eigenvectors, Sᵀ Mσ S = I
-  const T* Aii;            // [nr][Nx][(P−1)²] inverse interior block of the mode-k element matrix
-  const T* Z;              // [nr][Nx][2][P−1]  E_bi E_ii⁻¹ (left, right boundary rows)
+  const T* ST;             // [nr*nr]   ST[k*nr + j] = S[j*nr + k] (the backward transform reads it)
+  // the element blocks are stored mode-fastest, so that threads of consecutive modes read
+  // consecutive words
+  const T* Aii;            // [Nx][P−1][P−1][nr] inverse interior block of the mode-k element matrix
+  const T* Z;              // [Nx][2][P−1][nr]  E_bi E_ii⁻¹ (left, right boundary rows)
   const T* te;             // [nr][nif] interface tridiagonal off-diagonals
   const T* tm;             // [nr][nif] Thomas pivots 1/(d_j − e_{j−1} c'_{j−1})
   const T* tcp;            // [nr][nif] Thomas c'_j
