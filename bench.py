@@ -386,14 +386,16 @@ def rel_l2(a, b) -> float:
 
 
 def c3_run(dev, prec: str, wls, init, steps: int, warmup: int, keep=(), flush=None, timing=False, clocks=None,
-           world: int = 1):
+           world: int = 1, tol: float | None = None):
     """C3 batch in one precision: `warmup` untimed steps (the state after the first is kept for the
     tanks in `keep`), then `steps` steps, each timed alone with CUDA events on the stream, L2
     flushed before each (clocks sampled and library launches counted over the timed steps).
     Returns (figures, kept states, per-tank counters, stage-launch timing, final states)."""
     import torch
     import paper_1512_02548_gb300 as sem
-    meshes = [sem.Mesh.from_workload(wl, precision=prec, tol=1e-13 if prec == "fp64" else 1e-12) for wl in wls]
+    if tol is None:
+        tol = 1e-13 if prec == "fp64" else 1e-12
+    meshes = [sem.Mesh.from_workload(wl, precision=prec, tol=tol) for wl in wls]
     batch = sem.Batch(meshes)
     etas = [torch.tensor(e, device=dev) for e, _ in init]
     phis = [torch.tensor(p, device=dev) for _, p in init]
@@ -778,6 +780,12 @@ def run_gpu(args):
     mix, keptmx, cntmx, tmmx, _ = c3_run(dev, "mixed", wls, init, args.steps, args.warmup, keep=sample,
                                          flush=flush, timing=True, world=world)
     seq = c3_sequential(dev, wls, init, max(1, min(2, args.steps))) if lead else None
+    # both paths at one looser tolerance, 1e-10, still far inside the 1e-8 error target
+    loose = {}
+    for prec in ("fp64", "mixed"):
+        fig, kept, _, _, _ = c3_run(dev, prec, wls, init, max(1, min(5, args.steps)), args.warmup, keep=sample,
+                                    flush=flush, world=world, tol=1e-10)
+        loose[prec] = ({k: v for k, v in fig.items() if k not in ("total_ms", "clocks", "launches")}, kept)
 
     # roofline of the batched fused stage kernel.  The launches of the (order, precision, cluster
     # size) groups run at the same time on their own streams, so the unit is the whole step: FP64
@@ -802,6 +810,11 @@ def run_gpu(args):
           "mixed_over_batched_fp64": mix["laplace_dof_per_s"] / f64["laplace_dof_per_s"],
           "mixed_over_sequential_fp64": (mix["laplace_dof_per_s"] / seq["laplace_dof_per_s"]) if seq else None,
           "batched_fp64_over_sequential_fp64": (f64["laplace_dof_per_s"] / seq["laplace_dof_per_s"]) if seq else None,
+          "at_tol_1e-10": {"fp64": loose["fp64"][0], "mixed": loose["mixed"][0],
+                           "mixed_over_fp64": loose["mixed"][0]["laplace_dof_per_s"] /
+                           loose["fp64"][0]["laplace_dof_per_s"],
+                           "note": "both paths at relative residual tolerance 1e-10; errors against the "
+                                   "oracle in oracle_check"},
           "fp64_work_per_step_gflop": {"fp64": flops / args.steps / 1e9, "mixed": flops_mx / args.steps / 1e9},
           "stage_launch_ms": {"fp64": avg_launch_ms, "mixed": tmmx.krylov_ms / max(tmmx.krylov_launches, 1)}}
 
@@ -828,7 +841,10 @@ def run_gpu(args):
                      "unit_of_time": "event-timed device time of the timed steps",
                      "launches": tm64.krylov_launches, "avg_launch_ms": avg_launch_ms,
                      "flops_per_step": flops / args.steps,
-                     "traffic": profiled_traffic("k_stage_batch")},
+                     # the unit of `achieved` is a whole step (all concurrent launches); the committed
+                     # capture measured one group's launch alone, so it is reported beside, not as, traffic
+                     "traffic": None,
+                     "dram_bytes_per_group_launch_profiled": profiled_traffic("k_stage_batch")},
         "e2e": e2e,
         "gpu_launches": f64["launches"],
         "clocks": f64["clocks"],
@@ -851,6 +867,7 @@ def run_gpu(args):
         line["apply_long_tank"] = apply_roofline(dev)
 
     if check:
+        extras["c3_loose"] = {p: loose[p][1] for p in loose}
         oracle_checks(line, sample, init, kept64, keptmx, extras)
     if world > 1:
         dist.barrier()
@@ -884,6 +901,9 @@ def oracle_checks(line, sample, init, kept64, keptmx, extras):
         c3 = line["c3_uneven_batch"]
         c3["oracle_check"] = {"tanks": list(sample), "steps": 1, "fp64_max_rel_l2": err64, "mixed_max_rel_l2": errmx,
                               "tolerance": {"fp64": 1e-10, "mixed": 1e-8}}
+        for prec, kept in extras.get("c3_loose", {}).items():
+            c3["oracle_check"][f"{prec}_at_tol_1e-10_max_rel_l2"] = max(
+                max(rel_l2(kept[i][0], r[1][0]), rel_l2(kept[i][1], r[1][1])) for i, r in zip(sample, res))
         line["mixed"]["max_rel_l2_vs_oracle"] = errmx
         line["max_rel_l2_vs_oracle"] = err64
         pending = []

@@ -879,9 +879,14 @@ __device__ int cg_solve(const DevGeom& g, Smem<P, T>& s, const Range& R, const T
 template <int P>
 __device__ bool fp64_residual(const DevGeom& g, Smem<P, double>& s, const Range& R, const Team& tm,
                               const PcgArgs& A, bool want_b, double* red, int* s_flag, double& rr, double& bb,
-                              double* dx = nullptr, const double* gc = nullptr) {
-  // dx (optional): on entry dx[0] is this thread's partial ‖δ‖² of the last correction; on
-  // exit dx[0] = ‖δ‖² and dx[1] = ‖x‖² over the whole team (interior nodes).
+                              double* dx = nullptr, const double* gc = nullptr, float* d32 = nullptr,
+                              float* r32 = nullptr) {
+  // dx (optional): on exit dx[0] = ‖δ‖² of the correction d32 and dx[1] = ‖x‖² over the whole team
+  // (interior nodes).
+  // d32 (optional, mixed precision): the FP32 correction of the last inner solve, not yet added:
+  // the apply takes x + δ, then x ← x + δ on owned nodes and δ ← 0 (the next inner solve's start).
+  // r32 (optional): receives the FP32 copy of the residual (0 on the surface row), the next inner
+  // solve's right-hand side.
   const int nrow = g.nrow;
   const double* x = A.x;
   const double* phis = A.phis;
@@ -893,7 +898,9 @@ __device__ bool fp64_residual(const DevGeom& g, Smem<P, double>& s, const Range&
         g, s, ex0, ne,
         [&](int e, int a, int iz) -> double {
           const int col = col_of(g, e, a);
-          return iz == nrow - 1 ? phis[col] : ldcg(x + (size_t)col * nrow + iz);
+          if (iz == nrow - 1) return phis[col];
+          const size_t i = (size_t)col * nrow + iz;
+          return d32 ? ldcg(x + i) + (double)ldcg(d32 + i) : ldcg(x + i);
         },
         [&](int e, int a, int iz, double y) {
           if (owns_local_col(g, e, a)) A.q64[(size_t)col_of(g, e, a) * nrow + iz] = y;
@@ -919,19 +926,34 @@ __device__ bool fp64_residual(const DevGeom& g, Smem<P, double>& s, const Range&
     s.load_tables(g);
   }
   if (!grid_barrier(tm, s_flag)) return false;
-  double acc[4] = {0.0, 0.0, dx ? dx[0] : 0.0, 0.0};
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
   const int ncols = R.c1 - R.c0;
   for (int t = threadIdx.x; t < ncols * nrow; t += blockDim.x) {
     const int cq = g.dv_nrow.div(t), col = R.c0 + cq, iz = t - cq * nrow;
     const size_t i = (size_t)col * nrow + iz;
-    if (iz == nrow - 1) { A.x[i] = phis[col]; continue; }
-    if (dx) acc[3] += A.x[i] * A.x[i];
+    if (iz == nrow - 1) {
+      A.x[i] = phis[col];
+      if (d32) d32[i] = 0.f;
+      if (r32) r32[i] = 0.f;
+      continue;
+    }
+    if (d32) {
+      const double d = (double)d32[i];
+      const double xn = A.x[i] + d;
+      A.x[i] = xn;
+      d32[i] = 0.f;
+      acc[2] += d * d;
+      acc[3] += xn * xn;
+    } else if (dx) {
+      acc[3] += A.x[i] * A.x[i];
+    }
     const bool le = has_left_edge_p<P>(g, col);
     const size_t ie = le ? (size_t)left_element_p<P>(g, col) * nrow + iz : 0;
     double qv = A.q64[i];
     if (le) qv += ldcg(A.edge64 + ie);
     const double rv = -qv;
     A.r64[i] = rv;
+    if (r32) r32[i] = (float)rv;
     acc[0] += rv * rv;
     if (want_b) {
       double bv = A.q64b[i];
@@ -977,7 +999,18 @@ __device__ bool solve_body(const DevGeom& g, const PcgArgs& A, const Team& tm, u
     gc = c;
   }
   double rr = 0.0, bb = 0.0;
-  if (!fp64_residual<P>(g, s64, R, tm, A, true, red, &s_flag, rr, bb, nullptr, gc)) return false;
+  // mixed precision: the residual loop also starts the first inner solve (δ = 0, FP32 residual)
+  if (!fp64_residual<P>(g, s64, R, tm, A, true, red, &s_flag, rr, bb, nullptr, gc, nullptr,
+                        MIXED ? A.r32 : nullptr))
+    return false;
+  if (MIXED) {
+    const int ncols = R.c1 - R.c0;
+    for (int t = threadIdx.x; t < ncols * nrow; t += blockDim.x) {
+      const int cq = g.dv_nrow.div(t);
+      A.d32[(size_t)(R.c0 + cq) * nrow + (t - cq * nrow)] = 0.f;
+    }
+    __syncthreads();
+  }
   SEM_MARK(g, tm, TR_RESIDUAL);
   const double target = A.tol * A.tol * bb;
   int iters = 0, refinements = 0;
@@ -1021,15 +1054,9 @@ __device__ bool solve_body(const DevGeom& g, const PcgArgs& A, const Team& tm, u
       __syncthreads();
       if (!s_go) break;
       s32.load_tables(g);
-      // inner: A δ = r in FP32 from δ = 0, to a relative residual inner_rtol (or the outer target)
-      const int ncols = R.c1 - R.c0;
-      for (int t = threadIdx.x; t < ncols * nrow; t += blockDim.x) {
-        const int cq = g.dv_nrow.div(t), col = R.c0 + cq, iz = t - cq * nrow;
-        const size_t i = (size_t)col * nrow + iz;
-        A.d32[i] = 0.f;
-        A.r32[i] = iz == nrow - 1 ? 0.f : (float)A.r64[i];
-      }
-      if (!grid_barrier(tm, &s_flag)) return false;
+      // inner: A δ = r in FP32 from δ = 0 (δ and the FP32 residual were set by the last FP64
+      // residual, whose closing barrier orders them before every CTA's reads), to a relative
+      // residual inner_rtol (or the outer target)
       const double tgt_in = fmax(A.inner_rtol * A.inner_rtol * rr, 0.25 * target);
       double rr_in = rr;
       const int it = cg_solve<P, float, float, float, CACHE>(g, s32, R, tm, A, A.pv32, V, tgt_in, A.max_iter - iters, red,
@@ -1037,21 +1064,12 @@ __device__ bool solve_body(const DevGeom& g, const PcgArgs& A, const Team& tm, u
       if (it < 0) return false;
       iters += it;
       ++refinements;
-      // x += δ (FP64), then the true FP64 residual
-      dx[0] = 0.0;
-      for (int t = threadIdx.x; t < ncols * nrow; t += blockDim.x) {
-        const int cq = g.dv_nrow.div(t), col = R.c0 + cq, iz = t - cq * nrow;
-        if (iz == nrow - 1) continue;
-        const size_t i = (size_t)col * nrow + iz;
-        const double d = (double)A.d32[i];
-        A.x[i] += d;
-        dx[0] += d * d;
-      }
+      // the true FP64 residual of x + δ; x ← x + δ, δ ← 0 and the FP32 residual on the way
       __syncthreads();
       s64.load_tables(g);
-      if (!grid_barrier(tm, &s_flag)) return false;
       double dummy_b = 0.0;
-      if (!fp64_residual<P>(g, s64, R, tm, A, false, red, &s_flag, rr, dummy_b, dx, gc)) return false;
+      if (!fp64_residual<P>(g, s64, R, tm, A, false, red, &s_flag, rr, dummy_b, dx, gc, A.d32, A.r32))
+        return false;
       SEM_MARK(g, tm, TR_REFINE);
       stalled = dx[0] > 0.25 * dd_prev;
       dd_prev = dx[0];
@@ -1520,7 +1538,10 @@ __device__ void stage_body(Instance& I, const Team& tm, int stage, int step, uns
       for (int i = R.c0 * g.nrow + threadIdx.x; i < R.c1 * g.nrow; i += blockDim.x) Pk[i] = I.pa.x[i];
   }
   // w̃ on owned columns; element S_x of η and φ̃; condensation of M'
-  for (int col = R.c0 + warp; col < R.c1; col += nw) wsurf_column(t, I.pa.x, ein, I.wt, col, lane);
+  for (int c0 = R.c0 + 4 * warp; c0 < R.c1; c0 += 4 * nw) {
+    const int col = c0 + (lane >> 3);
+    wsurf_column8(t, I.pa.x, ein, I.wt, col < R.c1 ? col : -1, lane & 7);
+  }
   for (int q = threadIdx.x; q < 2 * ne * Q; q += blockDim.x) {
     const int fld = q / (ne * Q), r = q - fld * ne * Q;
     sx_item(t, ein, pin, I.R, fld * t.Nx * Q + R.e0 * Q + r);

@@ -33,6 +33,21 @@ __device__ __forceinline__ void wsurf_column(const SurfTables& t, const double* 
   if (lane == 0) w[col] = acc / (eta[col] + t.h[col]);
 }
 
+// The same for four columns per warp, eight lanes per column (col < 0: no column; every lane of
+// the warp must call it).
+__device__ __forceinline__ void wsurf_column8(const SurfTables& t, const double* __restrict__ Phi,
+                                              const double* __restrict__ eta, double* __restrict__ w,
+                                              int col, int sub) {
+  double acc = 0.0;
+  if (col >= 0) {
+    const double* phi = Phi + (size_t)col * t.nrow;
+    for (int iz = sub; iz < t.nrow; iz += 8) acc = fma(t.wrow[iz], phi[iz], acc);
+  }
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (col >= 0 && sub == 0) w[col] = acc / (eta[col] + t.h[col]);
+}
+
 // Element-local S_x f = M·D f_e (the Δx/2 and 2/Δx scales cancel); item k over
 // [field][ex][a], two fields.
 __device__ __forceinline__ void sx_item(const SurfTables& t, const double* __restrict__ f0,
