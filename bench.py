@@ -302,10 +302,12 @@ def run_reference(args):
 # ---------------------------------------------------------------------------------------------
 # Supplementary: the operator apply on a long tank (working set above L2)
 # ---------------------------------------------------------------------------------------------
-def apply_roofline(dev, reps: int = 20, Nx: int = 65536, kernels=("fp64_column", "fp64_tile", "fp32_tile")):
-    """The operator apply y = 𝓛x on a 65536×4, P=6 periodic tank (9.8 M nodes), three kernels:
+def apply_roofline(dev, reps: int = 20, Nx: int = 65536,
+                   kernels=("fp64_column", "fp64_tile", "fp32_tile", "fp32_tile_tc")):
+    """The operator apply y = 𝓛x on a 65536×4, P=6 periodic tank (9.8 M nodes), four kernels:
     the FP64 tiled kernel (sem_laplace_apply), the FP64 element-column kernel (same call with
-    SEM_APPLY_KERNEL=column) and the FP32 tiled kernel of the mixed path (sem_laplace_apply_f32).
+    SEM_APPLY_KERNEL=column), the FP32 tiled kernel (sem_laplace_apply_f32) and the tensor-core
+    FP32 tiled kernel (same call with SEM_APPLY_F32=tc).
 
     Algorithmic work per apply: (8(P+1)+7) flops per element-local node; algorithmic bytes:
     read x + write y, 16 B (FP64) or 8 B (FP32) per node.  Design bytes add the per-column
@@ -343,16 +345,24 @@ def apply_roofline(dev, reps: int = 20, Nx: int = 65536, kernels=("fp64_column",
             ts.append(e0.elapsed_time(e1))
         return float(np.median(ts))
 
-    def column64():
-        old = os.environ.get("SEM_APPLY_KERNEL")
-        os.environ["SEM_APPLY_KERNEL"] = "column"
+    def with_env(key, value, fn):
+        old = os.environ.get(key)
+        os.environ[key] = value
         try:
-            mesh.laplace_apply(x, y)
+            fn()
         finally:
             if old is None:
-                del os.environ["SEM_APPLY_KERNEL"]
+                del os.environ[key]
             else:
-                os.environ["SEM_APPLY_KERNEL"] = old
+                os.environ[key] = old
+
+    def column64():
+        with_env("SEM_APPLY_KERNEL", "column", lambda: mesh.laplace_apply(x, y))
+
+    y32t = torch.empty_like(x32)
+
+    def tc32():
+        with_env("SEM_APPLY_F32", "tc", lambda: mesh.laplace_apply_f32(x32, y32t))
 
     P = wl.P
     flops = wl.Nx * wl.Nz * (P + 1) ** 2 * (8 * (P + 1) + 7)
@@ -361,7 +371,8 @@ def apply_roofline(dev, reps: int = 20, Nx: int = 65536, kernels=("fp64_column",
     hbm = peaks.get("hbm_gbs")
     out = {"workload": wl.name, "n_nodes": mesh.n, "flops_per_apply": flops, "l2_flushed": True}
     for name, fn, elem in (("fp64_column", column64, 8), ("fp64_tile", lambda: mesh.laplace_apply(x, y), 8),
-                           ("fp32_tile", lambda: mesh.laplace_apply_f32(x32, y32), 4)):
+                           ("fp32_tile", lambda: mesh.laplace_apply_f32(x32, y32), 4),
+                           ("fp32_tile_tc", tc32, 4)):
         if name not in kernels:
             continue
         ms = timed(fn)
@@ -374,8 +385,10 @@ def apply_roofline(dev, reps: int = 20, Nx: int = 65536, kernels=("fp64_column",
             out[name]["fp64_frac"] = flops / ms / 1e9 / FP64_PEAK_TFLOPS
     out["hbm_peak"] = hbm
     out["fp64_peak"] = FP64_PEAK_TFLOPS
-    if "fp32_tile" in kernels and len(kernels) > 1:
+    if "fp32_tile" in kernels and "fp64_tile" in kernels:
         out["fp32_vs_fp64_rel_l2"] = float(torch.linalg.norm(y32.double() - y) / torch.linalg.norm(y))
+    if "fp32_tile_tc" in kernels and "fp64_tile" in kernels:
+        out["fp32_tc_vs_fp64_rel_l2"] = float(torch.linalg.norm(y32t.double() - y) / torch.linalg.norm(y))
     mesh.close()
     return out
 
@@ -419,6 +432,7 @@ def c3_run(dev, prec: str, wls, init, steps: int, warmup: int, keep=(), flush=No
     if clocks is not None:
         clocks.start()
     launches0 = sem.launch_count()
+    per_step = []
     for _ in range(steps):
         if flush is not None:
             flush.zero_()
@@ -428,7 +442,8 @@ def c3_run(dev, prec: str, wls, init, steps: int, warmup: int, keep=(), flush=No
         batch.rk4_step(etas, phis, dts, 1)                 # synchronises (status check)
         e1.record(stream)
         e1.synchronize()
-        total += e0.elapsed_time(e1)
+        per_step.append(e0.elapsed_time(e1))
+        total += per_step[-1]
     torch.cuda.synchronize()
     launches = sem.launch_count() - launches0
     if world > 1:
@@ -440,7 +455,9 @@ def c3_run(dev, prec: str, wls, init, steps: int, warmup: int, keep=(), flush=No
     info = batch.info()
     dof_step = 4 * sum(wl.n_unknowns for wl in wls)
     ms = total / steps
+    srt = sorted(per_step)
     fig = {"ms_per_rk4_step": ms, "laplace_dof_per_s": dof_step / ms * 1e3,
+           "step_ms": {"min": srt[0], "median": srt[len(srt) // 2], "max": srt[-1]},
            "tank_steps_per_s": len(wls) / ms * 1e3, **info, "total_ms": total, "launches": launches,
            "clocks": clk,
            "iterations_per_solve": sum(c.iterations for c in cnt) / max(1, sum(c.solves for c in cnt)),
@@ -978,7 +995,7 @@ def main():
     ap.add_argument("--long-runs", action="store_true",
                     help="only the full-length C2 and C4 runs with the oracle's volume and energy diagnostics")
     ap.add_argument("--apply-only", default=None,
-                    help="comma list of fp64_column,fp64_tile,fp32_tile: time only these applies (for profiling)")
+                    help="comma list of fp64_column,fp64_tile,fp32_tile,fp32_tile_tc: time only these applies")
     ap.add_argument("--apply-nx", type=int, default=65536)
     ap.add_argument("--apply-reps", type=int, default=20)
     args = ap.parse_args()

@@ -32,7 +32,8 @@
  * Environment (tuning and testing).  Read by sem_mesh_create: SEM_GRID_LIMIT caps the number
  * of CTAs of the persistent Krylov kernel and of a mesh's fused stage (default: all
  * co-resident); SEM_FUSED_STAGE=0 makes sem_rk4_step run the multi-kernel path instead of one
- * fused launch per RK stage.  Read by sem_laplace_apply: SEM_APPLY_KERNEL=column (see there).
+ * fused launch per RK stage.  Read by sem_laplace_apply: SEM_APPLY_KERNEL=column (see there);
+ * by sem_laplace_apply_f32: SEM_APPLY_F32=tc (see there).
  * Read by sem_batch_create: SEM_BATCH_WIDE=1 (or 0) makes every group of the batch use the
  * two-CTAs-per-SM build of the fused stage (or the one-CTA-per-SM build); by default groups of
  * more than 8 instances use the former.  SEM_BATCH_CLUSTER=1 (or 0) makes the batch run its
@@ -167,7 +168,9 @@ int sem_laplace_apply(sem_mesh* m, const double* x_d, double* y_d, void* stream)
  * with the FP32 copy of the geometry of the last sem_update_geometry.  One kernel, tiles of
  * consecutive x-elements with the element left of each tile recomputed, so every output
  * column is complete in one CTA and written once; uses no workspace.  x_d, y_d: device,
- * float, n values, must not overlap. */
+ * float, n values, must not overlap.  The environment variable SEM_APPLY_F32=tc selects, for
+ * orders 4..7, a kernel whose element contractions run on the tensor cores (TF32 products
+ * split three ways for FP32 accuracy; same result up to rounding, and slower on GB300). */
 int sem_laplace_apply_f32(const sem_mesh* m, const float* x_d, float* y_d, void* stream);
 
 /* Allocation-free form of sem_laplace_apply (the paper has no counterpart; this is a

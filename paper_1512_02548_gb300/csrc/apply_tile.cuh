@@ -82,7 +82,7 @@ struct TileLayout {
   // stride of one (element, layer) block of a line buffer: at least Q·QP and ≡ 8 (mod 16), so
   // that the σ-lines of consecutive layers (one warp) fall in different shared-memory banks
   static constexpr int BS = Q * QP + ((8 - (Q * QP) % 16) + 16) % 16;
-  int E, en_max, tcols, xbuf, nline;
+  int E, en_max, tcols, xbuf, nline, ybuf;
   __host__ __device__ TileLayout(int E_, int nrow, int Nz, int elem) {
     E = E_;
     en_max = E + 1;
@@ -92,12 +92,19 @@ struct TileLayout {
     const int per16 = 16 / elem;
     xbuf = ((tcols * nrow + 2 * per16 + per16 - 1) / per16) * per16;
     nline = en_max * Nz * BS;
+    ybuf = ((tcols * nrow + 3) / 4) * 4;   // the tile's nodes (tensor-core kernel), 16-byte multiple
   }
   // bytes of dynamic shared memory for element size `elem`: two mbarriers (16 B), two staging
   // buffers, the line buffers and the tile's geometry
   __host__ __device__ size_t bytes(int nrow, int Nz, int elem) const {
     return 16 + (size_t)elem * (2 * (size_t)xbuf + 3 * (size_t)nline + (size_t)en_max * Q * 4 +
                                 (size_t)en_max * Nz * 2 + nrow + Q + 2 * (size_t)en_max * Nz * Q);
+  }
+  // the same for the tensor-core kernel (FP32): the tile's node buffer and `scratch` floats per
+  // warp in place of the three line buffers
+  __host__ __device__ size_t bytes_tc(int nrow, int Nz, int scratch) const {
+    return 16 + 4 * (2 * (size_t)xbuf + (size_t)ybuf + (size_t)(kThreads / 32) * scratch +
+                     (size_t)en_max * Q * 4 + (size_t)en_max * Nz * 2 + nrow + Q + 2 * (size_t)en_max * Nz * Q);
   }
 };
 

@@ -923,7 +923,10 @@ int sem_laplace_apply(sem_mesh* m, const double* x_d, double* y_d, void* stream)
 int sem_laplace_apply_f32(const sem_mesh* m, const float* x_d, float* y_d, void* stream) {
   if (!m || !x_d || !y_d || x_d == y_d) return fail(SEM_ERR_INVALID_ARG, "bad pointer");
   DeviceGuard dg(m->device);
-  CUDA_TRY(launch_apply_tile(1, m->g, x_d, y_d, (cudaStream_t)stream));
+  // "tc": the tensor-core kernel for orders 4..7 (measured slower than the CUDA-core kernel on
+  // GB300; kept for comparison), else the CUDA-core kernel
+  const char* k = std::getenv("SEM_APPLY_F32");
+  CUDA_TRY(launch_apply_tile(k && std::strcmp(k, "tc") == 0 ? 3 : 1, m->g, x_d, y_d, (cudaStream_t)stream));
   return SEM_OK;
 }
 

@@ -340,6 +340,7 @@ __global__ void __launch_bounds__(kThreads) k_apply(DevGeom g, const double* __r
 }  // namespace semgb
 
 #include "apply_tile.cuh"
+#include "apply_tc.cuh"
 
 namespace semgb {
 
@@ -1759,10 +1760,68 @@ cudaError_t launch_stage_cluster_impl(int mixed, int wide, const StageArgs& a, i
 
 // Tiled apply (apply_tile.cuh): widest tile of at most 16 elements whose shared memory keeps
 // three CTAs per SM; persistent CTAs (at most the co-resident count) stride over the tiles.
+// The tensor-core FP32 kernel (apply_tc.cuh, fp32 = 3, orders 4..7) takes tiles of 64/Nz − 1
+// elements: with the recomputed left neighbour, 64 element blocks, four block pairs per warp.
 constexpr size_t kTileSmemTarget = 76 * 1024;
 
 template <int P>
+static int tile_grid(const void* fn, size_t smem, int E, int Nx, int slot, cudaError_t* err) {
+  // the attribute, the SM count and the occupancy for the last (device, smem) of each kernel
+  // variant are kept, so that a repeated apply costs one launch on the host
+  static std::mutex mu;
+  static int last_dev[9] = {-1, -1, -1, -1, -1, -1, -1, -1, -1}, last_sms[9] = {0}, last_per_sm[9] = {0};
+  static size_t last_smem[9] = {0};
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) { *err = e; return 0; }
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (last_dev[slot] != dev || last_smem[slot] != smem) {
+      if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem)) != cudaSuccess ||
+          (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
+          (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem)) != cudaSuccess) {
+        *err = e;
+        return 0;
+      }
+      last_dev[slot] = dev; last_smem[slot] = smem; last_sms[slot] = sms; last_per_sm[slot] = per_sm;
+    }
+    sms = last_sms[slot];
+    per_sm = last_per_sm[slot];
+  }
+  if (per_sm < 1) { *err = cudaErrorInvalidConfiguration; return 0; }
+  const long long ntiles = (Nx + E - 1) / E;
+  *err = cudaSuccess;
+  return (int)(ntiles < (long long)per_sm * sms ? ntiles : (long long)per_sm * sms);
+}
+
+template <int P>
 cudaError_t launch_apply_tile_impl(int fp32, const DevGeom& g, const void* x, void* y, cudaStream_t s) {
+  const int bulk_ok = (reinterpret_cast<uintptr_t>(x) % 16) == 0 ? 1 : 0;   // bulk copies need 16-B alignment
+  const float* xf = static_cast<const float*>(x);
+  float* yf = static_cast<float*>(y);
+  cudaError_t e = cudaSuccess;
+  if constexpr (P >= 4 && P <= 7) {
+    if (fp32 == 3) {   // tensor-core kernel
+      int E = g.Nz < 64 ? 64 / g.Nz - 1 : 1;
+      while (E > 1 && apply_tile_tc_smem<P>(E, g.nrow, g.Nz) > kTileSmemTarget) E = (E + 1) / 2 - 1;
+      const size_t smem = apply_tile_tc_smem<P>(E, g.nrow, g.Nz);
+      if (smem > (size_t)kMaxDynSmem) return cudaErrorInvalidValue;
+      const int nzc = (g.Nz == 1 || g.Nz == 2 || g.Nz == 4) ? g.Nz : 0;
+      const int k = 5 + (nzc == 4 ? 3 : nzc);
+      const void* fns[4] = {(const void*)k_apply_tile_tc<P, 0>, (const void*)k_apply_tile_tc<P, 1>,
+                            (const void*)k_apply_tile_tc<P, 2>, (const void*)k_apply_tile_tc<P, 4>};
+      const int grid = tile_grid<P>(fns[k - 5], smem, E, g.Nx, k, &e);
+      if (e != cudaSuccess) return e;
+      switch (k) {
+        case 5: k_apply_tile_tc<P, 0><<<grid, kThreads, smem, s>>>(g, xf, yf, E, bulk_ok); break;
+        case 6: k_apply_tile_tc<P, 1><<<grid, kThreads, smem, s>>>(g, xf, yf, E, bulk_ok); break;
+        case 7: k_apply_tile_tc<P, 2><<<grid, kThreads, smem, s>>>(g, xf, yf, E, bulk_ok); break;
+        default: k_apply_tile_tc<P, 4><<<grid, kThreads, smem, s>>>(g, xf, yf, E, bulk_ok); break;
+      }
+      count_launch();
+      return cudaGetLastError();
+    }
+  }
   const size_t elem = fp32 ? sizeof(float) : sizeof(double);
   int E = 16;
   while (E > 1 && apply_tile_smem<P>(E, g.nrow, g.Nz, elem) > kTileSmemTarget) E >>= 1;
@@ -1776,33 +1835,8 @@ cudaError_t launch_apply_tile_impl(int fp32, const DevGeom& g, const void* x, vo
   const void* fns[5] = {(const void*)k_apply_tile<P, double, 0>, (const void*)k_apply_tile<P, float, 0>,
                         (const void*)k_apply_tile<P, float, 1>, (const void*)k_apply_tile<P, float, 2>,
                         (const void*)k_apply_tile<P, float, 4>};
-  const void* fn = fns[k];
-  // the attribute, the SM count and the occupancy for the last (device, smem) of each variant are
-  // kept, so that a repeated apply costs one launch on the host
-  static std::mutex mu;
-  static int last_dev[5] = {-1, -1, -1, -1, -1}, last_sms[5] = {0}, last_per_sm[5] = {0};
-  static size_t last_smem[5] = {0};
-  int dev = 0, sms = 0, per_sm = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  const int grid = tile_grid<P>(fns[k], smem, E, g.Nx, k, &e);
   if (e != cudaSuccess) return e;
-  {
-    std::lock_guard<std::mutex> lk(mu);
-    if (last_dev[k] != dev || last_smem[k] != smem) {
-      if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem)) != cudaSuccess)
-        return e;
-      if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-      if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem)) != cudaSuccess) return e;
-      last_dev[k] = dev; last_smem[k] = smem; last_sms[k] = sms; last_per_sm[k] = per_sm;
-    }
-    sms = last_sms[k];
-    per_sm = last_per_sm[k];
-  }
-  if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  const long long ntiles = (g.Nx + E - 1) / E;
-  const int grid = (int)(ntiles < (long long)per_sm * sms ? ntiles : (long long)per_sm * sms);
-  const int bulk_ok = (reinterpret_cast<uintptr_t>(x) % 16) == 0 ? 1 : 0;   // bulk copies need 16-B alignment
-  const float* xf = static_cast<const float*>(x);
-  float* yf = static_cast<float*>(y);
   switch (k) {
     case 0: k_apply_tile<P, double, 0><<<grid, kThreads, smem, s>>>(g, static_cast<const double*>(x),
                                                                    static_cast<double*>(y), E, bulk_ok); break;

@@ -259,8 +259,9 @@ cudaError_t launch_geometry(const DevGeom& g, const double* eta, bool with_diag,
 cudaError_t launch_apply(const DevGeom& g, const double* x, double* y, double* qtmp, double* edge,
                          cudaStream_t s);
 cudaError_t launch_l2g(const DevGeom& g, int32_t* l2g, cudaStream_t s);
-// Tiled apply y = 𝓛x at every node in FP32 (fp32 = 1, x, y float) or FP64 (x, y double), from the
-// geometry of the last launch_geometry; x and y must not overlap.  No workspace.
+// Tiled apply y = 𝓛x at every node in FP32 (fp32 = 1: CUDA-core kernel; fp32 = 3: tensor-core
+// kernel for orders 4..7, else the CUDA-core one; x, y float) or FP64 (fp32 = 0, x, y double), from
+// the geometry of the last launch_geometry; x and y must not overlap.  No workspace.
 cudaError_t launch_apply_tile(int fp32, const DevGeom& g, const void* x, void* y, cudaStream_t s);
 // Tile width of the tiled apply for (P, Nz): 0 = the widest that keeps three CTAs per SM.
 void set_apply_tile_width(int P, int Nz, int E);

@@ -113,3 +113,50 @@ def test_unaligned_input_takes_the_plain_staging_path():
     gm.laplace_apply_f32(x, a)
     gm.laplace_apply_f32(xu, b)
     assert torch.equal(a, b)
+
+
+TC_CASES = [
+    dict(P=4, Nx=130, Nz=1),
+    dict(P=5, Nx=70, Nz=2, periodic=False, bar=True),
+    dict(P=6, Nx=47, Nz=4),
+    dict(P=7, Nx=44, Nz=3, periodic=False),
+    dict(P=6, Nx=16, Nz=4, periodic=False),
+    dict(P=6, Nx=1, Nz=4, periodic=False),
+    dict(P=5, Nx=25, Nz=5, bar=True),
+    dict(P=7, Nx=9, Nz=1, periodic=False),
+]
+
+
+def tc_env(fn):
+    old = os.environ.get("SEM_APPLY_F32")
+    os.environ["SEM_APPLY_F32"] = "tc"
+    try:
+        return fn()
+    finally:
+        if old is None:
+            del os.environ["SEM_APPLY_F32"]
+        else:
+            os.environ["SEM_APPLY_F32"] = old
+
+
+@pytest.mark.parametrize("case", TC_CASES, ids=lambda c: "-".join(f"{k}{v}" for k, v in c.items()))
+def test_tensor_core_fp32_apply_matches_the_oracle_and_the_scalar_kernel(case):
+    """Orders 4..7 with SEM_APPLY_F32=tc take the tensor-core kernel (3×TF32 products, tiles of
+    64/Nz − 1 elements): the cases cover one to several tiles with ragged last tiles, an odd block
+    count (last block pair half empty), walls and periodic ends, a bar, and layer counts 1–5 (5:
+    the run-time layer count).  Same tolerance as the CUDA-core FP32 kernel, 2e-6, against the
+    oracle and against that kernel; the tensor-core result is bitwise reproducible."""
+    wl, om, gm, eta = setup(**case)
+    x = random_field(om.n, 9)
+    ref = om.stiffness(eta) @ x
+    xd = torch.tensor(x, device=DEV).float()
+    y_sc = torch.full((om.n,), float("nan"), dtype=torch.float32, device=DEV)
+    gm.laplace_apply_f32(xd, y_sc)
+    y_tc = torch.full((om.n,), float("nan"), dtype=torch.float32, device=DEV)
+    tc_env(lambda: gm.laplace_apply_f32(xd, y_tc))
+    y_tc2 = torch.full((om.n,), float("nan"), dtype=torch.float32, device=DEV)
+    tc_env(lambda: gm.laplace_apply_f32(xd, y_tc2))
+    assert bool(torch.isfinite(y_tc).all()) and torch.equal(y_tc, y_tc2)
+    assert rel(y_tc, ref) < 2e-6
+    assert rel(y_sc, ref) < 2e-6
+    assert rel(y_tc, y_sc.double().cpu().numpy()) < 2e-6
