@@ -398,16 +398,18 @@ def rel_l2(a, b) -> float:
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300))
 
 
+C3_TOL = 1e-10                     # the C3 configuration's refined residual
+STRICT_TOL = {"fp64": 1e-13, "mixed": 1e-12}
+
+
 def c3_run(dev, prec: str, wls, init, steps: int, warmup: int, keep=(), flush=None, timing=False, clocks=None,
-           world: int = 1, tol: float | None = None):
+           world: int = 1, tol: float = C3_TOL):
     """C3 batch in one precision: `warmup` untimed steps (the state after the first is kept for the
     tanks in `keep`), then `steps` steps, each timed alone with CUDA events on the stream, L2
     flushed before each (clocks sampled and library launches counted over the timed steps).
     Returns (figures, kept states, per-tank counters, stage-launch timing, final states)."""
     import torch
     import paper_1512_02548_gb300 as sem
-    if tol is None:
-        tol = 1e-13 if prec == "fp64" else 1e-12
     meshes = [sem.Mesh.from_workload(wl, precision=prec, tol=tol) for wl in wls]
     batch = sem.Batch(meshes)
     etas = [torch.tensor(e, device=dev) for e, _ in init]
@@ -476,7 +478,7 @@ def c3_e2e(dev, wls, init, steps: int, warmup: int):
     import numpy as np
     import torch
     import paper_1512_02548_gb300 as sem
-    meshes = [sem.Mesh.from_workload(wl, tol=1e-13) for wl in wls]
+    meshes = [sem.Mesh.from_workload(wl, tol=C3_TOL) for wl in wls]
     batch = sem.Batch(meshes)
     eta_h = torch.tensor(np.concatenate([e for e, _ in init])).pin_memory()
     phis_h = torch.tensor(np.concatenate([p for _, p in init])).pin_memory()
@@ -498,7 +500,7 @@ def c3_sequential(dev, wls, init, steps: int):
     """The same tanks one after another on the plain FP64 single-mesh path (sem_rk4_step)."""
     import torch
     import paper_1512_02548_gb300 as sem
-    meshes = [sem.Mesh.from_workload(wl) for wl in wls]
+    meshes = [sem.Mesh.from_workload(wl, tol=C3_TOL) for wl in wls]
     etas = [torch.tensor(e, device=dev) for e, _ in init]
     phis = [torch.tensor(p, device=dev) for _, p in init]
     for m, e, p, wl in zip(meshes, etas, phis, wls):
@@ -646,14 +648,24 @@ def c5_serving(rates=(100.0, 1000.0), count: int = 1000, sample: int = 4, steps_
             warm = False
         ent = {"laplace_share": sum(r.kind == "laplace" for r in base) / count,
                "nodes_total": int(sum(r.wl.n_nodes for r in base))}
+        def slowest(rs, n=10):
+            done = [r for r in rs if r.error is None and r.finished is not None]
+            done.sort(key=lambda r: r.finished - r.arrival, reverse=True)
+            return [{"kind": r.kind, "nodes": r.wl.n_nodes, "P": r.wl.P, "latency_ms": 1e3 * (r.finished - r.arrival),
+                     "wait_ms": (1e3 * (r.admitted - r.arrival)) if r.admitted is not None else None}
+                    for r in done[:n]]
+
         reqs = fresh()
         s = Server(GpuExecutor("mixed"), 150 << 30, keep_results=keep, max_steps_per_tick=steps_per_tick).run(reqs)
-        ent["served_mixed"] = {k: s[k] for k in keys + ("ticks", "peak_active")}
+        ent["served_mixed"] = {k: s[k] for k in keys + ("ticks", "peak_active", "host_phases")}
+        ent["served_mixed"]["slowest"] = slowest(reqs)
         for r in reqs:
             if r.rid in keep and r.error is None:
                 checks.append((rate, count, r.rid, r.kind, r.eta0, r.phis0, r.nsteps, r.result))
-        s = sequential(fresh(), "fp64")
+        reqs = fresh()
+        s = sequential(reqs, "fp64")
         ent["sequential_fp64"] = {k: s[k] for k in keys}
+        ent["sequential_fp64"]["slowest"] = slowest(reqs)
         ent["served_mixed_dof_speedup_vs_sequential_fp64"] = (ent["served_mixed"]["laplace_dof_per_s"] /
                                                               ent["sequential_fp64"]["laplace_dof_per_s"])
         out[f"rate_{int(rate)}_per_s"] = ent
@@ -797,12 +809,12 @@ def run_gpu(args):
     mix, keptmx, cntmx, tmmx, _ = c3_run(dev, "mixed", wls, init, args.steps, args.warmup, keep=sample,
                                          flush=flush, timing=True, world=world)
     seq = c3_sequential(dev, wls, init, max(1, min(2, args.steps))) if lead else None
-    # both paths at one looser tolerance, 1e-10, still far inside the 1e-8 error target
-    loose = {}
+    # both paths again at the strict tolerances of the other configurations (1e-13 FP64, 1e-12 mixed)
+    strict = {}
     for prec in ("fp64", "mixed"):
         fig, kept, _, _, _ = c3_run(dev, prec, wls, init, max(1, min(5, args.steps)), args.warmup, keep=sample,
-                                    flush=flush, world=world, tol=1e-10)
-        loose[prec] = ({k: v for k, v in fig.items() if k not in ("total_ms", "clocks", "launches")}, kept)
+                                    flush=flush, world=world, tol=STRICT_TOL[prec])
+        strict[prec] = ({k: v for k, v in fig.items() if k not in ("total_ms", "clocks", "launches")}, kept)
 
     # roofline of the batched fused stage kernel.  The launches of the (order, precision, cluster
     # size) groups run at the same time on their own streams, so the unit is the whole step: FP64
@@ -827,11 +839,11 @@ def run_gpu(args):
           "mixed_over_batched_fp64": mix["laplace_dof_per_s"] / f64["laplace_dof_per_s"],
           "mixed_over_sequential_fp64": (mix["laplace_dof_per_s"] / seq["laplace_dof_per_s"]) if seq else None,
           "batched_fp64_over_sequential_fp64": (f64["laplace_dof_per_s"] / seq["laplace_dof_per_s"]) if seq else None,
-          "at_tol_1e-10": {"fp64": loose["fp64"][0], "mixed": loose["mixed"][0],
-                           "mixed_over_fp64": loose["mixed"][0]["laplace_dof_per_s"] /
-                           loose["fp64"][0]["laplace_dof_per_s"],
-                           "note": "both paths at relative residual tolerance 1e-10; errors against the "
-                                   "oracle in oracle_check"},
+          "at_strict_tol": {"fp64": strict["fp64"][0], "mixed": strict["mixed"][0],
+                            "mixed_over_fp64": strict["mixed"][0]["laplace_dof_per_s"] /
+                            strict["fp64"][0]["laplace_dof_per_s"],
+                            "note": "relative residual 1e-13 (FP64) and 1e-12 with refinement (mixed); errors "
+                                    "against the oracle in oracle_check"},
           "fp64_work_per_step_gflop": {"fp64": flops / args.steps / 1e9, "mixed": flops_mx / args.steps / 1e9},
           "stage_launch_ms": {"fp64": avg_launch_ms, "mixed": tmmx.krylov_ms / max(tmmx.krylov_launches, 1)}}
 
@@ -840,7 +852,7 @@ def run_gpu(args):
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": C3_NAME, "instances": len(wls), "n_unknowns": dof_step // 4, "precision": "fp64",
-                   "tol": "relative residual 1e-13 (FP64), 1e-12 with refinement (mixed)",
+                   "tol": "relative residual 1e-10 (FP64 PCG; mixed: refined FP64 residual), the C3 configuration's",
                    "l2": "flushed between timed steps (256 MB write, untimed); working set above L2",
                    "parallelism": "replicas" if world > 1 else "single"},
         "rk4_steps_per_s": tank_steps,
@@ -884,7 +896,7 @@ def run_gpu(args):
         line["apply_long_tank"] = apply_roofline(dev)
 
     if check:
-        extras["c3_loose"] = {p: loose[p][1] for p in loose}
+        extras["c3_strict"] = {p: strict[p][1] for p in strict}
         oracle_checks(line, sample, init, kept64, keptmx, extras)
     if world > 1:
         dist.barrier()
@@ -918,8 +930,8 @@ def oracle_checks(line, sample, init, kept64, keptmx, extras):
         c3 = line["c3_uneven_batch"]
         c3["oracle_check"] = {"tanks": list(sample), "steps": 1, "fp64_max_rel_l2": err64, "mixed_max_rel_l2": errmx,
                               "tolerance": {"fp64": 1e-10, "mixed": 1e-8}}
-        for prec, kept in extras.get("c3_loose", {}).items():
-            c3["oracle_check"][f"{prec}_at_tol_1e-10_max_rel_l2"] = max(
+        for prec, kept in extras.get("c3_strict", {}).items():
+            c3["oracle_check"][f"{prec}_at_strict_tol_max_rel_l2"] = max(
                 max(rel_l2(kept[i][0], r[1][0]), rel_l2(kept[i][1], r[1][1])) for i, r in zip(sample, res))
         line["mixed"]["max_rel_l2_vs_oracle"] = errmx
         line["max_rel_l2_vs_oracle"] = err64

@@ -98,3 +98,28 @@ def test_nonfinite_request_fails_alone(reqs_and_alone):
     s = Server(GpuExecutor("fp64"), hbm_budget=8 << 30).run(served)
     assert bad.error == "error code 5" and s["failed"] == 1
     check([r for r in served if r is not bad], alone, 1e-10)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-8)])
+def test_requests_run_alone_inside_a_tick_give_the_same_results(reqs_and_alone, precision, tol):
+    """With a low solo threshold, each tick runs its larger requests on their own single-mesh path
+    and batches the rest: results are those of the requests run alone."""
+    reqs, alone = reqs_and_alone
+    served = copy(reqs)
+    ex = GpuExecutor(precision, solo_nodes=4000)
+    assert any(r.wl.n_nodes >= 4000 for r in served) and any(r.wl.n_nodes < 4000 for r in served)
+    s = Server(ex, hbm_budget=8 << 30).run(served)
+    assert s["completed"] == len(reqs) and s["peak_active"] > 1
+    check(served, alone, tol)
+
+
+def test_nonfinite_request_run_alone_fails_alone(reqs_and_alone):
+    reqs, alone = reqs_and_alone
+    served = copy(reqs)
+    bad = max((r for r in served if r.kind == "rk4"), key=lambda r: r.wl.n_nodes)
+    bad.eta0 = bad.eta0.copy()
+    bad.eta0[1] = np.nan
+    ex = GpuExecutor("fp64", solo_nodes=bad.wl.n_nodes)
+    s = Server(ex, hbm_budget=8 << 30).run(served)
+    assert bad.error == "error code 5" and s["failed"] == 1
+    check([r for r in served if r is not bad], alone, 1e-10)
