@@ -56,12 +56,13 @@ def flops_per_apply(wl) -> float:
 
 
 def fp64_solver_flops(wl, solves: int, iterations: int, refinements: int, mixed: bool) -> float:
-    """FP64 algorithmic flops of `solves` Laplace solves: two applies per solve for the lifted
-    right-hand side and the initial residual, one per Krylov iteration with its vector work
-    (plain FP64), or one per refinement (mixed: its inner iterations run in FP32)."""
+    """FP64 algorithmic flops of `solves` Laplace solves: one apply per solve for the initial
+    residual 𝓛[x; φ̃] (the lifted right-hand side enters only through its norm, taken with an FP32
+    apply), one per Krylov iteration with its vector work (plain FP64), or one per refinement
+    (mixed: its inner iterations run in FP32)."""
     if mixed:
-        return (2 * solves + refinements) * flops_per_apply(wl)
-    return (2 * solves + iterations) * flops_per_apply(wl) + iterations * 13 * wl.n_unknowns
+        return (solves + refinements) * flops_per_apply(wl)
+    return (solves + iterations) * flops_per_apply(wl) + iterations * 13 * wl.n_unknowns
 
 
 def max_over_ranks(value: float, device=None) -> float:
