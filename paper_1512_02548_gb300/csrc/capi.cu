@@ -665,6 +665,7 @@ static int mesh_create_impl(const sem_params* pin, const double* x_edges_h, cons
 
   Carve cv;
   const size_t nE = (size_t)Nx * nrow;
+  const size_t o_cxz = cv.take<double>((size_t)Nx * Nz * 2), o_r2dx = cv.take<double>(Nx);
   const size_t o_h = cv.take<double>(ncol), o_hx = cv.take<double>((size_t)Nx * Q), o_dxe = cv.take<double>(Nx),
                o_dsl = cv.take<double>(Nz), o_sig = cv.take<double>(nrow), o_geo64 = cv.take<double>((size_t)Nx * Q * 4),
                o_geo32 = cv.take<float>((size_t)Nx * Q * 4), o_id64 = cv.take<double>(n), o_id32 = cv.take<float>(n),
@@ -732,6 +733,18 @@ static int mesh_create_impl(const sem_params* pin, const double* x_edges_h, cons
   }
   up(o_h, std::vector<double>(h_h, h_h + ncol));
   up(o_hx, hx_loc); up(o_dxe, dxe); up(o_dsl, dsl); up(o_sig, sig);
+  {
+    std::vector<double> cxz((size_t)Nx * Nz * 2);
+    for (int e = 0; e < Nx; ++e)
+      for (int l = 0; l < Nz; ++l) {
+        cxz[((size_t)e * Nz + l) * 2] = dsl[l] / dxe[e];
+        cxz[((size_t)e * Nz + l) * 2 + 1] = dxe[e] / dsl[l];
+      }
+    up(o_cxz, cxz);
+    std::vector<double> r2dx(Nx);
+    for (int e = 0; e < Nx; ++e) r2dx[e] = 2.0 / dxe[e];
+    up(o_r2dx, r2dx);
+  }
   up(o_tD, L.D); up(o_tMD, MD); up(o_tB, B); up(o_tI, I); up(o_tF, F); up(o_twr, wrow);
   up(o_tAii, Aii); up(o_tZ, Z); up(o_tse, se); up(o_te, th_e); up(o_tm, th_m); up(o_tcp, th_cp); up(o_tz, th_z);
   up(o_lam, lam);
@@ -757,7 +770,8 @@ static int mesh_create_impl(const sem_params* pin, const double* x_edges_h, cons
 
   DevGeom& g = m->g;
   g.P = P; g.Nx = Nx; g.Nz = Nz; g.ncol = ncol; g.nrow = nrow; g.periodic = p.periodic ? 1 : 0; g.chunk = chunk;
-  g.h = D_(o_h); g.hx_loc = D_(o_hx); g.dxe = D_(o_dxe); g.dsl = D_(o_dsl); g.sig = D_(o_sig);
+  g.h = D_(o_h); g.hx_loc = D_(o_hx); g.dxe = D_(o_dxe); g.dsl = D_(o_dsl); g.sig = D_(o_sig); g.cxz = D_(o_cxz);
+  g.r2dx = D_(o_r2dx);
   g.geo64 = D_(o_geo64); g.geo32 = F_(o_geo32); g.invdiag64 = D_(o_id64); g.invdiag32 = F_(o_id32);
   g.status = reinterpret_cast<int*>(m->pool + o_status);
   g.gglob = D_(o_gglob);

@@ -69,7 +69,7 @@ __device__ __forceinline__ void geometry_item(const DevGeom& g, const double* __
   double etax = 0.0;
 #pragma unroll
   for (int c = 0; c < Q; ++c) etax = fma(D[c], __ldcg(eta + col_of(g, ex, c)), etax);
-  etax *= 2.0 / g.dxe[ex];
+  etax *= g.r2dx[ex];
   const int col = col_of(g, ex, a);
   const double d = __ldcg(eta + col) + g.h[col];
   const double hx = g.hx_loc[t];
@@ -215,10 +215,9 @@ __device__ void fill_gcache(const DevGeom& g, int e0, int e1, double* gc) {
     const int l = rem0 / (Q * Q), rem = rem0 - l * (Q * Q), a = rem / Q, b = rem - a * Q;
     const int ge = e0 + e;
     const double* geo = g.geo64 + (size_t)ge * Q * 4 + a * 4;
-    const double dxe = g.dxe[ge], dsl = g.dsl[l];
+    const double* cz = g.cxz + ((size_t)ge * g.Nz + l) * 2;   // the layer's ratios, not a division per node
     double G11, G12, G22;
-    geo_factors<double>(geo[0], geo[1], geo[2], geo[3], dsl / dxe, dxe / dsl, w[a], w[b], g.sig[l * P + b], G11,
-                        G12, G22);
+    geo_factors<double>(geo[0], geo[1], geo[2], geo[3], cz[0], cz[1], w[a], w[b], g.sig[l * P + b], G11, G12, G22);
     gc[3 * t] = G11;
     gc[3 * t + 1] = G12;
     gc[3 * t + 2] = G22;
@@ -236,12 +235,8 @@ __device__ __forceinline__ T apply_element_chunk(const DevGeom& g, Smem<P, T>& s
   if (gc == nullptr) {
     const T* geo = geo_ptr<T>(g) + (size_t)ex0 * Q * 4;
     for (int t = threadIdx.x; t < ne * 4 * Q; t += blockDim.x) s.geo[t] = geo[t];
-    for (int t = threadIdx.x; t < ne * Nz; t += blockDim.x) {
-      const int e = t / Nz, l = t - e * Nz;
-      const double dxe = g.dxe[ex0 + e], dsl = g.dsl[l];
-      s.cxz[2 * t] = (T)(dsl / dxe);
-      s.cxz[2 * t + 1] = (T)(dxe / dsl);
-    }
+    const double* cz = g.cxz + (size_t)ex0 * Nz * 2;
+    for (int t = threadIdx.x; t < ne * Nz * 2; t += blockDim.x) s.cxz[t] = (T)cz[t];
   }
   for (int t = threadIdx.x; t < ne * colsz; t += blockDim.x) {
     const int e = g.dv_colsz.div(t), rem = t - e * colsz;
@@ -1127,7 +1122,7 @@ __device__ __forceinline__ double prec_kx_entry(const DevGeom& g, int ex, int t)
   double s = 0.0;
 #pragma unroll
   for (int a = 0; a < Q; ++a) s = fma(D[a * Q + i] * w[a] * geo[a * 4 + 0], D[a * Q + j], s);
-  return (2.0 / g.dxe[ex]) * s;
+  return g.r2dx[ex] * s;
 }
 template <int P>
 __device__ __forceinline__ double prec_mw_entry(const DevGeom& g, int ex, int i) {

@@ -41,6 +41,8 @@ struct DevGeom {
   const double* dxe;     // [Nx] element widths Δx_e
   const double* dsl;     // [Nz] layer heights Δσ_l
   const double* sig;     // [nrow] σ of each row
+  const double* cxz;     // [Nx][Nz][2] Δσ_l/Δx_e, Δx_e/Δσ_l (constant per mesh)
+  const double* r2dx;    // [Nx] 2/Δx_e
   double* geo64;         // [Nx*(P+1)*4] per element-local column: d, 1/d, ∂x h, ∂x d
   float* geo32;          // same in FP32 (inner solves of the mixed path)
   double* invdiag64;     // [n] 1 / diag(−𝓛) at interior nodes, 0 at the surface
