@@ -1171,15 +1171,20 @@ __device__ __forceinline__ void prec_elem_mode(const DevGeom& g, const PrecSetup
   for (int i = 0; i < Pm; ++i)
 #pragma unroll
     for (int j = 0; j < Pm; ++j) A32[(i * Pm + j) * nr] = 0.5f * (Ai[i][j] + Ai[j][i]);
+  // Z = E_bi E_ii⁻¹ from the FP32 inverse, accumulated in FP32: the inverse carries FP32 error
+  // already, and the FP64 pipe is the scarce one (the Schur complements below stay FP64)
+  float kb0[Pm], kb1[Pm];
+#pragma unroll
+  for (int m = 0; m < Pm; ++m) { kb0[m] = (float)Kx[1 + m]; kb1[m] = (float)Kx[P * Q + 1 + m]; }
   double Z0[Pm], Z1[Pm];
 #pragma unroll
   for (int i = 0; i < Pm; ++i) {
-    double a0 = 0.0, a1 = 0.0;
+    float a0 = 0.f, a1 = 0.f;
 #pragma unroll
     for (int m = 0; m < Pm; ++m) {
-      const double am = (double)(0.5f * (Ai[m][i] + Ai[i][m]));
-      a0 = fma(Kx[1 + m], am, a0);
-      a1 = fma(Kx[P * Q + 1 + m], am, a1);
+      const float am = 0.5f * (Ai[m][i] + Ai[i][m]);
+      a0 = fmaf(kb0[m], am, a0);
+      a1 = fmaf(kb1[m], am, a1);
     }
     Z0[i] = a0; Z1[i] = a1;
   }
