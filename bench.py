@@ -989,6 +989,10 @@ def column_positions(wl):
 
 
 def main():
+    # one hardware work queue per stream of the batch's group launches (15 for the 512-tank batch;
+    # CUDA's default of 8 makes streams share queues, where a launch waits behind another stream's);
+    # read when the CUDA context is created, so before anything touches the GPU
+    os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)

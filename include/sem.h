@@ -39,7 +39,10 @@
  * more than 8 instances use the former.  SEM_BATCH_CLUSTER=1 (or 0) makes the batch run its
  * instances as thread-block-cluster teams on concurrent streams (or as cooperative launches, one
  * per RK stage and (order, precision) group); by default the batch takes the plan it estimates
- * faster.
+ * faster.  The cluster plan runs one stream per group of its launches (15 for 512 uneven tanks of
+ * orders 4..8): a CUDA context with at least that many hardware work queues
+ * (CUDA_DEVICE_MAX_CONNECTIONS, read when the context is created; default 8) keeps one group's
+ * launch from waiting behind another's.
  *
  * Device memory.  Each mesh and batch owns one device block, taken at creation from a
  * per-device cache of blocks freed by earlier meshes and batches (or from cudaMalloc) and given

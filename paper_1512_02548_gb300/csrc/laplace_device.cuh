@@ -994,6 +994,7 @@ __device__ bool solve_body(const DevGeom& g, const PcgArgs& A, const Team& tm, u
     __syncthreads();
     gc = c;
   }
+  SEM_MARK(g, tm, TR_GCACHE);
   double rr = 0.0, bb = 0.0;
   // mixed precision: the residual loop also starts the first inner solve (δ = 0, FP32 residual)
   if (!fp64_residual<P>(g, s64, R, tm, A, true, red, &s_flag, rr, bb, nullptr, gc, nullptr,

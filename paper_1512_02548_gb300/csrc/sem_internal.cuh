@@ -64,7 +64,7 @@ struct DevGeom {
 // stamps %globaltimer with a tag at the phase boundaries of the Krylov and fused stage kernels.
 constexpr int kTraceMax = 4096;
 enum : int {
-  TR_START = 1, TR_SETUP = 2, TR_BAR_SETUP = 3, TR_PIVOTS = 4, TR_RESIDUAL = 5,
+  TR_START = 1, TR_SETUP = 2, TR_BAR_SETUP = 3, TR_PIVOTS = 4, TR_RESIDUAL = 5, TR_GCACHE = 6,
   TR_IT_APPLY = 10, TR_IT_BAR1 = 11, TR_IT_SCALARS = 12, TR_IT_UPDATE = 13, TR_IT_BAR2 = 14,
   TR_IT_INTERFACE = 15, TR_IT_BAR3 = 16, TR_IT_BACKSUB = 17, TR_CG_START = 18, TR_CG_END = 19,
   TR_REFINE = 20, TR_SOLVED = 30, TR_WSX = 31, TR_MINT1 = 32, TR_MBACK1 = 33, TR_ZAK = 34, TR_MINT2 = 35,
