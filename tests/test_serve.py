@@ -231,3 +231,17 @@ def test_multi_step_ticks_when_nothing_waits():
     assert multi and all(c[2] <= 8 for c in multi)
     one = serve(requests(rate=50.0, count=40), budget=1 << 60)[0]
     assert sum(1 for c in ex.calls if c[0] == "step") < sum(1 for c in one.calls if c[0] == "step")
+
+
+def test_host_phase_times_add_up_to_at_most_the_wall_time():
+    """The loop reports where its host time went (admission, solves, steps, release, idle); with a
+    simulated clock the phases are non-negative and their sum does not exceed the wall time."""
+    reqs = requests(rate=200.0, count=30)
+    clk = Clock()
+    ex = FakeExecutor(clk, 2e-3)
+    s = Server(ex, 1 << 60, clock=clk, sleep=clk.sleep).run(reqs)
+    ph = s["host_phases"]
+    keys = ("admit_s", "solve_s", "step_s", "release_s", "idle_s")
+    assert all(ph[k] >= 0.0 for k in keys)
+    assert ph["step_s"] > 0.0 and ph["solve_s"] > 0.0
+    assert sum(ph[k] for k in keys) <= s["wall_s"] + 1e-9
