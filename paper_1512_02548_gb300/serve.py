@@ -47,9 +47,9 @@ class GpuExecutor:
     solo_nodes (off by default): a tick's requests of at least that many nodes, and a tick's only
     request, run on their mesh's own single-instance path (sem_rk4_step / sem_laplace_solve: one
     fused launch per RK stage over all SMs), one after another, and the rest as one batch.
-    Measured on the C5 stream with solo_nodes = 50 000, it raised the p99 latency at 100 requests/s
-    (298 against 217 ms) and cut the throughput at 1000 requests/s (1.32× instead of 2.38× the
-    sequential FP64 path): the requests run alone no longer overlap with the batch."""
+    Measured on the C5 stream (two runs each, host tables warm), solo_nodes = 50 000 raised the p99
+    latency at 100 requests/s (228–236 against 181–200 ms) and cut the throughput at 1000 requests/s
+    (153 against 272 M DOF/s): the requests run alone no longer overlap with the batch."""
 
     def __init__(self, precision: str = "mixed", device: str = "cuda:0", tol: float | None = None,
                  solo_nodes: int | None = None):
@@ -83,6 +83,20 @@ class GpuExecutor:
                               wl.filter_ic, wl.g, tol=self.tol, precision=self.precision)
         state = 2 * wl.ncol + (wl.n_nodes if req.kind == "laplace" else 0)
         return sem.mesh_footprint(prm, wl.element_edges(), self._h(wl)) + 8 * state
+
+    def warm(self, requests) -> int:
+        """Build the per-process host tables of every (order, layers, over-integration order,
+        filter) combination among `requests` (a server's start-up step): the first mesh of a
+        combination otherwise builds them at admission, in long double, which stalls the loop for
+        up to tens of milliseconds on some hosts.  Returns the number of combinations."""
+        seen = set()
+        for r in requests:
+            wl = r.wl
+            key = (wl.P, wl.Nz, wl.Pf, wl.filter_alpha, wl.filter_s, wl.filter_ic)
+            if key not in seen:
+                seen.add(key)
+                self.footprint(r)
+        return len(seen)
 
     def admit(self, req: Request):
         torch, wl = self.torch, req.wl

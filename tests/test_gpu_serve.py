@@ -123,3 +123,9 @@ def test_nonfinite_request_run_alone_fails_alone(reqs_and_alone):
     s = Server(ex, hbm_budget=8 << 30).run(served)
     assert bad.error == "error code 5" and s["failed"] == 1
     check([r for r in served if r is not bad], alone, 1e-10)
+
+
+def test_warm_builds_each_table_combination_once(reqs_and_alone):
+    reqs, _ = reqs_and_alone
+    combos = {(r.wl.P, r.wl.Nz, r.wl.Pf, r.wl.filter_alpha, r.wl.filter_s, r.wl.filter_ic) for r in reqs}
+    assert GpuExecutor("mixed").warm(reqs) == len(combos)
