@@ -531,20 +531,37 @@ static __device__ __forceinline__ bool is_halo_col(const DevGeom& g, const Range
   return a == g.P && ex == R.e1 - 1 && !owns_local_col(g, ex, g.P);
 }
 
-// Σ_j a[j·sa] b[j] over j < n with four partial sums (j mod 4), added pairwise at the end: four
-// short dependent chains instead of one of length n.
+// o[q] = Σ_j M[j·nr + c0 + q] x[j], j < nr, for four consecutive columns c0..c0+3 of the nr×nr
+// matrix M: each x[j] is loaded once for the four, and when nr is a multiple of 4 the four M
+// values are one 16-byte load (the rows are then 16-byte aligned).  Columns past nr are read at
+// nr − 1 and their sums are meaningless (the caller drops them).  One chain per column, j in order.
 template <class TP>
-__device__ __forceinline__ TP dot4(const TP* a, int sa, const TP* b, int n) {
-  TP v0 = TP(0), v1 = TP(0), v2 = TP(0), v3 = TP(0);
-  int j = 0;
-  for (; j + 4 <= n; j += 4) {
-    v0 = fmx(a[j * sa], b[j], v0);
-    v1 = fmx(a[(j + 1) * sa], b[j + 1], v1);
-    v2 = fmx(a[(j + 2) * sa], b[j + 2], v2);
-    v3 = fmx(a[(j + 3) * sa], b[j + 3], v3);
+__device__ __forceinline__ void dot_cols4(const TP* M, int nr, int c0, const TP* x, TP (&o)[4]) {
+  o[0] = o[1] = o[2] = o[3] = TP(0);
+  if constexpr (sizeof(TP) == 4) {
+    if ((nr & 3) == 0) {
+      const float4* M4 = reinterpret_cast<const float4*>(M + c0);
+      const int s4 = nr >> 2;
+      for (int j = 0; j < nr; ++j) {
+        const float4 m = M4[j * s4];
+        const float xj = x[j];
+        o[0] = fmaf(m.x, xj, o[0]);
+        o[1] = fmaf(m.y, xj, o[1]);
+        o[2] = fmaf(m.z, xj, o[2]);
+        o[3] = fmaf(m.w, xj, o[3]);
+      }
+      return;
+    }
   }
-  for (; j < n; ++j) v0 = fmx(a[j * sa], b[j], v0);
-  return (v0 + v1) + (v2 + v3);
+  const int c1 = min(c0 + 1, nr - 1), c2 = min(c0 + 2, nr - 1), c3 = min(c0 + 3, nr - 1);
+  for (int j = 0; j < nr; ++j) {
+    const TP* Mj = M + j * nr;
+    const TP xj = x[j];
+    o[0] = fmx(Mj[c0], xj, o[0]);
+    o[1] = fmx(Mj[c1], xj, o[1]);
+    o[2] = fmx(Mj[c2], xj, o[2]);
+    o[3] = fmx(Mj[c3], xj, o[3]);
+  }
 }
 
 // Update of the Chronopoulos–Gear recurrences on owned nodes (and, for r, on the halo column),
@@ -631,13 +648,22 @@ __device__ void cg_update(const DevGeom& g, Smem<P, T>& s, const Range& R, const
     if (precond == PREC_JACOBI) continue;
     __syncthreads();
     SEM_MARK(g, tm, TR_UPD_VEC);
-    for (int t = threadIdx.x; t < ne * qn; t += blockDim.x) {
-      const int e = g.dv_qn.div(t), rem = t - e * qn;
-      const int a = g.dv_nr.div(rem), k = rem - a * nr, ex = ex0 + e;
-      const TP* Xa = X + e * qn + a * nr;
-      const TP v = dot4<TP>(pv.S + k, nr, Xa, nr);
-      RH[t] = v;
-      if (owns_local_col(g, ex, a)) pv.rhat[(size_t)col_of(g, ex, a) * nr + k] = v;
+    // r̂ = Sᵀ r per element-local column, four modes per thread
+    const int nq = (nr + 3) >> 2;
+    for (int t = threadIdx.x; t < ne * Q * nq; t += blockDim.x) {
+      const int ea = t / nq, k0 = (t - ea * nq) * 4;
+      const int e = ea / Q, a = ea - e * Q, ex = ex0 + e;
+      TP v[4];
+      dot_cols4<TP>(pv.S, nr, k0, X + e * qn + a * nr, v);
+      const bool own = owns_local_col(g, ex, a);
+      TP* rh = pv.rhat + (size_t)col_of(g, ex, a) * nr;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int k = k0 + q;
+        if (k >= nr) break;
+        RH[e * qn + a * nr + k] = v[q];
+        if (own) rh[k] = v[q];
+      }
     }
     __syncthreads();
     SEM_MARK(g, tm, TR_UPD_SIGMA);
@@ -740,16 +766,24 @@ __device__ void phase_backsub(const DevGeom& g, Smem<P, T>& s, const Range& R, c
     }
     __syncthreads();
     SEM_MARK(g, tm, TR_BS_INTERIOR);
-    for (int t = threadIdx.x; t < ne * qn; t += blockDim.x) {
-      const int e = g.dv_qn.div(t), rem = t - e * qn;
-      const int a = g.dv_nr.div(rem), j = rem - a * nr, ex = ex0 + e;
+    // u = S ẑ per element-local column, four rows per thread (threads of consecutive row quads
+    // read consecutive words of Sᵀ)
+    const int nq = (nr + 3) >> 2;
+    for (int t = threadIdx.x; t < ne * Q * nq; t += blockDim.x) {
+      const int ea = t / nq, j0 = (t - ea * nq) * 4;
+      const int e = ea / Q, a = ea - e * Q, ex = ex0 + e;
       const bool own = owns_local_col(g, ex, a);
       const bool halo = is_halo_col(g, R, ex, a);
       if (!own && !halo) continue;
-      const TP* Za = ZH + e * qn + a * nr;
-      const TP v = dot4<TP>(pv.ST + j, nr, Za, nr);   // threads of consecutive j read consecutive words
-      if (own) V.u[(size_t)col_of(g, ex, a) * nrow + j] = (T)v;
-      else V.uh[(size_t)tm.rank * nrow + j] = (T)v;
+      TP v[4];
+      dot_cols4<TP>(pv.ST, nr, j0, ZH + e * qn + a * nr, v);
+      T* dst = own ? V.u + (size_t)col_of(g, ex, a) * nrow : V.uh + (size_t)tm.rank * nrow;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int j = j0 + q;
+        if (j >= nr) break;
+        dst[j] = (T)v[q];
+      }
     }
     __syncthreads();
     SEM_MARK(g, tm, TR_BS_SIGMA);
