@@ -717,7 +717,7 @@ __device__ void phase_interface(const DevGeom& g, const PrecView<T>& pv, const T
 
 // Back-substitution of the element interiors, then u = S ẑ on owned columns and on the halo
 // column (whose modal values are interface unknowns, known to every CTA after the solve).
-template <int P, class T, class TP, bool ILP = false>
+template <int P, class T, class TP>
 __device__ void phase_backsub(const DevGeom& g, Smem<P, T>& s, const Range& R, const Team& tm,
                               const PrecView<TP>& pv, const CgVecs<T>& V) {
   constexpr int Q = P + 1, Pm = P - 1;
@@ -726,42 +726,55 @@ __device__ void phase_backsub(const DevGeom& g, Smem<P, T>& s, const Range& R, c
   const int E = g.chunk, qn = Q * nr;
   for (int ex0 = R.e0; ex0 < R.e1; ex0 += E) {
     const int ne = min(E, R.e1 - ex0);
-    // (ILP: two items per thread and pass, their interface values loaded together)
-    constexpr int UB = ILP ? 2 : 1;
-    const int nt = ne * qn;
-    for (int t0 = threadIdx.x; t0 < nt; t0 += UB * blockDim.x) {
-      TP zl[UB], zr[UB];
-      int kk[UB], aa[UB], ee[UB];
-#pragma unroll
-      for (int q = 0; q < UB; ++q) {
-        const int t = t0 + q * blockDim.x;
-        if (t >= nt) continue;
+    // chunks with few (element, mode) pairs (under a quarter of the threads; a one-element chunk of a
+    // C2-like column): one (element, column, mode) per thread
+    const bool by_row = ne * nr * 4 < (int)blockDim.x;
+    if (by_row) {
+      for (int t = threadIdx.x; t < ne * qn; t += blockDim.x) {
         const int e = g.dv_qn.div(t), rem = t - e * qn;
         const int a = g.dv_nr.div(rem), k = rem - a * nr, ex = ex0 + e;
-        const int jl = ex, jr = (ex + 1 == N) ? 0 : ex + 1;
-        zl[q] = ldcg(pv.zb + (size_t)k * N + jl);
-        zr[q] = ldcg(pv.zb + (size_t)k * N + jr);
-        kk[q] = k; aa[q] = a; ee[q] = ex;
-      }
-#pragma unroll
-      for (int q = 0; q < UB; ++q) {
-        const int t = t0 + q * blockDim.x;
-        if (t >= nt) continue;
-        const int a = aa[q], k = kk[q], ex = ee[q];
         TP v;
-        if (a == 0) v = zl[q];
-        else if (a == P) v = zr[q];
+        if (a == 0) v = ldcg(pv.zb + (size_t)k * N + ex);
+        else if (a == P) v = ldcg(pv.zb + (size_t)k * N + ((ex + 1 == N) ? 0 : ex + 1));
         else {
           const int i = a - 1;
+          const TP zl = ldcg(pv.zb + (size_t)k * N + ex);
+          const TP zr = ldcg(pv.zb + (size_t)k * N + ((ex + 1 == N) ? 0 : ex + 1));
           const TP* Ai = pv.Aii + ((size_t)ex * Pm + i) * Pm * nr + k;   // Ai[m·nr]
           const TP* Zl = pv.Z + (size_t)ex * 2 * Pm * nr + k;
           v = 0;
 #pragma unroll
           for (int m = 0; m < Pm; ++m) v = fmx(Ai[m * nr], pv.rhat[(size_t)(ex * P + 1 + m) * nr + k], v);
-          v = fmx(-Zl[i * nr], zl[q], v);
-          v = fmx(-Zl[(Pm + i) * nr], zr[q], v);
+          v = fmx(-Zl[i * nr], zl, v);
+          v = fmx(-Zl[(Pm + i) * nr], zr, v);
         }
         ZH[t] = v;
+      }
+    }
+    // otherwise one (element, mode) per thread: the element's interior values of the mode from
+    // the condensed residual and the two interface values, each loaded once for all P−1 rows
+    // (the same sums in the same order either way)
+    for (int t = threadIdx.x; !by_row && t < ne * nr; t += blockDim.x) {
+      const int e = g.dv_nr.div(t), k = t - e * nr, ex = ex0 + e;
+      const int jr = (ex + 1 == N) ? 0 : ex + 1;
+      const TP zl = ldcg(pv.zb + (size_t)k * N + ex);
+      const TP zr = ldcg(pv.zb + (size_t)k * N + jr);
+      TP rh[Pm];
+#pragma unroll
+      for (int m = 0; m < Pm; ++m) rh[m] = pv.rhat[(size_t)(ex * P + 1 + m) * nr + k];
+      TP* zh = ZH + e * qn + k;
+      zh[0] = zl;
+      zh[P * nr] = zr;
+      const TP* Zl = pv.Z + (size_t)ex * 2 * Pm * nr + k;
+#pragma unroll
+      for (int i = 0; i < Pm; ++i) {
+        const TP* Ai = pv.Aii + ((size_t)ex * Pm + i) * Pm * nr + k;   // Ai[m·nr]
+        TP v = 0;
+#pragma unroll
+        for (int m = 0; m < Pm; ++m) v = fmx(Ai[m * nr], rh[m], v);
+        v = fmx(-Zl[i * nr], zl, v);
+        v = fmx(-Zl[(Pm + i) * nr], zr, v);
+        zh[(1 + i) * nr] = v;
       }
     }
     __syncthreads();
@@ -802,7 +815,7 @@ __device__ bool finish_precondition(const DevGeom& g, Smem<P, T>& s, const Range
   SEM_MARK(g, tm, TR_IT_INTERFACE);
   if (!grid_barrier(tm, s_flag)) return false;
   SEM_MARK(g, tm, TR_IT_BAR3);
-  phase_backsub<P, T, TP, CACHE>(g, s, R, tm, pv, V);
+  phase_backsub<P, T, TP>(g, s, R, tm, pv, V);
   return true;
 }
 
