@@ -226,12 +226,16 @@ __device__ void fill_gcache(const DevGeom& g, int e0, int e1, double* gc) {
 
 // gc (FP64 only, optional): the chunk's geometric factors from fill_gcache, used instead of
 // staging the geometry and recomputing them.
-template <int P, class T, class LoadX, class Store>
+// TOP: only the top element layer (an input that is zero below the surface row, whose image is zero
+// below the top layer's lowest row): rows under that row get no store.
+template <int P, class T, bool TOP = false, class LoadX, class Store>
 __device__ __forceinline__ T apply_element_chunk(const DevGeom& g, Smem<P, T>& s, int ex0, int ne,
                                                  LoadX loadx, Store store, const double* gc = nullptr) {
   constexpr int Q = P + 1;
   const int nrow = g.nrow, Nz = g.Nz;
   const int colsz = Q * nrow, elsz = Nz * Q * Q;
+  const int l_first = TOP ? Nz - 1 : 0;   // first layer computed
+  const int nl = Nz - l_first;
   if (gc == nullptr) {
     const T* geo = geo_ptr<T>(g) + (size_t)ex0 * Q * 4;
     for (int t = threadIdx.x; t < ne * 4 * Q; t += blockDim.x) s.geo[t] = geo[t];
@@ -244,7 +248,12 @@ __device__ __forceinline__ T apply_element_chunk(const DevGeom& g, Smem<P, T>& s
     s.X[t] = loadx(ex0 + e, a, iz);
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < ne * elsz; t += blockDim.x) {
+  for (int tt = threadIdx.x; tt < ne * nl * Q * Q; tt += blockDim.x) {
+    int t = tt;
+    if constexpr (TOP) {   // layer l_first of element e: its items in the full numbering
+      const int e = tt / (Q * Q);
+      t = e * elsz + l_first * Q * Q + (tt - e * Q * Q);
+    }
     const int e = g.dv_elsz.div(t), rem0 = t - e * elsz;
     const int l = rem0 / (Q * Q), rem = rem0 - l * (Q * Q), a = rem / Q, b = rem - a * Q;
     const T* Xe = s.X + e * colsz;
@@ -277,6 +286,7 @@ __device__ __forceinline__ T apply_element_chunk(const DevGeom& g, Smem<P, T>& s
     const int e = g.dv_colsz.div(t), rem = t - e * colsz;
     const int a = g.dv_nrow.div(rem), iz = rem - a * nrow;
     const int l = iz / P, b = iz - l * P;
+    if (TOP && l < l_first) continue;
     const T* F1e = s.F1 + e * elsz;
     const T* F2e = s.F2 + e * elsz;
     T y = 0;
@@ -289,7 +299,7 @@ __device__ __forceinline__ T apply_element_chunk(const DevGeom& g, Smem<P, T>& s
         y = fmx(s.D[c * Q + b], F2[c], y);
       }
     }
-    if (b == 0 && l > 0) {
+    if (b == 0 && l > l_first) {
       const int lm = l - 1;
       const T* F1 = F1e + (lm * Q) * Q + P;
       const T* F2 = F2e + (lm * Q + a) * Q;
@@ -958,8 +968,10 @@ __device__ bool fp64_residual(const DevGeom& g, Smem<P, double>& s, const Range&
     Smem<P, float> s32;
     s32.carve(reinterpret_cast<unsigned char*>(s.D), nrow, g.Nz, g.chunk);
     s32.load_tables(g);
+    // only the top element layer: [0; φ̃] is zero below the surface row, and the rows below the top
+    // layer keep the zeros they were created with
     for (int ex0 = R.e0; ex0 < R.e1; ex0 += g.chunk)
-      apply_element_chunk<P, float>(
+      apply_element_chunk<P, float, true>(
           g, s32, ex0, min(g.chunk, R.e1 - ex0),
           [&](int e, int a, int iz) -> float { return iz == nrow - 1 ? (float)phis[col_of(g, e, a)] : 0.f; },
           [&](int e, int a, int iz, float y) {
