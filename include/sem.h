@@ -307,8 +307,10 @@ typedef struct sem_batch_tuning {
 } sem_batch_tuning;
 int sem_set_batch_tuning(const sem_batch_tuning* t);
 int sem_get_batch_tuning(sem_batch_tuning* t);
-/* Tile width (elements per tile, 1..16) of the tiled apply for order P and Nz layers, as measured by
- * the autotuner; 0 restores the default (the widest tile that keeps three CTAs per SM).  Process-wide. */
+/* Tile width (elements per tile, 1..16) of the FP32 tiled apply (sem_laplace_apply_f32, CUDA-core
+ * kernel) for order P and Nz layers, as measured by the autotuner; 0 restores the default (the widest
+ * tile up to 16 that keeps three CTAs per SM).  The FP64 apply takes the widest tile up to 16 that
+ * fits in shared memory.  Process-wide. */
 int sem_set_apply_tile_width(int P, int Nz, int E);
 
 /* Per-instance result of the last sem_batch_rk4_step or sem_batch_laplace_solve:

@@ -231,6 +231,8 @@ class Mesh:
                  precond: str = "separable", relax_left: float = 0.0, relax_right: float = 0.0,
                  relax_tau: float = 0.0, wave=None):
         lib = load_library()
+        from .autotune import apply_tuning
+        apply_tuning(batch=False)   # the measured tile widths of the tiled apply, once per process
         prm = mesh_params(P, Nx, Nz, periodic, Pf, filter_alpha, filter_s, filter_ic, g, tol, max_iter, precision,
                           precond, relax_left, relax_right, relax_tau)
         xe = np.ascontiguousarray(x_edges, dtype=np.float64)
@@ -366,7 +368,7 @@ class Batch:
         lib = load_library()
         if tuned:
             from .autotune import apply_tuning
-            apply_tuning()
+            apply_tuning(tiles=False)
         self.meshes = list(meshes)
         arr = (ctypes.c_void_p * len(self.meshes))(*[m._h.value for m in self.meshes])
         handle = ctypes.c_void_p()

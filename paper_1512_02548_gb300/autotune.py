@@ -11,12 +11,15 @@ It measures, with CUDA events on the launching stream,
   tuned on), for every candidate of the batch planning parameters of ``sem_set_batch_tuning``:
   the cluster team share, the largest cluster and the group size up to which the one-CTA-per-SM
   build is used; the candidate with the smallest summed step time wins;
-* the FP32 tiled apply on a long periodic tank for every order P = 2..12, layer count Nz = 1, 2, 4
-  and tile width E = 1, 2, 4, 8, 16 that fits in shared memory; the fastest width per (P, Nz) wins;
+* the FP32 tiled apply on a long periodic tank of about 9.8 M nodes (above the L2, flushed before
+  each timed apply) for every order P = 2..12, layer count Nz = 1, 2, 4 and tile width E = 1..16
+  that fits in shared memory; the fastest width per (P, Nz) wins (the FP64 apply keeps its rule);
 
-and writes the winners with every measurement to ``tuning.json`` next to this file (or PATH).
-:func:`apply_tuning` reads that file once per process and hands the winners to the library, if
-it was measured on a GPU of the same name; ``Batch`` calls it before its first batch.  Results do
+and writes the winners with every measurement to ``tuning.json`` next to this file (or PATH);
+``--apply-only`` re-measures the tile widths alone and keeps the file's batch section.
+:func:`apply_tuning` reads that file and hands the winners to the library, if it was measured on
+a GPU of the same name, each part once per process: ``Batch`` applies the batch parameters before
+its first batch and ``Mesh`` the tile widths when the first mesh is created.  Results do
 not depend on the tuning (team sizes and tile widths change only the summation order within each
 team's reductions), which ``tests/test_gpu_autotune.py`` checks.
 """
@@ -32,16 +35,17 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 TUNING_PATH = os.path.join(HERE, "tuning.json")
-_applied = False
+_applied: set = set()
 
 
-def apply_tuning(path: str = TUNING_PATH) -> dict | None:
-    """Hand the measured winners in `path` to the library (once per process); None if there is
-    no file or it was measured on another GPU."""
-    global _applied
-    if _applied:
+def apply_tuning(path: str = TUNING_PATH, batch: bool = True, tiles: bool = True) -> dict | None:
+    """Hand the measured winners in `path` to the library: the batch planning parameters and/or
+    the tile widths, each at most once per process; None if there is no file or it was measured on
+    another GPU."""
+    parts = [p for p, on in (("batch", batch), ("tiles", tiles)) if on and p not in _applied]
+    if not parts:
         return None
-    _applied = True
+    _applied.update(parts)
     if not os.path.exists(path):
         return None
     import torch
@@ -49,12 +53,14 @@ def apply_tuning(path: str = TUNING_PATH) -> dict | None:
     data = json.load(open(path))
     if not torch.cuda.is_available() or data.get("device") != torch.cuda.get_device_name(0):
         return None
-    b = data["batch"]
-    set_batch_tuning(cluster_share=b["cluster_share"], max_cluster=b["max_cluster"], narrow_max=b["narrow_max"],
-                     plan=b["plan"])
-    for key, E in data.get("apply_tile_width", {}).items():
-        P, Nz = (int(v) for v in key.split(","))
-        set_apply_tile_width(P, Nz, E)
+    if "batch" in parts:
+        b = data["batch"]
+        set_batch_tuning(cluster_share=b["cluster_share"], max_cluster=b["max_cluster"],
+                         narrow_max=b["narrow_max"], plan=b["plan"])
+    if "tiles" in parts:
+        for key, E in data.get("apply_tile_width", {}).items():
+            P, Nz = (int(v) for v in key.split(","))
+            set_apply_tile_width(P, Nz, E)
     return data
 
 
@@ -121,11 +127,14 @@ def tune_batch(dev, count: int = 512, seed: int = 1, steps: int = 3, quick: bool
     return {k: best[k] for k in ("cluster_share", "max_cluster", "narrow_max", "plan")}, rows
 
 
-def tune_apply(dev, nodes: float = 4e6, reps: int = 5, quick: bool = False):
+def tune_apply(dev, nodes: float = 9.8e6, reps: int = 7, quick: bool = False):
+    """FP32 tile widths on long tanks of about `nodes` nodes (x and y above the L2), the L2 flushed
+    before each timed apply, median of `reps`."""
     import torch
     from . import Mesh, set_apply_tile_width
     from sem_workloads import roofline_tank
     winners, rows = {}, []
+    flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)   # 256 MB, above the L2
     orders = (4, 6, 8) if quick else range(2, 13)
     for P in orders:
         for Nz in (1, 2, 4):
@@ -136,7 +145,7 @@ def tune_apply(dev, nodes: float = 4e6, reps: int = 5, quick: bool = False):
             x = torch.randn(mesh.n, dtype=torch.float32, device=dev)
             y = torch.empty_like(x)
             best = None
-            for E in (1, 2, 4, 8, 16):
+            for E in range(1, 17):
                 set_apply_tile_width(P, Nz, E)
                 try:
                     for _ in range(2):
@@ -146,6 +155,7 @@ def tune_apply(dev, nodes: float = 4e6, reps: int = 5, quick: bool = False):
                 torch.cuda.synchronize()
                 ts = []
                 for _ in range(reps):
+                    flush.zero_()
                     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                     e0.record()
                     mesh.laplace_apply_f32(x, y)
@@ -169,11 +179,17 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", default=TUNING_PATH)
     ap.add_argument("--quick", action="store_true", help="fewer candidates (for tests)")
+    ap.add_argument("--apply-only", action="store_true",
+                    help="re-measure the tile widths only; keep the batch section of the existing file")
     args = ap.parse_args()
     load_library()
     dev = torch.device("cuda", 0)
     t0 = time.time()
-    batch, batch_rows = tune_batch(dev, quick=args.quick)
+    if args.apply_only:
+        old = json.load(open(args.out))
+        batch, batch_rows = old["batch"], old["measured"]["batch"]
+    else:
+        batch, batch_rows = tune_batch(dev, quick=args.quick)
     tiles, tile_rows = tune_apply(dev, quick=args.quick)
     out = {"device": torch.cuda.get_device_name(0), "when": time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime()),
            "batch": batch, "apply_tile_width": tiles,

@@ -1819,7 +1819,8 @@ cudaError_t launch_stage_cluster_impl(int mixed, int wide, const StageArgs& a, i
 }
 
 // Tiled apply (apply_tile.cuh): widest tile of at most 16 elements whose shared memory keeps
-// three CTAs per SM; persistent CTAs (at most the co-resident count) stride over the tiles.
+// three CTAs per SM (FP32; the measured width where one is set) or fits at all (FP64, one CTA per
+// SM); persistent CTAs (at most the co-resident count) stride over the tiles.
 // The tensor-core FP32 kernel (apply_tc.cuh, fp32 = 3, orders 4..7) takes tiles of 64/Nz − 1
 // elements: with the recomputed left neighbour, 64 element blocks, four block pairs per warp.
 constexpr size_t kTileSmemTarget = 76 * 1024;
@@ -1883,9 +1884,11 @@ cudaError_t launch_apply_tile_impl(int fp32, const DevGeom& g, const void* x, vo
     }
   }
   const size_t elem = fp32 ? sizeof(float) : sizeof(double);
+  // the FP64 kernel holds one CTA per SM (its registers), so only the shared-memory maximum caps it
+  const size_t cap = fp32 ? kTileSmemTarget : (size_t)kMaxDynSmem;
   int E = 16;
-  while (E > 1 && apply_tile_smem<P>(E, g.nrow, g.Nz, elem) > kTileSmemTarget) E >>= 1;
-  const int Et = apply_tile_width(P, g.Nz);   // a measured width (autotuner), if one is set
+  while (E > 1 && apply_tile_smem<P>(E, g.nrow, g.Nz, elem) > cap) E >>= 1;
+  const int Et = fp32 ? apply_tile_width(P, g.Nz) : 0;   // a measured FP32 width (autotuner), if set
   if (Et > 0 && apply_tile_smem<P>(Et, g.nrow, g.Nz, elem) <= (size_t)kMaxDynSmem) E = Et;
   const size_t smem = apply_tile_smem<P>(E, g.nrow, g.Nz, elem);
   if (smem > (size_t)kMaxDynSmem) return cudaErrorInvalidValue;
