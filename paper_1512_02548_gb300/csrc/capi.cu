@@ -665,9 +665,20 @@ static int mesh_create_impl(const sem_params* pin, const double* x_edges_h, cons
 
   Carve cv;
   const size_t nE = (size_t)Nx * nrow;
+  // the arrays filled on the host come first: one copy uploads all of them ([0, up_end) of the block)
   const size_t o_cxz = cv.take<double>((size_t)Nx * Nz * 2), o_r2dx = cv.take<double>(Nx);
   const size_t o_h = cv.take<double>(ncol), o_hx = cv.take<double>((size_t)Nx * Q), o_dxe = cv.take<double>(Nx),
-               o_dsl = cv.take<double>(Nz), o_sig = cv.take<double>(nrow), o_geo64 = cv.take<double>((size_t)Nx * Q * 4),
+               o_dsl = cv.take<double>(Nz), o_sig = cv.take<double>(nrow);
+  const size_t o_S32 = cv.take<float>((size_t)nr * nr), o_ST32 = cv.take<float>((size_t)nr * nr),
+               o_lam = cv.take<double>(nr), o_xcol = cv.take<double>(ncol);
+  // surface tables
+  const size_t o_tD = cv.take<double>(Q * Q), o_tMD = cv.take<double>(Q * Q), o_tB = cv.take<double>((size_t)Q * Qf),
+               o_tI = cv.take<double>((size_t)Qf * Q), o_tF = cv.take<double>(Q * Q), o_twr = cv.take<double>((size_t)nrow),
+               o_tAii = cv.take<double>((size_t)Pm * Pm + 1), o_tZ = cv.take<double>((size_t)2 * Pm + 1),
+               o_tse = cv.take<double>(Nx), o_te = cv.take<double>(N), o_tm = cv.take<double>(N),
+               o_tcp = cv.take<double>(N), o_tz = cv.take<double>(N);
+  const size_t up_end = cv.off;
+  const size_t o_geo64 = cv.take<double>((size_t)Nx * Q * 4),
                o_geo32 = cv.take<float>((size_t)Nx * Q * 4), o_id64 = cv.take<double>(n), o_id32 = cv.take<float>(n),
                o_status = cv.take<int>(4), o_rec = cv.take<SolveRecord>(1), o_bar = cv.take<unsigned>(4),
                o_part = cv.take<double>((size_t)16 * m->grid);
@@ -682,15 +693,14 @@ static int mesh_create_impl(const sem_params* pin, const double* x_edges_h, cons
   const size_t o_s64b = cv.take<double>(n), o_s32b = cv.take<float>(n);
   const size_t o_uh64 = cv.take<double>((size_t)m->grid * nrow), o_uh32 = cv.take<float>((size_t)m->grid * nrow);
   const size_t nEl = (size_t)nr * Nx, nIf = (size_t)nr * N;
-  const size_t o_S32 = cv.take<float>((size_t)nr * nr), o_ST32 = cv.take<float>((size_t)nr * nr),
-               o_lam = cv.take<double>(nr), o_schur = cv.take<double>(nEl * 3),
+  const size_t o_schur = cv.take<double>(nEl * 3),
                o_A32 = cv.take<float>(nEl * Pm * Pm + 1), o_Z32 = cv.take<float>(nEl * 2 * Pm + 1),
                o_te32 = cv.take<float>(nIf), o_tm32 = cv.take<float>(nIf),
                o_tcp32 = cv.take<float>(nIf), o_tz32 = cv.take<float>(nIf),
                o_tvl32 = cv.take<float>(nr), o_tfac32 = cv.take<float>(nr),
                o_gL32 = cv.take<float>(nEl), o_gR32 = cv.take<float>(nEl), o_zb32 = cv.take<float>(nIf),
                o_rh32 = cv.take<float>((size_t)ncol * nr);
-  const size_t o_xcol = cv.take<double>(ncol), o_wave = cv.take<double>(4 * kMaxWaveComp);
+  const size_t o_wave = cv.take<double>(4 * kMaxWaveComp);
   const bool zones = p.relax_left > 0.0 || p.relax_right > 0.0;
   const size_t o_wA = cv.take<double>(zones ? 4 * kMaxWaveComp : 0), o_wEP = cv.take<double>(zones ? 2 * ncol : 0);
   const size_t o_wt = cv.take<double>(ncol), o_etax = cv.take<double>(ncol), o_phisx = cv.take<double>(ncol),
@@ -703,12 +713,6 @@ static int mesh_create_impl(const sem_params* pin, const double* x_edges_h, cons
                o_D32 = cv.take<double>(n);
   const size_t o_gglob = cv.take<double>((size_t)3 * Nx * Nz * Q * Q);
   const size_t o_inst = cv.take<Instance>(1), o_ctai = cv.take<int>((size_t)m->grid), o_sbar = cv.take<unsigned>(4);
-  // surface tables
-  const size_t o_tD = cv.take<double>(Q * Q), o_tMD = cv.take<double>(Q * Q), o_tB = cv.take<double>((size_t)Q * Qf),
-               o_tI = cv.take<double>((size_t)Qf * Q), o_tF = cv.take<double>(Q * Q), o_twr = cv.take<double>((size_t)nrow),
-               o_tAii = cv.take<double>((size_t)Pm * Pm + 1), o_tZ = cv.take<double>((size_t)2 * Pm + 1),
-               o_tse = cv.take<double>(Nx), o_te = cv.take<double>(N), o_tm = cv.take<double>(N),
-               o_tcp = cv.take<double>(N), o_tz = cv.take<double>(N);
   const size_t total = cv.off + 256;
   if (footprint_only) {
     *footprint_only = total;
@@ -721,14 +725,14 @@ static int mesh_create_impl(const sem_params* pin, const double* x_edges_h, cons
   auto D_ = [&](size_t o) { return reinterpret_cast<double*>(m->pool + o); };
   auto F_ = [&](size_t o) { return reinterpret_cast<float*>(m->pool + o); };
   int code = SEM_OK;
+  // host image of [0, up_end): the arrays are written into it and go up in one copy (zero padding
+  // between them); the rest of the block is zeroed on the device
+  std::vector<unsigned char> stage(up_end, 0);
   auto up = [&](size_t o, const std::vector<double>& v) {
-    if (code == SEM_OK && !v.empty()) {
-      cudaError_t e = cudaMemcpy(m->pool + o, v.data(), v.size() * sizeof(double), cudaMemcpyHostToDevice);
-      if (e != cudaSuccess) code = fail(SEM_ERR_CUDA, std::string("upload: ") + cudaGetErrorString(e));
-    }
+    if (!v.empty()) std::memcpy(stage.data() + o, v.data(), v.size() * sizeof(double));
   };
   {
-    cudaError_t e = cudaMemset(m->pool, 0, total);
+    cudaError_t e = cudaMemset(m->pool + up_end, 0, total - up_end);
     if (e != cudaSuccess) code = fail(SEM_ERR_CUDA, std::string("memset: ") + cudaGetErrorString(e));
   }
   up(o_h, std::vector<double>(h_h, h_h + ncol));
@@ -757,13 +761,15 @@ static int mesh_create_impl(const sem_params* pin, const double* x_edges_h, cons
     up(o_xcol, xc);
     m->xcol_h = xc;
   }
-  if (code == SEM_OK) {
+  {
     std::vector<float> S32(Sg.begin(), Sg.end()), ST32(S32.size());
     for (int j = 0; j < nr; ++j)
       for (int k = 0; k < nr; ++k) ST32[(size_t)k * nr + j] = S32[(size_t)j * nr + k];
-    cudaError_t e = cudaMemcpy(m->pool + o_S32, S32.data(), S32.size() * sizeof(float), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-      e = cudaMemcpy(m->pool + o_ST32, ST32.data(), ST32.size() * sizeof(float), cudaMemcpyHostToDevice);
+    std::memcpy(stage.data() + o_S32, S32.data(), S32.size() * sizeof(float));
+    std::memcpy(stage.data() + o_ST32, ST32.data(), ST32.size() * sizeof(float));
+  }
+  if (code == SEM_OK) {
+    cudaError_t e = cudaMemcpy(m->pool, stage.data(), up_end, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) code = fail(SEM_ERR_CUDA, std::string("upload: ") + cudaGetErrorString(e));
   }
   if (code != SEM_OK) { dev_free(dev, m->pool); delete m; return code; }
