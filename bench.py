@@ -5,8 +5,9 @@ independent periodic tanks from seed 0 (Nx ∈ [16,128], Nz ∈ {1,2,4}, P ∈ {
 kh ∈ [0.5,3], H/L ∈ [0.01,0.09], 3.18 M Laplace unknowns) — each RK4 step being four
 σ-geometry updates, four Dirichlet-lifted Laplace solves, four gradient recoveries, four
 over-integrated Zakharov right-hand sides, the RK4 combination and the modal filter per tank,
-run as one fused launch per RK stage and (order, precision) group, all in the library's
-CUDA kernels.
+run as one fused launch per RK stage and (order, precision, cluster size) group, the groups on
+concurrent streams, all in the library's CUDA kernels; every solve to the C3 configuration's
+relative residual of 1e-10 (the strict tolerances are reported beside it).
 
 value   = Laplace DOF/s of the batched plain FP64 path = 4 · Σ unknowns · steps / device time;
           the batched mixed-precision path (FP32 inner, FP64 refinement), the same tanks one
@@ -240,6 +241,12 @@ def c3_sample(count: int, seed: int = 7):
     return sorted(range(512), key=lambda i: keys[i])[:count]
 
 
+def c3_unknowns() -> int:
+    """Laplace unknowns of the 512-tank C3 batch (one solve of every tank)."""
+    from sem_workloads import c3_instances
+    return int(sum(wl.n_unknowns for wl in c3_instances(512)))
+
+
 def c3_initial(i: int):
     import numpy as np
     from sem_workloads import c3_instances, initial_state
@@ -287,9 +294,10 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": C3_NAME, "instances": 512, "precision": "fp64",
+        "config": {"workload": C3_NAME, "instances": 512, "n_unknowns": c3_unknowns(), "precision": "fp64",
+                   "tol": "direct banded-Cholesky solves (the oracle)",
                    "step": f"one RK4 step of {cores} of the tanks (seeded rotation) on the CPU oracle",
-                   "parallelism": "replicas"},
+                   "parallelism": "single" if args.gpus == 1 else "replicas"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"{args.steps} steps of {cores} C3 tanks each, one RK4 step (four "
                                    f"banded-Cholesky Laplace solves) per tank, one process per core, "
